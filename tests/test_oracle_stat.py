@@ -1,0 +1,87 @@
+"""Statistical pins of the oracle: Monte Carlo averages against exact
+diagonalisation of the transformed Hamiltonian, symmetries, and the
+autocorrelation estimator against an AR(1) closed form.
+
+Runs are seeded, so each test is deterministic; tolerances are in units of
+the binned standard error.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import analysis as A
+from oracle import ed as E
+from oracle import model as M
+from oracle import oracle as O
+
+
+def _mean_err(x, nb=25):
+    b = np.asarray(x)[: len(x) // nb * nb].reshape(nb, -1).mean(1)
+    return b.mean(), b.std(ddof=1) / math.sqrt(nb)
+
+
+def _compare(geom, size, u, al, beta, dtau, nsw, seed, g=None):
+    m = M.Model(geom, size)
+    ref = E.ED(m, M.couplings(u, al), beta).observables()
+    ch = O.Chain(geom, size, beta, dtau, u, al, seed=seed, n_stab=5, n_adapt=150, g=g, model=m)
+    ch.sweep(150)
+    obs = ch.sweep(nsw)
+    out = {}
+    for name, col, r in [("E", 12, ref["E"]), ("m2", 0, ref["m2"]), ("S1_0", 1, ref["S0"][0]),
+                         ("S3_0", 3, ref["S0"][2]), ("S1_dq", 6, ref["Sdq"][0]), ("S3_dq", 8, ref["Sdq"][2])]:
+        mu, err = _mean_err(obs[:, col])
+        out[name] = (mu - r) / err
+    return out, obs
+
+
+@pytest.mark.parametrize("geom,size,u,al", [(M.TORUS, 2, 4.0, 0.3), (M.SPHERE, 2, 1.0, 0.2)])
+def test_monte_carlo_matches_exact_diagonalisation(geom, size, u, al):
+    dev, obs = _compare(geom, size, u, al, beta=2.0, dtau=0.05, nsw=2500, seed=1)
+    for k, z in dev.items():
+        assert abs(z) < 4.0, (k, z)
+    assert obs[:, 16].max() < 1e-8      # sign monitor
+    assert 0.3 < obs[:, 13].mean() < 0.8
+
+
+def test_planted_coupling_mistake_is_detected():
+    """The ED comparison is sensitive: a chain run with g_3 of the wrong sign
+    (a plausible slip in the Fierz couplings) misses ED by many sigma and also
+    loses the sign-free property."""
+    m = M.Model(M.TORUS, 2)
+    g = M.couplings(4.0, 0.3) * np.array([1, 1, 1, -1])
+    dev, obs = _compare(M.TORUS, 2, 4.0, 0.3, 2.0, 0.1, 1200, 1, g=g)
+    assert abs(dev["E"]) > 20
+    assert obs[:, 16].max() > 1e-3
+
+
+def test_symmetries_so5_line_and_u1_x_su2():
+    """alpha = 0: all five S^i equal within errors (SO(5)); alpha != 0: S^1 =
+    S^2 (valley U(1)), and S^3 = S^4 = S^5 on every configuration."""
+    ch = O.Chain(M.TORUS, 3, 2.0, 0.1, 2.0, 0.0, seed=2, n_adapt=100)
+    ch.sweep(100)
+    obs = ch.sweep(1500)
+    assert np.all(obs[:, 3] == obs[:, 4]) and np.all(obs[:, 4] == obs[:, 5])
+    m1, e1 = _mean_err(obs[:, 1])
+    m3, e3 = _mean_err(obs[:, 3])
+    assert abs(m1 - m3) < 4 * math.hypot(e1, e3)
+    ch = O.Chain(M.TORUS, 3, 2.0, 0.1, 2.0, 0.4, seed=2, n_adapt=100)
+    ch.sweep(100)
+    obs = ch.sweep(1500)
+    m1, e1 = _mean_err(obs[:, 1])
+    m2, e2 = _mean_err(obs[:, 2])
+    assert abs(m1 - m2) < 4 * math.hypot(e1, e2)
+
+
+def test_tau_int_of_ar1_process():
+    rho = 0.8
+    rng = np.random.default_rng(0)
+    n = 200000
+    x = np.empty(n)
+    x[0] = 0
+    e = rng.normal(size=n)
+    for i in range(1, n):
+        x[i] = rho * x[i - 1] + e[i]
+    exact = (1 + rho) / (2 * (1 - rho))
+    assert abs(A.tau_int(x[:20000]) - exact) < 0.15 * exact
+    assert abs(A.tau_int(rng.normal(size=5000)) - 0.5) < 0.1
