@@ -1,0 +1,171 @@
+/*
+ * qmc.h -- C ABI of libqmc, a GB300 (sm_103a) implementation of the
+ * continuous-field determinant QMC (CF-DQMC) sweep for the lowest-Landau-
+ * level-projected SO(5) model with Wess-Zumino-Witten term
+ * (arXiv:2605.03700).
+ *
+ * The library simulates H = sum_{i=0..3} g_i sum_q n^{O^i}_q n^{O^i}_{qbar}
+ * (Methods, Eq. newmodel) with g = (1 + U_N, -(U_K + U_N), -(U_K + U_N),
+ * 2 U_N), U_N = u + alpha/sqrt(2), U_K = u - alpha/sqrt(2) (Results,
+ * "Theoretical model ..." and "Universal phase diagram"), by whole-slice MALA
+ * updates of the continuous Hubbard-Stratonovich field phi^i_{tau,q}
+ * (Methods, "Langevin-based global update scheme"), each accepted by the
+ * exact fermion-determinant ratio.
+ *
+ * Conventions for every entry point:
+ *   - return 0 on success, a negative QMC_ERR_* code on failure; the message
+ *     of the last failure on a context is in qmc_last_error(ctx);
+ *   - pointers named "host" are host memory owned by the caller; the library
+ *     never retains or frees them;
+ *   - all device memory is allocated by qmc_create and released by
+ *     qmc_destroy;
+ *   - work is enqueued on the context's CUDA stream (qmc_set_stream); calls
+ *     that return data to the host synchronise that stream.
+ */
+#ifndef QMC_H
+#define QMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qmc_ctx qmc_ctx;
+
+enum { QMC_TORUS = 0, QMC_SPHERE = 1 };
+
+enum {
+    QMC_OK = 0,
+    QMC_ERR_ARG = -1,       /* invalid argument or unsupported size */
+    QMC_ERR_CUDA = -2,      /* a CUDA call failed */
+    QMC_ERR_OOM = -3,       /* device allocation failed */
+    QMC_ERR_UNSTABLE = -4,  /* G error at a restabilisation above opts.stab_tol */
+    QMC_ERR_SIGN = -5,      /* |sin Im log R| above opts.sign_tol: sign problem */
+    QMC_ERR_NONFINITE = -6, /* a determinant ratio or field became NaN/Inf */
+    QMC_ERR_TIMEOUT = -7    /* a device-side bounded wait gave up */
+};
+
+/* Number of doubles per observable record (qmc_get_series, qmc_measure). */
+#define QMC_NOBS 20
+/* Layout of an observable record (one per chain per sweep):
+ *  0 m2 = sum_{i=1..5} S^i_{q=0} / (5 N_phi^2)      (Results, m^2_SO(5))
+ *  1..5  S^i_{q=0}, i = 1..5                         (S^i_q = <n_q n_qbar>)
+ *  6..10 S^i at the smallest non-zero momenta, averaged (torus: (+-1,0),
+ *        (0,+-1); sphere: l = 1)
+ *  11 R = 1 - S(dq)/S(0), S = sum_i S^i              (Results, correlation ratio)
+ *  12 E = <H> of Eq. newmodel
+ *  13 acceptance rate of the sweep
+ *  14 Langevin step eps used during the sweep
+ *  15 max |G_wrap - G_stable| / max |G_stable| over the sweep's restabilisations
+ *  16 max |sin Im log R| over the sweep (0 for a sign-free weight)
+ *  17 accepted updates in the sweep
+ *  18, 19 reserved (0)
+ */
+
+/* Per-update record of the optional trace (qmc_get_trace), 8 doubles:
+ * sweep, slice (1-based), Re log R, Im log R, log A, log u, accepted, eps. */
+#define QMC_NTRACE 8
+
+typedef struct {
+    int n_stab;            /* slices between restabilisations (default 10) */
+    int precision;         /* 0 = FP64 everywhere (default) */
+    double eps0;           /* initial Langevin step (default 0.5) */
+    double deps;           /* step adaptation rate Delta eps (default 0.1) */
+    double r0;             /* target acceptance (default 0.574) */
+    int n_adapt;           /* adapt eps after the first n_adapt sweeps; -1 = always (default) */
+    int n_orb_sphere;      /* sphere orbital count; 0 = N_phi + 1 (default) */
+    int n_chains;          /* independent chains in the batch (default 1) */
+    const double *couplings;    /* host, n_chains values of u, or NULL = all `coupling` */
+    const double *anisotropies; /* host, n_chains values of alpha, or NULL = all `anisotropy` */
+    const uint64_t *seeds;      /* host, n_chains seeds, or NULL: chain c uses seed + c */
+    int series_capacity;   /* observable records kept per chain (default 4096, ring) */
+    int trace_capacity;    /* per-update records kept per chain (default 0 = off) */
+    double stab_tol;       /* QMC_ERR_UNSTABLE threshold (default 1e-6) */
+    double sign_tol;       /* QMC_ERR_SIGN threshold (default 1e-6) */
+} qmc_opts;
+
+/* Fill *o with the defaults listed above. */
+int qmc_default_opts(qmc_opts *o);
+
+/* Create a batch of chains on the current CUDA device.
+ *   geometry   QMC_TORUS (magnetic torus, Methods Eq. torus_density_operator)
+ *              or QMC_SPHERE (monopole sphere, Eq. sphere_density_operator)
+ *   N_phi      flux quanta; torus: N_phi orbitals and momenta
+ *              {q in Z^2 : exp(-2 pi |q|^2/(4 N_phi)) > 0.01}; sphere:
+ *              opts.n_orb_sphere orbitals (default N_phi + 1), N_q = n_orb^2
+ *   beta, dtau inverse temperature and Trotter step; L = beta/dtau must be an
+ *              integer (QMC_ERR_ARG otherwise)
+ *   coupling   u, anisotropy alpha (Results, "Universal phase diagram"); the
+ *              weight is sign-free only for U_N >= 0 and U_K + U_N >= 0, other
+ *              values are rejected with QMC_ERR_ARG
+ *   seed       Philox4x32-10 key of chain 0
+ * The fields start i.i.d. N(0,1), all slice propagators are built and G(0) is
+ * computed by the stabilised UDV chain.  *out is set to NULL on failure. */
+int qmc_create(qmc_ctx **out, int geometry, int N_phi, double beta, double dtau,
+               double coupling, double anisotropy, uint64_t seed,
+               const qmc_opts *opts);
+
+/* Release every device allocation of the context. NULL is accepted. */
+int qmc_destroy(qmc_ctx *ctx);
+
+/* Use `stream` (a cudaStream_t, or NULL for the legacy default stream) for
+ * all subsequent work of the context. */
+int qmc_set_stream(qmc_ctx *ctx, void *stream);
+
+/* Enqueue n_sweeps sweeps of all chains (Methods, "Langevin-based global
+ * update scheme"): for tau = 1..L, wrap G <- B_tau G B_tau^-1, propose
+ * phi' = phi - (eps^2/2) grad S + eps xi for the whole slice, accept with
+ * min{1, e^{-S'} f(phi|phi') / (e^{-S} f(phi'|phi))} using the exact ratio
+ * det[1 + (Delta - 1)(1 - G)], update G <- G M^-1, and restabilise every
+ * n_stab slices; after the sweep adapt eps <- eps + (r_a - r_0) d_eps and
+ * record one observable record per chain.  Asynchronous: errors detected on
+ * the device are reported by the next synchronising call. */
+int qmc_sweep(qmc_ctx *ctx, int n_sweeps);
+
+/* Wait for the context's stream and report device-side errors
+ * (QMC_ERR_UNSTABLE, QMC_ERR_SIGN, QMC_ERR_NONFINITE). */
+int qmc_sync(qmc_ctx *ctx);
+
+/* Measure all chains on their current G and copy the records to
+ * host_out[n_chains * QMC_NOBS]. */
+int qmc_measure(qmc_ctx *ctx, double *host_out);
+
+/* Copy the latest `count` observable records per chain (oldest first) to
+ * host_out[n_chains][count][QMC_NOBS]; count <= records available. */
+int qmc_get_series(qmc_ctx *ctx, int count, double *host_out);
+int qmc_series_length(const qmc_ctx *ctx);
+
+/* Copy chain `chain`'s equal-time Green's function to host_buf as the full
+ * 4 N_orb x 4 N_orb matrix G_s (x) I_spin in the order (spin, valley,
+ * orbital), row-major, interleaved complex: len >= 2 * (4 N_orb)^2 doubles. */
+int qmc_get_green(qmc_ctx *ctx, int chain, double *host_buf, size_t len);
+
+/* One spin block only: 2 N_orb x 2 N_orb, order (valley, orbital). */
+int qmc_get_green_block(qmc_ctx *ctx, int chain, double *host_buf, size_t len);
+
+/* Fields of chain `chain`: host_buf[L][4][N_q] (slice, channel, real field). */
+int qmc_get_fields(qmc_ctx *ctx, int chain, double *host_buf, size_t len);
+
+/* Per-update trace (opts.trace_capacity > 0): host_buf[count][QMC_NTRACE],
+ * returns the number of records in *count. */
+int qmc_get_trace(qmc_ctx *ctx, int chain, double *host_buf, size_t len, long *count);
+
+/* Sizes of the context. */
+int qmc_sizes(const qmc_ctx *ctx, int *n_orb, int *n_q, int *L, int *n_chains);
+
+/* Current Langevin step of each chain: host_out[n_chains]. */
+int qmc_get_eps(qmc_ctx *ctx, double *host_out);
+
+/* Integrated autocorrelation time of x[0..n) with Sokal's automatic window
+ * (c = 5): tau = 1/2 + sum_{t<=W} rho(t), smallest W >= c tau.  Host only. */
+double qmc_tau_int(const double *x, int n);
+
+const char *qmc_strerror(int code);
+const char *qmc_last_error(const qmc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QMC_H */

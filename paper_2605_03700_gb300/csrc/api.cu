@@ -1,0 +1,922 @@
+// api.cu -- C ABI and sweep engine of libqmc.
+//
+// The engine keeps every chain's state resident on the device (fields, slice
+// propagators B_tau and B_tau^-1, the eigenpairs of each slice's channel
+// matrices, G, the left UDV stack) and runs all chains of the batch in lock
+// step, one slice at a time, with batched kernels (grid z or y = chain).
+// Control never returns to the host inside a sweep: accept decisions are
+// device flags consumed by the commit kernel.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "linalg.cuh"
+#include "model.cuh"
+
+#define CK(x)                                                                      \
+    do {                                                                           \
+        cudaError_t e_ = (x);                                                      \
+        if (e_ != cudaSuccess) {                                                   \
+            ctx->err = std::string(#x) + ": " + cudaGetErrorString(e_);            \
+            return QMC_ERR_CUDA;                                                   \
+        }                                                                          \
+    } while (0)
+
+struct qmc_ctx {
+    int geom = 0, nphi = 0, n = 0, N = 0, nq = 0, nf = 0, L = 0, nb = 0;
+    long long NN = 0, n2 = 0;
+    double beta = 0, dtau = 0;
+    qmc_opts o;
+    std::vector<double> u, anis, g;
+    std::vector<cd> alpha;
+    std::vector<uint64_t> seeds;
+    std::vector<int> sp;  // stabilisation slices, ascending, last == L
+    int q0 = 0;
+    std::vector<int> dq;
+    cudaStream_t st = 0;
+    uint32_t sweep = 0;
+    long long series_n = 0;
+    std::string err;
+    std::vector<void *> allocs;
+
+    // tables
+    cd *ff_val = nullptr, *trF = nullptr;
+    int *ff_col = nullptr, *qxy = nullptr, *partner = nullptr, *fkind = nullptr, *frA = nullptr,
+        *frB = nullptr, *fq = nullptr, *fk = nullptr, *aptr = nullptr, *aq = nullptr;
+    cd *alpha_d = nullptr;
+    double *g_d = nullptr;
+    uint32_t *keys = nullptr;
+    // chain state
+    double *phi = nullptr, *eigW = nullptr;
+    cd *eigU = nullptr, *B = nullptr, *Binv = nullptr, *G = nullptr;
+    cd *LQ = nullptr, *LW = nullptr;
+    double *LD = nullptr;
+    cd *RQ = nullptr, *RW = nullptr;
+    double *RD = nullptr;
+    // scratch
+    cd *Fm, *V, *Vp, *T, *Tp, *lam, *Dg, *Dgi, *lamp, *Dgp, *Dgip;
+    cd *Ah, *Y1, *Cacc, *At, *tq, *Up, *Bp, *Bpi, *X1, *X2, *M, *Gp, *Gs, *Qt, *Vt, *Eye, *dinvR,
+        *dinvL, *logdet, *ax;
+    double *Wp, *phip, *grad, *gradp, *Dt, *ones, *stats, *eps, *eps_used, *series, *trace;
+    int *piv, *flag, *errf;
+    long long *trace_n;
+};
+
+template <class T>
+static int dalloc(qmc_ctx *ctx, T **p, size_t count)
+{
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, (count ? count : 1) * sizeof(T));
+    if (e != cudaSuccess) {
+        ctx->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+        return QMC_ERR_OOM;
+    }
+    cudaMemset(q, 0, (count ? count : 1) * sizeof(T));
+    ctx->allocs.push_back(q);
+    *p = (T *)q;
+    return 0;
+}
+
+#define DA(ptr, count)                                   \
+    do {                                                 \
+        int r_ = dalloc(ctx, &(ptr), (size_t)(count));   \
+        if (r_) return r_;                               \
+    } while (0)
+
+static const cd ONE = {1, 0}, ZERO = {0, 0}, MONE = {-1, 0};
+
+// ------------------------------------------------------------ pipeline ----
+// V, T and the factor diagonals of a slice from its eigenpairs
+static void factors_from_eig(qmc_ctx *ctx, const cd *U, long long U_cs, const double *W,
+                             long long W_cs, cd *V, cd *T, cd *lam, cd *Dg, cd *Dgi)
+{
+    const int nb = ctx->nb, N = ctx->N;
+    const long long NN = ctx->NN;
+    launch_build_V(ctx->st, nb, ctx->n, U, U_cs, V);
+    // T01 = V0^H V1, T12 = V1^H V2, T23 = V2^H V3
+    for (int x = 0; x < 3; ++x)
+        zgemm_sq(ctx->st, N, nb, V + x * NN, 4 * NN, 2, V + (x + 1) * NN, 4 * NN, 0, T + x * NN,
+                 3 * NN);
+    launch_lambda(ctx->st, nb, ctx->n, W, W_cs, ctx->alpha_d, lam, Dg, Dgi);
+}
+
+// B = V0 D0 T01 D1 T12 D2 T23 D3 T23^H D4 T12^H D5 T01^H D6 V0^H and the
+// inverse with the diagonals reversed and inverted
+static void build_B(qmc_ctx *ctx, const cd *V, const cd *T, const cd *Dg, const cd *Dgi, cd *Bout,
+                    long long Bo_cs, cd *Biout, long long Bio_cs)
+{
+    const int nb = ctx->nb, N = ctx->N;
+    const long long NN = ctx->NN;
+    const int tidx[6] = {0, 1, 2, 2, 1, 0};
+    for (int inv = 0; inv < 2; ++inv) {
+        const cd *dg = inv ? Dgi : Dg;
+        cd *dst = inv ? Biout : Bout;
+        long long dcs = inv ? Bio_cs : Bo_cs;
+        cd *a = ctx->X1, *b = ctx->X2;
+        for (int step = 0; step < 7; ++step) {
+            int j = inv ? 6 - step : step;  // diagonal used at this position
+            const cd *dj = dg + (long long)j * N;
+            if (step == 0) {
+                zgemm_sq(ctx->st, N, nb, V, 4 * NN, 0, T + 0 * NN, 3 * NN, 0, a, NN, dj, 7 * N);
+            } else if (step < 6) {
+                int op = step < 3 ? 0 : 2;
+                zgemm_sq(ctx->st, N, nb, a, NN, 0, T + (long long)tidx[step] * NN, 3 * NN, op, b,
+                         NN, dj, 7 * N);
+                std::swap(a, b);
+            } else {
+                zgemm_sq(ctx->st, N, nb, a, NN, 0, V, 4 * NN, 2, dst, dcs, dj, 7 * N);
+            }
+        }
+    }
+}
+
+// exact grad S of one slice (Methods, Eq. action_gradient): chain of the
+// matrices A_j = P_j^-1 (1 - G) P_j in the eigenbases of the seven factors,
+// Daleckii-Krein weights, back-transform per channel, traces with F_q
+static void gradient(qmc_ctx *ctx, const cd *Gm, const cd *V, const cd *T, const cd *lam,
+                     const cd *Dg, const cd *Dgi, const double *phi, long long phi_cs, double *grad)
+{
+    const int nb = ctx->nb, N = ctx->N;
+    const long long NN = ctx->NN;
+    cudaStream_t s = ctx->st;
+    // Ah = I - V0^H G V0
+    zgemm_sq(s, N, nb, V, 4 * NN, 2, Gm, NN, 0, ctx->Y1, NN);
+    zgemm_sq(s, N, nb, ctx->Y1, NN, 0, V, 4 * NN, 0, ctx->Ah, NN, nullptr, 0, MONE, ZERO, 1);
+    const int tidx[6] = {0, 1, 2, 2, 1, 0};
+    for (int j = 0; j < 7; ++j) {
+        launch_accum(s, nb, N, j, j < 4, ctx->alpha_d, lam, ctx->Ah, ctx->Cacc);
+        if (j == 6) break;
+        const cd *Tx = T + (long long)tidx[j] * NN;
+        int op1 = j < 3 ? 2 : 0, op2 = j < 3 ? 0 : 2;
+        zgemm_sq(s, N, nb, Tx, 3 * NN, op1, ctx->Ah, NN, 0, ctx->Y1, NN, Dgi + (long long)j * N,
+                 7 * N);
+        zgemm_sq(s, N, nb, ctx->Y1, NN, 0, Tx, 3 * NN, op2, ctx->Ah, NN, Dg + (long long)j * N,
+                 7 * N);
+    }
+    for (int i = 0; i < 4; ++i) {
+        zgemm_sq(s, N, nb, V + i * NN, 4 * NN, 0, ctx->Cacc + i * NN, 4 * NN, 0, ctx->Y1, NN);
+        zgemm_sq(s, N, nb, ctx->Y1, NN, 0, V + i * NN, 4 * NN, 2, ctx->At + i * NN, 4 * NN);
+    }
+    launch_trace_grad(s, nb, ctx->n, ctx->nq, ctx->At, ctx->ff_val, ctx->ff_col, ctx->trF,
+                      ctx->alpha_d, ctx->tq, ctx->fq, ctx->fk, ctx->partner, phi, phi_cs, grad);
+}
+
+// eigenpairs of the four channel matrices of fields phi (chain stride phi_cs)
+static int eig_of_fields(qmc_ctx *ctx, const double *phi, long long phi_cs, cd *U, long long U_cs,
+                         double *W, long long W_cs)
+{
+    launch_assemble(ctx->st, ctx->nb, ctx->n, ctx->nq, phi, phi_cs, ctx->fkind, ctx->frA, ctx->frB,
+                    ctx->aptr, ctx->aq, ctx->ff_val, ctx->Fm);
+    const long long n2 = ctx->n2;
+    if (U_cs == 4 * n2 && W_cs == 4 * ctx->n) {
+        return eigh_batched(ctx->st, ctx->n, ctx->Fm, n2, U, n2, W, ctx->n, 4 * ctx->nb);
+    }
+    for (int c = 0; c < ctx->nb; ++c) {
+        int r = eigh_batched(ctx->st, ctx->n, ctx->Fm + c * 4 * n2, n2, U + c * U_cs, n2,
+                             W + c * W_cs, ctx->n, 4);
+        if (r) return r;
+    }
+    return 0;
+}
+
+// G = QL DbL^-1 [DbR^-1 QR^H QL DbL^-1 + DsR WR WL^H DsL]^-1 DbR^-1 QR^H
+static int green_from_udv(qmc_ctx *ctx, const cd *QR, const double *DR, const cd *WR,
+                          long long R_cs, long long RD_cs, const cd *QL, const double *DL,
+                          const cd *WL, long long L_cs, long long LD_cs, cd *Gout)
+{
+    const int nb = ctx->nb, N = ctx->N;
+    const long long NN = ctx->NN;
+    cudaStream_t s = ctx->st;
+    zgemm_sq(s, N, nb, QR, R_cs, 2, QL, L_cs, 0, ctx->X1, NN);
+    zgemm_sq(s, N, nb, WR, R_cs, 0, WL, L_cs, 2, ctx->X2, NN);
+    launch_stab_mix(s, nb, N, ctx->X1, ctx->X2, DR, RD_cs, DL, LD_cs, ctx->M);
+    if (lu_batched(s, N, ctx->M, NN, ctx->piv, N, nullptr, nb)) return QMC_ERR_ARG;
+    launch_inv_big(s, nb, N, DL, LD_cs, ctx->dinvL);
+    launch_inv_big(s, nb, N, DR, RD_cs, ctx->dinvR);
+    // X1 = QL diag(dinvL): GEMM against the identity keeps the scaling on device
+    zgemm_sq(s, N, nb, QL, L_cs, 0, ctx->Eye, NN, 0, ctx->X1, NN, ctx->dinvL, N);
+    if (rdiv_batched(s, N, ctx->X1, NN, ctx->M, NN, ctx->piv, N, ctx->X2, NN, nb))
+        return QMC_ERR_ARG;
+    zgemm_sq(s, N, nb, ctx->X2, NN, 0, QR, R_cs, 2, Gout, NN, ctx->dinvR, N);
+    return 0;
+}
+
+// left stack B(beta, tau)^H = Q D W at every stabilisation point and at 0
+static int build_left_stack(qmc_ctx *ctx)
+{
+    const int nb = ctx->nb, N = ctx->N, nsp = (int)ctx->sp.size();
+    const long long NN = ctx->NN, Ls = (long long)(nsp + 1) * NN, LDs = (long long)(nsp + 1) * N;
+    cudaStream_t s = ctx->st;
+    const long long BL = (long long)ctx->L * NN;
+    int k = nsp - 1;
+    CK(cudaMemcpyAsync(ctx->X1, ctx->Eye, sizeof(cd) * NN * nb, cudaMemcpyDeviceToDevice, s));
+    for (int c = 0; c < nb; ++c) {
+        CK(cudaMemcpyAsync(ctx->LQ + c * Ls + k * NN, ctx->Eye, sizeof(cd) * NN,
+                           cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(ctx->LW + c * Ls + k * NN, ctx->Eye, sizeof(cd) * NN,
+                           cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(ctx->LD + c * LDs + k * N, ctx->ones, sizeof(double) * N,
+                           cudaMemcpyDeviceToDevice, s));
+    }
+    for (k = nsp - 1; k >= 0; --k) {
+        int hi = ctx->sp[k], lo = k > 0 ? ctx->sp[k - 1] : 0;
+        int dst = k > 0 ? k - 1 : nsp;
+        launch_scale_cols(s, nb, N, ctx->LQ + k * NN, Ls, ctx->LD + k * N, LDs, ctx->X1, NN);
+        cd *a = ctx->X1, *b = ctx->X2;
+        for (int t = hi; t > lo; --t) {
+            zgemm_sq(s, N, nb, ctx->B + (long long)(t - 1) * NN, BL, 2, a, NN, 0, b, NN);
+            std::swap(a, b);
+        }
+        if (qrp_batched(s, N, a, NN, ctx->LQ + dst * NN, Ls, ctx->LD + dst * N, LDs, ctx->Vt, NN,
+                        nb))
+            return QMC_ERR_ARG;
+        zgemm_sq(s, N, nb, ctx->Vt, NN, 0, ctx->LW + k * NN, Ls, 0, ctx->LW + dst * NN, Ls);
+    }
+    return 0;
+}
+
+static void reset_right_stack(qmc_ctx *ctx)
+{
+    cudaMemcpyAsync(ctx->RQ, ctx->Eye, sizeof(cd) * ctx->NN * ctx->nb, cudaMemcpyDeviceToDevice,
+                    ctx->st);
+    cudaMemcpyAsync(ctx->RW, ctx->Eye, sizeof(cd) * ctx->NN * ctx->nb, cudaMemcpyDeviceToDevice,
+                    ctx->st);
+    cudaMemcpyAsync(ctx->RD, ctx->ones, sizeof(double) * ctx->N * ctx->nb,
+                    cudaMemcpyDeviceToDevice, ctx->st);
+}
+
+// G(0) = (1 + B(beta, 0))^-1 from the left stack at 0
+static int green_at_zero(qmc_ctx *ctx)
+{
+    const int nsp = (int)ctx->sp.size();
+    const long long NN = ctx->NN, Ls = (long long)(nsp + 1) * NN, LDs = (long long)(nsp + 1) * ctx->N;
+    reset_right_stack(ctx);
+    return green_from_udv(ctx, ctx->RQ, ctx->RD, ctx->RW, NN, ctx->N, ctx->LQ + nsp * NN,
+                          ctx->LD + nsp * ctx->N, ctx->LW + nsp * NN, Ls, LDs, ctx->G);
+}
+
+// one MALA proposal + MH test on slice t (1-based) for every chain
+static int update_slice(qmc_ctx *ctx, int t)
+{
+    const int nb = ctx->nb, N = ctx->N, n = ctx->n, nf = ctx->nf;
+    const long long NN = ctx->NN, n2 = ctx->n2;
+    const int s0 = t - 1;
+    cudaStream_t s = ctx->st;
+    const long long L = ctx->L;
+    const double *phi_s = ctx->phi + (long long)s0 * nf;
+    const long long phi_cs = L * nf;
+    cd *Bs = ctx->B + (long long)s0 * NN, *Bis = ctx->Binv + (long long)s0 * NN;
+    // forward gradient at the current fields
+    factors_from_eig(ctx, ctx->eigU + (long long)s0 * 4 * n2, L * 4 * n2,
+                     ctx->eigW + (long long)s0 * 4 * n, L * 4 * n, ctx->V, ctx->T, ctx->lam,
+                     ctx->Dg, ctx->Dgi);
+    gradient(ctx, ctx->G, ctx->V, ctx->T, ctx->lam, ctx->Dg, ctx->Dgi, phi_s, phi_cs, ctx->grad);
+    launch_propose(s, nb, nf, phi_s, phi_cs, ctx->grad, ctx->eps, ctx->keys, (uint32_t)s0,
+                   ctx->sweep, ctx->phip);
+    // proposal factors and propagators
+    int r = eig_of_fields(ctx, ctx->phip, nf, ctx->Up, 4 * n2, ctx->Wp, 4 * n);
+    if (r) {
+        ctx->err = "eigensolver: unsupported size";
+        return QMC_ERR_ARG;
+    }
+    factors_from_eig(ctx, ctx->Up, 4 * n2, ctx->Wp, 4 * n, ctx->Vp, ctx->Tp, ctx->lamp, ctx->Dgp,
+                     ctx->Dgip);
+    build_B(ctx, ctx->Vp, ctx->Tp, ctx->Dgp, ctx->Dgip, ctx->Bp, NN, ctx->Bpi, NN);
+    // M = 1 + (B' B^-1 - 1)(1 - G)
+    zgemm_sq(s, N, nb, ctx->Bp, NN, 0, Bis, L * NN, 0, ctx->X1, NN);
+    launch_axpyI(s, nb, N, ctx->X1, NN, ONE, MONE, ctx->X1, NN);
+    launch_axpyI(s, nb, N, ctx->G, NN, MONE, ONE, ctx->X2, NN);
+    zgemm_sq(s, N, nb, ctx->X1, NN, 0, ctx->X2, NN, 0, ctx->M, NN, nullptr, 0, ONE, ZERO, 1);
+    if (lu_batched(s, N, ctx->M, NN, ctx->piv, N, ctx->logdet, nb)) return QMC_ERR_ARG;
+    if (rdiv_batched(s, N, ctx->G, NN, ctx->M, NN, ctx->piv, N, ctx->Gp, NN, nb)) return QMC_ERR_ARG;
+    // reverse gradient at the proposal with G'
+    gradient(ctx, ctx->Gp, ctx->Vp, ctx->Tp, ctx->lamp, ctx->Dgp, ctx->Dgip, ctx->phip, nf,
+             ctx->gradp);
+    AcceptP ap;
+    ap.nq = ctx->nq;
+    ap.phi = phi_s;
+    ap.phi_cs = phi_cs;
+    ap.phip = ctx->phip;
+    ap.grad = ctx->grad;
+    ap.gradp = ctx->gradp;
+    ap.eps = ctx->eps;
+    ap.alpha = ctx->alpha_d;
+    ap.logdet = ctx->logdet;
+    ap.trF = ctx->trF;
+    ap.fkind = ctx->fkind;
+    ap.frA = ctx->frA;
+    ap.frB = ctx->frB;
+    ap.keys = ctx->keys;
+    ap.slice = t;
+    ap.sweep = ctx->sweep;
+    ap.flag = ctx->flag;
+    ap.st = ctx->stats;
+    ap.errf = ctx->errf;
+    ap.sign_tol = ctx->o.sign_tol;
+    ap.trace = ctx->o.trace_capacity > 0 ? ctx->trace : nullptr;
+    ap.trace_cap = ctx->o.trace_capacity;
+    ap.trace_n = ctx->trace_n;
+    launch_accept(s, nb, ap);
+    CommitP cp;
+    cp.N = N;
+    cp.n = n;
+    cp.nf = nf;
+    cp.L = ctx->L;
+    cp.s = s0;
+    cp.flag = ctx->flag;
+    cp.B = ctx->B;
+    cp.Binv = ctx->Binv;
+    cp.G = ctx->G;
+    cp.U = ctx->eigU;
+    cp.W = ctx->eigW;
+    cp.phi = ctx->phi;
+    cp.Bp = ctx->Bp;
+    cp.Bpi = ctx->Bpi;
+    cp.Gp = ctx->Gp;
+    cp.Up = ctx->Up;
+    cp.Wp = ctx->Wp;
+    cp.phip = ctx->phip;
+    launch_commit(s, nb, cp);
+    return 0;
+}
+
+// right stack advanced over slices (prev, t], fresh G(t) and its error
+static int restabilise(qmc_ctx *ctx, int k, int prev, int t)
+{
+    const int nb = ctx->nb, N = ctx->N, nsp = (int)ctx->sp.size();
+    const long long NN = ctx->NN, Ls = (long long)(nsp + 1) * NN, LDs = (long long)(nsp + 1) * N;
+    const long long BL = (long long)ctx->L * NN;
+    cudaStream_t s = ctx->st;
+    launch_scale_cols(s, nb, N, ctx->RQ, NN, ctx->RD, N, ctx->X1, NN);
+    cd *a = ctx->X1, *b = ctx->X2;
+    for (int u = prev + 1; u <= t; ++u) {
+        zgemm_sq(s, N, nb, ctx->B + (long long)(u - 1) * NN, BL, 0, a, NN, 0, b, NN);
+        std::swap(a, b);
+    }
+    if (qrp_batched(s, N, a, NN, ctx->Qt, NN, ctx->Dt, N, ctx->Vt, NN, nb)) return QMC_ERR_ARG;
+    zgemm_sq(s, N, nb, ctx->Vt, NN, 0, ctx->RW, NN, 0, ctx->X1, NN);
+    std::swap(ctx->RW, ctx->X1);
+    std::swap(ctx->RQ, ctx->Qt);
+    std::swap(ctx->RD, ctx->Dt);
+    int r = green_from_udv(ctx, ctx->RQ, ctx->RD, ctx->RW, NN, N, ctx->LQ + k * NN,
+                           ctx->LD + k * N, ctx->LW + k * NN, Ls, LDs, ctx->Gs);
+    if (r) return r;
+    launch_stab_err(s, nb, N, ctx->G, ctx->Gs, ctx->stats, ctx->errf, ctx->o.stab_tol);
+    return 0;
+}
+
+static void measure_into(qmc_ctx *ctx, double *out, long long out_cs)
+{
+    MeasP mp;
+    mp.nq = ctx->nq;
+    mp.n = ctx->n;
+    mp.L = ctx->L;
+    mp.ax = ctx->ax;
+    mp.partner = ctx->partner;
+    mp.trF = ctx->trF;
+    mp.g = ctx->g_d;
+    mp.q0 = ctx->q0;
+    mp.ndq = (int)ctx->dq.size();
+    for (int i = 0; i < 8; ++i) mp.dq[i] = i < mp.ndq ? ctx->dq[i] : 0;
+    mp.out = out;
+    mp.out_cs = out_cs;
+    mp.st = ctx->stats;
+    mp.eps_used = ctx->eps_used;
+    launch_measure(ctx->st, ctx->nb, ctx->n, ctx->nq, ctx->G, ctx->ff_val, ctx->ff_col,
+                   ctx->partner, ctx->ax, mp);
+}
+
+static int one_sweep(qmc_ctx *ctx)
+{
+    int r = build_left_stack(ctx);
+    if (r) return r;
+    r = green_at_zero(ctx);
+    if (r) return r;
+    const int N = ctx->N, nb = ctx->nb;
+    const long long NN = ctx->NN, BL = (long long)ctx->L * NN;
+    int k = 0, prev = 0;
+    for (int t = 1; t <= ctx->L; ++t) {
+        zgemm_sq(ctx->st, N, nb, ctx->B + (long long)(t - 1) * NN, BL, 0, ctx->G, NN, 0, ctx->X1,
+                 NN);
+        zgemm_sq(ctx->st, N, nb, ctx->X1, NN, 0, ctx->Binv + (long long)(t - 1) * NN, BL, 0, ctx->G,
+                 NN);
+        r = update_slice(ctx, t);
+        if (r) return r;
+        if (t == ctx->sp[k]) {
+            r = restabilise(ctx, k, prev, t);
+            if (r) return r;
+            prev = t;
+            ++k;
+        }
+    }
+    const int cap = ctx->o.series_capacity;
+    long long idx = ctx->series_n % cap;
+    measure_into(ctx, ctx->series + idx * QMC_NOBS, (long long)cap * QMC_NOBS);
+    int adapt = ctx->o.n_adapt < 0 || (int)ctx->sweep < ctx->o.n_adapt;
+    launch_end_sweep(ctx->st, nb, ctx->L, adapt, ctx->o.r0, ctx->o.deps, ctx->eps, ctx->eps_used,
+                     ctx->stats);
+    ctx->sweep++;
+    ctx->series_n++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        ctx->err = std::string("kernel launch: ") + cudaGetErrorString(e);
+        return QMC_ERR_CUDA;
+    }
+    return 0;
+}
+
+// ------------------------------------------------------------- create -----
+static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy)
+{
+    const int n = ctx->n, nb = ctx->nb;
+    // torus momenta: q_y outer, q_x inner, exp(-2 pi |q|^2/(4 N_phi)) > 0.01
+    std::vector<int> qxy;
+    int R = (int)floor(sqrt((double)(int)(4.0 * n * log(100.0) / (2.0 * M_PI)))) + 2;
+    for (int qy = -R; qy <= R; ++qy)
+        for (int qx = -R; qx <= R; ++qx)
+            if (exp(-2.0 * M_PI * (double)(qx * qx + qy * qy) / (4.0 * n)) > 0.01) {
+                qxy.push_back(qx);
+                qxy.push_back(qy);
+            }
+    const int nq = (int)qxy.size() / 2;
+    ctx->nq = nq;
+    ctx->nf = 4 * nq;
+    std::vector<int> partner(nq), fkind(nq), frA(nq), frB(nq), fq(nq), fk(nq);
+    for (int q = 0; q < nq; ++q)
+        for (int p = 0; p < nq; ++p)
+            if (qxy[2 * p] == -qxy[2 * q] && qxy[2 * p + 1] == -qxy[2 * q + 1]) partner[q] = p;
+    int rr = 0;
+    for (int q = 0; q < nq; ++q) {
+        int p = partner[q];
+        if (p == q) {
+            fkind[q] = 0; frA[q] = rr; frB[q] = -1;
+            fq[rr] = q; fk[rr] = 0;
+            rr += 1;
+        } else if (p > q) {
+            fkind[q] = 1; frA[q] = rr; frB[q] = rr + 1;
+            fkind[p] = 2; frA[p] = rr; frB[p] = rr + 1;
+            fq[rr] = q; fk[rr] = 1;
+            fq[rr + 1] = q; fk[rr + 1] = 2;
+            rr += 2;
+        }
+    }
+    // assembly lists: entry (k, (k - q_y) mod n) <- q, q ascending
+    std::vector<std::vector<int>> lists((size_t)n * n);
+    for (int q = 0; q < nq; ++q)
+        for (int k = 0; k < n; ++k) {
+            int c = ((k - qxy[2 * q + 1]) % n + n) % n;
+            lists[(size_t)k * n + c].push_back(q);
+        }
+    std::vector<int> aptr((size_t)n * n + 1, 0), aq;
+    for (size_t e = 0; e < lists.size(); ++e) {
+        aptr[e] = (int)aq.size();
+        for (int q : lists[e]) aq.push_back(q);
+    }
+    aptr[(size_t)n * n] = (int)aq.size();
+    ctx->q0 = -1;
+    ctx->dq.clear();
+    for (int q = 0; q < nq; ++q) {
+        int x = qxy[2 * q], y = qxy[2 * q + 1];
+        if (x == 0 && y == 0) ctx->q0 = q;
+        if (abs(x) + abs(y) == 1) ctx->dq.push_back(q);
+    }
+    // couplings per chain
+    ctx->u.resize(nb);
+    ctx->anis.resize(nb);
+    ctx->seeds.resize(nb);
+    ctx->g.resize(4 * nb);
+    ctx->alpha.resize(4 * nb);
+    std::vector<uint32_t> keys(2 * nb);
+    for (int c = 0; c < nb; ++c) {
+        double u = ctx->o.couplings ? ctx->o.couplings[c] : coupling;
+        double a = ctx->o.anisotropies ? ctx->o.anisotropies[c] : anisotropy;
+        uint64_t sd = ctx->o.seeds ? ctx->o.seeds[c] : seed + (uint64_t)c;
+        double UN = u + a / sqrt(2.0), UK = u - a / sqrt(2.0);
+        if (!(UN >= 0.0) || !(UK + UN >= 0.0)) {
+            ctx->err = "coupling outside the sign-free region (need U_N >= 0, U_K + U_N >= 0)";
+            return QMC_ERR_ARG;
+        }
+        ctx->u[c] = u;
+        ctx->anis[c] = a;
+        ctx->seeds[c] = sd;
+        double gg[4] = {1.0 + UN, -(UK + UN), -(UK + UN), 2.0 * UN};
+        for (int i = 0; i < 4; ++i) {
+            ctx->g[4 * c + i] = gg[i];
+            double v = -ctx->dtau * gg[i];
+            ctx->alpha[4 * c + i] = v >= 0 ? cmk(sqrt(v), 0.0) : cmk(0.0, sqrt(-v));
+        }
+        keys[2 * c] = (uint32_t)(sd & 0xffffffffu);
+        keys[2 * c + 1] = (uint32_t)(sd >> 32);
+    }
+    // stabilisation points
+    ctx->sp.clear();
+    for (int t = ctx->o.n_stab; t < ctx->L; t += ctx->o.n_stab) ctx->sp.push_back(t);
+    ctx->sp.push_back(ctx->L);
+    const int nsp = (int)ctx->sp.size();
+    const int N = ctx->N;
+    const long long NN = ctx->NN, n2 = ctx->n2, L = ctx->L;
+    const int nf = ctx->nf;
+    // device allocations
+    DA(ctx->qxy, 2 * nq);
+    DA(ctx->ff_val, (size_t)nq * n);
+    DA(ctx->ff_col, (size_t)nq * n);
+    DA(ctx->trF, nq);
+    DA(ctx->partner, nq);
+    DA(ctx->fkind, nq);
+    DA(ctx->frA, nq);
+    DA(ctx->frB, nq);
+    DA(ctx->fq, nq);
+    DA(ctx->fk, nq);
+    DA(ctx->aptr, aptr.size());
+    DA(ctx->aq, aq.size());
+    DA(ctx->alpha_d, 4 * nb);
+    DA(ctx->g_d, 4 * nb);
+    DA(ctx->keys, 2 * nb);
+    DA(ctx->phi, (size_t)nb * L * nf);
+    DA(ctx->eigU, (size_t)nb * L * 4 * n2);
+    DA(ctx->eigW, (size_t)nb * L * 4 * n);
+    DA(ctx->B, (size_t)nb * L * NN);
+    DA(ctx->Binv, (size_t)nb * L * NN);
+    DA(ctx->G, (size_t)nb * NN);
+    DA(ctx->LQ, (size_t)nb * (nsp + 1) * NN);
+    DA(ctx->LW, (size_t)nb * (nsp + 1) * NN);
+    DA(ctx->LD, (size_t)nb * (nsp + 1) * N);
+    DA(ctx->RQ, (size_t)nb * NN);
+    DA(ctx->RW, (size_t)nb * NN);
+    DA(ctx->RD, (size_t)nb * N);
+    DA(ctx->Fm, (size_t)nb * 4 * n2);
+    DA(ctx->V, (size_t)nb * 4 * NN);
+    DA(ctx->Vp, (size_t)nb * 4 * NN);
+    DA(ctx->T, (size_t)nb * 3 * NN);
+    DA(ctx->Tp, (size_t)nb * 3 * NN);
+    DA(ctx->lam, (size_t)nb * 7 * N);
+    DA(ctx->Dg, (size_t)nb * 7 * N);
+    DA(ctx->Dgi, (size_t)nb * 7 * N);
+    DA(ctx->lamp, (size_t)nb * 7 * N);
+    DA(ctx->Dgp, (size_t)nb * 7 * N);
+    DA(ctx->Dgip, (size_t)nb * 7 * N);
+    DA(ctx->Ah, (size_t)nb * NN);
+    DA(ctx->Y1, (size_t)nb * NN);
+    DA(ctx->Cacc, (size_t)nb * 4 * NN);
+    DA(ctx->At, (size_t)nb * 4 * NN);
+    DA(ctx->tq, (size_t)nb * 4 * nq);
+    DA(ctx->Up, (size_t)nb * 4 * n2);
+    DA(ctx->Wp, (size_t)nb * 4 * n);
+    DA(ctx->Bp, (size_t)nb * NN);
+    DA(ctx->Bpi, (size_t)nb * NN);
+    DA(ctx->X1, (size_t)nb * NN);
+    DA(ctx->X2, (size_t)nb * NN);
+    DA(ctx->M, (size_t)nb * NN);
+    DA(ctx->Gp, (size_t)nb * NN);
+    DA(ctx->Gs, (size_t)nb * NN);
+    DA(ctx->Qt, (size_t)nb * NN);
+    DA(ctx->Vt, (size_t)nb * NN);
+    DA(ctx->Eye, (size_t)nb * NN);
+    DA(ctx->dinvR, (size_t)nb * N);
+    DA(ctx->dinvL, (size_t)nb * N);
+    DA(ctx->logdet, nb);
+    DA(ctx->ax, (size_t)nb * 4 * nq * 2);
+    DA(ctx->phip, (size_t)nb * nf);
+    DA(ctx->grad, (size_t)nb * nf);
+    DA(ctx->gradp, (size_t)nb * nf);
+    DA(ctx->Dt, (size_t)nb * N);
+    DA(ctx->ones, (size_t)nb * N);
+    DA(ctx->stats, (size_t)nb * 4);
+    DA(ctx->eps, nb);
+    DA(ctx->eps_used, nb);
+    DA(ctx->series, (size_t)nb * ctx->o.series_capacity * QMC_NOBS);
+    DA(ctx->trace, (size_t)nb * (ctx->o.trace_capacity > 0 ? ctx->o.trace_capacity : 1) * QMC_NTRACE);
+    DA(ctx->trace_n, nb);
+    DA(ctx->piv, (size_t)nb * N);
+    DA(ctx->flag, nb);
+    DA(ctx->errf, nb);
+    cudaStream_t s = ctx->st;
+    CK(cudaMemcpyAsync(ctx->qxy, qxy.data(), sizeof(int) * qxy.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->partner, partner.data(), sizeof(int) * nq, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->fkind, fkind.data(), sizeof(int) * nq, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->frA, frA.data(), sizeof(int) * nq, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->frB, frB.data(), sizeof(int) * nq, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->fq, fq.data(), sizeof(int) * nq, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->fk, fk.data(), sizeof(int) * nq, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->aptr, aptr.data(), sizeof(int) * aptr.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->aq, aq.data(), sizeof(int) * aq.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->alpha_d, ctx->alpha.data(), sizeof(cd) * 4 * nb, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->g_d, ctx->g.data(), sizeof(double) * 4 * nb, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->keys, keys.data(), sizeof(uint32_t) * 2 * nb, cudaMemcpyHostToDevice, s));
+    {
+        std::vector<cd> eye((size_t)nb * NN, cmk(0, 0));
+        std::vector<double> ones((size_t)nb * N, 1.0), eps(nb, ctx->o.eps0);
+        for (int c = 0; c < nb; ++c)
+            for (int x = 0; x < N; ++x) eye[(size_t)c * NN + (size_t)x * N + x] = cmk(1, 0);
+        CK(cudaMemcpy(ctx->Eye, eye.data(), sizeof(cd) * eye.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->ones, ones.data(), sizeof(double) * ones.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->eps, eps.data(), sizeof(double) * nb, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->eps_used, eps.data(), sizeof(double) * nb, cudaMemcpyHostToDevice));
+    }
+    launch_ff_torus(s, n, nq, ctx->qxy, ctx->ff_val, ctx->ff_col, ctx->trF);
+    launch_init_phi(s, nb, ctx->L, nf, ctx->keys, ctx->phi);
+    // eigenpairs and propagators of every slice
+    for (int t = 0; t < ctx->L; ++t) {
+        int r = eig_of_fields(ctx, ctx->phi + (long long)t * nf, L * nf,
+                              ctx->eigU + (long long)t * 4 * n2, L * 4 * n2,
+                              ctx->eigW + (long long)t * 4 * n, L * 4 * n);
+        if (r) {
+            ctx->err = "eigensolver: unsupported size";
+            return QMC_ERR_ARG;
+        }
+        factors_from_eig(ctx, ctx->eigU + (long long)t * 4 * n2, L * 4 * n2,
+                         ctx->eigW + (long long)t * 4 * n, L * 4 * n, ctx->V, ctx->T, ctx->lam,
+                         ctx->Dg, ctx->Dgi);
+        build_B(ctx, ctx->V, ctx->T, ctx->Dg, ctx->Dgi, ctx->B + (long long)t * NN, L * NN,
+                ctx->Binv + (long long)t * NN, L * NN);
+    }
+    int r = build_left_stack(ctx);
+    if (r) return r;
+    r = green_at_zero(ctx);
+    if (r) return r;
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    return 0;
+}
+
+// ----------------------------------------------------------------- ABI ----
+extern "C" {
+
+int qmc_default_opts(qmc_opts *o)
+{
+    if (!o) return QMC_ERR_ARG;
+    memset(o, 0, sizeof(*o));
+    o->n_stab = 10;
+    o->precision = 0;
+    o->eps0 = 0.5;
+    o->deps = 0.1;
+    o->r0 = 0.574;
+    o->n_adapt = -1;
+    o->n_orb_sphere = 0;
+    o->n_chains = 1;
+    o->series_capacity = 4096;
+    o->trace_capacity = 0;
+    o->stab_tol = 1e-6;
+    o->sign_tol = 1e-6;
+    return QMC_OK;
+}
+
+int qmc_create(qmc_ctx **out, int geometry, int N_phi, double beta, double dtau, double coupling,
+               double anisotropy, uint64_t seed, const qmc_opts *opts)
+{
+    if (!out) return QMC_ERR_ARG;
+    *out = nullptr;
+    qmc_ctx *ctx = new qmc_ctx();
+    if (opts) ctx->o = *opts;
+    else qmc_default_opts(&ctx->o);
+    int code = QMC_OK;
+    if (geometry != QMC_TORUS) {
+        ctx->err = "only the torus geometry is available on the GPU path";
+        code = QMC_ERR_ARG;
+    } else if (N_phi < 2 || N_phi > 56) {
+        ctx->err = "N_phi must be in [2, 56] (single-block shared-memory kernels)";
+        code = QMC_ERR_ARG;
+    } else if (!(beta > 0) || !(dtau > 0)) {
+        ctx->err = "beta and dtau must be positive";
+        code = QMC_ERR_ARG;
+    } else if (ctx->o.n_chains < 1 || ctx->o.n_stab < 1 || ctx->o.series_capacity < 1 ||
+               ctx->o.trace_capacity < 0 || ctx->o.precision != 0) {
+        ctx->err = "invalid options";
+        code = QMC_ERR_ARG;
+    } else {
+        long Lr = lround(beta / dtau);
+        if (Lr < 1 || fabs(Lr * dtau - beta) > 1e-9 * (beta > 1 ? beta : 1)) {
+            ctx->err = "beta / dtau is not an integer";
+            code = QMC_ERR_ARG;
+        } else {
+            ctx->geom = geometry;
+            ctx->nphi = N_phi;
+            ctx->n = N_phi;
+            ctx->N = 2 * N_phi;
+            ctx->NN = (long long)ctx->N * ctx->N;
+            ctx->n2 = (long long)N_phi * N_phi;
+            ctx->L = (int)Lr;
+            ctx->nb = ctx->o.n_chains;
+            ctx->beta = beta;
+            ctx->dtau = dtau;
+            ctx->o.couplings = ctx->o.anisotropies = nullptr;
+            ctx->o.seeds = nullptr;
+            qmc_opts tmp = ctx->o;
+            if (opts) {
+                tmp.couplings = opts->couplings;
+                tmp.anisotropies = opts->anisotropies;
+                tmp.seeds = opts->seeds;
+            }
+            ctx->o = tmp;
+            code = setup(ctx, seed, coupling, anisotropy);
+            ctx->o.couplings = ctx->o.anisotropies = nullptr;
+            ctx->o.seeds = nullptr;
+        }
+    }
+    if (code != QMC_OK) {
+        fprintf(stderr, "qmc_create: %s\n", ctx->err.c_str());
+        qmc_destroy(ctx);
+        return code;
+    }
+    *out = ctx;
+    return QMC_OK;
+}
+
+int qmc_destroy(qmc_ctx *ctx)
+{
+    if (!ctx) return QMC_OK;
+    if (ctx->st) cudaStreamSynchronize(ctx->st);
+    else cudaDeviceSynchronize();
+    for (void *p : ctx->allocs) cudaFree(p);
+    delete ctx;
+    return QMC_OK;
+}
+
+int qmc_set_stream(qmc_ctx *ctx, void *stream)
+{
+    if (!ctx) return QMC_ERR_ARG;
+    ctx->st = (cudaStream_t)stream;
+    return QMC_OK;
+}
+
+int qmc_sweep(qmc_ctx *ctx, int n_sweeps)
+{
+    if (!ctx || n_sweeps < 0) return QMC_ERR_ARG;
+    for (int i = 0; i < n_sweeps; ++i) {
+        int r = one_sweep(ctx);
+        if (r) return r;
+    }
+    return QMC_OK;
+}
+
+int qmc_sync(qmc_ctx *ctx)
+{
+    if (!ctx) return QMC_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->st));
+    std::vector<int> ef(ctx->nb);
+    CK(cudaMemcpy(ef.data(), ctx->errf, sizeof(int) * ctx->nb, cudaMemcpyDeviceToHost));
+    int f = 0;
+    for (int v : ef) f |= v;
+    if (f & 4) {
+        ctx->err = "non-finite determinant ratio or stabilised G";
+        return QMC_ERR_NONFINITE;
+    }
+    if (f & 2) {
+        ctx->err = "sign of the weight ratio deviates from +1 (sign problem)";
+        return QMC_ERR_SIGN;
+    }
+    if (f & 1) {
+        ctx->err = "G error at restabilisation above stab_tol";
+        return QMC_ERR_UNSTABLE;
+    }
+    return QMC_OK;
+}
+
+int qmc_measure(qmc_ctx *ctx, double *host_out)
+{
+    if (!ctx || !host_out) return QMC_ERR_ARG;
+    double *tmp = ctx->series;  // measure into a scratch record, then copy
+    (void)tmp;
+    measure_into(ctx, ctx->gradp, QMC_NOBS);  // gradp has >= nb * QMC_NOBS doubles
+    CK(cudaMemcpyAsync(host_out, ctx->gradp, sizeof(double) * ctx->nb * QMC_NOBS,
+                       cudaMemcpyDeviceToHost, ctx->st));
+    return qmc_sync(ctx);
+}
+
+int qmc_series_length(const qmc_ctx *ctx)
+{
+    if (!ctx) return 0;
+    long long n = ctx->series_n;
+    return (int)(n < ctx->o.series_capacity ? n : ctx->o.series_capacity);
+}
+
+int qmc_get_series(qmc_ctx *ctx, int count, double *host_out)
+{
+    if (!ctx || !host_out || count < 0 || count > qmc_series_length(ctx)) return QMC_ERR_ARG;
+    const int cap = ctx->o.series_capacity;
+    CK(cudaStreamSynchronize(ctx->st));
+    for (int c = 0; c < ctx->nb; ++c)
+        for (int k = 0; k < count; ++k) {
+            long long idx = (ctx->series_n - count + k) % cap;
+            CK(cudaMemcpy(host_out + ((size_t)c * count + k) * QMC_NOBS,
+                          ctx->series + ((long long)c * cap + idx) * QMC_NOBS,
+                          sizeof(double) * QMC_NOBS, cudaMemcpyDeviceToHost));
+        }
+    return qmc_sync(ctx);
+}
+
+int qmc_get_green_block(qmc_ctx *ctx, int chain, double *host_buf, size_t len)
+{
+    if (!ctx || !host_buf || chain < 0 || chain >= ctx->nb || len < 2 * (size_t)ctx->NN)
+        return QMC_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->st));
+    CK(cudaMemcpy(host_buf, ctx->G + (long long)chain * ctx->NN, sizeof(cd) * ctx->NN,
+                  cudaMemcpyDeviceToHost));
+    return QMC_OK;
+}
+
+int qmc_get_green(qmc_ctx *ctx, int chain, double *host_buf, size_t len)
+{
+    if (!ctx || !host_buf) return QMC_ERR_ARG;
+    const int N = ctx->N, F = 2 * N;
+    if (len < 2 * (size_t)F * F) return QMC_ERR_ARG;
+    std::vector<double> blk(2 * (size_t)ctx->NN);
+    int r = qmc_get_green_block(ctx, chain, blk.data(), blk.size());
+    if (r) return r;
+    memset(host_buf, 0, sizeof(double) * 2 * (size_t)F * F);
+    for (int sp = 0; sp < 2; ++sp)
+        for (int x = 0; x < N; ++x)
+            for (int y = 0; y < N; ++y) {
+                size_t d = ((size_t)(sp * N + x) * F + sp * N + y) * 2;
+                size_t s = ((size_t)x * N + y) * 2;
+                host_buf[d] = blk[s];
+                host_buf[d + 1] = blk[s + 1];
+            }
+    return QMC_OK;
+}
+
+int qmc_get_fields(qmc_ctx *ctx, int chain, double *host_buf, size_t len)
+{
+    if (!ctx || !host_buf || chain < 0 || chain >= ctx->nb) return QMC_ERR_ARG;
+    size_t cnt = (size_t)ctx->L * ctx->nf;
+    if (len < cnt) return QMC_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->st));
+    CK(cudaMemcpy(host_buf, ctx->phi + (size_t)chain * cnt, sizeof(double) * cnt,
+                  cudaMemcpyDeviceToHost));
+    return QMC_OK;
+}
+
+int qmc_get_trace(qmc_ctx *ctx, int chain, double *host_buf, size_t len, long *count)
+{
+    if (!ctx || !count || chain < 0 || chain >= ctx->nb) return QMC_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->st));
+    long long n = 0;
+    CK(cudaMemcpy(&n, ctx->trace_n + chain, sizeof(long long), cudaMemcpyDeviceToHost));
+    *count = (long)n;
+    if (n == 0) return QMC_OK;
+    if (!host_buf || len < (size_t)n * QMC_NTRACE) return QMC_ERR_ARG;
+    CK(cudaMemcpy(host_buf, ctx->trace + (size_t)chain * ctx->o.trace_capacity * QMC_NTRACE,
+                  sizeof(double) * n * QMC_NTRACE, cudaMemcpyDeviceToHost));
+    return QMC_OK;
+}
+
+int qmc_sizes(const qmc_ctx *ctx, int *n_orb, int *n_q, int *L, int *n_chains)
+{
+    if (!ctx) return QMC_ERR_ARG;
+    if (n_orb) *n_orb = ctx->n;
+    if (n_q) *n_q = ctx->nq;
+    if (L) *L = ctx->L;
+    if (n_chains) *n_chains = ctx->nb;
+    return QMC_OK;
+}
+
+int qmc_get_eps(qmc_ctx *ctx, double *host_out)
+{
+    if (!ctx || !host_out) return QMC_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->st));
+    CK(cudaMemcpy(host_out, ctx->eps, sizeof(double) * ctx->nb, cudaMemcpyDeviceToHost));
+    return QMC_OK;
+}
+
+double qmc_tau_int(const double *x, int n)
+{
+    if (!x || n < 2) return 0.5;
+    double mean = 0.0;
+    for (int i = 0; i < n; ++i) mean += x[i];
+    mean /= n;
+    double var = 0.0;
+    for (int i = 0; i < n; ++i) var += (x[i] - mean) * (x[i] - mean);
+    var /= n;
+    if (var <= 0.0) return 0.5;
+    double tau = 0.5;
+    for (int W = 1; W < n; ++W) {
+        double s = 0.0;
+        for (int i = 0; i + W < n; ++i) s += (x[i] - mean) * (x[i + W] - mean);
+        tau += s / (n * var);
+        if (W >= 5.0 * tau) break;
+    }
+    return tau < 0.5 ? 0.5 : tau;
+}
+
+const char *qmc_strerror(int code)
+{
+    switch (code) {
+    case QMC_OK: return "ok";
+    case QMC_ERR_ARG: return "invalid argument or unsupported size";
+    case QMC_ERR_CUDA: return "CUDA error";
+    case QMC_ERR_OOM: return "device allocation failed";
+    case QMC_ERR_UNSTABLE: return "G error at restabilisation above tolerance";
+    case QMC_ERR_SIGN: return "weight ratio not positive (sign problem)";
+    case QMC_ERR_NONFINITE: return "non-finite value";
+    case QMC_ERR_TIMEOUT: return "bounded device wait gave up";
+    default: return "unknown error";
+    }
+}
+
+const char *qmc_last_error(const qmc_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+}  // extern "C"

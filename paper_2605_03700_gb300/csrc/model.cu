@@ -1,0 +1,635 @@
+// model.cu -- CF-DQMC model kernels of libqmc (FP64): LLL form factors,
+// slice-field assembly, eigenbasis factors of the symmetric Trotter slice,
+// the exact action gradient, the MALA proposal / Metropolis-Hastings test,
+// restabilisation helpers and the Wick measurements.
+#include "model.cuh"
+
+// ------------------------------------------------------- form factors ----
+// Torus LLL density operator (Methods, Eq. torus_density_operator):
+// (F_q)[k-1, (k - q_y) mod N_phi] = pref(q) exp(i/2 (2k - q_y) q_x 2 pi/N_phi),
+// k = 1..N_phi, pref(q) = exp(-2 pi |q|^2 / (4 N_phi)) / (4 pi sqrt(N_phi)).
+__global__ void k_ff_torus(int n, int nq, const int *qxy, cd *val, int *col)
+{
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nq * n) return;
+    int q = e / n, k0 = e % n;
+    int qx = qxy[2 * q], qy = qxy[2 * q + 1];
+    const double twopi = 6.283185307179586;
+    double pref = exp(-twopi * (double)(qx * qx + qy * qy) / (4.0 * n)) /
+                  (2.0 * twopi * sqrt((double)n));
+    int k = k0 + 1;
+    double ph = 0.5 * (double)(2 * k - qy) * (double)qx * (twopi / n);
+    double s, c;
+    sincos(ph, &s, &c);
+    val[e] = cmk(pref * c, pref * s);
+    col[e] = ((k0 - qy) % n + n) % n;
+}
+
+// Tr F_q (the channel-0 background is b_q = 2 Tr F_q)
+__global__ void k_trF(int n, int nq, const cd *val, const int *col, cd *trF)
+{
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    cd s = cmk(0, 0);
+    for (int k = 0; k < n; ++k)
+        if (col[q * n + k] == k) s = cadd(s, val[q * n + k]);
+    trF[q] = s;
+}
+
+// --------------------------------------------------------------- fields ---
+// phi ~ N(0,1) i.i.d. (counter: field, slice, sweep 0, purpose 0)
+__global__ void k_init_phi(int nb, int L, int nf, const uint32_t *keys, double *phi)
+{
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long per = (long long)L * nf;
+    if (e >= per * nb) return;
+    int c = (int)(e / per);
+    int s = (int)((e % per) / nf), f = (int)(e % nf);
+    phi[e] = rng_normal((uint32_t)f, (uint32_t)s, 0u, RNG_INIT, keys[2 * c], keys[2 * c + 1]);
+}
+
+// complex field z_q of one channel from its N_q real fields (Methods, Eq.
+// interaction_squares): kind 0: sqrt(2) phi_A; 1: phi_A + i phi_B;
+// 2: phi_A - i phi_B
+QMC_DEVFN cd zfield(const double *ph, int kind, int a, int b)
+{
+    if (kind == 0) return cmk(1.4142135623730951 * ph[a], 0.0);
+    if (kind == 1) return cmk(ph[a], ph[b]);
+    return cmk(ph[a], -ph[b]);
+}
+
+// F^(i) = sum_q z^i_q F_q for the four channels (Methods, Eq. hs_transform),
+// by gathering over the q that land on each entry (fixed q order)
+__global__ void k_assemble(int nb, int n, int nq, const double *phi, long long phi_cs,
+                           const int *fkind, const int *frA, const int *frB, const int *aptr,
+                           const int *aq, const cd *val, cd *F)
+{
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = blockIdx.y, c = blockIdx.z;
+    if (e >= n * n) return;
+    const double *ph = phi + (long long)c * phi_cs + (long long)i * nq;
+    int k = e / n;
+    cd s = cmk(0, 0);
+    for (int t = aptr[e]; t < aptr[e + 1]; ++t) {
+        int q = aq[t];
+        cfma(s, zfield(ph, fkind[q], frA[q], frB[q]), val[q * n + k]);
+    }
+    F[((long long)c * 4 + i) * n * n + e] = s;
+}
+
+// V_i = R_i (x) U_i, the eigenvectors of O^i (x) F^(i)
+__global__ void k_build_V(int nb, int n, const cd *U, long long U_cs, cd *V)
+{
+    int N = 2 * n;
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = blockIdx.y, c = blockIdx.z;
+    if (e >= N * N) return;
+    int r = e / N, cc = e % N;
+    int v = r / n, k = r % n, w = cc / n, kp = cc % n;
+    cd u = U[(long long)c * U_cs + (long long)i * n * n + k * n + kp];
+    V[((long long)c * 4 + i) * N * N + e] = cmul(valley_R(i, v, w), u);
+}
+
+// lambda_j(x) = c_j alpha_i o_i(v) w_i(k) for the seven factors, and
+// D_j = e^{lambda_j}, Dinv_j = e^{-lambda_j}
+__global__ void k_lambda(int nb, int n, const double *w, long long w_cs, const cd *alpha, cd *lam,
+                         cd *Dg, cd *Dgi)
+{
+    int N = 2 * n;
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y, c = blockIdx.z;
+    if (x >= N) return;
+    int i = trotter_channel(j);
+    int v = x / n, k = x % n;
+    double mu = valley_o(i, v) * w[(long long)c * w_cs + i * n + k];
+    cd a = cscale(alpha[c * 4 + i], trotter_coef(j) * mu);
+    long long o = ((long long)c * 7 + j) * N + x;
+    lam[o] = a;
+    Dg[o] = cexp_d(a);
+    Dgi[o] = cexp_d(cmk(-a.x, -a.y));
+}
+
+// (e^x - 1)/x
+QMC_DEVFN cd phi1(cd x)
+{
+    if (x.x * x.x + x.y * x.y < 0.01) {
+        cd s = cmk(0, 0), t = cmk(1, 0);
+        for (int k = 1; k <= 16; ++k) {
+            s = cadd(s, t);
+            t = cscale(cmul(t, x), 1.0 / (double)(k + 1));
+        }
+        return s;
+    }
+    cd e = cexp_d(x);
+    return cdiv(cmk(e.x - 1.0, e.y), x);
+}
+
+// C_i (+)= a_j * (Ah o Phi_j), Phi_j[m][k] = phi1(lambda_j[k] - lambda_j[m]):
+// the Daleckii-Krein form of int_0^1 e^{-sX} A e^{sX} ds in the eigenbasis
+__global__ void k_accum(int nb, int N, int j, int first, const cd *alpha, const cd *lam,
+                        const cd *Ah, cd *Cacc)
+{
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    int c = blockIdx.y;
+    if (e >= N * N) return;
+    int i = trotter_channel(j);
+    int m = e / N, k = e % N;
+    const cd *lj = lam + ((long long)c * 7 + j) * N;
+    cd a = cscale(alpha[c * 4 + i], trotter_coef(j));
+    cd v = cmul(a, cmul(Ah[(long long)c * N * N + e], phi1(csub(lj[k], lj[m]))));
+    cd *dst = Cacc + ((long long)c * 4 + i) * N * N + e;
+    *dst = first ? v : cadd(*dst, v);
+}
+
+// t^(i)_q = Tr[(O^i (x) F_q) Atilde^(i)] - delta_{i0} alpha_0 Tr F_q
+__global__ void k_trace_t(int nb, int n, int nq, const cd *At, const cd *val, const int *col,
+                          const cd *trF, const cd *alpha, cd *t)
+{
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = blockIdx.y, c = blockIdx.z;
+    if (q >= nq) return;
+    int N = 2 * n;
+    const cd *A = At + ((long long)c * 4 + i) * N * N;
+    cd s = cmk(0, 0);
+    for (int v = 0; v < 2; ++v) {
+        int w = (i == 1 || i == 2) ? 1 - v : v;
+        cd o = valley_O(i, v, w);
+        for (int k = 0; k < n; ++k) {
+            int cc = col[q * n + k];
+            if (cc < 0) continue;
+            cfma(s, cmul(o, val[q * n + k]), A[(w * n + cc) * N + (v * n + k)]);
+        }
+    }
+    if (i == 0) s = csub(s, cmul(alpha[c * 4], trF[q]));
+    t[((long long)c * 4 + i) * nq + q] = s;
+}
+
+// grad_phi S = phi - 2 Re d ln(bracket)/d phi for every real field
+__global__ void k_grad(int nb, int nq, const int *fq, const int *fk, const int *partner,
+                       const double *phi, long long phi_cs, const cd *t, double *grad)
+{
+    int f = blockIdx.x * blockDim.x + threadIdx.x;
+    int c = blockIdx.y;
+    if (f >= 4 * nq) return;
+    int i = f / nq, r = f % nq;
+    int q = fq[r], kind = fk[r];
+    const cd *ti = t + ((long long)c * 4 + i) * nq;
+    double d;
+    if (kind == 0) d = 1.4142135623730951 * ti[q].x;
+    else if (kind == 1) d = ti[q].x + ti[partner[q]].x;
+    else d = -(ti[q].y - ti[partner[q]].y);
+    grad[(long long)c * 4 * nq + f] = phi[(long long)c * phi_cs + f] - 2.0 * d;
+}
+
+// phi' = phi - (eps^2/2) grad + eps xi (Methods, Eq. langevin_proposal with
+// the drift along -grad S)
+__global__ void k_propose(int nb, int nf, const double *phi, long long phi_cs, const double *grad,
+                          const double *eps, const uint32_t *keys, uint32_t slice, uint32_t sweep,
+                          double *phip)
+{
+    int f = blockIdx.x * blockDim.x + threadIdx.x;
+    int c = blockIdx.y;
+    if (f >= nf) return;
+    double e = eps[c];
+    double xi = rng_normal((uint32_t)f, slice, sweep, RNG_NOISE, keys[2 * c], keys[2 * c + 1]);
+    phip[(long long)c * nf + f] = phi[(long long)c * phi_cs + f] -
+                                  0.5 * e * e * grad[(long long)c * nf + f] + e * xi;
+}
+
+// Y = a X + b I
+__global__ void k_axpyI(int nb, int N, const cd *X, long long sX, cd a, cd b, cd *Y, long long sY)
+{
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    int c = blockIdx.y;
+    if (e >= N * N) return;
+    cd v = cmul(a, X[(long long)c * sX + e]);
+    if (e / N == e % N) v = cadd(v, b);
+    Y[(long long)c * sY + e] = v;
+}
+
+// ------------------------------------------------------- reductions ------
+QMC_DEVFN double block_sum(double v, double *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) s += sh[w];
+    return s;  // valid in thread 0
+}
+
+// Metropolis-Hastings test of the MALA proposal (Methods, P_acc):
+// log A = 2 Re log R - (S0' - S0) - |phi - phi' + e^2/2 g'|^2/(2e^2)
+//         + |phi' - phi + e^2/2 g|^2/(2e^2),
+// log R = log det M - (Tr W0' - Tr W0)/2, Tr W0 = 2 alpha_0 sum_q z_q Tr F_q.
+__global__ void __launch_bounds__(256) k_accept(AcceptP p)
+{
+    __shared__ double sh[32];
+    const int c = blockIdx.x, tid = threadIdx.x;
+    const int nq = p.nq, nf = 4 * nq;
+    const double *ph = p.phi + (long long)c * p.phi_cs;
+    const double *pp = p.phip + (long long)c * nf;
+    const double *g = p.grad + (long long)c * nf;
+    const double *gp = p.gradp + (long long)c * nf;
+    const double e = p.eps[c];
+    const double h = 0.5 * e * e;
+    double s0 = 0, s0p = 0, fw = 0, bw = 0, tr = 0, ti = 0, trp = 0, tip = 0;
+    for (int f = tid; f < nf; f += blockDim.x) {
+        double a = ph[f], b = pp[f];
+        s0 += 0.5 * a * a;
+        s0p += 0.5 * b * b;
+        double x = b - a + h * g[f];
+        double y = a - b + h * gp[f];
+        fw += x * x;
+        bw += y * y;
+    }
+    for (int q = tid; q < nq; q += blockDim.x) {
+        cd z = zfield(ph, p.fkind[q], p.frA[q], p.frB[q]);
+        cd zp = zfield(pp, p.fkind[q], p.frA[q], p.frB[q]);
+        cd a = cmul(z, p.trF[q]), b = cmul(zp, p.trF[q]);
+        tr += a.x;
+        ti += a.y;
+        trp += b.x;
+        tip += b.y;
+    }
+    s0 = block_sum(s0, sh);
+    s0p = block_sum(s0p, sh);
+    fw = block_sum(fw, sh);
+    bw = block_sum(bw, sh);
+    tr = block_sum(tr, sh);
+    ti = block_sum(ti, sh);
+    trp = block_sum(trp, sh);
+    tip = block_sum(tip, sh);
+    if (tid == 0) {
+        cd a0 = p.alpha[c * 4];
+        cd w0 = cscale(cmul(a0, cmk(tr, ti)), 2.0);
+        cd w0p = cscale(cmul(a0, cmk(trp, tip)), 2.0);
+        cd lr = csub(p.logdet[c], cscale(csub(w0p, w0), 0.5));
+        double logA = 2.0 * lr.x - (s0p - s0) - bw / (2 * e * e) + fw / (2 * e * e);
+        u32x4 wv = philox10(u32x4{0u, (uint32_t)(p.slice - 1), p.sweep, (uint32_t)RNG_ACCEPT},
+                            p.keys[2 * c], p.keys[2 * c + 1]);
+        double logu = log(unif53(wv.a, wv.b));
+        int acc = logu < logA;
+        if (!isfinite(logA) || !isfinite(lr.x)) {
+            acc = 0;
+            atomicOr(p.errf + c, 4);
+        }
+        double sd = fabs(sin(lr.y));
+        p.flag[c] = acc;
+        double *st = p.st + c * 4;
+        st[0] += acc;
+        if (sd > st[2]) st[2] = sd;
+        if (sd > p.sign_tol) atomicOr(p.errf + c, 2);
+        if (p.trace) {
+            long long k = p.trace_n[c];
+            if (k < p.trace_cap) {
+                double *rw = p.trace + ((long long)c * p.trace_cap + k) * 8;
+                rw[0] = p.sweep;
+                rw[1] = p.slice;
+                rw[2] = lr.x;
+                rw[3] = lr.y;
+                rw[4] = logA;
+                rw[5] = logu;
+                rw[6] = acc;
+                rw[7] = e;
+                p.trace_n[c] = k + 1;
+            }
+        }
+    }
+}
+
+// accepted proposals replace the slice's fields, propagators, eigenpairs and G
+__global__ void k_commit(CommitP p)
+{
+    const int c = blockIdx.y;
+    if (!p.flag[c]) return;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long NN = (long long)p.N * p.N, n2 = (long long)p.n * p.n;
+    const long long cs = (long long)c * p.L + p.s;  // (chain, slice)
+    if (e < NN) {
+        p.B[cs * NN + e] = p.Bp[c * NN + e];
+        p.Binv[cs * NN + e] = p.Bpi[c * NN + e];
+        p.G[c * NN + e] = p.Gp[c * NN + e];
+    }
+    if (e < 4 * n2) p.U[cs * 4 * n2 + e] = p.Up[c * 4 * n2 + e];
+    if (e < 4 * p.n) p.W[cs * 4 * p.n + e] = p.Wp[c * 4 * p.n + e];
+    if (e < p.nf) p.phi[cs * p.nf + e] = p.phip[(long long)c * p.nf + e];
+}
+
+// -------------------------------------------------------- stabilisation --
+// Y = X diag(d) (d real)
+__global__ void k_scale_cols(int nb, int N, const cd *X, long long sX, const double *d,
+                             long long sd, cd *Y, long long sY)
+{
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    int c = blockIdx.y;
+    if (e >= N * N) return;
+    Y[(long long)c * sY + e] = cscale(X[(long long)c * sX + e], d[(long long)c * sd + e % N]);
+}
+
+// X = DbR^-1 T1 DbL^-1 + DsR T2 DsL with Db = max(D,1), Ds = min(D,1)
+__global__ void k_stab_mix(int nb, int N, const cd *T1, const cd *T2, const double *DR,
+                           long long sDR, const double *DL, long long sDL, cd *X)
+{
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    int c = blockIdx.y;
+    if (e >= N * N) return;
+    int r = e / N, k = e % N;
+    double dr = DR[(long long)c * sDR + r], dl = DL[(long long)c * sDL + k];
+    double dbr = dr > 1 ? dr : 1, dsr = dr > 1 ? 1 : dr;
+    double dbl = dl > 1 ? dl : 1, dsl = dl > 1 ? 1 : dl;
+    long long o = (long long)c * N * N + e;
+    cd a = cscale(T1[o], 1.0 / (dbr * dbl));
+    cd b = cscale(T2[o], dsr * dsl);
+    X[o] = cadd(a, b);
+}
+
+// the diagonals 1/max(D,1) as complex vectors (GEMM scaling) and the
+// column scaling of QL by 1/max(DL,1)
+__global__ void k_inv_big(int nb, int N, const double *D, long long sD, cd *out)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int c = blockIdx.y;
+    if (x >= N) return;
+    double d = D[(long long)c * sD + x];
+    out[(long long)c * N + x] = cmk(1.0 / (d > 1 ? d : 1), 0.0);
+}
+
+// err = max |Gs - G| / max |Gs|; G <- Gs
+__global__ void __launch_bounds__(256) k_stab_err(int N, cd *G, const cd *Gs, double *st,
+                                                  int *errf, double tol)
+{
+    __shared__ double sh[2][32];
+    const int c = blockIdx.x, tid = threadIdx.x;
+    const long long NN = (long long)N * N;
+    double dm = 0, gm = 0;
+    for (long long e = tid; e < NN; e += blockDim.x) {
+        cd a = Gs[c * NN + e], b = G[c * NN + e];
+        double d = cabs2(csub(a, b)), g = cabs2(a);
+        dm = d > dm ? d : dm;
+        gm = g > gm ? g : gm;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        double x = __shfl_xor_sync(0xffffffffu, dm, o), y = __shfl_xor_sync(0xffffffffu, gm, o);
+        dm = x > dm ? x : dm;
+        gm = y > gm ? y : gm;
+    }
+    if ((tid & 31) == 0) {
+        sh[0][tid >> 5] = dm;
+        sh[1][tid >> 5] = gm;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int w = 0; w < (int)blockDim.x / 32; ++w) {
+            dm = sh[0][w] > dm ? sh[0][w] : dm;
+            gm = sh[1][w] > gm ? sh[1][w] : gm;
+        }
+        double err = gm > 0 ? sqrt(dm / gm) : sqrt(dm);
+        if (!(err == err)) {
+            atomicOr(errf + c, 4);
+        } else {
+            if (err > st[c * 4 + 1]) st[c * 4 + 1] = err;
+            if (err > tol) atomicOr(errf + c, 1);
+        }
+    }
+    __syncthreads();
+    for (long long e = tid; e < NN; e += blockDim.x) G[c * NN + e] = Gs[c * NN + e];
+}
+
+// ------------------------------------------------------- measurements ----
+// a(i,q) = Tr[(O^i (x) F_q)(1 - G)],
+// x(i,q) = Tr[(O^i (x) F_q) G (O^i (x) F_qbar)(1 - G)]  (Wick's theorem for
+// one spin block; O^i (x) F_q has one entry per row)
+__global__ void __launch_bounds__(256) k_meas_ax(int n, int nq, const cd *G, const cd *val,
+                                                 const int *col, const int *partner, cd *ax)
+{
+    __shared__ double sh[32];
+    const int q = blockIdx.x, i = blockIdx.y, c = blockIdx.z, tid = threadIdx.x;
+    const int N = 2 * n;
+    const cd *Gc = G + (long long)c * N * N;
+    const int qb = partner[q];
+    double ar = 0, ai = 0, xr = 0, xi = 0;
+    // a
+    for (int x = tid; x < N; x += blockDim.x) {
+        int v = x / n, k = x % n;
+        int w = (i == 1 || i == 2) ? 1 - v : v;
+        int cc = col[q * n + k];
+        if (cc < 0) continue;
+        int px = w * n + cc;
+        cd m = cmul(valley_O(i, v, w), val[q * n + k]);
+        cd g = Gc[(long long)px * N + x];
+        cd one_m_g = cmk((px == x ? 1.0 : 0.0) - g.x, -g.y);
+        cd t = cmul(m, one_m_g);
+        ar += t.x;
+        ai += t.y;
+    }
+    // x: sum over rows x and y' of M_q[x,px] G[px,y'] M_qb[y',py] (1-G)[py,x]
+    for (int t = tid; t < N * N; t += blockDim.x) {
+        int x = t / N, y = t % N;
+        int v = x / n, k = x % n;
+        int w = (i == 1 || i == 2) ? 1 - v : v;
+        int cc = col[q * n + k];
+        if (cc < 0) continue;
+        int px = w * n + cc;
+        int v2 = y / n, k2 = y % n;
+        int w2 = (i == 1 || i == 2) ? 1 - v2 : v2;
+        int cc2 = col[qb * n + k2];
+        if (cc2 < 0) continue;
+        int py = w2 * n + cc2;
+        cd m1 = cmul(valley_O(i, v, w), val[q * n + k]);
+        cd m2 = cmul(valley_O(i, v2, w2), val[qb * n + k2]);
+        cd g1 = Gc[(long long)px * N + y];
+        cd g2 = Gc[(long long)py * N + x];
+        cd omg = cmk((py == x ? 1.0 : 0.0) - g2.x, -g2.y);
+        cd r = cmul(cmul(m1, g1), cmul(m2, omg));
+        xr += r.x;
+        xi += r.y;
+    }
+    ar = block_sum(ar, sh);
+    ai = block_sum(ai, sh);
+    xr = block_sum(xr, sh);
+    xi = block_sum(xi, sh);
+    if (tid == 0) {
+        cd *o = ax + (((long long)c * 4 + i) * nq + q) * 2;
+        o[0] = cmk(ar, ai);
+        o[1] = cmk(xr, xi);
+    }
+}
+
+// per chain: S^i_q for Gamma^1..5, m^2_SO(5), correlation ratio, energy
+__global__ void __launch_bounds__(256) k_meas_final(MeasP p)
+{
+    __shared__ double sh[32];
+    const int c = blockIdx.x, tid = threadIdx.x, nq = p.nq;
+    const cd *ax = p.ax + (long long)c * 4 * nq * 2;
+    double E = 0.0;
+    for (int t = tid; t < 4 * nq; t += blockDim.x) {
+        int i = t / nq, q = t % nq, qb = p.partner[q];
+        cd a = cscale(ax[(i * nq + q) * 2], 2.0), ab = cscale(ax[(i * nq + qb) * 2], 2.0);
+        if (i == 0) {
+            a = csub(a, cscale(p.trF[q], 2.0));
+            ab = csub(ab, cscale(p.trF[qb], 2.0));
+        }
+        cd x = cscale(ax[(i * nq + q) * 2 + 1], 2.0);
+        E += p.g[c * 4 + i] * (cmul(a, ab).x + x.x);
+    }
+    E = block_sum(E, sh);
+    if (tid == 0) {
+        double S0[5], Sd[5];
+        for (int which = 0; which < 2; ++which) {
+            int nl = which == 0 ? 1 : p.ndq;
+            double acc[5] = {0, 0, 0, 0, 0};
+            for (int e = 0; e < nl; ++e) {
+                int q = which == 0 ? p.q0 : p.dq[e];
+                int qb = p.partner[q];
+                for (int i = 1; i <= 2; ++i) {
+                    cd a = ax[(i * nq + q) * 2], ab = ax[(i * nq + qb) * 2];
+                    cd x = ax[(i * nq + q) * 2 + 1];
+                    acc[i - 1] += 4.0 * cmul(a, ab).x + 2.0 * x.x;
+                }
+                double s3 = 2.0 * ax[(3 * nq + q) * 2 + 1].x;
+                acc[2] += s3;
+                acc[3] += s3;
+                acc[4] += s3;
+            }
+            for (int i = 0; i < 5; ++i) {
+                if (which == 0) S0[i] = acc[i];
+                else Sd[i] = acc[i] / nl;
+            }
+        }
+        double *o = p.out + (long long)c * p.out_cs;
+        double t0 = 0, td = 0;
+        for (int i = 0; i < 5; ++i) {
+            o[1 + i] = S0[i];
+            o[6 + i] = Sd[i];
+            t0 += S0[i];
+            td += Sd[i];
+        }
+        o[0] = t0 / (5.0 * (double)p.n * (double)p.n);
+        o[11] = t0 != 0 ? 1.0 - td / t0 : 0.0;
+        o[12] = E;
+        const double *st = p.st + c * 4;
+        o[13] = st[0] / p.L;
+        o[14] = p.eps_used ? p.eps_used[c] : 0.0;
+        o[15] = st[1];
+        o[16] = st[2];
+        o[17] = st[0];
+        o[18] = 0.0;
+        o[19] = 0.0;
+    }
+}
+
+// eps <- eps + (r_a - r_0) d_eps, clamped to [1e-4, 10]; reset sweep stats
+__global__ void k_end_sweep(int nb, int L, int adapt, double r0, double deps, double *eps,
+                            double *eps_used, double *st)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nb) return;
+    if (adapt) {
+        double ra = st[c * 4] / L;
+        double e = eps[c] + (ra - r0) * deps;
+        e = e < 1e-4 ? 1e-4 : (e > 10.0 ? 10.0 : e);
+        eps[c] = e;
+    }
+    st[c * 4 + 0] = 0;
+    st[c * 4 + 1] = 0;
+    st[c * 4 + 2] = 0;
+    eps_used[c] = eps[c];
+}
+
+// --------------------------------------------------------- launchers -----
+void launch_ff_torus(cudaStream_t s, int n, int nq, const int *qxy, cd *val, int *col, cd *trF)
+{
+    k_ff_torus<<<cdiv_up(nq * n, 256), 256, 0, s>>>(n, nq, qxy, val, col);
+    k_trF<<<cdiv_up(nq, 128), 128, 0, s>>>(n, nq, val, col, trF);
+}
+void launch_init_phi(cudaStream_t s, int nb, int L, int nf, const uint32_t *keys, double *phi)
+{
+    long long tot = (long long)nb * L * nf;
+    k_init_phi<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(nb, L, nf, keys, phi);
+}
+void launch_assemble(cudaStream_t s, int nb, int n, int nq, const double *phi, long long phi_cs,
+                     const int *fkind, const int *frA, const int *frB, const int *aptr,
+                     const int *aq, const cd *val, cd *F)
+{
+    k_assemble<<<dim3(cdiv_up(n * n, 128), 4, nb), 128, 0, s>>>(nb, n, nq, phi, phi_cs, fkind, frA,
+                                                                frB, aptr, aq, val, F);
+}
+void launch_build_V(cudaStream_t s, int nb, int n, const cd *U, long long U_cs, cd *V)
+{
+    int N = 2 * n;
+    k_build_V<<<dim3(cdiv_up(N * N, 256), 4, nb), 256, 0, s>>>(nb, n, U, U_cs, V);
+}
+void launch_lambda(cudaStream_t s, int nb, int n, const double *w, long long w_cs,
+                   const cd *alpha, cd *lam, cd *Dg, cd *Dgi)
+{
+    k_lambda<<<dim3(cdiv_up(2 * n, 128), 7, nb), 128, 0, s>>>(nb, n, w, w_cs, alpha, lam, Dg, Dgi);
+}
+void launch_accum(cudaStream_t s, int nb, int N, int j, int first, const cd *alpha,
+                  const cd *lam, const cd *Ah, cd *Cacc)
+{
+    k_accum<<<dim3(cdiv_up(N * N, 256), nb), 256, 0, s>>>(nb, N, j, first, alpha, lam, Ah, Cacc);
+}
+void launch_trace_grad(cudaStream_t s, int nb, int n, int nq, const cd *At, const cd *val,
+                       const int *col, const cd *trF, const cd *alpha, cd *t, const int *fq,
+                       const int *fk, const int *partner, const double *phi, long long phi_cs,
+                       double *grad)
+{
+    k_trace_t<<<dim3(cdiv_up(nq, 64), 4, nb), 64, 0, s>>>(nb, n, nq, At, val, col, trF, alpha, t);
+    k_grad<<<dim3(cdiv_up(4 * nq, 128), nb), 128, 0, s>>>(nb, nq, fq, fk, partner, phi, phi_cs, t,
+                                                           grad);
+}
+void launch_propose(cudaStream_t s, int nb, int nf, const double *phi, long long phi_cs,
+                    const double *grad, const double *eps, const uint32_t *keys, uint32_t slice,
+                    uint32_t sweep, double *phip)
+{
+    k_propose<<<dim3(cdiv_up(nf, 128), nb), 128, 0, s>>>(nb, nf, phi, phi_cs, grad, eps, keys, slice,
+                                                          sweep, phip);
+}
+void launch_axpyI(cudaStream_t s, int nb, int N, const cd *X, long long sX, cd a, cd b, cd *Y,
+                  long long sY)
+{
+    k_axpyI<<<dim3(cdiv_up(N * N, 256), nb), 256, 0, s>>>(nb, N, X, sX, a, b, Y, sY);
+}
+void launch_accept(cudaStream_t s, int nb, const AcceptP &p)
+{
+    k_accept<<<nb, 256, 0, s>>>(p);
+}
+void launch_commit(cudaStream_t s, int nb, const CommitP &p)
+{
+    long long mx = (long long)p.N * p.N;
+    if (p.nf > mx) mx = p.nf;
+    k_commit<<<dim3((unsigned)((mx + 255) / 256), nb), 256, 0, s>>>(p);
+}
+void launch_scale_cols(cudaStream_t s, int nb, int N, const cd *X, long long sX, const double *d,
+                       long long sd, cd *Y, long long sY)
+{
+    k_scale_cols<<<dim3(cdiv_up(N * N, 256), nb), 256, 0, s>>>(nb, N, X, sX, d, sd, Y, sY);
+}
+void launch_stab_mix(cudaStream_t s, int nb, int N, const cd *T1, const cd *T2, const double *DR,
+                     long long sDR, const double *DL, long long sDL, cd *X)
+{
+    k_stab_mix<<<dim3(cdiv_up(N * N, 256), nb), 256, 0, s>>>(nb, N, T1, T2, DR, sDR, DL, sDL, X);
+}
+void launch_inv_big(cudaStream_t s, int nb, int N, const double *D, long long sD, cd *out)
+{
+    k_inv_big<<<dim3(cdiv_up(N, 128), nb), 128, 0, s>>>(nb, N, D, sD, out);
+}
+void launch_stab_err(cudaStream_t s, int nb, int N, cd *G, const cd *Gs, double *st, int *errf,
+                     double tol)
+{
+    k_stab_err<<<nb, 256, 0, s>>>(N, G, Gs, st, errf, tol);
+}
+void launch_measure(cudaStream_t s, int nb, int n, int nq, const cd *G, const cd *val,
+                    const int *col, const int *partner, cd *ax, const MeasP &p)
+{
+    k_meas_ax<<<dim3(nq, 4, nb), 256, 0, s>>>(n, nq, G, val, col, partner, ax);
+    k_meas_final<<<nb, 256, 0, s>>>(p);
+}
+void launch_end_sweep(cudaStream_t s, int nb, int L, int adapt, double r0, double deps,
+                      double *eps, double *eps_used, double *st)
+{
+    k_end_sweep<<<cdiv_up(nb, 64), 64, 0, s>>>(nb, L, adapt, r0, deps, eps, eps_used, st);
+}

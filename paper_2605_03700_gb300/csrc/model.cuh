@@ -1,0 +1,78 @@
+// model.cuh -- CF-DQMC model kernels of libqmc (see model.cu)
+#pragma once
+#include "qmc_internal.cuh"
+
+struct AcceptP {
+    int nq;
+    const double *phi;
+    long long phi_cs;
+    const double *phip, *grad, *gradp, *eps;
+    const cd *alpha, *logdet, *trF;
+    const int *fkind, *frA, *frB;
+    const uint32_t *keys;
+    int slice;  // 1-based
+    uint32_t sweep;
+    int *flag;
+    double *st;  // per chain: accepted, max stab err, max sign dev, spare
+    int *errf;
+    double sign_tol;
+    double *trace;
+    long long trace_cap;
+    long long *trace_n;
+};
+
+struct CommitP {
+    int N, n, nf, L, s;  // s: 0-based slice
+    const int *flag;
+    cd *B, *Binv, *G, *U;
+    double *W, *phi;
+    const cd *Bp, *Bpi, *Gp, *Up;
+    const double *Wp, *phip;
+};
+
+struct MeasP {
+    int nq, n, L;
+    const cd *ax;
+    const int *partner;
+    const cd *trF;
+    const double *g;
+    int q0, ndq;
+    int dq[8];
+    double *out;
+    long long out_cs;
+    const double *st;
+    const double *eps_used;
+};
+
+void launch_ff_torus(cudaStream_t s, int n, int nq, const int *qxy, cd *val, int *col, cd *trF);
+void launch_init_phi(cudaStream_t s, int nb, int L, int nf, const uint32_t *keys, double *phi);
+void launch_assemble(cudaStream_t s, int nb, int n, int nq, const double *phi, long long phi_cs,
+                     const int *fkind, const int *frA, const int *frB, const int *aptr,
+                     const int *aq, const cd *val, cd *F);
+void launch_build_V(cudaStream_t s, int nb, int n, const cd *U, long long U_cs, cd *V);
+void launch_lambda(cudaStream_t s, int nb, int n, const double *w, long long w_cs,
+                   const cd *alpha, cd *lam, cd *Dg, cd *Dgi);
+void launch_accum(cudaStream_t s, int nb, int N, int j, int first, const cd *alpha,
+                  const cd *lam, const cd *Ah, cd *Cacc);
+void launch_trace_grad(cudaStream_t s, int nb, int n, int nq, const cd *At, const cd *val,
+                       const int *col, const cd *trF, const cd *alpha, cd *t, const int *fq,
+                       const int *fk, const int *partner, const double *phi, long long phi_cs,
+                       double *grad);
+void launch_propose(cudaStream_t s, int nb, int nf, const double *phi, long long phi_cs,
+                    const double *grad, const double *eps, const uint32_t *keys, uint32_t slice,
+                    uint32_t sweep, double *phip);
+void launch_axpyI(cudaStream_t s, int nb, int N, const cd *X, long long sX, cd a, cd b, cd *Y,
+                  long long sY);
+void launch_accept(cudaStream_t s, int nb, const AcceptP &p);
+void launch_commit(cudaStream_t s, int nb, const CommitP &p);
+void launch_scale_cols(cudaStream_t s, int nb, int N, const cd *X, long long sX, const double *d,
+                       long long sd, cd *Y, long long sY);
+void launch_stab_mix(cudaStream_t s, int nb, int N, const cd *T1, const cd *T2, const double *DR,
+                     long long sDR, const double *DL, long long sDL, cd *X);
+void launch_inv_big(cudaStream_t s, int nb, int N, const double *D, long long sD, cd *out);
+void launch_stab_err(cudaStream_t s, int nb, int N, cd *G, const cd *Gs, double *st, int *errf,
+                     double tol);
+void launch_measure(cudaStream_t s, int nb, int n, int nq, const cd *G, const cd *val,
+                    const int *col, const int *partner, cd *ax, const MeasP &p);
+void launch_end_sweep(cudaStream_t s, int nb, int L, int adapt, double r0, double deps,
+                      double *eps, double *eps_used, double *st);

@@ -1,0 +1,210 @@
+"""Thin ctypes binding of libqmc (include/qmc.h).
+
+Argument marshalling only: every step of the sweep runs in the CUDA library.
+The functions carry the C names; ``Chain`` is a small convenience wrapper.
+There is no CPU fallback: if libqmc.so is missing or no CUDA device is
+present, loading fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB = os.path.join(HERE, "libqmc.so")
+
+QMC_TORUS = 0
+QMC_SPHERE = 1
+QMC_NOBS = 20
+QMC_NTRACE = 8
+OBS_NAMES = ["m2", "S1_0", "S2_0", "S3_0", "S4_0", "S5_0", "S1_dq", "S2_dq",
+             "S3_dq", "S4_dq", "S5_dq", "R", "E", "acc", "eps", "stab_err",
+             "sign_dev", "n_acc", "_", "_"]
+
+
+class qmc_opts(C.Structure):
+    _fields_ = [
+        ("n_stab", C.c_int),
+        ("precision", C.c_int),
+        ("eps0", C.c_double),
+        ("deps", C.c_double),
+        ("r0", C.c_double),
+        ("n_adapt", C.c_int),
+        ("n_orb_sphere", C.c_int),
+        ("n_chains", C.c_int),
+        ("couplings", C.POINTER(C.c_double)),
+        ("anisotropies", C.POINTER(C.c_double)),
+        ("seeds", C.POINTER(C.c_uint64)),
+        ("series_capacity", C.c_int),
+        ("trace_capacity", C.c_int),
+        ("stab_tol", C.c_double),
+        ("sign_tol", C.c_double),
+    ]
+
+
+class QMCError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def lib():
+    """Load libqmc.so (built by paper_2605_03700_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise QMCError(f"{LIB} is missing: run paper_2605_03700_gb300.build.build() first")
+        L = C.CDLL(LIB)
+        vp, dp = C.c_void_p, C.POINTER(C.c_double)
+        L.qmc_default_opts.argtypes = [C.POINTER(qmc_opts)]
+        L.qmc_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.c_double, C.c_double,
+                                 C.c_double, C.c_double, C.c_uint64, C.POINTER(qmc_opts)]
+        L.qmc_destroy.argtypes = [vp]
+        L.qmc_set_stream.argtypes = [vp, vp]
+        L.qmc_sweep.argtypes = [vp, C.c_int]
+        L.qmc_sync.argtypes = [vp]
+        L.qmc_measure.argtypes = [vp, dp]
+        L.qmc_get_series.argtypes = [vp, C.c_int, dp]
+        L.qmc_series_length.argtypes = [vp]
+        L.qmc_get_green.argtypes = [vp, C.c_int, dp, C.c_size_t]
+        L.qmc_get_green_block.argtypes = [vp, C.c_int, dp, C.c_size_t]
+        L.qmc_get_fields.argtypes = [vp, C.c_int, dp, C.c_size_t]
+        L.qmc_get_trace.argtypes = [vp, C.c_int, dp, C.c_size_t, C.POINTER(C.c_long)]
+        L.qmc_sizes.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                C.POINTER(C.c_int)]
+        L.qmc_get_eps.argtypes = [vp, dp]
+        L.qmc_tau_int.restype = C.c_double
+        L.qmc_tau_int.argtypes = [dp, C.c_int]
+        L.qmc_strerror.restype = C.c_char_p
+        L.qmc_strerror.argtypes = [C.c_int]
+        L.qmc_last_error.restype = C.c_char_p
+        L.qmc_last_error.argtypes = [vp]
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _check(code, h=None):
+    if code != 0:
+        msg = lib().qmc_strerror(code).decode()
+        if h:
+            msg += ": " + lib().qmc_last_error(h).decode()
+        raise QMCError(f"libqmc error {code}: {msg}")
+
+
+def qmc_default_opts() -> qmc_opts:
+    o = qmc_opts()
+    _check(lib().qmc_default_opts(C.byref(o)))
+    return o
+
+
+def qmc_tau_int(x) -> float:
+    x = np.ascontiguousarray(x, dtype=float)
+    return lib().qmc_tau_int(_dp(x), len(x))
+
+
+class Chain:
+    """A batch of independent CF-DQMC chains resident on the current GPU."""
+
+    def __init__(self, geometry, N_phi, beta, dtau, coupling, anisotropy=0.0, seed=0, *,
+                 n_chains=1, couplings=None, anisotropies=None, seeds=None, n_stab=10,
+                 eps0=0.5, deps=0.1, r0=0.574, n_adapt=-1, series_capacity=4096,
+                 trace_capacity=0, stab_tol=1e-6, sign_tol=1e-6, stream=None):
+        o = qmc_default_opts()
+        o.n_stab = n_stab
+        o.eps0, o.deps, o.r0, o.n_adapt = eps0, deps, r0, n_adapt
+        o.n_chains = n_chains
+        o.series_capacity = series_capacity
+        o.trace_capacity = trace_capacity
+        o.stab_tol, o.sign_tol = stab_tol, sign_tol
+        self._keep = []
+        if couplings is not None:
+            a = np.ascontiguousarray(couplings, dtype=float)
+            self._keep.append(a)
+            o.couplings = _dp(a)
+        if anisotropies is not None:
+            a = np.ascontiguousarray(anisotropies, dtype=float)
+            self._keep.append(a)
+            o.anisotropies = _dp(a)
+        if seeds is not None:
+            a = np.ascontiguousarray(seeds, dtype=np.uint64)
+            self._keep.append(a)
+            o.seeds = a.ctypes.data_as(C.POINTER(C.c_uint64))
+        h = C.c_void_p()
+        if stream is not None:
+            pass
+        _check(lib().qmc_create(C.byref(h), geometry, N_phi, beta, dtau, coupling, anisotropy,
+                                seed, C.byref(o)))
+        self.h = h
+        if stream is not None:
+            self.set_stream(stream)
+        n_orb, n_q, L, nb = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        lib().qmc_sizes(h, C.byref(n_orb), C.byref(n_q), C.byref(L), C.byref(nb))
+        self.n_orb, self.n_q, self.L, self.n_chains = n_orb.value, n_q.value, L.value, nb.value
+        self.N = 2 * self.n_orb
+        self.trace_capacity = trace_capacity
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().qmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        """stream: a cudaStream_t handle as int (e.g. torch.cuda.Stream().cuda_stream)."""
+        _check(lib().qmc_set_stream(self.h, C.c_void_p(int(stream))), self.h)
+
+    def sweep(self, n=1):
+        _check(lib().qmc_sweep(self.h, n), self.h)
+
+    def sync(self):
+        _check(lib().qmc_sync(self.h), self.h)
+
+    def measure(self):
+        out = np.zeros((self.n_chains, QMC_NOBS))
+        _check(lib().qmc_measure(self.h, _dp(out)), self.h)
+        return out
+
+    def series(self, count=None):
+        n = lib().qmc_series_length(self.h)
+        count = n if count is None else count
+        out = np.zeros((self.n_chains, count, QMC_NOBS))
+        _check(lib().qmc_get_series(self.h, count, _dp(out)), self.h)
+        return out
+
+    def green(self, chain=0, block=True):
+        if block:
+            G = np.zeros((self.N, self.N), complex)
+            _check(lib().qmc_get_green_block(self.h, chain, _dp(G.view(float)), 2 * G.size), self.h)
+        else:
+            G = np.zeros((2 * self.N, 2 * self.N), complex)
+            _check(lib().qmc_get_green(self.h, chain, _dp(G.view(float)), 2 * G.size), self.h)
+        return G
+
+    def fields(self, chain=0):
+        p = np.zeros((self.L, 4, self.n_q))
+        _check(lib().qmc_get_fields(self.h, chain, _dp(p), p.size), self.h)
+        return p
+
+    def trace(self, chain=0):
+        cap = max(self.trace_capacity, 1)
+        buf = np.zeros((cap, QMC_NTRACE))
+        cnt = C.c_long()
+        _check(lib().qmc_get_trace(self.h, chain, _dp(buf), buf.size, C.byref(cnt)), self.h)
+        return buf[: cnt.value].copy()
+
+    def eps(self):
+        out = np.zeros(self.n_chains)
+        _check(lib().qmc_get_eps(self.h, _dp(out)), self.h)
+        return out

@@ -1,0 +1,148 @@
+"""Parity of the CUDA sweep (libqmc, FP64) with the FP64 CPU oracle.
+
+Same seeds, same Philox streams, same slice order: the two must make
+identical accept/reject decisions, agree on every log determinant ratio to
+1e-10 and on G to 1e-9 relative (max-norm over the matrix relative to
+max|G|).  Cases span several GEMM tiles and ragged tails (N = 2 N_phi not a
+multiple of 16, odd N_phi for the Jacobi ordering, L not a multiple of
+n_stab), batches of chains with different couplings, the full matrix size of
+the N_phi = 36 workload, and its full imaginary-time length on
+size-independent properties.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import model as M
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL_LOGR = 1e-10
+TOL_G = 1e-9
+
+
+@pytest.fixture(scope="module")
+def qmc():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2605_03700_gb300 import build
+    build.build()
+    import paper_2605_03700_gb300 as P
+    return P
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _compare_chain(gpu, c, orc, nsw, trace_gpu, trace_orc):
+    assert len(trace_gpu) == len(trace_orc) == nsw * orc.L
+    # identical decisions and per-update quantities
+    assert np.array_equal(trace_gpu[:, 6], trace_orc[:, 6]), "accept decisions differ"
+    assert np.array_equal(trace_gpu[:, :2], trace_orc[:, :2])
+    assert np.abs(trace_gpu[:, 2] - trace_orc[:, 2]).max() < TOL_LOGR
+    dA = np.abs(trace_gpu[:, 4] - trace_orc[:, 4]) / np.maximum(1, np.abs(trace_orc[:, 4]))
+    assert dA.max() < 1e-8
+    assert np.abs(trace_gpu[:, 5] - trace_orc[:, 5]).max() < 1e-12
+    assert np.abs(trace_gpu[:, 7] - trace_orc[:, 7]).max() < 1e-12
+    assert _rel(gpu.green(c), orc.green()) < TOL_G
+    assert np.abs(gpu.fields(c) - orc.phi()).max() < 1e-9
+
+
+def test_config1_ten_thousand_updates_decision_identical(qmc):
+    """torus N_phi = 4 (N = 8, N_q = 37), beta = 2, dtau = 0.1, u = 1,
+    seed 0, stabilise every 5 slices: 500 sweeps x 20 slices = 10^4 updates."""
+    nsw = 500
+    g = qmc.Chain(qmc.QMC_TORUS, 4, 2.0, 0.1, 1.0, 0.0, 0, n_stab=5, trace_capacity=nsw * 20)
+    g.sweep(nsw)
+    g.sync()
+    o = O.Chain(M.TORUS, 4, 2.0, 0.1, 1.0, 0.0, 0, n_stab=5)
+    o.enable_trace(nsw * 20)
+    obs_o = o.sweep(nsw)
+    _compare_chain(g, 0, o, nsw, g.trace(0), o.trace())
+    obs_g = g.series()[0]
+    assert obs_g.shape == obs_o.shape
+    for col in (0, 1, 3, 6, 11, 12):
+        assert np.abs(obs_g[:, col] - obs_o[:, col]).max() < 1e-9 * max(1, np.abs(obs_o[:, col]).max())
+    assert np.array_equal(obs_g[:, 17], obs_o[:, 17])
+    assert np.abs(obs_g[:, 14] - obs_o[:, 14]).max() < 1e-12
+    assert obs_g[:, 15].max() < 1e-9 and obs_g[:, 16].max() < 1e-9
+
+
+@pytest.mark.parametrize("nphi,beta,nstab", [(3, 1.3, 5), (5, 1.0, 4), (9, 0.8, 3)])
+def test_ragged_sizes_parity(qmc, nphi, beta, nstab):
+    nsw = 6
+    L = int(round(beta / 0.1))
+    g = qmc.Chain(qmc.QMC_TORUS, nphi, beta, 0.1, 1.5, 0.1, 7, n_stab=nstab, trace_capacity=nsw * L)
+    g.sweep(nsw)
+    g.sync()
+    o = O.Chain(M.TORUS, nphi, beta, 0.1, 1.5, 0.1, 7, n_stab=nstab)
+    o.enable_trace(nsw * L)
+    o.sweep(nsw)
+    _compare_chain(g, 0, o, nsw, g.trace(0), o.trace())
+
+
+def test_batched_chains_with_different_couplings(qmc):
+    us = [0.5, 1.2, 2.0]
+    als = [0.0, 0.1, -0.15]
+    seeds = [3, 11, 42]
+    nsw = 20
+    g = qmc.Chain(qmc.QMC_TORUS, 4, 1.0, 0.1, 0.0, 0.0, 0, n_chains=3, couplings=us,
+                  anisotropies=als, seeds=seeds, n_stab=5, trace_capacity=nsw * 10)
+    g.sweep(nsw)
+    g.sync()
+    for c in range(3):
+        o = O.Chain(M.TORUS, 4, 1.0, 0.1, us[c], als[c], seeds[c], n_stab=5)
+        o.enable_trace(nsw * 10)
+        o.sweep(nsw)
+        _compare_chain(g, c, o, nsw, g.trace(c), o.trace())
+
+
+def test_full_matrix_size_of_the_nphi36_workload(qmc):
+    """N_phi = 36 (N = 72, N_q = 333, 1332 fields per slice), the matrix
+    sizes the benchmark times, with a short imaginary-time axis the oracle
+    finishes in seconds: beta = 0.4, L = 4, two chains, u in {0.5, 2.0}."""
+    us = [0.5, 2.0]
+    g = qmc.Chain(qmc.QMC_TORUS, 36, 0.4, 0.1, 0.0, 0.0, 0, n_chains=2, couplings=us,
+                  seeds=[0, 1], n_stab=10, eps0=0.2, trace_capacity=8)
+    g.sweep(2)
+    g.sync()
+    m = M.Model(M.TORUS, 36)
+    for c in range(2):
+        o = O.Chain(M.TORUS, 36, 0.4, 0.1, us[c], 0.0, c, n_stab=10, eps0=0.2, model=m)
+        o.enable_trace(8)
+        o.sweep(2)
+        _compare_chain(g, c, o, 2, g.trace(c), o.trace())
+
+
+def test_full_length_nphi36_properties(qmc):
+    """The benchmark's workload itself (N_phi = 36, beta = 36, L = 360, eight
+    couplings in [0.5, 2.0], stabilisation every 10 slices): properties that
+    hold at any size -- sign-free ratios, G fresh to 1e-8 at every
+    restabilisation, the full 4 N_phi Green's function equal to G (x) I_spin,
+    finite observables with S^3 = S^4 = S^5."""
+    us = np.linspace(0.5, 2.0, 8)
+    g = qmc.Chain(qmc.QMC_TORUS, 36, 36.0, 0.1, 0.0, 0.0, 0, n_chains=8, couplings=us,
+                  seeds=np.arange(8), n_stab=10, eps0=0.2)
+    g.sweep(1)
+    g.sync()
+    s = g.series()
+    assert s.shape == (8, 1, 20)
+    assert s[:, :, 15].max() < 1e-8
+    assert s[:, :, 16].max() < 1e-8
+    assert np.all(np.isfinite(s))
+    assert np.all(s[:, :, 3] == s[:, :, 4]) and np.all(s[:, :, 4] == s[:, :, 5])
+    Gf = g.green(3, block=False)
+    Gb = g.green(3)
+    N = Gb.shape[0]
+    assert np.array_equal(Gf[:N, :N], Gb) and np.array_equal(Gf[N:, N:], Gb)
+    assert np.abs(Gf[:N, N:]).max() == 0 and np.abs(Gf[N:, :N]).max() == 0
+
+
+def test_tau_int_matches_oracle_estimator(qmc):
+    from oracle import analysis as A
+    rng = np.random.default_rng(5)
+    x = np.cumsum(rng.normal(size=3000)) * 0.01 + rng.normal(size=3000)
+    assert abs(qmc.qmc_tau_int(x) - A.tau_int(x)) < 1e-9
