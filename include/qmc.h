@@ -137,6 +137,11 @@ int qmc_measure(qmc_ctx *ctx, double *host_out);
 int qmc_get_series(qmc_ctx *ctx, int count, double *host_out);
 int qmc_series_length(const qmc_ctx *ctx);
 
+/* Enqueue, without synchronising, the copy of the newest observable record
+ * of every chain to host_out[n_chains * QMC_NOBS] (pinned host memory for an
+ * asynchronous copy); the data are valid after the next qmc_sync. */
+int qmc_copy_latest_async(qmc_ctx *ctx, double *host_out);
+
 /* Copy chain `chain`'s equal-time Green's function to host_buf as the full
  * 4 N_orb x 4 N_orb matrix G_s (x) I_spin in the order (spin, valley,
  * orbital), row-major, interleaved complex: len >= 2 * (4 N_orb)^2 doubles. */
@@ -161,6 +166,17 @@ int qmc_get_eps(qmc_ctx *ctx, double *host_out);
 /* Integrated autocorrelation time of x[0..n) with Sokal's automatic window
  * (c = 5): tau = 1/2 + sum_{t<=W} rho(t), smallest W >= c tau.  Host only. */
 double qmc_tau_int(const double *x, int n);
+
+/* Number of CUDA kernels this library has launched since it was loaded (all
+ * contexts; a host-side count of kernel launches, no synchronisation). */
+long long qmc_launch_count(void);
+
+/* Event timing of every batched complex GEMM launch.  enable = 1 starts
+ * recording (a pair of CUDA events around each launch on its stream);
+ * enable = 0 stops, synchronises the device and returns the summed device
+ * time in *total_ms, the number of launches and their algorithmic flops
+ * (8 M N K per complex product) -- the inputs of the GEMM roofline. */
+int qmc_profile_gemm(int enable, double *total_ms, long long *launches, double *flops);
 
 const char *qmc_strerror(int code);
 const char *qmc_last_error(const qmc_ctx *ctx);

@@ -4,7 +4,9 @@ The compute path is libqmc.so (hand-written CUDA for sm_103a behind a C ABI,
 include/qmc.h); ``qmc`` is its ctypes binding.
 """
 from .qmc import (QMC_NOBS, QMC_NTRACE, QMC_SPHERE, QMC_TORUS, OBS_NAMES, Chain, QMCError,
-                  lib, qmc_default_opts, qmc_tau_int)
+                  lib, qmc_default_opts, qmc_launch_count, qmc_profile_gemm,
+                  qmc_tau_int)
 
 __all__ = ["Chain", "QMCError", "QMC_TORUS", "QMC_SPHERE", "QMC_NOBS", "QMC_NTRACE",
-           "OBS_NAMES", "lib", "qmc_default_opts", "qmc_tau_int"]
+           "OBS_NAMES", "lib", "qmc_default_opts", "qmc_tau_int", "qmc_launch_count",
+           "qmc_profile_gemm"]

@@ -26,6 +26,8 @@
         }                                                                          \
     } while (0)
 
+long long g_qmc_launches = 0;
+
 struct qmc_ctx {
     int geom = 0, nphi = 0, n = 0, N = 0, nq = 0, nf = 0, L = 0, nb = 0;
     long long NN = 0, n2 = 0;
@@ -269,7 +271,7 @@ static int update_slice(qmc_ctx *ctx, int t)
     const long long L = ctx->L;
     const double *phi_s = ctx->phi + (long long)s0 * nf;
     const long long phi_cs = L * nf;
-    cd *Bs = ctx->B + (long long)s0 * NN, *Bis = ctx->Binv + (long long)s0 * NN;
+    cd *Bis = ctx->Binv + (long long)s0 * NN;
     // forward gradient at the current fields
     factors_from_eig(ctx, ctx->eigU + (long long)s0 * 4 * n2, L * 4 * n2,
                      ctx->eigW + (long long)s0 * 4 * n, L * 4 * n, ctx->V, ctx->T, ctx->lam,
@@ -779,12 +781,22 @@ int qmc_sync(qmc_ctx *ctx)
 int qmc_measure(qmc_ctx *ctx, double *host_out)
 {
     if (!ctx || !host_out) return QMC_ERR_ARG;
-    double *tmp = ctx->series;  // measure into a scratch record, then copy
-    (void)tmp;
     measure_into(ctx, ctx->gradp, QMC_NOBS);  // gradp has >= nb * QMC_NOBS doubles
     CK(cudaMemcpyAsync(host_out, ctx->gradp, sizeof(double) * ctx->nb * QMC_NOBS,
                        cudaMemcpyDeviceToHost, ctx->st));
     return qmc_sync(ctx);
+}
+
+int qmc_copy_latest_async(qmc_ctx *ctx, double *host_out)
+{
+    if (!ctx || !host_out || ctx->series_n < 1) return QMC_ERR_ARG;
+    const int cap = ctx->o.series_capacity;
+    long long idx = (ctx->series_n - 1) % cap;
+    for (int c = 0; c < ctx->nb; ++c)
+        CK(cudaMemcpyAsync(host_out + (size_t)c * QMC_NOBS,
+                           ctx->series + ((long long)c * cap + idx) * QMC_NOBS,
+                           sizeof(double) * QMC_NOBS, cudaMemcpyDeviceToHost, ctx->st));
+    return QMC_OK;
 }
 
 int qmc_series_length(const qmc_ctx *ctx)
@@ -918,5 +930,17 @@ const char *qmc_strerror(int code)
 }
 
 const char *qmc_last_error(const qmc_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+long long qmc_launch_count(void) { return g_qmc_launches; }
+
+int qmc_profile_gemm(int enable, double *total_ms, long long *launches, double *flops)
+{
+    if (enable) {
+        gemm_prof_start();
+    } else {
+        gemm_prof_stop(total_ms, launches, flops);
+    }
+    return QMC_OK;
+}
 
 }  // extern "C"

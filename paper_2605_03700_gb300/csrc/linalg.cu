@@ -4,6 +4,8 @@
 // column pivoting (UDV).  All matrices are row-major interleaved complex.
 #include "linalg.cuh"
 
+#include <vector>
+
 // ------------------------------------------------------------------ GEMM --
 // C[b] = alpha * op(A[b]) * diag(d[b]) * op(B[b]) + beta * C[b] (+ I)
 // op: 0 = none, 1 = transpose, 2 = conjugate transpose.  16 x 16 output tile
@@ -57,10 +59,63 @@ __global__ void __launch_bounds__(256) k_zgemm(GemmP p)
     }
 }
 
+// optional event timing of every GEMM launch (roofline of the GEMM class)
+struct GemmProf {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;
+    size_t used = 0;
+    double flops = 0.0;
+    long long launches = 0;
+};
+static GemmProf g_gprof;
+
+void gemm_prof_start()
+{
+    g_gprof.on = true;
+    g_gprof.used = 0;
+    g_gprof.flops = 0.0;
+    g_gprof.launches = 0;
+}
+
+void gemm_prof_stop(double *ms, long long *launches, double *flops)
+{
+    g_gprof.on = false;
+    cudaDeviceSynchronize();
+    double tot = 0.0;
+    for (size_t i = 0; i + 1 < g_gprof.used; i += 2) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, g_gprof.ev[i], g_gprof.ev[i + 1]);
+        tot += t;
+    }
+    if (ms) *ms = tot;
+    if (launches) *launches = g_gprof.launches;
+    if (flops) *flops = g_gprof.flops;
+    g_gprof.used = 0;
+}
+
+static cudaEvent_t gprof_event()
+{
+    if (g_gprof.used == g_gprof.ev.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        g_gprof.ev.push_back(e);
+    }
+    return g_gprof.ev[g_gprof.used++];
+}
+
 void zgemm(cudaStream_t st, const GemmP &p, int batch)
 {
     dim3 grid(cdiv_up(p.N, GT), cdiv_up(p.M, GT), batch);
-    k_zgemm<<<grid, dim3(GT, GT), 0, st>>>(p);
+    if (g_gprof.on) {
+        cudaEventRecord(gprof_event(), st);
+        k_zgemm<<<grid, dim3(GT, GT), 0, st>>>(p);
+        cudaEventRecord(gprof_event(), st);
+        g_gprof.flops += 8.0 * p.M * (double)p.N * p.K * batch;
+        g_gprof.launches++;
+    } else {
+        k_zgemm<<<grid, dim3(GT, GT), 0, st>>>(p);
+    }
+    QMC_COUNT(1);
 }
 
 // -------------------------------------------------------- Jacobi eigh ----
@@ -209,6 +264,7 @@ int eigh_batched(cudaStream_t st, int n, const cd *H, long long sH, cd *U, long 
         attr = true;
     }
     k_eigh<<<batch, 256, smem, st>>>(n, H, sH, U, sU, w, sw);
+    QMC_COUNT(1);
     return 0;
 }
 
@@ -221,8 +277,6 @@ __global__ void __launch_bounds__(256) k_lu(int n, cd *A, long long sA, int *piv
 {
     extern __shared__ cd sm_l[];
     cd *M = sm_l;
-    __shared__ double bv[32];
-    __shared__ int bi[32];
     __shared__ int s_p;
     const int b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
     cd *Ab = A + (long long)b * sA;
@@ -296,6 +350,7 @@ int lu_batched(cudaStream_t st, int n, cd *A, long long sA, int *piv, long long 
         attr = true;
     }
     k_lu<<<batch, 256, smem, st>>>(n, A, sA, piv, spiv, logdet);
+    QMC_COUNT(1);
     return 0;
 }
 
@@ -371,6 +426,7 @@ int rdiv_batched(cudaStream_t st, int n, const cd *G, long long sG, const cd *LU
     }
     dim3 grid(cdiv_up(n, RD_ROWS), batch);
     k_rdiv<<<grid, RD_ROWS * 32, smem, st>>>(n, G, sG, LU, sLU, piv, spiv, X, sX);
+    QMC_COUNT(1);
     return 0;
 }
 
@@ -502,5 +558,6 @@ int qrp_batched(cudaStream_t st, int n, const cd *X, long long sX, cd *Q, long l
         attr = true;
     }
     k_qrp<<<batch, 256, smem, st>>>(n, X, sX, Q, sQ, D, sD, V, sV);
+    QMC_COUNT(1);
     return 0;
 }

@@ -22,6 +22,8 @@ struct GemmP {
 };
 
 void zgemm(cudaStream_t st, const GemmP &p, int batch);
+void gemm_prof_start();
+void gemm_prof_stop(double *ms, long long *launches, double *flops);
 int eigh_batched(cudaStream_t st, int n, const cd *H, long long sH, cd *U, long long sU, double *w,
                  long long sw, int batch);
 int lu_batched(cudaStream_t st, int n, cd *A, long long sA, int *piv, long long spiv, cd *logdet,

@@ -544,11 +544,13 @@ void launch_ff_torus(cudaStream_t s, int n, int nq, const int *qxy, cd *val, int
 {
     k_ff_torus<<<cdiv_up(nq * n, 256), 256, 0, s>>>(n, nq, qxy, val, col);
     k_trF<<<cdiv_up(nq, 128), 128, 0, s>>>(n, nq, val, col, trF);
+    QMC_COUNT(2);
 }
 void launch_init_phi(cudaStream_t s, int nb, int L, int nf, const uint32_t *keys, double *phi)
 {
     long long tot = (long long)nb * L * nf;
     k_init_phi<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(nb, L, nf, keys, phi);
+    QMC_COUNT(1);
 }
 void launch_assemble(cudaStream_t s, int nb, int n, int nq, const double *phi, long long phi_cs,
                      const int *fkind, const int *frA, const int *frB, const int *aptr,
@@ -556,6 +558,7 @@ void launch_assemble(cudaStream_t s, int nb, int n, int nq, const double *phi, l
 {
     k_assemble<<<dim3(cdiv_up(n * n, 128), 4, nb), 128, 0, s>>>(nb, n, nq, phi, phi_cs, fkind, frA,
                                                                 frB, aptr, aq, val, F);
+    QMC_COUNT(1);
 }
 void launch_build_V(cudaStream_t s, int nb, int n, const cd *U, long long U_cs, cd *V)
 {
@@ -566,11 +569,13 @@ void launch_lambda(cudaStream_t s, int nb, int n, const double *w, long long w_c
                    const cd *alpha, cd *lam, cd *Dg, cd *Dgi)
 {
     k_lambda<<<dim3(cdiv_up(2 * n, 128), 7, nb), 128, 0, s>>>(nb, n, w, w_cs, alpha, lam, Dg, Dgi);
+    QMC_COUNT(1);
 }
 void launch_accum(cudaStream_t s, int nb, int N, int j, int first, const cd *alpha,
                   const cd *lam, const cd *Ah, cd *Cacc)
 {
     k_accum<<<dim3(cdiv_up(N * N, 256), nb), 256, 0, s>>>(nb, N, j, first, alpha, lam, Ah, Cacc);
+    QMC_COUNT(1);
 }
 void launch_trace_grad(cudaStream_t s, int nb, int n, int nq, const cd *At, const cd *val,
                        const int *col, const cd *trF, const cd *alpha, cd *t, const int *fq,
@@ -580,6 +585,7 @@ void launch_trace_grad(cudaStream_t s, int nb, int n, int nq, const cd *At, cons
     k_trace_t<<<dim3(cdiv_up(nq, 64), 4, nb), 64, 0, s>>>(nb, n, nq, At, val, col, trF, alpha, t);
     k_grad<<<dim3(cdiv_up(4 * nq, 128), nb), 128, 0, s>>>(nb, nq, fq, fk, partner, phi, phi_cs, t,
                                                            grad);
+    QMC_COUNT(2);
 }
 void launch_propose(cudaStream_t s, int nb, int nf, const double *phi, long long phi_cs,
                     const double *grad, const double *eps, const uint32_t *keys, uint32_t slice,
@@ -587,6 +593,7 @@ void launch_propose(cudaStream_t s, int nb, int nf, const double *phi, long long
 {
     k_propose<<<dim3(cdiv_up(nf, 128), nb), 128, 0, s>>>(nb, nf, phi, phi_cs, grad, eps, keys, slice,
                                                           sweep, phip);
+    QMC_COUNT(1);
 }
 void launch_axpyI(cudaStream_t s, int nb, int N, const cd *X, long long sX, cd a, cd b, cd *Y,
                   long long sY)
@@ -596,40 +603,48 @@ void launch_axpyI(cudaStream_t s, int nb, int N, const cd *X, long long sX, cd a
 void launch_accept(cudaStream_t s, int nb, const AcceptP &p)
 {
     k_accept<<<nb, 256, 0, s>>>(p);
+    QMC_COUNT(1);
 }
 void launch_commit(cudaStream_t s, int nb, const CommitP &p)
 {
     long long mx = (long long)p.N * p.N;
     if (p.nf > mx) mx = p.nf;
     k_commit<<<dim3((unsigned)((mx + 255) / 256), nb), 256, 0, s>>>(p);
+    QMC_COUNT(1);
 }
 void launch_scale_cols(cudaStream_t s, int nb, int N, const cd *X, long long sX, const double *d,
                        long long sd, cd *Y, long long sY)
 {
     k_scale_cols<<<dim3(cdiv_up(N * N, 256), nb), 256, 0, s>>>(nb, N, X, sX, d, sd, Y, sY);
+    QMC_COUNT(1);
 }
 void launch_stab_mix(cudaStream_t s, int nb, int N, const cd *T1, const cd *T2, const double *DR,
                      long long sDR, const double *DL, long long sDL, cd *X)
 {
     k_stab_mix<<<dim3(cdiv_up(N * N, 256), nb), 256, 0, s>>>(nb, N, T1, T2, DR, sDR, DL, sDL, X);
+    QMC_COUNT(1);
 }
 void launch_inv_big(cudaStream_t s, int nb, int N, const double *D, long long sD, cd *out)
 {
     k_inv_big<<<dim3(cdiv_up(N, 128), nb), 128, 0, s>>>(nb, N, D, sD, out);
+    QMC_COUNT(1);
 }
 void launch_stab_err(cudaStream_t s, int nb, int N, cd *G, const cd *Gs, double *st, int *errf,
                      double tol)
 {
     k_stab_err<<<nb, 256, 0, s>>>(N, G, Gs, st, errf, tol);
+    QMC_COUNT(1);
 }
 void launch_measure(cudaStream_t s, int nb, int n, int nq, const cd *G, const cd *val,
                     const int *col, const int *partner, cd *ax, const MeasP &p)
 {
     k_meas_ax<<<dim3(nq, 4, nb), 256, 0, s>>>(n, nq, G, val, col, partner, ax);
     k_meas_final<<<nb, 256, 0, s>>>(p);
+    QMC_COUNT(2);
 }
 void launch_end_sweep(cudaStream_t s, int nb, int L, int adapt, double r0, double deps,
                       double *eps, double *eps_used, double *st)
 {
     k_end_sweep<<<cdiv_up(nb, 64), 64, 0, s>>>(nb, L, adapt, r0, deps, eps, eps_used, st);
+    QMC_COUNT(1);
 }

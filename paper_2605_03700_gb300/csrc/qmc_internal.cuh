@@ -97,6 +97,10 @@ __device__ __forceinline__ double rng_normal(uint32_t f, uint32_t slice, uint32_
 }
 
 // ------------------------------------------------------- small utilities --
+// number of kernels this library has launched (all contexts, host-side count)
+extern long long g_qmc_launches;
+#define QMC_COUNT(k) (g_qmc_launches += (k))
+
 #define QMC_DEVFN __device__ __forceinline__
 
 static inline int cdiv_up(int a, int b) { return (a + b - 1) / b; }

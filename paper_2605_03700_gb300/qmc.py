@@ -82,6 +82,10 @@ def lib():
         L.qmc_strerror.argtypes = [C.c_int]
         L.qmc_last_error.restype = C.c_char_p
         L.qmc_last_error.argtypes = [vp]
+        L.qmc_copy_latest_async.argtypes = [vp, dp]
+        L.qmc_launch_count.restype = C.c_longlong
+        L.qmc_launch_count.argtypes = []
+        L.qmc_profile_gemm.argtypes = [C.c_int, dp, C.POINTER(C.c_longlong), dp]
         _lib = L
     return _lib
 
@@ -102,6 +106,18 @@ def qmc_default_opts() -> qmc_opts:
     o = qmc_opts()
     _check(lib().qmc_default_opts(C.byref(o)))
     return o
+
+
+def qmc_launch_count() -> int:
+    return int(lib().qmc_launch_count())
+
+
+def qmc_profile_gemm(enable: bool):
+    """Start (True) or stop (False) GEMM event timing; stop returns
+    (total_ms, launches, flops)."""
+    ms, n, fl = C.c_double(), C.c_longlong(), C.c_double()
+    _check(lib().qmc_profile_gemm(1 if enable else 0, C.byref(ms), C.byref(n), C.byref(fl)))
+    return None if enable else (ms.value, n.value, fl.value)
 
 
 def qmc_tau_int(x) -> float:
@@ -182,6 +198,12 @@ class Chain:
         out = np.zeros((self.n_chains, count, QMC_NOBS))
         _check(lib().qmc_get_series(self.h, count, _dp(out)), self.h)
         return out
+
+    def copy_latest_async(self, host_ptr):
+        """Enqueue the D2H copy of the newest records into host memory at
+        host_ptr (an int address of n_chains * QMC_NOBS doubles, pinned)."""
+        _check(lib().qmc_copy_latest_async(self.h, C.cast(C.c_void_p(host_ptr),
+                                                           C.POINTER(C.c_double))), self.h)
 
     def green(self, chain=0, block=True):
         if block:
