@@ -54,8 +54,9 @@ L_SAMPLE = 10
 
 def workload_config(extra=None):
     cfg = {
-        "workload": "CF-DQMC sweep, torus N_phi=36 (N=72, N_q=333), beta=36, dtau=0.1 (L=360), "
-                    "8 chains u=linspace(0.5,2,8) seeds 0-7 (+8*rank), n_stab=10, FP64",
+        "workload": f"CF-DQMC sweep, torus N_phi=36 (N=72, N_q=333), beta={BETA:g}, dtau=0.1 "
+                    f"(L={int(round(BETA / DTAU))}), 8 chains u=linspace(0.5,2,8) seeds 0-7 "
+                    "(+8*rank), n_stab=10, FP64",
         "n_chains_per_gpu": NCH,
         "L": int(round(BETA / DTAU)),
         "l2": "inputs larger than L2: 8 chains x 360 slices x (B, B^-1) = 478 MB resident",
@@ -303,7 +304,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--beta", type=float, default=BETA,
+                    help="override beta (shorter imaginary-time axis, same kernels and matrix "
+                         "sizes; used for profiler launch lists)")
     args = ap.parse_args()
+    globals()["BETA"] = args.beta
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -167,6 +167,23 @@ int qmc_get_eps(qmc_ctx *ctx, double *host_out);
  * (c = 5): tau = 1/2 + sum_{t<=W} rho(t), smallest W >= c tau.  Host only. */
 double qmc_tau_int(const double *x, int n);
 
+/* The determinant ratio and Green's-function update of one MALA proposal
+ * (Methods, MH criterion of the "Langevin-based global update scheme"; the
+ * ratio det(1 + B'(b,0))/det(1 + B(b,0)) = det M with
+ * M = 1 + (Delta - 1)(1 - G), Delta = B'_tau B_tau^-1, and the new
+ * G' = G M^-1 of Eq. green_function), for `batch` independent matrices.
+ *   N       matrix size (single-particle states of one spin block), 1..116
+ *   G       device, batch x N x N, row-major interleaved complex (2 doubles)
+ *   Delta   device, same layout
+ *   Gp      device output, same layout (must not alias G or Delta)
+ *   logdet  device output, batch complex values log det M (2 doubles each;
+ *           imaginary part modulo 2 pi)
+ *   stream  cudaStream_t or NULL
+ * Scratch (3 batch N^2 complex + batch N ints) is allocated with cudaMalloc
+ * and freed before returning; the call synchronises `stream`. */
+int qmc_ratio_update(int N, int batch, const double *G, const double *Delta, double *Gp,
+                     double *logdet, void *stream);
+
 /* Number of CUDA kernels this library has launched since it was loaded (all
  * contexts; a host-side count of kernel launches, no synchronisation). */
 long long qmc_launch_count(void);

@@ -431,6 +431,20 @@ static int one_sweep(qmc_ctx *ctx)
     return 0;
 }
 
+// M = 1 + (Delta - 1)(1 - G), log det M, G' = G M^-1 for `batch` matrices,
+// with caller-provided device scratch X1, X2, M (batch N x N) and piv (batch N)
+static int ratio_update_core(cudaStream_t s, int N, int batch, const cd *G, const cd *Dl, cd *Gp,
+                             cd *logdet, cd *X1, cd *X2, cd *M, int *piv)
+{
+    const long long NN = (long long)N * N;
+    launch_axpyI(s, batch, N, Dl, NN, ONE, MONE, X1, NN);
+    launch_axpyI(s, batch, N, G, NN, MONE, ONE, X2, NN);
+    zgemm_sq(s, N, batch, X1, NN, 0, X2, NN, 0, M, NN, nullptr, 0, ONE, ZERO, 1);
+    if (lu_batched(s, N, M, NN, piv, N, logdet, batch)) return QMC_ERR_ARG;
+    if (rdiv_batched(s, N, G, NN, M, NN, piv, N, Gp, NN, batch)) return QMC_ERR_ARG;
+    return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
 // ------------------------------------------------------------- create -----
 static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy)
 {
@@ -932,6 +946,32 @@ const char *qmc_strerror(int code)
 const char *qmc_last_error(const qmc_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
 
 long long qmc_launch_count(void) { return g_qmc_launches; }
+
+int qmc_ratio_update(int N, int batch, const double *G, const double *Delta, double *Gp,
+                     double *logdet, void *stream)
+{
+    if (N < 1 || N > 116 || batch < 1 || !G || !Delta || !Gp || !logdet) return QMC_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t NN = (size_t)N * N;
+    cd *X1 = nullptr, *X2 = nullptr, *M = nullptr;
+    int *piv = nullptr;
+    int code = QMC_OK;
+    if (cudaMalloc(&X1, sizeof(cd) * NN * batch) != cudaSuccess ||
+        cudaMalloc(&X2, sizeof(cd) * NN * batch) != cudaSuccess ||
+        cudaMalloc(&M, sizeof(cd) * NN * batch) != cudaSuccess ||
+        cudaMalloc(&piv, sizeof(int) * N * batch) != cudaSuccess) {
+        code = QMC_ERR_OOM;
+    } else {
+        code = ratio_update_core(s, N, batch, (const cd *)G, (const cd *)Delta, (cd *)Gp,
+                                 (cd *)logdet, X1, X2, M, piv);
+        if (cudaStreamSynchronize(s) != cudaSuccess) code = QMC_ERR_CUDA;
+    }
+    cudaFree(X1);
+    cudaFree(X2);
+    cudaFree(M);
+    cudaFree(piv);
+    return code;
+}
 
 int qmc_profile_gemm(int enable, double *total_ms, long long *launches, double *flops)
 {

@@ -83,6 +83,7 @@ def lib():
         L.qmc_last_error.restype = C.c_char_p
         L.qmc_last_error.argtypes = [vp]
         L.qmc_copy_latest_async.argtypes = [vp, dp]
+        L.qmc_ratio_update.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp, vp]
         L.qmc_launch_count.restype = C.c_longlong
         L.qmc_launch_count.argtypes = []
         L.qmc_profile_gemm.argtypes = [C.c_int, dp, C.POINTER(C.c_longlong), dp]
@@ -118,6 +119,12 @@ def qmc_profile_gemm(enable: bool):
     ms, n, fl = C.c_double(), C.c_longlong(), C.c_double()
     _check(lib().qmc_profile_gemm(1 if enable else 0, C.byref(ms), C.byref(n), C.byref(fl)))
     return None if enable else (ms.value, n.value, fl.value)
+
+
+def qmc_ratio_update(N, batch, G_ptr, Delta_ptr, Gp_ptr, logdet_ptr, stream=0):
+    """Device pointers (ints) of complex128 buffers; see include/qmc.h."""
+    _check(lib().qmc_ratio_update(N, batch, C.c_void_p(G_ptr), C.c_void_p(Delta_ptr),
+                                  C.c_void_p(Gp_ptr), C.c_void_p(logdet_ptr), C.c_void_p(stream)))
 
 
 def qmc_tau_int(x) -> float:

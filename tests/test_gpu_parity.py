@@ -146,3 +146,37 @@ def test_tau_int_matches_oracle_estimator(qmc):
     rng = np.random.default_rng(5)
     x = np.cumsum(rng.normal(size=3000)) * 0.01 + rng.normal(size=3000)
     assert abs(qmc.qmc_tau_int(x) - A.tau_int(x)) < 1e-9
+
+
+def test_ratio_update_entry_point_matches_oracle(qmc):
+    """qmc_ratio_update (det M and G M^-1 for a batch) against the oracle's
+    brute-force-G ratio of a random proposal on three slices."""
+    import torch
+    ch = O.Chain(M.TORUS, 5, 1.0, 0.1, 2.0, 0.2, seed=4)
+    rng = np.random.default_rng(8)
+    Gs, Ds, refs = [], [], []
+    for t in (2, 5, 9):
+        G = ch.green_bruteforce(t)
+        B, Bi = ch.B(t)
+        E, tw = ch.factors(t)
+        p0 = ch.phi()[t - 1].copy()
+        p1 = p0 + 0.3 * rng.normal(size=p0.shape)
+        logR, Gp = ch.ratio_at(t, p1)
+        ch.set_slice_phi(t, p1)
+        Bp, _ = ch.B(t)
+        _, twp = ch.factors(t)
+        ch.set_slice_phi(t, p0)
+        Gs.append(G)
+        Ds.append(Bp @ Bi)
+        refs.append((logR + 0.5 * (twp - tw), Gp))
+    N = Gs[0].shape[0]
+    Gd = torch.tensor(np.array(Gs), dtype=torch.complex128, device="cuda")
+    Dd = torch.tensor(np.array(Ds), dtype=torch.complex128, device="cuda")
+    Gp = torch.empty_like(Gd)
+    ld = torch.empty(3, dtype=torch.complex128, device="cuda")
+    qmc.qmc_ratio_update(N, 3, Gd.data_ptr(), Dd.data_ptr(), Gp.data_ptr(), ld.data_ptr())
+    Gp, ld = Gp.cpu().numpy(), ld.cpu().numpy()
+    for b, (lr, gref) in enumerate(refs):
+        assert abs(ld[b].real - lr.real) < TOL_LOGR
+        assert abs(np.exp(1j * ld[b].imag) - np.exp(1j * lr.imag)) < 1e-9
+        assert _rel(Gp[b], gref) < TOL_G
