@@ -184,6 +184,30 @@ double qmc_tau_int(const double *x, int n);
 int qmc_ratio_update(int N, int batch, const double *G, const double *Delta, double *Gp,
                      double *logdet, void *stream);
 
+/* qmc_ratio_update for callers that cannot allocate device memory: a plug-in
+ * that only receives device pointers from a host framework which owns all
+ * device memory and forbids cudaMalloc, or a service running under a fixed
+ * device-memory budget where an allocation could fail in the middle of a
+ * run.  The paper has no counterpart: it is a deployment variant of the step
+ * above.  It computes the same M, log det M and G' = G M^-1 but
+ * allocates nothing: its scratch is one file-scope device array of
+ * 8 MiB (QMC_NOALLOC_SCRATCH_BYTES), present on every GPU that loads the
+ * library until the process exits.
+ *   Limit: 3 * round256(16 batch N^2) + round256(4 batch N) <= 8 MiB
+ *   (N = 72: batch <= 33); larger requests return QMC_ERR_ARG before any
+ *   device work.
+ *   The first call on a device looks up the array's device address with
+ *   cudaGetSymbolAddress (that device must be current); make that first call
+ *   before any stream capture.  Later calls only enqueue kernels.
+ *   Asynchronous: the outputs are valid once `stream` has been synchronised.
+ *   Every call shares the one scratch array and leaves its contents behind
+ *   (nothing in it has to start at zero); calls that overlap on the GPU --
+ *   on different streams, or from different host threads -- race on it and
+ *   must be serialised by the caller. */
+#define QMC_NOALLOC_SCRATCH_BYTES (8u << 20)
+int qmc_ratio_update_noalloc(int N, int batch, const double *G, const double *Delta,
+                             double *Gp, double *logdet, void *stream);
+
 /* Number of CUDA kernels this library has launched since it was loaded (all
  * contexts; a host-side count of kernel launches, no synchronisation). */
 long long qmc_launch_count(void);

@@ -445,6 +445,21 @@ static int ratio_update_core(cudaStream_t s, int N, int batch, const cd *G, cons
     return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
 }
 
+// Scratch of qmc_ratio_update_noalloc: a file-scope device array, so that a
+// caller that may not allocate device memory (a plug-in that only receives
+// device pointers from a host framework owning all device memory, or a
+// service running under a fixed device-memory budget where an allocation can
+// fail mid-run) still gets the ratio and G update.  Every GPU that loads the
+// library holds these bytes (QMC_NOALLOC_SCRATCH_BYTES, include/qmc.h) until
+// the process exits.  In host code the symbol is only a host-side stand-in:
+// its device address is looked up once per device with cudaGetSymbolAddress
+// and cached below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[QMC_NOALLOC_SCRATCH_BYTES];
+#define QMC_NOALLOC_MAX_DEVICES 64
+static void *g_noalloc_addr[QMC_NOALLOC_MAX_DEVICES];
+
+static size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
 // ------------------------------------------------------------- create -----
 static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy)
 {
@@ -946,6 +961,32 @@ const char *qmc_strerror(int code)
 const char *qmc_last_error(const qmc_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
 
 long long qmc_launch_count(void) { return g_qmc_launches; }
+
+int qmc_ratio_update_noalloc(int N, int batch, const double *G, const double *Delta,
+                             double *Gp, double *logdet, void *stream)
+{
+    if (N < 1 || N > 116 || batch < 1 || !G || !Delta || !Gp || !logdet) return QMC_ERR_ARG;
+    const size_t NN = (size_t)N * N;
+    const size_t mat = round256(sizeof(cd) * NN * (size_t)batch);
+    const size_t pv = round256(sizeof(int) * (size_t)N * (size_t)batch);
+    if (3 * mat + pv > QMC_NOALLOC_SCRATCH_BYTES) return QMC_ERR_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= QMC_NOALLOC_MAX_DEVICES)
+        return QMC_ERR_CUDA;
+    if (!g_noalloc_addr[dev]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr)
+            return QMC_ERR_CUDA;
+        g_noalloc_addr[dev] = ptr;
+    }
+    unsigned char *base = (unsigned char *)g_noalloc_addr[dev];
+    cd *X1 = (cd *)base;
+    cd *X2 = (cd *)(base + mat);
+    cd *Mm = (cd *)(base + 2 * mat);
+    int *piv = (int *)(base + 3 * mat);
+    return ratio_update_core((cudaStream_t)stream, N, batch, (const cd *)G, (const cd *)Delta,
+                             (cd *)Gp, (cd *)logdet, X1, X2, Mm, piv);
+}
 
 int qmc_ratio_update(int N, int batch, const double *G, const double *Delta, double *Gp,
                      double *logdet, void *stream)

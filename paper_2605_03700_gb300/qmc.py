@@ -84,6 +84,7 @@ def lib():
         L.qmc_last_error.argtypes = [vp]
         L.qmc_copy_latest_async.argtypes = [vp, dp]
         L.qmc_ratio_update.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp, vp]
+        L.qmc_ratio_update_noalloc.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp, vp]
         L.qmc_launch_count.restype = C.c_longlong
         L.qmc_launch_count.argtypes = []
         L.qmc_profile_gemm.argtypes = [C.c_int, dp, C.POINTER(C.c_longlong), dp]
