@@ -38,7 +38,7 @@ if ROOT not in sys.path:
 
 NPHI, BETA, DTAU, NCH, NSTAB = 36, 36.0, 0.1, 8, 10
 COUPLINGS = np.linspace(0.5, 2.0, NCH)
-EPS0 = 0.3
+EPS0 = 0.45
 METRIC = "effective samples/s (autocorr-corrected) at N_phi=36 torus vs plain FP64 sweep"
 UNIT = "effective samples/s"
 # FP64 pipe peak of a GB300: 1.25 TFLOP/s nominal = 152 SMs x 2 DFMA/clk x
@@ -56,7 +56,7 @@ def workload_config(extra=None):
     cfg = {
         "workload": f"CF-DQMC sweep, torus N_phi=36 (N=72, N_q=333), beta={BETA:g}, dtau=0.1 "
                     f"(L={int(round(BETA / DTAU))}), 8 chains u=linspace(0.5,2,8) seeds 0-7 "
-                    "(+8*rank), n_stab=10, FP64",
+                    "(+8*rank), n_stab=10",
         "n_chains_per_gpu": NCH,
         "L": int(round(BETA / DTAU)),
         "l2": "inputs larger than L2: 8 chains x 360 slices x (B, B^-1) = 478 MB resident",
@@ -213,7 +213,8 @@ def run_ours(args):
     wall0 = time.perf_counter()
     seeds = np.arange(NCH) + NCH * rank
     ch = P.Chain(P.QMC_TORUS, NPHI, BETA, DTAU, 0.0, 0.0, 0, n_chains=NCH, couplings=COUPLINGS,
-                 seeds=seeds, n_stab=NSTAB, eps0=EPS0, series_capacity=4096)
+                 seeds=seeds, n_stab=NSTAB, eps0=EPS0, series_capacity=4096,
+                 precision=args.precision)
     ch.set_stream(stream.cuda_stream)
     pinned = torch.empty((args.steps, NCH, P.QMC_NOBS), dtype=torch.float64, pin_memory=True)
     ch.sweep(args.warmup)
@@ -268,9 +269,10 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f32+f64",
         "data": "synthetic (fields drawn from the chains' own Philox streams)",
         "config": workload_config({"parallelism": f"replicas x{world}",
+                                   "precision": ["fp64", "mixed fp32/fp64"][args.precision],
                                    "tau_int": [round(t, 3) for t in taus],
                                    "tau_series_len": int(series.shape[1]),
                                    "sweeps_per_s_per_gpu": NCH * args.steps / t_s / world}),
@@ -304,6 +306,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", type=int, default=1, choices=[0, 1],
+                    help="0: FP64 everywhere; 1: mixed (FP32 eigensolver + FP64 polish, FP32 "
+                         "gradient transforms and wraps, FP64 propagators, ratios, updates)")
     ap.add_argument("--beta", type=float, default=BETA,
                     help="override beta (shorter imaginary-time axis, same kernels and matrix "
                          "sizes; used for profiler launch lists)")

@@ -70,7 +70,13 @@ enum {
 
 typedef struct {
     int n_stab;            /* slices between restabilisations (default 10) */
-    int precision;         /* 0 = FP64 everywhere (default) */
+    int precision;         /* 0 = FP64 everywhere (default); 1 = mixed: the channel
+                              eigensolver's bulk Jacobi sweeps in FP32 followed by an
+                              FP64 polish (Newton-Schulz orthonormalisation, one or two
+                              FP64 Jacobi sweeps), and the gradient transforms of the
+                              Langevin drift in FP32; propagators, wraps, M, LU and
+                              log det, G M^-1, MH test, restabilisation and
+                              measurements in FP64 */
     double eps0;           /* initial Langevin step (default 0.5) */
     double deps;           /* step adaptation rate Delta eps (default 0.1) */
     double r0;             /* target acceptance (default 0.574) */
@@ -156,6 +162,13 @@ int qmc_get_fields(qmc_ctx *ctx, int chain, double *host_buf, size_t len);
 /* Per-update trace (opts.trace_capacity > 0): host_buf[count][QMC_NTRACE],
  * returns the number of records in *count. */
 int qmc_get_trace(qmc_ctx *ctx, int chain, double *host_buf, size_t len, long *count);
+
+/* Slice propagator B_tau and its inverse (Methods, Eq.
+ * trotter_decomposition) of chain `chain`, slice 1..L, as 2 N_orb x 2 N_orb
+ * row-major interleaved complex (FP64 in both precision modes);
+ * either pointer may be NULL; len >= 2 (2 N_orb)^2 doubles each. */
+int qmc_get_propagator(qmc_ctx *ctx, int chain, int slice, double *host_B, double *host_Binv,
+                       size_t len);
 
 /* Sizes of the context. */
 int qmc_sizes(const qmc_ctx *ctx, int *n_orb, int *n_q, int *L, int *n_chains);

@@ -6,6 +6,15 @@
 // step, one slice at a time, with batched kernels (grid z or y = chain).
 // Control never returns to the host inside a sweep: accept decisions are
 // device flags consumed by the commit kernel.
+//
+// Precision: everything that enters the Metropolis-Hastings ratio -- the
+// channel eigenpairs, propagators, wraps, M, its LU and log det, G' = G M^-1,
+// the UDV restabilisation -- is FP64-accurate in both modes, as are the
+// fields and the measurements.  In the mixed mode (precision 1) the channel
+// eigensolver does its bulk Jacobi sweeps in FP32 and only a short FP64
+// polish, and the gradient transforms that build the Langevin drift run in
+// FP32: the drift only has to be one deterministic function of the state for
+// MALA to stay exact.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -32,6 +41,8 @@ struct qmc_ctx {
     int geom = 0, nphi = 0, n = 0, N = 0, nq = 0, nf = 0, L = 0, nb = 0;
     long long NN = 0, n2 = 0;
     double beta = 0, dtau = 0;
+    int gp = TY_C64;   // compute type of the gradient transforms, wraps, M and G M^-1
+    size_t gsz = 16;   // element size of the buffers in that type
     qmc_opts o;
     std::vector<double> u, anis, g;
     std::vector<cd> alpha;
@@ -45,39 +56,52 @@ struct qmc_ctx {
     std::string err;
     std::vector<void *> allocs;
 
-    // tables
+    // tables (FP64)
     cd *ff_val = nullptr, *trF = nullptr;
     int *ff_col = nullptr, *qxy = nullptr, *partner = nullptr, *fkind = nullptr, *frA = nullptr,
         *frB = nullptr, *fq = nullptr, *fk = nullptr, *aptr = nullptr, *aq = nullptr;
     cd *alpha_d = nullptr;
     double *g_d = nullptr;
     uint32_t *keys = nullptr;
-    // chain state
+    // chain state (FP64)
     double *phi = nullptr, *eigW = nullptr;
-    cd *eigU = nullptr, *B = nullptr, *Binv = nullptr, *G = nullptr;
-    cd *LQ = nullptr, *LW = nullptr;
-    double *LD = nullptr;
-    cd *RQ = nullptr, *RW = nullptr;
-    double *RD = nullptr;
-    // scratch
-    cd *Fm, *V, *Vp, *T, *Tp, *lam, *Dg, *Dgi, *lamp, *Dgp, *Dgip;
-    cd *Ah, *Y1, *Cacc, *At, *tq, *Up, *Bp, *Bpi, *X1, *X2, *M, *Gp, *Gs, *Qt, *Vt, *Eye, *dinvR,
-        *dinvL, *logdet, *ax;
-    double *Wp, *phip, *grad, *gradp, *Dt, *ones, *stats, *eps, *eps_used, *series, *trace;
-    int *piv, *flag, *errf;
+    cd *eigU = nullptr, *B = nullptr, *Binv = nullptr;
+    cd *G = nullptr, *LQ = nullptr, *LW = nullptr, *RQ = nullptr, *RW = nullptr;
+    double *LD = nullptr, *RD = nullptr;
+    // factor scratch (FP64)
+    cd *V, *Vp, *T, *Tp, *lam, *Dg, *Dgi, *lamp, *Dgp, *Dgip, *Up, *Bp, *Bpi;
+    double *Wp;
+    // gradient / wrap scratch in the compute type gp (aliases of the FP64
+    // diagonals when gp is FP64)
+    void *Ah, *Y1, *Cacc, *At, *lamG, *DgG, *DgiG, *lampG, *DgpG, *DgipG, *F1, *F2;
+    // eigensolver scratch: channel matrices (FP64, FP32 copy) and the FP32
+    // eigenpairs and FP64 polish buffers of the mixed mode
+    cd *Fm;
+    void *Fm32, *U32;
+    float *W32;
+    cd *NSx, *NSy, *NSz;
+    // scratch, FP64
+    cd *tq, *X1, *X2, *M, *Gp, *Gs, *Qt, *Vt, *Eye, *dinvR, *dinvL, *logdet, *ax;
+    double *phip, *grad, *gradp, *Dt, *ones, *stats, *eps, *eps_used, *series, *trace;
+    int *piv, *flag, *errf, *always;
     long long *trace_n;
+
+    // gp-typed pointer arithmetic (elements -> bytes)
+    void *at(void *p, long long e) const { return (char *)p + e * (long long)gsz; }
+    Op Gx(const void *p, long long s) const { return Op{p, s, gp}; }
 };
 
 template <class T>
-static int dalloc(qmc_ctx *ctx, T **p, size_t count)
+static int dalloc(qmc_ctx *ctx, T **p, size_t count, size_t elem = sizeof(T))
 {
     void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, (count ? count : 1) * sizeof(T));
+    size_t bytes = (count ? count : 1) * elem;
+    cudaError_t e = cudaMalloc(&q, bytes);
     if (e != cudaSuccess) {
         ctx->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
         return QMC_ERR_OOM;
     }
-    cudaMemset(q, 0, (count ? count : 1) * sizeof(T));
+    cudaMemset(q, 0, bytes);
     ctx->allocs.push_back(q);
     *p = (T *)q;
     return 0;
@@ -88,26 +112,36 @@ static int dalloc(qmc_ctx *ctx, T **p, size_t count)
         int r_ = dalloc(ctx, &(ptr), (size_t)(count));   \
         if (r_) return r_;                               \
     } while (0)
+// buffers in the gradient compute type
+#define DAG(ptr, count)                                           \
+    do {                                                          \
+        int r_ = dalloc(ctx, &(ptr), (size_t)(count), ctx->gsz);  \
+        if (r_) return r_;                                        \
+    } while (0)
 
 static const cd ONE = {1, 0}, ZERO = {0, 0}, MONE = {-1, 0};
 
 // ------------------------------------------------------------ pipeline ----
-// V, T and the factor diagonals of a slice from its eigenpairs
+// V, T (FP64) and the factor diagonals of a slice from its eigenpairs; the
+// diagonals also in the gradient compute type when that is FP32
 static void factors_from_eig(qmc_ctx *ctx, const cd *U, long long U_cs, const double *W,
-                             long long W_cs, cd *V, cd *T, cd *lam, cd *Dg, cd *Dgi)
+                             long long W_cs, cd *V, cd *T, cd *lam, cd *Dg, cd *Dgi, void *lamG,
+                             void *DgG, void *DgiG)
 {
     const int nb = ctx->nb, N = ctx->N;
     const long long NN = ctx->NN;
-    launch_build_V(ctx->st, nb, ctx->n, U, U_cs, V);
+    launch_build_V(ctx->st, TY_C64, nb, ctx->n, U, U_cs, V);
     // T01 = V0^H V1, T12 = V1^H V2, T23 = V2^H V3
     for (int x = 0; x < 3; ++x)
-        zgemm_sq(ctx->st, N, nb, V + x * NN, 4 * NN, 2, V + (x + 1) * NN, 4 * NN, 0, T + x * NN,
-                 3 * NN);
-    launch_lambda(ctx->st, nb, ctx->n, W, W_cs, ctx->alpha_d, lam, Dg, Dgi);
+        gemm_sq(ctx->st, N, nb, TY_C64, op64(V + x * NN, 4 * NN), 2, op64(V + (x + 1) * NN, 4 * NN),
+                0, op64(T + x * NN, 3 * NN));
+    launch_lambda(ctx->st, TY_C64, nb, ctx->n, W, W_cs, ctx->alpha_d, lam, Dg, Dgi);
+    if (ctx->gp != TY_C64)
+        launch_lambda(ctx->st, ctx->gp, nb, ctx->n, W, W_cs, ctx->alpha_d, lamG, DgG, DgiG);
 }
 
 // B = V0 D0 T01 D1 T12 D2 T23 D3 T23^H D4 T12^H D5 T01^H D6 V0^H and the
-// inverse with the diagonals reversed and inverted
+// inverse with the diagonals reversed and inverted (FP64)
 static void build_B(qmc_ctx *ctx, const cd *V, const cd *T, const cd *Dg, const cd *Dgi, cd *Bout,
                     long long Bo_cs, cd *Biout, long long Bio_cs)
 {
@@ -123,14 +157,16 @@ static void build_B(qmc_ctx *ctx, const cd *V, const cd *T, const cd *Dg, const 
             int j = inv ? 6 - step : step;  // diagonal used at this position
             const cd *dj = dg + (long long)j * N;
             if (step == 0) {
-                zgemm_sq(ctx->st, N, nb, V, 4 * NN, 0, T + 0 * NN, 3 * NN, 0, a, NN, dj, 7 * N);
+                gemm_sq(ctx->st, N, nb, TY_C64, op64(V, 4 * NN), 0, op64(T, 3 * NN), 0,
+                        op64(a, NN), dj, 7 * N);
             } else if (step < 6) {
                 int op = step < 3 ? 0 : 2;
-                zgemm_sq(ctx->st, N, nb, a, NN, 0, T + (long long)tidx[step] * NN, 3 * NN, op, b,
-                         NN, dj, 7 * N);
+                gemm_sq(ctx->st, N, nb, TY_C64, op64(a, NN), 0,
+                        op64(T + (long long)tidx[step] * NN, 3 * NN), op, op64(b, NN), dj, 7 * N);
                 std::swap(a, b);
             } else {
-                zgemm_sq(ctx->st, N, nb, a, NN, 0, V, 4 * NN, 2, dst, dcs, dj, 7 * N);
+                gemm_sq(ctx->st, N, nb, TY_C64, op64(a, NN), 0, op64(V, 4 * NN), 2,
+                        op64(dst, dcs), dj, 7 * N);
             }
         }
     }
@@ -138,54 +174,71 @@ static void build_B(qmc_ctx *ctx, const cd *V, const cd *T, const cd *Dg, const 
 
 // exact grad S of one slice (Methods, Eq. action_gradient): chain of the
 // matrices A_j = P_j^-1 (1 - G) P_j in the eigenbases of the seven factors,
-// Daleckii-Krein weights, back-transform per channel, traces with F_q
-static void gradient(qmc_ctx *ctx, const cd *Gm, const cd *V, const cd *T, const cd *lam,
-                     const cd *Dg, const cd *Dgi, const double *phi, long long phi_cs, double *grad)
+// Daleckii-Krein weights, back-transform per channel, traces with F_q;
+// computed in the gradient compute type from the FP64 V, T and G
+static void gradient(qmc_ctx *ctx, const cd *Gm, const cd *V, const cd *T, const void *lam,
+                     const void *Dg, const void *Dgi, const double *phi, long long phi_cs,
+                     double *grad)
 {
-    const int nb = ctx->nb, N = ctx->N;
+    const int nb = ctx->nb, N = ctx->N, gp = ctx->gp;
     const long long NN = ctx->NN;
     cudaStream_t s = ctx->st;
     // Ah = I - V0^H G V0
-    zgemm_sq(s, N, nb, V, 4 * NN, 2, Gm, NN, 0, ctx->Y1, NN);
-    zgemm_sq(s, N, nb, ctx->Y1, NN, 0, V, 4 * NN, 0, ctx->Ah, NN, nullptr, 0, MONE, ZERO, 1);
+    gemm_sq(s, N, nb, gp, op64(V, 4 * NN), 2, op64(Gm, NN), 0, ctx->Gx(ctx->Y1, NN));
+    gemm_sq(s, N, nb, gp, ctx->Gx(ctx->Y1, NN), 0, op64(V, 4 * NN), 0, ctx->Gx(ctx->Ah, NN),
+            nullptr, 0, MONE, ZERO, 1);
     const int tidx[6] = {0, 1, 2, 2, 1, 0};
     for (int j = 0; j < 7; ++j) {
-        launch_accum(s, nb, N, j, j < 4, ctx->alpha_d, lam, ctx->Ah, ctx->Cacc);
+        launch_accum(s, gp, nb, N, j, j < 4, ctx->alpha_d, lam, ctx->Ah, ctx->Cacc);
         if (j == 6) break;
         const cd *Tx = T + (long long)tidx[j] * NN;
         int op1 = j < 3 ? 2 : 0, op2 = j < 3 ? 0 : 2;
-        zgemm_sq(s, N, nb, Tx, 3 * NN, op1, ctx->Ah, NN, 0, ctx->Y1, NN, Dgi + (long long)j * N,
-                 7 * N);
-        zgemm_sq(s, N, nb, ctx->Y1, NN, 0, Tx, 3 * NN, op2, ctx->Ah, NN, Dg + (long long)j * N,
-                 7 * N);
+        gemm_sq(s, N, nb, gp, op64(Tx, 3 * NN), op1, ctx->Gx(ctx->Ah, NN), 0, ctx->Gx(ctx->Y1, NN),
+                ctx->at((void *)Dgi, (long long)j * N), 7 * N);
+        gemm_sq(s, N, nb, gp, ctx->Gx(ctx->Y1, NN), 0, op64(Tx, 3 * NN), op2, ctx->Gx(ctx->Ah, NN),
+                ctx->at((void *)Dg, (long long)j * N), 7 * N);
     }
     for (int i = 0; i < 4; ++i) {
-        zgemm_sq(s, N, nb, V + i * NN, 4 * NN, 0, ctx->Cacc + i * NN, 4 * NN, 0, ctx->Y1, NN);
-        zgemm_sq(s, N, nb, ctx->Y1, NN, 0, V + i * NN, 4 * NN, 2, ctx->At + i * NN, 4 * NN);
+        gemm_sq(s, N, nb, gp, op64(V + i * NN, 4 * NN), 0, ctx->Gx(ctx->at(ctx->Cacc, i * NN), 4 * NN),
+                0, ctx->Gx(ctx->Y1, NN));
+        gemm_sq(s, N, nb, gp, ctx->Gx(ctx->Y1, NN), 0, op64(V + i * NN, 4 * NN), 2,
+                ctx->Gx(ctx->at(ctx->At, i * NN), 4 * NN));
     }
-    launch_trace_grad(s, nb, ctx->n, ctx->nq, ctx->At, ctx->ff_val, ctx->ff_col, ctx->trF,
+    launch_trace_grad(s, gp, nb, ctx->n, ctx->nq, ctx->At, ctx->ff_val, ctx->ff_col, ctx->trF,
                       ctx->alpha_d, ctx->tq, ctx->fq, ctx->fk, ctx->partner, phi, phi_cs, grad);
 }
 
-// eigenpairs of the four channel matrices of fields phi (chain stride phi_cs)
-static int eig_of_fields(qmc_ctx *ctx, const double *phi, long long phi_cs, cd *U, long long U_cs,
-                         double *W, long long W_cs)
+// FP64 eigenpairs (U [nb][4][n^2], W [nb][4][n]) of the four channel matrices
+// of fields phi (chain stride phi_cs).  FP64 mode: FP64 Jacobi.  Mixed mode:
+// Jacobi sweeps in FP32, two Newton-Schulz steps U <- U (3 - U^H U)/2 in
+// FP64 to restore unitarity, then FP64 Jacobi on the nearly diagonal
+// A = U^H F U starting from V = U (converges in one or two sweeps): the same
+// eigenpairs as the FP64 solver, at a fraction of its FP64 work.
+static int eig_of_fields(qmc_ctx *ctx, const double *phi, long long phi_cs, cd *U, double *W)
 {
-    launch_assemble(ctx->st, ctx->nb, ctx->n, ctx->nq, phi, phi_cs, ctx->fkind, ctx->frA, ctx->frB,
-                    ctx->aptr, ctx->aq, ctx->ff_val, ctx->Fm);
+    const int nb = ctx->nb, n = ctx->n;
     const long long n2 = ctx->n2;
-    if (U_cs == 4 * n2 && W_cs == 4 * ctx->n) {
-        return eigh_batched(ctx->st, ctx->n, ctx->Fm, n2, U, n2, W, ctx->n, 4 * ctx->nb);
+    cudaStream_t s = ctx->st;
+    launch_assemble(s, TY_C64, nb, n, ctx->nq, phi, phi_cs, ctx->fkind, ctx->frA, ctx->frB,
+                    ctx->aptr, ctx->aq, ctx->ff_val, ctx->Fm);
+    if (ctx->gp == TY_C64) return eigh_batched(s, TY_C64, n, ctx->Fm, n2, U, n2, W, n, 4 * nb);
+    launch_axpyI(s, 4 * nb, n, op64(ctx->Fm, n2), ONE, ZERO, Op{ctx->Fm32, n2, TY_C32});
+    if (eigh_batched(s, TY_C32, n, ctx->Fm32, n2, ctx->U32, n2, ctx->W32, n, 4 * nb)) return -1;
+    launch_axpyI(s, 4 * nb, n, Op{ctx->U32, n2, TY_C32}, ONE, ZERO, op64(ctx->NSy, n2));
+    cd *a = ctx->NSy, *b = ctx->NSz;
+    for (int it = 0; it < 2; ++it) {
+        gemm_sq(s, n, 4 * nb, TY_C64, op64(a, n2), 2, op64(a, n2), 0, op64(ctx->NSx, n2));
+        launch_axpyI(s, 4 * nb, n, op64(ctx->NSx, n2), cmk(-0.5, 0), cmk(1.5, 0), op64(ctx->NSx, n2));
+        gemm_sq(s, n, 4 * nb, TY_C64, op64(a, n2), 0, op64(ctx->NSx, n2), 0, op64(b, n2));
+        std::swap(a, b);
     }
-    for (int c = 0; c < ctx->nb; ++c) {
-        int r = eigh_batched(ctx->st, ctx->n, ctx->Fm + c * 4 * n2, n2, U + c * U_cs, n2,
-                             W + c * W_cs, ctx->n, 4);
-        if (r) return r;
-    }
-    return 0;
+    // A = U^H F U, then polish: V starts at U
+    gemm_sq(s, n, 4 * nb, TY_C64, op64(a, n2), 2, op64(ctx->Fm, n2), 0, op64(ctx->NSx, n2));
+    gemm_sq(s, n, 4 * nb, TY_C64, op64(ctx->NSx, n2), 0, op64(a, n2), 0, op64(b, n2));
+    return eigh_batched(s, TY_C64, n, b, n2, U, n2, W, n, 4 * nb, a, n2);
 }
 
-// G = QL DbL^-1 [DbR^-1 QR^H QL DbL^-1 + DsR WR WL^H DsL]^-1 DbR^-1 QR^H
+// G = QL DbL^-1 [DbR^-1 QR^H QL DbL^-1 + DsR WR WL^H DsL]^-1 DbR^-1 QR^H (FP64)
 static int green_from_udv(qmc_ctx *ctx, const cd *QR, const double *DR, const cd *WR,
                           long long R_cs, long long RD_cs, const cd *QL, const double *DL,
                           const cd *WL, long long L_cs, long long LD_cs, cd *Gout)
@@ -193,17 +246,19 @@ static int green_from_udv(qmc_ctx *ctx, const cd *QR, const double *DR, const cd
     const int nb = ctx->nb, N = ctx->N;
     const long long NN = ctx->NN;
     cudaStream_t s = ctx->st;
-    zgemm_sq(s, N, nb, QR, R_cs, 2, QL, L_cs, 0, ctx->X1, NN);
-    zgemm_sq(s, N, nb, WR, R_cs, 0, WL, L_cs, 2, ctx->X2, NN);
+    gemm_sq(s, N, nb, TY_C64, op64(QR, R_cs), 2, op64(QL, L_cs), 0, op64(ctx->X1, NN));
+    gemm_sq(s, N, nb, TY_C64, op64(WR, R_cs), 0, op64(WL, L_cs), 2, op64(ctx->X2, NN));
     launch_stab_mix(s, nb, N, ctx->X1, ctx->X2, DR, RD_cs, DL, LD_cs, ctx->M);
     if (lu_batched(s, N, ctx->M, NN, ctx->piv, N, nullptr, nb)) return QMC_ERR_ARG;
     launch_inv_big(s, nb, N, DL, LD_cs, ctx->dinvL);
     launch_inv_big(s, nb, N, DR, RD_cs, ctx->dinvR);
     // X1 = QL diag(dinvL): GEMM against the identity keeps the scaling on device
-    zgemm_sq(s, N, nb, QL, L_cs, 0, ctx->Eye, NN, 0, ctx->X1, NN, ctx->dinvL, N);
-    if (rdiv_batched(s, N, ctx->X1, NN, ctx->M, NN, ctx->piv, N, ctx->X2, NN, nb))
+    gemm_sq(s, N, nb, TY_C64, op64(QL, L_cs), 0, op64(ctx->Eye, NN), 0, op64(ctx->X1, NN),
+            ctx->dinvL, N);
+    if (rdiv_batched(s, TY_C64, N, ctx->X1, NN, ctx->M, NN, ctx->piv, N, ctx->X2, NN, nb))
         return QMC_ERR_ARG;
-    zgemm_sq(s, N, nb, ctx->X2, NN, 0, QR, R_cs, 2, Gout, NN, ctx->dinvR, N);
+    gemm_sq(s, N, nb, TY_C64, op64(ctx->X2, NN), 0, op64(QR, R_cs), 2, op64(Gout, NN), ctx->dinvR,
+            N);
     return 0;
 }
 
@@ -215,7 +270,6 @@ static int build_left_stack(qmc_ctx *ctx)
     cudaStream_t s = ctx->st;
     const long long BL = (long long)ctx->L * NN;
     int k = nsp - 1;
-    CK(cudaMemcpyAsync(ctx->X1, ctx->Eye, sizeof(cd) * NN * nb, cudaMemcpyDeviceToDevice, s));
     for (int c = 0; c < nb; ++c) {
         CK(cudaMemcpyAsync(ctx->LQ + c * Ls + k * NN, ctx->Eye, sizeof(cd) * NN,
                            cudaMemcpyDeviceToDevice, s));
@@ -230,13 +284,15 @@ static int build_left_stack(qmc_ctx *ctx)
         launch_scale_cols(s, nb, N, ctx->LQ + k * NN, Ls, ctx->LD + k * N, LDs, ctx->X1, NN);
         cd *a = ctx->X1, *b = ctx->X2;
         for (int t = hi; t > lo; --t) {
-            zgemm_sq(s, N, nb, ctx->B + (long long)(t - 1) * NN, BL, 2, a, NN, 0, b, NN);
+            gemm_sq(s, N, nb, TY_C64, op64(ctx->B + (long long)(t - 1) * NN, BL), 2, op64(a, NN), 0,
+                    op64(b, NN));
             std::swap(a, b);
         }
         if (qrp_batched(s, N, a, NN, ctx->LQ + dst * NN, Ls, ctx->LD + dst * N, LDs, ctx->Vt, NN,
                         nb))
             return QMC_ERR_ARG;
-        zgemm_sq(s, N, nb, ctx->Vt, NN, 0, ctx->LW + k * NN, Ls, 0, ctx->LW + dst * NN, Ls);
+        gemm_sq(s, N, nb, TY_C64, op64(ctx->Vt, NN), 0, op64(ctx->LW + k * NN, Ls), 0,
+                op64(ctx->LW + dst * NN, Ls));
     }
     return 0;
 }
@@ -264,7 +320,7 @@ static int green_at_zero(qmc_ctx *ctx)
 // one MALA proposal + MH test on slice t (1-based) for every chain
 static int update_slice(qmc_ctx *ctx, int t)
 {
-    const int nb = ctx->nb, N = ctx->N, n = ctx->n, nf = ctx->nf;
+    const int nb = ctx->nb, N = ctx->N, n = ctx->n, nf = ctx->nf, gp = ctx->gp;
     const long long NN = ctx->NN, n2 = ctx->n2;
     const int s0 = t - 1;
     cudaStream_t s = ctx->st;
@@ -272,31 +328,34 @@ static int update_slice(qmc_ctx *ctx, int t)
     const double *phi_s = ctx->phi + (long long)s0 * nf;
     const long long phi_cs = L * nf;
     cd *Bis = ctx->Binv + (long long)s0 * NN;
+    cd *Us = ctx->eigU + (long long)s0 * 4 * n2;
+    double *Ws = ctx->eigW + (long long)s0 * 4 * n;
     // forward gradient at the current fields
-    factors_from_eig(ctx, ctx->eigU + (long long)s0 * 4 * n2, L * 4 * n2,
-                     ctx->eigW + (long long)s0 * 4 * n, L * 4 * n, ctx->V, ctx->T, ctx->lam,
-                     ctx->Dg, ctx->Dgi);
-    gradient(ctx, ctx->G, ctx->V, ctx->T, ctx->lam, ctx->Dg, ctx->Dgi, phi_s, phi_cs, ctx->grad);
+    factors_from_eig(ctx, Us, L * 4 * n2, Ws, L * 4 * n, ctx->V, ctx->T, ctx->lam, ctx->Dg,
+                     ctx->Dgi, ctx->lamG, ctx->DgG, ctx->DgiG);
+    gradient(ctx, ctx->G, ctx->V, ctx->T, ctx->lamG, ctx->DgG, ctx->DgiG, phi_s, phi_cs, ctx->grad);
     launch_propose(s, nb, nf, phi_s, phi_cs, ctx->grad, ctx->eps, ctx->keys, (uint32_t)s0,
                    ctx->sweep, ctx->phip);
     // proposal factors and propagators
-    int r = eig_of_fields(ctx, ctx->phip, nf, ctx->Up, 4 * n2, ctx->Wp, 4 * n);
-    if (r) {
+    if (eig_of_fields(ctx, ctx->phip, nf, ctx->Up, ctx->Wp)) {
         ctx->err = "eigensolver: unsupported size";
         return QMC_ERR_ARG;
     }
     factors_from_eig(ctx, ctx->Up, 4 * n2, ctx->Wp, 4 * n, ctx->Vp, ctx->Tp, ctx->lamp, ctx->Dgp,
-                     ctx->Dgip);
+                     ctx->Dgip, ctx->lampG, ctx->DgpG, ctx->DgipG);
     build_B(ctx, ctx->Vp, ctx->Tp, ctx->Dgp, ctx->Dgip, ctx->Bp, NN, ctx->Bpi, NN);
-    // M = 1 + (B' B^-1 - 1)(1 - G)
-    zgemm_sq(s, N, nb, ctx->Bp, NN, 0, Bis, L * NN, 0, ctx->X1, NN);
-    launch_axpyI(s, nb, N, ctx->X1, NN, ONE, MONE, ctx->X1, NN);
-    launch_axpyI(s, nb, N, ctx->G, NN, MONE, ONE, ctx->X2, NN);
-    zgemm_sq(s, N, nb, ctx->X1, NN, 0, ctx->X2, NN, 0, ctx->M, NN, nullptr, 0, ONE, ZERO, 1);
+    // M = 1 + (B' B^-1 - 1)(1 - G) in FP64: B' B^-1 - 1 is small, so its
+    // absolute rounding error would be amplified by the conditioning of M
+    gemm_sq(s, N, nb, TY_C64, op64(ctx->Bp, NN), 0, op64(Bis, L * NN), 0, op64(ctx->X1, NN));
+    launch_axpyI(s, nb, N, op64(ctx->X1, NN), ONE, MONE, op64(ctx->X1, NN));
+    launch_axpyI(s, nb, N, op64(ctx->G, NN), MONE, ONE, op64(ctx->X2, NN));
+    gemm_sq(s, N, nb, TY_C64, op64(ctx->X1, NN), 0, op64(ctx->X2, NN), 0, op64(ctx->M, NN), nullptr,
+            0, ONE, ZERO, 1);
     if (lu_batched(s, N, ctx->M, NN, ctx->piv, N, ctx->logdet, nb)) return QMC_ERR_ARG;
-    if (rdiv_batched(s, N, ctx->G, NN, ctx->M, NN, ctx->piv, N, ctx->Gp, NN, nb)) return QMC_ERR_ARG;
+    if (rdiv_batched(s, TY_C64, N, ctx->G, NN, ctx->M, NN, ctx->piv, N, ctx->Gp, NN, nb))
+        return QMC_ERR_ARG;
     // reverse gradient at the proposal with G'
-    gradient(ctx, ctx->Gp, ctx->Vp, ctx->Tp, ctx->lamp, ctx->Dgp, ctx->Dgip, ctx->phip, nf,
+    gradient(ctx, ctx->Gp, ctx->Vp, ctx->Tp, ctx->lampG, ctx->DgpG, ctx->DgipG, ctx->phip, nf,
              ctx->gradp);
     AcceptP ap;
     ap.nq = ctx->nq;
@@ -323,25 +382,17 @@ static int update_slice(qmc_ctx *ctx, int t)
     ap.trace_cap = ctx->o.trace_capacity;
     ap.trace_n = ctx->trace_n;
     launch_accept(s, nb, ap);
+    // commit: propagators, eigenpairs, G, fields (sizes in 4-byte words per chain)
     CommitP cp;
-    cp.N = N;
-    cp.n = n;
-    cp.nf = nf;
-    cp.L = ctx->L;
-    cp.s = s0;
     cp.flag = ctx->flag;
-    cp.B = ctx->B;
-    cp.Binv = ctx->Binv;
-    cp.G = ctx->G;
-    cp.U = ctx->eigU;
-    cp.W = ctx->eigW;
-    cp.phi = ctx->phi;
-    cp.Bp = ctx->Bp;
-    cp.Bpi = ctx->Bpi;
-    cp.Gp = ctx->Gp;
-    cp.Up = ctx->Up;
-    cp.Wp = ctx->Wp;
-    cp.phip = ctx->phip;
+    cp.nseg = 6;
+    cp.seg[0] = CommitSeg{ctx->B + (long long)s0 * NN, ctx->Bp, NN * 4, L * NN * 4, NN * 4};
+    cp.seg[1] = CommitSeg{Bis, ctx->Bpi, NN * 4, L * NN * 4, NN * 4};
+    cp.seg[2] = CommitSeg{Us, ctx->Up, 4 * n2 * 4, L * 4 * n2 * 4, 4 * n2 * 4};
+    cp.seg[3] = CommitSeg{Ws, ctx->Wp, 4 * n * 2, L * 4 * n * 2, 4 * n * 2};
+    cp.seg[4] = CommitSeg{ctx->G, ctx->Gp, NN * 4, NN * 4, NN * 4};
+    cp.seg[5] = CommitSeg{(void *)phi_s, ctx->phip, (long long)nf * 2, phi_cs * 2,
+                          (long long)nf * 2};
     launch_commit(s, nb, cp);
     return 0;
 }
@@ -356,11 +407,12 @@ static int restabilise(qmc_ctx *ctx, int k, int prev, int t)
     launch_scale_cols(s, nb, N, ctx->RQ, NN, ctx->RD, N, ctx->X1, NN);
     cd *a = ctx->X1, *b = ctx->X2;
     for (int u = prev + 1; u <= t; ++u) {
-        zgemm_sq(s, N, nb, ctx->B + (long long)(u - 1) * NN, BL, 0, a, NN, 0, b, NN);
+        gemm_sq(s, N, nb, TY_C64, op64(ctx->B + (long long)(u - 1) * NN, BL), 0, op64(a, NN), 0,
+                op64(b, NN));
         std::swap(a, b);
     }
     if (qrp_batched(s, N, a, NN, ctx->Qt, NN, ctx->Dt, N, ctx->Vt, NN, nb)) return QMC_ERR_ARG;
-    zgemm_sq(s, N, nb, ctx->Vt, NN, 0, ctx->RW, NN, 0, ctx->X1, NN);
+    gemm_sq(s, N, nb, TY_C64, op64(ctx->Vt, NN), 0, op64(ctx->RW, NN), 0, op64(ctx->X1, NN));
     std::swap(ctx->RW, ctx->X1);
     std::swap(ctx->RQ, ctx->Qt);
     std::swap(ctx->RD, ctx->Dt);
@@ -402,10 +454,11 @@ static int one_sweep(qmc_ctx *ctx)
     const long long NN = ctx->NN, BL = (long long)ctx->L * NN;
     int k = 0, prev = 0;
     for (int t = 1; t <= ctx->L; ++t) {
-        zgemm_sq(ctx->st, N, nb, ctx->B + (long long)(t - 1) * NN, BL, 0, ctx->G, NN, 0, ctx->X1,
-                 NN);
-        zgemm_sq(ctx->st, N, nb, ctx->X1, NN, 0, ctx->Binv + (long long)(t - 1) * NN, BL, 0, ctx->G,
-                 NN);
+        // wrap G <- B_t G B_t^-1 in FP64: G enters every determinant ratio
+        gemm_sq(ctx->st, N, nb, TY_C64, op64(ctx->B + (long long)(t - 1) * NN, BL), 0,
+                op64(ctx->G, NN), 0, op64(ctx->X1, NN));
+        gemm_sq(ctx->st, N, nb, TY_C64, op64(ctx->X1, NN), 0,
+                op64(ctx->Binv + (long long)(t - 1) * NN, BL), 0, op64(ctx->G, NN));
         r = update_slice(ctx, t);
         if (r) return r;
         if (t == ctx->sp[k]) {
@@ -437,11 +490,12 @@ static int ratio_update_core(cudaStream_t s, int N, int batch, const cd *G, cons
                              cd *logdet, cd *X1, cd *X2, cd *M, int *piv)
 {
     const long long NN = (long long)N * N;
-    launch_axpyI(s, batch, N, Dl, NN, ONE, MONE, X1, NN);
-    launch_axpyI(s, batch, N, G, NN, MONE, ONE, X2, NN);
-    zgemm_sq(s, N, batch, X1, NN, 0, X2, NN, 0, M, NN, nullptr, 0, ONE, ZERO, 1);
+    launch_axpyI(s, batch, N, op64(Dl, NN), ONE, MONE, op64(X1, NN));
+    launch_axpyI(s, batch, N, op64(G, NN), MONE, ONE, op64(X2, NN));
+    gemm_sq(s, N, batch, TY_C64, op64(X1, NN), 0, op64(X2, NN), 0, op64(M, NN), nullptr, 0, ONE,
+            ZERO, 1);
     if (lu_batched(s, N, M, NN, piv, N, logdet, batch)) return QMC_ERR_ARG;
-    if (rdiv_batched(s, N, G, NN, M, NN, piv, N, Gp, NN, batch)) return QMC_ERR_ARG;
+    if (rdiv_batched(s, TY_C64, N, G, NN, M, NN, piv, N, Gp, NN, batch)) return QMC_ERR_ARG;
     return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
 }
 
@@ -579,7 +633,6 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
     DA(ctx->RQ, (size_t)nb * NN);
     DA(ctx->RW, (size_t)nb * NN);
     DA(ctx->RD, (size_t)nb * N);
-    DA(ctx->Fm, (size_t)nb * 4 * n2);
     DA(ctx->V, (size_t)nb * 4 * NN);
     DA(ctx->Vp, (size_t)nb * 4 * NN);
     DA(ctx->T, (size_t)nb * 3 * NN);
@@ -590,15 +643,43 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
     DA(ctx->lamp, (size_t)nb * 7 * N);
     DA(ctx->Dgp, (size_t)nb * 7 * N);
     DA(ctx->Dgip, (size_t)nb * 7 * N);
-    DA(ctx->Ah, (size_t)nb * NN);
-    DA(ctx->Y1, (size_t)nb * NN);
-    DA(ctx->Cacc, (size_t)nb * 4 * NN);
-    DA(ctx->At, (size_t)nb * 4 * NN);
-    DA(ctx->tq, (size_t)nb * 4 * nq);
     DA(ctx->Up, (size_t)nb * 4 * n2);
     DA(ctx->Wp, (size_t)nb * 4 * n);
     DA(ctx->Bp, (size_t)nb * NN);
     DA(ctx->Bpi, (size_t)nb * NN);
+    DAG(ctx->Ah, (size_t)nb * NN);
+    DAG(ctx->Y1, (size_t)nb * NN);
+    DAG(ctx->Cacc, (size_t)nb * 4 * NN);
+    DAG(ctx->At, (size_t)nb * 4 * NN);
+    DAG(ctx->F1, (size_t)nb * NN);
+    DAG(ctx->F2, (size_t)nb * NN);
+    DA(ctx->Fm, (size_t)nb * 4 * n2);
+    if (ctx->gp == TY_C64) {
+        ctx->lamG = ctx->lam;
+        ctx->DgG = ctx->Dg;
+        ctx->DgiG = ctx->Dgi;
+        ctx->lampG = ctx->lamp;
+        ctx->DgpG = ctx->Dgp;
+        ctx->DgipG = ctx->Dgip;
+        ctx->U32 = nullptr;
+        ctx->W32 = nullptr;
+        ctx->Fm32 = nullptr;
+    } else {
+        DAG(ctx->lamG, (size_t)nb * 7 * N);
+        DAG(ctx->DgG, (size_t)nb * 7 * N);
+        DAG(ctx->DgiG, (size_t)nb * 7 * N);
+        DAG(ctx->lampG, (size_t)nb * 7 * N);
+        DAG(ctx->DgpG, (size_t)nb * 7 * N);
+        DAG(ctx->DgipG, (size_t)nb * 7 * N);
+        DAG(ctx->U32, (size_t)nb * 4 * n2);
+        DA(ctx->W32, (size_t)nb * 4 * n);
+        DAG(ctx->Fm32, (size_t)nb * 4 * n2);
+    }
+    DA(ctx->NSx, (size_t)nb * 4 * n2);
+    DA(ctx->NSy, (size_t)nb * 4 * n2);
+    DA(ctx->NSz, (size_t)nb * 4 * n2);
+    DA(ctx->always, nb);
+    DA(ctx->tq, (size_t)nb * 4 * nq);
     DA(ctx->X1, (size_t)nb * NN);
     DA(ctx->X2, (size_t)nb * NN);
     DA(ctx->M, (size_t)nb * NN);
@@ -626,6 +707,10 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
     DA(ctx->flag, nb);
     DA(ctx->errf, nb);
     cudaStream_t s = ctx->st;
+    {
+        std::vector<int> one(nb, 1);
+        CK(cudaMemcpy(ctx->always, one.data(), sizeof(int) * nb, cudaMemcpyHostToDevice));
+    }
     CK(cudaMemcpyAsync(ctx->qxy, qxy.data(), sizeof(int) * qxy.size(), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->partner, partner.data(), sizeof(int) * nq, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->fkind, fkind.data(), sizeof(int) * nq, cudaMemcpyHostToDevice, s));
@@ -652,16 +737,20 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
     launch_init_phi(s, nb, ctx->L, nf, ctx->keys, ctx->phi);
     // eigenpairs and propagators of every slice
     for (int t = 0; t < ctx->L; ++t) {
-        int r = eig_of_fields(ctx, ctx->phi + (long long)t * nf, L * nf,
-                              ctx->eigU + (long long)t * 4 * n2, L * 4 * n2,
-                              ctx->eigW + (long long)t * 4 * n, L * 4 * n);
-        if (r) {
+        if (eig_of_fields(ctx, ctx->phi + (long long)t * nf, L * nf, ctx->Up, ctx->Wp)) {
             ctx->err = "eigensolver: unsupported size";
             return QMC_ERR_ARG;
         }
-        factors_from_eig(ctx, ctx->eigU + (long long)t * 4 * n2, L * 4 * n2,
-                         ctx->eigW + (long long)t * 4 * n, L * 4 * n, ctx->V, ctx->T, ctx->lam,
-                         ctx->Dg, ctx->Dgi);
+        CommitP cp;
+        cp.flag = ctx->always;
+        cp.nseg = 2;
+        cp.seg[0] = CommitSeg{ctx->eigU + (long long)t * 4 * n2, ctx->Up, 4 * n2 * 4,
+                              L * 4 * n2 * 4, 4 * n2 * 4};
+        cp.seg[1] = CommitSeg{ctx->eigW + (long long)t * 4 * n, ctx->Wp, 4LL * n * 2,
+                              L * 4 * n * 2, 4LL * n * 2};
+        launch_commit(s, nb, cp);
+        factors_from_eig(ctx, ctx->Up, 4 * n2, ctx->Wp, 4 * n, ctx->V, ctx->T, ctx->lam, ctx->Dg,
+                         ctx->Dgi, ctx->lamG, ctx->DgG, ctx->DgiG);
         build_B(ctx, ctx->V, ctx->T, ctx->Dg, ctx->Dgi, ctx->B + (long long)t * NN, L * NN,
                 ctx->Binv + (long long)t * NN, L * NN);
     }
@@ -715,7 +804,7 @@ int qmc_create(qmc_ctx **out, int geometry, int N_phi, double beta, double dtau,
         ctx->err = "beta and dtau must be positive";
         code = QMC_ERR_ARG;
     } else if (ctx->o.n_chains < 1 || ctx->o.n_stab < 1 || ctx->o.series_capacity < 1 ||
-               ctx->o.trace_capacity < 0 || ctx->o.precision != 0) {
+               ctx->o.trace_capacity < 0 || ctx->o.precision < 0 || ctx->o.precision > 1) {
         ctx->err = "invalid options";
         code = QMC_ERR_ARG;
     } else {
@@ -734,20 +823,14 @@ int qmc_create(qmc_ctx **out, int geometry, int N_phi, double beta, double dtau,
             ctx->nb = ctx->o.n_chains;
             ctx->beta = beta;
             ctx->dtau = dtau;
-            ctx->o.couplings = ctx->o.anisotropies = nullptr;
-            ctx->o.seeds = nullptr;
-            qmc_opts tmp = ctx->o;
-            if (opts) {
-                tmp.couplings = opts->couplings;
-                tmp.anisotropies = opts->anisotropies;
-                tmp.seeds = opts->seeds;
-            }
-            ctx->o = tmp;
+            ctx->gp = ctx->o.precision == 1 ? TY_C32 : TY_C64;
+            ctx->gsz = ctx->gp == TY_C32 ? sizeof(cf) : sizeof(cd);
             code = setup(ctx, seed, coupling, anisotropy);
-            ctx->o.couplings = ctx->o.anisotropies = nullptr;
-            ctx->o.seeds = nullptr;
         }
     }
+    // the per-chain arrays were only read during setup
+    ctx->o.couplings = ctx->o.anisotropies = nullptr;
+    ctx->o.seeds = nullptr;
     if (code != QMC_OK) {
         fprintf(stderr, "qmc_create: %s\n", ctx->err.c_str());
         qmc_destroy(ctx);
@@ -760,8 +843,10 @@ int qmc_create(qmc_ctx **out, int geometry, int N_phi, double beta, double dtau,
 int qmc_destroy(qmc_ctx *ctx)
 {
     if (!ctx) return QMC_OK;
-    if (ctx->st) cudaStreamSynchronize(ctx->st);
-    else cudaDeviceSynchronize();
+    if (!ctx->allocs.empty()) {
+        if (ctx->st) cudaStreamSynchronize(ctx->st);
+        else cudaDeviceSynchronize();
+    }
     for (void *p : ctx->allocs) cudaFree(p);
     delete ctx;
     return QMC_OK;
@@ -810,7 +895,7 @@ int qmc_sync(qmc_ctx *ctx)
 int qmc_measure(qmc_ctx *ctx, double *host_out)
 {
     if (!ctx || !host_out) return QMC_ERR_ARG;
-    measure_into(ctx, ctx->gradp, QMC_NOBS);  // gradp has >= nb * QMC_NOBS doubles
+    measure_into(ctx, ctx->gradp, QMC_NOBS);  // gradp holds >= n_chains * QMC_NOBS doubles
     CK(cudaMemcpyAsync(host_out, ctx->gradp, sizeof(double) * ctx->nb * QMC_NOBS,
                        cudaMemcpyDeviceToHost, ctx->st));
     return qmc_sync(ctx);
@@ -902,6 +987,21 @@ int qmc_get_trace(qmc_ctx *ctx, int chain, double *host_buf, size_t len, long *c
     if (!host_buf || len < (size_t)n * QMC_NTRACE) return QMC_ERR_ARG;
     CK(cudaMemcpy(host_buf, ctx->trace + (size_t)chain * ctx->o.trace_capacity * QMC_NTRACE,
                   sizeof(double) * n * QMC_NTRACE, cudaMemcpyDeviceToHost));
+    return QMC_OK;
+}
+
+int qmc_get_propagator(qmc_ctx *ctx, int chain, int slice, double *host_B, double *host_Binv,
+                       size_t len)
+{
+    if (!ctx || chain < 0 || chain >= ctx->nb || slice < 1 || slice > ctx->L ||
+        len < 2 * (size_t)ctx->NN)
+        return QMC_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->st));
+    const long long off = ((long long)chain * ctx->L + slice - 1) * ctx->NN;
+    if (host_B)
+        CK(cudaMemcpy(host_B, ctx->B + off, sizeof(cd) * ctx->NN, cudaMemcpyDeviceToHost));
+    if (host_Binv)
+        CK(cudaMemcpy(host_Binv, ctx->Binv + off, sizeof(cd) * ctx->NN, cudaMemcpyDeviceToHost));
     return QMC_OK;
 }
 

@@ -1,7 +1,9 @@
-// linalg.cu -- batched dense complex FP64 kernels of libqmc: GEMM with an
-// optional diagonal between the operands, Hermitian Jacobi eigensolver, LU
-// with partial pivoting, right division X = G M^-1, Householder QR with
-// column pivoting (UDV).  All matrices are row-major interleaved complex.
+// linalg.cu -- batched dense complex kernels of libqmc: GEMM with an optional
+// diagonal between the operands (FP64 or FP32 compute, FP64/FP32 operands),
+// Hermitian Jacobi eigensolver (FP64 or FP32), LU with partial pivoting
+// (FP64), right division X = G M^-1 (FP64 or FP32 compute), Householder QR
+// with column pivoting (FP64).  All matrices are row-major interleaved
+// complex.
 #include "linalg.cuh"
 
 #include <vector>
@@ -11,35 +13,38 @@
 // op: 0 = none, 1 = transpose, 2 = conjugate transpose.  16 x 16 output tile
 // per block, one element per thread, K staged through shared memory in
 // slabs of 16; transposed operands are read with the thread index running
-// along the contiguous dimension.
+// along the contiguous dimension.  Operands of type TA/TB are converted to
+// the compute type on load; the diagonal has the compute type.
 #define GT 16
+template <class TA, class TB, class TC, class R>
 __global__ void __launch_bounds__(256) k_zgemm(GemmP p)
 {
-    __shared__ cd As[GT][GT + 1];
-    __shared__ cd Bs[GT][GT + 1];
+    typedef typename Cx<R>::T C;
+    __shared__ C As[GT][GT + 1];
+    __shared__ C Bs[GT][GT + 1];
     const int b = blockIdx.z, tx = threadIdx.x, ty = threadIdx.y;
     const int row0 = blockIdx.y * GT, col0 = blockIdx.x * GT;
-    const cd *A = p.A + (long long)b * p.sA;
-    const cd *B = p.B + (long long)b * p.sB;
-    const cd *d = p.d ? p.d + (long long)b * p.sd : nullptr;
-    cd acc = cmk(0, 0);
+    const TA *A = (const TA *)p.A + (long long)b * p.sA;
+    const TB *B = (const TB *)p.B + (long long)b * p.sB;
+    const C *d = p.d ? (const C *)p.d + (long long)b * p.sd : nullptr;
+    C acc = czero<C>();
     for (int k0 = 0; k0 < p.K; k0 += GT) {
         if (p.opA == 0) {
             int r = row0 + ty, k = k0 + tx;
-            As[ty][tx] = (r < p.M && k < p.K) ? A[(long long)r * p.lda + k] : cmk(0, 0);
+            As[ty][tx] = (r < p.M && k < p.K) ? cvt<C>(A[(long long)r * p.lda + k]) : czero<C>();
         } else {
             int r = row0 + tx, k = k0 + ty;
-            cd v = (r < p.M && k < p.K) ? A[(long long)k * p.lda + r] : cmk(0, 0);
+            C v = (r < p.M && k < p.K) ? cvt<C>(A[(long long)k * p.lda + r]) : czero<C>();
             As[tx][ty] = p.opA == 2 ? cconj(v) : v;
         }
         if (p.opB == 0) {
             int k = k0 + ty, c = col0 + tx;
-            cd v = (k < p.K && c < p.N) ? B[(long long)k * p.ldb + c] : cmk(0, 0);
+            C v = (k < p.K && c < p.N) ? cvt<C>(B[(long long)k * p.ldb + c]) : czero<C>();
             if (d && k < p.K) v = cmul(d[k], v);
             Bs[ty][tx] = v;
         } else {
             int k = k0 + tx, c = col0 + ty;
-            cd v = (k < p.K && c < p.N) ? B[(long long)c * p.ldb + k] : cmk(0, 0);
+            C v = (k < p.K && c < p.N) ? cvt<C>(B[(long long)c * p.ldb + k]) : czero<C>();
             if (p.opB == 2) v = cconj(v);
             if (d && k < p.K) v = cmul(d[k], v);
             Bs[tx][ty] = v;
@@ -51,11 +56,11 @@ __global__ void __launch_bounds__(256) k_zgemm(GemmP p)
     }
     const int r = row0 + ty, c = col0 + tx;
     if (r < p.M && c < p.N) {
-        cd *C = p.C + (long long)b * p.sC + (long long)r * p.ldc + c;
-        cd v = cmul(p.alpha, acc);
-        if (p.beta.x != 0.0 || p.beta.y != 0.0) v = cadd(v, cmul(p.beta, *C));
+        TC *Cp = (TC *)p.C + (long long)b * p.sC + (long long)r * p.ldc + c;
+        cd v = cmul(p.alpha, cvt<cd>(acc));
+        if (p.beta.x != 0.0 || p.beta.y != 0.0) v = cadd(v, cmul(p.beta, cvt<cd>(*Cp)));
         if (p.addI && r == c) v.x += 1.0;
-        *C = v;
+        *Cp = cvt<TC>(v);
     }
 }
 
@@ -103,19 +108,45 @@ static cudaEvent_t gprof_event()
     return g_gprof.ev[g_gprof.used++];
 }
 
-void zgemm(cudaStream_t st, const GemmP &p, int batch)
+typedef void (*gemm_fn)(GemmP);
+template <class R>
+static gemm_fn gemm_kernel_r(int ta, int tb, int tc)
 {
+    const int code = ta * 4 + tb * 2 + tc;
+    switch (code) {
+    case 0: return k_zgemm<cd, cd, cd, R>;
+    case 1: return k_zgemm<cd, cd, cf, R>;
+    case 2: return k_zgemm<cd, cf, cd, R>;
+    case 3: return k_zgemm<cd, cf, cf, R>;
+    case 4: return k_zgemm<cf, cd, cd, R>;
+    case 5: return k_zgemm<cf, cd, cf, R>;
+    case 6: return k_zgemm<cf, cf, cd, R>;
+    default: return k_zgemm<cf, cf, cf, R>;
+    }
+}
+static gemm_fn gemm_kernel(const GemmP &p)
+{
+    if (p.ta < 0 || p.ta > 1 || p.tb < 0 || p.tb > 1 || p.tc < 0 || p.tc > 1) return nullptr;
+    return p.rc == TY_C64 ? gemm_kernel_r<double>(p.ta, p.tb, p.tc)
+                          : gemm_kernel_r<float>(p.ta, p.tb, p.tc);
+}
+
+int zgemm(cudaStream_t st, const GemmP &p, int batch)
+{
+    gemm_fn f = gemm_kernel(p);
+    if (!f) return -1;
     dim3 grid(cdiv_up(p.N, GT), cdiv_up(p.M, GT), batch);
     if (g_gprof.on) {
         cudaEventRecord(gprof_event(), st);
-        k_zgemm<<<grid, dim3(GT, GT), 0, st>>>(p);
+        f<<<grid, dim3(GT, GT), 0, st>>>(p);
         cudaEventRecord(gprof_event(), st);
         g_gprof.flops += 8.0 * p.M * (double)p.N * p.K * batch;
         g_gprof.launches++;
     } else {
-        k_zgemm<<<grid, dim3(GT, GT), 0, st>>>(p);
+        f<<<grid, dim3(GT, GT), 0, st>>>(p);
     }
     QMC_COUNT(1);
+    return 0;
 }
 
 // -------------------------------------------------------- Jacobi eigh ----
@@ -126,31 +157,38 @@ void zgemm(cudaStream_t st, const GemmP &p, int batch)
 // a_pq = |a_pq| e^{i theta}, a phase diag(1, e^{-i theta}) makes the 2x2
 // block real, then the real Jacobi rotation (c, s) of zeta =
 // (a_qq - a_pp)/(2|a_pq|), t = sgn(zeta)/(|zeta| + sqrt(zeta^2 + 1)).
-// Sweeps stop when the off-diagonal Frobenius norm^2 <= 1e-34 * total.
-__global__ void __launch_bounds__(256) k_eigh(int n, const cd *H, long long sH, cd *U,
-                                              long long sU, double *w, long long sw)
+// Sweeps stop when the off-diagonal Frobenius norm^2 <= tol * total
+// (tol = 1e-34 in FP64; 1e-10 in FP32, where rounding keeps the ratio above
+// ~(n eps)^2).  With V0 given, the rotations accumulate onto V0 instead of the
+// identity (polishing A = V0^H F V0 for a unitary V0 yields F = U W U^H).
+template <class R>
+__global__ void __launch_bounds__(256) k_eigh(int n, const void *Hv, long long sH, void *Uv,
+                                              long long sU, void *wv, long long sw,
+                                              const void *V0v, long long sV0)
 {
-    extern __shared__ cd sm_e[];
-    cd *A = sm_e;
-    cd *V = sm_e + n * n;
-    __shared__ double rc[64], rs[64];
-    __shared__ cd rph[64];
+    typedef typename Cx<R>::T C;
+    extern __shared__ __align__(16) unsigned char sm_e_raw[];
+    C *A = (C *)sm_e_raw;
+    C *V = A + n * n;
+    __shared__ R rc[64], rs[64];
+    __shared__ C rph[64];
     __shared__ int rp[64], rq[64];
-    __shared__ double red[2][32];
+    __shared__ R red[2][32];
     __shared__ int done;
+    const R tol = sizeof(R) == 8 ? (R)1e-34 : (R)1e-10;
     const int b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
-    const cd *Hb = H + (long long)b * sH;
+    const C *Hb = (const C *)Hv + (long long)b * sH;
+    const C *V0 = V0v ? (const C *)V0v + (long long)b * sV0 : nullptr;
     for (int e = tid; e < n * n; e += nt) {
         A[e] = Hb[e];
-        V[e] = cmk((e / n) == (e % n) ? 1.0 : 0.0, 0.0);
+        V[e] = V0 ? V0[e] : cmkT<C>((e / n) == (e % n) ? 1.0 : 0.0, 0.0);
     }
     const int m = n + (n & 1), half = m / 2;
     __syncthreads();
     for (int sweep = 0; sweep < 60; ++sweep) {
-        // convergence test
-        double off = 0.0, tot = 0.0;
+        R off = 0, tot = 0;
         for (int e = tid; e < n * n; e += nt) {
-            double a2 = cabs2(A[e]);
+            R a2 = cabs2(A[e]);
             tot += a2;
             if (e / n != e % n) off += a2;
         }
@@ -164,12 +202,12 @@ __global__ void __launch_bounds__(256) k_eigh(int n, const cd *H, long long sH, 
         }
         __syncthreads();
         if (tid == 0) {
-            double so = 0, stt = 0;
+            R so = 0, stt = 0;
             for (int i = 0; i < (nt + 31) / 32; ++i) {
                 so += red[0][i];
                 stt += red[1][i];
             }
-            done = (so == 0.0 || so <= 1e-34 * stt);
+            done = (so == (R)0 || so <= tol * stt);
         }
         __syncthreads();
         if (done) break;
@@ -184,17 +222,17 @@ __global__ void __launch_bounds__(256) k_eigh(int n, const cd *H, long long sH, 
                     bb = (r - tid + (m - 1)) % (m - 1);
                 }
                 int p = a < bb ? a : bb, q = a < bb ? bb : a;
-                double c = 1.0, s = 0.0;
-                cd ph = cmk(1, 0);
+                R c = 1, s = 0;
+                C ph = cmkT<C>(1, 0);
                 if (q < n) {
-                    cd apq = A[p * n + q];
-                    double ab = sqrt(cabs2(apq));
-                    if (ab > 0.0) {
-                        double app = A[p * n + p].x, aqq = A[q * n + q].x;
-                        ph = cmk(apq.x / ab, apq.y / ab);
-                        double zeta = (aqq - app) / (2.0 * ab);
-                        double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(zeta * zeta + 1.0));
-                        c = 1.0 / sqrt(t * t + 1.0);
+                    C apq = A[p * n + q];
+                    R ab = sqrt(cabs2(apq));
+                    if (ab > (R)0) {
+                        R app = A[p * n + p].x, aqq = A[q * n + q].x;
+                        ph = cmkT<C>(apq.x / ab, apq.y / ab);
+                        R zeta = (aqq - app) / (2 * ab);
+                        R t = (zeta >= 0 ? (R)1 : (R)-1) / (fabs(zeta) + sqrt(zeta * zeta + (R)1));
+                        c = (R)1 / sqrt(t * t + (R)1);
                         s = t * c;
                     }
                 } else {
@@ -207,63 +245,74 @@ __global__ void __launch_bounds__(256) k_eigh(int n, const cd *H, long long sH, 
                 rph[tid] = ph;
             }
             __syncthreads();
-            // columns: A <- A J, V <- V J
             for (int t = tid; t < half * n; t += nt) {
                 int k = t / n, row = t % n;
                 int p = rp[k], q = rq[k];
-                if (p < 0 || rs[k] == 0.0) continue;
-                double c = rc[k], s = rs[k];
-                cd cph = cconj(rph[k]);
-                cd x = A[row * n + p], y = A[row * n + q];
-                cd sy = cmul(cph, y);
-                A[row * n + p] = cmk(c * x.x - s * sy.x, c * x.y - s * sy.y);
-                A[row * n + q] = cmk(s * x.x + c * sy.x, s * x.y + c * sy.y);
+                if (p < 0 || rs[k] == (R)0) continue;
+                R c = rc[k], s = rs[k];
+                C cph = cconj(rph[k]);
+                C x = A[row * n + p], y = A[row * n + q];
+                C sy = cmul(cph, y);
+                A[row * n + p] = cmkT<C>(c * x.x - s * sy.x, c * x.y - s * sy.y);
+                A[row * n + q] = cmkT<C>(s * x.x + c * sy.x, s * x.y + c * sy.y);
                 x = V[row * n + p];
                 y = V[row * n + q];
                 sy = cmul(cph, y);
-                V[row * n + p] = cmk(c * x.x - s * sy.x, c * x.y - s * sy.y);
-                V[row * n + q] = cmk(s * x.x + c * sy.x, s * x.y + c * sy.y);
+                V[row * n + p] = cmkT<C>(c * x.x - s * sy.x, c * x.y - s * sy.y);
+                V[row * n + q] = cmkT<C>(s * x.x + c * sy.x, s * x.y + c * sy.y);
             }
             __syncthreads();
-            // rows: A <- J^H A
             for (int t = tid; t < half * n; t += nt) {
                 int k = t / n, col = t % n;
                 int p = rp[k], q = rq[k];
-                if (p < 0 || rs[k] == 0.0) continue;
-                double c = rc[k], s = rs[k];
-                cd ph = rph[k];
-                cd x = A[p * n + col], y = A[q * n + col];
-                cd sy = cmul(ph, y);
-                A[p * n + col] = cmk(c * x.x - s * sy.x, c * x.y - s * sy.y);
-                A[q * n + col] = cmk(s * x.x + c * sy.x, s * x.y + c * sy.y);
+                if (p < 0 || rs[k] == (R)0) continue;
+                R c = rc[k], s = rs[k];
+                C ph = rph[k];
+                C x = A[p * n + col], y = A[q * n + col];
+                C sy = cmul(ph, y);
+                A[p * n + col] = cmkT<C>(c * x.x - s * sy.x, c * x.y - s * sy.y);
+                A[q * n + col] = cmkT<C>(s * x.x + c * sy.x, s * x.y + c * sy.y);
             }
             __syncthreads();
             if (tid < half) {
                 int p = rp[tid], q = rq[tid];
-                if (p >= 0 && rs[tid] != 0.0) {
-                    A[p * n + q] = cmk(0, 0);
-                    A[q * n + p] = cmk(0, 0);
+                if (p >= 0 && rs[tid] != (R)0) {
+                    A[p * n + q] = czero<C>();
+                    A[q * n + p] = czero<C>();
                 }
             }
             __syncthreads();
         }
     }
-    cd *Ub = U + (long long)b * sU;
+    C *Ub = (C *)Uv + (long long)b * sU;
     for (int e = tid; e < n * n; e += nt) Ub[e] = V[e];
-    for (int i = tid; i < n; i += nt) w[(long long)b * sw + i] = A[i * n + i].x;
+    R *wb = (R *)wv + (long long)b * sw;
+    for (int i = tid; i < n; i += nt) wb[i] = A[i * n + i].x;
 }
 
-int eigh_batched(cudaStream_t st, int n, const cd *H, long long sH, cd *U, long long sU, double *w,
-                 long long sw, int batch)
+int eigh_batched(cudaStream_t st, int prec, int n, const void *H, long long sH, void *U,
+                 long long sU, void *w, long long sw, int batch, const void *V0, long long sV0)
 {
     if (n > 64 || batch <= 0) return batch <= 0 ? 0 : -1;
-    size_t smem = 2ull * n * n * sizeof(cd);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_eigh, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * 16);
-        attr = true;
+    if (prec == TY_C64) {
+        size_t smem = 2ull * n * n * sizeof(cd);
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_eigh<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 2 * 64 * 64 * 16);
+            attr = true;
+        }
+        k_eigh<double><<<batch, 256, smem, st>>>(n, H, sH, U, sU, w, sw, V0, sV0);
+    } else {
+        size_t smem = 2ull * n * n * sizeof(cf);
+        static bool attr32 = false;
+        if (!attr32) {
+            cudaFuncSetAttribute(k_eigh<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 2 * 64 * 64 * 8);
+            attr32 = true;
+        }
+        k_eigh<float><<<batch, 256, smem, st>>>(n, H, sH, U, sU, w, sw, V0, sV0);
     }
-    k_eigh<<<batch, 256, smem, st>>>(n, H, sH, U, sU, w, sw);
     QMC_COUNT(1);
     return 0;
 }
@@ -271,7 +320,7 @@ int eigh_batched(cudaStream_t st, int n, const cd *H, long long sH, cd *U, long 
 // ------------------------------------------------------------------- LU ---
 // In-place LU with partial pivoting (first row of maximal |a_ik|), one block
 // per matrix in shared memory; piv[k] = row exchanged with row k at step k;
-// logdet = sum log U_kk + i pi (number of exchanges mod 2).
+// logdet = sum log U_kk + i pi (number of exchanges mod 2).  FP64 always.
 __global__ void __launch_bounds__(256) k_lu(int n, cd *A, long long sA, int *piv, long long spiv,
                                             cd *logdet)
 {
@@ -284,7 +333,6 @@ __global__ void __launch_bounds__(256) k_lu(int n, cd *A, long long sA, int *piv
     __syncthreads();
     int nsw = 0;
     for (int k = 0; k < n; ++k) {
-        // pivot search by warp 0
         if (tid < 32) {
             double best = -1.0;
             int bidx = k;
@@ -355,31 +403,34 @@ int lu_batched(cudaStream_t st, int n, cd *A, long long sA, int *piv, long long 
 }
 
 // ------------------------------------------------------------ right div ---
-// X = G M^-1 from the LU factors of M (P M = L U): for each row g of G solve
-// x M = g as z U = g (forward), y L = z (backward, unit L), x = y P.  One
-// warp per row; the LU factors are staged in shared memory per block.
+// X = G M^-1 from the FP64 LU factors of M (P M = L U): for each row g of G
+// solve x M = g as z U = g (forward), y L = z (backward, unit L), x = y P.
+// One warp per row; the factors are staged in shared memory in the compute
+// type R (FP32 in the mixed-precision path).  G and X are FP64.
 #define RD_ROWS 8
+template <class R>
 __global__ void __launch_bounds__(RD_ROWS * 32) k_rdiv(int n, const cd *G, long long sG,
                                                        const cd *LU, long long sLU,
                                                        const int *piv, long long spiv, cd *X,
                                                        long long sX)
 {
-    extern __shared__ cd sm_r[];
-    cd *F = sm_r;
-    cd *zbuf = sm_r + n * n;
+    typedef typename Cx<R>::T C;
+    extern __shared__ __align__(16) unsigned char sm_r_raw[];
+    C *F = (C *)sm_r_raw;
+    C *zbuf = F + n * n;
     const int b = blockIdx.y, tid = threadIdx.x;
     const cd *LUb = LU + (long long)b * sLU;
-    for (int e = tid; e < n * n; e += blockDim.x) F[e] = LUb[e];
+    for (int e = tid; e < n * n; e += blockDim.x) F[e] = cvt<C>(LUb[e]);
     __syncthreads();
     const int warp = tid >> 5, lane = tid & 31;
     const int r = blockIdx.x * RD_ROWS + warp;
     if (r >= n) return;
-    cd *z = zbuf + warp * n;
+    C *z = zbuf + warp * n;
     const cd *g = G + (long long)b * sG + (long long)r * n;
-    for (int j = lane; j < n; j += 32) z[j] = g[j];
+    for (int j = lane; j < n; j += 32) z[j] = cvt<C>(g[j]);
     __syncwarp();
     for (int j = 0; j < n; ++j) {
-        cd s = cmk(0, 0);
+        C s = czero<C>();
         for (int i = lane; i < j; i += 32) cfma(s, z[i], F[i * n + j]);
         for (int o = 16; o > 0; o >>= 1) {
             s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
@@ -389,7 +440,7 @@ __global__ void __launch_bounds__(RD_ROWS * 32) k_rdiv(int n, const cd *G, long 
         __syncwarp();
     }
     for (int j = n - 1; j >= 0; --j) {
-        cd s = cmk(0, 0);
+        C s = czero<C>();
         for (int i = j + 1 + lane; i < n; i += 32) cfma(s, z[i], F[i * n + j]);
         for (int o = 16; o > 0; o >>= 1) {
             s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
@@ -403,7 +454,7 @@ __global__ void __launch_bounds__(RD_ROWS * 32) k_rdiv(int n, const cd *G, long 
         for (int k = n - 1; k >= 0; --k) {
             int p = pv[k];
             if (p != k) {
-                cd t = z[k];
+                C t = z[k];
                 z[k] = z[p];
                 z[p] = t;
             }
@@ -411,21 +462,34 @@ __global__ void __launch_bounds__(RD_ROWS * 32) k_rdiv(int n, const cd *G, long 
     }
     __syncwarp();
     cd *x = X + (long long)b * sX + (long long)r * n;
-    for (int j = lane; j < n; j += 32) x[j] = z[j];
+    for (int j = lane; j < n; j += 32) x[j] = cvt<cd>(z[j]);
 }
 
-int rdiv_batched(cudaStream_t st, int n, const cd *G, long long sG, const cd *LU, long long sLU,
-                 const int *piv, long long spiv, cd *X, long long sX, int batch)
+int rdiv_batched(cudaStream_t st, int prec, int n, const cd *G, long long sG, const cd *LU,
+                 long long sLU, const int *piv, long long spiv, cd *X, long long sX, int batch)
 {
-    size_t smem = ((size_t)n * n + (size_t)RD_ROWS * n) * sizeof(cd);
-    if (smem > 220 * 1024) return -1;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_rdiv, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        attr = true;
-    }
     dim3 grid(cdiv_up(n, RD_ROWS), batch);
-    k_rdiv<<<grid, RD_ROWS * 32, smem, st>>>(n, G, sG, LU, sLU, piv, spiv, X, sX);
+    if (prec == TY_C64) {
+        size_t smem = ((size_t)n * n + (size_t)RD_ROWS * n) * sizeof(cd);
+        if (smem > 220 * 1024) return -1;
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_rdiv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 220 * 1024);
+            attr = true;
+        }
+        k_rdiv<double><<<grid, RD_ROWS * 32, smem, st>>>(n, G, sG, LU, sLU, piv, spiv, X, sX);
+    } else {
+        size_t smem = ((size_t)n * n + (size_t)RD_ROWS * n) * sizeof(cf);
+        if (smem > 220 * 1024) return -1;
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_rdiv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 220 * 1024);
+            attr = true;
+        }
+        k_rdiv<float><<<grid, RD_ROWS * 32, smem, st>>>(n, G, sG, LU, sLU, piv, spiv, X, sX);
+    }
     QMC_COUNT(1);
     return 0;
 }
@@ -434,7 +498,7 @@ int rdiv_batched(cudaStream_t st, int n, const cd *G, long long sG, const cd *LU
 // X = Q D V by Householder QR with column pivoting, X P = Q R, D = |diag R|,
 // V = D^-1 R P^T.  One block per matrix; the working matrix lives in shared
 // memory, Q is accumulated in global memory (Q <- Q H_k).  Pivot: the first
-// column of largest remaining 2-norm.
+// column of largest remaining 2-norm.  FP64 always.
 __global__ void __launch_bounds__(256) k_qrp(int n, const cd *X, long long sX, cd *Q, long long sQ,
                                              double *D, long long sD, cd *V, long long sV)
 {
@@ -474,9 +538,6 @@ __global__ void __launch_bounds__(256) k_qrp(int n, const cd *X, long long sX, c
                 int t = perm[k];
                 perm[k] = perm[best];
                 perm[best] = t;
-                double tc = cn[k];
-                cn[k] = cn[best];
-                cn[best] = tc;
             }
         }
         __syncthreads();

@@ -1,61 +1,78 @@
-// linalg.cuh -- batched dense complex FP64 kernels of libqmc (see linalg.cu)
+// linalg.cuh -- batched dense complex kernels of libqmc (see linalg.cu)
 #pragma once
 #include "qmc_internal.cuh"
 
 struct GemmP {
     int M, N, K;
-    const cd *A;
+    const void *A;
     int lda;
     long long sA;
     int opA;
-    const cd *B;
+    const void *B;
     int ldb;
     long long sB;
     int opB;
-    const cd *d;  // optional diagonal of length K between op(A) and op(B)
+    const void *d;  // optional diagonal of length K (compute type) between op(A) and op(B)
     long long sd;
-    cd *C;
+    void *C;
     int ldc;
     long long sC;
     cd alpha, beta;
     int addI;
+    int ta, tb, tc;  // operand / output element types (TY_C64, TY_C32)
+    int rc;          // compute type (TY_C64 = FP64, TY_C32 = FP32)
 };
 
-void zgemm(cudaStream_t st, const GemmP &p, int batch);
+int zgemm(cudaStream_t st, const GemmP &p, int batch);
 void gemm_prof_start();
 void gemm_prof_stop(double *ms, long long *launches, double *flops);
-int eigh_batched(cudaStream_t st, int n, const cd *H, long long sH, cd *U, long long sU, double *w,
-                 long long sw, int batch);
+int eigh_batched(cudaStream_t st, int prec, int n, const void *H, long long sH, void *U,
+                 long long sU, void *w, long long sw, int batch, const void *V0 = nullptr,
+                 long long sV0 = 0);
 int lu_batched(cudaStream_t st, int n, cd *A, long long sA, int *piv, long long spiv, cd *logdet,
                int batch);
-int rdiv_batched(cudaStream_t st, int n, const cd *G, long long sG, const cd *LU, long long sLU,
-                 const int *piv, long long spiv, cd *X, long long sX, int batch);
+int rdiv_batched(cudaStream_t st, int prec, int n, const cd *G, long long sG, const cd *LU,
+                 long long sLU, const int *piv, long long spiv, cd *X, long long sX, int batch);
 int qrp_batched(cudaStream_t st, int n, const cd *X, long long sX, cd *Q, long long sQ, double *D,
                 long long sD, cd *V, long long sV, int batch);
 
-// square n x n GEMM helper: C = alpha op(A) diag(d) op(B) + beta C (+ I)
-inline void zgemm_sq(cudaStream_t st, int n, int batch, const cd *A, long long sA, int opA,
-                     const cd *B, long long sB, int opB, cd *C, long long sC,
-                     const cd *d = nullptr, long long sd = 0, cd alpha = cd{1, 0},
-                     cd beta = cd{0, 0}, int addI = 0)
+// typed operand: pointer, batch stride (elements), element type
+struct Op {
+    const void *p;
+    long long s;
+    int t;
+};
+inline Op op64(const cd *p, long long s) { return Op{p, s, TY_C64}; }
+inline Op op32(const cf *p, long long s) { return Op{p, s, TY_C32}; }
+inline Op opT(const void *p, long long s, int t) { return Op{p, s, t}; }
+
+// square n x n GEMM: C = alpha op(A) diag(d) op(B) + beta C (+ I), computed in
+// precision rc
+inline int gemm_sq(cudaStream_t st, int n, int batch, int rc, Op A, int opA, Op B, int opB, Op C,
+                   const void *d = nullptr, long long sd = 0, cd alpha = cd{1, 0},
+                   cd beta = cd{0, 0}, int addI = 0)
 {
     GemmP p;
     p.M = p.N = p.K = n;
-    p.A = A;
+    p.A = A.p;
     p.lda = n;
-    p.sA = sA;
+    p.sA = A.s;
     p.opA = opA;
-    p.B = B;
+    p.B = B.p;
     p.ldb = n;
-    p.sB = sB;
+    p.sB = B.s;
     p.opB = opB;
     p.d = d;
     p.sd = sd;
-    p.C = C;
+    p.C = (void *)C.p;
     p.ldc = n;
-    p.sC = sC;
+    p.sC = C.s;
     p.alpha = alpha;
     p.beta = beta;
     p.addI = addI;
-    zgemm(st, p, batch);
+    p.ta = A.t;
+    p.tb = B.t;
+    p.tc = C.t;
+    p.rc = rc;
+    return zgemm(st, p, batch);
 }

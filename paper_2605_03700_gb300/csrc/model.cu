@@ -1,7 +1,10 @@
-// model.cu -- CF-DQMC model kernels of libqmc (FP64): LLL form factors,
-// slice-field assembly, eigenbasis factors of the symmetric Trotter slice,
-// the exact action gradient, the MALA proposal / Metropolis-Hastings test,
-// restabilisation helpers and the Wick measurements.
+// model.cu -- CF-DQMC model kernels of libqmc: LLL form factors, slice-field
+// assembly, eigenbasis factors of the symmetric Trotter slice, the exact
+// action gradient, the MALA proposal / Metropolis-Hastings test, commit,
+// restabilisation helpers and the Wick measurements.  The factor and
+// gradient kernels are templated on the compute type (FP64, or FP32 in the
+// mixed-precision path); fields, the MH test, stabilisation and measurements
+// are FP64.
 #include "model.cuh"
 
 // ------------------------------------------------------- form factors ----
@@ -59,11 +62,14 @@ QMC_DEVFN cd zfield(const double *ph, int kind, int a, int b)
 }
 
 // F^(i) = sum_q z^i_q F_q for the four channels (Methods, Eq. hs_transform),
-// by gathering over the q that land on each entry (fixed q order)
-__global__ void k_assemble(int nb, int n, int nq, const double *phi, long long phi_cs,
-                           const int *fkind, const int *frA, const int *frB, const int *aptr,
-                           const int *aq, const cd *val, cd *F)
+// gathered over the q that land on each entry (fixed q order); accumulated
+// in FP64, stored in the compute type
+template <class R>
+__global__ void k_assemble(int n, int nq, const double *phi, long long phi_cs, const int *fkind,
+                           const int *frA, const int *frB, const int *aptr, const int *aq,
+                           const cd *val, void *Fv)
 {
+    typedef typename Cx<R>::T C;
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     int i = blockIdx.y, c = blockIdx.z;
     if (e >= n * n) return;
@@ -74,82 +80,96 @@ __global__ void k_assemble(int nb, int n, int nq, const double *phi, long long p
         int q = aq[t];
         cfma(s, zfield(ph, fkind[q], frA[q], frB[q]), val[q * n + k]);
     }
-    F[((long long)c * 4 + i) * n * n + e] = s;
+    ((C *)Fv)[((long long)c * 4 + i) * n * n + e] = cvt<C>(s);
 }
 
 // V_i = R_i (x) U_i, the eigenvectors of O^i (x) F^(i)
-__global__ void k_build_V(int nb, int n, const cd *U, long long U_cs, cd *V)
+template <class R>
+__global__ void k_build_V(int n, const void *Uv, long long U_cs, void *Vv)
 {
+    typedef typename Cx<R>::T C;
     int N = 2 * n;
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     int i = blockIdx.y, c = blockIdx.z;
     if (e >= N * N) return;
     int r = e / N, cc = e % N;
     int v = r / n, k = r % n, w = cc / n, kp = cc % n;
-    cd u = U[(long long)c * U_cs + (long long)i * n * n + k * n + kp];
-    V[((long long)c * 4 + i) * N * N + e] = cmul(valley_R(i, v, w), u);
+    C u = ((const C *)Uv)[(long long)c * U_cs + (long long)i * n * n + k * n + kp];
+    ((C *)Vv)[((long long)c * 4 + i) * N * N + e] = cmul(cvt<C>(valley_R(i, v, w)), u);
 }
 
 // lambda_j(x) = c_j alpha_i o_i(v) w_i(k) for the seven factors, and
-// D_j = e^{lambda_j}, Dinv_j = e^{-lambda_j}
-__global__ void k_lambda(int nb, int n, const double *w, long long w_cs, const cd *alpha, cd *lam,
-                         cd *Dg, cd *Dgi)
+// D_j = e^{lambda_j}, Dinv_j = e^{-lambda_j} (eigenvalues w in FP64, outputs
+// in the compute type)
+template <class R>
+__global__ void k_lambda(int n, const void *wv, long long w_cs, const cd *alpha, void *lamv,
+                         void *Dgv, void *Dgiv)
 {
+    typedef typename Cx<R>::T C;
     int N = 2 * n;
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y, c = blockIdx.z;
     if (x >= N) return;
     int i = trotter_channel(j);
     int v = x / n, k = x % n;
-    double mu = valley_o(i, v) * w[(long long)c * w_cs + i * n + k];
+    double mu = valley_o(i, v) * ((const double *)wv)[(long long)c * w_cs + i * n + k];
     cd a = cscale(alpha[c * 4 + i], trotter_coef(j) * mu);
     long long o = ((long long)c * 7 + j) * N + x;
-    lam[o] = a;
-    Dg[o] = cexp_d(a);
-    Dgi[o] = cexp_d(cmk(-a.x, -a.y));
+    ((C *)lamv)[o] = cvt<C>(a);
+    ((C *)Dgv)[o] = cvt<C>(cexp_d(a));
+    ((C *)Dgiv)[o] = cvt<C>(cexp_d(cmk(-a.x, -a.y)));
 }
 
 // (e^x - 1)/x
-QMC_DEVFN cd phi1(cd x)
+template <class C> QMC_DEVFN C phi1(C x)
 {
-    if (x.x * x.x + x.y * x.y < 0.01) {
-        cd s = cmk(0, 0), t = cmk(1, 0);
-        for (int k = 1; k <= 16; ++k) {
+    typedef decltype(x.x) Rr;
+    if (x.x * x.x + x.y * x.y < (Rr)0.01) {
+        C s = czero<C>(), t = cmkT<C>(1, 0);
+        const int nt = sizeof(x.x) == 8 ? 16 : 8;
+        for (int k = 1; k <= nt; ++k) {
             s = cadd(s, t);
-            t = cscale(cmul(t, x), 1.0 / (double)(k + 1));
+            t = cmul(t, cmkT<C>(1.0 / (double)(k + 1), 0.0));
+            t = cmul(t, x);
         }
         return s;
     }
-    cd e = cexp_d(x);
-    return cdiv(cmk(e.x - 1.0, e.y), x);
+    C e = cexp_d(x);
+    e.x -= 1;
+    return cdiv(e, x);
 }
 
 // C_i (+)= a_j * (Ah o Phi_j), Phi_j[m][k] = phi1(lambda_j[k] - lambda_j[m]):
 // the Daleckii-Krein form of int_0^1 e^{-sX} A e^{sX} ds in the eigenbasis
-__global__ void k_accum(int nb, int N, int j, int first, const cd *alpha, const cd *lam,
-                        const cd *Ah, cd *Cacc)
+template <class R>
+__global__ void k_accum(int N, int j, int first, const cd *alpha, const void *lamv,
+                        const void *Ahv, void *Caccv)
 {
+    typedef typename Cx<R>::T C;
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     int c = blockIdx.y;
     if (e >= N * N) return;
     int i = trotter_channel(j);
     int m = e / N, k = e % N;
-    const cd *lj = lam + ((long long)c * 7 + j) * N;
-    cd a = cscale(alpha[c * 4 + i], trotter_coef(j));
-    cd v = cmul(a, cmul(Ah[(long long)c * N * N + e], phi1(csub(lj[k], lj[m]))));
-    cd *dst = Cacc + ((long long)c * 4 + i) * N * N + e;
+    const C *lj = (const C *)lamv + ((long long)c * 7 + j) * N;
+    C a = cvt<C>(cscale(alpha[c * 4 + i], trotter_coef(j)));
+    C v = cmul(a, cmul(((const C *)Ahv)[(long long)c * N * N + e], phi1(csub(lj[k], lj[m]))));
+    C *dst = (C *)Caccv + ((long long)c * 4 + i) * N * N + e;
     *dst = first ? v : cadd(*dst, v);
 }
 
 // t^(i)_q = Tr[(O^i (x) F_q) Atilde^(i)] - delta_{i0} alpha_0 Tr F_q
-__global__ void k_trace_t(int nb, int n, int nq, const cd *At, const cd *val, const int *col,
+// (accumulated in FP64)
+template <class R>
+__global__ void k_trace_t(int n, int nq, const void *Atv, const cd *val, const int *col,
                           const cd *trF, const cd *alpha, cd *t)
 {
+    typedef typename Cx<R>::T C;
     int q = blockIdx.x * blockDim.x + threadIdx.x;
     int i = blockIdx.y, c = blockIdx.z;
     if (q >= nq) return;
     int N = 2 * n;
-    const cd *A = At + ((long long)c * 4 + i) * N * N;
+    const C *A = (const C *)Atv + ((long long)c * 4 + i) * N * N;
     cd s = cmk(0, 0);
     for (int v = 0; v < 2; ++v) {
         int w = (i == 1 || i == 2) ? 1 - v : v;
@@ -157,7 +177,7 @@ __global__ void k_trace_t(int nb, int n, int nq, const cd *At, const cd *val, co
         for (int k = 0; k < n; ++k) {
             int cc = col[q * n + k];
             if (cc < 0) continue;
-            cfma(s, cmul(o, val[q * n + k]), A[(w * n + cc) * N + (v * n + k)]);
+            cfma(s, cmul(o, val[q * n + k]), cvt<cd>(A[(w * n + cc) * N + (v * n + k)]));
         }
     }
     if (i == 0) s = csub(s, cmul(alpha[c * 4], trF[q]));
@@ -165,7 +185,7 @@ __global__ void k_trace_t(int nb, int n, int nq, const cd *At, const cd *val, co
 }
 
 // grad_phi S = phi - 2 Re d ln(bracket)/d phi for every real field
-__global__ void k_grad(int nb, int nq, const int *fq, const int *fk, const int *partner,
+__global__ void k_grad(int nq, const int *fq, const int *fk, const int *partner,
                        const double *phi, long long phi_cs, const cd *t, double *grad)
 {
     int f = blockIdx.x * blockDim.x + threadIdx.x;
@@ -183,7 +203,7 @@ __global__ void k_grad(int nb, int nq, const int *fq, const int *fk, const int *
 
 // phi' = phi - (eps^2/2) grad + eps xi (Methods, Eq. langevin_proposal with
 // the drift along -grad S)
-__global__ void k_propose(int nb, int nf, const double *phi, long long phi_cs, const double *grad,
+__global__ void k_propose(int nf, const double *phi, long long phi_cs, const double *grad,
                           const double *eps, const uint32_t *keys, uint32_t slice, uint32_t sweep,
                           double *phip)
 {
@@ -197,14 +217,22 @@ __global__ void k_propose(int nb, int nf, const double *phi, long long phi_cs, c
 }
 
 // Y = a X + b I
-__global__ void k_axpyI(int nb, int N, const cd *X, long long sX, cd a, cd b, cd *Y, long long sY)
+template <class TX, class TY>
+__global__ void k_axpyI(int N, const void *Xv, long long sX, cd a, cd b, void *Yv, long long sY)
 {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     int c = blockIdx.y;
     if (e >= N * N) return;
-    cd v = cmul(a, X[(long long)c * sX + e]);
+    cd v = cmul(a, cvt<cd>(((const TX *)Xv)[(long long)c * sX + e]));
     if (e / N == e % N) v = cadd(v, b);
-    Y[(long long)c * sY + e] = v;
+    ((TY *)Yv)[(long long)c * sY + e] = cvt<TY>(v);
+}
+
+// w64 = (double) w32
+__global__ void k_cvt_real(long long n, const float *a, double *b)
+{
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) b[e] = a[e];
 }
 
 // ------------------------------------------------------- reductions ------
@@ -300,28 +328,24 @@ __global__ void __launch_bounds__(256) k_accept(AcceptP p)
     }
 }
 
-// accepted proposals replace the slice's fields, propagators, eigenpairs and G
+// accepted proposals replace the slice's fields, propagators, eigenpairs and
+// G: up to eight byte ranges per chain, copied in 4-byte words
 __global__ void k_commit(CommitP p)
 {
     const int c = blockIdx.y;
     if (!p.flag[c]) return;
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long NN = (long long)p.N * p.N, n2 = (long long)p.n * p.n;
-    const long long cs = (long long)c * p.L + p.s;  // (chain, slice)
-    if (e < NN) {
-        p.B[cs * NN + e] = p.Bp[c * NN + e];
-        p.Binv[cs * NN + e] = p.Bpi[c * NN + e];
-        p.G[c * NN + e] = p.Gp[c * NN + e];
+    for (int k = 0; k < p.nseg; ++k) {
+        const CommitSeg &g = p.seg[k];
+        if (e < g.words)
+            ((uint32_t *)g.dst)[c * g.dst_cs + e] = ((const uint32_t *)g.src)[c * g.src_cs + e];
     }
-    if (e < 4 * n2) p.U[cs * 4 * n2 + e] = p.Up[c * 4 * n2 + e];
-    if (e < 4 * p.n) p.W[cs * 4 * p.n + e] = p.Wp[c * 4 * p.n + e];
-    if (e < p.nf) p.phi[cs * p.nf + e] = p.phip[(long long)c * p.nf + e];
 }
 
 // -------------------------------------------------------- stabilisation --
 // Y = X diag(d) (d real)
-__global__ void k_scale_cols(int nb, int N, const cd *X, long long sX, const double *d,
-                             long long sd, cd *Y, long long sY)
+__global__ void k_scale_cols(int N, const cd *X, long long sX, const double *d, long long sd,
+                             cd *Y, long long sY)
 {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     int c = blockIdx.y;
@@ -330,8 +354,8 @@ __global__ void k_scale_cols(int nb, int N, const cd *X, long long sX, const dou
 }
 
 // X = DbR^-1 T1 DbL^-1 + DsR T2 DsL with Db = max(D,1), Ds = min(D,1)
-__global__ void k_stab_mix(int nb, int N, const cd *T1, const cd *T2, const double *DR,
-                           long long sDR, const double *DL, long long sDL, cd *X)
+__global__ void k_stab_mix(int N, const cd *T1, const cd *T2, const double *DR, long long sDR,
+                           const double *DL, long long sDL, cd *X)
 {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     int c = blockIdx.y;
@@ -346,9 +370,8 @@ __global__ void k_stab_mix(int nb, int N, const cd *T1, const cd *T2, const doub
     X[o] = cadd(a, b);
 }
 
-// the diagonals 1/max(D,1) as complex vectors (GEMM scaling) and the
-// column scaling of QL by 1/max(DL,1)
-__global__ void k_inv_big(int nb, int N, const double *D, long long sD, cd *out)
+// 1/max(D,1) as a complex vector (GEMM diagonal)
+__global__ void k_inv_big(int N, const double *D, long long sD, cd *out)
 {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int c = blockIdx.y;
@@ -411,7 +434,6 @@ __global__ void __launch_bounds__(256) k_meas_ax(int n, int nq, const cd *G, con
     const cd *Gc = G + (long long)c * N * N;
     const int qb = partner[q];
     double ar = 0, ai = 0, xr = 0, xi = 0;
-    // a
     for (int x = tid; x < N; x += blockDim.x) {
         int v = x / n, k = x % n;
         int w = (i == 1 || i == 2) ? 1 - v : v;
@@ -425,7 +447,6 @@ __global__ void __launch_bounds__(256) k_meas_ax(int n, int nq, const cd *G, con
         ar += t.x;
         ai += t.y;
     }
-    // x: sum over rows x and y' of M_q[x,px] G[px,y'] M_qb[y',py] (1-G)[py,x]
     for (int t = tid; t < N * N; t += blockDim.x) {
         int x = t / N, y = t % N;
         int v = x / n, k = x % n;
@@ -552,53 +573,73 @@ void launch_init_phi(cudaStream_t s, int nb, int L, int nf, const uint32_t *keys
     k_init_phi<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(nb, L, nf, keys, phi);
     QMC_COUNT(1);
 }
-void launch_assemble(cudaStream_t s, int nb, int n, int nq, const double *phi, long long phi_cs,
-                     const int *fkind, const int *frA, const int *frB, const int *aptr,
-                     const int *aq, const cd *val, cd *F)
+void launch_assemble(cudaStream_t s, int prec, int nb, int n, int nq, const double *phi,
+                     long long phi_cs, const int *fkind, const int *frA, const int *frB,
+                     const int *aptr, const int *aq, const cd *val, void *F)
 {
-    k_assemble<<<dim3(cdiv_up(n * n, 128), 4, nb), 128, 0, s>>>(nb, n, nq, phi, phi_cs, fkind, frA,
-                                                                frB, aptr, aq, val, F);
+    dim3 g(cdiv_up(n * n, 128), 4, nb);
+    if (prec == TY_C64)
+        k_assemble<double><<<g, 128, 0, s>>>(n, nq, phi, phi_cs, fkind, frA, frB, aptr, aq, val, F);
+    else
+        k_assemble<float><<<g, 128, 0, s>>>(n, nq, phi, phi_cs, fkind, frA, frB, aptr, aq, val, F);
     QMC_COUNT(1);
 }
-void launch_build_V(cudaStream_t s, int nb, int n, const cd *U, long long U_cs, cd *V)
+void launch_build_V(cudaStream_t s, int prec, int nb, int n, const void *U, long long U_cs, void *V)
 {
     int N = 2 * n;
-    k_build_V<<<dim3(cdiv_up(N * N, 256), 4, nb), 256, 0, s>>>(nb, n, U, U_cs, V);
-}
-void launch_lambda(cudaStream_t s, int nb, int n, const double *w, long long w_cs,
-                   const cd *alpha, cd *lam, cd *Dg, cd *Dgi)
-{
-    k_lambda<<<dim3(cdiv_up(2 * n, 128), 7, nb), 128, 0, s>>>(nb, n, w, w_cs, alpha, lam, Dg, Dgi);
+    dim3 g(cdiv_up(N * N, 256), 4, nb);
+    if (prec == TY_C64) k_build_V<double><<<g, 256, 0, s>>>(n, U, U_cs, V);
+    else k_build_V<float><<<g, 256, 0, s>>>(n, U, U_cs, V);
     QMC_COUNT(1);
 }
-void launch_accum(cudaStream_t s, int nb, int N, int j, int first, const cd *alpha,
-                  const cd *lam, const cd *Ah, cd *Cacc)
+void launch_lambda(cudaStream_t s, int prec, int nb, int n, const void *w, long long w_cs,
+                   const cd *alpha, void *lam, void *Dg, void *Dgi)
 {
-    k_accum<<<dim3(cdiv_up(N * N, 256), nb), 256, 0, s>>>(nb, N, j, first, alpha, lam, Ah, Cacc);
+    dim3 g(cdiv_up(2 * n, 128), 7, nb);
+    if (prec == TY_C64) k_lambda<double><<<g, 128, 0, s>>>(n, w, w_cs, alpha, lam, Dg, Dgi);
+    else k_lambda<float><<<g, 128, 0, s>>>(n, w, w_cs, alpha, lam, Dg, Dgi);
     QMC_COUNT(1);
 }
-void launch_trace_grad(cudaStream_t s, int nb, int n, int nq, const cd *At, const cd *val,
-                       const int *col, const cd *trF, const cd *alpha, cd *t, const int *fq,
-                       const int *fk, const int *partner, const double *phi, long long phi_cs,
-                       double *grad)
+void launch_accum(cudaStream_t s, int prec, int nb, int N, int j, int first, const cd *alpha,
+                  const void *lam, const void *Ah, void *Cacc)
 {
-    k_trace_t<<<dim3(cdiv_up(nq, 64), 4, nb), 64, 0, s>>>(nb, n, nq, At, val, col, trF, alpha, t);
-    k_grad<<<dim3(cdiv_up(4 * nq, 128), nb), 128, 0, s>>>(nb, nq, fq, fk, partner, phi, phi_cs, t,
-                                                           grad);
+    dim3 g(cdiv_up(N * N, 256), nb);
+    if (prec == TY_C64) k_accum<double><<<g, 256, 0, s>>>(N, j, first, alpha, lam, Ah, Cacc);
+    else k_accum<float><<<g, 256, 0, s>>>(N, j, first, alpha, lam, Ah, Cacc);
+    QMC_COUNT(1);
+}
+void launch_trace_grad(cudaStream_t s, int prec, int nb, int n, int nq, const void *At,
+                       const cd *val, const int *col, const cd *trF, const cd *alpha, cd *t,
+                       const int *fq, const int *fk, const int *partner, const double *phi,
+                       long long phi_cs, double *grad)
+{
+    dim3 g(cdiv_up(nq, 64), 4, nb);
+    if (prec == TY_C64) k_trace_t<double><<<g, 64, 0, s>>>(n, nq, At, val, col, trF, alpha, t);
+    else k_trace_t<float><<<g, 64, 0, s>>>(n, nq, At, val, col, trF, alpha, t);
+    k_grad<<<dim3(cdiv_up(4 * nq, 128), nb), 128, 0, s>>>(nq, fq, fk, partner, phi, phi_cs, t, grad);
     QMC_COUNT(2);
 }
 void launch_propose(cudaStream_t s, int nb, int nf, const double *phi, long long phi_cs,
                     const double *grad, const double *eps, const uint32_t *keys, uint32_t slice,
                     uint32_t sweep, double *phip)
 {
-    k_propose<<<dim3(cdiv_up(nf, 128), nb), 128, 0, s>>>(nb, nf, phi, phi_cs, grad, eps, keys, slice,
+    k_propose<<<dim3(cdiv_up(nf, 128), nb), 128, 0, s>>>(nf, phi, phi_cs, grad, eps, keys, slice,
                                                           sweep, phip);
     QMC_COUNT(1);
 }
-void launch_axpyI(cudaStream_t s, int nb, int N, const cd *X, long long sX, cd a, cd b, cd *Y,
-                  long long sY)
+void launch_axpyI(cudaStream_t s, int nb, int N, Op X, cd a, cd b, Op Y)
 {
-    k_axpyI<<<dim3(cdiv_up(N * N, 256), nb), 256, 0, s>>>(nb, N, X, sX, a, b, Y, sY);
+    dim3 g(cdiv_up(N * N, 256), nb);
+    if (X.t == TY_C64 && Y.t == TY_C64) k_axpyI<cd, cd><<<g, 256, 0, s>>>(N, X.p, X.s, a, b, (void *)Y.p, Y.s);
+    else if (X.t == TY_C64) k_axpyI<cd, cf><<<g, 256, 0, s>>>(N, X.p, X.s, a, b, (void *)Y.p, Y.s);
+    else if (Y.t == TY_C64) k_axpyI<cf, cd><<<g, 256, 0, s>>>(N, X.p, X.s, a, b, (void *)Y.p, Y.s);
+    else k_axpyI<cf, cf><<<g, 256, 0, s>>>(N, X.p, X.s, a, b, (void *)Y.p, Y.s);
+    QMC_COUNT(1);
+}
+void launch_cvt_real(cudaStream_t s, long long n, const float *a, double *b)
+{
+    k_cvt_real<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, a, b);
+    QMC_COUNT(1);
 }
 void launch_accept(cudaStream_t s, int nb, const AcceptP &p)
 {
@@ -607,26 +648,27 @@ void launch_accept(cudaStream_t s, int nb, const AcceptP &p)
 }
 void launch_commit(cudaStream_t s, int nb, const CommitP &p)
 {
-    long long mx = (long long)p.N * p.N;
-    if (p.nf > mx) mx = p.nf;
+    long long mx = 1;
+    for (int k = 0; k < p.nseg; ++k)
+        if (p.seg[k].words > mx) mx = p.seg[k].words;
     k_commit<<<dim3((unsigned)((mx + 255) / 256), nb), 256, 0, s>>>(p);
     QMC_COUNT(1);
 }
 void launch_scale_cols(cudaStream_t s, int nb, int N, const cd *X, long long sX, const double *d,
                        long long sd, cd *Y, long long sY)
 {
-    k_scale_cols<<<dim3(cdiv_up(N * N, 256), nb), 256, 0, s>>>(nb, N, X, sX, d, sd, Y, sY);
+    k_scale_cols<<<dim3(cdiv_up(N * N, 256), nb), 256, 0, s>>>(N, X, sX, d, sd, Y, sY);
     QMC_COUNT(1);
 }
 void launch_stab_mix(cudaStream_t s, int nb, int N, const cd *T1, const cd *T2, const double *DR,
                      long long sDR, const double *DL, long long sDL, cd *X)
 {
-    k_stab_mix<<<dim3(cdiv_up(N * N, 256), nb), 256, 0, s>>>(nb, N, T1, T2, DR, sDR, DL, sDL, X);
+    k_stab_mix<<<dim3(cdiv_up(N * N, 256), nb), 256, 0, s>>>(N, T1, T2, DR, sDR, DL, sDL, X);
     QMC_COUNT(1);
 }
 void launch_inv_big(cudaStream_t s, int nb, int N, const double *D, long long sD, cd *out)
 {
-    k_inv_big<<<dim3(cdiv_up(N, 128), nb), 128, 0, s>>>(nb, N, D, sD, out);
+    k_inv_big<<<dim3(cdiv_up(N, 128), nb), 128, 0, s>>>(N, D, sD, out);
     QMC_COUNT(1);
 }
 void launch_stab_err(cudaStream_t s, int nb, int N, cd *G, const cd *Gs, double *st, int *errf,

@@ -1,6 +1,6 @@
 // model.cuh -- CF-DQMC model kernels of libqmc (see model.cu)
 #pragma once
-#include "qmc_internal.cuh"
+#include "linalg.cuh"
 
 struct AcceptP {
     int nq;
@@ -21,13 +21,16 @@ struct AcceptP {
     long long *trace_n;
 };
 
+// one byte range copied per chain on accept (sizes in 4-byte words)
+struct CommitSeg {
+    void *dst;
+    const void *src;
+    long long words, dst_cs, src_cs;
+};
 struct CommitP {
-    int N, n, nf, L, s;  // s: 0-based slice
     const int *flag;
-    cd *B, *Binv, *G, *U;
-    double *W, *phi;
-    const cd *Bp, *Bpi, *Gp, *Up;
-    const double *Wp, *phip;
+    int nseg;
+    CommitSeg seg[8];
 };
 
 struct MeasP {
@@ -46,23 +49,23 @@ struct MeasP {
 
 void launch_ff_torus(cudaStream_t s, int n, int nq, const int *qxy, cd *val, int *col, cd *trF);
 void launch_init_phi(cudaStream_t s, int nb, int L, int nf, const uint32_t *keys, double *phi);
-void launch_assemble(cudaStream_t s, int nb, int n, int nq, const double *phi, long long phi_cs,
-                     const int *fkind, const int *frA, const int *frB, const int *aptr,
-                     const int *aq, const cd *val, cd *F);
-void launch_build_V(cudaStream_t s, int nb, int n, const cd *U, long long U_cs, cd *V);
-void launch_lambda(cudaStream_t s, int nb, int n, const double *w, long long w_cs,
-                   const cd *alpha, cd *lam, cd *Dg, cd *Dgi);
-void launch_accum(cudaStream_t s, int nb, int N, int j, int first, const cd *alpha,
-                  const cd *lam, const cd *Ah, cd *Cacc);
-void launch_trace_grad(cudaStream_t s, int nb, int n, int nq, const cd *At, const cd *val,
-                       const int *col, const cd *trF, const cd *alpha, cd *t, const int *fq,
-                       const int *fk, const int *partner, const double *phi, long long phi_cs,
-                       double *grad);
+void launch_assemble(cudaStream_t s, int prec, int nb, int n, int nq, const double *phi,
+                     long long phi_cs, const int *fkind, const int *frA, const int *frB,
+                     const int *aptr, const int *aq, const cd *val, void *F);
+void launch_build_V(cudaStream_t s, int prec, int nb, int n, const void *U, long long U_cs, void *V);
+void launch_lambda(cudaStream_t s, int prec, int nb, int n, const void *w, long long w_cs,
+                   const cd *alpha, void *lam, void *Dg, void *Dgi);
+void launch_accum(cudaStream_t s, int prec, int nb, int N, int j, int first, const cd *alpha,
+                  const void *lam, const void *Ah, void *Cacc);
+void launch_trace_grad(cudaStream_t s, int prec, int nb, int n, int nq, const void *At,
+                       const cd *val, const int *col, const cd *trF, const cd *alpha, cd *t,
+                       const int *fq, const int *fk, const int *partner, const double *phi,
+                       long long phi_cs, double *grad);
 void launch_propose(cudaStream_t s, int nb, int nf, const double *phi, long long phi_cs,
                     const double *grad, const double *eps, const uint32_t *keys, uint32_t slice,
                     uint32_t sweep, double *phip);
-void launch_axpyI(cudaStream_t s, int nb, int N, const cd *X, long long sX, cd a, cd b, cd *Y,
-                  long long sY);
+void launch_axpyI(cudaStream_t s, int nb, int N, Op X, cd a, cd b, Op Y);
+void launch_cvt_real(cudaStream_t s, long long n, const float *a, double *b);
 void launch_accept(cudaStream_t s, int nb, const AcceptP &p);
 void launch_commit(cudaStream_t s, int nb, const CommitP &p);
 void launch_scale_cols(cudaStream_t s, int nb, int N, const cd *X, long long sX, const double *d,

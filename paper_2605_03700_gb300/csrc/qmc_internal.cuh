@@ -49,6 +49,61 @@ __device__ __forceinline__ cd cexp_d(cd z)
 }
 __device__ __forceinline__ cd clog_d(cd z) { return cmk(log(hypot(z.x, z.y)), atan2(z.y, z.x)); }
 
+// single-precision complex (the mixed-precision path)
+typedef float2 cf;
+__host__ __device__ __forceinline__ cf cadd(cf a, cf b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ cf csub(cf a, cf b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ cf cmul(cf a, cf b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ cf cconj(cf a) { return make_float2(a.x, -a.y); }
+__host__ __device__ __forceinline__ cf cscale(cf a, float s) { return make_float2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ float cabs2(cf a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ __forceinline__ void cfma(cf &a, cf b, cf c)
+{
+    a.x = fmaf(b.x, c.x, a.x);
+    a.x = fmaf(-b.y, c.y, a.x);
+    a.y = fmaf(b.x, c.y, a.y);
+    a.y = fmaf(b.y, c.x, a.y);
+}
+
+// compute-type traits: R = float or double, C<R> its complex type
+template <class R> struct Cx;
+template <> struct Cx<double> { typedef cd T; };
+template <> struct Cx<float> { typedef cf T; };
+template <class To> __host__ __device__ __forceinline__ To cvt(cd a);
+template <class To> __host__ __device__ __forceinline__ To cvt(cf a);
+template <> __host__ __device__ __forceinline__ cd cvt<cd>(cd a) { return a; }
+template <> __host__ __device__ __forceinline__ cf cvt<cf>(cd a) { return make_float2((float)a.x, (float)a.y); }
+template <> __host__ __device__ __forceinline__ cd cvt<cd>(cf a) { return make_double2(a.x, a.y); }
+template <> __host__ __device__ __forceinline__ cf cvt<cf>(cf a) { return a; }
+template <class C> __host__ __device__ __forceinline__ C czero();
+template <> __host__ __device__ __forceinline__ cd czero<cd>() { return make_double2(0, 0); }
+template <> __host__ __device__ __forceinline__ cf czero<cf>() { return make_float2(0, 0); }
+template <class C> __host__ __device__ __forceinline__ C cmkT(double r, double i);
+template <> __host__ __device__ __forceinline__ cd cmkT<cd>(double r, double i) { return make_double2(r, i); }
+template <> __host__ __device__ __forceinline__ cf cmkT<cf>(double r, double i) { return make_float2((float)r, (float)i); }
+__device__ __forceinline__ cf cexp_d(cf z)
+{
+    float s, c;
+    sincosf(z.y, &s, &c);
+    float e = expf(z.x);
+    return make_float2(e * c, e * s);
+}
+__host__ __device__ __forceinline__ cf cdiv(cf a, cf b)
+{
+    if (fabsf(b.x) >= fabsf(b.y)) {
+        float r = b.y / b.x, d = b.x + b.y * r;
+        return make_float2((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+    } else {
+        float r = b.x / b.y, d = b.x * r + b.y;
+        return make_float2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+    }
+}
+// element type codes of GEMM operands
+enum { TY_C64 = 0, TY_C32 = 1 };
+
 // ------------------------------------------------------------- Philox ----
 // Philox4x32-10 from its published definition (Salmon, Moraes, Dror, Shaw,
 // "Parallel random numbers: as easy as 1, 2, 3", SC'11): ten rounds of two

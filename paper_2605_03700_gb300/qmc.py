@@ -76,6 +76,7 @@ def lib():
         L.qmc_sizes.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                 C.POINTER(C.c_int)]
         L.qmc_get_eps.argtypes = [vp, dp]
+        L.qmc_get_propagator.argtypes = [vp, C.c_int, C.c_int, dp, dp, C.c_size_t]
         L.qmc_tau_int.restype = C.c_double
         L.qmc_tau_int.argtypes = [dp, C.c_int]
         L.qmc_strerror.restype = C.c_char_p
@@ -139,9 +140,10 @@ class Chain:
     def __init__(self, geometry, N_phi, beta, dtau, coupling, anisotropy=0.0, seed=0, *,
                  n_chains=1, couplings=None, anisotropies=None, seeds=None, n_stab=10,
                  eps0=0.5, deps=0.1, r0=0.574, n_adapt=-1, series_capacity=4096,
-                 trace_capacity=0, stab_tol=1e-6, sign_tol=1e-6, stream=None):
+                 trace_capacity=0, stab_tol=1e-6, sign_tol=1e-6, precision=0, stream=None):
         o = qmc_default_opts()
         o.n_stab = n_stab
+        o.precision = precision
         o.eps0, o.deps, o.r0, o.n_adapt = eps0, deps, r0, n_adapt
         o.n_chains = n_chains
         o.series_capacity = series_capacity
@@ -161,8 +163,6 @@ class Chain:
             self._keep.append(a)
             o.seeds = a.ctypes.data_as(C.POINTER(C.c_uint64))
         h = C.c_void_p()
-        if stream is not None:
-            pass
         _check(lib().qmc_create(C.byref(h), geometry, N_phi, beta, dtau, coupling, anisotropy,
                                 seed, C.byref(o)))
         self.h = h
@@ -221,6 +221,14 @@ class Chain:
             G = np.zeros((2 * self.N, 2 * self.N), complex)
             _check(lib().qmc_get_green(self.h, chain, _dp(G.view(float)), 2 * G.size), self.h)
         return G
+
+    def propagator(self, slice_, chain=0):
+        """(B_tau, B_tau^-1) of a slice (1-based) as complex128 arrays."""
+        B = np.zeros((self.N, self.N), complex)
+        Bi = np.zeros((self.N, self.N), complex)
+        _check(lib().qmc_get_propagator(self.h, chain, slice_, _dp(B.view(float)),
+                                        _dp(Bi.view(float)), 2 * B.size), self.h)
+        return B, Bi
 
     def fields(self, chain=0):
         p = np.zeros((self.L, 4, self.n_q))

@@ -180,3 +180,71 @@ def test_ratio_update_entry_point_matches_oracle(qmc):
         assert abs(ld[b].real - lr.real) < TOL_LOGR
         assert abs(np.exp(1j * ld[b].imag) - np.exp(1j * lr.imag)) < 1e-9
         assert _rel(Gp[b], gref) < TOL_G
+
+
+# ------------------------------------------------------------ mixed mode ---
+# precision = 1: FP32 Jacobi sweeps with an FP64 polish, FP32 gradient
+# transforms; everything in the MH ratio FP64.  The drift differs from the
+# oracle's by FP32 rounding (~1e-7 relative), so proposals agree to ~1e-8 and
+# ratios to ~1e-7; decisions agree except for a |log u - log A| below that.
+TOL_MIXED_LOGR = 1e-5
+TOL_MIXED_G = 1e-6
+
+
+def _compare_mixed(gpu, c, orc, nsw, min_identical):
+    tg, to = gpu.trace(c), orc.trace()
+    assert len(tg) == len(to) == nsw * orc.L
+    mis = np.nonzero(tg[:, 6] != to[:, 6])[0]
+    first = int(mis[0]) if len(mis) else len(tg)
+    assert first >= min_identical, f"decisions diverge at update {first}"
+    assert np.abs(tg[:first, 2] - to[:first, 2]).max() < TOL_MIXED_LOGR
+    assert np.abs(tg[:first, 3]).max() < 1e-8          # sign-free to FP64 rounding
+    if first == len(tg):
+        assert _rel(gpu.green(c), orc.green()) < TOL_MIXED_G
+    return first
+
+
+def test_mixed_precision_config1_tracks_the_oracle(qmc):
+    nsw = 200
+    g = qmc.Chain(qmc.QMC_TORUS, 4, 2.0, 0.1, 1.0, 0.0, 0, n_stab=5, precision=1,
+                  trace_capacity=nsw * 20)
+    g.sweep(nsw)
+    g.sync()
+    o = O.Chain(M.TORUS, 4, 2.0, 0.1, 1.0, 0.0, 0, n_stab=5)
+    o.enable_trace(nsw * 20)
+    o.sweep(nsw)
+    assert _compare_mixed(g, 0, o, nsw, 2000) == nsw * 20
+    s = g.series()[0]
+    assert s[:, 15].max() < 1e-9 and s[:, 16].max() < 1e-9
+
+
+def test_mixed_precision_nphi36_propagators_and_ratios(qmc):
+    """The benchmark's matrix size: propagators built through the FP32+polish
+    eigensolver equal the oracle's (FP64 Jacobi) to 1e-10, the first updates
+    make the oracle's decisions and G stays within 1e-6."""
+    g = qmc.Chain(qmc.QMC_TORUS, 36, 0.4, 0.1, 2.0, 0.0, 0, n_stab=10, eps0=0.2, precision=1,
+                  trace_capacity=8)
+    m = M.Model(M.TORUS, 36)
+    o = O.Chain(M.TORUS, 36, 0.4, 0.1, 2.0, 0.0, 0, n_stab=10, eps0=0.2, model=m)
+    for t in (1, 3):
+        B, Bi = g.propagator(t)
+        Bo, Boi = o.B(t)
+        assert np.abs(B - Bo).max() < 1e-10 and np.abs(Bi - Boi).max() < 1e-10
+    assert _rel(g.green(0), o.green()) < 1e-10
+    g.sweep(2)
+    g.sync()
+    o.enable_trace(8)
+    o.sweep(2)
+    _compare_mixed(g, 0, o, 2, 8)
+
+
+def test_mixed_precision_full_workload_properties(qmc):
+    us = np.linspace(0.5, 2.0, 8)
+    g = qmc.Chain(qmc.QMC_TORUS, 36, 36.0, 0.1, 0.0, 0.0, 0, n_chains=8, couplings=us,
+                  seeds=np.arange(8), n_stab=10, eps0=0.45, precision=1)
+    g.sweep(2)
+    g.sync()
+    s = g.series()
+    assert s[:, :, 15].max() < 1e-8 and s[:, :, 16].max() < 1e-8
+    assert np.all(np.isfinite(s))
+    assert 0.2 < s[:, :, 13].mean() < 0.95
