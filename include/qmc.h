@@ -225,6 +225,12 @@ int qmc_ratio_update_noalloc(int N, int batch, const double *G, const double *De
  * contexts; a host-side count of kernel launches, no synchronisation). */
 long long qmc_launch_count(void);
 
+/* Tile edge the GEMM autotuner chose for n x n complex products computed in
+ * FP64 (precision 0) or FP32 (precision 1); qmc_create times every candidate
+ * (8, 12, 16, 18, 24, 32) on its own sizes and batch and keeps the fastest;
+ * 16 before any tuning. */
+int qmc_gemm_tile(int n, int precision);
+
 /* Event timing of every batched complex GEMM launch.  enable = 1 starts
  * recording (a pair of CUDA events around each launch on its stream);
  * enable = 0 stops, synchronises the device and returns the summed device

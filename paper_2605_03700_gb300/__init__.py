@@ -5,8 +5,8 @@ include/qmc.h); ``qmc`` is its ctypes binding.
 """
 from .qmc import (QMC_NOBS, QMC_NTRACE, QMC_SPHERE, QMC_TORUS, OBS_NAMES, Chain, QMCError,
                   lib, qmc_default_opts, qmc_launch_count, qmc_profile_gemm,
-                  qmc_ratio_update, qmc_tau_int)
+                  qmc_ratio_update, qmc_tau_int, qmc_gemm_tile)
 
 __all__ = ["Chain", "QMCError", "QMC_TORUS", "QMC_SPHERE", "QMC_NOBS", "QMC_NTRACE",
            "OBS_NAMES", "lib", "qmc_default_opts", "qmc_tau_int", "qmc_launch_count",
-           "qmc_profile_gemm", "qmc_ratio_update"]
+           "qmc_profile_gemm", "qmc_ratio_update", "qmc_gemm_tile"]

@@ -235,6 +235,8 @@ static int eig_of_fields(qmc_ctx *ctx, const double *phi, long long phi_cs, cd *
     // A = U^H F U, then polish: V starts at U
     gemm_sq(s, n, 4 * nb, TY_C64, op64(a, n2), 2, op64(ctx->Fm, n2), 0, op64(ctx->NSx, n2));
     gemm_sq(s, n, 4 * nb, TY_C64, op64(ctx->NSx, n2), 0, op64(a, n2), 0, op64(b, n2));
+    // polish to full FP64 convergence (quadratic from FP32 quality: two or
+    // three sweeps)
     return eigh_batched(s, TY_C64, n, b, n2, U, n2, W, n, 4 * nb, a, n2);
 }
 
@@ -320,7 +322,7 @@ static int green_at_zero(qmc_ctx *ctx)
 // one MALA proposal + MH test on slice t (1-based) for every chain
 static int update_slice(qmc_ctx *ctx, int t)
 {
-    const int nb = ctx->nb, N = ctx->N, n = ctx->n, nf = ctx->nf, gp = ctx->gp;
+    const int nb = ctx->nb, N = ctx->N, n = ctx->n, nf = ctx->nf;
     const long long NN = ctx->NN, n2 = ctx->n2;
     const int s0 = t - 1;
     cudaStream_t s = ctx->st;
@@ -735,6 +737,38 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
     }
     launch_ff_torus(s, n, nq, ctx->qxy, ctx->ff_val, ctx->ff_col, ctx->trF);
     launch_init_phi(s, nb, ctx->L, nf, ctx->keys, ctx->phi);
+    // GEMM tile autotuning for this matrix size and batch (scratch operands)
+    {
+        GemmP p;
+        memset(&p, 0, sizeof p);
+        p.M = p.N = p.K = N;
+        p.lda = p.ldb = p.ldc = N;
+        p.sA = p.sB = p.sC = NN;
+        p.alpha = ONE;
+        p.A = ctx->Eye;
+        p.B = ctx->X2;
+        p.C = ctx->X1;
+        p.ta = p.tb = p.tc = p.rc = TY_C64;
+        gemm_autotune(s, p, nb, nullptr);
+        if (ctx->gp == TY_C32) {
+            p.opA = 2;
+            p.B = ctx->Ah;
+            p.C = ctx->Y1;
+            p.tb = p.tc = p.rc = TY_C32;
+            gemm_autotune(s, p, nb, nullptr);
+        }
+        GemmP q;
+        memset(&q, 0, sizeof q);
+        q.M = q.N = q.K = n;
+        q.lda = q.ldb = q.ldc = n;
+        q.sA = q.sB = q.sC = n2;
+        q.alpha = ONE;
+        q.A = ctx->NSx;
+        q.B = ctx->NSy;
+        q.C = ctx->NSz;
+        q.ta = q.tb = q.tc = q.rc = TY_C64;
+        gemm_autotune(s, q, 4 * nb, nullptr);
+    }
     // eigenpairs and propagators of every slice
     for (int t = 0; t < ctx->L; ++t) {
         if (eig_of_fields(ctx, ctx->phi + (long long)t * nf, L * nf, ctx->Up, ctx->Wp)) {
@@ -1061,6 +1095,11 @@ const char *qmc_strerror(int code)
 const char *qmc_last_error(const qmc_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
 
 long long qmc_launch_count(void) { return g_qmc_launches; }
+
+int qmc_gemm_tile(int n, int precision)
+{
+    return gemm_get_tile(n, precision == 1 ? TY_C32 : TY_C64);
+}
 
 int qmc_ratio_update_noalloc(int N, int batch, const double *G, const double *Delta,
                              double *Gp, double *logdet, void *stream)

@@ -10,25 +10,25 @@
 
 // ------------------------------------------------------------------ GEMM --
 // C[b] = alpha * op(A[b]) * diag(d[b]) * op(B[b]) + beta * C[b] (+ I)
-// op: 0 = none, 1 = transpose, 2 = conjugate transpose.  16 x 16 output tile
-// per block, one element per thread, K staged through shared memory in
-// slabs of 16; transposed operands are read with the thread index running
-// along the contiguous dimension.  Operands of type TA/TB are converted to
-// the compute type on load; the diagonal has the compute type.
-#define GT 16
-template <class TA, class TB, class TC, class R>
-__global__ void __launch_bounds__(256) k_zgemm(GemmP p)
+// op: 0 = none, 1 = transpose, 2 = conjugate transpose.  TT x TT output tile
+// per block, one element per thread, K staged through shared memory in slabs
+// of TT; transposed operands are read with the thread index running along the
+// contiguous dimension.  Operands of type TA/TB are converted to the compute
+// type on load; the diagonal has the compute type.  The tile edge TT is
+// chosen per (matrix size, compute type) by the autotuner below.
+template <int TT, class TA, class TB, class TC, class R>
+__global__ void __launch_bounds__(TT * TT) k_zgemm(GemmP p)
 {
     typedef typename Cx<R>::T C;
-    __shared__ C As[GT][GT + 1];
-    __shared__ C Bs[GT][GT + 1];
+    __shared__ C As[TT][TT + 1];
+    __shared__ C Bs[TT][TT + 1];
     const int b = blockIdx.z, tx = threadIdx.x, ty = threadIdx.y;
-    const int row0 = blockIdx.y * GT, col0 = blockIdx.x * GT;
+    const int row0 = blockIdx.y * TT, col0 = blockIdx.x * TT;
     const TA *A = (const TA *)p.A + (long long)b * p.sA;
     const TB *B = (const TB *)p.B + (long long)b * p.sB;
     const C *d = p.d ? (const C *)p.d + (long long)b * p.sd : nullptr;
     C acc = czero<C>();
-    for (int k0 = 0; k0 < p.K; k0 += GT) {
+    for (int k0 = 0; k0 < p.K; k0 += TT) {
         if (p.opA == 0) {
             int r = row0 + ty, k = k0 + tx;
             As[ty][tx] = (r < p.M && k < p.K) ? cvt<C>(A[(long long)r * p.lda + k]) : czero<C>();
@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(256) k_zgemm(GemmP p)
         }
         __syncthreads();
 #pragma unroll
-        for (int k = 0; k < GT; ++k) cfma(acc, As[ty][k], Bs[k][tx]);
+        for (int k = 0; k < TT; ++k) cfma(acc, As[ty][k], Bs[k][tx]);
         __syncthreads();
     }
     const int r = row0 + ty, c = col0 + tx;
@@ -109,73 +109,157 @@ static cudaEvent_t gprof_event()
 }
 
 typedef void (*gemm_fn)(GemmP);
-template <class R>
-static gemm_fn gemm_kernel_r(int ta, int tb, int tc)
+static const int kTiles[] = {8, 12, 16, 18, 24, 32};
+static const int kNTiles = 6;
+
+// the operand/compute combinations the two precision modes use:
+// 0: FP64 everywhere; 1: (FP64, FP64) -> FP32; 2: (FP32, FP64) -> FP32;
+// 3: (FP64, FP32) -> FP32, all with FP32 compute
+static int combo_of(const GemmP &p)
 {
-    const int code = ta * 4 + tb * 2 + tc;
-    switch (code) {
-    case 0: return k_zgemm<cd, cd, cd, R>;
-    case 1: return k_zgemm<cd, cd, cf, R>;
-    case 2: return k_zgemm<cd, cf, cd, R>;
-    case 3: return k_zgemm<cd, cf, cf, R>;
-    case 4: return k_zgemm<cf, cd, cd, R>;
-    case 5: return k_zgemm<cf, cd, cf, R>;
-    case 6: return k_zgemm<cf, cf, cd, R>;
-    default: return k_zgemm<cf, cf, cf, R>;
+    if (p.rc == TY_C64) return (p.ta == TY_C64 && p.tb == TY_C64 && p.tc == TY_C64) ? 0 : -1;
+    if (p.tc != TY_C32) return -1;
+    if (p.ta == TY_C64 && p.tb == TY_C64) return 1;
+    if (p.ta == TY_C32 && p.tb == TY_C64) return 2;
+    if (p.ta == TY_C64 && p.tb == TY_C32) return 3;
+    return -1;
+}
+
+template <int TT>
+static gemm_fn gemm_kernel_t(int combo)
+{
+    switch (combo) {
+    case 0: return k_zgemm<TT, cd, cd, cd, double>;
+    case 1: return k_zgemm<TT, cd, cd, cf, float>;
+    case 2: return k_zgemm<TT, cf, cd, cf, float>;
+    case 3: return k_zgemm<TT, cd, cf, cf, float>;
+    default: return nullptr;
     }
 }
-static gemm_fn gemm_kernel(const GemmP &p)
+
+static gemm_fn gemm_kernel(int combo, int tile)
 {
-    if (p.ta < 0 || p.ta > 1 || p.tb < 0 || p.tb > 1 || p.tc < 0 || p.tc > 1) return nullptr;
-    return p.rc == TY_C64 ? gemm_kernel_r<double>(p.ta, p.tb, p.tc)
-                          : gemm_kernel_r<float>(p.ta, p.tb, p.tc);
+    switch (tile) {
+    case 8: return gemm_kernel_t<8>(combo);
+    case 12: return gemm_kernel_t<12>(combo);
+    case 16: return gemm_kernel_t<16>(combo);
+    case 18: return gemm_kernel_t<18>(combo);
+    case 24: return gemm_kernel_t<24>(combo);
+    case 32: return gemm_kernel_t<32>(combo);
+    default: return nullptr;
+    }
+}
+
+// autotuned tile edge per (matrix size, compute type); 16 until tuned
+struct TileKey {
+    int n, rc;
+};
+static std::vector<std::pair<TileKey, int>> g_tiles;
+
+static int tile_for(int n, int rc)
+{
+    for (auto &e : g_tiles)
+        if (e.first.n == n && e.first.rc == rc) return e.second;
+    return 16;
+}
+
+void gemm_set_tile(int n, int rc, int tile)
+{
+    for (auto &e : g_tiles)
+        if (e.first.n == n && e.first.rc == rc) {
+            e.second = tile;
+            return;
+        }
+    g_tiles.push_back({TileKey{n, rc}, tile});
+}
+
+int gemm_get_tile(int n, int rc) { return tile_for(n, rc); }
+
+static int launch_gemm(cudaStream_t st, const GemmP &p, int batch, int tile)
+{
+    int combo = combo_of(p);
+    gemm_fn f = combo < 0 ? nullptr : gemm_kernel(combo, tile);
+    if (!f) return -1;
+    dim3 grid(cdiv_up(p.N, tile), cdiv_up(p.M, tile), batch);
+    f<<<grid, dim3(tile, tile), 0, st>>>(p);
+    return 0;
 }
 
 int zgemm(cudaStream_t st, const GemmP &p, int batch)
 {
-    gemm_fn f = gemm_kernel(p);
-    if (!f) return -1;
-    dim3 grid(cdiv_up(p.N, GT), cdiv_up(p.M, GT), batch);
+    const int tile = tile_for(p.N, p.rc);
+    int r;
     if (g_gprof.on) {
         cudaEventRecord(gprof_event(), st);
-        f<<<grid, dim3(GT, GT), 0, st>>>(p);
+        r = launch_gemm(st, p, batch, tile);
         cudaEventRecord(gprof_event(), st);
         g_gprof.flops += 8.0 * p.M * (double)p.N * p.K * batch;
         g_gprof.launches++;
     } else {
-        f<<<grid, dim3(GT, GT), 0, st>>>(p);
+        r = launch_gemm(st, p, batch, tile);
     }
     QMC_COUNT(1);
-    return 0;
+    return r;
+}
+
+// Time every tile edge on the given square product (3 launches after one
+// warm-up each) and keep the fastest for (n, rc).  Runs on `st`, which it
+// synchronises.
+int gemm_autotune(cudaStream_t st, const GemmP &p, int batch, float *best_ms)
+{
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = 16;
+    float bt = 1e30f;
+    for (int i = 0; i < kNTiles; ++i) {
+        const int tile = kTiles[i];
+        if (launch_gemm(st, p, batch, tile)) continue;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3; ++r) launch_gemm(st, p, batch, tile);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (t < bt) {
+            bt = t;
+            best = tile;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    QMC_COUNT(4 * kNTiles);
+    gemm_set_tile(p.N, p.rc, best);
+    if (best_ms) *best_ms = bt / 3;
+    return best;
 }
 
 // -------------------------------------------------------- Jacobi eigh ----
 // H = U diag(w) U^H for a batch of Hermitian n x n matrices, one block per
 // matrix, both matrices in shared memory.  Cyclic Jacobi with the parallel
-// round-robin ordering: each step applies n/2 disjoint rotations at once
-// (A <- J^H A J, U <- U J).  Rotation for the pair (p,q): with
-// a_pq = |a_pq| e^{i theta}, a phase diag(1, e^{-i theta}) makes the 2x2
-// block real, then the real Jacobi rotation (c, s) of zeta =
-// (a_qq - a_pp)/(2|a_pq|), t = sgn(zeta)/(|zeta| + sqrt(zeta^2 + 1)).
-// Sweeps stop when the off-diagonal Frobenius norm^2 <= tol * total
-// (tol = 1e-34 in FP64; 1e-10 in FP32, where rounding keeps the ratio above
-// ~(n eps)^2).  With V0 given, the rotations accumulate onto V0 instead of the
-// identity (polishing A = V0^H F V0 for a unitary V0 yields F = U W U^H).
+// round-robin ordering: each round applies n/2 disjoint rotations at once,
+// A <- J^H A J and U <- U J, with J block-diagonal over the pairs.  Rotation
+// for the pair (p,q): with a_pq = |a_pq| e^{i theta}, J_pq = D P,
+// D = diag(1, e^{-i theta}) making the 2x2 block real and P the real Jacobi
+// rotation [[c, s], [-s, c]] of zeta = (a_qq - a_pp)/(2|a_pq|),
+// t = sgn(zeta)/(|zeta| + sqrt(zeta^2 + 1)).  Because the pairs are disjoint,
+// every 2x2 block A[{p1,q1},{p2,q2}] maps to J_1^H A_blk J_2 independently, so
+// a round is one parallel phase over the (n/2)^2 blocks.
+// Sweeps stop when off-diagonal Frobenius norm^2 <= tol * total.
 template <class R>
 __global__ void __launch_bounds__(256) k_eigh(int n, const void *Hv, long long sH, void *Uv,
                                               long long sU, void *wv, long long sw,
-                                              const void *V0v, long long sV0)
+                                              const void *V0v, long long sV0, R tol)
 {
     typedef typename Cx<R>::T C;
     extern __shared__ __align__(16) unsigned char sm_e_raw[];
     C *A = (C *)sm_e_raw;
     C *V = A + n * n;
-    __shared__ R rc[64], rs[64];
-    __shared__ C rph[64];
-    __shared__ int rp[64], rq[64];
+    __shared__ C jm[32][4];  // per pair: J_pp, J_pq, J_qp, J_qq
+    __shared__ int rp[32], rq[32];
     __shared__ R red[2][32];
     __shared__ int done;
-    const R tol = sizeof(R) == 8 ? (R)1e-34 : (R)1e-10;
+    __shared__ R thr;  // rotations below rounding of the matrix norm are skipped
     const int b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
     const C *Hb = (const C *)Hv + (long long)b * sH;
     const C *V0 = V0v ? (const C *)V0v + (long long)b * sV0 : nullptr;
@@ -208,6 +292,11 @@ __global__ void __launch_bounds__(256) k_eigh(int n, const void *Hv, long long s
                 stt += red[1][i];
             }
             done = (so == (R)0 || so <= tol * stt);
+            // 1e-3 eps ||A||_F: far below what the stop test accepts, and it
+            // keeps |a_pq| clear of the underflow range, where the phase
+            // a_pq / |a_pq| would lose its unit modulus and the rotation its
+            // unitarity
+            thr = sqrt(stt) * (R)(sizeof(R) == 4 ? 1.2e-10 : 2.2e-19);
         }
         __syncthreads();
         if (done) break;
@@ -222,64 +311,82 @@ __global__ void __launch_bounds__(256) k_eigh(int n, const void *Hv, long long s
                     bb = (r - tid + (m - 1)) % (m - 1);
                 }
                 int p = a < bb ? a : bb, q = a < bb ? bb : a;
-                R c = 1, s = 0;
+                R c = 1, sn = 0;
                 C ph = cmkT<C>(1, 0);
                 if (q < n) {
                     C apq = A[p * n + q];
-                    R ab = sqrt(cabs2(apq));
-                    if (ab > (R)0) {
+                    R ab = hypot(apq.x, apq.y);
+                    if (ab > thr) {
                         R app = A[p * n + p].x, aqq = A[q * n + q].x;
                         ph = cmkT<C>(apq.x / ab, apq.y / ab);
                         R zeta = (aqq - app) / (2 * ab);
                         R t = (zeta >= 0 ? (R)1 : (R)-1) / (fabs(zeta) + sqrt(zeta * zeta + (R)1));
                         c = (R)1 / sqrt(t * t + (R)1);
-                        s = t * c;
+                        sn = t * c;
                     }
                 } else {
-                    p = q = -1;
+                    q = -1;  // dummy partner of an odd size: identity
                 }
+                C cph = cconj(ph);
                 rp[tid] = p;
                 rq[tid] = q;
-                rc[tid] = c;
-                rs[tid] = s;
-                rph[tid] = ph;
+                jm[tid][0] = cmkT<C>(c, 0);
+                jm[tid][1] = cmkT<C>(sn, 0);
+                jm[tid][2] = cmkT<C>(-sn * cph.x, -sn * cph.y);
+                jm[tid][3] = cmkT<C>(c * cph.x, c * cph.y);
             }
             __syncthreads();
-            for (int t = tid; t < half * n; t += nt) {
-                int k = t / n, row = t % n;
-                int p = rp[k], q = rq[k];
-                if (p < 0 || rs[k] == (R)0) continue;
-                R c = rc[k], s = rs[k];
-                C cph = cconj(rph[k]);
-                C x = A[row * n + p], y = A[row * n + q];
-                C sy = cmul(cph, y);
-                A[row * n + p] = cmkT<C>(c * x.x - s * sy.x, c * x.y - s * sy.y);
-                A[row * n + q] = cmkT<C>(s * x.x + c * sy.x, s * x.y + c * sy.y);
-                x = V[row * n + p];
-                y = V[row * n + q];
-                sy = cmul(cph, y);
-                V[row * n + p] = cmkT<C>(c * x.x - s * sy.x, c * x.y - s * sy.y);
-                V[row * n + q] = cmkT<C>(s * x.x + c * sy.x, s * x.y + c * sy.y);
-            }
-            __syncthreads();
-            for (int t = tid; t < half * n; t += nt) {
-                int k = t / n, col = t % n;
-                int p = rp[k], q = rq[k];
-                if (p < 0 || rs[k] == (R)0) continue;
-                R c = rc[k], s = rs[k];
-                C ph = rph[k];
-                C x = A[p * n + col], y = A[q * n + col];
-                C sy = cmul(ph, y);
-                A[p * n + col] = cmkT<C>(c * x.x - s * sy.x, c * x.y - s * sy.y);
-                A[q * n + col] = cmkT<C>(s * x.x + c * sy.x, s * x.y + c * sy.y);
-            }
-            __syncthreads();
-            if (tid < half) {
-                int p = rp[tid], q = rq[tid];
-                if (p >= 0 && rs[tid] != (R)0) {
-                    A[p * n + q] = czero<C>();
-                    A[q * n + p] = czero<C>();
+            // A <- J^H A J blockwise; dummy rows/columns (q < 0) are 1 x 1
+            for (int t = tid; t < half * half; t += nt) {
+                const int k1 = t / half, k2 = t % half;
+                const int p1 = rp[k1], q1 = rq[k1], p2 = rp[k2], q2 = rq[k2];
+                if (p1 >= n || p2 >= n) continue;
+                C a00 = A[p1 * n + p2];
+                C a01 = q2 >= 0 ? A[p1 * n + q2] : czero<C>();
+                C a10 = q1 >= 0 ? A[q1 * n + p2] : czero<C>();
+                C a11 = (q1 >= 0 && q2 >= 0) ? A[q1 * n + q2] : czero<C>();
+                // X = A_blk J2
+                C x00, x01, x10, x11;
+                if (q2 >= 0) {
+                    const C *j = jm[k2];
+                    x00 = cadd(cmul(a00, j[0]), cmul(a01, j[2]));
+                    x01 = cadd(cmul(a00, j[1]), cmul(a01, j[3]));
+                    x10 = cadd(cmul(a10, j[0]), cmul(a11, j[2]));
+                    x11 = cadd(cmul(a10, j[1]), cmul(a11, j[3]));
+                } else {
+                    x00 = a00; x01 = a01; x10 = a10; x11 = a11;
                 }
+                // Y = J1^H X
+                if (q1 >= 0) {
+                    const C *j = jm[k1];
+                    C h00 = cconj(j[0]), h01 = cconj(j[2]), h10 = cconj(j[1]), h11 = cconj(j[3]);
+                    a00 = cadd(cmul(h00, x00), cmul(h01, x10));
+                    a01 = cadd(cmul(h00, x01), cmul(h01, x11));
+                    a10 = cadd(cmul(h10, x00), cmul(h11, x10));
+                    a11 = cadd(cmul(h10, x01), cmul(h11, x11));
+                } else {
+                    a00 = x00; a01 = x01; a10 = x10; a11 = x11;
+                }
+                if (k1 == k2 && q1 >= 0) {  // the rotated pivot block is diagonal
+                    a01 = czero<C>();
+                    a10 = czero<C>();
+                    a00.y = 0;
+                    a11.y = 0;
+                }
+                A[p1 * n + p2] = a00;
+                if (q2 >= 0) A[p1 * n + q2] = a01;
+                if (q1 >= 0) A[q1 * n + p2] = a10;
+                if (q1 >= 0 && q2 >= 0) A[q1 * n + q2] = a11;
+            }
+            // V <- V J (rows x pairs)
+            for (int t = tid; t < half * n; t += nt) {
+                const int k = t / n, row = t % n;
+                const int p = rp[k], q = rq[k];
+                if (p >= n || q < 0) continue;
+                const C *j = jm[k];
+                C x = V[row * n + p], y = V[row * n + q];
+                V[row * n + p] = cadd(cmul(x, j[0]), cmul(y, j[2]));
+                V[row * n + q] = cadd(cmul(x, j[1]), cmul(y, j[3]));
             }
             __syncthreads();
         }
@@ -291,7 +398,8 @@ __global__ void __launch_bounds__(256) k_eigh(int n, const void *Hv, long long s
 }
 
 int eigh_batched(cudaStream_t st, int prec, int n, const void *H, long long sH, void *U,
-                 long long sU, void *w, long long sw, int batch, const void *V0, long long sV0)
+                 long long sU, void *w, long long sw, int batch, const void *V0, long long sV0,
+                 double tol)
 {
     if (n > 64 || batch <= 0) return batch <= 0 ? 0 : -1;
     if (prec == TY_C64) {
@@ -302,7 +410,8 @@ int eigh_batched(cudaStream_t st, int prec, int n, const void *H, long long sH, 
                                  2 * 64 * 64 * 16);
             attr = true;
         }
-        k_eigh<double><<<batch, 256, smem, st>>>(n, H, sH, U, sU, w, sw, V0, sV0);
+        k_eigh<double><<<batch, 256, smem, st>>>(n, H, sH, U, sU, w, sw, V0, sV0,
+                                                 tol > 0 ? tol : 1e-34);
     } else {
         size_t smem = 2ull * n * n * sizeof(cf);
         static bool attr32 = false;
@@ -311,7 +420,8 @@ int eigh_batched(cudaStream_t st, int prec, int n, const void *H, long long sH, 
                                  2 * 64 * 64 * 8);
             attr32 = true;
         }
-        k_eigh<float><<<batch, 256, smem, st>>>(n, H, sH, U, sU, w, sw, V0, sV0);
+        k_eigh<float><<<batch, 256, smem, st>>>(n, H, sH, U, sU, w, sw, V0, sV0,
+                                                (float)(tol > 0 ? tol : 1e-10));
     }
     QMC_COUNT(1);
     return 0;
@@ -496,22 +606,40 @@ int rdiv_batched(cudaStream_t st, int prec, int n, const cd *G, long long sG, co
 
 // ------------------------------------------------------------------ QRP ---
 // X = Q D V by Householder QR with column pivoting, X P = Q R, D = |diag R|,
-// V = D^-1 R P^T.  One block per matrix; the working matrix lives in shared
-// memory, Q is accumulated in global memory (Q <- Q H_k).  Pivot: the first
-// column of largest remaining 2-norm.  FP64 always.
+// V = D^-1 R P^T.  One block per matrix, working matrix and (when it fits) Q
+// in shared memory.  Pivot: the first column of largest remaining 2-norm.
+// Every step is parallel: column norms and the Householder dot products are
+// warp reductions (one warp per column / row), the rank-1 updates of A and
+// of Q (Q <- Q H_k) run over all threads.  FP64 always.
+__device__ __forceinline__ cd warp_csum(cd v)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+
 __global__ void __launch_bounds__(256) k_qrp(int n, const cd *X, long long sX, cd *Q, long long sQ,
-                                             double *D, long long sD, cd *V, long long sV)
+                                             double *D, long long sD, cd *V, long long sV,
+                                             int q_in_smem)
 {
     extern __shared__ cd sm_q[];
     cd *A = sm_q;
-    cd *v = sm_q + n * n;
-    double *cn = (double *)(v + n);
+    cd *v = A + n * n;
+    cd *sv = v + n;   // per-column dot products of the trailing matrix
+    cd *sq = sv + n;  // per-row dot products of Q
+    double *cn = (double *)(sq + n);
     int *perm = (int *)(cn + n);
+    // Q after the int array, rounded up to a 16-byte boundary
+    cd *Qs = q_in_smem ? (cd *)((((uintptr_t)(perm + n)) + 15) & ~(uintptr_t)15) : nullptr;
     __shared__ int s_best;
-    __shared__ double s_vn;
+    __shared__ double s_f;
     const int b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
     const cd *Xb = X + (long long)b * sX;
-    cd *Qb = Q + (long long)b * sQ;
+    cd *Qg = Q + (long long)b * sQ;
+    cd *Qb = q_in_smem ? Qs : Qg;
     for (int e = tid; e < n * n; e += nt) {
         A[e] = Xb[e];
         Qb[e] = cmk((e / n) == (e % n) ? 1.0 : 0.0, 0.0);
@@ -519,10 +647,12 @@ __global__ void __launch_bounds__(256) k_qrp(int n, const cd *X, long long sX, c
     for (int j = tid; j < n; j += nt) perm[j] = j;
     __syncthreads();
     for (int k = 0; k < n; ++k) {
-        for (int j = k + tid; j < n; j += nt) {
+        // remaining column norms (warp per column)
+        for (int j = k + warp; j < n; j += nw) {
             double s = 0.0;
-            for (int i = k; i < n; ++i) s += cabs2(A[i * n + j]);
-            cn[j] = s;
+            for (int i = k + lane; i < n; i += 32) s += cabs2(A[i * n + j]);
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) cn[j] = s;
         }
         __syncthreads();
         if (tid == 0) {
@@ -541,7 +671,7 @@ __global__ void __launch_bounds__(256) k_qrp(int n, const cd *X, long long sX, c
             }
         }
         __syncthreads();
-        int best = s_best;
+        const int best = s_best;
         if (best != k)
             for (int i = tid; i < n; i += nt) {
                 cd t = A[i * n + k];
@@ -549,76 +679,90 @@ __global__ void __launch_bounds__(256) k_qrp(int n, const cd *X, long long sX, c
                 A[i * n + best] = t;
             }
         __syncthreads();
-        if (tid == 0) {
-            double xn = 0.0;
-            for (int i = k; i < n; ++i) xn += cabs2(A[i * n + k]);
-            xn = sqrt(xn);
-            cd x0 = A[k * n + k];
-            double ax0 = sqrt(cabs2(x0));
-            cd ph = ax0 > 0 ? cmk(x0.x / ax0, x0.y / ax0) : cmk(1, 0);
-            cd alpha = cmk(-ph.x * xn, -ph.y * xn);
-            double vn = 0.0;
-            for (int i = k; i < n; ++i) {
-                cd vi = A[i * n + k];
-                if (i == k) vi = csub(vi, alpha);
-                v[i] = vi;
-                vn += cabs2(vi);
-            }
-            s_vn = (xn == 0.0) ? 0.0 : vn;
-        }
-        __syncthreads();
-        double vn = s_vn;
-        if (vn > 0.0) {
-            double f = 2.0 / vn;
-            for (int j = k + tid; j < n; j += nt) {
-                cd s = cmk(0, 0);
-                for (int i = k; i < n; ++i) cfma(s, cconj(v[i]), A[i * n + j]);
-                s = cscale(s, f);
-                for (int i = k; i < n; ++i) {
-                    cd a = A[i * n + j];
-                    cfma(a, cmk(-s.x, -s.y), v[i]);
-                    A[i * n + j] = a;
-                }
-            }
-            for (int r = tid; r < n; r += nt) {
-                cd s = cmk(0, 0);
-                for (int i = k; i < n; ++i) cfma(s, Qb[(long long)r * n + i], v[i]);
-                s = cscale(s, f);
-                for (int i = k; i < n; ++i) {
-                    cd q = Qb[(long long)r * n + i];
-                    cfma(q, cmk(-s.x, -s.y), cconj(v[i]));
-                    Qb[(long long)r * n + i] = q;
-                }
+        // Householder vector v = x - alpha e1, alpha = -e^{i arg x0} |x|;
+        // the tail norm is summed directly (|x|^2 - |x0|^2 would cancel when
+        // the column is nearly e1)
+        if (warp == 0) {
+            double tail = 0.0;
+            for (int i = k + 1 + lane; i < n; i += 32) tail += cabs2(A[i * n + k]);
+            for (int o = 16; o > 0; o >>= 1) tail += __shfl_xor_sync(0xffffffffu, tail, o);
+            if (lane == 0) {
+                cd x0 = A[k * n + k];
+                double ax0 = sqrt(cabs2(x0));
+                double xn = sqrt(tail + ax0 * ax0);
+                cd ph = ax0 > 0 ? cmk(x0.x / ax0, x0.y / ax0) : cmk(1, 0);
+                cd alpha = cmk(-ph.x * xn, -ph.y * xn);
+                cd v0 = csub(x0, alpha);
+                double vn = tail + cabs2(v0);
+                v[k] = v0;
+                s_f = (xn == 0.0 || vn == 0.0) ? 0.0 : 2.0 / vn;
+                A[k * n + k] = alpha;
             }
         }
+        for (int i = k + 1 + tid; i < n; i += nt) v[i] = A[i * n + k];
         __syncthreads();
+        const double f = s_f;
+        if (f != 0.0) {
+            // s_j = f sum_i conj(v_i) A_ij for the trailing columns
+            for (int j = k + 1 + warp; j < n; j += nw) {
+                cd s = cmk(0, 0);
+                for (int i = k + lane; i < n; i += 32) cfma(s, cconj(v[i]), A[i * n + j]);
+                s = warp_csum(s);
+                if (lane == 0) sv[j] = cscale(s, f);
+            }
+            __syncthreads();
+            const int w = n - k, wj = n - k - 1;
+            for (int t = tid; t < w * wj; t += nt) {
+                int i = k + t / wj, j = k + 1 + t % wj;
+                cd a = A[i * n + j], sj = sv[j];
+                cfma(a, cmk(-sj.x, -sj.y), v[i]);
+                A[i * n + j] = a;
+            }
+            // t_r = f sum_i Q_ri v_i, Q_ri -= t_r conj(v_i)
+            for (int r = warp; r < n; r += nw) {
+                cd s = cmk(0, 0);
+                for (int i = k + lane; i < n; i += 32) cfma(s, Qb[(long long)r * n + i], v[i]);
+                s = warp_csum(s);
+                if (lane == 0) sq[r] = cscale(s, f);
+            }
+            __syncthreads();
+            for (int t = tid; t < n * w; t += nt) {
+                int r = t / w, i = k + t % w;
+                cd q = Qb[(long long)r * n + i], tr = sq[r];
+                cfma(q, cmk(-tr.x, -tr.y), cconj(v[i]));
+                Qb[(long long)r * n + i] = q;
+            }
+        }
         for (int i = k + 1 + tid; i < n; i += nt) A[i * n + k] = cmk(0, 0);
         __syncthreads();
     }
     double *Db = D + (long long)b * sD;
     cd *Vb = V + (long long)b * sV;
     for (int i = tid; i < n; i += nt) Db[i] = sqrt(cabs2(A[i * n + i]));
-    __syncthreads();
     for (int e = tid; e < n * n; e += nt) {
         int i = e / n, j = e % n;
         double di = sqrt(cabs2(A[i * n + i]));
         cd val = (j >= i) ? A[i * n + j] : cmk(0, 0);
         Vb[(long long)i * n + perm[j]] = cmk(val.x / di, val.y / di);
+        if (q_in_smem) Qg[e] = Qs[e];
     }
 }
 
 int qrp_batched(cudaStream_t st, int n, const cd *X, long long sX, cd *Q, long long sQ, double *D,
                 long long sD, cd *V, long long sV, int batch)
 {
-    size_t smem = (size_t)n * n * sizeof(cd) + (size_t)n * sizeof(cd) + (size_t)n * sizeof(double) +
-                  (size_t)n * sizeof(int) + 64;
+    size_t base = (size_t)n * n * sizeof(cd) + 3 * (size_t)n * sizeof(cd) +
+                  (size_t)n * sizeof(double) + (size_t)n * sizeof(int) + 16;
+    size_t withq = base + (size_t)n * n * sizeof(cd);
+    int qs = withq <= 220 * 1024;
+    size_t smem = qs ? withq : base;
     if (smem > 220 * 1024) return -1;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_qrp, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         attr = true;
     }
-    k_qrp<<<batch, 256, smem, st>>>(n, X, sX, Q, sQ, D, sD, V, sV);
+    k_qrp<<<batch, 256, smem, st>>>(n, X, sX, Q, sQ, D, sD, V, sV, qs);
     QMC_COUNT(1);
     return 0;
 }

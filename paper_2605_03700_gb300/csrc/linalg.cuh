@@ -24,11 +24,14 @@ struct GemmP {
 };
 
 int zgemm(cudaStream_t st, const GemmP &p, int batch);
+int gemm_autotune(cudaStream_t st, const GemmP &p, int batch, float *best_ms);
+void gemm_set_tile(int n, int rc, int tile);
+int gemm_get_tile(int n, int rc);
 void gemm_prof_start();
 void gemm_prof_stop(double *ms, long long *launches, double *flops);
 int eigh_batched(cudaStream_t st, int prec, int n, const void *H, long long sH, void *U,
                  long long sU, void *w, long long sw, int batch, const void *V0 = nullptr,
-                 long long sV0 = 0);
+                 long long sV0 = 0, double tol = 0.0);
 int lu_batched(cudaStream_t st, int n, cd *A, long long sA, int *piv, long long spiv, cd *logdet,
                int batch);
 int rdiv_batched(cudaStream_t st, int prec, int n, const cd *G, long long sG, const cd *LU,

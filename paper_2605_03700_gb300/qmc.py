@@ -86,6 +86,7 @@ def lib():
         L.qmc_copy_latest_async.argtypes = [vp, dp]
         L.qmc_ratio_update.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp, vp]
         L.qmc_ratio_update_noalloc.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp, vp]
+        L.qmc_gemm_tile.argtypes = [C.c_int, C.c_int]
         L.qmc_launch_count.restype = C.c_longlong
         L.qmc_launch_count.argtypes = []
         L.qmc_profile_gemm.argtypes = [C.c_int, dp, C.POINTER(C.c_longlong), dp]
@@ -109,6 +110,10 @@ def qmc_default_opts() -> qmc_opts:
     o = qmc_opts()
     _check(lib().qmc_default_opts(C.byref(o)))
     return o
+
+
+def qmc_gemm_tile(n: int, precision: int) -> int:
+    return int(lib().qmc_gemm_tile(n, precision))
 
 
 def qmc_launch_count() -> int:
