@@ -79,7 +79,7 @@ struct qmc_ctx {
     cd *Fm;
     void *Fm32, *U32;
     float *W32;
-    cd *NSx, *NSy, *NSz;
+    cd *NSx, *NSy, *NSz, *NSs, *NSr, *NSe;  // eigensolver work, [nb][4][n^2]
     // scratch, FP64
     cd *tq, *X1, *X2, *M, *Gp, *Gs, *Qt, *Vt, *Eye, *dinvR, *dinvL, *logdet, *ax;
     double *phip, *grad, *gradp, *Dt, *ones, *stats, *eps, *eps_used, *series, *trace;
@@ -210,9 +210,9 @@ static void gradient(qmc_ctx *ctx, const cd *Gm, const cd *V, const cd *T, const
 
 // FP64 eigenpairs (U [nb][4][n^2], W [nb][4][n]) of the four channel matrices
 // of fields phi (chain stride phi_cs).  FP64 mode: FP64 Jacobi.  Mixed mode:
-// Jacobi sweeps in FP32, two Newton-Schulz steps U <- U (3 - U^H U)/2 in
-// FP64 to restore unitarity, then FP64 Jacobi on the nearly diagonal
-// A = U^H F U starting from V = U (converges in one or two sweeps): the same
+// Jacobi sweeps in FP32, two FP64 refinement steps of the eigenvectors
+// (GEMMs over all chains and channels), and the FP64 Jacobi only as a check
+// that returns at once unless a near-degenerate cluster is left: the same
 // eigenpairs as the FP64 solver, at a fraction of its FP64 work.
 static int eig_of_fields(qmc_ctx *ctx, const double *phi, long long phi_cs, cd *U, double *W)
 {
@@ -222,22 +222,17 @@ static int eig_of_fields(qmc_ctx *ctx, const double *phi, long long phi_cs, cd *
     launch_assemble(s, TY_C64, nb, n, ctx->nq, phi, phi_cs, ctx->fkind, ctx->frA, ctx->frB,
                     ctx->aptr, ctx->aq, ctx->ff_val, ctx->Fm);
     if (ctx->gp == TY_C64) return eigh_batched(s, TY_C64, n, ctx->Fm, n2, U, n2, W, n, 4 * nb);
-    launch_axpyI(s, 4 * nb, n, op64(ctx->Fm, n2), ONE, ZERO, Op{ctx->Fm32, n2, TY_C32});
-    if (eigh_batched(s, TY_C32, n, ctx->Fm32, n2, ctx->U32, n2, ctx->W32, n, 4 * nb)) return -1;
-    launch_axpyI(s, 4 * nb, n, Op{ctx->U32, n2, TY_C32}, ONE, ZERO, op64(ctx->NSy, n2));
-    cd *a = ctx->NSy, *b = ctx->NSz;
-    for (int it = 0; it < 2; ++it) {
-        gemm_sq(s, n, 4 * nb, TY_C64, op64(a, n2), 2, op64(a, n2), 0, op64(ctx->NSx, n2));
-        launch_axpyI(s, 4 * nb, n, op64(ctx->NSx, n2), cmk(-0.5, 0), cmk(1.5, 0), op64(ctx->NSx, n2));
-        gemm_sq(s, n, 4 * nb, TY_C64, op64(a, n2), 0, op64(ctx->NSx, n2), 0, op64(b, n2));
-        std::swap(a, b);
-    }
-    // A = U^H F U, then polish: V starts at U
-    gemm_sq(s, n, 4 * nb, TY_C64, op64(a, n2), 2, op64(ctx->Fm, n2), 0, op64(ctx->NSx, n2));
-    gemm_sq(s, n, 4 * nb, TY_C64, op64(ctx->NSx, n2), 0, op64(a, n2), 0, op64(b, n2));
-    // polish to full FP64 convergence (quadratic from FP32 quality: two or
-    // three sweeps)
-    return eigh_batched(s, TY_C64, n, b, n2, U, n2, W, n, 4 * nb, a, n2);
+    EighWork wk;
+    wk.A32 = (cf *)ctx->Fm32;
+    wk.U32 = (cf *)ctx->U32;
+    wk.w32 = ctx->W32;
+    wk.X = ctx->NSx;
+    wk.Xn = ctx->NSy;
+    wk.T = ctx->NSz;
+    wk.S = ctx->NSs;
+    wk.R = ctx->NSr;
+    wk.E = ctx->NSe;
+    return eigh_mixed(s, n, 4 * nb, ctx->Fm, U, W, wk);
 }
 
 // G = QL DbL^-1 [DbR^-1 QR^H QL DbL^-1 + DsR WR WL^H DsL]^-1 DbR^-1 QR^H (FP64)
@@ -680,6 +675,9 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
     DA(ctx->NSx, (size_t)nb * 4 * n2);
     DA(ctx->NSy, (size_t)nb * 4 * n2);
     DA(ctx->NSz, (size_t)nb * 4 * n2);
+    DA(ctx->NSs, (size_t)nb * 4 * n2);
+    DA(ctx->NSr, (size_t)nb * 4 * n2);
+    DA(ctx->NSe, (size_t)nb * 4 * n2);
     DA(ctx->always, nb);
     DA(ctx->tq, (size_t)nb * 4 * nq);
     DA(ctx->X1, (size_t)nb * NN);

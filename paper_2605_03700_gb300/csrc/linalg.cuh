@@ -32,6 +32,16 @@ void gemm_prof_stop(double *ms, long long *launches, double *flops);
 int eigh_batched(cudaStream_t st, int prec, int n, const void *H, long long sH, void *U,
                  long long sU, void *w, long long sw, int batch, const void *V0 = nullptr,
                  long long sV0 = 0, double tol = 0.0);
+// work buffers of eigh_mixed, each batch x n^2 (A32, U32: FP32; w32: batch x n)
+struct EighWork {
+    cf *A32, *U32;
+    float *w32;
+    cd *X, *Xn, *T, *S, *R, *E;
+};
+// FP64-accurate eigenpairs of batch Hermitian n x n matrices (dense, stride
+// n^2): FP32 Jacobi, two FP64 refinement steps, FP64 Jacobi safety net
+int eigh_mixed(cudaStream_t st, int n, int batch, const cd *A, cd *U, double *w,
+               const EighWork &wk, double tol32 = 1e-10);
 int lu_batched(cudaStream_t st, int n, cd *A, long long sA, int *piv, long long spiv, cd *logdet,
                int batch);
 int rdiv_batched(cudaStream_t st, int prec, int n, const cd *G, long long sG, const cd *LU,
