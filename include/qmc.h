@@ -101,6 +101,9 @@ int qmc_default_opts(qmc_opts *o);
  *   N_phi      flux quanta; torus: N_phi orbitals and momenta
  *              {q in Z^2 : exp(-2 pi |q|^2/(4 N_phi)) > 0.01}; sphere:
  *              opts.n_orb_sphere orbitals (default N_phi + 1), N_q = n_orb^2
+ *              momenta (l, m), l < n_orb.  The orbital count must lie in
+ *              [2, 56] (the LU, QR and eigensolver kernels keep one matrix in
+ *              one CTA's shared memory); QMC_ERR_ARG otherwise
  *   beta, dtau inverse temperature and Trotter step; L = beta/dtau must be an
  *              integer (QMC_ERR_ARG otherwise)
  *   coupling   u, anisotropy alpha (Results, "Universal phase diagram"); the

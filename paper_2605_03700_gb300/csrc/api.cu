@@ -515,22 +515,40 @@ static size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy)
 {
     const int n = ctx->n, nb = ctx->nb;
-    // torus momenta: q_y outer, q_x inner, exp(-2 pi |q|^2/(4 N_phi)) > 0.01
+    // momenta.  Torus: q_y outer, q_x inner, exp(-2 pi |q|^2/(4 N_phi)) > 0.01,
+    // stored as (q_x, q_y).  Sphere: (l, m), l = 0..n_orb-1, m = -l..l, at
+    // index l^2 + l + m.
+    const bool sph = ctx->geom == QMC_SPHERE;
     std::vector<int> qxy;
-    int R = (int)floor(sqrt((double)(int)(4.0 * n * log(100.0) / (2.0 * M_PI)))) + 2;
-    for (int qy = -R; qy <= R; ++qy)
-        for (int qx = -R; qx <= R; ++qx)
-            if (exp(-2.0 * M_PI * (double)(qx * qx + qy * qy) / (4.0 * n)) > 0.01) {
-                qxy.push_back(qx);
-                qxy.push_back(qy);
+    if (sph) {
+        for (int l = 0; l < n; ++l)
+            for (int m = -l; m <= l; ++m) {
+                qxy.push_back(l);
+                qxy.push_back(m);
             }
+    } else {
+        int R = (int)floor(sqrt((double)(int)(4.0 * n * log(100.0) / (2.0 * M_PI)))) + 2;
+        for (int qy = -R; qy <= R; ++qy)
+            for (int qx = -R; qx <= R; ++qx)
+                if (exp(-2.0 * M_PI * (double)(qx * qx + qy * qy) / (4.0 * n)) > 0.01) {
+                    qxy.push_back(qx);
+                    qxy.push_back(qy);
+                }
+    }
     const int nq = (int)qxy.size() / 2;
     ctx->nq = nq;
     ctx->nf = 4 * nq;
     std::vector<int> partner(nq), fkind(nq), frA(nq), frB(nq), fq(nq), fk(nq);
-    for (int q = 0; q < nq; ++q)
-        for (int p = 0; p < nq; ++p)
-            if (qxy[2 * p] == -qxy[2 * q] && qxy[2 * p + 1] == -qxy[2 * q + 1]) partner[q] = p;
+    // partner: -q on the torus, (l, -m) on the sphere (n_q^dagger = n_qbar)
+    for (int q = 0; q < nq; ++q) {
+        if (sph) {
+            const int l = qxy[2 * q], m = qxy[2 * q + 1];
+            partner[q] = l * l + l - m;
+        } else {
+            for (int p = 0; p < nq; ++p)
+                if (qxy[2 * p] == -qxy[2 * q] && qxy[2 * p + 1] == -qxy[2 * q + 1]) partner[q] = p;
+        }
+    }
     int rr = 0;
     for (int q = 0; q < nq; ++q) {
         int p = partner[q];
@@ -546,11 +564,18 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
             rr += 2;
         }
     }
-    // assembly lists: entry (k, (k - q_y) mod n) <- q, q ascending
+    // assembly lists, q ascending: torus entry (k, (k - q_y) mod n) <- q;
+    // sphere entry (r, r + m) <- q where 0 <= r + m < n
     std::vector<std::vector<int>> lists((size_t)n * n);
     for (int q = 0; q < nq; ++q)
         for (int k = 0; k < n; ++k) {
-            int c = ((k - qxy[2 * q + 1]) % n + n) % n;
+            int c;
+            if (sph) {
+                c = k + qxy[2 * q + 1];
+                if (c < 0 || c >= n) continue;
+            } else {
+                c = ((k - qxy[2 * q + 1]) % n + n) % n;
+            }
             lists[(size_t)k * n + c].push_back(q);
         }
     std::vector<int> aptr((size_t)n * n + 1, 0), aq;
@@ -561,10 +586,12 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
     aptr[(size_t)n * n] = (int)aq.size();
     ctx->q0 = -1;
     ctx->dq.clear();
+    // q = 0 and the smallest non-zero momenta of the correlation ratio:
+    // torus (+-1, 0), (0, +-1); sphere l = 1, all m
     for (int q = 0; q < nq; ++q) {
         int x = qxy[2 * q], y = qxy[2 * q + 1];
         if (x == 0 && y == 0) ctx->q0 = q;
-        if (abs(x) + abs(y) == 1) ctx->dq.push_back(q);
+        if (sph ? x == 1 : abs(x) + abs(y) == 1) ctx->dq.push_back(q);
     }
     // couplings per chain
     ctx->u.resize(nb);
@@ -733,7 +760,8 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
         CK(cudaMemcpy(ctx->eps, eps.data(), sizeof(double) * nb, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(ctx->eps_used, eps.data(), sizeof(double) * nb, cudaMemcpyHostToDevice));
     }
-    launch_ff_torus(s, n, nq, ctx->qxy, ctx->ff_val, ctx->ff_col, ctx->trF);
+    if (sph) launch_ff_sphere(s, n, ctx->ff_val, ctx->ff_col, ctx->trF);
+    else launch_ff_torus(s, n, nq, ctx->qxy, ctx->ff_val, ctx->ff_col, ctx->trF);
     launch_init_phi(s, nb, ctx->L, nf, ctx->keys, ctx->phi);
     // GEMM tile autotuning for this matrix size and batch (scratch operands)
     {
@@ -826,11 +854,14 @@ int qmc_create(qmc_ctx **out, int geometry, int N_phi, double beta, double dtau,
     if (opts) ctx->o = *opts;
     else qmc_default_opts(&ctx->o);
     int code = QMC_OK;
-    if (geometry != QMC_TORUS) {
-        ctx->err = "only the torus geometry is available on the GPU path";
+    const int norb = geometry == QMC_SPHERE
+                         ? (ctx->o.n_orb_sphere > 0 ? ctx->o.n_orb_sphere : N_phi + 1)
+                         : N_phi;
+    if (geometry != QMC_TORUS && geometry != QMC_SPHERE) {
+        ctx->err = "geometry must be QMC_TORUS or QMC_SPHERE";
         code = QMC_ERR_ARG;
-    } else if (N_phi < 2 || N_phi > 56) {
-        ctx->err = "N_phi must be in [2, 56] (single-block shared-memory kernels)";
+    } else if (N_phi < 1 || norb < 2 || norb > 56) {
+        ctx->err = "orbital count must be in [2, 56] (single-block shared-memory kernels)";
         code = QMC_ERR_ARG;
     } else if (!(beta > 0) || !(dtau > 0)) {
         ctx->err = "beta and dtau must be positive";
@@ -847,10 +878,10 @@ int qmc_create(qmc_ctx **out, int geometry, int N_phi, double beta, double dtau,
         } else {
             ctx->geom = geometry;
             ctx->nphi = N_phi;
-            ctx->n = N_phi;
-            ctx->N = 2 * N_phi;
+            ctx->n = norb;
+            ctx->N = 2 * norb;
             ctx->NN = (long long)ctx->N * ctx->N;
-            ctx->n2 = (long long)N_phi * N_phi;
+            ctx->n2 = (long long)norb * norb;
             ctx->L = (int)Lr;
             ctx->nb = ctx->o.n_chains;
             ctx->beta = beta;

@@ -28,6 +28,150 @@ __global__ void k_ff_torus(int n, int nq, const int *qxy, cd *val, int *col)
     col[e] = ((k0 - qy) % n + n) % n;
 }
 
+// Double-double numbers (value hi + lo, |lo| <= ulp(hi)/2, about 32 digits),
+// from the error-free transformations of Knuth (TwoSum) and Dekker
+// (exact product, here through one fused multiply-add), with Dekker's
+// normalisation; used where a recursion amplifies FP64 rounding.
+struct dd {
+    double hi, lo;
+};
+__device__ __forceinline__ dd dd_fast2(double a, double b)  // needs |a| >= |b|
+{
+    double s = a + b;
+    return dd{s, b - (s - a)};
+}
+__device__ __forceinline__ dd dd_two_sum(double a, double b)
+{
+    double s = a + b, v = s - a;
+    return dd{s, (a - (s - v)) + (b - v)};
+}
+__device__ __forceinline__ dd dd_add(dd x, dd y)
+{
+    dd s = dd_two_sum(x.hi, y.hi), t = dd_two_sum(x.lo, y.lo);
+    s.lo += t.hi;
+    s = dd_fast2(s.hi, s.lo);
+    s.lo += t.lo;
+    return dd_fast2(s.hi, s.lo);
+}
+__device__ __forceinline__ dd dd_neg(dd x) { return dd{-x.hi, -x.lo}; }
+__device__ __forceinline__ dd dd_mul(dd x, dd y)
+{
+    double p = x.hi * y.hi;
+    double e = fma(x.hi, y.hi, -p);
+    e += x.hi * y.lo + x.lo * y.hi;
+    return dd_fast2(p, e);
+}
+__device__ __forceinline__ dd dd_div(dd x, dd y)
+{
+    double q1 = x.hi / y.hi;
+    dd r = dd_add(x, dd_neg(dd_mul(y, dd{q1, 0.0})));
+    double q2 = r.hi / y.hi;
+    r = dd_add(r, dd_neg(dd_mul(y, dd{q2, 0.0})));
+    double q3 = r.hi / y.hi;
+    return dd_add(dd_fast2(q1, q2), dd{q3, 0.0});
+}
+// square root of a non-negative integer below 2^52: one Newton step from
+// the FP64 root, with the residual d - s^2 formed exactly
+__device__ __forceinline__ dd dd_sqrt_int(long long d)
+{
+    if (d <= 0) return dd{0.0, 0.0};
+    double x = (double)d, s = sqrt(x);
+    double p = s * s, e = fma(s, s, -p);
+    double r = (x - p) - e;
+    return dd_fast2(s, r / (2.0 * s));
+}
+
+// Sphere form factors (Methods, Eq. sphere_density_operator): for q = (l, m),
+// index q = l^2 + l + m, the n_orb = 2s + 1 LLL orbitals m_k = r - s (row r)
+// and m >= 0, F_q[r, r + m] = (-1)^{2s} sqrt(2l + 1) / 2
+//   x <s m_k; l m | s m_k + m> <s s; l 0 | s s>,
+// which is the paper's (2s + 1) sqrt(2l + 1) / 2 (-1)^{s + m_k + m} times its
+// two 3j symbols, rewritten with (j1 j2 j3; m1 m2 m3) = (-1)^{j1 - j2 - m3}
+// <j1 m1; j2 m2 | j3 -m3> / sqrt(2 j3 + 1) and the reflection symmetry of the
+// Clebsch-Gordan coefficients.  F_{l,-m} = F_{l,m}^dagger (the rotation-
+// invariant pairing of n_{l,m} with its adjoint).
+// The coefficients <s m1; l m2 | s M> come from the highest-weight state
+// (J+ |s s> = 0 fixes the ratios along m1 + m2 = s; Condon-Shortley sign:
+// positive at m1 = s) and the lowering operator J- = j1- + j2-, one M at a
+// time: no alternating factorial sums.  The lowering steps amplify rounding
+// (FP64 alone loses all digits by n_orb ~ 56), so they run in double-double.
+// One CTA per l, one thread per m1 (n_orb <= 64).
+__global__ void __launch_bounds__(64) k_ff_sphere(int n, cd *val, int *col)
+{
+    __shared__ dd cbuf[2][64];
+    __shared__ dd c0;
+    const int l = blockIdx.x, i1 = threadIdx.x, S2 = n - 1;  // S2 = 2s
+    const int q0 = l * l;                                      // q(l, -l)
+    const bool act = i1 <= S2;
+    // rows without an entry keep col = -1
+    for (int e = i1; e < (2 * l + 1) * n; e += blockDim.x) {
+        val[(long long)q0 * n + e] = cmk(0, 0);
+        col[(long long)q0 * n + e] = -1;
+    }
+    // highest weight M = s: m1 from s - l to s (i1 = S2 - l .. S2), m2 = s - m1;
+    // c(m1 + 1) a(l, m2 - 1) = -c(m1) a(s, m1), a(j, m) = sqrt((j - m)(j + m + 1))
+    if (i1 == 0) {
+        dd norm = {0.0, 0.0};
+        dd c = {1.0, 0.0};
+        for (int k = S2 - l; k <= S2; ++k) {
+            if (k > S2 - l) {
+                const int km = k - 1;    // i1 index of the previous m1
+                const int m2n = S2 - k;  // m2 of the new entry
+                const dd a_s = dd_sqrt_int((long long)(S2 - km) * (km + 1));
+                const dd a_l = dd_sqrt_int((long long)(l - m2n) * (l + m2n + 1));
+                c = dd_neg(dd_div(dd_mul(c, a_s), a_l));
+            }
+            cbuf[0][k] = c;
+            norm = dd_add(norm, dd_mul(c, c));
+        }
+        // c is now the m1 = s entry: normalise and make it positive
+        // 1/sqrt(norm): FP64 start and one Newton step f <- f (3 - norm f^2) / 2
+        dd f = {1.0 / sqrt(norm.hi), 0.0};
+        f = dd_mul(f, dd_add(dd{1.5, 0.0}, dd_neg(dd_mul(dd{0.5, 0.0}, dd_mul(norm, dd_mul(f, f))))));
+        if (c.hi < 0) f = dd_neg(f);
+        for (int k = S2 - l; k <= S2; ++k) cbuf[0][k] = dd_mul(cbuf[0][k], f);
+        c0 = cbuf[0][S2];
+    }
+    __syncthreads();
+    const double sgn = (S2 & 1) ? -1.0 : 1.0;
+    const dd pref = dd_mul(dd{sgn * 0.5, 0.0}, dd_mul(dd_sqrt_int(2 * l + 1), c0));
+    int cur = 0;
+    for (int iM = S2; iM >= 0; --iM) {  // M = iM - s
+        // emit <s m1; l m | s M> for this thread's m1 with 0 <= m <= l
+        const int m = iM - i1;
+        if (act && m >= 0 && m <= l) {
+            const dd v = dd_mul(pref, cbuf[cur][i1]);
+            const double vd = v.hi + v.lo;
+            const int r = i1, c = iM;
+            val[(long long)(q0 + l + m) * n + r] = cmk(vd, 0);
+            col[(long long)(q0 + l + m) * n + r] = c;
+            if (m > 0) {
+                val[(long long)(q0 + l - m) * n + c] = cmk(vd, 0);
+                col[(long long)(q0 + l - m) * n + c] = r;
+            }
+        }
+        if (iM == 0) break;
+        // lower: c'(m1) = [c(m1 + 1) b(s, m1 + 1) + c(m1) b(l, M - m1)] / b(s, M),
+        // b(j, m) = sqrt((j + m)(j - m + 1)); entries outside |m2| <= l are 0
+        dd v = {0.0, 0.0};
+        if (act) {
+            const int m2n = iM - 1 - i1;  // m2 of the new entry
+            if (m2n >= -l && m2n <= l) {
+                if (i1 + 1 <= S2 && iM - (i1 + 1) >= -l && iM - (i1 + 1) <= l)
+                    v = dd_mul(cbuf[cur][i1 + 1], dd_sqrt_int((long long)(i1 + 1) * (S2 - i1)));
+                const int m2o = iM - i1;
+                if (m2o >= -l && m2o <= l)
+                    v = dd_add(v, dd_mul(cbuf[cur][i1],
+                                         dd_sqrt_int((long long)(l + m2o) * (l - m2o + 1))));
+                v = dd_div(v, dd_sqrt_int((long long)iM * (S2 - iM + 1)));
+            }
+            cbuf[cur ^ 1][i1] = v;
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+}
+
 // Tr F_q (the channel-0 background is b_q = 2 Tr F_q)
 __global__ void k_trF(int n, int nq, const cd *val, const int *col, cd *trF)
 {
@@ -565,6 +709,12 @@ void launch_ff_torus(cudaStream_t s, int n, int nq, const int *qxy, cd *val, int
 {
     k_ff_torus<<<cdiv_up(nq * n, 256), 256, 0, s>>>(n, nq, qxy, val, col);
     k_trF<<<cdiv_up(nq, 128), 128, 0, s>>>(n, nq, val, col, trF);
+    QMC_COUNT(2);
+}
+void launch_ff_sphere(cudaStream_t s, int n, cd *val, int *col, cd *trF)
+{
+    k_ff_sphere<<<n, 64, 0, s>>>(n, val, col);
+    k_trF<<<cdiv_up(n * n, 128), 128, 0, s>>>(n, n * n, val, col, trF);
     QMC_COUNT(2);
 }
 void launch_init_phi(cudaStream_t s, int nb, int L, int nf, const uint32_t *keys, double *phi)

@@ -48,6 +48,7 @@ struct MeasP {
 };
 
 void launch_ff_torus(cudaStream_t s, int n, int nq, const int *qxy, cd *val, int *col, cd *trF);
+void launch_ff_sphere(cudaStream_t s, int n, cd *val, int *col, cd *trF);
 void launch_init_phi(cudaStream_t s, int nb, int L, int nf, const uint32_t *keys, double *phi);
 void launch_assemble(cudaStream_t s, int prec, int nb, int n, int nq, const double *phi,
                      long long phi_cs, const int *fkind, const int *frA, const int *frB,

@@ -145,9 +145,11 @@ class Chain:
     def __init__(self, geometry, N_phi, beta, dtau, coupling, anisotropy=0.0, seed=0, *,
                  n_chains=1, couplings=None, anisotropies=None, seeds=None, n_stab=10,
                  eps0=0.5, deps=0.1, r0=0.574, n_adapt=-1, series_capacity=4096,
-                 trace_capacity=0, stab_tol=1e-6, sign_tol=1e-6, precision=0, stream=None):
+                 trace_capacity=0, stab_tol=1e-6, sign_tol=1e-6, precision=0, n_orb_sphere=0,
+                 stream=None):
         o = qmc_default_opts()
         o.n_stab = n_stab
+        o.n_orb_sphere = n_orb_sphere
         o.precision = precision
         o.eps0, o.deps, o.r0, o.n_adapt = eps0, deps, r0, n_adapt
         o.n_chains = n_chains

@@ -1,0 +1,91 @@
+"""Parity of the CUDA sweep on the sphere (monopole-harmonic form factors,
+Methods Eq. sphere_density_operator) with the FP64 CPU oracle.
+
+The GPU builds the form factors from Clebsch-Gordan coefficients by the
+lowering-operator recursion in double-double arithmetic; the oracle from the
+Racah formula in exact rational arithmetic.  Same seeds and Philox streams:
+identical accept/reject decisions, log ratios within 1e-10 relative to
+max(1, |log R|) at the paper's sphere couplings, G and the measurements
+within 1e-9; propagators of the same fields equal to 1e-12 up to 56 orbitals, where
+an FP64 recursion would already have lost every digit.
+"""
+import numpy as np
+import pytest
+
+from oracle import model as M
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qmc():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2605_03700_gb300 import build
+    build.build()
+    import paper_2605_03700_gb300 as P
+    return P
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+# (orbitals, beta, sweeps, coupling u, anisotropy, bound on the relative log-ratio
+# difference).  The sphere form factors are ~15x the torus ones, so u = 1.2
+# makes B far worse conditioned: G(0) of identical propagators (1e-14) already
+# differs by ~1e-12 between two FP64 evaluation orders, and the ratios by
+# ~1e-8.  The paper's sphere runs use u <= 0.3, where the bound is 1e-10.
+@pytest.mark.parametrize("norb,beta,nsw,u,aniso,tol", [(3, 2.0, 100, 0.3, 0.0, 1e-10),
+                                                       (4, 1.0, 60, 0.3, 0.15, 1e-10),
+                                                       (7, 0.6, 12, 0.3, -0.1, 1e-10),
+                                                       (7, 0.6, 12, 1.2, -0.1, 1e-7)])
+def test_sphere_decision_identical(qmc, norb, beta, nsw, u, aniso, tol):
+    L = int(round(beta / 0.1))
+    g = qmc.Chain(qmc.QMC_SPHERE, norb - 1, beta, 0.1, u, aniso, 3, n_stab=5,
+                  trace_capacity=nsw * L)
+    assert g.n_orb == norb and g.n_q == norb * norb
+    g.sweep(nsw)
+    g.sync()
+    o = O.Chain(M.SPHERE, norb, beta, 0.1, u, aniso, 3, n_stab=5)
+    o.enable_trace(nsw * L)
+    obs_o = o.sweep(nsw)
+    tg, to = g.trace(0), o.trace()
+    assert len(tg) == len(to) == nsw * L
+    assert np.array_equal(tg[:, 6], to[:, 6]), "accept decisions differ"
+    assert 0 < tg[:, 6].sum() < len(tg)
+    d = np.abs(tg[:, 2] - to[:, 2]) / np.maximum(1.0, np.abs(to[:, 2]))
+    assert d.max() < tol
+    assert np.abs(np.sin(tg[:, 3])).max() < 100 * tol   # the bracket ratio stays real
+    assert _rel(g.green(0), o.green()) < 10 * tol
+    assert np.abs(g.fields(0) - o.phi()).max() < 10 * tol
+    # measurements (S^i at l = 0 and l = 1, m^2, R, E) agree sweep by sweep
+    obs_g = g.series()[0]
+    assert obs_g.shape == obs_o.shape
+    for col in range(13):
+        assert np.abs(obs_g[:, col] - obs_o[:, col]).max() < 10 * tol * max(1, np.abs(obs_o[:, col]).max())
+    assert np.array_equal(obs_g[:, 17], obs_o[:, 17])
+
+
+@pytest.mark.parametrize("norb", [24, 56])
+def test_sphere_propagators_large_orbital_counts(qmc, norb):
+    """Propagators of identical fields: the GPU form factors carry the exact
+    rational values of the oracle to rounding."""
+    g = qmc.Chain(qmc.QMC_SPHERE, norb - 1, 0.2, 0.1, 1.0, 0.0, 5, n_stab=2)
+    m = M.Model(M.SPHERE, norb)
+    o = O.Chain(M.SPHERE, norb, 0.2, 0.1, 1.0, 0.0, 5, n_stab=2, model=m)
+    assert np.abs(g.fields(0) - o.phi()).max() < 1e-13
+    for t in (1, 2):
+        B, Bi = g.propagator(t)
+        Bo, Boi = o.B(t)
+        assert _rel(B, Bo) < 1e-12 and _rel(Bi, Boi) < 1e-12
+    assert _rel(g.green(0), o.green()) < 1e-10
+
+
+def test_sphere_orbital_count_option_and_limits(qmc):
+    g = qmc.Chain(qmc.QMC_SPHERE, 5, 0.2, 0.1, 1.0, n_orb_sphere=4)
+    assert g.n_orb == 4 and g.n_q == 16
+    g.close()
+    with pytest.raises(qmc.QMCError):
+        qmc.Chain(qmc.QMC_SPHERE, 56, 0.2, 0.1, 1.0)   # 57 orbitals
