@@ -133,6 +133,31 @@ int qmc_set_stream(qmc_ctx *ctx, void *stream);
  * the device are reported by the next synchronising call. */
 int qmc_sweep(qmc_ctx *ctx, int n_sweeps);
 
+/* Same as qmc_sweep, through a CUDA graph: the first call captures one sweep
+ * of every chain (all kernels, device copies and the measurement record) on a
+ * private stream and instantiates it; every sweep is then one graph launch on
+ * the context's stream.  The sweep number, the Langevin-step adaptation and
+ * the series slot live in device memory, so each replay draws its own Philox
+ * counters and writes its own record: results are identical to qmc_sweep.
+ * Capture errors return QMC_ERR_CUDA and leave the context usable with
+ * qmc_sweep. */
+int qmc_sweep_graph(qmc_ctx *ctx, int n_sweeps);
+
+/* Batched chains of different sizes (BASELINE pattern, not in the paper): a
+ * group sweeps several contexts -- any mix of geometry, orbital count,
+ * couplings and precision -- as one CUDA graph per sweep.  Each member's
+ * sweep is captured on its own branch of the graph, so kernels of different
+ * matrix sizes run concurrently and fill the GPU where one size alone cannot.
+ * The members stay owned by the caller and must outlive the group; the graph
+ * is ordered after work already on each member's stream and before work
+ * enqueued there later.  n_members >= 1, no member twice (QMC_ERR_ARG). */
+typedef struct qmc_group qmc_group;
+int qmc_group_create(qmc_group **out, qmc_ctx *const *members, int n_members);
+int qmc_group_sweep(qmc_group *g, int n_sweeps);
+/* Wait for the group's work; the first member error (as qmc_sync) or 0. */
+int qmc_group_sync(qmc_group *g);
+int qmc_group_destroy(qmc_group *g);
+
 /* Wait for the context's stream and report device-side errors
  * (QMC_ERR_UNSTABLE, QMC_ERR_SIGN, QMC_ERR_NONFINITE). */
 int qmc_sync(qmc_ctx *ctx);

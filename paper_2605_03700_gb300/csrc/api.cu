@@ -53,6 +53,10 @@ struct qmc_ctx {
     cudaStream_t st = 0;
     uint32_t sweep = 0;
     long long series_n = 0;
+    uint32_t *ctr = nullptr;             // device: sweep number, series slot (QMC_CTR_*)
+    cudaStream_t cap_st = nullptr;       // private stream the sweep graph is captured on
+    cudaGraphExec_t gexec = nullptr;     // one captured sweep of all chains
+    long long graph_kernels = 0;         // kernels in that graph
     std::string err;
     std::vector<void *> allocs;
 
@@ -332,7 +336,7 @@ static int update_slice(qmc_ctx *ctx, int t)
                      ctx->Dgi, ctx->lamG, ctx->DgG, ctx->DgiG);
     gradient(ctx, ctx->G, ctx->V, ctx->T, ctx->lamG, ctx->DgG, ctx->DgiG, phi_s, phi_cs, ctx->grad);
     launch_propose(s, nb, nf, phi_s, phi_cs, ctx->grad, ctx->eps, ctx->keys, (uint32_t)s0,
-                   ctx->sweep, ctx->phip);
+                   ctx->ctr, ctx->phip);
     // proposal factors and propagators
     if (eig_of_fields(ctx, ctx->phip, nf, ctx->Up, ctx->Wp)) {
         ctx->err = "eigensolver: unsupported size";
@@ -370,7 +374,7 @@ static int update_slice(qmc_ctx *ctx, int t)
     ap.frB = ctx->frB;
     ap.keys = ctx->keys;
     ap.slice = t;
-    ap.sweep = ctx->sweep;
+    ap.ctr = ctx->ctr;
     ap.flag = ctx->flag;
     ap.st = ctx->stats;
     ap.errf = ctx->errf;
@@ -420,7 +424,10 @@ static int restabilise(qmc_ctx *ctx, int k, int prev, int t)
     return 0;
 }
 
-static void measure_into(qmc_ctx *ctx, double *out, long long out_cs)
+// the measurement record of every chain: at out + c * out_cs, or, with the
+// device counters, in slot ctr[QMC_CTR_SERIES] % slots of that ring
+static void measure_into(qmc_ctx *ctx, double *out, long long out_cs,
+                         const uint32_t *ctr = nullptr, int slots = 1)
 {
     MeasP mp;
     mp.nq = ctx->nq;
@@ -435,13 +442,17 @@ static void measure_into(qmc_ctx *ctx, double *out, long long out_cs)
     for (int i = 0; i < 8; ++i) mp.dq[i] = i < mp.ndq ? ctx->dq[i] : 0;
     mp.out = out;
     mp.out_cs = out_cs;
+    mp.ctr = ctr;
+    mp.slots = slots;
     mp.st = ctx->stats;
     mp.eps_used = ctx->eps_used;
     launch_measure(ctx->st, ctx->nb, ctx->n, ctx->nq, ctx->G, ctx->ff_val, ctx->ff_col,
                    ctx->partner, ctx->ax, mp);
 }
 
-static int one_sweep(qmc_ctx *ctx)
+// enqueue one sweep of every chain on ctx->st; nothing on the host depends on
+// the sweep number, so the same launches replay from a captured graph
+static int enqueue_sweep(qmc_ctx *ctx)
 {
     int r = build_left_stack(ctx);
     if (r) return r;
@@ -466,13 +477,9 @@ static int one_sweep(qmc_ctx *ctx)
         }
     }
     const int cap = ctx->o.series_capacity;
-    long long idx = ctx->series_n % cap;
-    measure_into(ctx, ctx->series + idx * QMC_NOBS, (long long)cap * QMC_NOBS);
-    int adapt = ctx->o.n_adapt < 0 || (int)ctx->sweep < ctx->o.n_adapt;
-    launch_end_sweep(ctx->st, nb, ctx->L, adapt, ctx->o.r0, ctx->o.deps, ctx->eps, ctx->eps_used,
-                     ctx->stats);
-    ctx->sweep++;
-    ctx->series_n++;
+    measure_into(ctx, ctx->series, (long long)cap * QMC_NOBS, ctx->ctr, cap);
+    launch_end_sweep(ctx->st, nb, ctx->L, ctx->o.n_adapt, ctx->ctr, ctx->o.r0, ctx->o.deps,
+                     ctx->eps, ctx->eps_used, ctx->stats);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         ctx->err = std::string("kernel launch: ") + cudaGetErrorString(e);
@@ -593,6 +600,7 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
         if (x == 0 && y == 0) ctx->q0 = q;
         if (sph ? x == 1 : abs(x) + abs(y) == 1) ctx->dq.push_back(q);
     }
+    linalg_init();
     // couplings per chain
     ctx->u.resize(nb);
     ctx->anis.resize(nb);
@@ -630,6 +638,7 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
     const long long NN = ctx->NN, n2 = ctx->n2, L = ctx->L;
     const int nf = ctx->nf;
     // device allocations
+    DA(ctx->ctr, QMC_CTR_N);
     DA(ctx->qxy, 2 * nq);
     DA(ctx->ff_val, (size_t)nq * n);
     DA(ctx->ff_col, (size_t)nq * n);
@@ -910,6 +919,8 @@ int qmc_destroy(qmc_ctx *ctx)
         if (ctx->st) cudaStreamSynchronize(ctx->st);
         else cudaDeviceSynchronize();
     }
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);
     for (void *p : ctx->allocs) cudaFree(p);
     delete ctx;
     return QMC_OK;
@@ -926,9 +937,171 @@ int qmc_sweep(qmc_ctx *ctx, int n_sweeps)
 {
     if (!ctx || n_sweeps < 0) return QMC_ERR_ARG;
     for (int i = 0; i < n_sweeps; ++i) {
-        int r = one_sweep(ctx);
+        int r = enqueue_sweep(ctx);
+        if (r) return r;
+        ctx->sweep++;
+        ctx->series_n++;
+    }
+    return QMC_OK;
+}
+
+// capture enqueue_sweep of each context on its own branch of one graph:
+// origin -> fork to every member's capture stream -> join on origin
+static int capture_sweeps(qmc_ctx *const *m, int nm, cudaStream_t origin, cudaGraphExec_t *exec,
+                          long long *kernels, std::string *err)
+{
+    const bool prof = gemm_prof_enable(false);
+    const long long k0 = g_qmc_launches;
+    std::vector<cudaStream_t> saved(nm);
+    std::vector<cudaEvent_t> ev(nm + 1, nullptr);
+    cudaGraph_t graph = nullptr;
+    int r = QMC_OK;
+    for (auto &e : ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    if (cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        *err = "cudaStreamBeginCapture failed";
+        r = QMC_ERR_CUDA;
+    } else {
+        cudaEventRecord(ev[nm], origin);
+        for (int i = 0; i < nm && r == QMC_OK; ++i) {
+            saved[i] = m[i]->st;
+            m[i]->st = m[i]->cap_st;
+            cudaStreamWaitEvent(m[i]->cap_st, ev[nm], 0);
+            r = enqueue_sweep(m[i]);
+            if (r) *err = m[i]->err;
+            cudaEventRecord(ev[i], m[i]->cap_st);
+            cudaStreamWaitEvent(origin, ev[i], 0);
+            m[i]->st = saved[i];
+        }
+        cudaError_t e = cudaStreamEndCapture(origin, &graph);
+        if (r == QMC_OK && e != cudaSuccess) {
+            *err = std::string("stream capture: ") + cudaGetErrorString(e);
+            r = QMC_ERR_CUDA;
+        }
+    }
+    if (r == QMC_OK && cudaGraphInstantiate(exec, graph, 0) != cudaSuccess) {
+        *err = "cudaGraphInstantiate failed";
+        r = QMC_ERR_CUDA;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    for (auto &e : ev) cudaEventDestroy(e);
+    *kernels = g_qmc_launches - k0;
+    g_qmc_launches = k0;
+    gemm_prof_enable(prof);
+    cudaGetLastError();
+    return r;
+}
+
+int qmc_sweep_graph(qmc_ctx *ctx, int n_sweeps)
+{
+    if (!ctx || n_sweeps < 0) return QMC_ERR_ARG;
+    if (n_sweeps == 0) return QMC_OK;
+    if (!ctx->gexec) {
+        qmc_ctx *one[1] = {ctx};
+        if (!ctx->cap_st) CK(cudaStreamCreateWithFlags(&ctx->cap_st, cudaStreamNonBlocking));
+        int r = capture_sweeps(one, 1, ctx->cap_st, &ctx->gexec, &ctx->graph_kernels, &ctx->err);
         if (r) return r;
     }
+    for (int i = 0; i < n_sweeps; ++i) {
+        CK(cudaGraphLaunch(ctx->gexec, ctx->st));
+        g_qmc_launches += ctx->graph_kernels;
+        ctx->sweep++;
+        ctx->series_n++;
+    }
+    return QMC_OK;
+}
+
+// ------------------------------------------------------------- groups -----
+struct qmc_group {
+    std::vector<qmc_ctx *> m;
+    cudaStream_t origin = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    long long graph_kernels = 0;
+    std::vector<cudaEvent_t> ev;
+    std::string err;
+};
+
+int qmc_group_create(qmc_group **out, qmc_ctx *const *members, int n_members)
+{
+    if (!out || !members || n_members < 1) return QMC_ERR_ARG;
+    *out = nullptr;
+    for (int i = 0; i < n_members; ++i) {
+        if (!members[i]) return QMC_ERR_ARG;
+        for (int j = 0; j < i; ++j)
+            if (members[j] == members[i]) return QMC_ERR_ARG;
+    }
+    qmc_group *g = new qmc_group();
+    g->m.assign(members, members + n_members);
+    cudaError_t e = cudaStreamCreateWithFlags(&g->origin, cudaStreamNonBlocking);
+    for (qmc_ctx *c : g->m)
+        if (e == cudaSuccess && !c->cap_st) e = cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking);
+    g->ev.resize(n_members + 1, nullptr);
+    for (auto &v : g->ev)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v, cudaEventDisableTiming);
+    int r = e == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+    if (r == QMC_OK) r = capture_sweeps(g->m.data(), n_members, g->origin, &g->gexec,
+                                        &g->graph_kernels, &g->err);
+    if (r) {
+        if (!g->err.empty()) fprintf(stderr, "qmc_group_create: %s\n", g->err.c_str());
+        qmc_group_destroy(g);
+        return r;
+    }
+    *out = g;
+    return QMC_OK;
+}
+
+#define GK(x)                                                                      \
+    do {                                                                           \
+        cudaError_t e_ = (x);                                                      \
+        if (e_ != cudaSuccess) {                                                   \
+            g->err = std::string(#x) + ": " + cudaGetErrorString(e_);              \
+            return QMC_ERR_CUDA;                                                   \
+        }                                                                          \
+    } while (0)
+
+int qmc_group_sweep(qmc_group *g, int n_sweeps)
+{
+    if (!g || n_sweeps < 0) return QMC_ERR_ARG;
+    if (n_sweeps == 0) return QMC_OK;
+    const int nm = (int)g->m.size();
+    // the graph runs after the work already on every member's stream ...
+    for (int i = 0; i < nm; ++i) {
+        GK(cudaEventRecord(g->ev[i], g->m[i]->st));
+        GK(cudaStreamWaitEvent(g->origin, g->ev[i], 0));
+    }
+    for (int k = 0; k < n_sweeps; ++k) {
+        GK(cudaGraphLaunch(g->gexec, g->origin));
+        g_qmc_launches += g->graph_kernels;
+    }
+    // ... and later work on those streams after the graph
+    GK(cudaEventRecord(g->ev[nm], g->origin));
+    for (int i = 0; i < nm; ++i) {
+        GK(cudaStreamWaitEvent(g->m[i]->st, g->ev[nm], 0));
+        g->m[i]->sweep += n_sweeps;
+        g->m[i]->series_n += n_sweeps;
+    }
+    return QMC_OK;
+}
+
+int qmc_group_sync(qmc_group *g)
+{
+    if (!g) return QMC_ERR_ARG;
+    int first = QMC_OK;
+    for (qmc_ctx *c : g->m) {
+        int r = qmc_sync(c);
+        if (r && first == QMC_OK) first = r;
+    }
+    return first;
+}
+
+int qmc_group_destroy(qmc_group *g)
+{
+    if (!g) return QMC_OK;
+    if (g->origin) cudaStreamSynchronize(g->origin);
+    if (g->gexec) cudaGraphExecDestroy(g->gexec);
+    for (auto &v : g->ev)
+        if (v) cudaEventDestroy(v);
+    if (g->origin) cudaStreamDestroy(g->origin);
+    delete g;
     return QMC_OK;
 }
 

@@ -98,6 +98,13 @@ void gemm_prof_stop(double *ms, long long *launches, double *flops)
     g_gprof.used = 0;
 }
 
+bool gemm_prof_enable(bool on)
+{
+    bool was = g_gprof.on;
+    g_gprof.on = on;
+    return was;
+}
+
 static cudaEvent_t gprof_event()
 {
     if (g_gprof.used == g_gprof.ev.size()) {
@@ -404,22 +411,10 @@ int eigh_batched(cudaStream_t st, int prec, int n, const void *H, long long sH, 
     if (n > 64 || batch <= 0) return batch <= 0 ? 0 : -1;
     if (prec == TY_C64) {
         size_t smem = 2ull * n * n * sizeof(cd);
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_eigh<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 2 * 64 * 64 * 16);
-            attr = true;
-        }
         k_eigh<double><<<batch, 256, smem, st>>>(n, H, sH, U, sU, w, sw, V0, sV0,
                                                  tol > 0 ? tol : 1e-34);
     } else {
         size_t smem = 2ull * n * n * sizeof(cf);
-        static bool attr32 = false;
-        if (!attr32) {
-            cudaFuncSetAttribute(k_eigh<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 2 * 64 * 64 * 8);
-            attr32 = true;
-        }
         k_eigh<float><<<batch, 256, smem, st>>>(n, H, sH, U, sU, w, sw, V0, sV0,
                                                 (float)(tol > 0 ? tol : 1e-10));
     }
@@ -617,11 +612,6 @@ int lu_batched(cudaStream_t st, int n, cd *A, long long sA, int *piv, long long 
 {
     size_t smem = (size_t)n * n * sizeof(cd);
     if (smem > 220 * 1024) return -1;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        attr = true;
-    }
     k_lu<<<batch, 256, smem, st>>>(n, A, sA, piv, spiv, logdet);
     QMC_COUNT(1);
     return 0;
@@ -697,22 +687,10 @@ int rdiv_batched(cudaStream_t st, int prec, int n, const cd *G, long long sG, co
     if (prec == TY_C64) {
         size_t smem = ((size_t)n * n + (size_t)RD_ROWS * n) * sizeof(cd);
         if (smem > 220 * 1024) return -1;
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_rdiv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 220 * 1024);
-            attr = true;
-        }
         k_rdiv<double><<<grid, RD_ROWS * 32, smem, st>>>(n, G, sG, LU, sLU, piv, spiv, X, sX);
     } else {
         size_t smem = ((size_t)n * n + (size_t)RD_ROWS * n) * sizeof(cf);
         if (smem > 220 * 1024) return -1;
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_rdiv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 220 * 1024);
-            attr = true;
-        }
         k_rdiv<float><<<grid, RD_ROWS * 32, smem, st>>>(n, G, sG, LU, sLU, piv, spiv, X, sX);
     }
     QMC_COUNT(1);
@@ -872,12 +850,23 @@ int qrp_batched(cudaStream_t st, int n, const cd *X, long long sX, cd *Q, long l
     int qs = withq <= 220 * 1024;
     size_t smem = qs ? withq : base;
     if (smem > 220 * 1024) return -1;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_qrp, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        attr = true;
-    }
     k_qrp<<<batch, 256, smem, st>>>(n, X, sX, Q, sQ, D, sD, V, sV, qs);
     QMC_COUNT(1);
     return 0;
 }
+
+// ------------------------------------------------------------------ init --
+// dynamic shared-memory limits of the one-CTA-per-matrix kernels, set on the
+// current device (once per context creation, never inside a stream capture)
+void linalg_init()
+{
+    cudaFuncSetAttribute(k_eigh<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         2 * 64 * 64 * 16);
+    cudaFuncSetAttribute(k_eigh<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         2 * 64 * 64 * 8);
+    cudaFuncSetAttribute(k_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(k_rdiv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(k_rdiv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(k_qrp, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+}
+

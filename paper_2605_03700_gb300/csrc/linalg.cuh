@@ -23,7 +23,10 @@ struct GemmP {
     int rc;          // compute type (TY_C64 = FP64, TY_C32 = FP32)
 };
 
+void linalg_init();
 int zgemm(cudaStream_t st, const GemmP &p, int batch);
+// pause (false) or resume the per-launch GEMM timing; returns the previous state
+bool gemm_prof_enable(bool on);
 int gemm_autotune(cudaStream_t st, const GemmP &p, int batch, float *best_ms);
 void gemm_set_tile(int n, int rc, int tile);
 int gemm_get_tile(int n, int rc);

@@ -348,12 +348,13 @@ __global__ void k_grad(int nq, const int *fq, const int *fk, const int *partner,
 // phi' = phi - (eps^2/2) grad + eps xi (Methods, Eq. langevin_proposal with
 // the drift along -grad S)
 __global__ void k_propose(int nf, const double *phi, long long phi_cs, const double *grad,
-                          const double *eps, const uint32_t *keys, uint32_t slice, uint32_t sweep,
-                          double *phip)
+                          const double *eps, const uint32_t *keys, uint32_t slice,
+                          const uint32_t *ctr, double *phip)
 {
     int f = blockIdx.x * blockDim.x + threadIdx.x;
     int c = blockIdx.y;
     if (f >= nf) return;
+    const uint32_t sweep = ctr[QMC_CTR_SWEEP];
     double e = eps[c];
     double xi = rng_normal((uint32_t)f, slice, sweep, RNG_NOISE, keys[2 * c], keys[2 * c + 1]);
     phip[(long long)c * nf + f] = phi[(long long)c * phi_cs + f] -
@@ -398,6 +399,7 @@ QMC_DEVFN double block_sum(double v, double *sh)
 // log R = log det M - (Tr W0' - Tr W0)/2, Tr W0 = 2 alpha_0 sum_q z_q Tr F_q.
 __global__ void __launch_bounds__(256) k_accept(AcceptP p)
 {
+    const uint32_t sweep = p.ctr[QMC_CTR_SWEEP];
     __shared__ double sh[32];
     const int c = blockIdx.x, tid = threadIdx.x;
     const int nq = p.nq, nf = 4 * nq;
@@ -440,7 +442,7 @@ __global__ void __launch_bounds__(256) k_accept(AcceptP p)
         cd w0p = cscale(cmul(a0, cmk(trp, tip)), 2.0);
         cd lr = csub(p.logdet[c], cscale(csub(w0p, w0), 0.5));
         double logA = 2.0 * lr.x - (s0p - s0) - bw / (2 * e * e) + fw / (2 * e * e);
-        u32x4 wv = philox10(u32x4{0u, (uint32_t)(p.slice - 1), p.sweep, (uint32_t)RNG_ACCEPT},
+        u32x4 wv = philox10(u32x4{0u, (uint32_t)(p.slice - 1), sweep, (uint32_t)RNG_ACCEPT},
                             p.keys[2 * c], p.keys[2 * c + 1]);
         double logu = log(unif53(wv.a, wv.b));
         int acc = logu < logA;
@@ -458,7 +460,7 @@ __global__ void __launch_bounds__(256) k_accept(AcceptP p)
             long long k = p.trace_n[c];
             if (k < p.trace_cap) {
                 double *rw = p.trace + ((long long)c * p.trace_cap + k) * 8;
-                rw[0] = p.sweep;
+                rw[0] = sweep;
                 rw[1] = p.slice;
                 rw[2] = lr.x;
                 rw[3] = lr.y;
@@ -665,6 +667,7 @@ __global__ void __launch_bounds__(256) k_meas_final(MeasP p)
             }
         }
         double *o = p.out + (long long)c * p.out_cs;
+        if (p.ctr) o += (long long)(p.ctr[QMC_CTR_SERIES] % (uint32_t)p.slots) * QMC_NOBS;
         double t0 = 0, td = 0;
         for (int i = 0; i < 5; ++i) {
             o[1 + i] = S0[i];
@@ -687,12 +690,12 @@ __global__ void __launch_bounds__(256) k_meas_final(MeasP p)
 }
 
 // eps <- eps + (r_a - r_0) d_eps, clamped to [1e-4, 10]; reset sweep stats
-__global__ void k_end_sweep(int nb, int L, int adapt, double r0, double deps, double *eps,
-                            double *eps_used, double *st)
+__global__ void k_end_sweep(int nb, int L, int n_adapt, const uint32_t *ctr, double r0,
+                            double deps, double *eps, double *eps_used, double *st)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nb) return;
-    if (adapt) {
+    if (n_adapt < 0 || ctr[QMC_CTR_SWEEP] < (uint32_t)n_adapt) {
         double ra = st[c * 4] / L;
         double e = eps[c] + (ra - r0) * deps;
         e = e < 1e-4 ? 1e-4 : (e > 10.0 ? 10.0 : e);
@@ -702,6 +705,14 @@ __global__ void k_end_sweep(int nb, int L, int adapt, double r0, double deps, do
     st[c * 4 + 1] = 0;
     st[c * 4 + 2] = 0;
     eps_used[c] = eps[c];
+}
+
+// advance the sweep number and the series slot (after every kernel of the
+// sweep has read them)
+__global__ void k_next_sweep(uint32_t *ctr)
+{
+    ctr[QMC_CTR_SWEEP] += 1u;
+    ctr[QMC_CTR_SERIES] += 1u;
 }
 
 // --------------------------------------------------------- launchers -----
@@ -771,10 +782,10 @@ void launch_trace_grad(cudaStream_t s, int prec, int nb, int n, int nq, const vo
 }
 void launch_propose(cudaStream_t s, int nb, int nf, const double *phi, long long phi_cs,
                     const double *grad, const double *eps, const uint32_t *keys, uint32_t slice,
-                    uint32_t sweep, double *phip)
+                    const uint32_t *ctr, double *phip)
 {
     k_propose<<<dim3(cdiv_up(nf, 128), nb), 128, 0, s>>>(nf, phi, phi_cs, grad, eps, keys, slice,
-                                                          sweep, phip);
+                                                          ctr, phip);
     QMC_COUNT(1);
 }
 void launch_axpyI(cudaStream_t s, int nb, int N, Op X, cd a, cd b, Op Y)
@@ -834,9 +845,11 @@ void launch_measure(cudaStream_t s, int nb, int n, int nq, const cd *G, const cd
     k_meas_final<<<nb, 256, 0, s>>>(p);
     QMC_COUNT(2);
 }
-void launch_end_sweep(cudaStream_t s, int nb, int L, int adapt, double r0, double deps,
-                      double *eps, double *eps_used, double *st)
+void launch_end_sweep(cudaStream_t s, int nb, int L, int n_adapt, uint32_t *ctr, double r0,
+                      double deps, double *eps, double *eps_used, double *st)
 {
-    k_end_sweep<<<cdiv_up(nb, 64), 64, 0, s>>>(nb, L, adapt, r0, deps, eps, eps_used, st);
+    k_end_sweep<<<cdiv_up(nb, 64), 64, 0, s>>>(nb, L, n_adapt, ctr, r0, deps, eps, eps_used, st);
+    k_next_sweep<<<1, 1, 0, s>>>(ctr);
+    QMC_COUNT(1);
     QMC_COUNT(1);
 }

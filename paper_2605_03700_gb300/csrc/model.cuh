@@ -2,6 +2,10 @@
 #pragma once
 #include "linalg.cuh"
 
+// device counters of a context, read by the kernels so that a captured sweep
+// replays with the current values
+enum { QMC_CTR_SWEEP = 0, QMC_CTR_SERIES = 1, QMC_CTR_N = 2 };
+
 struct AcceptP {
     int nq;
     const double *phi;
@@ -10,8 +14,8 @@ struct AcceptP {
     const cd *alpha, *logdet, *trF;
     const int *fkind, *frA, *frB;
     const uint32_t *keys;
-    int slice;  // 1-based
-    uint32_t sweep;
+    int slice;            // 1-based
+    const uint32_t *ctr;  // device counters (QMC_CTR_SWEEP: sweep number)
     int *flag;
     double *st;  // per chain: accepted, max stab err, max sign dev, spare
     int *errf;
@@ -43,6 +47,8 @@ struct MeasP {
     int dq[8];
     double *out;
     long long out_cs;
+    const uint32_t *ctr;  // non-null: out is a ring of `slots` records per chain and
+    int slots;            // the record goes to slot ctr[QMC_CTR_SERIES] % slots
     const double *st;
     const double *eps_used;
 };
@@ -64,7 +70,7 @@ void launch_trace_grad(cudaStream_t s, int prec, int nb, int n, int nq, const vo
                        long long phi_cs, double *grad);
 void launch_propose(cudaStream_t s, int nb, int nf, const double *phi, long long phi_cs,
                     const double *grad, const double *eps, const uint32_t *keys, uint32_t slice,
-                    uint32_t sweep, double *phip);
+                    const uint32_t *ctr, double *phip);
 void launch_axpyI(cudaStream_t s, int nb, int N, Op X, cd a, cd b, Op Y);
 void launch_cvt_real(cudaStream_t s, long long n, const float *a, double *b);
 void launch_accept(cudaStream_t s, int nb, const AcceptP &p);
@@ -78,5 +84,5 @@ void launch_stab_err(cudaStream_t s, int nb, int N, cd *G, const cd *Gs, double 
                      double tol);
 void launch_measure(cudaStream_t s, int nb, int n, int nq, const cd *G, const cd *val,
                     const int *col, const int *partner, cd *ax, const MeasP &p);
-void launch_end_sweep(cudaStream_t s, int nb, int L, int adapt, double r0, double deps,
-                      double *eps, double *eps_used, double *st);
+void launch_end_sweep(cudaStream_t s, int nb, int L, int n_adapt, uint32_t *ctr, double r0,
+                      double deps, double *eps, double *eps_used, double *st);

@@ -65,6 +65,11 @@ def lib():
         L.qmc_destroy.argtypes = [vp]
         L.qmc_set_stream.argtypes = [vp, vp]
         L.qmc_sweep.argtypes = [vp, C.c_int]
+        L.qmc_sweep_graph.argtypes = [vp, C.c_int]
+        L.qmc_group_create.argtypes = [C.POINTER(vp), C.POINTER(vp), C.c_int]
+        L.qmc_group_sweep.argtypes = [vp, C.c_int]
+        L.qmc_group_sync.argtypes = [vp]
+        L.qmc_group_destroy.argtypes = [vp]
         L.qmc_sync.argtypes = [vp]
         L.qmc_measure.argtypes = [vp, dp]
         L.qmc_get_series.argtypes = [vp, C.c_int, dp]
@@ -196,8 +201,11 @@ class Chain:
         """stream: a cudaStream_t handle as int (e.g. torch.cuda.Stream().cuda_stream)."""
         _check(lib().qmc_set_stream(self.h, C.c_void_p(int(stream))), self.h)
 
-    def sweep(self, n=1):
-        _check(lib().qmc_sweep(self.h, n), self.h)
+    def sweep(self, n=1, graph=False):
+        """Enqueue n sweeps of all chains; graph=True replays one captured
+        sweep (qmc_sweep_graph) instead of launching every kernel."""
+        f = lib().qmc_sweep_graph if graph else lib().qmc_sweep
+        _check(f(self.h, n), self.h)
 
     def sync(self):
         _check(lib().qmc_sync(self.h), self.h)
@@ -253,3 +261,37 @@ class Chain:
         out = np.zeros(self.n_chains)
         _check(lib().qmc_get_eps(self.h, _dp(out)), self.h)
         return out
+
+
+class Group:
+    """Several Chain objects (any sizes) swept together as one CUDA graph per
+    sweep, each on its own graph branch (qmc_group_*).  The chains must stay
+    open while the group lives."""
+
+    def __init__(self, chains):
+        self.chains = list(chains)
+        arr = (C.c_void_p * len(self.chains))(*[c.h.value for c in self.chains])
+        h = C.c_void_p()
+        _check(lib().qmc_group_create(C.byref(h), arr, len(self.chains)))
+        self.h = h
+
+    def sweep(self, n=1):
+        _check(lib().qmc_group_sweep(self.h, n))
+
+    def sync(self):
+        code = lib().qmc_group_sync(self.h)
+        if code != 0:
+            for c in self.chains:
+                c.sync()
+            _check(code)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().qmc_group_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
