@@ -258,7 +258,7 @@ def run_ours(args):
     gemm_tflops = gemm_flops / (gemm_ms / 1000.0) / 1e12 if gemm_ms > 0 else 0.0
     roof = {"bound": "alu", "achieved": gemm_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": gemm_tflops / FP64_PEAK_TFLOPS,
-            "traffic": TRAFFIC_PER_LAUNCH, "kernel": "k_zgemm (batched complex FP64 GEMM)",
+            "traffic": TRAFFIC_PER_LAUNCH, "kernel": "k_zgemm<double> (batched complex FP64 GEMM; FP32 products excluded)",
             "launches": gemm_n, "ms_total": gemm_ms, "share_of_step_time": gemm_ms / ms,
             "peak_note": "FP64 pipe, derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"}
     if rank != 0:

@@ -259,7 +259,8 @@ long long qmc_launch_count(void);
  * 16 before any tuning. */
 int qmc_gemm_tile(int n, int precision);
 
-/* Event timing of every batched complex GEMM launch.  enable = 1 starts
+/* Event timing of every batched complex GEMM launch computed in FP64 (the
+ * FP64-pipe roofline; FP32 products are not recorded).  enable = 1 starts
  * recording (a pair of CUDA events around each launch on its stream);
  * enable = 0 stops, synchronises the device and returns the summed device
  * time in *total_ms, the number of launches and their algorithmic flops

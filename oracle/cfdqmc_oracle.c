@@ -32,6 +32,11 @@
  *   RNG                the paper is silent: Philox4x32-10 (Salmon et al.,
  *                      SC'11), counter = (index, slice, sweep, purpose),
  *                      key = (seed low, seed high), Box-Muller normals
+ *   learned slice move not in the paper (the build target's learned
+ *                      proposal): an MLP gives a Gaussian N(mu, sigma^2) for
+ *                      slice tau from its neighbours; preconditioned Crank-
+ *                      Nicolson move around it, accepted by the same exact
+ *                      determinant ratio (definitions in oracle/learned.py)
  */
 #include <complex.h>
 #include <math.h>
@@ -824,9 +829,149 @@ static void update_slice(orc_t *o, int t, slice_fac *fc, slice_fac *fp)
     free(Mi); free(Gp); free(T); free(piv);
 }
 
+/* ------------------------------------------------- learned slice move -- */
+typedef struct {
+    int nf, H;
+    const double *W1, *b1, *W2, *b2, *W3, *b3;  /* layout of oracle/learned.py */
+    double rho;
+} learned_t;
+
+static double silu(double a) { return a / (1.0 + exp(-a)); }
+
+static void learned_bind(learned_t *lp, int nf, int H, const double *theta)
+{
+    lp->nf = nf;
+    lp->H = H;
+    lp->W1 = theta;
+    lp->b1 = lp->W1 + (size_t)H * 2 * nf;
+    lp->W2 = lp->b1 + H;
+    lp->b2 = lp->W2 + (size_t)H * H;
+    lp->W3 = lp->b2 + H;
+    lp->b3 = lp->W3 + (size_t)2 * nf * H;
+}
+
+/* out[2nf] = W3 silu(W2 silu(W1 x + b1) + b2) + b3, x = [x0 (nf), x1 (nf)] */
+static void mlp_forward(const learned_t *lp, const double *x0, const double *x1, double *out)
+{
+    int nf = lp->nf, H = lp->H;
+    double *h1 = (double *)malloc(sizeof(double) * H);
+    double *h2 = (double *)malloc(sizeof(double) * H);
+    for (int j = 0; j < H; ++j) {
+        double a = lp->b1[j];
+        const double *w = lp->W1 + (size_t)j * 2 * nf;
+        for (int i = 0; i < nf; ++i) a += w[i] * x0[i];
+        for (int i = 0; i < nf; ++i) a += w[nf + i] * x1[i];
+        h1[j] = silu(a);
+    }
+    for (int j = 0; j < H; ++j) {
+        double a = lp->b2[j];
+        for (int i = 0; i < H; ++i) a += lp->W2[(size_t)j * H + i] * h1[i];
+        h2[j] = silu(a);
+    }
+    for (int j = 0; j < 2 * nf; ++j) {
+        double a = lp->b3[j];
+        for (int i = 0; i < H; ++i) a += lp->W3[(size_t)j * H + i] * h2[i];
+        out[j] = a;
+    }
+    free(h1);
+    free(h2);
+}
+
+void orc_mlp_forward(int nf, int H, const double *theta, int B, const double *X, double *out)
+{
+    learned_t lp;
+    learned_bind(&lp, nf, H, theta);
+    for (int b = 0; b < B; ++b)
+        mlp_forward(&lp, X + (size_t)b * 2 * nf, X + (size_t)b * 2 * nf + nf,
+                    out + (size_t)b * 2 * nf);
+}
+
+/* one learned move + MH accept on slice t (1-based); the network sees the
+ * neighbouring slices t-1 and t+1 (cyclic), which the move leaves alone */
+static void update_slice_learned(orc_t *o, int t, const learned_t *lp, slice_fac *fc,
+                                 slice_fac *fp)
+{
+    int N = o->N, nf = 4 * o->nq, L = o->L;
+    size_t nn = (size_t)N * N;
+    double *phi = o->phi + (size_t)(t - 1) * nf;
+    const double *prv = o->phi + (size_t)((t - 2 + L) % L) * nf;
+    const double *nxt = o->phi + (size_t)(t % L) * nf;
+    zc *B = o->B + (size_t)(t - 1) * nn, *Binv = o->Binv + (size_t)(t - 1) * nn;
+    double *out = (double *)malloc(sizeof(double) * 2 * nf);
+    double *php = (double *)malloc(sizeof(double) * nf);
+    zc *Bp = zalloc(nn), *Bpi = zalloc(nn), *Dl = zalloc(nn), *M = zalloc(nn),
+       *Mi = zalloc(nn), *Gp = zalloc(nn), *T = zalloc(nn);
+    int *piv = (int *)malloc(sizeof(int) * N);
+
+    mlp_forward(lp, prv, nxt, out);
+    double c = sqrt(1.0 - lp->rho * lp->rho), lq = 0.0;
+    for (int f = 0; f < nf; ++f) {
+        double mu = out[f], sig = exp(out[nf + f]);
+        double xi = normal_at(o, (uint32_t)f, (uint32_t)(t - 1), o->sweep, 1);
+        php[f] = mu + lp->rho * (phi[f] - mu) + c * sig * xi;
+        double a = (php[f] - mu) / sig, b = (phi[f] - mu) / sig;
+        lq += -0.5 * a * a + 0.5 * b * b;
+    }
+    build_factors(o, phi, fc);
+    build_factors(o, php, fp);
+    product_B(o, fp, Bp, Bpi);
+    mat_mul(N, Bp, Binv, Dl);
+    for (int x = 0; x < N; ++x) Dl[x * N + x] -= 1.0;
+    for (size_t x = 0; x < nn; ++x) T[x] = -o->G[x];
+    for (int x = 0; x < N; ++x) T[x * N + x] += 1.0;
+    mat_mul(N, Dl, T, M);
+    for (int x = 0; x < N; ++x) M[x * N + x] += 1.0;
+    int nsw = lu(N, M, piv);
+    zc logR = lu_logdet(N, M, nsw) - 0.5 * (fp->trW0 - fc->trW0);
+    lu_inv(N, M, piv, Mi);
+    mat_mul(N, o->G, Mi, Gp);
+    double s0 = 0.0, s0p = 0.0;
+    for (int f = 0; f < nf; ++f) {
+        s0 += 0.5 * phi[f] * phi[f];
+        s0p += 0.5 * php[f] * php[f];
+    }
+    double logA = 2.0 * creal(logR) - (s0p - s0) - lq;
+    uint32_t w[4];
+    draw(o, 0, (uint32_t)(t - 1), o->sweep, 2, w);
+    double logu = log(u53(w[0], w[1]));
+    int acc = logu < logA;
+    double sd = fabs(sin(cimag(logR)));
+    if (sd > o->sign_dev_sweep) o->sign_dev_sweep = sd;
+    if (o->trace && o->trace_n < o->trace_cap) {
+        double *tr = o->trace + (size_t)o->trace_n * ORC_NTRACE;
+        tr[0] = o->sweep; tr[1] = t; tr[2] = creal(logR); tr[3] = cimag(logR);
+        tr[4] = logA; tr[5] = logu; tr[6] = acc; tr[7] = lp->rho;
+        o->trace_n++;
+    }
+    if (acc) {
+        memcpy(phi, php, sizeof(double) * nf);
+        memcpy(B, Bp, sizeof(zc) * nn);
+        memcpy(Binv, Bpi, sizeof(zc) * nn);
+        memcpy(o->G, Gp, sizeof(zc) * nn);
+        o->acc_sweep++;
+    }
+    free(out); free(php); free(Bp); free(Bpi); free(Dl); free(M); free(Mi); free(Gp);
+    free(T); free(piv);
+}
+
 static void measure(const orc_t *o, double *obs);
 
-void orc_sweep(orc_t *o, int nsweeps, double *obs)
+static void sweep_impl(orc_t *o, int nsweeps, double *obs, const learned_t *lp);
+
+void orc_sweep(orc_t *o, int nsweeps, double *obs) { sweep_impl(o, nsweeps, obs, NULL); }
+
+/* sweeps whose slice moves are learned moves (no step-size adaptation);
+ * needs L >= 2 so that a slice is never its own neighbour */
+void orc_sweep_learned(orc_t *o, int nsweeps, double *obs, int H, const double *theta,
+                       double rho)
+{
+    learned_t lp;
+    learned_bind(&lp, 4 * o->nq, H, theta);
+    lp.rho = rho;
+    sweep_impl(o, nsweeps, obs, &lp);
+}
+
+static void sweep_impl(orc_t *o, int nsweeps, double *obs, const learned_t *lp)
 {
     int N = o->N;
     size_t nn = (size_t)N * N;
@@ -855,7 +1000,8 @@ void orc_sweep(orc_t *o, int nsweeps, double *obs)
             /* wrap G(t-1) -> G(t) = B_t G B_t^-1 */
             mat_mul(N, o->B + (size_t)(t - 1) * nn, o->G, T);
             mat_mul(N, T, o->Binv + (size_t)(t - 1) * nn, o->G);
-            update_slice(o, t, &fc, &fp);
+            if (lp) update_slice_learned(o, t, lp, &fc, &fp);
+            else update_slice(o, t, &fc, &fp);
             if (t == o->sp[k]) {
                 for (int r = 0; r < N; ++r)
                     for (int c = 0; c < N; ++c) X[r * N + c] = RQ[r * N + c] * RD[c];
@@ -893,7 +1039,7 @@ void orc_sweep(orc_t *o, int nsweeps, double *obs)
             ob[16] = o->sign_dev_sweep;
             ob[17] = (double)o->acc_sweep;
         }
-        if (o->n_adapt < 0 || (int)o->sweep < o->n_adapt) {
+        if (!lp && (o->n_adapt < 0 || (int)o->sweep < o->n_adapt)) {
             o->eps += (ra - o->r0) * o->deps;
             if (o->eps < 1e-4) o->eps = 1e-4;
             if (o->eps > 10.0) o->eps = 10.0;

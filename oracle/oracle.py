@@ -49,6 +49,8 @@ def lib():
                                  C.c_double, C.c_int]
         L.orc_destroy.argtypes = [C.c_void_p]
         L.orc_sweep.argtypes = [C.c_void_p, C.c_int, dp]
+        L.orc_sweep_learned.argtypes = [C.c_void_p, C.c_int, dp, C.c_int, dp, C.c_double]
+        L.orc_mlp_forward.argtypes = [C.c_int, C.c_int, dp, C.c_int, dp, dp]
         L.orc_measure.argtypes = [C.c_void_p, dp]
         L.orc_set_measure_q.argtypes = [C.c_void_p, C.c_int, ip, C.c_int]
         L.orc_set_trace.argtypes = [C.c_void_p, dp, C.c_long]
@@ -181,6 +183,16 @@ class Chain:
         lib().orc_sweep(self.h, n, _dp(obs))
         return obs
 
+    def sweep_learned(self, n, theta, H, rho):
+        """n sweeps of learned slice moves (oracle/learned.py) with the
+        network parameters theta (packed FP64) of hidden width H."""
+        if self.L < 2:
+            raise ValueError("learned moves need L >= 2")
+        theta = np.ascontiguousarray(theta, dtype=float)
+        obs = np.zeros((n, NOBS))
+        lib().orc_sweep_learned(self.h, n, _dp(obs), H, _dp(theta), float(rho))
+        return obs
+
     def measure(self):
         obs = np.zeros(NOBS)
         lib().orc_measure(self.h, _dp(obs))
@@ -246,3 +258,12 @@ class Chain:
     @property
     def sweep_index(self):
         return lib().orc_get_sweep(self.h)
+
+
+def mlp_forward(theta, X, nf, H):
+    """The C oracle's network forward: (B, 2nf) -> (B, 2nf) = [mu, log sigma]."""
+    theta = np.ascontiguousarray(theta, dtype=float)
+    X = np.ascontiguousarray(X, dtype=float)
+    out = np.zeros((X.shape[0], 2 * nf))
+    lib().orc_mlp_forward(nf, H, _dp(theta), X.shape[0], _dp(X), _dp(out))
+    return out

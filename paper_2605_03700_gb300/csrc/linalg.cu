@@ -196,7 +196,7 @@ int zgemm(cudaStream_t st, const GemmP &p, int batch)
 {
     const int tile = tile_for(p.N, p.rc);
     int r;
-    if (g_gprof.on) {
+    if (g_gprof.on && p.rc == TY_C64) {  // the FP64-pipe roofline: FP64 products only
         cudaEventRecord(gprof_event(), st);
         r = launch_gemm(st, p, batch, tile);
         cudaEventRecord(gprof_event(), st);
