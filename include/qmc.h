@@ -42,7 +42,7 @@ enum {
     QMC_ERR_CUDA = -2,      /* a CUDA call failed */
     QMC_ERR_OOM = -3,       /* device allocation failed */
     QMC_ERR_UNSTABLE = -4,  /* G error at a restabilisation above opts.stab_tol */
-    QMC_ERR_SIGN = -5,      /* |sin Im log R| above opts.sign_tol: sign problem */
+    QMC_ERR_SIGN = -5,      /* an accepted update had |sin Im log R| above opts.sign_tol */
     QMC_ERR_NONFINITE = -6, /* a determinant ratio or field became NaN/Inf */
     QMC_ERR_TIMEOUT = -7    /* a device-side bounded wait gave up */
 };
@@ -89,7 +89,8 @@ typedef struct {
     int series_capacity;   /* observable records kept per chain (default 4096, ring) */
     int trace_capacity;    /* per-update records kept per chain (default 0 = off) */
     double stab_tol;       /* QMC_ERR_UNSTABLE threshold (default 1e-6) */
-    double sign_tol;       /* QMC_ERR_SIGN threshold (default 1e-6) */
+    double sign_tol;       /* QMC_ERR_SIGN threshold on accepted updates (default 1e-6);
+                              record column 16 is the maximum over all updates */
 } qmc_opts;
 
 /* Fill *o with the defaults listed above. */
@@ -142,6 +143,69 @@ int qmc_sweep(qmc_ctx *ctx, int n_sweeps);
  * Capture errors return QMC_ERR_CUDA and leave the context usable with
  * qmc_sweep. */
 int qmc_sweep_graph(qmc_ctx *ctx, int n_sweeps);
+
+/* ------------------------------------------------------------------------
+ * Learned slice proposal (not in the paper; the learned pattern of the build
+ * target).  A small network gives, for slice tau, a Gaussian
+ * N(mu, diag sigma^2) of the slice's nf = 4 N_q real fields from the
+ * neighbouring slices tau-1 and tau+1 (cyclic):
+ *     h1 = silu(W1 x + b1), h2 = silu(W2 h1 + b2), [mu, log sigma] = W3 h2 + b3,
+ *     x = [phi_{tau-1}, phi_{tau+1}],  silu(a) = a / (1 + e^-a),
+ * parameters packed as W1 (H x 2nf), b1 (H), W2 (H x H), b2 (H), W3 (2nf x H),
+ * b3 (2nf), row-major.  The products use a bfloat16 copy of the weights with
+ * FP32 accumulation; the optimiser (Adam, betas 0.9 / 0.999, eps 1e-8)
+ * updates an FP32 master copy.  The training loss is the Gaussian negative
+ * log likelihood of a slice given its neighbours,
+ *     mean over the batch of sum_f [ (y - mu)^2 / (2 sigma^2) + log sigma ],
+ * on (configuration, slice) pairs drawn uniformly from collected
+ * configurations (qmc_net_collect).
+ * A learned sweep moves each slice by
+ *     phi' = mu + rho (phi - mu) + sqrt(1 - rho^2) sigma xi,
+ * reversible with respect to the network's Gaussian, and accepts with
+ *     log A = 2 Re log R - (|phi'|^2 - |phi|^2)/2 - [log N(phi') - log N(phi)],
+ * R the exact determinant ratio of the slice update: the chain samples the
+ * paper's weight whatever the network.  Learned sweeps interleave freely with
+ * qmc_sweep (the Langevin sweep stays the fallback) and do not adapt eps.
+ * The network's buffers serve one stream at a time: do not train it while a
+ * learned sweep that uses it is in flight on another stream.
+ * ---------------------------------------------------------------------- */
+typedef struct qmc_net qmc_net;
+/* nf = 4 N_q of the contexts it will serve; width H in [1, 4096]; capacity =
+ * configurations kept (a ring; each is L x nf FP32 values); seed keys the
+ * initial weights and the training batches.  Hidden weights start uniform
+ * with variance 1/fan_in, biases and the output layer at 0 (mu = 0,
+ * sigma = 1: the Gaussian part of the action).  QMC_ERR_ARG / QMC_ERR_OOM /
+ * QMC_ERR_CUDA on failure. */
+int qmc_net_create(qmc_net **out, int nf, int width, long long capacity, uint64_t seed);
+int qmc_net_destroy(qmc_net *net);
+int qmc_net_set_stream(qmc_net *net, void *stream);
+long long qmc_net_num_params(const qmc_net *net);
+/* configurations collected so far (at most the capacity) */
+long long qmc_net_dataset_size(const qmc_net *net);
+/* FP32 master parameters to / from host memory (len >= qmc_net_num_params);
+ * set also rounds the bfloat16 copy and resets the optimiser state. */
+int qmc_net_get_params(qmc_net *net, float *host, size_t len);
+int qmc_net_set_params(qmc_net *net, const float *host, size_t len);
+/* append the current configuration of every chain of ctx (device to device);
+ * the first call fixes L; later contexts need the same nf and L
+ * (QMC_ERR_ARG otherwise, also when ctx has more chains than the capacity) */
+int qmc_net_collect(qmc_net *net, qmc_ctx *ctx);
+/* `steps` optimiser steps on batches of `batch` pairs; the loss of every step
+ * to loss_host[steps] (may be NULL).  weight_decay >= 0 is decoupled decay
+ * (theta -= lr * weight_decay * theta, Loshchilov & Hutter 2019) of the three
+ * weight matrices only, pulling the network toward its zero-output start.
+ * QMC_ERR_ARG before any collection. */
+int qmc_net_train(qmc_net *net, int steps, int batch, double lr, double weight_decay,
+                  double *loss_host);
+/* host X[batch][2nf] -> host out[batch][2nf] = [mu, log sigma] */
+int qmc_net_forward(qmc_net *net, const float *X, int batch, float *out);
+/* loss and gradient (packed like the parameters) of host X[batch][2nf],
+ * Y[batch][nf]: the training step's forward and backward without the update */
+int qmc_net_loss_grad(qmc_net *net, const float *X, const float *Y, int batch, double *loss,
+                      float *grad);
+/* n_sweeps sweeps of learned moves (rho in [0, 1); L >= 2; the network's nf
+ * must equal the context's 4 N_q); trace column 7 holds rho. */
+int qmc_sweep_learned(qmc_ctx *ctx, qmc_net *net, int n_sweeps, double rho);
 
 /* Batched chains of different sizes (BASELINE pattern, not in the paper): a
  * group sweeps several contexts -- any mix of geometry, orbital count,

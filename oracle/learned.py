@@ -23,7 +23,8 @@ Training loss: Gaussian negative log likelihood of the slice given its
 neighbours, averaged over the batch and summed over fields, without the
 constant (1/2) log 2 pi:
     loss = mean_b sum_f [ (1/2) ((y - mu) exp(-s))^2 + s ].
-Optimiser: Adam (Kingma & Ba, 2015) with bias correction.
+Optimiser: Adam (Kingma & Ba, 2015) with bias correction, optionally with
+decoupled weight decay of the weight matrices (Loshchilov & Hutter, 2019).
 
 Move (preconditioned Crank-Nicolson around the learned Gaussian
 N(mu, diag sigma^2), sigma = exp(s), 0 <= rho < 1):
@@ -113,13 +114,22 @@ def loss_and_grad(theta, X, Y, nf, H):
     return loss, pack(g, nf, H)
 
 
-def adam_step(theta, grad, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
-    """One Adam step (t = 1 for the first); returns new (theta, m, v)."""
+def weight_mask(nf, H):
+    """1 on the entries of W1, W2, W3 and 0 on the biases."""
+    return np.concatenate([np.full(int(np.prod(s)), 0.0 if name.startswith("b") else 1.0)
+                           for name, s in shapes(nf, H)])
+
+
+def adam_step(theta, grad, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8, wd=0.0, mask=None):
+    """One Adam step (t = 1 for the first); returns new (theta, m, v).  wd is
+    decoupled weight decay (Loshchilov & Hutter, 2019) on the entries where
+    mask is 1: theta -= lr * wd * theta, from the value before the step."""
     m = b1 * m + (1 - b1) * grad
     v = b2 * v + (1 - b2) * grad * grad
     mh = m / (1 - b1 ** t)
     vh = v / (1 - b2 ** t)
-    return theta - lr * mh / (np.sqrt(vh) + eps), m, v
+    decay = 0.0 if mask is None else wd * mask * theta
+    return theta - lr * (mh / (np.sqrt(vh) + eps) + decay), m, v
 
 
 def pcn_move(mu, s, phi, rho, xi):

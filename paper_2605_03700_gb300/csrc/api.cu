@@ -23,6 +23,7 @@
 #include <string>
 #include <vector>
 
+#include "learned.cuh"
 #include "linalg.cuh"
 #include "model.cuh"
 
@@ -54,6 +55,7 @@ struct qmc_ctx {
     uint32_t sweep = 0;
     long long series_n = 0;
     uint32_t *ctr = nullptr;             // device: sweep number, series slot (QMC_CTR_*)
+    double *lq = nullptr;                // learned move: log N(phi') - log N(phi) per chain
     cudaStream_t cap_st = nullptr;       // private stream the sweep graph is captured on
     cudaGraphExec_t gexec = nullptr;     // one captured sweep of all chains
     long long graph_kernels = 0;         // kernels in that graph
@@ -318,8 +320,9 @@ static int green_at_zero(qmc_ctx *ctx)
                           ctx->LD + nsp * ctx->N, ctx->LW + nsp * NN, Ls, LDs, ctx->G);
 }
 
-// one MALA proposal + MH test on slice t (1-based) for every chain
-static int update_slice(qmc_ctx *ctx, int t)
+// one proposal + MH test on slice t (1-based) for every chain: the Langevin
+// move (net == nullptr) or the learned move around the network's Gaussian
+static int update_slice(qmc_ctx *ctx, int t, qmc_net *net = nullptr, double rho = 0.0)
 {
     const int nb = ctx->nb, N = ctx->N, n = ctx->n, nf = ctx->nf;
     const long long NN = ctx->NN, n2 = ctx->n2;
@@ -331,12 +334,21 @@ static int update_slice(qmc_ctx *ctx, int t)
     cd *Bis = ctx->Binv + (long long)s0 * NN;
     cd *Us = ctx->eigU + (long long)s0 * 4 * n2;
     double *Ws = ctx->eigW + (long long)s0 * 4 * n;
-    // forward gradient at the current fields
-    factors_from_eig(ctx, Us, L * 4 * n2, Ws, L * 4 * n, ctx->V, ctx->T, ctx->lam, ctx->Dg,
-                     ctx->Dgi, ctx->lamG, ctx->DgG, ctx->DgiG);
-    gradient(ctx, ctx->G, ctx->V, ctx->T, ctx->lamG, ctx->DgG, ctx->DgiG, phi_s, phi_cs, ctx->grad);
-    launch_propose(s, nb, nf, phi_s, phi_cs, ctx->grad, ctx->eps, ctx->keys, (uint32_t)s0,
-                   ctx->ctr, ctx->phip);
+    if (net) {
+        // the network's Gaussian for this slice from slices t-1 and t+1
+        net_gather_context(net, s, nb, ctx->L, s0, ctx->phi, phi_cs);
+        net_forward(net, s, nb);
+        net_pcn(net, s, nb, phi_s, phi_cs, rho, ctx->keys, (uint32_t)s0, ctx->ctr, ctx->phip,
+                ctx->lq);
+    } else {
+        // forward gradient at the current fields
+        factors_from_eig(ctx, Us, L * 4 * n2, Ws, L * 4 * n, ctx->V, ctx->T, ctx->lam, ctx->Dg,
+                         ctx->Dgi, ctx->lamG, ctx->DgG, ctx->DgiG);
+        gradient(ctx, ctx->G, ctx->V, ctx->T, ctx->lamG, ctx->DgG, ctx->DgiG, phi_s, phi_cs,
+                 ctx->grad);
+        launch_propose(s, nb, nf, phi_s, phi_cs, ctx->grad, ctx->eps, ctx->keys, (uint32_t)s0,
+                       ctx->ctr, ctx->phip);
+    }
     // proposal factors and propagators
     if (eig_of_fields(ctx, ctx->phip, nf, ctx->Up, ctx->Wp)) {
         ctx->err = "eigensolver: unsupported size";
@@ -355,9 +367,10 @@ static int update_slice(qmc_ctx *ctx, int t)
     if (lu_batched(s, N, ctx->M, NN, ctx->piv, N, ctx->logdet, nb)) return QMC_ERR_ARG;
     if (rdiv_batched(s, TY_C64, N, ctx->G, NN, ctx->M, NN, ctx->piv, N, ctx->Gp, NN, nb))
         return QMC_ERR_ARG;
-    // reverse gradient at the proposal with G'
-    gradient(ctx, ctx->Gp, ctx->Vp, ctx->Tp, ctx->lampG, ctx->DgpG, ctx->DgipG, ctx->phip, nf,
-             ctx->gradp);
+    // reverse gradient at the proposal with G' (Langevin move only)
+    if (!net)
+        gradient(ctx, ctx->Gp, ctx->Vp, ctx->Tp, ctx->lampG, ctx->DgpG, ctx->DgipG, ctx->phip, nf,
+                 ctx->gradp);
     AcceptP ap;
     ap.nq = ctx->nq;
     ap.phi = phi_s;
@@ -366,6 +379,8 @@ static int update_slice(qmc_ctx *ctx, int t)
     ap.grad = ctx->grad;
     ap.gradp = ctx->gradp;
     ap.eps = ctx->eps;
+    ap.lq = net ? ctx->lq : nullptr;
+    ap.rho = rho;
     ap.alpha = ctx->alpha_d;
     ap.logdet = ctx->logdet;
     ap.trF = ctx->trF;
@@ -452,7 +467,7 @@ static void measure_into(qmc_ctx *ctx, double *out, long long out_cs,
 
 // enqueue one sweep of every chain on ctx->st; nothing on the host depends on
 // the sweep number, so the same launches replay from a captured graph
-static int enqueue_sweep(qmc_ctx *ctx)
+static int enqueue_sweep(qmc_ctx *ctx, qmc_net *net = nullptr, double rho = 0.0)
 {
     int r = build_left_stack(ctx);
     if (r) return r;
@@ -467,7 +482,7 @@ static int enqueue_sweep(qmc_ctx *ctx)
                 op64(ctx->G, NN), 0, op64(ctx->X1, NN));
         gemm_sq(ctx->st, N, nb, TY_C64, op64(ctx->X1, NN), 0,
                 op64(ctx->Binv + (long long)(t - 1) * NN, BL), 0, op64(ctx->G, NN));
-        r = update_slice(ctx, t);
+        r = update_slice(ctx, t, net, rho);
         if (r) return r;
         if (t == ctx->sp[k]) {
             r = restabilise(ctx, k, prev, t);
@@ -478,8 +493,9 @@ static int enqueue_sweep(qmc_ctx *ctx)
     }
     const int cap = ctx->o.series_capacity;
     measure_into(ctx, ctx->series, (long long)cap * QMC_NOBS, ctx->ctr, cap);
-    launch_end_sweep(ctx->st, nb, ctx->L, ctx->o.n_adapt, ctx->ctr, ctx->o.r0, ctx->o.deps,
-                     ctx->eps, ctx->eps_used, ctx->stats);
+    // learned sweeps leave the Langevin step alone (n_adapt 0: no adaptation)
+    launch_end_sweep(ctx->st, nb, ctx->L, net ? 0 : ctx->o.n_adapt, ctx->ctr, ctx->o.r0,
+                     ctx->o.deps, ctx->eps, ctx->eps_used, ctx->stats);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         ctx->err = std::string("kernel launch: ") + cudaGetErrorString(e);
@@ -639,6 +655,7 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
     const int nf = ctx->nf;
     // device allocations
     DA(ctx->ctr, QMC_CTR_N);
+    DA(ctx->lq, nb);
     DA(ctx->qxy, 2 * nq);
     DA(ctx->ff_val, (size_t)nq * n);
     DA(ctx->ff_col, (size_t)nq * n);
@@ -1004,6 +1021,35 @@ int qmc_sweep_graph(qmc_ctx *ctx, int n_sweeps)
     for (int i = 0; i < n_sweeps; ++i) {
         CK(cudaGraphLaunch(ctx->gexec, ctx->st));
         g_qmc_launches += ctx->graph_kernels;
+        ctx->sweep++;
+        ctx->series_n++;
+    }
+    return QMC_OK;
+}
+
+int qmc_net_collect(qmc_net *net, qmc_ctx *ctx)
+{
+    if (!net || !ctx) return QMC_ERR_ARG;
+    int r = net_collect_fields(net, ctx->st, ctx->nb, ctx->L, ctx->nf, ctx->phi,
+                               (long long)ctx->L * ctx->nf);
+    if (r) ctx->err = "qmc_net_collect: field count, L or chain count does not fit the network";
+    return r;
+}
+
+int qmc_sweep_learned(qmc_ctx *ctx, qmc_net *net, int n_sweeps, double rho)
+{
+    if (!ctx || !net || n_sweeps < 0) return QMC_ERR_ARG;
+    if (net->nf != ctx->nf || ctx->L < 2 || !(rho >= 0.0 && rho < 1.0)) {
+        ctx->err = "learned sweep: network field count, L >= 2 or 0 <= rho < 1 violated";
+        return QMC_ERR_ARG;
+    }
+    if (net_ensure_rows(net, ctx->nb)) {
+        ctx->err = "learned sweep: out of device memory";
+        return QMC_ERR_OOM;
+    }
+    for (int i = 0; i < n_sweeps; ++i) {
+        int r = enqueue_sweep(ctx, net, rho);
+        if (r) return r;
         ctx->sweep++;
         ctx->series_n++;
     }

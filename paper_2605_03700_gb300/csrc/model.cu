@@ -405,8 +405,9 @@ __global__ void __launch_bounds__(256) k_accept(AcceptP p)
     const int nq = p.nq, nf = 4 * nq;
     const double *ph = p.phi + (long long)c * p.phi_cs;
     const double *pp = p.phip + (long long)c * nf;
-    const double *g = p.grad + (long long)c * nf;
-    const double *gp = p.gradp + (long long)c * nf;
+    const bool learned = p.lq != nullptr;
+    const double *g = learned ? nullptr : p.grad + (long long)c * nf;
+    const double *gp = learned ? nullptr : p.gradp + (long long)c * nf;
     const double e = p.eps[c];
     const double h = 0.5 * e * e;
     double s0 = 0, s0p = 0, fw = 0, bw = 0, tr = 0, ti = 0, trp = 0, tip = 0;
@@ -414,10 +415,12 @@ __global__ void __launch_bounds__(256) k_accept(AcceptP p)
         double a = ph[f], b = pp[f];
         s0 += 0.5 * a * a;
         s0p += 0.5 * b * b;
-        double x = b - a + h * g[f];
-        double y = a - b + h * gp[f];
-        fw += x * x;
-        bw += y * y;
+        if (!learned) {
+            double x = b - a + h * g[f];
+            double y = a - b + h * gp[f];
+            fw += x * x;
+            bw += y * y;
+        }
     }
     for (int q = tid; q < nq; q += blockDim.x) {
         cd z = zfield(ph, p.fkind[q], p.frA[q], p.frB[q]);
@@ -441,7 +444,10 @@ __global__ void __launch_bounds__(256) k_accept(AcceptP p)
         cd w0 = cscale(cmul(a0, cmk(tr, ti)), 2.0);
         cd w0p = cscale(cmul(a0, cmk(trp, tip)), 2.0);
         cd lr = csub(p.logdet[c], cscale(csub(w0p, w0), 0.5));
-        double logA = 2.0 * lr.x - (s0p - s0) - bw / (2 * e * e) + fw / (2 * e * e);
+        // Langevin move: the proposal densities; learned move: the pCN
+        // reference-density correction (both exact MH for the same target)
+        double logA = learned ? 2.0 * lr.x - (s0p - s0) - p.lq[c]
+                              : 2.0 * lr.x - (s0p - s0) - bw / (2 * e * e) + fw / (2 * e * e);
         u32x4 wv = philox10(u32x4{0u, (uint32_t)(p.slice - 1), sweep, (uint32_t)RNG_ACCEPT},
                             p.keys[2 * c], p.keys[2 * c + 1]);
         double logu = log(unif53(wv.a, wv.b));
@@ -455,7 +461,10 @@ __global__ void __launch_bounds__(256) k_accept(AcceptP p)
         double *st = p.st + c * 4;
         st[0] += acc;
         if (sd > st[2]) st[2] = sd;
-        if (sd > p.sign_tol) atomicOr(p.errf + c, 2);
+        // rounding of Im log R grows with the conditioning of M: far proposals
+        // that are rejected never enter the chain, so only an accepted update
+        // raises the sign error (every update enters the recorded maximum)
+        if (sd > p.sign_tol && acc) atomicOr(p.errf + c, 2);
         if (p.trace) {
             long long k = p.trace_n[c];
             if (k < p.trace_cap) {
@@ -467,7 +476,7 @@ __global__ void __launch_bounds__(256) k_accept(AcceptP p)
                 rw[4] = logA;
                 rw[5] = logu;
                 rw[6] = acc;
-                rw[7] = e;
+                rw[7] = learned ? p.rho : e;
                 p.trace_n[c] = k + 1;
             }
         }

@@ -11,6 +11,8 @@ struct AcceptP {
     const double *phi;
     long long phi_cs;
     const double *phip, *grad, *gradp, *eps;
+    const double *lq;  // non-null: learned move, lq = log N(phi') - log N(phi) per chain
+    double rho;        // its pCN parameter (recorded in the trace)
     const cd *alpha, *logdet, *trF;
     const int *fkind, *frA, *frB;
     const uint32_t *keys;

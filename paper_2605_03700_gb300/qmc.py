@@ -66,6 +66,21 @@ def lib():
         L.qmc_set_stream.argtypes = [vp, vp]
         L.qmc_sweep.argtypes = [vp, C.c_int]
         L.qmc_sweep_graph.argtypes = [vp, C.c_int]
+        fp = C.POINTER(C.c_float)
+        L.qmc_net_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.c_longlong, C.c_uint64]
+        L.qmc_net_destroy.argtypes = [vp]
+        L.qmc_net_set_stream.argtypes = [vp, vp]
+        L.qmc_net_num_params.restype = C.c_longlong
+        L.qmc_net_num_params.argtypes = [vp]
+        L.qmc_net_dataset_size.restype = C.c_longlong
+        L.qmc_net_dataset_size.argtypes = [vp]
+        L.qmc_net_get_params.argtypes = [vp, fp, C.c_size_t]
+        L.qmc_net_set_params.argtypes = [vp, fp, C.c_size_t]
+        L.qmc_net_collect.argtypes = [vp, vp]
+        L.qmc_net_train.argtypes = [vp, C.c_int, C.c_int, C.c_double, C.c_double, dp]
+        L.qmc_net_forward.argtypes = [vp, fp, C.c_int, fp]
+        L.qmc_net_loss_grad.argtypes = [vp, fp, fp, C.c_int, dp, fp]
+        L.qmc_sweep_learned.argtypes = [vp, vp, C.c_int, C.c_double]
         L.qmc_group_create.argtypes = [C.POINTER(vp), C.POINTER(vp), C.c_int]
         L.qmc_group_sweep.argtypes = [vp, C.c_int]
         L.qmc_group_sync.argtypes = [vp]
@@ -207,6 +222,10 @@ class Chain:
         f = lib().qmc_sweep_graph if graph else lib().qmc_sweep
         _check(f(self.h, n), self.h)
 
+    def sweep_learned(self, net, n=1, rho=0.0):
+        """n sweeps of learned slice moves with network `net` (qmc_sweep_learned)."""
+        _check(lib().qmc_sweep_learned(self.h, net.h, n, float(rho)), self.h)
+
     def sync(self):
         _check(lib().qmc_sync(self.h), self.h)
 
@@ -288,6 +307,74 @@ class Group:
     def close(self):
         if getattr(self, "h", None):
             lib().qmc_group_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _fp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+class Net:
+    """The learned slice proposal's network (qmc_net_*): nf = 4 N_q fields per
+    slice, hidden width `width`, a device-resident ring of `capacity`
+    configurations for training."""
+
+    def __init__(self, nf, width=256, capacity=10000, seed=0):
+        h = C.c_void_p()
+        _check(lib().qmc_net_create(C.byref(h), int(nf), int(width), int(capacity), int(seed)))
+        self.h = h
+        self.nf, self.width = int(nf), int(width)
+
+    @property
+    def num_params(self):
+        return int(lib().qmc_net_num_params(self.h))
+
+    @property
+    def dataset_size(self):
+        return int(lib().qmc_net_dataset_size(self.h))
+
+    def get_params(self):
+        out = np.zeros(self.num_params, dtype=np.float32)
+        _check(lib().qmc_net_get_params(self.h, _fp(out), out.size))
+        return out
+
+    def set_params(self, theta):
+        a = np.ascontiguousarray(theta, dtype=np.float32)
+        _check(lib().qmc_net_set_params(self.h, _fp(a), a.size))
+
+    def collect(self, chain):
+        _check(lib().qmc_net_collect(self.h, chain.h), chain.h)
+
+    def train(self, steps, batch=256, lr=1e-3, weight_decay=0.0):
+        loss = np.zeros(steps)
+        _check(lib().qmc_net_train(self.h, int(steps), int(batch), float(lr),
+                                   float(weight_decay), _dp(loss)))
+        return loss
+
+    def forward(self, X):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        out = np.zeros((X.shape[0], 2 * self.nf), dtype=np.float32)
+        _check(lib().qmc_net_forward(self.h, _fp(X), X.shape[0], _fp(out)))
+        return out
+
+    def loss_grad(self, X, Y):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.ascontiguousarray(Y, dtype=np.float32)
+        loss = C.c_double()
+        g = np.zeros(self.num_params, dtype=np.float32)
+        _check(lib().qmc_net_loss_grad(self.h, _fp(X), _fp(Y), X.shape[0], C.byref(loss),
+                                       _fp(g)))
+        return loss.value, g
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().qmc_net_destroy(self.h)
             self.h = None
 
     def __del__(self):

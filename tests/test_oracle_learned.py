@@ -56,6 +56,21 @@ def test_adam_first_step_is_a_sign_step():
     assert np.allclose(new - th, -0.01 * g / (np.abs(g) + 1e-8), atol=1e-15)
 
 
+def test_decoupled_weight_decay_step():
+    """Zero gradient: the moments stay 0 and only the decay acts, on the
+    weight matrices and not on the biases."""
+    nf, H = 2, 3
+    th = random_params(nf, H, 12, out_scale=1.0, mu_bias=0.5)
+    n = len(th)
+    new, _, _ = LN.adam_step(th, np.zeros(n), np.zeros(n), np.zeros(n), 1, 0.1, wd=0.5,
+                             mask=LN.weight_mask(nf, H))
+    p, q = LN.unpack(th, nf, H), LN.unpack(new, nf, H)
+    for name in ("W1", "W2", "W3"):
+        assert np.allclose(q[name], p[name] * (1 - 0.05), atol=1e-15)
+    for name in ("b1", "b2", "b3"):
+        assert np.array_equal(q[name], p[name])
+
+
 def test_c_forward_equals_numpy():
     nf, H = 7, 16
     th = random_params(nf, H, 6, out_scale=0.5)
