@@ -94,10 +94,12 @@ def test_training_and_weight_decay(qmc):
     loss = net.train(400, 128, 3e-3)
     assert loss[-50:].mean() < loss[:20].mean() - 1.0
     w0 = net.get_params()
-    net.train(200, 128, 1e-3, weight_decay=5.0)
+    # lr * weight_decay = 0.02 per step: the decay factor over 200 steps is
+    # ~0.02, far below the drift Adam's own steps (~lr each) can undo
+    net.train(200, 128, 1e-3, weight_decay=20.0)
     w1 = net.get_params()
     p0, p1 = LN.unpack(w0.astype(float), net.nf, 32), LN.unpack(w1.astype(float), net.nf, 32)
-    assert np.abs(p1["W2"]).mean() < 0.6 * np.abs(p0["W2"]).mean()
+    assert np.abs(p1["W2"]).mean() < 0.4 * np.abs(p0["W2"]).mean()
 
 
 def test_learned_chain_exact_and_decorrelates_faster(qmc):
