@@ -48,9 +48,10 @@ UNIT = "effective samples/s"
 # FP64 pipe peak of a GB300: 1.25 TFLOP/s nominal = 152 SMs x 2 DFMA/clk x
 # 2 flop x 2.07 GHz (derivation and measurement in the design notes)
 FP64_PEAK_TFLOPS = 1.25
-# dram bytes per launch of the dominant kernel from the ncu capture in
-# profiles/ (null until taken for the current kernel)
-TRAFFIC_PER_LAUNCH = None
+# dram bytes (read + write) of one FP64 GEMM launch from the ncu capture
+# summarised in profiles/k_zgemm_fp64_n36_full.md (n = 36, batch 32; the
+# N = 72 batch-8 products move the same 2 MB of operands)
+TRAFFIC_PER_LAUNCH = 1338624
 # oracle sample: one sweep of an L_SAMPLE-slice chain at the same N_phi, one
 # process per chain, scaled to L = 360
 L_SAMPLE = 10
