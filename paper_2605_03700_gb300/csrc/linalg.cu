@@ -544,20 +544,24 @@ int eigh_mixed(cudaStream_t st, int n, int batch, const cd *A, cd *U, double *w,
 __global__ void __launch_bounds__(256) k_lu(int n, cd *A, long long sA, int *piv, long long spiv,
                                             cd *logdet)
 {
+    // row stride n + 1 (odd): column walks hit distinct banks
     extern __shared__ cd sm_l[];
+    const int ld = n + 1;
     cd *M = sm_l;
-    __shared__ int s_p;
+    __shared__ cd s_inv;
     const int b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    const int tx = tid & 31, ty = tid >> 5, nty = nt >> 5;
     cd *Ab = A + (long long)b * sA;
-    for (int e = tid; e < n * n; e += nt) M[e] = Ab[e];
+    for (int e = tid; e < n * n; e += nt) M[(e / n) * ld + e % n] = Ab[e];
     __syncthreads();
     int nsw = 0;
     for (int k = 0; k < n; ++k) {
-        if (tid < 32) {
+        // warp 0: pivot (first row of maximal |a_ik|), row swap, 1 / pivot
+        if (ty == 0) {
             double best = -1.0;
             int bidx = k;
-            for (int i = k + tid; i < n; i += 32) {
-                double v = cabs2(M[i * n + k]);
+            for (int i = k + tx; i < n; i += 32) {
+                double v = cabs2(M[i * ld + k]);
                 if (v > best) {
                     best = v;
                     bidx = i;
@@ -571,37 +575,41 @@ __global__ void __launch_bounds__(256) k_lu(int n, cd *A, long long sA, int *piv
                     bidx = oi;
                 }
             }
-            if (tid == 0) s_p = bidx;
-        }
-        __syncthreads();
-        int p = s_p;
-        if (p != k) {
-            for (int j = tid; j < n; j += nt) {
-                cd t = M[k * n + j];
-                M[k * n + j] = M[p * n + j];
-                M[p * n + j] = t;
+            const int p = bidx;  // identical in every lane
+            if (p != k) {
+                for (int j = tx; j < n; j += 32) {
+                    cd t = M[k * ld + j];
+                    M[k * ld + j] = M[p * ld + j];
+                    M[p * ld + j] = t;
+                }
+                ++nsw;
             }
-            ++nsw;
+            __syncwarp();
+            if (tx == 0) {
+                piv[(long long)b * spiv + k] = p;
+                s_inv = cdiv(cmk(1.0, 0.0), M[k * ld + k]);
+            }
         }
-        if (tid == 0) piv[(long long)b * spiv + k] = p;
         __syncthreads();
-        cd pk = M[k * n + k];
-        for (int i = k + 1 + tid; i < n; i += nt) M[i * n + k] = cdiv(M[i * n + k], pk);
+        const cd inv = s_inv;
+        for (int i = k + 1 + tid; i < n; i += nt) M[i * ld + k] = cmul(M[i * ld + k], inv);
         __syncthreads();
-        int w = n - k - 1;
-        for (int t = tid; t < w * w; t += nt) {
-            int i = k + 1 + t / w, j = k + 1 + t % w;
-            cd l = M[i * n + k], u = M[k * n + j];
-            cd v = M[i * n + j];
-            cfma(v, cmk(-l.x, -l.y), u);
-            M[i * n + j] = v;
+        // trailing update, rows by warp, columns by lane
+        for (int i = k + 1 + ty; i < n; i += nty) {
+            const cd l = M[i * ld + k];
+            const cd ml = cmk(-l.x, -l.y);
+            for (int j = k + 1 + tx; j < n; j += 32) {
+                cd v = M[i * ld + j];
+                cfma(v, ml, M[k * ld + j]);
+                M[i * ld + j] = v;
+            }
         }
         __syncthreads();
     }
-    for (int e = tid; e < n * n; e += nt) Ab[e] = M[e];
+    for (int e = tid; e < n * n; e += nt) Ab[e] = M[(e / n) * ld + e % n];
     if (tid == 0 && logdet) {
         cd s = cmk(0, 0);
-        for (int k = 0; k < n; ++k) s = cadd(s, clog_d(M[k * n + k]));
+        for (int k = 0; k < n; ++k) s = cadd(s, clog_d(M[k * ld + k]));
         if (nsw & 1) s.y += 3.14159265358979323846;
         logdet[b] = s;
     }
@@ -610,7 +618,7 @@ __global__ void __launch_bounds__(256) k_lu(int n, cd *A, long long sA, int *piv
 int lu_batched(cudaStream_t st, int n, cd *A, long long sA, int *piv, long long spiv, cd *logdet,
                int batch)
 {
-    size_t smem = (size_t)n * n * sizeof(cd);
+    size_t smem = (size_t)n * (n + 1) * sizeof(cd);
     if (smem > 220 * 1024) return -1;
     k_lu<<<batch, 256, smem, st>>>(n, A, sA, piv, spiv, logdet);
     QMC_COUNT(1);
@@ -630,12 +638,18 @@ __global__ void __launch_bounds__(RD_ROWS * 32) k_rdiv(int n, const cd *G, long 
                                                        long long sX)
 {
     typedef typename Cx<R>::T C;
+    // the factors transposed, row stride n + 1: FT[j (n+1) + i] = F[i][j], so
+    // the dot products over i walk consecutive addresses; dinv = 1 / U_jj
     extern __shared__ __align__(16) unsigned char sm_r_raw[];
-    C *F = (C *)sm_r_raw;
-    C *zbuf = F + n * n;
+    const int ld = n + 1;
+    C *FT = (C *)sm_r_raw;
+    C *dinv = FT + n * ld;
+    C *zbuf = dinv + n;
     const int b = blockIdx.y, tid = threadIdx.x;
     const cd *LUb = LU + (long long)b * sLU;
-    for (int e = tid; e < n * n; e += blockDim.x) F[e] = cvt<C>(LUb[e]);
+    for (int e = tid; e < n * n; e += blockDim.x) FT[(e % n) * ld + e / n] = cvt<C>(LUb[e]);
+    for (int j = tid; j < n; j += blockDim.x)
+        dinv[j] = cvt<C>(cdiv(cmk(1.0, 0.0), LUb[(long long)j * n + j]));
     __syncthreads();
     const int warp = tid >> 5, lane = tid & 31;
     const int r = blockIdx.x * RD_ROWS + warp;
@@ -646,17 +660,19 @@ __global__ void __launch_bounds__(RD_ROWS * 32) k_rdiv(int n, const cd *G, long 
     __syncwarp();
     for (int j = 0; j < n; ++j) {
         C s = czero<C>();
-        for (int i = lane; i < j; i += 32) cfma(s, z[i], F[i * n + j]);
+        const C *fj = FT + j * ld;
+        for (int i = lane; i < j; i += 32) cfma(s, z[i], fj[i]);
         for (int o = 16; o > 0; o >>= 1) {
             s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
             s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
         }
-        if (lane == 0) z[j] = cdiv(csub(z[j], s), F[j * n + j]);
+        if (lane == 0) z[j] = cmul(csub(z[j], s), dinv[j]);
         __syncwarp();
     }
     for (int j = n - 1; j >= 0; --j) {
         C s = czero<C>();
-        for (int i = j + 1 + lane; i < n; i += 32) cfma(s, z[i], F[i * n + j]);
+        const C *fj = FT + j * ld;
+        for (int i = j + 1 + lane; i < n; i += 32) cfma(s, z[i], fj[i]);
         for (int o = 16; o > 0; o >>= 1) {
             s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
             s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
@@ -685,11 +701,11 @@ int rdiv_batched(cudaStream_t st, int prec, int n, const cd *G, long long sG, co
 {
     dim3 grid(cdiv_up(n, RD_ROWS), batch);
     if (prec == TY_C64) {
-        size_t smem = ((size_t)n * n + (size_t)RD_ROWS * n) * sizeof(cd);
+        size_t smem = ((size_t)n * (n + 1) + (size_t)(RD_ROWS + 1) * n) * sizeof(cd);
         if (smem > 220 * 1024) return -1;
         k_rdiv<double><<<grid, RD_ROWS * 32, smem, st>>>(n, G, sG, LU, sLU, piv, spiv, X, sX);
     } else {
-        size_t smem = ((size_t)n * n + (size_t)RD_ROWS * n) * sizeof(cf);
+        size_t smem = ((size_t)n * (n + 1) + (size_t)(RD_ROWS + 1) * n) * sizeof(cf);
         if (smem > 220 * 1024) return -1;
         k_rdiv<float><<<grid, RD_ROWS * 32, smem, st>>>(n, G, sG, LU, sLU, piv, spiv, X, sX);
     }
@@ -717,9 +733,11 @@ __global__ void __launch_bounds__(256) k_qrp(int n, const cd *X, long long sX, c
                                              double *D, long long sD, cd *V, long long sV,
                                              int q_in_smem)
 {
+    // working matrix with row stride n + 1 (odd): column walks hit distinct banks
     extern __shared__ cd sm_q[];
+    const int ld = n + 1;
     cd *A = sm_q;
-    cd *v = A + n * n;
+    cd *v = A + n * ld;
     cd *sv = v + n;   // per-column dot products of the trailing matrix
     cd *sq = sv + n;  // per-row dot products of Q
     double *cn = (double *)(sq + n);
@@ -734,7 +752,7 @@ __global__ void __launch_bounds__(256) k_qrp(int n, const cd *X, long long sX, c
     cd *Qg = Q + (long long)b * sQ;
     cd *Qb = q_in_smem ? Qs : Qg;
     for (int e = tid; e < n * n; e += nt) {
-        A[e] = Xb[e];
+        A[(e / n) * ld + e % n] = Xb[e];
         Qb[e] = cmk((e / n) == (e % n) ? 1.0 : 0.0, 0.0);
     }
     for (int j = tid; j < n; j += nt) perm[j] = j;
@@ -743,7 +761,7 @@ __global__ void __launch_bounds__(256) k_qrp(int n, const cd *X, long long sX, c
         // remaining column norms (warp per column)
         for (int j = k + warp; j < n; j += nw) {
             double s = 0.0;
-            for (int i = k + lane; i < n; i += 32) s += cabs2(A[i * n + j]);
+            for (int i = k + lane; i < n; i += 32) s += cabs2(A[i * ld + j]);
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
             if (lane == 0) cn[j] = s;
         }
@@ -767,9 +785,9 @@ __global__ void __launch_bounds__(256) k_qrp(int n, const cd *X, long long sX, c
         const int best = s_best;
         if (best != k)
             for (int i = tid; i < n; i += nt) {
-                cd t = A[i * n + k];
-                A[i * n + k] = A[i * n + best];
-                A[i * n + best] = t;
+                cd t = A[i * ld + k];
+                A[i * ld + k] = A[i * ld + best];
+                A[i * ld + best] = t;
             }
         __syncthreads();
         // Householder vector v = x - alpha e1, alpha = -e^{i arg x0} |x|;
@@ -777,10 +795,10 @@ __global__ void __launch_bounds__(256) k_qrp(int n, const cd *X, long long sX, c
         // the column is nearly e1)
         if (warp == 0) {
             double tail = 0.0;
-            for (int i = k + 1 + lane; i < n; i += 32) tail += cabs2(A[i * n + k]);
+            for (int i = k + 1 + lane; i < n; i += 32) tail += cabs2(A[i * ld + k]);
             for (int o = 16; o > 0; o >>= 1) tail += __shfl_xor_sync(0xffffffffu, tail, o);
             if (lane == 0) {
-                cd x0 = A[k * n + k];
+                cd x0 = A[k * ld + k];
                 double ax0 = sqrt(cabs2(x0));
                 double xn = sqrt(tail + ax0 * ax0);
                 cd ph = ax0 > 0 ? cmk(x0.x / ax0, x0.y / ax0) : cmk(1, 0);
@@ -789,27 +807,30 @@ __global__ void __launch_bounds__(256) k_qrp(int n, const cd *X, long long sX, c
                 double vn = tail + cabs2(v0);
                 v[k] = v0;
                 s_f = (xn == 0.0 || vn == 0.0) ? 0.0 : 2.0 / vn;
-                A[k * n + k] = alpha;
+                A[k * ld + k] = alpha;
             }
         }
-        for (int i = k + 1 + tid; i < n; i += nt) v[i] = A[i * n + k];
+        for (int i = k + 1 + tid; i < n; i += nt) v[i] = A[i * ld + k];
         __syncthreads();
         const double f = s_f;
         if (f != 0.0) {
             // s_j = f sum_i conj(v_i) A_ij for the trailing columns
             for (int j = k + 1 + warp; j < n; j += nw) {
                 cd s = cmk(0, 0);
-                for (int i = k + lane; i < n; i += 32) cfma(s, cconj(v[i]), A[i * n + j]);
+                for (int i = k + lane; i < n; i += 32) cfma(s, cconj(v[i]), A[i * ld + j]);
                 s = warp_csum(s);
                 if (lane == 0) sv[j] = cscale(s, f);
             }
             __syncthreads();
-            const int w = n - k, wj = n - k - 1;
-            for (int t = tid; t < w * wj; t += nt) {
-                int i = k + t / wj, j = k + 1 + t % wj;
-                cd a = A[i * n + j], sj = sv[j];
-                cfma(a, cmk(-sj.x, -sj.y), v[i]);
-                A[i * n + j] = a;
+            // A_ij -= s_j v_i: rows by warp, columns by lane
+            for (int i = k + warp; i < n; i += nw) {
+                const cd vi = v[i];
+                for (int j = k + 1 + lane; j < n; j += 32) {
+                    const cd sj = sv[j];
+                    cd a = A[i * ld + j];
+                    cfma(a, cmk(-sj.x, -sj.y), vi);
+                    A[i * ld + j] = a;
+                }
             }
             // t_r = f sum_i Q_ri v_i, Q_ri -= t_r conj(v_i)
             for (int r = warp; r < n; r += nw) {
@@ -819,23 +840,26 @@ __global__ void __launch_bounds__(256) k_qrp(int n, const cd *X, long long sX, c
                 if (lane == 0) sq[r] = cscale(s, f);
             }
             __syncthreads();
-            for (int t = tid; t < n * w; t += nt) {
-                int r = t / w, i = k + t % w;
-                cd q = Qb[(long long)r * n + i], tr = sq[r];
-                cfma(q, cmk(-tr.x, -tr.y), cconj(v[i]));
-                Qb[(long long)r * n + i] = q;
+            for (int r = warp; r < n; r += nw) {
+                const cd tr = sq[r];
+                const cd mt = cmk(-tr.x, -tr.y);
+                for (int i = k + lane; i < n; i += 32) {
+                    cd q = Qb[(long long)r * n + i];
+                    cfma(q, mt, cconj(v[i]));
+                    Qb[(long long)r * n + i] = q;
+                }
             }
         }
-        for (int i = k + 1 + tid; i < n; i += nt) A[i * n + k] = cmk(0, 0);
+        for (int i = k + 1 + tid; i < n; i += nt) A[i * ld + k] = cmk(0, 0);
         __syncthreads();
     }
     double *Db = D + (long long)b * sD;
     cd *Vb = V + (long long)b * sV;
-    for (int i = tid; i < n; i += nt) Db[i] = sqrt(cabs2(A[i * n + i]));
+    for (int i = tid; i < n; i += nt) Db[i] = sqrt(cabs2(A[i * ld + i]));
     for (int e = tid; e < n * n; e += nt) {
         int i = e / n, j = e % n;
-        double di = sqrt(cabs2(A[i * n + i]));
-        cd val = (j >= i) ? A[i * n + j] : cmk(0, 0);
+        double di = sqrt(cabs2(A[i * ld + i]));
+        cd val = (j >= i) ? A[i * ld + j] : cmk(0, 0);
         Vb[(long long)i * n + perm[j]] = cmk(val.x / di, val.y / di);
         if (q_in_smem) Qg[e] = Qs[e];
     }
@@ -844,7 +868,7 @@ __global__ void __launch_bounds__(256) k_qrp(int n, const cd *X, long long sX, c
 int qrp_batched(cudaStream_t st, int n, const cd *X, long long sX, cd *Q, long long sQ, double *D,
                 long long sD, cd *V, long long sV, int batch)
 {
-    size_t base = (size_t)n * n * sizeof(cd) + 3 * (size_t)n * sizeof(cd) +
+    size_t base = (size_t)n * (n + 1) * sizeof(cd) + 3 * (size_t)n * sizeof(cd) +
                   (size_t)n * sizeof(double) + (size_t)n * sizeof(int) + 16;
     size_t withq = base + (size_t)n * n * sizeof(cd);
     int qs = withq <= 220 * 1024;
