@@ -265,8 +265,10 @@ int gemm_autotune(cudaStream_t st, const GemmP &p, int batch, float *best_ms)
 // every 2x2 block A[{p1,q1},{p2,q2}] maps to J_1^H A_blk J_2 independently, so
 // a round is one parallel phase over the (n/2)^2 blocks.
 // Sweeps stop when off-diagonal Frobenius norm^2 <= tol * total.
-template <class R>
-__global__ void __launch_bounds__(256) k_eigh(int n, const void *Hv, long long sH, void *Uv,
+// NT threads per block: 256 for FP64 (FP64-pipe bound), 1024 for FP32 (one
+// pass per round over the block and column updates: latency bound)
+template <class R, int NT>
+__global__ void __launch_bounds__(NT) k_eigh(int n, const void *Hv, long long sH, void *Uv,
                                               long long sU, void *wv, long long sw,
                                               const void *V0v, long long sV0, R tol)
 {
@@ -423,11 +425,11 @@ int eigh_batched(cudaStream_t st, int prec, int n, const void *H, long long sH, 
     if (n > 64 || batch <= 0) return batch <= 0 ? 0 : -1;
     if (prec == TY_C64) {
         size_t smem = 2ull * n * n * sizeof(cd);
-        k_eigh<double><<<batch, 256, smem, st>>>(n, H, sH, U, sU, w, sw, V0, sV0,
+        k_eigh<double, 256><<<batch, 256, smem, st>>>(n, H, sH, U, sU, w, sw, V0, sV0,
                                                  tol > 0 ? tol : 1e-34);
     } else {
         size_t smem = 2ull * n * n * sizeof(cf);
-        k_eigh<float><<<batch, 256, smem, st>>>(n, H, sH, U, sU, w, sw, V0, sV0,
+        k_eigh<float, 1024><<<batch, 1024, smem, st>>>(n, H, sH, U, sU, w, sw, V0, sV0,
                                                 (float)(tol > 0 ? tol : 1e-10));
     }
     QMC_COUNT(1);
@@ -798,19 +800,31 @@ __global__ void __launch_bounds__(256) k_qrp(int n, const cd *X, long long sX, c
             if (lane == 0) cn[j] = s;
         }
         __syncthreads();
-        if (tid == 0) {
-            int best = k;
+        // pivot: first column of largest norm, warp-parallel (FP64 compares
+        // run on the FP64 pipe: a serial scan by one thread cost ~15% here)
+        if (warp == 0) {
+            int best = n;
             double bn = -1.0;
-            for (int j = k; j < n; ++j)
+            for (int j = k + lane; j < n; j += 32)
                 if (cn[j] > bn) {
                     bn = cn[j];
                     best = j;
                 }
-            s_best = best;
-            if (best != k) {
-                int t = perm[k];
-                perm[k] = perm[best];
-                perm[best] = t;
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, bn, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, best, o);
+                if (ov > bn || (ov == bn && oi < best)) {
+                    bn = ov;
+                    best = oi;
+                }
+            }
+            if (lane == 0) {
+                s_best = best;
+                if (best != k) {
+                    int t = perm[k];
+                    perm[k] = perm[best];
+                    perm[best] = t;
+                }
             }
         }
         __syncthreads();
@@ -833,7 +847,8 @@ __global__ void __launch_bounds__(256) k_qrp(int n, const cd *X, long long sX, c
                 cd x0 = A[k * ld + k];
                 double ax0 = sqrt(cabs2(x0));
                 double xn = sqrt(tail + ax0 * ax0);
-                cd ph = ax0 > 0 ? cmk(x0.x / ax0, x0.y / ax0) : cmk(1, 0);
+                const double rax = ax0 > 0 ? 1.0 / ax0 : 0.0;
+                cd ph = ax0 > 0 ? cmk(x0.x * rax, x0.y * rax) : cmk(1, 0);
                 cd alpha = cmk(-ph.x * xn, -ph.y * xn);
                 cd v0 = csub(x0, alpha);
                 double vn = tail + cabs2(v0);
@@ -922,9 +937,9 @@ int qrp_batched(cudaStream_t st, int n, const cd *X, long long sX, cd *Q, long l
 // current device (once per context creation, never inside a stream capture)
 void linalg_init()
 {
-    cudaFuncSetAttribute(k_eigh<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_eigh<double, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          2 * 64 * 64 * 16);
-    cudaFuncSetAttribute(k_eigh<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_eigh<float, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          2 * 64 * 64 * 8);
     cudaFuncSetAttribute(k_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     cudaFuncSetAttribute(k_rdiv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
