@@ -785,19 +785,21 @@ __global__ void __launch_bounds__(256) k_qrp(int n, const cd *X, long long sX, c
     const cd *Xb = X + (long long)b * sX;
     cd *Qg = Q + (long long)b * sQ;
     cd *Qb = q_in_smem ? Qs : Qg;
+    const int qld = q_in_smem ? n + 1 : n;  // Q row stride (padded in shared memory)
     for (int e = tid; e < n * n; e += nt) {
         A[(e / n) * ld + e % n] = Xb[e];
-        Qb[e] = cmk((e / n) == (e % n) ? 1.0 : 0.0, 0.0);
+        Qb[(e / n) * qld + e % n] = cmk((e / n) == (e % n) ? 1.0 : 0.0, 0.0);
     }
     for (int j = tid; j < n; j += nt) perm[j] = j;
     __syncthreads();
     for (int k = 0; k < n; ++k) {
-        // remaining column norms (warp per column)
-        for (int j = k + warp; j < n; j += nw) {
+        // remaining column norms, one thread per column (a warp reduction per
+        // column would spend more FP64 instructions on the reduction than on
+        // the sum: FP64 issue is the limit on this part)
+        for (int j = k + tid; j < n; j += nt) {
             double s = 0.0;
-            for (int i = k + lane; i < n; i += 32) s += cabs2(A[i * ld + j]);
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) cn[j] = s;
+            for (int i = k; i < n; ++i) s += cabs2(A[i * ld + j]);
+            cn[j] = s;
         }
         __syncthreads();
         // pivot: first column of largest norm, warp-parallel (FP64 compares
@@ -861,15 +863,21 @@ __global__ void __launch_bounds__(256) k_qrp(int n, const cd *X, long long sX, c
         __syncthreads();
         const double f = s_f;
         if (f != 0.0) {
-            // s_j = f sum_i conj(v_i) A_ij for the trailing columns
-            for (int j = k + 1 + warp; j < n; j += nw) {
-                cd s = cmk(0, 0);
-                for (int i = k + lane; i < n; i += 32) cfma(s, cconj(v[i]), A[i * ld + j]);
-                s = warp_csum(s);
-                if (lane == 0) sv[j] = cscale(s, f);
+            // s_j = f sum_i conj(v_i) A_ij (trailing columns) and
+            // t_r = f sum_i Q_ri v_i (rows of Q): one thread per output
+            for (int j = k + 1 + tid; j < n; j += nt) {
+                cd sacc = cmk(0, 0);
+                for (int i = k; i < n; ++i) cfma(sacc, cconj(v[i]), A[i * ld + j]);
+                sv[j] = cscale(sacc, f);
+            }
+            for (int r = tid; r < n; r += nt) {
+                cd sacc = cmk(0, 0);
+                const cd *qr = Qb + (long long)r * qld;
+                for (int i = k; i < n; ++i) cfma(sacc, qr[i], v[i]);
+                sq[r] = cscale(sacc, f);
             }
             __syncthreads();
-            // A_ij -= s_j v_i: rows by warp, columns by lane
+            // A_ij -= s_j v_i and Q_ri -= t_r conj(v_i): rows by warp, columns by lane
             for (int i = k + warp; i < n; i += nw) {
                 const cd vi = v[i];
                 for (int j = k + 1 + lane; j < n; j += 32) {
@@ -879,21 +887,13 @@ __global__ void __launch_bounds__(256) k_qrp(int n, const cd *X, long long sX, c
                     A[i * ld + j] = a;
                 }
             }
-            // t_r = f sum_i Q_ri v_i, Q_ri -= t_r conj(v_i)
-            for (int r = warp; r < n; r += nw) {
-                cd s = cmk(0, 0);
-                for (int i = k + lane; i < n; i += 32) cfma(s, Qb[(long long)r * n + i], v[i]);
-                s = warp_csum(s);
-                if (lane == 0) sq[r] = cscale(s, f);
-            }
-            __syncthreads();
             for (int r = warp; r < n; r += nw) {
                 const cd tr = sq[r];
                 const cd mt = cmk(-tr.x, -tr.y);
                 for (int i = k + lane; i < n; i += 32) {
-                    cd q = Qb[(long long)r * n + i];
+                    cd q = Qb[(long long)r * qld + i];
                     cfma(q, mt, cconj(v[i]));
-                    Qb[(long long)r * n + i] = q;
+                    Qb[(long long)r * qld + i] = q;
                 }
             }
         }
@@ -914,7 +914,7 @@ __global__ void __launch_bounds__(256) k_qrp(int n, const cd *X, long long sX, c
         int i = e / n, j = e % n;
         cd val = (j >= i) ? A[i * ld + j] : cmk(0, 0);
         Vb[(long long)i * n + perm[j]] = cscale(val, rinv[i]);
-        if (q_in_smem) Qg[e] = Qs[e];
+        if (q_in_smem) Qg[e] = Qs[i * qld + j];
     }
 }
 
@@ -923,7 +923,7 @@ int qrp_batched(cudaStream_t st, int n, const cd *X, long long sX, cd *Q, long l
 {
     size_t base = (size_t)n * (n + 1) * sizeof(cd) + 3 * (size_t)n * sizeof(cd) +
                   (size_t)n * sizeof(double) + (size_t)n * sizeof(int) + 16;
-    size_t withq = base + (size_t)n * n * sizeof(cd);
+    size_t withq = base + (size_t)n * (n + 1) * sizeof(cd);
     int qs = withq <= 220 * 1024;
     size_t smem = qs ? withq : base;
     if (smem > 220 * 1024) return -1;
