@@ -380,6 +380,7 @@ static int update_slice(qmc_ctx *ctx, int t, qmc_net *net = nullptr, double rho 
     ap.gradp = ctx->gradp;
     ap.eps = ctx->eps;
     ap.lq = net ? ctx->lq : nullptr;
+    ap.lq_n = net_pcn_blocks(nf);
     ap.rho = rho;
     ap.alpha = ctx->alpha_d;
     ap.logdet = ctx->logdet;
@@ -655,7 +656,7 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
     const int nf = ctx->nf;
     // device allocations
     DA(ctx->ctr, QMC_CTR_N);
-    DA(ctx->lq, nb);
+    DA(ctx->lq, (size_t)nb * net_pcn_blocks(nf));
     DA(ctx->qxy, 2 * nq);
     DA(ctx->ff_val, (size_t)nq * n);
     DA(ctx->ff_col, (size_t)nq * n);

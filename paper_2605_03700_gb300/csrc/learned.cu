@@ -53,6 +53,36 @@ __global__ void k_dense_fwd(int B, int In, int Out, const float *X, const __nv_b
     }
 }
 
+// the same for at most QMC_NET_SMALLB rows (the sweep's chains): one warp per
+// output neuron, lanes over the input; the tiled kernel above would run the
+// first layer on Out/16 = 16 CTAs
+#define QMC_NET_SMALLB 16
+__global__ void k_dense_fwd_rows(int B, int In, int Out, const float *X, const __nv_bfloat16 *W,
+                                 const float *bias, float *A, float *Hout, int act)
+{
+    const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (o >= Out) return;  // whole warps leave together
+    float acc[QMC_NET_SMALLB];
+#pragma unroll
+    for (int b = 0; b < QMC_NET_SMALLB; ++b) acc[b] = 0.0f;
+    const __nv_bfloat16 *w = W + (long long)o * In;
+    for (int k = lane; k < In; k += 32) {
+        const float wk = to_f(w[k]);
+#pragma unroll
+        for (int b = 0; b < QMC_NET_SMALLB; ++b)
+            if (b < B) acc[b] += wk * X[(long long)b * In + k];
+    }
+#pragma unroll
+    for (int b = 0; b < QMC_NET_SMALLB; ++b)
+        for (int s = 16; s > 0; s >>= 1) acc[b] += __shfl_xor_sync(0xffffffffu, acc[b], s);
+    if (lane == 0)
+        for (int b = 0; b < B; ++b) {
+            const float a = acc[b] + bias[o];
+            if (A) A[(long long)b * Out + o] = a;
+            Hout[(long long)b * Out + o] = act ? silu_f(a) : a;
+        }
+}
+
 // dX[b][i] = sum_o dA[b][o] W[o][i]
 __global__ void k_dense_bwd_x(int B, int In, int Out, const float *dA, const __nv_bfloat16 *W,
                               float *dX)
@@ -213,20 +243,22 @@ __global__ void __launch_bounds__(256) k_pcn(int nf, const float *O, const doubl
                                              double *lq)
 {
     __shared__ double red[8];
-    const int c = blockIdx.x;
+    const int c = blockIdx.y;
     const uint32_t sweep = ctr[QMC_CTR_SWEEP];
     const double cr = sqrt(1.0 - rho * rho);
     const double *ph = phi + (long long)c * phi_cs;
     const float *o = O + (long long)c * 2 * nf;
     double part = 0.0;
-    for (int f = threadIdx.x; f < nf; f += blockDim.x) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f < nf) {
         const double mu = (double)o[f], sig = exp((double)o[nf + f]);
         const double xi = rng_normal((uint32_t)f, slice0, sweep, RNG_NOISE, keys[2 * c],
                                      keys[2 * c + 1]);
         const double x = ph[f];
         const double xp = mu + rho * (x - mu) + cr * sig * xi;
         phip[(long long)c * nf + f] = xp;
-        const double a = (xp - mu) / sig, b = (x - mu) / sig;
+        const double is = 1.0 / sig;
+        const double a = (xp - mu) * is, b = (x - mu) * is;
         part += -0.5 * a * a + 0.5 * b * b;
     }
     for (int s = 16; s > 0; s >>= 1) part += __shfl_xor_sync(0xffffffffu, part, s);
@@ -235,7 +267,7 @@ __global__ void __launch_bounds__(256) k_pcn(int nf, const float *O, const doubl
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        lq[c] = t;
+        lq[(long long)c * gridDim.x + blockIdx.x] = t;  // partial of this block
     }
 }
 
@@ -280,8 +312,12 @@ int net_ensure_rows(qmc_net *net, int rows)
 static void dense(cudaStream_t s, int B, int In, int Out, const float *X, const __nv_bfloat16 *W,
                   const float *b, float *A, float *H, int act)
 {
-    dim3 g((Out + LT - 1) / LT, (B + LT - 1) / LT), t(LT, LT);
-    k_dense_fwd<<<g, t, 0, s>>>(B, In, Out, X, W, b, A, H, act);
+    if (B <= QMC_NET_SMALLB) {
+        k_dense_fwd_rows<<<(Out + 7) / 8, 256, 0, s>>>(B, In, Out, X, W, b, A, H, act);
+    } else {
+        dim3 g((Out + LT - 1) / LT, (B + LT - 1) / LT), t(LT, LT);
+        k_dense_fwd<<<g, t, 0, s>>>(B, In, Out, X, W, b, A, H, act);
+    }
     QMC_COUNT(1);
 }
 
@@ -331,7 +367,8 @@ void net_gather_context(qmc_net *net, cudaStream_t s, int nb, int L, int slice0,
 void net_pcn(qmc_net *net, cudaStream_t s, int nb, const double *phi, long long phi_cs, double rho,
              const uint32_t *keys, uint32_t slice0, const uint32_t *ctr, double *phip, double *lq)
 {
-    k_pcn<<<nb, 256, 0, s>>>(net->nf, net->O, phi, phi_cs, rho, keys, slice0, ctr, phip, lq);
+    k_pcn<<<dim3(net_pcn_blocks(net->nf), nb), 256, 0, s>>>(net->nf, net->O, phi, phi_cs, rho,
+                                                             keys, slice0, ctr, phip, lq);
     QMC_COUNT(1);
 }
 

@@ -39,8 +39,10 @@ void net_forward(qmc_net *net, cudaStream_t s, int rows);
 // X rows = [phi_{tau-1}, phi_{tau+1}] of every chain (FP64 fields, chain stride phi_cs)
 void net_gather_context(qmc_net *net, cudaStream_t s, int nb, int L, int slice0,
                         const double *phi, long long phi_cs);
-// phi' = mu + rho (phi - mu) + sqrt(1 - rho^2) sigma xi and
-// lq = log N(phi') - log N(phi) per chain, from net->O
+// phi' = mu + rho (phi - mu) + sqrt(1 - rho^2) sigma xi and the partial sums
+// of lq = log N(phi') - log N(phi): net_pcn_blocks(nf) per chain,
+// lq[c * blocks + j] (summed in order by the accept kernel)
+inline int net_pcn_blocks(int nf) { return (nf + 255) / 256; }
 void net_pcn(qmc_net *net, cudaStream_t s, int nb, const double *phi, long long phi_cs, double rho,
              const uint32_t *keys, uint32_t slice0, const uint32_t *ctr, double *phip, double *lq);
 // append the configuration [L][nf] of each of nb chains (chain stride phi_cs)

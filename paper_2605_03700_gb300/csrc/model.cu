@@ -446,7 +446,10 @@ __global__ void __launch_bounds__(256) k_accept(AcceptP p)
         cd lr = csub(p.logdet[c], cscale(csub(w0p, w0), 0.5));
         // Langevin move: the proposal densities; learned move: the pCN
         // reference-density correction (both exact MH for the same target)
-        double logA = learned ? 2.0 * lr.x - (s0p - s0) - p.lq[c]
+        double lqc = 0.0;
+        if (learned)
+            for (int j = 0; j < p.lq_n; ++j) lqc += p.lq[(long long)c * p.lq_n + j];
+        double logA = learned ? 2.0 * lr.x - (s0p - s0) - lqc
                               : 2.0 * lr.x - (s0p - s0) - bw / (2 * e * e) + fw / (2 * e * e);
         u32x4 wv = philox10(u32x4{0u, (uint32_t)(p.slice - 1), sweep, (uint32_t)RNG_ACCEPT},
                             p.keys[2 * c], p.keys[2 * c + 1]);

@@ -12,6 +12,7 @@ struct AcceptP {
     long long phi_cs;
     const double *phip, *grad, *gradp, *eps;
     const double *lq;  // non-null: learned move, lq = log N(phi') - log N(phi) per chain
+    int lq_n;          // as lq_n partial sums per chain, lq[c * lq_n + j]
     double rho;        // its pCN parameter (recorded in the trace)
     const cd *alpha, *logdet, *trF;
     const int *fkind, *frA, *frB;
