@@ -146,35 +146,33 @@ static void factors_from_eig(qmc_ctx *ctx, const cd *U, long long U_cs, const do
         launch_lambda(ctx->st, ctx->gp, nb, ctx->n, W, W_cs, ctx->alpha_d, lamG, DgG, DgiG);
 }
 
-// B = V0 D0 T01 D1 T12 D2 T23 D3 T23^H D4 T12^H D5 T01^H D6 V0^H and the
-// inverse with the diagonals reversed and inverted (FP64)
+// B = V0 D0 T01 D1 T12 D2 T23 D3 T23^H D2 T12^H D1 T01^H D0 V0^H and the
+// inverse with the diagonals inverted (FP64).  The product is a palindrome:
+// with Z = T01 D1 T12 D2 T23, B = (V0 D0 Z) D3 (V0 D0^* Z)^H, because in the
+// sign-free region D1, D2 are real (alpha_1,2 real: g_1,2 = -2u <= 0) and D0
+// is a phase (alpha_0 imaginary: g_0 > 0), so D0^* = D0^-1.  Five products
+// per matrix instead of seven.
 static void build_B(qmc_ctx *ctx, const cd *V, const cd *T, const cd *Dg, const cd *Dgi, cd *Bout,
                     long long Bo_cs, cd *Biout, long long Bio_cs)
 {
     const int nb = ctx->nb, N = ctx->N;
-    const long long NN = ctx->NN;
-    const int tidx[6] = {0, 1, 2, 2, 1, 0};
+    const long long NN = ctx->NN, dcs = 7LL * N;
+    cudaStream_t s = ctx->st;
     for (int inv = 0; inv < 2; ++inv) {
-        const cd *dg = inv ? Dgi : Dg;
+        const cd *dg = inv ? Dgi : Dg;   // D_j (or D_j^-1) at Trotter position j
+        const cd *dgc = inv ? Dg : Dgi;  // conj of position 0: D0^* = D0^-1
         cd *dst = inv ? Biout : Bout;
-        long long dcs = inv ? Bio_cs : Bo_cs;
-        cd *a = ctx->X1, *b = ctx->X2;
-        for (int step = 0; step < 7; ++step) {
-            int j = inv ? 6 - step : step;  // diagonal used at this position
-            const cd *dj = dg + (long long)j * N;
-            if (step == 0) {
-                gemm_sq(ctx->st, N, nb, TY_C64, op64(V, 4 * NN), 0, op64(T, 3 * NN), 0,
-                        op64(a, NN), dj, 7 * N);
-            } else if (step < 6) {
-                int op = step < 3 ? 0 : 2;
-                gemm_sq(ctx->st, N, nb, TY_C64, op64(a, NN), 0,
-                        op64(T + (long long)tidx[step] * NN, 3 * NN), op, op64(b, NN), dj, 7 * N);
-                std::swap(a, b);
-            } else {
-                gemm_sq(ctx->st, N, nb, TY_C64, op64(a, NN), 0, op64(V, 4 * NN), 2,
-                        op64(dst, dcs), dj, 7 * N);
-            }
-        }
+        const long long dst_cs = inv ? Bio_cs : Bo_cs;
+        gemm_sq(s, N, nb, TY_C64, op64(T, 3 * NN), 0, op64(T + NN, 3 * NN), 0, op64(ctx->X1, NN),
+                dg + 1 * N, dcs);
+        gemm_sq(s, N, nb, TY_C64, op64(ctx->X1, NN), 0, op64(T + 2 * NN, 3 * NN), 0,
+                op64(ctx->X2, NN), dg + 2 * N, dcs);
+        gemm_sq(s, N, nb, TY_C64, op64(V, 4 * NN), 0, op64(ctx->X2, NN), 0, op64(ctx->X1, NN), dg,
+                dcs);
+        gemm_sq(s, N, nb, TY_C64, op64(V, 4 * NN), 0, op64(ctx->X2, NN), 0, op64(ctx->M, NN), dgc,
+                dcs);
+        gemm_sq(s, N, nb, TY_C64, op64(ctx->X1, NN), 0, op64(ctx->M, NN), 2, op64(dst, dst_cs),
+                dg + 3 * N, dcs);
     }
 }
 
