@@ -320,7 +320,9 @@ long long qmc_launch_count(void);
 /* Tile edge the GEMM autotuner chose for n x n complex products computed in
  * FP64 (precision 0) or FP32 (precision 1); qmc_create times every candidate
  * (8, 12, 16, 18, 24, 32) on its own sizes and batch and keeps the fastest;
- * 16 before any tuning. */
+ * 16 before any tuning.  The environment variable QMC_GEMM_TILE=<edge> (one
+ * of the candidates) fixes the edge for every size instead of timing (for
+ * profiler runs, whose serialised launches make the timings meaningless). */
 int qmc_gemm_tile(int n, int precision);
 
 /* Event timing of every batched complex GEMM launch computed in FP64 (the

@@ -6,6 +6,7 @@
 // complex.
 #include "linalg.cuh"
 
+#include <cstdlib>
 #include <vector>
 
 // ------------------------------------------------------------------ GEMM --
@@ -218,6 +219,18 @@ int gemm_autotune(cudaStream_t st, const GemmP &p, int batch, float *best_ms)
     // then time every tile edge in three interleaved rounds of 10 launches and
     // keep each edge's fastest round: single short timings picked a tile 1.6x
     // slower than the best
+    // QMC_GEMM_TILE=<edge> fixes the edge without timing: under a profiler
+    // that serialises launches the timings are meaningless (ncu runs picked
+    // an edge 3.5x slower than the tuned one)
+    if (const char *env = getenv("QMC_GEMM_TILE")) {
+        const int t = atoi(env);
+        for (int i = 0; i < kNTiles; ++i)
+            if (kTiles[i] == t) {
+                gemm_set_tile(p.N, p.rc, t);
+                if (best_ms) *best_ms = 0.f;
+                return t;
+            }
+    }
     const int R = 10, rounds = 3;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
