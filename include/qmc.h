@@ -277,7 +277,9 @@ double qmc_tau_int(const double *x, int n);
  * ratio det(1 + B'(b,0))/det(1 + B(b,0)) = det M with
  * M = 1 + (Delta - 1)(1 - G), Delta = B'_tau B_tau^-1, and the new
  * G' = G M^-1 of Eq. green_function), for `batch` independent matrices.
- *   N       matrix size (single-particle states of one spin block), 1..116
+ *   N       matrix size (single-particle states of one spin block), 1..112
+ *           (the LU and division kernels keep one matrix in one CTA's shared
+ *           memory; also the largest N of a context)
  *   G       device, batch x N x N, row-major interleaved complex (2 doubles)
  *   Delta   device, same layout
  *   Gp      device output, same layout (must not alias G or Delta)
@@ -285,7 +287,9 @@ double qmc_tau_int(const double *x, int n);
  *           imaginary part modulo 2 pi)
  *   stream  cudaStream_t or NULL
  * Scratch (3 batch N^2 complex + batch N ints) is allocated with cudaMalloc
- * and freed before returning; the call synchronises `stream`. */
+ * and freed before returning; the call synchronises `stream`.  The first call
+ * on a device (without a context) also sets the kernels' shared-memory
+ * limits on it. */
 int qmc_ratio_update(int N, int batch, const double *G, const double *Delta, double *Gp,
                      double *logdet, void *stream);
 
@@ -302,8 +306,9 @@ int qmc_ratio_update(int N, int batch, const double *G, const double *Delta, dou
  *   (N = 72: batch <= 33); larger requests return QMC_ERR_ARG before any
  *   device work.
  *   The first call on a device looks up the array's device address with
- *   cudaGetSymbolAddress (that device must be current); make that first call
- *   before any stream capture.  Later calls only enqueue kernels.
+ *   cudaGetSymbolAddress (that device must be current) and sets the kernels'
+ *   shared-memory limits on it; make that first call before any stream
+ *   capture.  Later calls only enqueue kernels.
  *   Asynchronous: the outputs are valid once `stream` has been synchronised.
  *   Every call shares the one scratch array and leaves its contents behind
  *   (nothing in it has to start at zero); calls that overlap on the GPU --

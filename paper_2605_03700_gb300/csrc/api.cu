@@ -1351,11 +1351,13 @@ int qmc_gemm_tile(int n, int precision)
 int qmc_ratio_update_noalloc(int N, int batch, const double *G, const double *Delta,
                              double *Gp, double *logdet, void *stream)
 {
-    if (N < 1 || N > 116 || batch < 1 || !G || !Delta || !Gp || !logdet) return QMC_ERR_ARG;
+    if (N < 1 || N > 112 || batch < 1 || !G || !Delta || !Gp || !logdet) return QMC_ERR_ARG;
     const size_t NN = (size_t)N * N;
     const size_t mat = round256(sizeof(cd) * NN * (size_t)batch);
     const size_t pv = round256(sizeof(int) * (size_t)N * (size_t)batch);
     if (3 * mat + pv > QMC_NOALLOC_SCRATCH_BYTES) return QMC_ERR_ARG;
+    // shared-memory limits of the LU / division kernels (no context here)
+    if (!linalg_init_current_device()) return QMC_ERR_CUDA;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= QMC_NOALLOC_MAX_DEVICES)
         return QMC_ERR_CUDA;
@@ -1377,9 +1379,11 @@ int qmc_ratio_update_noalloc(int N, int batch, const double *G, const double *De
 int qmc_ratio_update(int N, int batch, const double *G, const double *Delta, double *Gp,
                      double *logdet, void *stream)
 {
-    if (N < 1 || N > 116 || batch < 1 || !G || !Delta || !Gp || !logdet) return QMC_ERR_ARG;
+    if (N < 1 || N > 112 || batch < 1 || !G || !Delta || !Gp || !logdet) return QMC_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t NN = (size_t)N * N;
+    // shared-memory limits of the LU / division kernels (no context here)
+    if (!linalg_init_current_device()) return QMC_ERR_CUDA;
     cd *X1 = nullptr, *X2 = nullptr, *M = nullptr;
     int *piv = nullptr;
     int code = QMC_OK;

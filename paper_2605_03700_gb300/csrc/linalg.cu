@@ -960,3 +960,16 @@ void linalg_init()
     cudaFuncSetAttribute(k_qrp, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
 }
 
+// linalg_init once per device, for entry points that run without a context
+// (the standalone ratio updates); returns false if the device is unknown
+bool linalg_init_current_device()
+{
+    static bool done[64] = {false};
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    if (!done[dev]) {
+        linalg_init();
+        done[dev] = true;
+    }
+    return true;
+}

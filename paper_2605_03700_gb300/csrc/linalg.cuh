@@ -24,6 +24,8 @@ struct GemmP {
 };
 
 void linalg_init();
+// linalg_init once per device (context-free entry points)
+bool linalg_init_current_device();
 int zgemm(cudaStream_t st, const GemmP &p, int batch);
 // pause (false) or resume the per-launch GEMM timing; returns the previous state
 bool gemm_prof_enable(bool on);
