@@ -248,3 +248,30 @@ def test_mixed_precision_full_workload_properties(qmc):
     assert s[:, :, 15].max() < 1e-8 and s[:, :, 16].max() < 1e-8
     assert np.all(np.isfinite(s))
     assert 0.2 < s[:, :, 13].mean() < 0.95
+
+
+def test_ratio_update_in_a_fresh_process(qmc):
+    """The context-free entry points must work in a process that never
+    created a context (the kernels' shared-memory limits are set by the
+    entry point itself)."""
+    import os
+    import subprocess
+    import sys
+    code = (
+        "import ctypes as C, numpy as np, torch\n"
+        "from paper_2605_03700_gb300 import qmc\n"
+        "N, b = 72, 2\n"
+        "r = np.random.default_rng(1)\n"
+        "G = torch.tensor(0.5 * np.eye(N) + 0.01 * r.normal(size=(b, N, N)), dtype=torch.complex128, device='cuda')\n"
+        "D = torch.tensor(np.eye(N) + 0.01 * r.normal(size=(b, N, N)), dtype=torch.complex128, device='cuda')\n"
+        "for f in (qmc.lib().qmc_ratio_update, qmc.lib().qmc_ratio_update_noalloc):\n"
+        "    Gp = torch.empty_like(G); ld = torch.empty(b, dtype=torch.complex128, device='cuda')\n"
+        "    c = f(N, b, C.c_void_p(G.data_ptr()), C.c_void_p(D.data_ptr()), C.c_void_p(Gp.data_ptr()),\n"
+        "          C.c_void_p(ld.data_ptr()), C.c_void_p(0))\n"
+        "    torch.cuda.synchronize()\n"
+        "    assert c == 0 and torch.isfinite(ld).all(), c\n"
+        "print('ok')\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True,
+                         timeout=300)
+    assert out.returncode == 0 and out.stdout.strip().endswith("ok"), out.stderr[-2000:]
