@@ -145,8 +145,7 @@ int qmc_sweep(qmc_ctx *ctx, int n_sweeps);
 int qmc_sweep_graph(qmc_ctx *ctx, int n_sweeps);
 
 /* ------------------------------------------------------------------------
- * Learned slice proposal (not in the paper; the learned pattern of the build
- * target).  A small network gives, for slice tau, a Gaussian
+ * Learned slice proposal (not in the paper; an addition to the method).  A small network gives, for slice tau, a Gaussian
  * N(mu, diag sigma^2) of the slice's nf = 4 N_q real fields from the
  * neighbouring slices tau-1 and tau+1 (cyclic):
  *     h1 = silu(W1 x + b1), h2 = silu(W2 h1 + b2), [mu, log sigma] = W3 h2 + b3,
@@ -207,7 +206,7 @@ int qmc_net_loss_grad(qmc_net *net, const float *X, const float *Y, int batch, d
  * must equal the context's 4 N_q); trace column 7 holds rho. */
 int qmc_sweep_learned(qmc_ctx *ctx, qmc_net *net, int n_sweeps, double rho);
 
-/* Batched chains of different sizes (BASELINE pattern, not in the paper): a
+/* Batched chains of different sizes (not in the paper; a deployment feature): a
  * group sweeps several contexts -- any mix of geometry, orbital count,
  * couplings and precision -- as one CUDA graph per sweep.  Each member's
  * sweep is captured on its own branch of the graph, so kernels of different

@@ -32,8 +32,8 @@
  *   RNG                the paper is silent: Philox4x32-10 (Salmon et al.,
  *                      SC'11), counter = (index, slice, sweep, purpose),
  *                      key = (seed low, seed high), Box-Muller normals
- *   learned slice move not in the paper (the build target's learned
- *                      proposal): an MLP gives a Gaussian N(mu, sigma^2) for
+ *   learned slice move not in the paper (a learned proposal added to
+ *                      the method): an MLP gives a Gaussian N(mu, sigma^2) for
  *                      slice tau from its neighbours; preconditioned Crank-
  *                      Nicolson move around it, accepted by the same exact
  *                      determinant ratio (definitions in oracle/learned.py)

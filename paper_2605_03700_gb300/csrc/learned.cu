@@ -1,5 +1,5 @@
-// learned.cu -- the learned slice proposal (not in the paper; the learned
-// pattern of the build target): a small MLP gives a Gaussian for one
+// learned.cu -- the learned slice proposal (not in the paper; an addition to
+// the method): a small MLP gives a Gaussian for one
 // imaginary-time slice of the Hubbard-Stratonovich field from its two
 // neighbours; moves around it (preconditioned Crank-Nicolson) are accepted by
 // the exact determinant ratio of the slice update, so the sampled
