@@ -3,8 +3,9 @@
 TEST INFRASTRUCTURE ONLY (like the rest of oracle/): the GPU path never
 imports this module.
 
-The proposal is not in the paper; it is added to the method: a small network q_theta(phi_tau | phi_{tau-1}, phi_{tau+1}) over one
-imaginary-time slice of the Hubbard-Stratonovich field, whose moves are
+The proposal is not in the paper; it is added to the method: a small
+network q_theta(phi_tau | phi_{tau-1}, phi_{tau+1}) over one imaginary-time
+slice of the Hubbard-Stratonovich field, whose moves are
 accepted by the exact Metropolis-Hastings test of the fermion weight
 (Methods, Eq. weight and the determinant ratio of the local update), so the
 sampled distribution is the paper's.
