@@ -120,6 +120,26 @@ class Clocks:
                 "samples": len(sm)}
 
 
+# ----------------------------------------------------------- replicas -----
+def replica_seeds(rank):
+    """Seeds of rank `rank`'s chains: disjoint across ranks, so the ranks are
+    independent replicas of the eight-chain workload."""
+    return np.arange(NCH) + NCH * rank
+
+
+def combine_over_ranks(dist, t_s, wall, ess, device):
+    """Whole-job figures: the slowest rank's timed seconds and end-to-end wall
+    clock (max over ranks) and the effective samples of all ranks (sum)."""
+    if dist is None:
+        return t_s, wall, ess
+    import torch
+    tt = torch.tensor([t_s, wall], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    es = torch.tensor([ess], device=device, dtype=torch.float64)
+    dist.all_reduce(es)
+    return float(tt[0]), float(tt[1]), float(es[0])
+
+
 # ------------------------------------------------------------- tau / ESS ---
 def tau_per_chain(series, tau_fn):
     """max over m^2 (col 0) and E (col 12) of the windowed tau_int"""
@@ -218,7 +238,7 @@ def run_ours(args):
 
     stream = torch.cuda.Stream()
     wall0 = time.perf_counter()
-    seeds = np.arange(NCH) + NCH * rank
+    seeds = replica_seeds(rank)
     ch = P.Chain(P.QMC_TORUS, NPHI, BETA, DTAU, 0.0, 0.0, 0, n_chains=NCH, couplings=COUPLINGS,
                  seeds=seeds, n_stab=NSTAB, eps0=EPS0, series_capacity=4096,
                  precision=args.precision)
@@ -270,13 +290,7 @@ def run_ours(args):
     acc_langevin = float(np.delete(series[:, :, 13], learned_steps, axis=1).mean())
     ess = sum(args.steps / (2.0 * t) for t in taus)
     t_s = ms / 1000.0
-    if dist:
-        tt = torch.tensor([t_s, wall_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_s, wall_e2e = float(tt[0]), float(tt[1])
-        ess_t = torch.tensor([ess], device="cuda", dtype=torch.float64)
-        dist.all_reduce(ess_t)
-        ess = float(ess_t[0])
+    t_s, wall_e2e, ess = combine_over_ranks(dist, t_s, wall_e2e, ess, "cuda")
     value = ess / t_s
     e2e = ess / wall_e2e
     # roofline of the GEMM class (event-timed over the timed region)
