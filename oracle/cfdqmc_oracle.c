@@ -1369,3 +1369,79 @@ void orc_ratio_at(const orc_t *o, int t, const double *phis, double *logR,
     free(Gd); free(G); free(Bp); free(Bpi); free(Dl); free(T); free(Mt);
     free(Mi); free(Gp); free(piv);
 }
+
+/* ------------------------------------------------- time-displaced G ------ */
+/* Time-displaced Green's functions of the current configuration from one
+ * time origin (slice 0), by plain propagation from G = G(0,0) (the
+ * equal-time G at the end of a sweep):
+ *   G(t,0)    = <c(t) c^dagger(0)>    = B(t,0) G,
+ *   Gbar(0,t) = <c^dagger(t) c(0)>^T  = (1 - G) B(t,0)^-1,
+ *   G(t,t)    = B(t,0) G B(t,0)^-1,
+ * with B(t,0) = B_t ... B_1 (Methods, Eq. green_function and the slice
+ * propagators).  No stabilisation: valid while B(t,0) is well conditioned
+ * (small beta), which is all the pins need.  Writes the three matrices at
+ * slice t (0 <= t <= L) interleaved. */
+static void green_tau(const orc_t *o, int t, zc *Gt0, zc *Gb0t, zc *Gtt)
+{
+    int N = o->N;
+    size_t nn = (size_t)N * N;
+    zc *T = zalloc(nn);
+    memcpy(Gt0, o->G, sizeof(zc) * nn);
+    for (size_t x = 0; x < nn; ++x) Gb0t[x] = -o->G[x];
+    for (int x = 0; x < N; ++x) Gb0t[x * N + x] += 1.0;
+    memcpy(Gtt, o->G, sizeof(zc) * nn);
+    for (int u = 1; u <= t; ++u) {
+        const zc *Bu = o->B + (size_t)(u - 1) * nn, *Biu = o->Binv + (size_t)(u - 1) * nn;
+        mat_mul(N, Bu, Gt0, T);
+        memcpy(Gt0, T, sizeof(zc) * nn);
+        mat_mul(N, Gb0t, Biu, T);
+        memcpy(Gb0t, T, sizeof(zc) * nn);
+        mat_mul(N, Bu, Gtt, T);
+        mat_mul(N, T, Biu, Gtt);
+    }
+    free(T);
+}
+
+void orc_green_tau(const orc_t *o, int t, double *Gt0, double *Gb0t, double *Gtt)
+{
+    size_t nn = (size_t)o->N * o->N;
+    zc *a = zalloc(nn), *b = zalloc(nn), *c = zalloc(nn);
+    green_tau(o, t, a, b, c);
+    to_interleaved(a, nn, Gt0);
+    to_interleaved(b, nn, Gb0t);
+    to_interleaved(c, nn, Gtt);
+    free(a); free(b); free(c);
+}
+
+/* time-displaced structure factors at q = 0 of the current configuration:
+ * out[k * 5 + i - 1] = S^i_0(tau_k) = <n^{Gamma^i}_0(tau_k) n^{Gamma^i}_0bar(0)>,
+ * tau_k = taus[k] slices, by Wick's theorem with the same one-spin-block
+ * conventions as the equal-time measurement:
+ *   i = 1, 2: 4 a_q(t) a_qbar(0) + 2 x(t),  i = 3, 4, 5: 2 x_z(t),
+ *   a_q(t) = Tr[(O (x) F_q)(1 - G(t,t))], x(t) = Tr[M_q G(t,0) M_qbar Gbar(0,t)];
+ * at t = 0 these are the equal-time S^i_0 (obs[1..5] of measure()). */
+void orc_measure_tau(const orc_t *o, int ntau, const int *taus, double *out)
+{
+    int N = o->N;
+    size_t nn = (size_t)N * N;
+    int q = o->mq0;
+    int p = o->partner[q];
+    zc *Gt0 = zalloc(nn), *Gb = zalloc(nn), *Gtt = zalloc(nn), *Gc = zalloc(nn),
+       *Gc0 = zalloc(nn);
+    for (size_t x = 0; x < nn; ++x) Gc0[x] = -o->G[x];
+    for (int x = 0; x < N; ++x) Gc0[x * N + x] += 1.0;
+    for (int k = 0; k < ntau; ++k) {
+        int t = taus[k];
+        green_tau(o, t, Gt0, Gb, Gtt);
+        for (size_t x = 0; x < nn; ++x) Gc[x] = -Gtt[x];
+        for (int x = 0; x < N; ++x) Gc[x * N + x] += 1.0;
+        for (int v = 1; v <= 2; ++v) {
+            zc a = wick_a(o, v, q, Gc), ap = wick_a(o, v, p, Gc0);
+            zc x = wick_x(o, v, q, Gt0, Gb);
+            out[k * 5 + v - 1] = creal(4.0 * a * ap + 2.0 * x);
+        }
+        zc xz = wick_x(o, 3, q, Gt0, Gb);
+        out[k * 5 + 2] = out[k * 5 + 3] = out[k * 5 + 4] = creal(2.0 * xz);
+    }
+    free(Gt0); free(Gb); free(Gtt); free(Gc); free(Gc0);
+}

@@ -140,6 +140,27 @@ class ED:
             return out
         return self.thermal(f)
 
+    def structure_factor_tau(self, gi: int, q: int, tau: float) -> float:
+        """S^i_q(tau) = <n^{Gamma^i}_q(tau) n^{Gamma^i}_qbar(0)>
+        = Tr[e^{-(beta - tau) H} n_q e^{-tau H} n_qbar] / Z, 0 <= tau <= beta."""
+        tv, ts = GAMMA[gi]
+        m = self.model
+        hq = one_body(m, q, PAULI[tv], PAULI[ts])
+        hp = one_body(m, int(m.partner[q]), PAULI[tv], PAULI[ts])
+        tot = 0.0
+        for key, (w, V, _) in self.blocks.items():
+            nu, nd = key
+            left = (V * np.exp(-(self.beta - tau) * (w - self.emin))) @ V.conj().T
+            for mid in [(nu, nd), (nu + 1, nd - 1), (nu - 1, nd + 1)]:
+                if mid not in self.blocks:
+                    continue
+                wm, Vm, _ = self.blocks[mid]
+                prop = (Vm * np.exp(-tau * (wm - self.emin))) @ Vm.conj().T
+                A = self.fock.op(hq, key, mid)
+                B = self.fock.op(hp, mid, key)
+                tot += np.trace(left @ A @ prop @ B).real
+        return tot / self.Z
+
     def observables(self) -> dict:
         m = self.model
         q0 = m.q0() if m.geom == M.TORUS else 0

@@ -51,6 +51,8 @@ def lib():
         L.orc_sweep.argtypes = [C.c_void_p, C.c_int, dp]
         L.orc_sweep_learned.argtypes = [C.c_void_p, C.c_int, dp, C.c_int, dp, C.c_double]
         L.orc_mlp_forward.argtypes = [C.c_int, C.c_int, dp, C.c_int, dp, dp]
+        L.orc_green_tau.argtypes = [C.c_void_p, C.c_int, dp, dp, dp]
+        L.orc_measure_tau.argtypes = [C.c_void_p, C.c_int, ip, dp]
         L.orc_measure.argtypes = [C.c_void_p, dp]
         L.orc_set_measure_q.argtypes = [C.c_void_p, C.c_int, ip, C.c_int]
         L.orc_set_trace.argtypes = [C.c_void_p, dp, C.c_long]
@@ -192,6 +194,21 @@ class Chain:
         obs = np.zeros((n, NOBS))
         lib().orc_sweep_learned(self.h, n, _dp(obs), H, _dp(theta), float(rho))
         return obs
+
+    def green_tau(self, t):
+        """(G(t,0), Gbar(0,t), G(t,t)) of the current configuration from the
+        time origin 0, t in slices (plain propagation: small beta)."""
+        out = [np.zeros((self.N, self.N), complex) for _ in range(3)]
+        lib().orc_green_tau(self.h, int(t), *[_dp(a.view(float)) for a in out])
+        return tuple(out)
+
+    def measure_tau(self, taus):
+        """S^i_{q=0}(tau) for i = 1..5 at slice offsets taus (time origin 0):
+        array (len(taus), 5)."""
+        t = np.ascontiguousarray(taus, dtype=np.int32)
+        out = np.zeros((len(t), 5))
+        lib().orc_measure_tau(self.h, len(t), _ip(t), _dp(out))
+        return out
 
     def measure(self):
         obs = np.zeros(NOBS)

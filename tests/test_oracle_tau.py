@@ -1,0 +1,97 @@
+"""Pins of the oracle's time-displaced Green's functions and structure factors
+(the groundwork of the SO(5) gap measurement; GPU kernels for them come
+later).
+
+Fixed by: the boundary values G(beta,0) = 1 - G and Gbar(0,beta) = G
+(antiperiodicity), the exact identities G(t,0) = [B(t,0)^-1 + B(beta,t)]^-1
+and Gbar(0,t) = [B(t,0) + B(beta,t)^-1]^-1 evaluated from the raw slice
+products, the equal-time limit, periodicity S(beta) = S(0), the free limit
+(no dynamics), and exact diagonalisation of the transformed Hamiltonian.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ed as E
+from oracle import model as M
+from oracle import oracle as O
+
+
+def _chain(beta=1.0, dtau=0.1, u=2.0, al=0.2, seed=3, g=None):
+    ch = O.Chain(M.TORUS, 2, beta, dtau, u, al, seed, n_stab=5, g=g)
+    ch.sweep(20)
+    return ch
+
+
+def _prod(ch, t1, t2):
+    """B(t2, t1) = B_t2 ... B_{t1+1} from the stored slice propagators"""
+    P = np.eye(ch.N, dtype=complex)
+    for t in range(t1 + 1, t2 + 1):
+        P = ch.B(t)[0] @ P
+    return P
+
+
+def test_boundary_values_and_identities():
+    ch = _chain()
+    G = ch.green()
+    L, I = ch.L, np.eye(ch.N)
+    Gt0, Gb, Gtt = ch.green_tau(0)
+    assert np.abs(Gt0 - G).max() < 1e-14 and np.abs(Gb - (I - G)).max() < 1e-14
+    Gt0, Gb, Gtt = ch.green_tau(L)
+    assert np.abs(Gt0 - (I - G)).max() < 1e-10       # G(beta, 0) = 1 - G
+    assert np.abs(Gb - G).max() < 1e-10              # Gbar(0, beta) = G
+    assert np.abs(Gtt - G).max() < 1e-10
+    for t in (1, 3, L // 2, L - 1):
+        Gt0, Gb, Gtt = ch.green_tau(t)
+        Bt0, Bbt = _prod(ch, 0, t), _prod(ch, t, L)
+        assert np.abs(Gt0 - np.linalg.inv(np.linalg.inv(Bt0) + Bbt)).max() < 1e-10
+        assert np.abs(Gb - np.linalg.inv(Bt0 + np.linalg.inv(Bbt))).max() < 1e-10
+        assert np.abs(Gtt - ch.green_bruteforce(t)).max() < 1e-10
+
+
+def test_equal_time_limit_and_periodicity():
+    ch = _chain()
+    S = ch.measure_tau([0, ch.L])
+    eq = ch.measure()[1:6]
+    assert np.abs(S[0] - eq).max() < 1e-12 * max(1.0, np.abs(eq).max())
+    assert np.abs(S[1] - S[0]).max() < 1e-10
+    # spin SO(3): the three spin components agree at every tau
+    S = ch.measure_tau([1, 4, 7])
+    assert np.all(S[:, 2] == S[:, 3]) and np.all(S[:, 3] == S[:, 4])
+
+
+def test_free_limit_has_no_dynamics():
+    ch = _chain(g=np.zeros(4))
+    S = ch.measure_tau(list(range(ch.L + 1)))
+    assert np.abs(S - S[0]).max() < 1e-14
+
+
+def _mean_err(x, nbin=50):
+    b = np.array_split(np.asarray(x), nbin)
+    m = np.array([v.mean() for v in b])
+    return m.mean(), m.std(ddof=1) / math.sqrt(nbin)
+
+
+def test_time_displaced_structure_factor_matches_exact_diagonalisation():
+    """torus N_phi = 2, u = 4, alpha = 0.3, beta = 2, dtau = 0.05: Monte Carlo
+    S^1_0(tau) and S^3_0(tau) at tau = 0.5 and 1 within 4 sigma of ED."""
+    m = M.Model(M.TORUS, 2)
+    beta, dtau = 2.0, 0.05
+    ed = E.ED(m, M.couplings(4.0, 0.3), beta)
+    ch = O.Chain(M.TORUS, 2, beta, dtau, 4.0, 0.3, seed=7, n_stab=5, n_adapt=150, model=m)
+    ch.sweep(150)
+    taus = [10, 20]
+    rec = []
+    for _ in range(2500):
+        ch.sweep(1)
+        rec.append(ch.measure_tau(taus))
+    rec = np.array(rec)
+    q0 = m.q0()
+    for k, t in enumerate(taus):
+        for gi, col in ((0, 0), (2, 2)):
+            ref = ed.structure_factor_tau(gi, q0, t * dtau)
+            mu, err = _mean_err(rec[:, k, col])
+            assert abs(mu - ref) < 4 * err, (t, gi, mu, ref, err)
+    # and S(tau) really decays away from tau = 0 in this model
+    assert ed.structure_factor_tau(0, q0, 1.0) < ed.structure_factor_tau(0, q0, 0.0)
