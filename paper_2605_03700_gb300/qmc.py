@@ -323,9 +323,10 @@ def _fp(a):
 class Net:
     """The learned slice proposal's network (qmc_net_*): nf = 4 N_q fields per
     slice, hidden width `width`, a device-resident ring of `capacity`
-    configurations for training."""
+    configurations for training, allocated on the first collect() as
+    capacity x L x nf FP32 values (N_phi = 36, L = 360: 1.9 MB each)."""
 
-    def __init__(self, nf, width=256, capacity=10000, seed=0):
+    def __init__(self, nf, width=256, capacity=1000, seed=0):
         h = C.c_void_p()
         _check(lib().qmc_net_create(C.byref(h), int(nf), int(width), int(capacity), int(seed)))
         self.h = h
