@@ -57,3 +57,36 @@ def test_tau_int_host_function(lib):
     assert abs(qmc.qmc_tau_int(x) - A.tau_int(x)) < 1e-9
     exact = (1 + 0.7) / (2 * (1 - 0.7))
     assert abs(qmc.qmc_tau_int(x) - exact) < 0.15 * exact
+
+
+def test_new_entry_points_reject_invalid_arguments_before_device_work(lib):
+    """The learned-proposal, graph, group and standalone ratio entry points
+    check their arguments before touching the device (runs without a GPU)."""
+    from paper_2605_03700_gb300 import qmc
+    L = qmc.lib()
+    h = C.c_void_p()
+    # network: null out, empty field count, oversized width, zero capacity
+    assert L.qmc_net_create(None, 10, 8, 4, 0) == -1
+    assert L.qmc_net_create(C.byref(h), 0, 8, 4, 0) == -1 and not h.value
+    assert L.qmc_net_create(C.byref(h), 10, 5000, 4, 0) == -1
+    assert L.qmc_net_create(C.byref(h), 10, 8, 0, 0) == -1
+    assert L.qmc_net_destroy(None) == 0
+    assert L.qmc_net_num_params(None) == -1 and L.qmc_net_dataset_size(None) == -1
+    assert L.qmc_net_train(None, 1, 1, 1e-3, 0.0, None) == -1
+    assert L.qmc_net_collect(None, None) == -1
+    # sweeps without a context
+    assert L.qmc_sweep_learned(None, None, 1, 0.0) == -1
+    assert L.qmc_sweep_graph(None, 1) == -1
+    # groups: null out, no members, a null member
+    arr = (C.c_void_p * 2)(None, None)
+    assert L.qmc_group_create(None, arr, 2) == -1
+    assert L.qmc_group_create(C.byref(h), arr, 0) == -1
+    assert L.qmc_group_create(C.byref(h), arr, 2) == -1
+    assert L.qmc_group_sweep(None, 1) == -1 and L.qmc_group_sync(None) == -1
+    assert L.qmc_group_destroy(None) == 0
+    # standalone ratio updates: sizes beyond what the kernels hold
+    assert L.qmc_ratio_update(113, 1, None, None, None, None, None) == -1
+    assert L.qmc_ratio_update_noalloc(72, 1, None, None, None, None, None) == -1
+    # sphere beyond 56 orbitals
+    o = qmc.qmc_default_opts()
+    assert L.qmc_create(C.byref(h), 1, 56, 1.0, 0.1, 1.0, 0.0, 0, C.byref(o)) == -1
