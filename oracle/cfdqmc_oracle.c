@@ -1445,3 +1445,115 @@ void orc_measure_tau(const orc_t *o, int ntau, const int *taus, double *out)
     }
     free(Gt0); free(Gb); free(Gtt); free(Gc); free(Gc0);
 }
+
+/* UDV of B(t,0) = Q D W (right) and of B(b,t)^H = Q D W (left) for the
+ * stored propagators, re-decomposed every n_stab slices as in the sweep */
+static void udv_right(const orc_t *o, int t, zc *Q, double *D, zc *W)
+{
+    int N = o->N;
+    size_t nn = (size_t)N * N;
+    zc *X = zalloc(nn), *T = zalloc(nn), *Qn = zalloc(nn), *Vn = zalloc(nn);
+    mat_eye(N, Q);
+    mat_eye(N, W);
+    for (int x = 0; x < N; ++x) D[x] = 1.0;
+    int u = 0;
+    while (u < t) {
+        int hi = u + o->nstab < t ? u + o->nstab : t;
+        for (int r = 0; r < N; ++r)
+            for (int c = 0; c < N; ++c) X[r * N + c] = Q[r * N + c] * D[c];
+        for (int s = u + 1; s <= hi; ++s) {
+            mat_mul(N, o->B + (size_t)(s - 1) * nn, X, T);
+            memcpy(X, T, sizeof(zc) * nn);
+        }
+        udv(N, X, Qn, D, Vn);
+        mat_mul(N, Vn, W, T);
+        memcpy(W, T, sizeof(zc) * nn);
+        memcpy(Q, Qn, sizeof(zc) * nn);
+        u = hi;
+    }
+    free(X); free(T); free(Qn); free(Vn);
+}
+
+static void udv_left(const orc_t *o, int t, zc *Q, double *D, zc *W)
+{
+    int N = o->N;
+    size_t nn = (size_t)N * N;
+    zc *X = zalloc(nn), *T = zalloc(nn), *Qn = zalloc(nn), *Vn = zalloc(nn), *Bh = zalloc(nn);
+    mat_eye(N, Q);
+    mat_eye(N, W);
+    for (int x = 0; x < N; ++x) D[x] = 1.0;
+    int u = o->L;
+    while (u > t) {
+        int lo = u - o->nstab > t ? u - o->nstab : t;
+        for (int r = 0; r < N; ++r)
+            for (int c = 0; c < N; ++c) X[r * N + c] = Q[r * N + c] * D[c];
+        for (int s = u; s > lo; --s) {
+            mat_adj(N, o->B + (size_t)(s - 1) * nn, Bh);
+            mat_mul(N, Bh, X, T);
+            memcpy(X, T, sizeof(zc) * nn);
+        }
+        udv(N, X, Qn, D, Vn);
+        mat_mul(N, Vn, W, T);
+        memcpy(W, T, sizeof(zc) * nn);
+        memcpy(Q, Qn, sizeof(zc) * nn);
+        u = lo;
+    }
+    free(X); free(T); free(Qn); free(Vn); free(Bh);
+}
+
+/* the same three Green's functions as green_tau, stable at any beta: with
+ * B(t,0) = QR DR WR, B(b,t)^H = QL DL WL and D = Db Ds (Db = max(D,1),
+ * Ds = min(D,1)),
+ *   J        = DbR^-1 QR^H QL DbL^-1 + DsR WR WL^H DsL   (well conditioned),
+ *   G(t,t)   = QL DbL^-1 J^-1 DbR^-1 QR^H,
+ *   G(t,0)   = [B(t,0)^-1 + B(b,t)]^-1   = QL DbL^-1 J^-1 DsR WR,
+ *   Gbar(0,t)= [B(t,0) + B(b,t)^-1]^-1   = WL^H DsL J^-1 DbR^-1 QR^H. */
+void orc_green_tau_stable(const orc_t *o, int t, double *Gt0_out, double *Gb0t_out,
+                          double *Gtt_out)
+{
+    int N = o->N;
+    size_t nn = (size_t)N * N;
+    zc *QR = zalloc(nn), *WR = zalloc(nn), *QL = zalloc(nn), *WL = zalloc(nn);
+    double *DR = (double *)malloc(sizeof(double) * N), *DL = (double *)malloc(sizeof(double) * N);
+    zc *T1 = zalloc(nn), *T2 = zalloc(nn), *J = zalloc(nn), *Ji = zalloc(nn), *S = zalloc(nn),
+       *R = zalloc(nn);
+    int *piv = (int *)malloc(sizeof(int) * N);
+    udv_right(o, t, QR, DR, WR);
+    udv_left(o, t, QL, DL, WL);
+#define DB(d) ((d) > 1 ? (d) : 1.0)
+#define DS(d) ((d) > 1 ? 1.0 : (d))
+    mat_adj(N, QR, T1);
+    mat_mul(N, T1, QL, T2);   /* QR^H QL */
+    mat_adj(N, WL, T1);
+    mat_mul(N, WR, T1, J);    /* WR WL^H */
+    for (int r = 0; r < N; ++r)
+        for (int c = 0; c < N; ++c)
+            J[r * N + c] = T2[r * N + c] / (DB(DR[r]) * DB(DL[c])) + DS(DR[r]) * J[r * N + c] * DS(DL[c]);
+    lu(N, J, piv);
+    lu_inv(N, J, piv, Ji);
+    /* G(t,t) = (QL DbL^-1) Ji (DbR^-1 QR^H) */
+    for (int r = 0; r < N; ++r)
+        for (int c = 0; c < N; ++c) S[r * N + c] = QL[r * N + c] / DB(DL[c]);
+    mat_adj(N, QR, T1);
+    for (int r = 0; r < N; ++r)
+        for (int c = 0; c < N; ++c) R[r * N + c] = T1[r * N + c] / DB(DR[r]);
+    mat_mul(N, S, Ji, T2);
+    mat_mul(N, T2, R, T1);
+    to_interleaved(T1, nn, Gtt_out);
+    /* G(t,0) = (QL DbL^-1) Ji (DsR WR) */
+    for (int r = 0; r < N; ++r)
+        for (int c = 0; c < N; ++c) J[r * N + c] = DS(DR[r]) * WR[r * N + c];
+    mat_mul(N, T2, J, T1);
+    to_interleaved(T1, nn, Gt0_out);
+    /* Gbar(0,t) = (WL^H DsL) Ji (DbR^-1 QR^H) */
+    mat_adj(N, WL, T1);
+    for (int r = 0; r < N; ++r)
+        for (int c = 0; c < N; ++c) S[r * N + c] = T1[r * N + c] * DS(DL[c]);
+    mat_mul(N, S, Ji, T2);
+    mat_mul(N, T2, R, T1);
+    to_interleaved(T1, nn, Gb0t_out);
+#undef DB
+#undef DS
+    free(QR); free(WR); free(QL); free(WL); free(DR); free(DL); free(T1); free(T2); free(J);
+    free(Ji); free(S); free(R); free(piv);
+}

@@ -52,6 +52,7 @@ def lib():
         L.orc_sweep_learned.argtypes = [C.c_void_p, C.c_int, dp, C.c_int, dp, C.c_double]
         L.orc_mlp_forward.argtypes = [C.c_int, C.c_int, dp, C.c_int, dp, dp]
         L.orc_green_tau.argtypes = [C.c_void_p, C.c_int, dp, dp, dp]
+        L.orc_green_tau_stable.argtypes = [C.c_void_p, C.c_int, dp, dp, dp]
         L.orc_measure_tau.argtypes = [C.c_void_p, C.c_int, ip, dp]
         L.orc_measure.argtypes = [C.c_void_p, dp]
         L.orc_set_measure_q.argtypes = [C.c_void_p, C.c_int, ip, C.c_int]
@@ -200,6 +201,13 @@ class Chain:
         time origin 0, t in slices (plain propagation: small beta)."""
         out = [np.zeros((self.N, self.N), complex) for _ in range(3)]
         lib().orc_green_tau(self.h, int(t), *[_dp(a.view(float)) for a in out])
+        return tuple(out)
+
+    def green_tau_stable(self, t):
+        """The same three matrices as green_tau, from UDV decompositions of
+        B(t,0) and B(beta,t): stable at any beta."""
+        out = [np.zeros((self.N, self.N), complex) for _ in range(3)]
+        lib().orc_green_tau_stable(self.h, int(t), *[_dp(a.view(float)) for a in out])
         return tuple(out)
 
     def measure_tau(self, taus):

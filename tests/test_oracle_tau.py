@@ -95,3 +95,32 @@ def test_time_displaced_structure_factor_matches_exact_diagonalisation():
             assert abs(mu - ref) < 4 * err, (t, gi, mu, ref, err)
     # and S(tau) really decays away from tau = 0 in this model
     assert ed.structure_factor_tau(0, q0, 1.0) < ed.structure_factor_tau(0, q0, 0.0)
+
+
+def test_stable_form_equals_plain_propagation_at_small_beta():
+    ch = _chain(beta=1.0)
+    for t in (0, 1, 4, 7, ch.L):
+        for a, b in zip(ch.green_tau(t), ch.green_tau_stable(t)):
+            assert np.abs(a - b).max() < 1e-10, t
+
+
+def test_stable_form_at_large_beta():
+    """beta = 10 (L = 100), u = 2: the boundary values, the sweep's own
+    stabilised G at t = 0, and the one-slice relations G(t+1,0) = B G(t,0),
+    Gbar(0,t+1) = Gbar(0,t) B^-1, G(t+1,t+1) = B G(t,t) B^-1 (each product a
+    single well-conditioned slice) hold to rounding."""
+    ch = O.Chain(M.TORUS, 2, 10.0, 0.1, 2.0, 0.2, 5, n_stab=5)
+    ch.sweep(10)
+    G, I, L = ch.green(), np.eye(ch.N), ch.L
+    Gt0, Gb, Gtt = ch.green_tau_stable(0)
+    assert np.abs(Gtt - G).max() < 1e-10 and np.abs(Gt0 - G).max() < 1e-10
+    Gt0, Gb, Gtt = ch.green_tau_stable(L)
+    assert np.abs(Gt0 - (I - G)).max() < 1e-9 and np.abs(Gb - G).max() < 1e-9
+    prev = ch.green_tau_stable(37)
+    cur = ch.green_tau_stable(38)
+    B, Bi = ch.B(38)
+    assert np.abs(cur[0] - B @ prev[0]).max() < 1e-9
+    assert np.abs(cur[1] - prev[1] @ Bi).max() < 1e-9
+    assert np.abs(cur[2] - B @ prev[2] @ Bi).max() < 1e-9
+    # all three are O(1): Green's functions, however large B(t,0) is
+    assert max(np.abs(m).max() for m in cur) < 10
