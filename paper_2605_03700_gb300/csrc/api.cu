@@ -36,7 +36,7 @@
         }                                                                          \
     } while (0)
 
-long long g_qmc_launches = 0;
+std::atomic<long long> g_qmc_launches{0};  // host-side count, any thread
 
 struct qmc_ctx {
     int geom = 0, nphi = 0, n = 0, N = 0, nq = 0, nf = 0, L = 0, nb = 0;
@@ -1000,8 +1000,9 @@ static int capture_sweeps(qmc_ctx *const *m, int nm, cudaStream_t origin, cudaGr
     }
     if (graph) cudaGraphDestroy(graph);
     for (auto &e : ev) cudaEventDestroy(e);
-    *kernels = g_qmc_launches - k0;
-    g_qmc_launches = k0;
+    // the captured kernels run at each launch of the graph, which counts them
+    *kernels = g_qmc_launches.load() - k0;
+    g_qmc_launches -= *kernels;
     gemm_prof_enable(prof);
     cudaGetLastError();
     return r;
@@ -1341,7 +1342,7 @@ const char *qmc_strerror(int code)
 
 const char *qmc_last_error(const qmc_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
 
-long long qmc_launch_count(void) { return g_qmc_launches; }
+long long qmc_launch_count(void) { return g_qmc_launches.load(); }
 
 int qmc_gemm_tile(int n, int precision)
 {

@@ -7,6 +7,7 @@
 #include "linalg.cuh"
 
 #include <cstdlib>
+#include <mutex>
 #include <vector>
 
 // ------------------------------------------------------------------ GEMM --
@@ -163,9 +164,11 @@ struct TileKey {
     int n, rc;
 };
 static std::vector<std::pair<TileKey, int>> g_tiles;
+static std::mutex g_tiles_mu;  // contexts may be created from several host threads
 
 static int tile_for(int n, int rc)
 {
+    std::lock_guard<std::mutex> lock(g_tiles_mu);
     for (auto &e : g_tiles)
         if (e.first.n == n && e.first.rc == rc) return e.second;
     return 16;
@@ -173,6 +176,7 @@ static int tile_for(int n, int rc)
 
 void gemm_set_tile(int n, int rc, int tile)
 {
+    std::lock_guard<std::mutex> lock(g_tiles_mu);
     for (auto &e : g_tiles)
         if (e.first.n == n && e.first.rc == rc) {
             e.second = tile;

@@ -1,5 +1,6 @@
 // qmc_internal.cuh -- shared device helpers and the context layout of libqmc.
 #pragma once
+#include <atomic>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -153,7 +154,7 @@ __device__ __forceinline__ double rng_normal(uint32_t f, uint32_t slice, uint32_
 
 // ------------------------------------------------------- small utilities --
 // number of kernels this library has launched (all contexts, host-side count)
-extern long long g_qmc_launches;
+extern std::atomic<long long> g_qmc_launches;
 #define QMC_COUNT(k) (g_qmc_launches += (k))
 
 #define QMC_DEVFN __device__ __forceinline__
