@@ -1,0 +1,176 @@
+"""Finite-size-scaling analysis of measured observables (host post-processing
+of the records the sweep produces; not part of the sweep).
+
+Implements the paper's analysis along the SO(5) line (Results, "Finite-size
+scaling"):
+
+* scaling variable x = (u/u_c - 1) * sqrt(N_phi)^(3 - Delta_s) (Eq.
+  finite-size-scaling-R); the correlation ratio obeys R = F(x) and the order
+  parameter m^2 N_phi^Delta_v = F(x) (Eq. finite-size-scaling-m), with F a
+  universal function;
+* R^2-optimised grid scan: F approximated by a polynomial of third order
+  around u_c, fitted by least squares for every (u_c, Delta_s) on a grid; the
+  collapse quality is the coefficient of determination
+  R^2 = 1 - sum (y - F(x))^2 / sum (y - mean y)^2, and the best grid point is
+  the estimate;
+* Delta_v from the slope of ln m^2 against ln N_phi, with the smallest sizes
+  progressively excluded from the fit;
+* crossing points of the correlation-ratio curves of consecutive sizes.
+
+Inputs are per-(u, N_phi) means (e.g. from Chain.series() with errors from
+mean_err); everything is numpy on the host.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def mean_err(x, tau=0.5):
+    """Mean of a Markov-chain series and its error sqrt(2 tau var / n), tau
+    the integrated autocorrelation time (0.5 for independent samples)."""
+    x = np.asarray(x, dtype=float)
+    return float(x.mean()), float(np.sqrt(2.0 * tau * x.var(ddof=1) / len(x)))
+
+
+def scaling_x(u, nphi, uc, ds):
+    """x = (u/u_c - 1) sqrt(N_phi)^(3 - Delta_s)"""
+    u = np.asarray(u, dtype=float)
+    nphi = np.asarray(nphi, dtype=float)
+    return (u / uc - 1.0) * np.sqrt(nphi) ** (3.0 - ds)
+
+
+def collapse_r2(u, nphi, y, uc, ds, order=3):
+    """Coefficient of determination of the polynomial collapse of y(u, N_phi)
+    onto F(x) at the trial (u_c, Delta_s); returns (R^2, polynomial coeffs)."""
+    y = np.asarray(y, dtype=float)
+    x = scaling_x(u, nphi, uc, ds)
+    coef = np.polyfit(x, y, order)
+    res = y - np.polyval(coef, x)
+    tot = y - y.mean()
+    return 1.0 - float(res @ res) / float(tot @ tot), coef
+
+
+def grid_scan(u, nphi, y, uc_grid, ds_grid, order=3):
+    """R^2 map over the (u_c, Delta_s) grid and its maximum:
+    returns (r2[len(uc_grid), len(ds_grid)], best_uc, best_ds, best_r2)."""
+    r2 = np.full((len(uc_grid), len(ds_grid)), -np.inf)
+    for i, uc in enumerate(uc_grid):
+        for j, ds in enumerate(ds_grid):
+            r2[i, j] = collapse_r2(u, nphi, y, uc, ds, order)[0]
+    i, j = np.unravel_index(np.argmax(r2), r2.shape)
+    return r2, float(uc_grid[i]), float(ds_grid[j]), float(r2[i, j])
+
+
+def order_parameter_collapse_y(m2, nphi, dv):
+    """y = m^2 N_phi^Delta_v, the left-hand side of the order-parameter
+    ansatz, for use with collapse_r2 / grid_scan at fixed Delta_v."""
+    return np.asarray(m2, dtype=float) * np.asarray(nphi, dtype=float) ** dv
+
+
+def power_law_dimension(nphi, m2, err=None, nmin_list=None):
+    """Delta_v from weighted linear fits of ln m^2 against ln N_phi over the
+    sizes N_phi >= N_min, for every N_min in nmin_list (default: every size
+    that leaves at least three points).  Returns a list of
+    (N_min, Delta_v, standard error)."""
+    nphi = np.asarray(nphi, dtype=float)
+    m2 = np.asarray(m2, dtype=float)
+    sig = np.ones_like(m2) if err is None else np.asarray(err, dtype=float) / m2
+    sizes = np.unique(nphi)
+    if nmin_list is None:
+        nmin_list = sizes[:-2]
+    out = []
+    for nmin in nmin_list:
+        k = nphi >= nmin
+        if k.sum() < 3:
+            continue
+        X = np.vstack([np.ones(k.sum()), np.log(nphi[k])]).T
+        w = 1.0 / sig[k] ** 2
+        A = X.T @ (X * w[:, None])
+        b = X.T @ (w * np.log(m2[k]))
+        beta = np.linalg.solve(A, b)
+        cov = np.linalg.inv(A)
+        if err is None:   # unit weights: scale by the residual variance
+            r = np.log(m2[k]) - X @ beta
+            cov = cov * (r @ r) / max(k.sum() - 2, 1)
+        out.append((float(nmin), float(-beta[1]), float(np.sqrt(cov[1, 1]))))
+    return out
+
+
+def crossings(u, nphi, R):
+    """u where the correlation-ratio curves of consecutive sizes cross
+    (linear interpolation of their difference on the common u grid): a list
+    of (N_phi_1, N_phi_2, u_cross); pairs that do not cross are skipped."""
+    u = np.asarray(u, dtype=float)
+    nphi = np.asarray(nphi, dtype=float)
+    R = np.asarray(R, dtype=float)
+    sizes = np.unique(nphi)
+    out = []
+    for a, b in zip(sizes[:-1], sizes[1:]):
+        ia, ib = nphi == a, nphi == b
+        oa, ob = np.argsort(u[ia]), np.argsort(u[ib])
+        ua, ra = u[ia][oa], R[ia][oa]
+        ub, rb = u[ib][ob], R[ib][ob]
+        grid = np.intersect1d(ua, ub)
+        if len(grid) < 2:
+            continue
+        d = np.interp(grid, ub, rb) - np.interp(grid, ua, ra)
+        s = np.nonzero((d[:-1] == 0) | (np.sign(d[:-1]) * np.sign(d[1:]) < 0))[0]
+        if len(s) == 0:
+            continue
+        i = s[0]
+        uc = grid[i] if d[i] == 0 else grid[i] - d[i] * (grid[i + 1] - grid[i]) / (d[i + 1] - d[i])
+        out.append((float(a), float(b), float(uc)))
+    return out
+
+
+def r2_region(r2, uc_grid, ds_grid, threshold=0.99):
+    """Ranges of u_c and Delta_s over the grid points whose collapse has
+    R^2 > threshold: ((uc_min, uc_max), (ds_min, ds_max)), or None when no
+    point passes."""
+    i, j = np.nonzero(np.asarray(r2) > threshold)
+    if len(i) == 0:
+        return None
+    uc, ds = np.asarray(uc_grid)[i], np.asarray(ds_grid)[j]
+    return (float(uc.min()), float(uc.max())), (float(ds.min()), float(ds.max()))
+
+
+def refine_scan(u, nphi, y, uc_grid, ds_grid, levels=2, shrink=5, order=3):
+    """grid_scan, then `levels` further scans on grids of the same size
+    centred on the best point and `shrink` times narrower; returns
+    (best_uc, best_ds, best_r2)."""
+    uc_grid, ds_grid = np.asarray(uc_grid, float), np.asarray(ds_grid, float)
+    _, uc, ds, r = grid_scan(u, nphi, y, uc_grid, ds_grid, order)
+    for _ in range(levels):
+        huc = (uc_grid[-1] - uc_grid[0]) / (2 * shrink)
+        hds = (ds_grid[-1] - ds_grid[0]) / (2 * shrink)
+        uc_grid = np.linspace(uc - huc, uc + huc, len(uc_grid))
+        ds_grid = np.linspace(ds - hds, ds + hds, len(ds_grid))
+        _, uc, ds, r = grid_scan(u, nphi, y, uc_grid, ds_grid, order)
+    return uc, ds, r
+
+
+def bootstrap_scan(u, nphi, y, err, uc_grid, ds_grid, n_boot=100, seed=0, order=3):
+    """Statistical error of the grid-scan estimate: rescan n_boot synthetic
+    data sets y + err * N(0, 1) (Gaussian resampling of the means within
+    their errors).  Returns (mean u_c, std u_c, mean Delta_s, std Delta_s)."""
+    rng = np.random.default_rng(seed)
+    y, err = np.asarray(y, float), np.asarray(err, float)
+    best = []
+    for _ in range(n_boot):
+        yb = y + err * rng.standard_normal(len(y))
+        best.append(grid_scan(u, nphi, yb, uc_grid, ds_grid, order)[1:3])
+    best = np.array(best)
+    return (float(best[:, 0].mean()), float(best[:, 0].std(ddof=1)),
+            float(best[:, 1].mean()), float(best[:, 1].std(ddof=1)))
+
+
+def select(u, nphi, *cols, nphi_min=None, u_range=None):
+    """Restrict the data to the critical window used in the fits
+    (N_phi >= nphi_min, u_range[0] <= u <= u_range[1])."""
+    u, nphi = np.asarray(u, float), np.asarray(nphi, float)
+    k = np.ones(len(u), dtype=bool)
+    if nphi_min is not None:
+        k &= nphi >= nphi_min
+    if u_range is not None:
+        k &= (u >= u_range[0]) & (u <= u_range[1])
+    return (u[k], nphi[k]) + tuple(np.asarray(c, float)[k] for c in cols)
