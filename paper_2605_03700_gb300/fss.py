@@ -15,7 +15,11 @@ scaling"):
   the estimate;
 * Delta_v from the slope of ln m^2 against ln N_phi, with the smallest sizes
   progressively excluded from the fit;
-* crossing points of the correlation-ratio curves of consecutive sizes.
+* crossing points of the curves of consecutive sizes, for R and for
+  m^2 N_phi^Delta_v (Supplementary Note 3, data scaling analysis);
+* the same scans in the anisotropy alpha for the VBS and AFM ratios away
+  from the SO(5) line (Results, "Phase boundaries away from the
+  SO(5)-symmetric line"; Supplementary Note 1).
 
 Inputs are per-(u, N_phi) means (e.g. from Chain.series() with errors from
 mean_err); everything is numpy on the host.
@@ -32,31 +36,57 @@ def mean_err(x, tau=0.5):
     return float(x.mean()), float(np.sqrt(2.0 * tau * x.var(ddof=1) / len(x)))
 
 
-def scaling_x(u, nphi, uc, ds):
-    """x = (u/u_c - 1) sqrt(N_phi)^(3 - Delta_s)"""
+# SO(5) components of an observable record: 1, 2 couple to U_K (valley,
+# Kekule VBS order), 3, 4, 5 to U_N (spin, Neel AFM order) (Model, Eq.
+# newmodel with U_1 = U_2 = U_K, U_3 = U_4 = U_5 = U_N).
+CHANNELS = {"SO5": (0, 1, 2, 3, 4), "VBS": (0, 1), "AFM": (2, 3, 4)}
+
+
+def order_parameters(records, nphi, channel="SO5"):
+    """m^2 and the correlation ratio R of one order parameter from observable
+    records (last axis the 20-double record: 1..5 S^i_{q=0}, 6..10 S^i at the
+    smallest non-zero momenta):
+    m^2_X = sum_{i in X} S^i_0 / (|X| N_phi^2) and R_X = 1 - S_X(dq)/S_X(0),
+    S_X = sum_{i in X} S^i (Results: m^2_SO(5), the correlation ratio; the
+    VBS and AFM ratios of the anisotropy scans use the subsets).  Pass the
+    mean record to get R as the ratio of expectation values."""
+    rec = np.asarray(records, dtype=float)
+    comp = np.asarray(CHANNELS[channel])
+    s0 = rec[..., 1 + comp].sum(-1)
+    sd = rec[..., 6 + comp].sum(-1)
+    return s0 / (len(comp) * float(nphi) ** 2), 1.0 - sd / s0
+
+
+def scaling_x(u, nphi, uc, ds, relative=True):
+    """x = (u/u_c - 1) sqrt(N_phi)^(3 - Delta_s) (relative, the SO(5)-line
+    form), or (u - u_c) sqrt(N_phi)^(3 - Delta_s) for a tuning parameter whose
+    critical value may be zero or negative (the anisotropy alpha); the two
+    differ by the factor u_c, which a polynomial F absorbs, so at u_c != 0
+    both give the same collapse."""
     u = np.asarray(u, dtype=float)
     nphi = np.asarray(nphi, dtype=float)
-    return (u / uc - 1.0) * np.sqrt(nphi) ** (3.0 - ds)
+    d = u / uc - 1.0 if relative else u - uc
+    return d * np.sqrt(nphi) ** (3.0 - ds)
 
 
-def collapse_r2(u, nphi, y, uc, ds, order=3):
+def collapse_r2(u, nphi, y, uc, ds, order=3, relative=True):
     """Coefficient of determination of the polynomial collapse of y(u, N_phi)
     onto F(x) at the trial (u_c, Delta_s); returns (R^2, polynomial coeffs)."""
     y = np.asarray(y, dtype=float)
-    x = scaling_x(u, nphi, uc, ds)
+    x = scaling_x(u, nphi, uc, ds, relative)
     coef = np.polyfit(x, y, order)
     res = y - np.polyval(coef, x)
     tot = y - y.mean()
     return 1.0 - float(res @ res) / float(tot @ tot), coef
 
 
-def grid_scan(u, nphi, y, uc_grid, ds_grid, order=3):
+def grid_scan(u, nphi, y, uc_grid, ds_grid, order=3, relative=True):
     """R^2 map over the (u_c, Delta_s) grid and its maximum:
     returns (r2[len(uc_grid), len(ds_grid)], best_uc, best_ds, best_r2)."""
     r2 = np.full((len(uc_grid), len(ds_grid)), -np.inf)
     for i, uc in enumerate(uc_grid):
         for j, ds in enumerate(ds_grid):
-            r2[i, j] = collapse_r2(u, nphi, y, uc, ds, order)[0]
+            r2[i, j] = collapse_r2(u, nphi, y, uc, ds, order, relative)[0]
     i, j = np.unravel_index(np.argmax(r2), r2.shape)
     return r2, float(uc_grid[i]), float(ds_grid[j]), float(r2[i, j])
 
@@ -97,9 +127,10 @@ def power_law_dimension(nphi, m2, err=None, nmin_list=None):
 
 
 def crossings(u, nphi, R):
-    """u where the correlation-ratio curves of consecutive sizes cross
-    (linear interpolation of their difference on the common u grid): a list
-    of (N_phi_1, N_phi_2, u_cross); pairs that do not cross are skipped."""
+    """u where the curves R(u) of consecutive sizes cross (R a correlation
+    ratio, or m^2 N_phi^Delta_v; linear interpolation of their difference on
+    the common u grid): a list of (N_phi_1, N_phi_2, u_cross); pairs that do
+    not cross are skipped."""
     u = np.asarray(u, dtype=float)
     nphi = np.asarray(nphi, dtype=float)
     R = np.asarray(R, dtype=float)
@@ -134,22 +165,23 @@ def r2_region(r2, uc_grid, ds_grid, threshold=0.99):
     return (float(uc.min()), float(uc.max())), (float(ds.min()), float(ds.max()))
 
 
-def refine_scan(u, nphi, y, uc_grid, ds_grid, levels=2, shrink=5, order=3):
+def refine_scan(u, nphi, y, uc_grid, ds_grid, levels=2, shrink=5, order=3, relative=True):
     """grid_scan, then `levels` further scans on grids of the same size
     centred on the best point and `shrink` times narrower; returns
     (best_uc, best_ds, best_r2)."""
     uc_grid, ds_grid = np.asarray(uc_grid, float), np.asarray(ds_grid, float)
-    _, uc, ds, r = grid_scan(u, nphi, y, uc_grid, ds_grid, order)
+    _, uc, ds, r = grid_scan(u, nphi, y, uc_grid, ds_grid, order, relative)
     for _ in range(levels):
         huc = (uc_grid[-1] - uc_grid[0]) / (2 * shrink)
         hds = (ds_grid[-1] - ds_grid[0]) / (2 * shrink)
         uc_grid = np.linspace(uc - huc, uc + huc, len(uc_grid))
         ds_grid = np.linspace(ds - hds, ds + hds, len(ds_grid))
-        _, uc, ds, r = grid_scan(u, nphi, y, uc_grid, ds_grid, order)
+        _, uc, ds, r = grid_scan(u, nphi, y, uc_grid, ds_grid, order, relative)
     return uc, ds, r
 
 
-def bootstrap_scan(u, nphi, y, err, uc_grid, ds_grid, n_boot=100, seed=0, order=3):
+def bootstrap_scan(u, nphi, y, err, uc_grid, ds_grid, n_boot=100, seed=0, order=3,
+                   relative=True):
     """Statistical error of the grid-scan estimate: rescan n_boot synthetic
     data sets y + err * N(0, 1) (Gaussian resampling of the means within
     their errors).  Returns (mean u_c, std u_c, mean Delta_s, std Delta_s)."""
@@ -158,7 +190,7 @@ def bootstrap_scan(u, nphi, y, err, uc_grid, ds_grid, n_boot=100, seed=0, order=
     best = []
     for _ in range(n_boot):
         yb = y + err * rng.standard_normal(len(y))
-        best.append(grid_scan(u, nphi, yb, uc_grid, ds_grid, order)[1:3])
+        best.append(grid_scan(u, nphi, yb, uc_grid, ds_grid, order, relative)[1:3])
     best = np.array(best)
     return (float(best[:, 0].mean()), float(best[:, 0].std(ddof=1)),
             float(best[:, 1].mean()), float(best[:, 1].std(ddof=1)))

@@ -146,3 +146,85 @@ def test_mean_err():
     m, e = fss.mean_err(x)
     assert abs(e - 0.01) < 0.001 and abs(m) < 4 * e
     assert abs(fss.mean_err(x, tau=2.0)[1] - 2 * e) < 1e-12
+
+
+def test_absolute_form_for_an_anisotropy_scan():
+    """Away from the SO(5) line the tuning parameter is alpha with alpha_c < 0:
+    the (alpha - alpha_c) form recovers it, and at a non-zero critical value
+    it gives exactly the relative form's R^2 (the factor is absorbed by F)."""
+    al = np.repeat(np.linspace(-0.5, -0.1, 9), len(SIZES))
+    n = np.tile(np.asarray(SIZES, float), 9)
+    ac, ds = -0.29, 1.43
+    y = _cubic((al - ac) * n ** ((3 - ds) / 2) * 3.0)
+    m, a, d, best = fss.grid_scan(al, n, y, np.round(np.arange(-0.40, -0.20, 0.01), 6),
+                                  np.round(np.arange(1.2, 1.7, 0.01), 6), relative=False)
+    assert abs(a - ac) < 1e-9 and abs(d - ds) < 1e-9 and abs(best - 1) < 1e-12
+    for trial in ((-0.25, 1.5), (-0.33, 1.3)):
+        ra = fss.collapse_r2(al, n, y, *trial, relative=False)[0]
+        rr = fss.collapse_r2(al, n, y, *trial, relative=True)[0]
+        assert abs(ra - rr) < 1e-12
+
+
+def _records(s0, sd):
+    rec = np.zeros(s0.shape[:-1] + (20,))
+    rec[..., 1:6], rec[..., 6:11] = s0, sd
+    return rec
+
+
+def test_order_parameters_from_records():
+    rng = np.random.default_rng(7)
+    s0 = rng.uniform(1, 3, (4, 5))
+    sd = rng.uniform(0, 1, (4, 5))
+    rec = _records(s0, sd)
+    for ch, comp in (("SO5", [0, 1, 2, 3, 4]), ("VBS", [0, 1]), ("AFM", [2, 3, 4])):
+        m2, R = fss.order_parameters(rec, 6, ch)
+        for r in range(4):
+            a = sum(s0[r, i] for i in comp)
+            b = sum(sd[r, i] for i in comp)
+            assert abs(m2[r] - a / (len(comp) * 36)) < 1e-15
+            assert abs(R[r] - (1 - b / a)) < 1e-15
+    # the SO(5) channel is the weighted mean of the VBS and AFM ones
+    m5 = fss.order_parameters(rec, 6)[0]
+    mv, ma = fss.order_parameters(rec, 6, "VBS")[0], fss.order_parameters(rec, 6, "AFM")[0]
+    assert np.allclose(m5, (2 * mv + 3 * ma) / 5, rtol=1e-14)
+    with pytest.raises(KeyError):
+        fss.order_parameters(rec, 6, "XY")
+
+
+def test_channels_against_the_oracle_chain_and_exact_diagonalisation():
+    """Torus N_phi = 2, u = 4, alpha = 0.3, beta = 2: the SO(5) channel
+    reproduces the sweep's own m^2 and R columns, and the VBS and AFM m^2 and
+    R (ratio of means) agree with exact diagonalisation within 4 sigma.
+    Sphere N_phi = 2, u = 1, alpha = -0.8 (U_K > U_N): VBS order exceeds AFM
+    order in both m^2 and R, as exact diagonalisation says (S^1_0 = 2.58 vs
+    S^3_0 = 2.25); a swapped channel assignment fails here.  (At N_phi = 2 the
+    torus channels differ by < 1%, too little to tell them apart.)"""
+    from oracle import ed as E
+    from oracle import model as M
+    from oracle import oracle as O
+    m = M.Model(M.TORUS, 2)
+    ref = E.ED(m, M.couplings(4.0, 0.3), 2.0).observables()
+    ch = O.Chain(M.TORUS, 2, 2.0, 0.05, 4.0, 0.3, seed=11, n_stab=5, n_adapt=150, model=m)
+    ch.sweep(150)
+    obs = ch.sweep(2500)
+    m2, R = fss.order_parameters(obs, 2)
+    assert np.allclose(m2, obs[:, 0], rtol=1e-13) and np.allclose(R, obs[:, 11], rtol=1e-12)
+    b = obs.reshape(25, -1, 20).mean(1)          # 25 bins of 100 sweeps
+    for chn, comp in (("VBS", [0, 1]), ("AFM", [2, 3, 4])):
+        s0, sd = ref["S0"][comp].sum(), ref["Sdq"][comp].sum()
+        for k, (val, exact) in enumerate(((fss.order_parameters(b, 2, chn)[0], s0 / (len(comp) * 4)),
+                                          (fss.order_parameters(b, 2, chn)[1], 1 - sd / s0))):
+            mu, err = val.mean(), val.std(ddof=1) / 5
+            assert abs(mu - exact) < 4 * err, (chn, k, mu, exact, err)
+
+    m = M.Model(M.SPHERE, 2)
+    ref = E.ED(m, M.couplings(1.0, -0.8), 2.0).observables()
+    assert ref["S0"][0] > 1.1 * ref["S0"][2]
+    assert ref["Sdq"][0] / ref["S0"][0] < ref["Sdq"][2] / ref["S0"][2]
+    ch = O.Chain(M.SPHERE, 2, 2.0, 0.1, 1.0, -0.8, seed=2, n_stab=5, n_adapt=150, model=m)
+    ch.sweep(150)
+    b = ch.sweep(2000).reshape(20, -1, 20).mean(1)
+    mv, Rv = fss.order_parameters(b, 2, "VBS")
+    ma, Ra = fss.order_parameters(b, 2, "AFM")
+    for d in (mv - ma, Rv - Ra):
+        assert d.mean() > 3 * d.std(ddof=1) / np.sqrt(20)
