@@ -32,6 +32,11 @@
  *   RNG                the paper is silent: Philox4x32-10 (Salmon et al.,
  *                      SC'11), counter = (index, slice, sweep, purpose),
  *                      key = (seed low, seed high), Box-Muller normals
+ *   slice variants     the same equations discretised two other ways (one
+ *                      exponential of the four channels; an independent
+ *                      field set for each half-factor), and the first-order
+ *                      drift (factors treated as commuting), all exact under
+ *                      MH; see ORC_SLICE_* and ORC_DRIFT_*
  *   learned slice move not in the paper (a learned proposal added to
  *                      the method): an MLP gives a Gaussian N(mu, sigma^2) for
  *                      slice tau from its neighbours; preconditioned Crank-
@@ -53,6 +58,24 @@ typedef double _Complex zc;
 static const int CH[7] = {0, 1, 2, 3, 2, 1, 0};
 static const double CJ[7] = {0.5, 0.5, 0.5, 1.0, 0.5, 0.5, 0.5};
 
+/* Slice discretisations (Methods, Eq. trotter_decomposition_methods and Eq.
+ * hs_transform_methods):
+ *  SYM    the paper's: seven factors e^{W0/2} e^{W1/2} e^{W2/2} e^{W3}
+ *         e^{W2/2} e^{W1/2} e^{W0/2}, W_i = alpha_i H_i(phi_i), the two
+ *         half-factors of a channel sharing its field;
+ *  SINGLE one exponential e^{W0 + W1 + W2 + W3} of the same four fields;
+ *  INDEP  the seven factors, each half-factor with a field of its own,
+ *         decoupling e^{-dtau g_i H_i / 2} by itself: exponent
+ *         sqrt(-dtau g_i / 2) H_i(phi_j).
+ * Drifts: EXACT grad S; FIRST the first-order drift, d ln det(1+B)/dX_j
+ * taken as Tr[(1-G) dX_j] for every factor (the factors treated as
+ * commuting), exact under MH because both proposal densities use it. */
+#define ORC_SLICE_SYM 0
+#define ORC_SLICE_SINGLE 1
+#define ORC_SLICE_INDEP 2
+#define ORC_DRIFT_EXACT 0
+#define ORC_DRIFT_FIRST 1
+
 typedef struct {
     int norb, N, nq, L, nstab;
     zc *ffval;          /* [nq][norb] */
@@ -66,7 +89,11 @@ typedef struct {
     double eps, deps, r0;
     int n_adapt;
     uint32_t sweep;
-    double *phi;        /* [L][4][nq] */
+    int slice_kind;     /* ORC_SLICE_*: discretisation of one slice */
+    int drift_kind;     /* ORC_DRIFT_*: drift of the Langevin proposal */
+    int nfs, nf;        /* field sets per slice (4, or 7 for independent
+                           half-factor fields) and nf = nfs * nq */
+    double *phi;        /* [L][nfs][nq] */
     zc *B, *Binv;       /* [L][N*N] */
     zc *G;              /* [N*N] */
     int nsp;            /* number of stabilisation points */
@@ -383,36 +410,104 @@ static zc Oval(int i, int v, int w)
     }
 }
 
+/* Factors of one slice.  SYM: eigenpairs of channel i at V[i], mu[i]
+ * (i < 4); INDEP: of factor j at V[j], mu[j]; both with E[j] = e^{X_j},
+ * Einv[j] = e^{-X_j}, j < 7.  SINGLE: E[0], Einv[0] and the exponent X. */
 typedef struct {
-    zc *V[4];
-    double *mu[4];
+    zc *V[7];
+    double *mu[7];
     zc *E[7], *Einv[7];
+    zc *X;
+    int nfac;
     zc trW0;
 } slice_fac;
 
 static void fac_alloc(const orc_t *o, slice_fac *f)
 {
     size_t nn = (size_t)o->N * o->N;
-    for (int i = 0; i < 4; ++i) {
-        f->V[i] = zalloc(nn);
-        f->mu[i] = (double *)calloc(o->N, sizeof(double));
-    }
     for (int j = 0; j < 7; ++j) {
+        f->V[j] = zalloc(nn);
+        f->mu[j] = (double *)calloc(o->N, sizeof(double));
         f->E[j] = zalloc(nn);
         f->Einv[j] = zalloc(nn);
     }
+    f->X = zalloc(nn);
+    f->nfac = o->slice_kind == ORC_SLICE_SINGLE ? 1 : 7;
 }
 
 static void fac_free(slice_fac *f)
 {
-    for (int i = 0; i < 4; ++i) {
-        free(f->V[i]);
-        free(f->mu[i]);
-    }
     for (int j = 0; j < 7; ++j) {
+        free(f->V[j]);
+        free(f->mu[j]);
         free(f->E[j]);
         free(f->Einv[j]);
     }
+    free(f->X);
+}
+
+/* field set, eigenpair slot and exponent coefficient of factor j (SYM and
+ * INDEP): X_j = coef * H_{CH[j]}(phi of the field set) */
+static int fac_set(const orc_t *o, int j) { return o->slice_kind == ORC_SLICE_INDEP ? j : CH[j]; }
+
+static zc fac_coef(const orc_t *o, int j)
+{
+    int i = CH[j];
+    if (o->slice_kind == ORC_SLICE_INDEP) return csqrt(-CJ[j] * o->dtau * o->g[i] + 0.0 * I);
+    return CJ[j] * o->alpha[i];
+}
+
+/* e^A for a general complex matrix: scaling and squaring with the Taylor
+ * series (||A / 2^s||_1 <= 1/4, 24 terms: truncation below 1e-30) */
+static void mat_expm(int n, const zc *A, zc *out)
+{
+    size_t nn = (size_t)n * n;
+    double nrm = 0.0;
+    for (int c = 0; c < n; ++c) {
+        double col = 0.0;
+        for (int r = 0; r < n; ++r) col += cabs(A[r * n + c]);
+        if (col > nrm) nrm = col;
+    }
+    int sq = 0;
+    while (nrm > 0.25) {
+        nrm *= 0.5;
+        ++sq;
+    }
+    double scale = ldexp(1.0, -sq);
+    zc *As = zalloc(nn), *term = zalloc(nn), *T = zalloc(nn);
+    for (size_t x = 0; x < nn; ++x) As[x] = A[x] * scale;
+    mat_eye(n, out);
+    mat_eye(n, term);
+    for (int k = 1; k <= 24; ++k) {
+        mat_mul(n, term, As, T);
+        for (size_t x = 0; x < nn; ++x) {
+            term[x] = T[x] / (double)k;
+            out[x] += term[x];
+        }
+    }
+    for (int k = 0; k < sq; ++k) {
+        mat_mul(n, out, out, T);
+        memcpy(out, T, sizeof(zc) * nn);
+    }
+    free(As); free(term); free(T);
+}
+
+/* Frechet derivative of the exponential, L(A, E) = int_0^1 e^{(1-s)A} E
+ * e^{sA} ds, as the upper right block of exp([[A, E], [0, A]]) */
+static void mat_expm_frechet(int n, const zc *A, const zc *E, zc *out)
+{
+    int m = 2 * n;
+    zc *Z = zalloc((size_t)m * m), *eZ = zalloc((size_t)m * m);
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) {
+            Z[r * m + c] = A[r * n + c];
+            Z[(r + n) * m + (c + n)] = A[r * n + c];
+            Z[r * m + (c + n)] = E[r * n + c];
+        }
+    mat_expm(m, Z, eZ);
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) out[r * n + c] = eZ[r * m + (c + n)];
+    free(Z); free(eZ);
 }
 
 /* H_i = O^i (x) F^(i), F^(i) = sum_q z_q F_q (Eq. hs_transform) */
@@ -437,29 +532,52 @@ static void channel_matrix(const orc_t *o, const double *phic, int i, zc *Hc)
     free(F);
 }
 
-/* factors of the slice propagator for the fields phis[4][nq] */
+/* factors of the slice propagator for the fields phis[nfs][nq]; trW0 is the
+ * sum of the channel-0 exponents' traces (the background factor of the
+ * weight is e^{-trW0/2} per spin block) */
 static void build_factors(const orc_t *o, const double *phis, slice_fac *f)
 {
-    int N = o->N;
+    int N = o->N, nq = o->nq;
     size_t nn = (size_t)N * N;
     zc *Hc = zalloc(nn), *T = zalloc(nn), *Vh = zalloc(nn);
     f->trW0 = 0.0;
-    for (int i = 0; i < 4; ++i) {
-        channel_matrix(o, phis + (size_t)i * o->nq, i, Hc);
-        if (i == 0)
-            for (int x = 0; x < N; ++x) f->trW0 += o->alpha[0] * Hc[x * N + x];
-        eigh(N, Hc, f->V[i], f->mu[i]);
+    f->nfac = o->slice_kind == ORC_SLICE_SINGLE ? 1 : 7;
+    if (o->slice_kind == ORC_SLICE_SINGLE) {
+        for (size_t x = 0; x < nn; ++x) f->X[x] = 0.0;
+        for (int i = 0; i < 4; ++i) {
+            channel_matrix(o, phis + (size_t)i * nq, i, Hc);
+            for (size_t x = 0; x < nn; ++x) f->X[x] += o->alpha[i] * Hc[x];
+            if (i == 0)
+                for (int x = 0; x < N; ++x) f->trW0 += o->alpha[0] * Hc[x * N + x];
+        }
+        mat_expm(N, f->X, f->E[0]);
+        for (size_t x = 0; x < nn; ++x) T[x] = -f->X[x];
+        mat_expm(N, T, f->Einv[0]);
+        free(Hc); free(T); free(Vh);
+        return;
+    }
+    /* eigenpairs: per channel (SYM) or per factor (INDEP) */
+    int neig = o->slice_kind == ORC_SLICE_INDEP ? 7 : 4;
+    for (int k = 0; k < neig; ++k) {
+        int i = o->slice_kind == ORC_SLICE_INDEP ? CH[k] : k;
+        channel_matrix(o, phis + (size_t)k * nq, i, Hc);
+        if (i == 0) {
+            /* SYM: both half-factors, alpha_0 / 2 each; INDEP: this one */
+            zc a = o->slice_kind == ORC_SLICE_INDEP ? fac_coef(o, k) : o->alpha[0];
+            for (int x = 0; x < N; ++x) f->trW0 += a * Hc[x * N + x];
+        }
+        eigh(N, Hc, f->V[k], f->mu[k]);
     }
     for (int j = 0; j < 7; ++j) {
-        int i = CH[j];
-        zc a = CJ[j] * o->alpha[i];
-        mat_adj(N, f->V[i], Vh);
+        int k = fac_set(o, j);
+        zc a = fac_coef(o, j);
+        mat_adj(N, f->V[k], Vh);
         for (int s = 0; s < 2; ++s) {
             zc *dst = s == 0 ? f->E[j] : f->Einv[j];
             for (int r = 0; r < N; ++r)
                 for (int c = 0; c < N; ++c) {
-                    zc e = cexp((s == 0 ? a : -a) * f->mu[i][c]);
-                    T[r * N + c] = f->V[i][r * N + c] * e;
+                    zc e = cexp((s == 0 ? a : -a) * f->mu[k][c]);
+                    T[r * N + c] = f->V[k][r * N + c] * e;
                 }
             mat_mul(N, T, Vh, dst);
         }
@@ -469,19 +587,19 @@ static void build_factors(const orc_t *o, const double *phis, slice_fac *f)
     free(Vh);
 }
 
-/* B = E_1 ... E_7, B^-1 = Einv_7 ... Einv_1 (Eq. trotter_decomposition) */
+/* B = E_1 ... E_n, B^-1 = Einv_n ... Einv_1 (Eq. trotter_decomposition) */
 static void product_B(const orc_t *o, const slice_fac *f, zc *B, zc *Binv)
 {
     int N = o->N;
     size_t nn = (size_t)N * N;
     zc *T = zalloc(nn);
     memcpy(B, f->E[0], sizeof(zc) * nn);
-    for (int j = 1; j < 7; ++j) {
+    for (int j = 1; j < f->nfac; ++j) {
         mat_mul(N, B, f->E[j], T);
         memcpy(B, T, sizeof(zc) * nn);
     }
-    memcpy(Binv, f->Einv[6], sizeof(zc) * nn);
-    for (int j = 5; j >= 0; --j) {
+    memcpy(Binv, f->Einv[f->nfac - 1], sizeof(zc) * nn);
+    for (int j = f->nfac - 2; j >= 0; --j) {
         mat_mul(N, Binv, f->Einv[j], T);
         memcpy(Binv, T, sizeof(zc) * nn);
     }
@@ -520,41 +638,66 @@ static zc trace_OF(const orc_t *o, int i, int q, const zc *A)
     return s;
 }
 
-/* grad_phi S for one slice (Eq. action_gradient, exact):
+/* grad_phi S for one slice (Eq. action_gradient).  Exact drift:
  * d ln det(1+B)/dphi = Tr[(1-G) dB B^-1] = sum_j Tr[dX_j Atilde_j],
  * Atilde_j = int_0^1 e^{-sX_j} P_j^-1 (1-G) P_j e^{sX_j} ds,
- * P_j = E_1..E_{j-1}; plus the background derivative; two spin blocks. */
+ * P_j = E_1..E_{j-1} (SYM, INDEP: through the eigenpairs; SINGLE: one factor,
+ * Atilde = L(X, B^-1 (1-G)) by the augmented exponential).  First-order
+ * drift: Atilde_j = 1-G for every factor.  Plus the background derivative;
+ * two spin blocks. */
 static void gradient(const orc_t *o, const double *phis, const slice_fac *f,
                      const zc *G, double *grad)
 {
-    int N = o->N, nq = o->nq;
+    int N = o->N, nq = o->nq, nfs = o->nfs;
     size_t nn = (size_t)N * N;
     zc *A = zalloc(nn), *Vh = zalloc(nn), *T = zalloc(nn), *Ah = zalloc(nn),
        *At = zalloc(nn);
-    zc *t = zalloc((size_t)4 * nq);
+    zc *t = zalloc((size_t)nfs * nq);
     for (size_t x = 0; x < nn; ++x) A[x] = -G[x];
     for (int x = 0; x < N; ++x) A[x * N + x] += 1.0;
-    for (int j = 0; j < 7; ++j) {
-        int i = CH[j];
-        zc a = CJ[j] * o->alpha[i];
-        const zc *V = f->V[i];
-        mat_adj(N, V, Vh);
-        mat_mul(N, Vh, A, T);
-        mat_mul(N, T, V, Ah);
-        for (int m = 0; m < N; ++m)
-            for (int k = 0; k < N; ++k)
-                Ah[m * N + k] *= phi1(a * (f->mu[i][k] - f->mu[i][m]));
-        mat_mul(N, V, Ah, T);
-        mat_mul(N, T, Vh, At);
-        for (int q = 0; q < nq; ++q) t[i * nq + q] += a * trace_OF(o, i, q, At);
-        mat_mul(N, f->Einv[j], A, T);
-        mat_mul(N, T, f->E[j], A);
+    if (o->slice_kind == ORC_SLICE_SINGLE) {
+        if (o->drift_kind == ORC_DRIFT_EXACT) {
+            mat_mul(N, f->Einv[0], A, T);
+            mat_expm_frechet(N, f->X, T, At);
+        } else {
+            memcpy(At, A, sizeof(zc) * nn);
+        }
+        for (int i = 0; i < 4; ++i)
+            for (int q = 0; q < nq; ++q) t[i * nq + q] += o->alpha[i] * trace_OF(o, i, q, At);
+    } else {
+        for (int j = 0; j < 7; ++j) {
+            int i = CH[j], k = fac_set(o, j);
+            zc a = fac_coef(o, j);
+            if (o->drift_kind == ORC_DRIFT_FIRST) {
+                for (int q = 0; q < nq; ++q) t[k * nq + q] += a * trace_OF(o, i, q, A);
+                continue;
+            }
+            const zc *V = f->V[k];
+            mat_adj(N, V, Vh);
+            mat_mul(N, Vh, A, T);
+            mat_mul(N, T, V, Ah);
+            for (int m = 0; m < N; ++m)
+                for (int c = 0; c < N; ++c)
+                    Ah[m * N + c] *= phi1(a * (f->mu[k][c] - f->mu[k][m]));
+            mat_mul(N, V, Ah, T);
+            mat_mul(N, T, Vh, At);
+            for (int q = 0; q < nq; ++q) t[k * nq + q] += a * trace_OF(o, i, q, At);
+            mat_mul(N, f->Einv[j], A, T);
+            mat_mul(N, T, f->E[j], A);
+        }
     }
-    for (int q = 0; q < nq; ++q) t[q] -= o->alpha[0] * o->trF[q];
-    for (int i = 0; i < 4; ++i) {
-        const zc *ti = t + (size_t)i * nq;
-        const double *ph = phis + (size_t)i * nq;
-        double *gr = grad + (size_t)i * nq;
+    /* background: -1/2 Tr of each channel-0 exponent, two spin blocks */
+    if (o->slice_kind == ORC_SLICE_INDEP) {
+        for (int j = 0; j < 7; ++j)
+            if (CH[j] == 0)
+                for (int q = 0; q < nq; ++q) t[j * nq + q] -= fac_coef(o, j) * o->trF[q];
+    } else {
+        for (int q = 0; q < nq; ++q) t[q] -= o->alpha[0] * o->trF[q];
+    }
+    for (int k = 0; k < nfs; ++k) {
+        const zc *ti = t + (size_t)k * nq;
+        const double *ph = phis + (size_t)k * nq;
+        double *gr = grad + (size_t)k * nq;
         for (int q = 0; q < nq; ++q) {
             int p = o->partner[q];
             switch (o->fkind[q]) {
@@ -651,6 +794,40 @@ static void build_left_stack(orc_t *o)
 /* ------------------------------------------------------------- API ----- */
 void orc_destroy(orc_t *o);
 
+/* initial fields phi ~ N(0,1), purpose 0 */
+static void init_fields(orc_t *o)
+{
+    int nf = o->nf;
+    o->phi = (double *)malloc(sizeof(double) * (size_t)o->L * nf);
+    for (int t = 0; t < o->L; ++t)
+        for (int f = 0; f < nf; ++f)
+            o->phi[(size_t)t * nf + f] = normal_at(o, (uint32_t)f, (uint32_t)t, 0, 0);
+}
+
+/* slice propagators from the fields, the left stack, and G(0) =
+ * (1 + B(b,0))^-1 */
+static void rebuild(orc_t *o)
+{
+    int N = o->N;
+    size_t nn = (size_t)N * N;
+    slice_fac fac;
+    fac_alloc(o, &fac);
+    for (int t = 0; t < o->L; ++t) {
+        build_factors(o, o->phi + (size_t)t * o->nf, &fac);
+        product_B(o, &fac, o->B + (size_t)t * nn, o->Binv + (size_t)t * nn);
+    }
+    fac_free(&fac);
+    build_left_stack(o);
+    zc *QI = zalloc(nn), *WI = zalloc(nn);
+    double *DI = (double *)malloc(sizeof(double) * N);
+    mat_eye(N, QI);
+    mat_eye(N, WI);
+    for (int x = 0; x < N; ++x) DI[x] = 1.0;
+    green_from_udv(N, QI, DI, WI, o->LQ + (size_t)o->nsp * nn,
+                   o->LD + (size_t)o->nsp * N, o->LW + (size_t)o->nsp * nn, o->G);
+    free(QI); free(WI); free(DI);
+}
+
 orc_t *orc_create(int norb, int nq, const double *ffval, const int *ffcol,
                   const int *partner, int L, int nstab, double dtau,
                   const double *g, uint64_t seed, double eps0, double deps,
@@ -712,34 +889,42 @@ orc_t *orc_create(int norb, int nq, const double *ffval, const int *ffcol,
     o->LQ = zalloc(nn * (o->nsp + 1));
     o->LW = zalloc(nn * (o->nsp + 1));
     o->LD = (double *)calloc((size_t)N * (o->nsp + 1), sizeof(double));
-    /* fields phi ~ N(0,1), purpose 0 */
-    int nf = 4 * nq;
-    o->phi = (double *)malloc(sizeof(double) * (size_t)L * nf);
-    for (int t = 0; t < L; ++t)
-        for (int f = 0; f < nf; ++f)
-            o->phi[(size_t)t * nf + f] = normal_at(o, (uint32_t)f, (uint32_t)t, 0, 0);
+    o->slice_kind = ORC_SLICE_SYM;
+    o->drift_kind = ORC_DRIFT_EXACT;
+    o->nfs = 4;
+    o->nf = 4 * nq;
+    init_fields(o);
     o->B = zalloc(nn * L);
     o->Binv = zalloc(nn * L);
-    slice_fac fac;
-    fac_alloc(o, &fac);
-    for (int t = 0; t < L; ++t) {
-        build_factors(o, o->phi + (size_t)t * nf, &fac);
-        product_B(o, &fac, o->B + (size_t)t * nn, o->Binv + (size_t)t * nn);
-    }
-    fac_free(&fac);
     o->G = zalloc(nn);
-    /* G(0) = (1 + B(b,0))^-1 */
-    build_left_stack(o);
-    zc *QI = zalloc(nn), *WI = zalloc(nn);
-    double *DI = (double *)malloc(sizeof(double) * N);
-    mat_eye(N, QI);
-    mat_eye(N, WI);
-    for (int x = 0; x < N; ++x) DI[x] = 1.0;
-    green_from_udv(N, QI, DI, WI, o->LQ + (size_t)o->nsp * nn,
-                   o->LD + (size_t)o->nsp * N, o->LW + (size_t)o->nsp * nn, o->G);
-    free(QI); free(WI); free(DI);
+    rebuild(o);
     return o;
 }
+
+/* Switch the slice discretisation and the drift (ORC_SLICE_*, ORC_DRIFT_*);
+ * only before the first sweep.  A change in the number of field sets per
+ * slice redraws the initial fields over the new layout; the propagators, the
+ * left stack and G are rebuilt.  Returns 0, or -1 for an unknown kind or a
+ * chain that has already swept. */
+int orc_set_variant(orc_t *o, int slice_kind, int drift_kind)
+{
+    if (slice_kind < ORC_SLICE_SYM || slice_kind > ORC_SLICE_INDEP ||
+        drift_kind < ORC_DRIFT_EXACT || drift_kind > ORC_DRIFT_FIRST || o->sweep != 0)
+        return -1;
+    o->slice_kind = slice_kind;
+    o->drift_kind = drift_kind;
+    int nfs = slice_kind == ORC_SLICE_INDEP ? 7 : 4;
+    if (nfs != o->nfs) {
+        o->nfs = nfs;
+        o->nf = nfs * o->nq;
+        free(o->phi);
+        init_fields(o);
+    }
+    rebuild(o);
+    return 0;
+}
+
+int orc_fields_per_slice(const orc_t *o) { return o->nf; }
 
 void orc_destroy(orc_t *o)
 {
@@ -764,7 +949,7 @@ long orc_trace_count(const orc_t *o) { return o->trace_n; }
  * and on exit (Methods, "Langevin-based global update scheme") */
 static void update_slice(orc_t *o, int t, slice_fac *fc, slice_fac *fp)
 {
-    int N = o->N, nf = 4 * o->nq;
+    int N = o->N, nf = o->nf;
     size_t nn = (size_t)N * N;
     double *phi = o->phi + (size_t)(t - 1) * nf;
     zc *B = o->B + (size_t)(t - 1) * nn, *Binv = o->Binv + (size_t)(t - 1) * nn;
@@ -891,7 +1076,7 @@ void orc_mlp_forward(int nf, int H, const double *theta, int B, const double *X,
 static void update_slice_learned(orc_t *o, int t, const learned_t *lp, slice_fac *fc,
                                  slice_fac *fp)
 {
-    int N = o->N, nf = 4 * o->nq, L = o->L;
+    int N = o->N, nf = o->nf, L = o->L;
     size_t nn = (size_t)N * N;
     double *phi = o->phi + (size_t)(t - 1) * nf;
     const double *prv = o->phi + (size_t)((t - 2 + L) % L) * nf;
@@ -966,7 +1151,7 @@ void orc_sweep_learned(orc_t *o, int nsweeps, double *obs, int H, const double *
                        double rho)
 {
     learned_t lp;
-    learned_bind(&lp, 4 * o->nq, H, theta);
+    learned_bind(&lp, o->nf, H, theta);
     lp.rho = rho;
     sweep_impl(o, nsweeps, obs, &lp);
 }
@@ -1168,7 +1353,7 @@ void orc_get_green(const orc_t *o, double *out)
 
 void orc_get_phi(const orc_t *o, double *out)
 {
-    memcpy(out, o->phi, sizeof(double) * (size_t)o->L * 4 * o->nq);
+    memcpy(out, o->phi, sizeof(double) * (size_t)o->L * o->nf);
 }
 
 double orc_get_eps(const orc_t *o) { return o->eps; }
@@ -1185,7 +1370,7 @@ void orc_get_B(const orc_t *o, int t, double *B, double *Binv)
 /* replace the fields of slice t (1-based) and rebuild B_t, B_t^-1 */
 void orc_set_slice_phi(orc_t *o, int t, const double *phis)
 {
-    int nf = 4 * o->nq;
+    int nf = o->nf;
     size_t nn = (size_t)o->N * o->N;
     memcpy(o->phi + (size_t)(t - 1) * nf, phis, sizeof(double) * nf);
     slice_fac f;
@@ -1213,7 +1398,7 @@ static void chain_product(const orc_t *o, int t1, int t2, zc *P)
  * block (no stabilisation: small beta only) */
 void orc_log_bracket(const orc_t *o, double *out)
 {
-    int N = o->N, nf = 4 * o->nq;
+    int N = o->N, nf = o->nf;
     size_t nn = (size_t)N * N;
     zc *P = zalloc(nn);
     int *piv = (int *)malloc(sizeof(int) * N);
@@ -1255,7 +1440,7 @@ void orc_green_bruteforce(const orc_t *o, int t, double *out)
  * force */
 void orc_gradient_at(const orc_t *o, int t, double *grad)
 {
-    int N = o->N, nf = 4 * o->nq;
+    int N = o->N, nf = o->nf;
     size_t nn = (size_t)N * N;
     double *Gd = (double *)malloc(sizeof(double) * 2 * nn);
     zc *G = zalloc(nn);
@@ -1271,17 +1456,21 @@ void orc_gradient_at(const orc_t *o, int t, double *grad)
 }
 
 /* the seven factors of slice t as dense matrices (for tests) */
-void orc_slice_factors(const orc_t *o, int t, double *E, double *trW0)
+/* factors e^{X_j} of slice t (7 of them, or 1 for the single exponential,
+ * the count returned) into E[7][N][N] interleaved, and the channel-0 trace */
+int orc_slice_factors(const orc_t *o, int t, double *E, double *trW0)
 {
-    int nf = 4 * o->nq;
+    int nf = o->nf;
     size_t nn = (size_t)o->N * o->N;
     slice_fac f;
     fac_alloc(o, &f);
     build_factors(o, o->phi + (size_t)(t - 1) * nf, &f);
-    for (int j = 0; j < 7; ++j) to_interleaved(f.E[j], nn, E + 2 * nn * j);
+    for (int j = 0; j < f.nfac; ++j) to_interleaved(f.E[j], nn, E + 2 * nn * j);
     trW0[0] = creal(f.trW0);
     trW0[1] = cimag(f.trW0);
+    int nfac = f.nfac;
     fac_free(&f);
+    return nfac;
 }
 
 void orc_normals(uint64_t seed, uint32_t slice, uint32_t sweep, uint32_t purpose,
@@ -1337,7 +1526,7 @@ void orc_logdet(int n, const double *A, double *out)
 void orc_ratio_at(const orc_t *o, int t, const double *phis, double *logR,
                   double *Gp_out)
 {
-    int N = o->N, nf = 4 * o->nq;
+    int N = o->N, nf = o->nf;
     size_t nn = (size_t)N * N;
     double *Gd = (double *)malloc(sizeof(double) * 2 * nn);
     zc *G = zalloc(nn), *Bp = zalloc(nn), *Bpi = zalloc(nn), *Dl = zalloc(nn),

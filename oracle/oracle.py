@@ -71,7 +71,12 @@ def lib():
         L.orc_log_bracket.argtypes = [C.c_void_p, dp]
         L.orc_green_bruteforce.argtypes = [C.c_void_p, C.c_int, dp]
         L.orc_gradient_at.argtypes = [C.c_void_p, C.c_int, dp]
+        L.orc_slice_factors.restype = C.c_int
         L.orc_slice_factors.argtypes = [C.c_void_p, C.c_int, dp, dp]
+        L.orc_set_variant.restype = C.c_int
+        L.orc_set_variant.argtypes = [C.c_void_p, C.c_int, C.c_int]
+        L.orc_fields_per_slice.restype = C.c_int
+        L.orc_fields_per_slice.argtypes = [C.c_void_p]
         L.orc_normals.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
                                   C.c_int, dp]
         L.orc_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
@@ -136,14 +141,24 @@ def logdet(A):
     return complex(out[0], out[1])
 
 
+SLICE_SYM, SLICE_SINGLE, SLICE_INDEP = 0, 1, 2
+DRIFT_EXACT, DRIFT_FIRST = 0, 1
+
+
 class Chain:
     """One Markov chain of the oracle.
 
     geom/size select the model (torus N_phi or sphere orbital count);
-    u, anis give the couplings; L = beta/dtau slices."""
+    u, anis give the couplings; L = beta/dtau slices.  slice_kind picks the
+    discretisation of a slice (SLICE_SYM: the paper's seven factors with
+    shared fields; SLICE_SINGLE: one exponential of the four channels;
+    SLICE_INDEP: seven factors with a field set each) and drift_kind the
+    Langevin drift (DRIFT_EXACT, or DRIFT_FIRST: each factor's derivative
+    taken as Tr[(1-G) dX])."""
 
     def __init__(self, geom, size, beta, dtau, u, anis, seed, n_stab=5,
-                 eps0=0.5, deps=0.1, r0=0.574, n_adapt=-1, g=None, model=None):
+                 eps0=0.5, deps=0.1, r0=0.574, n_adapt=-1, g=None, model=None,
+                 slice_kind=SLICE_SYM, drift_kind=DRIFT_EXACT):
         self.model = model if model is not None else M.Model(geom, size)
         L = int(round(beta / dtau))
         if abs(L * dtau - beta) > 1e-9 * max(1.0, beta):
@@ -160,6 +175,11 @@ class Chain:
         self.h = lib().orc_create(m.norb, m.nq, _dp(self._ffval.view(float)),
                                   _ip(self._ffcol), _ip(self._partner), L, n_stab,
                                   dtau, _dp(self._g), seed, eps0, deps, r0, n_adapt)
+        if (slice_kind, drift_kind) != (SLICE_SYM, DRIFT_EXACT):
+            if lib().orc_set_variant(self.h, slice_kind, drift_kind) != 0:
+                raise ValueError("unknown slice or drift variant")
+        self.slice_kind, self.drift_kind = slice_kind, drift_kind
+        self.nfs = lib().orc_fields_per_slice(self.h) // m.nq
         dq = np.array(m.delta_q(), dtype=np.int32)
         lib().orc_set_measure_q(self.h, m.q0() if m.geom == M.TORUS else 0,
                                 _ip(dq), len(dq))
@@ -234,12 +254,12 @@ class Chain:
         return G
 
     def phi(self):
-        p = np.zeros((self.L, 4, self.nq))
+        p = np.zeros((self.L, self.nfs, self.nq))
         lib().orc_get_phi(self.h, _dp(p))
         return p
 
     def set_slice_phi(self, t, phis):
-        phis = np.ascontiguousarray(phis, dtype=float).reshape(4 * self.nq)
+        phis = np.ascontiguousarray(phis, dtype=float).reshape(self.nfs * self.nq)
         lib().orc_set_slice_phi(self.h, t, _dp(phis))
 
     def B(self, t):
@@ -251,8 +271,8 @@ class Chain:
     def factors(self, t):
         E = np.zeros((7, self.N, self.N), complex)
         tw = np.zeros(2)
-        lib().orc_slice_factors(self.h, t, _dp(E.view(float)), _dp(tw))
-        return E, complex(tw[0], tw[1])
+        n = lib().orc_slice_factors(self.h, t, _dp(E.view(float)), _dp(tw))
+        return E[:n], complex(tw[0], tw[1])
 
     def log_bracket(self):
         out = np.zeros(2)
@@ -260,13 +280,13 @@ class Chain:
         return complex(out[0], out[1])
 
     def gradient(self, t):
-        g = np.zeros((4, self.nq))
+        g = np.zeros((self.nfs, self.nq))
         lib().orc_gradient_at(self.h, t, _dp(g))
         return g
 
     def ratio_at(self, t, phis):
         """(log R, G') for replacing slice t's fields by phis (G by brute force)."""
-        phis = np.ascontiguousarray(phis, dtype=float).reshape(4 * self.nq)
+        phis = np.ascontiguousarray(phis, dtype=float).reshape(self.nfs * self.nq)
         out = np.zeros(2)
         Gp = np.zeros((self.N, self.N), complex)
         lib().orc_ratio_at(self.h, t, _dp(phis), _dp(out), _dp(Gp.view(float)))
