@@ -161,6 +161,30 @@ class ED:
                 tot += np.trace(left @ A @ prop @ B).real
         return tot / self.Z
 
+    def gap(self, gi: int, q: int, rel_tol: float = 1e-10) -> float:
+        """Lowest excitation energy E_n - E_0 reachable from the ground state
+        by n^{Gamma^i}_q (spectral weight |<n| n_q |0>|^2 above rel_tol of
+        the total): the rate of the long-time decay of S^i_q(tau) at zero
+        temperature (Supplementary Note 2).  Needs a unique ground state."""
+        tv, ts = GAMMA[gi]
+        hq = one_body(self.model, q, PAULI[tv], PAULI[ts])
+        levels = sorted((w[k], key, k) for key, (w, _, _) in self.blocks.items() for k in range(len(w)))
+        e0, key0, k0 = levels[0]
+        if levels[1][0] - e0 < 1e-9 * max(1.0, abs(e0)):
+            raise ValueError("degenerate ground state")
+        psi0 = self.blocks[key0][1][:, k0]
+        nu, nd = key0
+        found = []
+        for mid in [(nu, nd), (nu + 1, nd - 1), (nu - 1, nd + 1)]:
+            if mid not in self.blocks:
+                continue
+            wm, Vm, _ = self.blocks[mid]
+            amp = Vm.conj().T @ (self.fock.op(hq, mid, key0) @ psi0)
+            found += [(e, abs(a) ** 2) for e, a in zip(wm, amp)]
+        tot = sum(a for _, a in found)
+        exc = [e - e0 for e, a in found if a > rel_tol * tot and e - e0 > 1e-9]
+        return float(min(exc))
+
     def observables(self) -> dict:
         m = self.model
         q0 = m.q0() if m.geom == M.TORUS else 0

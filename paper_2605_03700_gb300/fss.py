@@ -19,7 +19,9 @@ scaling"):
   m^2 N_phi^Delta_v (Supplementary Note 3, data scaling analysis);
 * the same scans in the anisotropy alpha for the VBS and AFM ratios away
   from the SO(5) line (Results, "Phase boundaries away from the
-  SO(5)-symmetric line"; Supplementary Note 1).
+  SO(5)-symmetric line"; Supplementary Note 1);
+* the SO(5) gap from the tail of the imaginary-time correlation and the
+  dynamical exponent z from its size dependence (Supplementary Note 2).
 
 Inputs are per-(u, N_phi) means (e.g. from Chain.series() with errors from
 mean_err); everything is numpy on the host.
@@ -206,3 +208,81 @@ def select(u, nphi, *cols, nphi_min=None, u_range=None):
     if u_range is not None:
         k &= (u >= u_range[0]) & (u <= u_range[1])
     return (u[k], nphi[k]) + tuple(np.asarray(c, float)[k] for c in cols)
+
+
+# ------------------------------------------------- gap and dynamics --------
+# Supplementary Note 2: the imaginary-time SO(5) correlation
+# m^2(tau, q=0) = (1/5) sum_i <n_0^{Gamma^i}(tau) n_0^{Gamma^i}(0)> decays as
+# e^{-Delta tau} at long times; Delta ~ sqrt(N_phi)^-z gives the dynamical
+# exponent z from ln Delta = z ln(1/sqrt(N_phi)) + C.
+
+def effective_gap(tau, C):
+    """-d ln C / d tau between consecutive points: (tau midpoints, Delta_eff);
+    a plateau marks the range where one exponential dominates."""
+    tau = np.asarray(tau, dtype=float)
+    C = np.asarray(C, dtype=float)
+    return 0.5 * (tau[1:] + tau[:-1]), -np.diff(np.log(C)) / np.diff(tau)
+
+
+def fit_gap(tau, C, err=None, tmin=None, tmax=None, beta=None):
+    """Gap from the long-time tail of a correlation function over
+    tmin <= tau <= tmax: without beta, the exponential A e^{-Delta tau}
+    (weighted linear fit of ln C); with beta, the periodic form
+    A (e^{-Delta tau} + e^{-Delta (beta - tau)}) of a finite-temperature
+    correlation (nonlinear least squares started from the exponential fit).
+    Returns (Delta, standard error, A)."""
+    tau = np.asarray(tau, dtype=float)
+    C = np.asarray(C, dtype=float)
+    sig = np.full(len(C), 1.0) if err is None else np.asarray(err, dtype=float)
+    k = np.ones(len(tau), dtype=bool)
+    if tmin is not None:
+        k &= tau >= tmin
+    if tmax is not None:
+        k &= tau <= tmax
+    t, c, s = tau[k], C[k], sig[k]
+    if len(t) < 3 or np.any(c <= 0):
+        raise ValueError("need at least three positive points in the window")
+    # ln C has error err / C; without errors, equal weights in ln C
+    w = np.ones(len(c)) if err is None else (c / s) ** 2
+    X = np.vstack([np.ones(len(t)), -t]).T
+    A = X.T @ (X * w[:, None])
+    beta_ = np.linalg.solve(A, X.T @ (w * np.log(c)))
+    cov = np.linalg.inv(A)
+    if err is None:
+        r = np.log(c) - X @ beta_
+        cov = cov * (r @ r) / max(len(t) - 2, 1)
+    gap, amp = float(beta_[1]), float(np.exp(beta_[0]))
+    egap = float(np.sqrt(cov[1, 1]))
+    if beta is None:
+        return gap, egap, amp
+    from scipy.optimize import curve_fit
+
+    def f(x, a, d):
+        return a * (np.exp(-d * x) + np.exp(-d * (beta - x)))
+    # start from the decay of the first half of the window (before the
+    # periodic image turns the curve up)
+    h = t <= 0.5 * beta
+    d0 = -np.polyfit(t[h], np.log(c[h]), 1)[0] if h.sum() >= 2 else 0.0
+    d0 = d0 if d0 > 0 else 1.0 / beta
+    a0 = float(c[0] / (np.exp(-d0 * t[0]) + np.exp(-d0 * (beta - t[0]))))
+    p, pc = curve_fit(f, t, c, p0=[a0, d0], sigma=s, absolute_sigma=err is not None,
+                      bounds=([0.0, 0.0], [np.inf, np.inf]))
+    return float(p[1]), float(np.sqrt(pc[1, 1])), float(p[0])
+
+
+def dynamical_exponent(nphi, gap, err=None):
+    """z and C of ln Delta = z ln(1/sqrt(N_phi)) + C (weighted by the gaps'
+    errors when given): returns (z, standard error, C)."""
+    nphi = np.asarray(nphi, dtype=float)
+    gap = np.asarray(gap, dtype=float)
+    x = np.log(1.0 / np.sqrt(nphi))
+    sig = np.ones(len(gap)) if err is None else np.asarray(err, dtype=float) / gap
+    w = 1.0 / sig ** 2
+    X = np.vstack([np.ones(len(x)), x]).T
+    A = X.T @ (X * w[:, None])
+    b = np.linalg.solve(A, X.T @ (w * np.log(gap)))
+    cov = np.linalg.inv(A)
+    if err is None:
+        r = np.log(gap) - X @ b
+        cov = cov * (r @ r) / max(len(x) - 2, 1)
+    return float(b[1]), float(np.sqrt(cov[1, 1])), float(b[0])

@@ -228,3 +228,56 @@ def test_channels_against_the_oracle_chain_and_exact_diagonalisation():
     ma, Ra = fss.order_parameters(b, 2, "AFM")
     for d in (mv - ma, Rv - Ra):
         assert d.mean() > 3 * d.std(ddof=1) / np.sqrt(20)
+
+
+def test_gap_fits_on_synthetic_correlations():
+    tau = np.arange(0, 10.01, 0.25)
+    C = 2.0 * np.exp(-0.7 * tau) + 0.5 * np.exp(-3.0 * tau)
+    mid, de = fss.effective_gap(tau, C)
+    assert de[0] > 1.0 and abs(de[-1] - 0.7) < 1e-9          # plateau at the gap
+    d, e, a = fss.fit_gap(tau, C, tmin=5)
+    assert abs(d - 0.7) < 1e-6 and abs(a - 2.0) < 1e-5
+    # finite temperature: the periodic form
+    beta = 12.0
+    Cb = 2.0 * (np.exp(-0.7 * tau) + np.exp(-0.7 * (beta - tau)))
+    d, e, a = fss.fit_gap(tau, Cb, tmin=2, tmax=10, beta=beta)
+    assert abs(d - 0.7) < 1e-8 and abs(a - 2.0) < 1e-7
+    assert abs(fss.fit_gap(tau, Cb, tmin=2, tmax=10)[0] - 0.7) > 0.05   # the plain exponential is biased
+    # noisy data: the error covers the truth
+    rng = np.random.default_rng(8)
+    err = 0.01 * C
+    Cn = C + err * rng.standard_normal(len(C))
+    d, e, _ = fss.fit_gap(tau, Cn, err, tmin=4)
+    assert 0 < e < 0.05 and abs(d - 0.7) < 4 * e
+    with pytest.raises(ValueError):
+        fss.fit_gap(tau, -C, tmin=4)
+
+
+def test_dynamical_exponent():
+    n = np.array([8.0, 12, 16, 24, 32])
+    z, ez, c = fss.dynamical_exponent(n, 3.0 * n ** -0.5)
+    assert abs(z - 1.0) < 1e-12 and abs(c - np.log(3.0)) < 1e-12 and ez < 1e-10
+    z, _, _ = fss.dynamical_exponent(n, 3.0 * n ** -1.0)
+    assert abs(z - 2.0) < 1e-12
+    rng = np.random.default_rng(9)
+    g = 3.0 * n ** -0.5 * (1 + 0.02 * rng.standard_normal(len(n)))
+    z, ez, _ = fss.dynamical_exponent(n, g, 0.02 * g)
+    assert 0.02 < ez < 0.5 and abs(z - 1.0) < 4 * ez
+
+
+def test_gap_fit_against_the_exact_spectrum():
+    """Torus N_phi = 2, u = 15 (deep in the disordered phase, the coupling of
+    the paper's dynamics measurement), beta = 40: the decay rate fitted to
+    the exact S^i_0(tau) equals the lowest excitation energy that n^{Gamma^i}_0
+    reaches from the ground state (ED spectrum)."""
+    from oracle import ed as E
+    from oracle import model as M
+    m = M.Model(M.TORUS, 2)
+    ed = E.ED(m, M.couplings(15.0, 0.0), 40.0)
+    q0 = m.q0()
+    taus = np.arange(0.0, 10.5, 1.0)      # S(tau) >= 1e-6 S(0): ED is exact there
+    for gi in (0, 2):
+        S = np.array([ed.structure_factor_tau(gi, q0, t) for t in taus])
+        d, e, _ = fss.fit_gap(taus, S, tmin=3, beta=40.0)
+        assert abs(d - ed.gap(gi, q0)) < 1e-8, (gi, d, ed.gap(gi, q0))
+        assert 0.9 < d < 1.2
