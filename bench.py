@@ -241,7 +241,8 @@ def run_ours(args):
     seeds = replica_seeds(rank)
     ch = P.Chain(P.QMC_TORUS, NPHI, BETA, DTAU, 0.0, 0.0, 0, n_chains=NCH, couplings=COUPLINGS,
                  seeds=seeds, n_stab=NSTAB, eps0=EPS0, series_capacity=4096,
-                 precision=args.precision)
+                 precision=args.precision,
+                 drift=P.QMC_DRIFT_FIRST if args.drift == "first" else P.QMC_DRIFT_EXACT)
     ch.set_stream(stream.cuda_stream)
     # learned mode: whole-slice moves around the network's Gaussian
     # (qmc_sweep_learned, rho = 0), a Langevin sweep every LANGEVIN_EVERY-th
@@ -314,6 +315,7 @@ def run_ours(args):
         "config": workload_config({"parallelism": f"replicas x{world}",
                                    "precision": ["fp64", "mixed fp32/fp64"][args.precision],
                                    "mode": args.mode,
+                                   "drift": args.drift,
                                    "schedule": ("plain Langevin sweeps" if args.mode == "plain" else
                                                 f"learned sweeps (rho 0), every {LANGEVIN_EVERY}th "
                                                 "step a Langevin sweep"),
@@ -358,6 +360,9 @@ def main():
     ap.add_argument("--mode", default="learned", choices=["learned", "plain"],
                     help="learned: learned-proposal sweeps with a Langevin sweep every "
                          "4th step; plain: Langevin sweeps only")
+    ap.add_argument("--drift", default="exact", choices=["exact", "first"],
+                    help="Langevin drift: exact grad S, or the first-order drift (factors "
+                         "treated as commuting; same target, no derivative chain)")
     ap.add_argument("--beta", type=float, default=BETA,
                     help="override beta (shorter imaginary-time axis, same kernels and matrix "
                          "sizes; used for profiler launch lists)")

@@ -36,6 +36,14 @@ typedef struct qmc_ctx qmc_ctx;
 
 enum { QMC_TORUS = 0, QMC_SPHERE = 1 };
 
+/* Drift of the Langevin proposal (qmc_opts.drift).  EXACT: grad S of the
+ * seven-factor slice, with the derivative of every exponential factor
+ * (Methods, Eq. action_gradient).  FIRST: the first-order drift, each
+ * factor's derivative taken as Tr[(1 - G) dX_j], as if the factors
+ * commuted; it differs from the exact drift at O(dtau) and the chain stays
+ * exact because the MH test evaluates both proposal densities with it. */
+enum { QMC_DRIFT_EXACT = 0, QMC_DRIFT_FIRST = 1 };
+
 enum {
     QMC_OK = 0,
     QMC_ERR_ARG = -1,       /* invalid argument or unsupported size */
@@ -91,6 +99,7 @@ typedef struct {
     double stab_tol;       /* QMC_ERR_UNSTABLE threshold (default 1e-6) */
     double sign_tol;       /* QMC_ERR_SIGN threshold on accepted updates (default 1e-6);
                               record column 16 is the maximum over all updates */
+    int drift;             /* QMC_DRIFT_EXACT (default) or QMC_DRIFT_FIRST */
 } qmc_opts;
 
 /* Fill *o with the defaults listed above. */

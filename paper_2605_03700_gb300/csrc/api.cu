@@ -176,10 +176,11 @@ static void build_B(qmc_ctx *ctx, const cd *V, const cd *T, const cd *Dg, const 
     }
 }
 
-// exact grad S of one slice (Methods, Eq. action_gradient): chain of the
+// grad S of one slice (Methods, Eq. action_gradient).  Exact: chain of the
 // matrices A_j = P_j^-1 (1 - G) P_j in the eigenbases of the seven factors,
 // Daleckii-Krein weights, back-transform per channel, traces with F_q;
-// computed in the gradient compute type from the FP64 V, T and G
+// computed in the gradient compute type from the FP64 V, T and G.
+// QMC_DRIFT_FIRST: traces of alpha_i (1 - G) alone (no chain)
 static void gradient(qmc_ctx *ctx, const cd *Gm, const cd *V, const cd *T, const void *lam,
                      const void *Dg, const void *Dgi, const double *phi, long long phi_cs,
                      double *grad)
@@ -187,6 +188,12 @@ static void gradient(qmc_ctx *ctx, const cd *Gm, const cd *V, const cd *T, const
     const int nb = ctx->nb, N = ctx->N, gp = ctx->gp;
     const long long NN = ctx->NN;
     cudaStream_t s = ctx->st;
+    if (ctx->o.drift == QMC_DRIFT_FIRST) {
+        launch_first_drift(s, gp, nb, N, Gm, ctx->alpha_d, ctx->At);
+        launch_trace_grad(s, gp, nb, ctx->n, ctx->nq, ctx->At, ctx->ff_val, ctx->ff_col, ctx->trF,
+                          ctx->alpha_d, ctx->tq, ctx->fq, ctx->fk, ctx->partner, phi, phi_cs, grad);
+        return;
+    }
     // Ah = I - V0^H G V0
     gemm_sq(s, N, nb, gp, op64(V, 4 * NN), 2, op64(Gm, NN), 0, ctx->Gx(ctx->Y1, NN));
     gemm_sq(s, N, nb, gp, ctx->Gx(ctx->Y1, NN), 0, op64(V, 4 * NN), 0, ctx->Gx(ctx->Ah, NN),
@@ -892,7 +899,8 @@ int qmc_create(qmc_ctx **out, int geometry, int N_phi, double beta, double dtau,
         ctx->err = "beta and dtau must be positive";
         code = QMC_ERR_ARG;
     } else if (ctx->o.n_chains < 1 || ctx->o.n_stab < 1 || ctx->o.series_capacity < 1 ||
-               ctx->o.trace_capacity < 0 || ctx->o.precision < 0 || ctx->o.precision > 1) {
+               ctx->o.trace_capacity < 0 || ctx->o.precision < 0 || ctx->o.precision > 1 ||
+               (ctx->o.drift != QMC_DRIFT_EXACT && ctx->o.drift != QMC_DRIFT_FIRST)) {
         ctx->err = "invalid options";
         code = QMC_ERR_ARG;
     } else {

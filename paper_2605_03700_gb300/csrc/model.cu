@@ -302,6 +302,22 @@ __global__ void k_accum(int N, int j, int first, const cd *alpha, const void *la
     *dst = first ? v : cadd(*dst, v);
 }
 
+// First-order drift: Atilde^(i) = alpha_i (1 - G) for every channel (each
+// factor's derivative Tr[(1 - G) dX_j]; the coefficients c_j of a channel's
+// factors sum to one); grid (N^2 / 256, 4 channels, chains)
+template <class R>
+__global__ void k_first_drift(int N, const cd *G, const cd *alpha, void *Atv)
+{
+    typedef typename Cx<R>::T C;
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = blockIdx.y, c = blockIdx.z;
+    if (e >= N * N) return;
+    cd g = G[(long long)c * N * N + e];
+    cd v = cmk(-g.x, -g.y);
+    if (e / N == e % N) v.x += 1.0;
+    ((C *)Atv)[((long long)c * 4 + i) * N * N + e] = cvt<C>(cmul(alpha[c * 4 + i], v));
+}
+
 // t^(i)_q = Tr[(O^i (x) F_q) Atilde^(i)] - delta_{i0} alpha_0 Tr F_q
 // (accumulated in FP64)
 template <class R>
@@ -779,6 +795,14 @@ void launch_accum(cudaStream_t s, int prec, int nb, int N, int j, int first, con
     dim3 g(cdiv_up(N * N, 256), nb);
     if (prec == TY_C64) k_accum<double><<<g, 256, 0, s>>>(N, j, first, alpha, lam, Ah, Cacc);
     else k_accum<float><<<g, 256, 0, s>>>(N, j, first, alpha, lam, Ah, Cacc);
+    QMC_COUNT(1);
+}
+void launch_first_drift(cudaStream_t s, int prec, int nb, int N, const cd *G, const cd *alpha,
+                        void *At)
+{
+    dim3 g(cdiv_up(N * N, 256), 4, nb);
+    if (prec == TY_C64) k_first_drift<double><<<g, 256, 0, s>>>(N, G, alpha, At);
+    else k_first_drift<float><<<g, 256, 0, s>>>(N, G, alpha, At);
     QMC_COUNT(1);
 }
 void launch_trace_grad(cudaStream_t s, int prec, int nb, int n, int nq, const void *At,

@@ -67,6 +67,8 @@ void launch_lambda(cudaStream_t s, int prec, int nb, int n, const void *w, long 
                    const cd *alpha, void *lam, void *Dg, void *Dgi);
 void launch_accum(cudaStream_t s, int prec, int nb, int N, int j, int first, const cd *alpha,
                   const void *lam, const void *Ah, void *Cacc);
+void launch_first_drift(cudaStream_t s, int prec, int nb, int N, const cd *G, const cd *alpha,
+                        void *At);
 void launch_trace_grad(cudaStream_t s, int prec, int nb, int n, int nq, const void *At,
                        const cd *val, const int *col, const cd *trF, const cd *alpha, cd *t,
                        const int *fq, const int *fk, const int *partner, const double *phi,

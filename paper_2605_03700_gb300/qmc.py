@@ -19,6 +19,7 @@ QMC_TORUS = 0
 QMC_SPHERE = 1
 QMC_NOBS = 20
 QMC_NTRACE = 8
+QMC_DRIFT_EXACT, QMC_DRIFT_FIRST = 0, 1
 OBS_NAMES = ["m2", "S1_0", "S2_0", "S3_0", "S4_0", "S5_0", "S1_dq", "S2_dq",
              "S3_dq", "S4_dq", "S5_dq", "R", "E", "acc", "eps", "stab_err",
              "sign_dev", "n_acc", "_", "_"]
@@ -41,6 +42,7 @@ class qmc_opts(C.Structure):
         ("trace_capacity", C.c_int),
         ("stab_tol", C.c_double),
         ("sign_tol", C.c_double),
+        ("drift", C.c_int),
     ]
 
 
@@ -166,9 +168,10 @@ class Chain:
                  n_chains=1, couplings=None, anisotropies=None, seeds=None, n_stab=10,
                  eps0=0.5, deps=0.1, r0=0.574, n_adapt=-1, series_capacity=4096,
                  trace_capacity=0, stab_tol=1e-6, sign_tol=1e-6, precision=0, n_orb_sphere=0,
-                 stream=None):
+                 drift=0, stream=None):
         o = qmc_default_opts()
         o.n_stab = n_stab
+        o.drift = drift
         o.n_orb_sphere = n_orb_sphere
         o.precision = precision
         o.eps0, o.deps, o.r0, o.n_adapt = eps0, deps, r0, n_adapt

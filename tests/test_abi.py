@@ -90,3 +90,26 @@ def test_new_entry_points_reject_invalid_arguments_before_device_work(lib):
     # sphere beyond 56 orbitals
     o = qmc.qmc_default_opts()
     assert L.qmc_create(C.byref(h), 1, 56, 1.0, 0.1, 1.0, 0.0, 0, C.byref(o)) == -1
+
+
+def test_opts_struct_matches_the_library(lib):
+    """qmc_default_opts writes exactly the binding's qmc_opts: nothing past
+    its end (a larger C struct would overrun the caller's buffer), and its
+    last field holds the default."""
+    from paper_2605_03700_gb300 import qmc
+    n = C.sizeof(qmc.qmc_opts)
+    buf = (C.c_ubyte * (n + 64))(*([0xA5] * (n + 64)))
+    assert lib.qmc_default_opts(C.cast(buf, C.POINTER(qmc.qmc_opts))) == 0
+    assert all(b == 0xA5 for b in bytes(buf)[n:])
+    o = qmc.qmc_opts.from_buffer(buf)
+    assert o.n_stab == 10 and o.sign_tol == 1e-6 and o.drift == qmc.QMC_DRIFT_EXACT
+    assert qmc.qmc_opts.drift.offset + C.sizeof(C.c_int) <= n
+
+
+def test_unknown_drift_is_rejected(lib):
+    from paper_2605_03700_gb300 import qmc
+    h = C.c_void_p()
+    o = qmc.qmc_default_opts()
+    o.drift = 2
+    assert lib.qmc_create(C.byref(h), 0, 4, 1.0, 0.1, 1.0, 0.0, 0, C.byref(o)) == -1
+    assert not h.value
