@@ -243,6 +243,21 @@ int qmc_measure(qmc_ctx *ctx, double *host_out);
 int qmc_get_series(qmc_ctx *ctx, int count, double *host_out);
 int qmc_series_length(const qmc_ctx *ctx);
 
+/* Time-displaced SO(5) structure factors of the current configuration of
+ * every chain (Supplementary Note 2; Wick's theorem with Methods, Eq.
+ * green_function): host_out[c][k][i] = S^{i+1}_{q=0}(tau_k) =
+ * <n^{Gamma^{i+1}}_0(tau_k) n^{Gamma^{i+1}}_0(0)> for chain c, tau_k =
+ * taus[k] slices after the time origin at slice 0, i = 0..4 (one spin
+ * block's Wick contractions, as the equal-time record: at tau = 0 these are
+ * record columns 1..5).  G(t,0), Gbar(0,t) and G(t,t) are formed in the
+ * stable UDV form at t = 0 and at every stabilisation point and carried
+ * across the slices between by the stored propagators.  taus: host,
+ * ascending, each in [0, L]; host_out: n_chains * ntau * 5 doubles, caller
+ * owned.  Allocates and frees its own device scratch (6 N^2 complex per
+ * chain); synchronous; overwrites no chain state.  QMC_ERR_ARG for bad
+ * taus or sizes. */
+int qmc_measure_tau(qmc_ctx *ctx, int ntau, const int *taus, double *host_out);
+
 /* Enqueue, without synchronising, the copy of the newest observable record
  * of every chain to host_out[n_chains * QMC_NOBS] (pinned host memory for an
  * asynchronous copy); the data are valid after the next qmc_sync. */

@@ -1609,7 +1609,10 @@ void orc_green_tau(const orc_t *o, int t, double *Gt0, double *Gb0t, double *Gtt
  *   i = 1, 2: 4 a_q(t) a_qbar(0) + 2 x(t),  i = 3, 4, 5: 2 x_z(t),
  *   a_q(t) = Tr[(O (x) F_q)(1 - G(t,t))], x(t) = Tr[M_q G(t,0) M_qbar Gbar(0,t)];
  * at t = 0 these are the equal-time S^i_0 (obs[1..5] of measure()). */
-void orc_measure_tau(const orc_t *o, int ntau, const int *taus, double *out)
+void orc_green_tau_stable(const orc_t *o, int t, double *Gt0_out, double *Gb0t_out,
+                          double *Gtt_out);
+
+static void measure_tau(const orc_t *o, int ntau, const int *taus, double *out, int stable)
 {
     int N = o->N;
     size_t nn = (size_t)N * N;
@@ -1621,7 +1624,18 @@ void orc_measure_tau(const orc_t *o, int ntau, const int *taus, double *out)
     for (int x = 0; x < N; ++x) Gc0[x * N + x] += 1.0;
     for (int k = 0; k < ntau; ++k) {
         int t = taus[k];
-        green_tau(o, t, Gt0, Gb, Gtt);
+        if (stable) {
+            double *d = (double *)malloc(sizeof(double) * 6 * nn);
+            orc_green_tau_stable(o, t, d, d + 2 * nn, d + 4 * nn);
+            for (size_t x = 0; x < nn; ++x) {
+                Gt0[x] = d[2 * x] + I * d[2 * x + 1];
+                Gb[x] = d[2 * nn + 2 * x] + I * d[2 * nn + 2 * x + 1];
+                Gtt[x] = d[4 * nn + 2 * x] + I * d[4 * nn + 2 * x + 1];
+            }
+            free(d);
+        } else {
+            green_tau(o, t, Gt0, Gb, Gtt);
+        }
         for (size_t x = 0; x < nn; ++x) Gc[x] = -Gtt[x];
         for (int x = 0; x < N; ++x) Gc[x * N + x] += 1.0;
         for (int v = 1; v <= 2; ++v) {
@@ -1633,6 +1647,17 @@ void orc_measure_tau(const orc_t *o, int ntau, const int *taus, double *out)
         out[k * 5 + 2] = out[k * 5 + 3] = out[k * 5 + 4] = creal(2.0 * xz);
     }
     free(Gt0); free(Gb); free(Gtt); free(Gc); free(Gc0);
+}
+
+void orc_measure_tau(const orc_t *o, int ntau, const int *taus, double *out)
+{
+    measure_tau(o, ntau, taus, out, 0);
+}
+
+/* the same with G(t,0), Gbar(0,t), G(t,t) in the stable UDV form (any beta) */
+void orc_measure_tau_stable(const orc_t *o, int ntau, const int *taus, double *out)
+{
+    measure_tau(o, ntau, taus, out, 1);
 }
 
 /* UDV of B(t,0) = Q D W (right) and of B(b,t)^H = Q D W (left) for the

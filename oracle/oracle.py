@@ -54,6 +54,7 @@ def lib():
         L.orc_green_tau.argtypes = [C.c_void_p, C.c_int, dp, dp, dp]
         L.orc_green_tau_stable.argtypes = [C.c_void_p, C.c_int, dp, dp, dp]
         L.orc_measure_tau.argtypes = [C.c_void_p, C.c_int, ip, dp]
+        L.orc_measure_tau_stable.argtypes = [C.c_void_p, C.c_int, ip, dp]
         L.orc_measure.argtypes = [C.c_void_p, dp]
         L.orc_set_measure_q.argtypes = [C.c_void_p, C.c_int, ip, C.c_int]
         L.orc_set_trace.argtypes = [C.c_void_p, dp, C.c_long]
@@ -230,12 +231,14 @@ class Chain:
         lib().orc_green_tau_stable(self.h, int(t), *[_dp(a.view(float)) for a in out])
         return tuple(out)
 
-    def measure_tau(self, taus):
+    def measure_tau(self, taus, stable=False):
         """S^i_{q=0}(tau) for i = 1..5 at slice offsets taus (time origin 0):
-        array (len(taus), 5)."""
+        array (len(taus), 5); from plain propagation (small beta) or, with
+        stable=True, from the stable UDV form of the Green's functions."""
         t = np.ascontiguousarray(taus, dtype=np.int32)
         out = np.zeros((len(t), 5))
-        lib().orc_measure_tau(self.h, len(t), _ip(t), _dp(out))
+        f = lib().orc_measure_tau_stable if stable else lib().orc_measure_tau
+        f(self.h, len(t), _ip(t), _dp(out))
         return out
 
     def measure(self):

@@ -445,6 +445,74 @@ static int restabilise(qmc_ctx *ctx, int k, int prev, int t)
     return 0;
 }
 
+// ---------------------------------------------- time-displaced G ------
+// scratch of qmc_measure_tau, per chain: six N x N matrices and two
+// complex diagonals, all in one allocation of its own
+struct TauWork {
+    cd *Gt0, *Gb0t, *Gtt, *G00, *Y, *T, *dsL, *dsR;
+};
+
+// right UDV B(t,0) = RQ RD RW advanced from slice prev to slice t (the first
+// half of restabilise)
+static int advance_right_udv(qmc_ctx *ctx, int prev, int t)
+{
+    const int nb = ctx->nb, N = ctx->N;
+    const long long NN = ctx->NN, BL = (long long)ctx->L * NN;
+    cudaStream_t s = ctx->st;
+    launch_scale_cols(s, nb, N, ctx->RQ, NN, ctx->RD, N, ctx->X1, NN);
+    cd *a = ctx->X1, *b = ctx->X2;
+    for (int u = prev + 1; u <= t; ++u) {
+        gemm_sq(s, N, nb, TY_C64, op64(ctx->B + (long long)(u - 1) * NN, BL), 0, op64(a, NN), 0,
+                op64(b, NN));
+        std::swap(a, b);
+    }
+    if (qrp_batched(s, N, a, NN, ctx->Qt, NN, ctx->Dt, N, ctx->Vt, NN, nb)) return QMC_ERR_ARG;
+    gemm_sq(s, N, nb, TY_C64, op64(ctx->Vt, NN), 0, op64(ctx->RW, NN), 0, op64(ctx->X1, NN));
+    std::swap(ctx->RW, ctx->X1);
+    std::swap(ctx->RQ, ctx->Qt);
+    std::swap(ctx->RD, ctx->Dt);
+    return 0;
+}
+
+// G(t,t), G(t,0), Gbar(0,t) in the stable form, from the right UDV in
+// RQ, RD, RW and the left one B(beta,t)^H = QL DL WL; with D = D_big D_small
+// and J = DbR^-1 QR^H QL DbL^-1 + DsR WR WL^H DsL (as green_from_udv):
+//   G(t,t)    = QL DbL^-1 J^-1 DbR^-1 QR^H,
+//   G(t,0)    = [B(t,0)^-1 + B(beta,t)]^-1 = QL DbL^-1 J^-1 DsR WR,
+//   Gbar(0,t) = [B(t,0) + B(beta,t)^-1]^-1 = WL^H DsL J^-1 DbR^-1 QR^H
+static int green_tau_from_udv(qmc_ctx *ctx, const cd *QL, const double *DL, const cd *WL,
+                              long long L_cs, long long LD_cs, TauWork &w)
+{
+    const int nb = ctx->nb, N = ctx->N;
+    const long long NN = ctx->NN;
+    cudaStream_t s = ctx->st;
+    const cd *QR = ctx->RQ, *WR = ctx->RW;
+    const double *DR = ctx->RD;
+    gemm_sq(s, N, nb, TY_C64, op64(QR, NN), 2, op64(QL, L_cs), 0, op64(ctx->X1, NN));
+    gemm_sq(s, N, nb, TY_C64, op64(WR, NN), 0, op64(WL, L_cs), 2, op64(ctx->X2, NN));
+    launch_stab_mix(s, nb, N, ctx->X1, ctx->X2, DR, N, DL, LD_cs, ctx->M);
+    if (lu_batched(s, N, ctx->M, NN, ctx->piv, N, nullptr, nb)) return QMC_ERR_ARG;
+    launch_inv_big(s, nb, N, DL, LD_cs, ctx->dinvL);
+    launch_inv_big(s, nb, N, DR, N, ctx->dinvR);
+    launch_small_part(s, nb, N, DL, LD_cs, w.dsL);
+    launch_small_part(s, nb, N, DR, N, w.dsR);
+    // X2 = QL DbL^-1 J^-1
+    gemm_sq(s, N, nb, TY_C64, op64(QL, L_cs), 0, op64(ctx->Eye, NN), 0, op64(ctx->X1, NN),
+            ctx->dinvL, N);
+    if (rdiv_batched(s, TY_C64, N, ctx->X1, NN, ctx->M, NN, ctx->piv, N, ctx->X2, NN, nb))
+        return QMC_ERR_ARG;
+    gemm_sq(s, N, nb, TY_C64, op64(ctx->X2, NN), 0, op64(QR, NN), 2, op64(w.Gtt, NN), ctx->dinvR,
+            N);
+    gemm_sq(s, N, nb, TY_C64, op64(ctx->X2, NN), 0, op64(WR, NN), 0, op64(w.Gt0, NN), w.dsR, N);
+    // X2 = WL^H DsL J^-1
+    gemm_sq(s, N, nb, TY_C64, op64(WL, L_cs), 2, op64(ctx->Eye, NN), 0, op64(w.Y, NN), w.dsL, N);
+    if (rdiv_batched(s, TY_C64, N, w.Y, NN, ctx->M, NN, ctx->piv, N, ctx->X2, NN, nb))
+        return QMC_ERR_ARG;
+    gemm_sq(s, N, nb, TY_C64, op64(ctx->X2, NN), 0, op64(QR, NN), 2, op64(w.Gb0t, NN),
+            ctx->dinvR, N);
+    return 0;
+}
+
 // the measurement record of every chain: at out + c * out_cs, or, with the
 // device counters, in slot ctr[QMC_CTR_SERIES] % slots of that ring
 static void measure_into(qmc_ctx *ctx, double *out, long long out_cs,
@@ -1189,6 +1257,102 @@ int qmc_measure(qmc_ctx *ctx, double *host_out)
     CK(cudaMemcpyAsync(host_out, ctx->gradp, sizeof(double) * ctx->nb * QMC_NOBS,
                        cudaMemcpyDeviceToHost, ctx->st));
     return qmc_sync(ctx);
+}
+
+// S^i_{q=0}(tau) of the current configuration of every chain (Supplementary
+// Note 2): stable G(t,0), Gbar(0,t), G(t,t) at t = 0 and at every
+// stabilisation point, propagated one slice at a time in between,
+// measured at the requested slices
+static int measure_tau_impl(qmc_ctx *ctx, int ntau, const int *taus, double *dout, TauWork &w)
+{
+    const int nb = ctx->nb, N = ctx->N, nsp = (int)ctx->sp.size();
+    const long long NN = ctx->NN, BL = (long long)ctx->L * NN;
+    const long long Ls = (long long)(nsp + 1) * NN, LDs = (long long)(nsp + 1) * N;
+    cudaStream_t s = ctx->st;
+    int r = build_left_stack(ctx);
+    if (r) return r;
+    reset_right_stack(ctx);
+    // t = 0: the left UDV of B(beta,0) sits at index nsp
+    r = green_tau_from_udv(ctx, ctx->LQ + nsp * NN, ctx->LD + nsp * N, ctx->LW + nsp * NN, Ls, LDs,
+                           w);
+    if (r) return r;
+    CK(cudaMemcpyAsync(w.G00, w.Gtt, sizeof(cd) * NN * nb, cudaMemcpyDeviceToDevice, s));
+    const int tmax = taus[ntau - 1];
+    int k = 0, next = 0, prev = 0;
+    for (int t = 0; t <= tmax; ++t) {
+        if (t > 0) {
+            if (t == ctx->sp[k]) {
+                r = advance_right_udv(ctx, prev, t);
+                if (r) return r;
+                r = green_tau_from_udv(ctx, ctx->LQ + k * NN, ctx->LD + k * N, ctx->LW + k * NN,
+                                       Ls, LDs, w);
+                if (r) return r;
+                prev = t;
+                ++k;
+            } else {
+                const cd *Bt = ctx->B + (long long)(t - 1) * NN;
+                const cd *Bi = ctx->Binv + (long long)(t - 1) * NN;
+                // G(t,0) = B_t G(t-1,0), Gbar(0,t) = Gbar(0,t-1) B_t^-1,
+                // G(t,t) = B_t G(t-1,t-1) B_t^-1 (w.T: scratch of this call)
+                gemm_sq(s, N, nb, TY_C64, op64(Bt, BL), 0, op64(w.Gt0, NN), 0, op64(w.T, NN));
+                std::swap(w.Gt0, w.T);
+                gemm_sq(s, N, nb, TY_C64, op64(w.Gb0t, NN), 0, op64(Bi, BL), 0, op64(w.T, NN));
+                std::swap(w.Gb0t, w.T);
+                gemm_sq(s, N, nb, TY_C64, op64(Bt, BL), 0, op64(w.Gtt, NN), 0, op64(w.T, NN));
+                gemm_sq(s, N, nb, TY_C64, op64(w.T, NN), 0, op64(Bi, BL), 0, op64(w.Gtt, NN));
+            }
+        }
+        while (next < ntau && taus[next] == t) {
+            launch_meas_tau(s, nb, ctx->n, ctx->q0, w.Gt0, w.Gb0t, w.Gtt, w.G00, ctx->ff_val,
+                            ctx->ff_col, ctx->partner, dout + (long long)next * 5,
+                            (long long)ntau * 5);
+            ++next;
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        ctx->err = std::string("kernel launch: ") + cudaGetErrorString(e);
+        return QMC_ERR_CUDA;
+    }
+    return 0;
+}
+
+int qmc_measure_tau(qmc_ctx *ctx, int ntau, const int *taus, double *host_out)
+{
+    if (!ctx || ntau < 1 || !taus || !host_out) return QMC_ERR_ARG;
+    for (int k = 0; k < ntau; ++k)
+        if (taus[k] < 0 || taus[k] > ctx->L || (k > 0 && taus[k] < taus[k - 1])) {
+            ctx->err = "taus must be ascending slice offsets in [0, L]";
+            return QMC_ERR_ARG;
+        }
+    const int nb = ctx->nb, N = ctx->N;
+    const size_t mat = sizeof(cd) * (size_t)ctx->NN * nb, vec = sizeof(cd) * (size_t)N * nb;
+    const size_t outb = sizeof(double) * (size_t)nb * ntau * 5;
+    void *buf = nullptr;
+    CK(cudaMalloc(&buf, 6 * mat + 2 * vec + outb));
+    char *p = (char *)buf;
+    TauWork w;
+    w.Gt0 = (cd *)p;
+    w.Gb0t = (cd *)(p + mat);
+    w.Gtt = (cd *)(p + 2 * mat);
+    w.G00 = (cd *)(p + 3 * mat);
+    w.Y = (cd *)(p + 4 * mat);
+    w.T = (cd *)(p + 5 * mat);
+    w.dsL = (cd *)(p + 6 * mat);
+    w.dsR = (cd *)(p + 6 * mat + vec);
+    double *dout = (double *)(p + 6 * mat + 2 * vec);
+    int r = measure_tau_impl(ctx, ntau, taus, dout, w);
+    cudaError_t e = cudaSuccess;
+    if (!r) e = cudaMemcpyAsync(host_out, dout, outb, cudaMemcpyDeviceToHost, ctx->st);
+    cudaError_t e2 = cudaStreamSynchronize(ctx->st);
+    cudaFree(buf);
+    if (r) return r;
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        ctx->err = std::string("qmc_measure_tau: ") +
+                   cudaGetErrorString(e != cudaSuccess ? e : e2);
+        return QMC_ERR_CUDA;
+    }
+    return QMC_OK;
 }
 
 int qmc_copy_latest_async(qmc_ctx *ctx, double *host_out)

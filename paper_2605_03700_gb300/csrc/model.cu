@@ -653,6 +653,96 @@ __global__ void __launch_bounds__(256) k_meas_ax(int n, int nq, const cd *G, con
     }
 }
 
+// Time-displaced structure factors at q (the ordering momentum q = 0) for one
+// tau (Supplementary Note 2), by Wick's theorem for one spin block with the
+// conventions of k_meas_ax:
+//   v = 1, 2:   S^v(t) = Re[4 a_v(t) abar_v(0) + 2 x_v(t)],
+//   v = 3..5:   S^v(t) = Re[2 x_3(t)],
+//   a_v(t)    = Tr[(O^v (x) F_q)(1 - G(t,t))],
+//   abar_v(0) = Tr[(O^v (x) F_qbar)(1 - G(0,0))],
+//   x_v(t)    = Tr[(O^v (x) F_q) G(t,0) (O^v (x) F_qbar) Gbar(0,t)].
+// Grid (3 channels v = 1..3, chains); out[c * out_cs + 0..4].
+__global__ void __launch_bounds__(256) k_meas_tau(int n, int q, const cd *Gt0, const cd *Gb0t,
+                                                  const cd *Gtt, const cd *G00, const cd *val,
+                                                  const int *col, const int *partner, double *out,
+                                                  long long out_cs)
+{
+    __shared__ double sh[32];
+    const int i = blockIdx.x + 1, c = blockIdx.y, tid = threadIdx.x;
+    const int N = 2 * n;
+    const long long NN = (long long)N * N;
+    const cd *A = Gt0 + c * NN, *Bm = Gb0t + c * NN, *T = Gtt + c * NN, *Z = G00 + c * NN;
+    const int qb = partner[q];
+    double ar = 0, ai = 0, br = 0, bi = 0, xr = 0, xi = 0;
+    for (int x = tid; x < N; x += blockDim.x) {
+        int v = x / n, k = x % n;
+        int w = (i == 1 || i == 2) ? 1 - v : v;
+        int cc = col[q * n + k];
+        if (cc >= 0) {
+            int px = w * n + cc;
+            cd m = cmul(valley_O(i, v, w), val[q * n + k]);
+            cd g = T[(long long)px * N + x];
+            cd t = cmul(m, cmk((px == x ? 1.0 : 0.0) - g.x, -g.y));
+            ar += t.x;
+            ai += t.y;
+        }
+        int cb = col[qb * n + k];
+        if (cb >= 0) {
+            int pb = w * n + cb;
+            cd m = cmul(valley_O(i, v, w), val[qb * n + k]);
+            cd g = Z[(long long)pb * N + x];
+            cd t = cmul(m, cmk((pb == x ? 1.0 : 0.0) - g.x, -g.y));
+            br += t.x;
+            bi += t.y;
+        }
+    }
+    for (int t = tid; t < N * N; t += blockDim.x) {
+        int x = t / N, y = t % N;
+        int v = x / n, k = x % n;
+        int w = (i == 1 || i == 2) ? 1 - v : v;
+        int cc = col[q * n + k];
+        if (cc < 0) continue;
+        int px = w * n + cc;
+        int v2 = y / n, k2 = y % n;
+        int w2 = (i == 1 || i == 2) ? 1 - v2 : v2;
+        int cc2 = col[qb * n + k2];
+        if (cc2 < 0) continue;
+        int py = w2 * n + cc2;
+        cd m1 = cmul(valley_O(i, v, w), val[q * n + k]);
+        cd m2 = cmul(valley_O(i, v2, w2), val[qb * n + k2]);
+        cd r = cmul(cmul(m1, A[(long long)px * N + y]), cmul(m2, Bm[(long long)py * N + x]));
+        xr += r.x;
+        xi += r.y;
+    }
+    ar = block_sum(ar, sh);
+    ai = block_sum(ai, sh);
+    br = block_sum(br, sh);
+    bi = block_sum(bi, sh);
+    xr = block_sum(xr, sh);
+    xi = block_sum(xi, sh);
+    if (tid == 0) {
+        double *o = out + (long long)c * out_cs;
+        if (i < 3) {
+            o[i - 1] = 4.0 * (ar * br - ai * bi) + 2.0 * xr;
+        } else {
+            o[2] = 2.0 * xr;
+            o[3] = 2.0 * xr;
+            o[4] = 2.0 * xr;
+        }
+    }
+}
+
+// D_small = min(D, 1) of the UDV split D = D_big D_small, as a complex
+// diagonal
+__global__ void k_small_part(int N, const double *D, long long sD, cd *out)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int c = blockIdx.y;
+    if (x >= N) return;
+    double d = D[(long long)c * sD + x];
+    out[(long long)c * N + x] = cmk(d < 1 ? d : 1.0, 0.0);
+}
+
 // per chain: S^i_q for Gamma^1..5, m^2_SO(5), correlation ratio, energy
 __global__ void __launch_bounds__(256) k_meas_final(MeasP p)
 {
@@ -880,6 +970,19 @@ void launch_measure(cudaStream_t s, int nb, int n, int nq, const cd *G, const cd
     k_meas_ax<<<dim3(nq, 4, nb), 256, 0, s>>>(n, nq, G, val, col, partner, ax);
     k_meas_final<<<nb, 256, 0, s>>>(p);
     QMC_COUNT(2);
+}
+void launch_meas_tau(cudaStream_t s, int nb, int n, int q, const cd *Gt0, const cd *Gb0t,
+                     const cd *Gtt, const cd *G00, const cd *val, const int *col,
+                     const int *partner, double *out, long long out_cs)
+{
+    k_meas_tau<<<dim3(3, nb), 256, 0, s>>>(n, q, Gt0, Gb0t, Gtt, G00, val, col, partner, out,
+                                           out_cs);
+    QMC_COUNT(1);
+}
+void launch_small_part(cudaStream_t s, int nb, int N, const double *D, long long sD, cd *out)
+{
+    k_small_part<<<dim3(cdiv_up(N, 128), nb), 128, 0, s>>>(N, D, sD, out);
+    QMC_COUNT(1);
 }
 void launch_end_sweep(cudaStream_t s, int nb, int L, int n_adapt, uint32_t *ctr, double r0,
                       double deps, double *eps, double *eps_used, double *st)

@@ -85,6 +85,10 @@ void launch_scale_cols(cudaStream_t s, int nb, int N, const cd *X, long long sX,
 void launch_stab_mix(cudaStream_t s, int nb, int N, const cd *T1, const cd *T2, const double *DR,
                      long long sDR, const double *DL, long long sDL, cd *X);
 void launch_inv_big(cudaStream_t s, int nb, int N, const double *D, long long sD, cd *out);
+void launch_small_part(cudaStream_t s, int nb, int N, const double *D, long long sD, cd *out);
+void launch_meas_tau(cudaStream_t s, int nb, int n, int q, const cd *Gt0, const cd *Gb0t,
+                     const cd *Gtt, const cd *G00, const cd *val, const int *col,
+                     const int *partner, double *out, long long out_cs);
 void launch_stab_err(cudaStream_t s, int nb, int N, cd *G, const cd *Gs, double *st, int *errf,
                      double tol);
 void launch_measure(cudaStream_t s, int nb, int n, int nq, const cd *G, const cd *val,

@@ -61,6 +61,7 @@ def lib():
             raise QMCError(f"{LIB} is missing: run paper_2605_03700_gb300.build.build() first")
         L = C.CDLL(LIB)
         vp, dp = C.c_void_p, C.POINTER(C.c_double)
+        L.qmc_measure_tau.argtypes = [vp, C.c_int, C.POINTER(C.c_int), dp]
         L.qmc_default_opts.argtypes = [C.POINTER(qmc_opts)]
         L.qmc_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.c_double, C.c_double,
                                  C.c_double, C.c_double, C.c_uint64, C.POINTER(qmc_opts)]
@@ -235,6 +236,16 @@ class Chain:
     def measure(self):
         out = np.zeros((self.n_chains, QMC_NOBS))
         _check(lib().qmc_measure(self.h, _dp(out)), self.h)
+        return out
+
+    def measure_tau(self, taus):
+        """S^i_{q=0}(tau) of the current configuration, i = 1..5, at the
+        ascending slice offsets taus from the time origin: array
+        (n_chains, len(taus), 5) (qmc_measure_tau)."""
+        t = np.ascontiguousarray(taus, dtype=np.int32)
+        out = np.zeros((self.n_chains, len(t), 5))
+        _check(lib().qmc_measure_tau(self.h, len(t), t.ctypes.data_as(C.POINTER(C.c_int)),
+                                     _dp(out)), self.h)
         return out
 
     def series(self, count=None):

@@ -124,3 +124,20 @@ def test_stable_form_at_large_beta():
     assert np.abs(cur[2] - B @ prev[2] @ Bi).max() < 1e-9
     # all three are O(1): Green's functions, however large B(t,0) is
     assert max(np.abs(m).max() for m in cur) < 10
+
+
+def test_stable_structure_factors():
+    """S^i_0(tau) from the stable Green's functions equals the plain
+    propagation at beta = 1, and at beta = 10 starts at the equal-time
+    record and is periodic, S(beta) = S(0)."""
+    ch = _chain(beta=1.0)
+    taus = [0, 1, 4, 5, 7, 10]
+    a, b = ch.measure_tau(taus), ch.measure_tau(taus, stable=True)
+    assert np.abs(a - b).max() < 1e-12 * np.abs(a).max()
+    ch = O.Chain(M.TORUS, 2, 10.0, 0.1, 2.0, 0.2, 3, n_stab=5)
+    ch.sweep(3)
+    S = ch.measure_tau([0, 37, ch.L], stable=True)
+    eq = ch.measure()[1:6]
+    assert np.abs(S[0] - eq).max() < 1e-10 * np.abs(eq).max()
+    assert np.abs(S[2] - S[0]).max() < 1e-9 * np.abs(eq).max()
+    assert np.all(S[1, 2:] < S[0, 2:])
