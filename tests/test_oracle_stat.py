@@ -110,3 +110,22 @@ def test_so5_multiplet_is_exact_up_to_the_momentum_cutoff(monkeypatch):
     ed = E.ED(m, M.couplings(15.0, 0.0), 20.0)
     g = [ed.gap(i, m.q0()) for i in range(5)]
     assert max(g) - min(g) < 1e-12 * g[0]
+
+
+def test_monte_carlo_matches_exact_diagonalisation_at_nphi3():
+    """Torus N_phi = 3 (a 4096-state Fock space), u = 4, alpha = 0.3,
+    beta = 2, dtau = 0.05: E, S^1_0, S^3_0 and the Delta q structure factors
+    within 4 sigma of ED (the Trotter bias at this dtau is ~0.3 sigma)."""
+    m = M.Model(M.TORUS, 3)
+    ed = E.ED(m, M.couplings(4.0, 0.3), 2.0)
+    q0, dq = m.q0(), m.delta_q()
+    ref = {12: ed.energy(), 1: ed.structure_factor(0, q0), 3: ed.structure_factor(2, q0),
+           6: np.mean([ed.structure_factor(0, q) for q in dq]),
+           8: np.mean([ed.structure_factor(2, q) for q in dq])}
+    ch = O.Chain(M.TORUS, 3, 2.0, 0.05, 4.0, 0.3, seed=1, n_stab=5, n_adapt=150, model=m)
+    ch.sweep(150)
+    obs = ch.sweep(2500)
+    for col, r in ref.items():
+        mu, err = _mean_err(obs[:, col])
+        assert abs(mu - r) < 4 * err, (col, mu, r, err)
+    assert obs[:, 16].max() < 1e-8
