@@ -243,6 +243,22 @@ int qmc_measure(qmc_ctx *ctx, double *host_out);
 int qmc_get_series(qmc_ctx *ctx, int count, double *host_out);
 int qmc_series_length(const qmc_ctx *ctx);
 
+/* Checkpoint and resume (not in the paper).  The state of a context is
+ * its fields, the Langevin step of every chain and the sweep number; the
+ * random streams (Philox counters) and the step-adaptation schedule follow
+ * from the sweep number.  Layout, doubles: [n_chains][L][4 N_q] fields
+ * (qmc_get_fields' layout per chain), then n_chains steps, then the sweep
+ * number.  qmc_state_size gives the count; qmc_get_state copies it to the
+ * caller's host buffer (synchronising); qmc_set_state loads it into a
+ * context created with the same arguments and options and recomputes the
+ * propagators, the stacks and G from the fields, so the context continues
+ * as the checkpointed one would have.  The observable series restarts
+ * empty.  QMC_ERR_ARG for a short buffer, a non-positive step or a sweep
+ * number that is not a 32-bit count. */
+int qmc_state_size(const qmc_ctx *ctx, size_t *n_doubles);
+int qmc_get_state(qmc_ctx *ctx, double *host_buf, size_t len);
+int qmc_set_state(qmc_ctx *ctx, const double *host_buf, size_t len);
+
 /* Time-displaced SO(5) structure factors of the current configuration of
  * every chain (Supplementary Note 2; Wick's theorem with Methods, Eq.
  * green_function): host_out[c][k][i] = S^{i+1}_{q=0}(tau_k) =

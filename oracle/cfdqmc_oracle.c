@@ -1360,6 +1360,30 @@ double orc_get_eps(const orc_t *o) { return o->eps; }
 void orc_set_eps(orc_t *o, double e) { o->eps = e; }
 unsigned orc_get_sweep(const orc_t *o) { return o->sweep; }
 
+/* Checkpoint (not in the paper): the state a continuation needs is the
+ * fields, the Langevin step and the sweep index (the Philox counters and
+ * the adaptation schedule follow from it); the propagators, the stacks and G
+ * are recomputed from the fields exactly as the sweep computes them.
+ * Layout: L * nf fields, eps, sweep.  Returns the number of doubles. */
+long orc_state_size(const orc_t *o) { return (long)o->L * o->nf + 2; }
+
+void orc_get_state(const orc_t *o, double *out)
+{
+    size_t n = (size_t)o->L * o->nf;
+    memcpy(out, o->phi, sizeof(double) * n);
+    out[n] = o->eps;
+    out[n + 1] = (double)o->sweep;
+}
+
+void orc_set_state(orc_t *o, const double *in)
+{
+    size_t n = (size_t)o->L * o->nf;
+    memcpy(o->phi, in, sizeof(double) * n);
+    o->eps = in[n];
+    o->sweep = (uint32_t)in[n + 1];
+    rebuild(o);
+}
+
 void orc_get_B(const orc_t *o, int t, double *B, double *Binv)
 {
     size_t nn = (size_t)o->N * o->N;

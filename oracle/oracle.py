@@ -74,6 +74,10 @@ def lib():
         L.orc_gradient_at.argtypes = [C.c_void_p, C.c_int, dp]
         L.orc_slice_factors.restype = C.c_int
         L.orc_slice_factors.argtypes = [C.c_void_p, C.c_int, dp, dp]
+        L.orc_state_size.restype = C.c_long
+        L.orc_state_size.argtypes = [C.c_void_p]
+        L.orc_get_state.argtypes = [C.c_void_p, dp]
+        L.orc_set_state.argtypes = [C.c_void_p, dp]
         L.orc_set_variant.restype = C.c_int
         L.orc_set_variant.argtypes = [C.c_void_p, C.c_int, C.c_int]
         L.orc_fields_per_slice.restype = C.c_int
@@ -294,6 +298,19 @@ class Chain:
         Gp = np.zeros((self.N, self.N), complex)
         lib().orc_ratio_at(self.h, t, _dp(phis), _dp(out), _dp(Gp.view(float)))
         return complex(out[0], out[1]), Gp
+
+    def get_state(self):
+        """checkpoint: fields, Langevin step, sweep index (orc_get_state)"""
+        out = np.zeros(lib().orc_state_size(self.h))
+        lib().orc_get_state(self.h, _dp(out))
+        return out
+
+    def set_state(self, state):
+        """resume from get_state() of a chain built with the same arguments"""
+        state = np.ascontiguousarray(state, dtype=float)
+        if len(state) != lib().orc_state_size(self.h):
+            raise ValueError("state size does not match this chain")
+        lib().orc_set_state(self.h, _dp(state))
 
     @property
     def eps(self):

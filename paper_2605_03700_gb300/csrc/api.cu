@@ -609,6 +609,33 @@ static void *g_noalloc_addr[QMC_NOALLOC_MAX_DEVICES];
 static size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // ------------------------------------------------------------- create -----
+// eigenpairs and propagators of every slice from the fields
+static int propagators_from_fields(qmc_ctx *ctx)
+{
+    const int n = ctx->n, nb = ctx->nb, nf = ctx->nf;
+    const long long NN = ctx->NN, n2 = ctx->n2, L = ctx->L;
+    cudaStream_t s = ctx->st;
+    for (int t = 0; t < ctx->L; ++t) {
+        if (eig_of_fields(ctx, ctx->phi + (long long)t * nf, L * nf, ctx->Up, ctx->Wp)) {
+            ctx->err = "eigensolver: unsupported size";
+            return QMC_ERR_ARG;
+        }
+        CommitP cp;
+        cp.flag = ctx->always;
+        cp.nseg = 2;
+        cp.seg[0] = CommitSeg{ctx->eigU + (long long)t * 4 * n2, ctx->Up, 4 * n2 * 4,
+                              L * 4 * n2 * 4, 4 * n2 * 4};
+        cp.seg[1] = CommitSeg{ctx->eigW + (long long)t * 4 * n, ctx->Wp, 4LL * n * 2,
+                              L * 4 * n * 2, 4LL * n * 2};
+        launch_commit(s, nb, cp);
+        factors_from_eig(ctx, ctx->Up, 4 * n2, ctx->Wp, 4 * n, ctx->V, ctx->T, ctx->lam, ctx->Dg,
+                         ctx->Dgi, ctx->lamG, ctx->DgG, ctx->DgiG);
+        build_B(ctx, ctx->V, ctx->T, ctx->Dg, ctx->Dgi, ctx->B + (long long)t * NN, L * NN,
+                ctx->Binv + (long long)t * NN, L * NN);
+    }
+    return 0;
+}
+
 static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy)
 {
     const int n = ctx->n, nb = ctx->nb;
@@ -895,26 +922,9 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
         q.ta = q.tb = q.tc = q.rc = TY_C64;
         gemm_autotune(s, q, 4 * nb, nullptr);
     }
-    // eigenpairs and propagators of every slice
-    for (int t = 0; t < ctx->L; ++t) {
-        if (eig_of_fields(ctx, ctx->phi + (long long)t * nf, L * nf, ctx->Up, ctx->Wp)) {
-            ctx->err = "eigensolver: unsupported size";
-            return QMC_ERR_ARG;
-        }
-        CommitP cp;
-        cp.flag = ctx->always;
-        cp.nseg = 2;
-        cp.seg[0] = CommitSeg{ctx->eigU + (long long)t * 4 * n2, ctx->Up, 4 * n2 * 4,
-                              L * 4 * n2 * 4, 4 * n2 * 4};
-        cp.seg[1] = CommitSeg{ctx->eigW + (long long)t * 4 * n, ctx->Wp, 4LL * n * 2,
-                              L * 4 * n * 2, 4LL * n * 2};
-        launch_commit(s, nb, cp);
-        factors_from_eig(ctx, ctx->Up, 4 * n2, ctx->Wp, 4 * n, ctx->V, ctx->T, ctx->lam, ctx->Dg,
-                         ctx->Dgi, ctx->lamG, ctx->DgG, ctx->DgiG);
-        build_B(ctx, ctx->V, ctx->T, ctx->Dg, ctx->Dgi, ctx->B + (long long)t * NN, L * NN,
-                ctx->Binv + (long long)t * NN, L * NN);
-    }
-    int r = build_left_stack(ctx);
+    int r = propagators_from_fields(ctx);
+    if (r) return r;
+    r = build_left_stack(ctx);
     if (r) return r;
     r = green_at_zero(ctx);
     if (r) return r;
@@ -1427,6 +1437,68 @@ int qmc_get_fields(qmc_ctx *ctx, int chain, double *host_buf, size_t len)
     CK(cudaStreamSynchronize(ctx->st));
     CK(cudaMemcpy(host_buf, ctx->phi + (size_t)chain * cnt, sizeof(double) * cnt,
                   cudaMemcpyDeviceToHost));
+    return QMC_OK;
+}
+
+// checkpoint: [n_chains][L][nf] fields, n_chains Langevin steps, the sweep
+// number (the Philox counters and the adaptation schedule follow from it)
+static size_t state_doubles(const qmc_ctx *ctx)
+{
+    return (size_t)ctx->nb * ctx->L * ctx->nf + ctx->nb + 1;
+}
+
+int qmc_state_size(const qmc_ctx *ctx, size_t *n_doubles)
+{
+    if (!ctx || !n_doubles) return QMC_ERR_ARG;
+    *n_doubles = state_doubles(ctx);
+    return QMC_OK;
+}
+
+int qmc_get_state(qmc_ctx *ctx, double *host_buf, size_t len)
+{
+    if (!ctx || !host_buf || len < state_doubles(ctx)) return QMC_ERR_ARG;
+    const size_t nphi = (size_t)ctx->nb * ctx->L * ctx->nf;
+    uint32_t ctr[QMC_CTR_N];
+    CK(cudaStreamSynchronize(ctx->st));
+    CK(cudaMemcpy(host_buf, ctx->phi, sizeof(double) * nphi, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(host_buf + nphi, ctx->eps, sizeof(double) * ctx->nb, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(ctr, ctx->ctr, sizeof ctr, cudaMemcpyDeviceToHost));
+    host_buf[nphi + ctx->nb] = (double)ctr[QMC_CTR_SWEEP];
+    return QMC_OK;
+}
+
+int qmc_set_state(qmc_ctx *ctx, const double *host_buf, size_t len)
+{
+    if (!ctx || !host_buf || len < state_doubles(ctx)) return QMC_ERR_ARG;
+    const size_t nphi = (size_t)ctx->nb * ctx->L * ctx->nf;
+    const double sw = host_buf[nphi + ctx->nb];
+    if (!(sw >= 0 && sw < 4294967296.0) || sw != floor(sw)) {
+        ctx->err = "checkpoint: the sweep number is not a 32-bit count";
+        return QMC_ERR_ARG;
+    }
+    for (int c = 0; c < ctx->nb; ++c)
+        if (!(host_buf[nphi + c] > 0)) {
+            ctx->err = "checkpoint: a Langevin step is not positive";
+            return QMC_ERR_ARG;
+        }
+    uint32_t ctr[QMC_CTR_N] = {0};
+    ctr[QMC_CTR_SWEEP] = (uint32_t)sw;
+    CK(cudaStreamSynchronize(ctx->st));
+    CK(cudaMemcpy(ctx->phi, host_buf, sizeof(double) * nphi, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->eps, host_buf + nphi, sizeof(double) * ctx->nb, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->eps_used, host_buf + nphi, sizeof(double) * ctx->nb,
+                  cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->ctr, ctr, sizeof ctr, cudaMemcpyHostToDevice));
+    ctx->sweep = ctr[QMC_CTR_SWEEP];
+    ctx->series_n = 0;
+    int r = propagators_from_fields(ctx);
+    if (r) return r;
+    r = build_left_stack(ctx);
+    if (r) return r;
+    r = green_at_zero(ctx);
+    if (r) return r;
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->st));
     return QMC_OK;
 }
 

@@ -61,6 +61,9 @@ def lib():
             raise QMCError(f"{LIB} is missing: run paper_2605_03700_gb300.build.build() first")
         L = C.CDLL(LIB)
         vp, dp = C.c_void_p, C.POINTER(C.c_double)
+        L.qmc_state_size.argtypes = [vp, C.POINTER(C.c_size_t)]
+        L.qmc_get_state.argtypes = [vp, dp, C.c_size_t]
+        L.qmc_set_state.argtypes = [vp, dp, C.c_size_t]
         L.qmc_measure_tau.argtypes = [vp, C.c_int, C.POINTER(C.c_int), dp]
         L.qmc_default_opts.argtypes = [C.POINTER(qmc_opts)]
         L.qmc_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.c_double, C.c_double,
@@ -237,6 +240,23 @@ class Chain:
         out = np.zeros((self.n_chains, QMC_NOBS))
         _check(lib().qmc_measure(self.h, _dp(out)), self.h)
         return out
+
+    def get_state(self):
+        """checkpoint: fields, Langevin steps and sweep number (qmc_get_state)"""
+        n = C.c_size_t()
+        _check(lib().qmc_state_size(self.h, C.byref(n)), self.h)
+        out = np.zeros(n.value)
+        _check(lib().qmc_get_state(self.h, _dp(out), n.value), self.h)
+        return out
+
+    def set_state(self, state):
+        """resume from get_state() of a context built with the same arguments"""
+        n = C.c_size_t()
+        _check(lib().qmc_state_size(self.h, C.byref(n)), self.h)
+        state = np.ascontiguousarray(state, dtype=float)
+        if state.size != n.value:
+            raise QMCError(f"state has {state.size} values, this context needs {n.value}")
+        _check(lib().qmc_set_state(self.h, _dp(state), n.value), self.h)
 
     def measure_tau(self, taus):
         """S^i_{q=0}(tau) of the current configuration, i = 1..5, at the

@@ -372,3 +372,22 @@ def test_zero_coupling_samples_standard_normal():
     x = np.array(xs)
     assert abs(x.mean()) < 0.03
     assert abs(x.var() - 1) < 0.05
+
+
+# ------------------------------------------------------ checkpointing ---
+@pytest.mark.parametrize("n_adapt", [-1, 6])
+def test_resumed_chain_is_bit_identical(n_adapt):
+    """Fields, step and sweep index are the whole state: a chain rebuilt from
+    a checkpoint continues exactly as the uninterrupted one (Philox is
+    counter based; propagators and G are recomputed as the sweep does)."""
+    a = O.Chain(M.TORUS, 3, 1.0, 0.1, 2.0, 0.1, 9, n_stab=4, n_adapt=n_adapt)
+    a.sweep(4)
+    st = a.get_state()
+    ref = a.sweep(5)
+    b = O.Chain(M.TORUS, 3, 1.0, 0.1, 2.0, 0.1, 9, n_stab=4, n_adapt=n_adapt)
+    b.set_state(st)
+    got = b.sweep(5)
+    assert np.array_equal(got, ref)
+    assert np.array_equal(a.phi(), b.phi()) and a.eps == b.eps
+    with pytest.raises(ValueError):
+        b.set_state(st[:-1])
