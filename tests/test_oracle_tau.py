@@ -141,3 +141,55 @@ def test_stable_structure_factors():
     assert np.abs(S[0] - eq).max() < 1e-10 * np.abs(eq).max()
     assert np.abs(S[2] - S[0]).max() < 1e-9 * np.abs(eq).max()
     assert np.all(S[1, 2:] < S[0, 2:])
+
+
+def _stable_triple(QR, DR, WR, QL, DL, WL):
+    Db, Ds = np.maximum, np.minimum
+    J = (QR.conj().T @ QL) / Db(DR, 1)[:, None] / Db(DL, 1)[None, :] \
+        + Ds(DR, 1)[:, None] * (WR @ WL.conj().T) * Ds(DL, 1)[None, :]
+    Ji = np.linalg.inv(J)
+    X = (QL / Db(DL, 1)[None, :]) @ Ji
+    R = QR.conj().T / Db(DR, 1)[:, None]
+    return X @ (Ds(DR, 1)[:, None] * WR), (WL.conj().T * Ds(DL, 1)[None, :]) @ Ji @ R, X @ R
+
+
+@pytest.mark.parametrize("nphi,beta,nstab", [(4, 2.0, 5), (5, 1.3, 4), (4, 10.0, 10)])
+def test_stabilisation_point_scheme(nphi, beta, nstab):
+    """The scheme of the GPU's time-displaced measurement: the left UDV stack
+    of B(beta, sp_k)^H built downward, the right UDV of B(sp_k, 0) advanced
+    upward, the stable triple at each stabilisation point and plain
+    propagation by one slice in between, reproduces the stable form at every
+    slice (to 1e-12 at beta = 10)."""
+    ch = O.Chain(M.TORUS, nphi, beta, 0.1, 1.5, 0.1, 3, n_stab=nstab)
+    ch.sweep(2)
+    N, L = ch.N, ch.L
+    sp = list(range(nstab, L, nstab)) + [L]
+    nsp = len(sp)
+    LQ, LD, LW = [None] * (nsp + 1), [None] * (nsp + 1), [None] * (nsp + 1)
+    LQ[nsp - 1], LD[nsp - 1], LW[nsp - 1] = np.eye(N), np.ones(N), np.eye(N)
+    for k in range(nsp - 1, -1, -1):
+        X = LQ[k] * LD[k][None, :]
+        for t in range(sp[k], sp[k - 1] if k > 0 else 0, -1):
+            X = ch.B(t)[0].conj().T @ X
+        Q, D, V = O.udv(X)
+        dst = k - 1 if k > 0 else nsp
+        LQ[dst], LD[dst], LW[dst] = Q, D, V @ LW[k]
+    RQ, RD, RW = np.eye(N, dtype=complex), np.ones(N), np.eye(N, dtype=complex)
+    cur = _stable_triple(RQ, RD, RW, LQ[nsp], LD[nsp], LW[nsp])
+    k, prev = 0, 0
+    for t in range(L + 1):
+        if t > 0:
+            B, Bi = ch.B(t)
+            if t == sp[k]:
+                X = RQ * RD[None, :]
+                for u in range(prev + 1, t + 1):
+                    X = ch.B(u)[0] @ X
+                Q, D, V = O.udv(X)
+                RQ, RD, RW = Q, D, V @ RW
+                cur = _stable_triple(RQ, RD, RW, LQ[k], LD[k], LW[k])
+                prev, k = t, k + 1
+            else:
+                cur = (B @ cur[0], cur[1] @ Bi, B @ cur[2] @ Bi)
+        ref = ch.green_tau_stable(t)
+        for a, b in zip(cur, ref):
+            assert np.abs(a - b).max() < 1e-12 * max(1.0, np.abs(b).max()), t
