@@ -391,3 +391,16 @@ def test_resumed_chain_is_bit_identical(n_adapt):
     assert np.array_equal(a.phi(), b.phi()) and a.eps == b.eps
     with pytest.raises(ValueError):
         b.set_state(st[:-1])
+
+
+def test_momentum_counts():
+    """N_q = (N_phi + 1)^2 = n_orb^2 on the sphere (all angular momentum
+    channels) and N_q proportional to N_phi on the torus: the disk
+    e^{-2 pi |q|^2 / (4 N_phi)} > 0.01 has area 2 N_phi ln 100
+    (Results, model section; Methods, toric and spherical regularisation)."""
+    for norb in (2, 3, 7, 16):
+        assert len(M.sphere_momenta(norb)) == norb ** 2
+    for nphi, nq in ((4, 37), (36, 333)):
+        assert len(M.torus_momenta(nphi)) == nq
+    r = [len(M.torus_momenta(n)) / n for n in (36, 64, 140)]
+    assert all(abs(x / (2 * math.log(100.0)) - 1) < 0.02 for x in r), r
