@@ -113,3 +113,15 @@ def test_unknown_drift_is_rejected(lib):
     o.drift = 2
     assert lib.qmc_create(C.byref(h), 0, 4, 1.0, 0.1, 1.0, 0.0, 0, C.byref(o)) == -1
     assert not h.value
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path, monkeypatch):
+    """No CPU fallback: with libqmc.so absent the binding raises instead of
+    computing anything."""
+    from paper_2605_03700_gb300 import qmc
+    monkeypatch.setattr(qmc, "LIB", str(tmp_path / "libqmc.so"))
+    monkeypatch.setattr(qmc, "_lib", None)
+    with pytest.raises(qmc.QMCError, match="missing"):
+        qmc.lib()
+    with pytest.raises(qmc.QMCError):
+        qmc.Chain(qmc.QMC_TORUS, 4, 1.0, 0.1, 1.0)
