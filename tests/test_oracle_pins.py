@@ -404,3 +404,20 @@ def test_momentum_counts():
         assert len(M.torus_momenta(nphi)) == nq
     r = [len(M.torus_momenta(n)) / n for n in (36, 64, 140)]
     assert all(abs(x / (2 * math.log(100.0)) - 1) < 0.02 for x in r), r
+
+
+def test_sign_free_region_is_u_n_nonnegative():
+    """The weight is sign-free wherever U_N = u + alpha/sqrt(2) >= 0, U_K
+    of either sign (g_1 = g_2 = -2u <= 0, g_0, g_3 >= 0); with U_N < 0 the
+    bracket acquires a phase, which is why qmc_create rejects that region."""
+    rng = np.random.default_rng(12)
+    for _ in range(6):
+        u = rng.uniform(0.05, 3.0)
+        al = rng.uniform(-math.sqrt(2) * u, 3.0)
+        ch = O.Chain(M.TORUS, 3, 1.0, 0.1, u, al, seed=int(rng.integers(100)))
+        assert abs(math.sin(ch.log_bracket().imag)) < 1e-10, (u, al)
+    for u, al in ((1.0, -2.0), (0.2, -0.5)):
+        assert u + al / math.sqrt(2) < 0
+        devs = [abs(math.sin(O.Chain(M.TORUS, 3, 1.0, 0.1, u, al, seed=s).log_bracket().imag))
+                for s in range(3)]
+        assert max(devs) > 1e-5, (u, al, devs)
