@@ -286,3 +286,31 @@ def dynamical_exponent(nphi, gap, err=None):
         r = np.log(gap) - X @ b
         cov = cov * (r @ r) / max(len(x) - 2, 1)
     return float(b[1]), float(np.sqrt(cov[1, 1])), float(b[0])
+
+
+# ---------------------------------------------------- errors of ratios -----
+def jackknife(records, fn, nbins=20):
+    """Jackknife mean and error of fn(mean record) over a Markov-chain series
+    of records (first axis: sweeps), with the series cut into nbins
+    consecutive bins (longer than the autocorrelation time): fn sees the
+    mean of all bins but one.  Returns (estimate, error), each shaped like
+    fn's value; the estimate is bias-corrected to O(1/nbins^2)."""
+    rec = np.asarray(records, dtype=float)
+    nb = int(nbins)
+    if nb < 2 or len(rec) < nb:
+        raise ValueError("need at least two bins with one record each")
+    m = len(rec) // nb
+    bins = rec[: m * nb].reshape((nb, m) + rec.shape[1:]).mean(axis=1)
+    total = bins.sum(axis=0)
+    full = np.asarray(fn(total / nb), dtype=float)
+    loo = np.array([fn((total - bins[k]) / (nb - 1)) for k in range(nb)], dtype=float)
+    mean_loo = loo.mean(axis=0)
+    err = np.sqrt((nb - 1) / nb * ((loo - mean_loo) ** 2).sum(axis=0))
+    return nb * full - (nb - 1) * mean_loo, err
+
+
+def order_parameter_errors(records, nphi, channel="SO5", nbins=20):
+    """(m^2, error, R, error) of one channel from a series of observable
+    records, R taken as the ratio of the means (jackknife errors)."""
+    (m2, R), (em2, eR) = jackknife(records, lambda r: order_parameters(r, nphi, channel), nbins)
+    return float(m2), float(em2), float(R), float(eR)

@@ -281,3 +281,39 @@ def test_gap_fit_against_the_exact_spectrum():
         d, e, _ = fss.fit_gap(taus, S, tmin=3, beta=40.0)
         assert abs(d - ed.gap(gi, q0)) < 1e-8, (gi, d, ed.gap(gi, q0))
         assert 0.9 < d < 1.2
+
+
+def test_jackknife_errors():
+    """Independent samples: the jackknife error of a mean equals the
+    standard error; for a ratio of means it matches the delta-method error,
+    and the estimate of a nonlinear function is bias-corrected."""
+    rng = np.random.default_rng(10)
+    n = 20000
+    x = rng.normal(3.0, 1.0, n)
+    y = rng.normal(2.0, 0.5, n)
+    rec = np.stack([x, y], axis=1)
+    est, err = fss.jackknife(rec, lambda r: r[0], nbins=50)
+    assert abs(est - x.mean()) < 1e-12 and abs(err / (x.std() / np.sqrt(n)) - 1) < 0.3
+    est, err = fss.jackknife(rec, lambda r: r[1] / r[0], nbins=50)
+    delta = (2.0 / 3.0) * np.sqrt((0.5 / 2.0) ** 2 + (1.0 / 3.0) ** 2) / np.sqrt(n)
+    assert abs(est - 2.0 / 3.0) < 4 * delta and abs(err / delta - 1) < 0.3
+    # bias correction: E[1/mean] over small samples
+    small = rng.normal(1.0, 0.5, (400, 10))
+    naive = np.mean([1.0 / s.mean() for s in small])
+    jk = np.mean([fss.jackknife(s[:, None], lambda r: 1.0 / r[0], nbins=10)[0] for s in small])
+    assert abs(jk - 1.0) < abs(naive - 1.0)
+    with pytest.raises(ValueError):
+        fss.jackknife(rec[:1], lambda r: r[0], nbins=2)
+
+
+def test_order_parameter_errors_on_records():
+    rng = np.random.default_rng(11)
+    s0 = rng.uniform(1, 3, (2000, 5))
+    sd = rng.uniform(0, 1, (2000, 5))
+    rec = np.zeros((2000, 20))
+    rec[:, 1:6], rec[:, 6:11] = s0, sd
+    m2, em2, R, eR = fss.order_parameter_errors(rec, 6)
+    assert abs(m2 - s0.sum(1).mean() / (5 * 36)) < 1e-12
+    assert 0 < em2 < 0.01 and 0 < eR < 0.01
+    # the ratio of means, up to the O(1/n) bias correction
+    assert abs(R - (1 - sd.sum(1).mean() / s0.sum(1).mean())) < 0.05 * eR
