@@ -37,6 +37,11 @@
  *                      field set for each half-factor), and the first-order
  *                      drift (factors treated as commuting), all exact under
  *                      MH; see ORC_SLICE_* and ORC_DRIFT_*
+ *   time-displaced G  G(t,0), Gbar(0,t), G(t,t) by propagation and in the
+ *                      stable UDV form; S^i_0(tau) by Wick's theorem
+ *                      (Supplementary Note 2)
+ *   checkpoint         not in the paper: fields, step and sweep index are
+ *                      the whole state (orc_get_state / orc_set_state)
  *   learned slice move not in the paper (a learned proposal added to
  *                      the method): an MLP gives a Gaussian N(mu, sigma^2) for
  *                      slice tau from its neighbours; preconditioned Crank-
