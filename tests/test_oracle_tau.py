@@ -193,3 +193,27 @@ def test_stabilisation_point_scheme(nphi, beta, nstab):
         ref = ch.green_tau_stable(t)
         for a, b in zip(cur, ref):
             assert np.abs(a - b).max() < 1e-12 * max(1.0, np.abs(b).max()), t
+
+
+def test_sphere_time_displaced_structure_factor_matches_ed():
+    """Sphere n_orb = 2, u = 1, alpha = 0.2, beta = 2, dtau = 0.05: Monte
+    Carlo S^1_0(tau) and S^3_0(tau) (l = 0) at tau = 0.1 and 0.25 within 4
+    sigma of ED (the sphere's form factors in the time-displaced Wick
+    contractions)."""
+    m = M.Model(M.SPHERE, 2)
+    beta, dtau = 2.0, 0.05
+    ed = E.ED(m, M.couplings(1.0, 0.2), beta)
+    ch = O.Chain(M.SPHERE, 2, beta, dtau, 1.0, 0.2, seed=7, n_stab=5, n_adapt=150, model=m)
+    ch.sweep(150)
+    taus = [2, 5]
+    rec = []
+    for _ in range(2500):
+        ch.sweep(1)
+        rec.append(ch.measure_tau(taus))
+    rec = np.array(rec)
+    for k, t in enumerate(taus):
+        for gi, col in ((0, 0), (2, 2)):
+            ref = ed.structure_factor_tau(gi, 0, t * dtau)
+            mu, err = _mean_err(rec[:, k, col])
+            assert abs(mu - ref) < 4 * err and err < 0.2 * ref, (t, gi, mu, ref, err)
+    assert ed.structure_factor_tau(0, 0, 0.25) < ed.structure_factor_tau(0, 0, 0.1)
