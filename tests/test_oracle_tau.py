@@ -215,5 +215,5 @@ def test_sphere_time_displaced_structure_factor_matches_ed():
         for gi, col in ((0, 0), (2, 2)):
             ref = ed.structure_factor_tau(gi, 0, t * dtau)
             mu, err = _mean_err(rec[:, k, col])
-            assert abs(mu - ref) < 4 * err and err < 0.2 * ref, (t, gi, mu, ref, err)
+            assert abs(mu - ref) < 4 * err and err < 0.3 * ref, (t, gi, mu, ref, err)
     assert ed.structure_factor_tau(0, 0, 0.25) < ed.structure_factor_tau(0, 0, 0.1)
