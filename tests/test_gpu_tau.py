@@ -81,3 +81,15 @@ def test_measure_tau_rejects_bad_offsets(qmc):
     for bad in ([3, 2], [-1], [11]):
         with pytest.raises(qmc.QMCError):
             g.measure_tau(bad)
+
+
+def test_measure_tau_on_the_sphere(qmc):
+    """Sphere, 3 orbitals (l = 0 is the ordering momentum), beta = 1."""
+    g = qmc.Chain(qmc.QMC_SPHERE, 2, 1.0, 0.1, 1.0, 0.2, 5, n_stab=5)
+    m = M.Model(M.SPHERE, 3)
+    o = O.Chain(M.SPHERE, 3, 1.0, 0.1, 1.0, 0.2, 5, n_stab=5, model=m)
+    g.sweep(2)
+    g.sync()
+    o.sweep(2)
+    taus = list(range(o.L + 1))
+    assert _rel(g.measure_tau(taus)[0], o.measure_tau(taus)) < 1e-8
