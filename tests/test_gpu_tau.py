@@ -84,10 +84,11 @@ def test_measure_tau_rejects_bad_offsets(qmc):
 
 
 def test_measure_tau_on_the_sphere(qmc):
-    """Sphere, 3 orbitals (l = 0 is the ordering momentum), beta = 1."""
-    g = qmc.Chain(qmc.QMC_SPHERE, 2, 1.0, 0.1, 1.0, 0.2, 5, n_stab=5)
+    """Sphere, 3 orbitals (l = 0 is the ordering momentum), beta = 1, at
+    the paper's sphere coupling scale u = 0.3."""
+    g = qmc.Chain(qmc.QMC_SPHERE, 2, 1.0, 0.1, 0.3, 0.1, 5, n_stab=5)
     m = M.Model(M.SPHERE, 3)
-    o = O.Chain(M.SPHERE, 3, 1.0, 0.1, 1.0, 0.2, 5, n_stab=5, model=m)
+    o = O.Chain(M.SPHERE, 3, 1.0, 0.1, 0.3, 0.1, 5, n_stab=5, model=m)
     g.sweep(2)
     g.sync()
     o.sweep(2)
