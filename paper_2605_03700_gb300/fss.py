@@ -23,8 +23,9 @@ scaling"):
 * the SO(5) gap from the tail of the imaginary-time correlation and the
   dynamical exponent z from its size dependence (Supplementary Note 2).
 
-Inputs are per-(u, N_phi) means (e.g. from Chain.series() with errors from
-mean_err); everything is numpy on the host.
+Inputs are per-(u, N_phi) means of the observable records (Chain.series()),
+with errors from order_parameter_errors (jackknife over bins) or mean_err;
+everything is numpy on the host.
 """
 from __future__ import annotations
 
