@@ -52,7 +52,8 @@ enum {
     QMC_ERR_UNSTABLE = -4,  /* G error at a restabilisation above opts.stab_tol */
     QMC_ERR_SIGN = -5,      /* an accepted update had |sin Im log R| above opts.sign_tol */
     QMC_ERR_NONFINITE = -6, /* a determinant ratio or field became NaN/Inf */
-    QMC_ERR_TIMEOUT = -7    /* a device-side bounded wait gave up */
+    QMC_ERR_TIMEOUT = -7,   /* a device-side bounded wait gave up */
+    QMC_ERR_IO = -8         /* checkpoint file: I/O error, bad format or checksum */
 };
 
 /* Number of doubles per observable record (qmc_get_series, qmc_measure). */
@@ -258,6 +259,35 @@ int qmc_series_length(const qmc_ctx *ctx);
 int qmc_state_size(const qmc_ctx *ctx, size_t *n_doubles);
 int qmc_get_state(qmc_ctx *ctx, double *host_buf, size_t len);
 int qmc_set_state(qmc_ctx *ctx, const double *host_buf, size_t len);
+
+/* Checkpoint files (not in the paper).  Layout, little-endian as written
+ * by the host: this header, header.n_doubles doubles of qmc_get_state, and
+ * a 64-bit FNV-1a checksum of header and state.  The header identifies the
+ * run, so a state is only loaded into a context built the same way
+ * (params_hash: FNV-1a of the chains' couplings, anisotropies and seeds). */
+#define QMC_CKPT_MAGIC 0x4b434d51u /* "QMCK" */
+#define QMC_CKPT_VERSION 1u
+typedef struct {
+    uint32_t magic, version;
+    int32_t geometry, n_orb, L, n_q, n_chains, precision, drift, n_stab;
+    double beta, dtau;
+    uint64_t params_hash;
+    uint64_t n_doubles;
+} qmc_checkpoint_header;  /* 72 bytes, no padding */
+
+/* Fill the header of a context's checkpoint (host only). */
+int qmc_checkpoint_header_of(const qmc_ctx *ctx, qmc_checkpoint_header *h);
+/* Write header, state (h->n_doubles doubles, host) and checksum to path,
+ * through a temporary file renamed into place.  QMC_ERR_IO on failure. */
+int qmc_checkpoint_write(const char *path, const qmc_checkpoint_header *h, const double *state);
+/* Read the header of a checkpoint file.  QMC_ERR_IO for a missing file or
+ * a bad magic / version. */
+int qmc_checkpoint_read_header(const char *path, qmc_checkpoint_header *h);
+/* Read the state (len >= header.n_doubles doubles, host).  QMC_ERR_ARG when
+ * the header differs from *expect (if given) or len is short; QMC_ERR_IO for
+ * a truncated, corrupted or overlong file. */
+int qmc_checkpoint_read(const char *path, const qmc_checkpoint_header *expect, double *state,
+                        size_t len);
 
 /* Time-displaced SO(5) structure factors of the current configuration of
  * every chain (Supplementary Note 2; Wick's theorem with Methods, Eq.

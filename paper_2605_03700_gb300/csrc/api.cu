@@ -1502,6 +1502,31 @@ int qmc_set_state(qmc_ctx *ctx, const double *host_buf, size_t len)
     return QMC_OK;
 }
 
+int qmc_checkpoint_header_of(const qmc_ctx *ctx, qmc_checkpoint_header *h)
+{
+    if (!ctx || !h) return QMC_ERR_ARG;
+    memset(h, 0, sizeof *h);
+    h->magic = QMC_CKPT_MAGIC;
+    h->version = QMC_CKPT_VERSION;
+    h->geometry = ctx->geom;
+    h->n_orb = ctx->n;
+    h->L = ctx->L;
+    h->n_q = ctx->nq;
+    h->n_chains = ctx->nb;
+    h->precision = ctx->o.precision;
+    h->drift = ctx->o.drift;
+    h->n_stab = ctx->o.n_stab;
+    h->beta = ctx->beta;
+    h->dtau = ctx->dtau;
+    uint64_t ph = 0xcbf29ce484222325ull;
+    ph = qmc_fnv1a(ctx->u.data(), sizeof(double) * ctx->u.size(), ph);
+    ph = qmc_fnv1a(ctx->anis.data(), sizeof(double) * ctx->anis.size(), ph);
+    ph = qmc_fnv1a(ctx->seeds.data(), sizeof(uint64_t) * ctx->seeds.size(), ph);
+    h->params_hash = ph;
+    h->n_doubles = state_doubles(ctx);
+    return QMC_OK;
+}
+
 int qmc_get_trace(qmc_ctx *ctx, int chain, double *host_buf, size_t len, long *count)
 {
     if (!ctx || !count || chain < 0 || chain >= ctx->nb) return QMC_ERR_ARG;
@@ -1580,6 +1605,7 @@ const char *qmc_strerror(int code)
     case QMC_ERR_SIGN: return "weight ratio not positive (sign problem)";
     case QMC_ERR_NONFINITE: return "non-finite value";
     case QMC_ERR_TIMEOUT: return "bounded device wait gave up";
+    case QMC_ERR_IO: return "checkpoint file: I/O error, bad format or checksum";
     default: return "unknown error";
     }
 }

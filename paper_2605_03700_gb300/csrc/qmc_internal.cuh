@@ -155,6 +155,8 @@ __device__ __forceinline__ double rng_normal(uint32_t f, uint32_t slice, uint32_
 // ------------------------------------------------------- small utilities --
 // number of kernels this library has launched (all contexts, host-side count)
 extern std::atomic<long long> g_qmc_launches;
+// 64-bit FNV-1a hash of n bytes, continuing from h (checkpoint.cu)
+uint64_t qmc_fnv1a(const void *p, size_t n, uint64_t h);
 #define QMC_COUNT(k) (g_qmc_launches += (k))
 
 #define QMC_DEVFN __device__ __forceinline__

@@ -46,6 +46,29 @@ class qmc_opts(C.Structure):
     ]
 
 
+QMC_CKPT_MAGIC = 0x4B434D51
+QMC_CKPT_VERSION = 1
+
+
+class qmc_checkpoint_header(C.Structure):
+    _fields_ = [
+        ("magic", C.c_uint32),
+        ("version", C.c_uint32),
+        ("geometry", C.c_int32),
+        ("n_orb", C.c_int32),
+        ("L", C.c_int32),
+        ("n_q", C.c_int32),
+        ("n_chains", C.c_int32),
+        ("precision", C.c_int32),
+        ("drift", C.c_int32),
+        ("n_stab", C.c_int32),
+        ("beta", C.c_double),
+        ("dtau", C.c_double),
+        ("params_hash", C.c_uint64),
+        ("n_doubles", C.c_uint64),
+    ]
+
+
 class QMCError(RuntimeError):
     pass
 
@@ -64,6 +87,11 @@ def lib():
         L.qmc_state_size.argtypes = [vp, C.POINTER(C.c_size_t)]
         L.qmc_get_state.argtypes = [vp, dp, C.c_size_t]
         L.qmc_set_state.argtypes = [vp, dp, C.c_size_t]
+        hp = C.POINTER(qmc_checkpoint_header)
+        L.qmc_checkpoint_header_of.argtypes = [vp, hp]
+        L.qmc_checkpoint_write.argtypes = [C.c_char_p, hp, dp]
+        L.qmc_checkpoint_read_header.argtypes = [C.c_char_p, hp]
+        L.qmc_checkpoint_read.argtypes = [C.c_char_p, hp, dp, C.c_size_t]
         L.qmc_measure_tau.argtypes = [vp, C.c_int, C.POINTER(C.c_int), dp]
         L.qmc_default_opts.argtypes = [C.POINTER(qmc_opts)]
         L.qmc_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.c_double, C.c_double,
@@ -136,6 +164,30 @@ def qmc_default_opts() -> qmc_opts:
     o = qmc_opts()
     _check(lib().qmc_default_opts(C.byref(o)))
     return o
+
+
+def checkpoint_write(path, header, state):
+    """Write a checkpoint file (qmc_checkpoint_write)."""
+    state = np.ascontiguousarray(state, dtype=float)
+    if state.size != header.n_doubles:
+        raise QMCError("state length differs from the header's n_doubles")
+    _check(lib().qmc_checkpoint_write(os.fsencode(path), C.byref(header), _dp(state)))
+
+
+def checkpoint_read_header(path):
+    h = qmc_checkpoint_header()
+    _check(lib().qmc_checkpoint_read_header(os.fsencode(path), C.byref(h)))
+    return h
+
+
+def checkpoint_read(path, expect=None):
+    """The state stored in a checkpoint file; with expect (a header) the file
+    must belong to a run built the same way."""
+    h = checkpoint_read_header(path)
+    out = np.zeros(h.n_doubles)
+    _check(lib().qmc_checkpoint_read(os.fsencode(path), C.byref(expect) if expect is not None else None,
+                                     _dp(out), out.size))
+    return out
 
 
 def qmc_gemm_tile(n: int, precision: int) -> int:
@@ -257,6 +309,19 @@ class Chain:
         if state.size != n.value:
             raise QMCError(f"state has {state.size} values, this context needs {n.value}")
         _check(lib().qmc_set_state(self.h, _dp(state), n.value), self.h)
+
+    def checkpoint_header(self):
+        h = qmc_checkpoint_header()
+        _check(lib().qmc_checkpoint_header_of(self.h, C.byref(h)), self.h)
+        return h
+
+    def save(self, path):
+        """checkpoint to a file: header, state, checksum"""
+        checkpoint_write(path, self.checkpoint_header(), self.get_state())
+
+    def load(self, path):
+        """resume from a file written by save() of a context built the same way"""
+        self.set_state(checkpoint_read(path, self.checkpoint_header()))
 
     def measure_tau(self, taus):
         """S^i_{q=0}(tau) of the current configuration, i = 1..5, at the

@@ -62,3 +62,23 @@ def test_resumed_context_continues_the_chain(qmc):
     bad[-1] = -1
     with pytest.raises(qmc.QMCError):
         b.set_state(bad)
+
+
+def test_checkpoint_file_round_trip(qmc, tmp_path):
+    a = _chain(qmc)
+    a.sweep(3)
+    p = tmp_path / "batch.ckpt"
+    a.save(p)
+    a.sweep(4)
+    a.sync()
+    ref = a.series()[:, -4:]
+    b = _chain(qmc)
+    b.load(p)
+    b.sweep(4)
+    b.sync()
+    assert np.array_equal(b.series()[:, :, 17], ref[:, :, 17])
+    # a context with other couplings refuses the file
+    c = qmc.Chain(qmc.QMC_TORUS, 4, 1.0, 0.1, 0.0, 0.0, 0, n_chains=3, couplings=[0.5, 1.2, 2.1],
+                  anisotropies=[0.0, 0.1, -0.15], seeds=[3, 11, 42], n_stab=5, n_adapt=8)
+    with pytest.raises(qmc.QMCError):
+        c.load(p)
