@@ -273,6 +273,7 @@ static int green_from_udv(qmc_ctx *ctx, const cd *QR, const double *DR, const cd
 // left stack B(beta, tau)^H = Q D W at every stabilisation point and at 0
 static int build_left_stack(qmc_ctx *ctx)
 {
+    QmcRange range("qmc.left_stack");
     const int nb = ctx->nb, N = ctx->N, nsp = (int)ctx->sp.size();
     const long long NN = ctx->NN, Ls = (long long)(nsp + 1) * NN, LDs = (long long)(nsp + 1) * N;
     cudaStream_t s = ctx->st;
@@ -329,6 +330,7 @@ static int green_at_zero(qmc_ctx *ctx)
 // move (net == nullptr) or the learned move around the network's Gaussian
 static int update_slice(qmc_ctx *ctx, int t, qmc_net *net = nullptr, double rho = 0.0)
 {
+    QmcRange range(net ? "qmc.update.learned" : "qmc.update.langevin");
     const int nb = ctx->nb, N = ctx->N, n = ctx->n, nf = ctx->nf;
     const long long NN = ctx->NN, n2 = ctx->n2;
     const int s0 = t - 1;
@@ -422,6 +424,7 @@ static int update_slice(qmc_ctx *ctx, int t, qmc_net *net = nullptr, double rho 
 // right stack advanced over slices (prev, t], fresh G(t) and its error
 static int restabilise(qmc_ctx *ctx, int k, int prev, int t)
 {
+    QmcRange range("qmc.restabilise");
     const int nb = ctx->nb, N = ctx->N, nsp = (int)ctx->sp.size();
     const long long NN = ctx->NN, Ls = (long long)(nsp + 1) * NN, LDs = (long long)(nsp + 1) * N;
     const long long BL = (long long)ctx->L * NN;
@@ -543,6 +546,7 @@ static void measure_into(qmc_ctx *ctx, double *out, long long out_cs,
 // the sweep number, so the same launches replay from a captured graph
 static int enqueue_sweep(qmc_ctx *ctx, qmc_net *net = nullptr, double rho = 0.0)
 {
+    QmcRange range("qmc.sweep");
     int r = build_left_stack(ctx);
     if (r) return r;
     r = green_at_zero(ctx);
@@ -1275,6 +1279,7 @@ int qmc_measure(qmc_ctx *ctx, double *host_out)
 // measured at the requested slices
 static int measure_tau_impl(qmc_ctx *ctx, int ntau, const int *taus, double *dout, TauWork &w)
 {
+    QmcRange range("qmc.measure_tau");
     const int nb = ctx->nb, N = ctx->N, nsp = (int)ctx->sp.size();
     const long long NN = ctx->NN, BL = (long long)ctx->L * NN;
     const long long Ls = (long long)(nsp + 1) * NN, LDs = (long long)(nsp + 1) * N;

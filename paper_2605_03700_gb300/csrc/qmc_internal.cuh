@@ -155,6 +155,21 @@ __device__ __forceinline__ double rng_normal(uint32_t f, uint32_t slice, uint32_
 // ------------------------------------------------------- small utilities --
 // number of kernels this library has launched (all contexts, host-side count)
 extern std::atomic<long long> g_qmc_launches;
+// NVTX range over a host scope (sweep phases); header-only NVTX 3, a no-op
+// unless a profiler is attached
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+struct QmcRange {
+    explicit QmcRange(const char *name) { nvtxRangePushA(name); }
+    ~QmcRange() { nvtxRangePop(); }
+    QmcRange(const QmcRange &) = delete;
+    QmcRange &operator=(const QmcRange &) = delete;
+};
+#else
+struct QmcRange {
+    explicit QmcRange(const char *) {}
+};
+#endif
 // 64-bit FNV-1a hash of n bytes, continuing from h (checkpoint.cu)
 uint64_t qmc_fnv1a(const void *p, size_t n, uint64_t h);
 #define QMC_COUNT(k) (g_qmc_launches += (k))
