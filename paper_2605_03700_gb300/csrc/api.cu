@@ -16,6 +16,7 @@
 // FP32: the drift only has to be one deterministic function of the state for
 // MALA to stay exact.
 #include <math.h>
+#include <cmath>
 #include <stdio.h>
 #include <string.h>
 
@@ -1482,8 +1483,14 @@ int qmc_set_state(qmc_ctx *ctx, const double *host_buf, size_t len)
         return QMC_ERR_ARG;
     }
     for (int c = 0; c < ctx->nb; ++c)
-        if (!(host_buf[nphi + c] > 0)) {
-            ctx->err = "checkpoint: a Langevin step is not positive";
+        if (!(host_buf[nphi + c] > 0) || !std::isfinite(host_buf[nphi + c])) {
+            ctx->err = "checkpoint: a Langevin step is not positive and finite";
+            return QMC_ERR_ARG;
+        }
+    // non-finite fields would reach the factorisations: rejected here
+    for (size_t x = 0; x < nphi; ++x)
+        if (!std::isfinite(host_buf[x])) {
+            ctx->err = "checkpoint: a field is not finite";
             return QMC_ERR_ARG;
         }
     uint32_t ctr[QMC_CTR_N] = {0};

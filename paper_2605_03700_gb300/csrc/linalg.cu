@@ -822,7 +822,9 @@ __global__ void __launch_bounds__(256) k_qrp(int n, const cd *X, long long sX, c
         // pivot: first column of largest norm, warp-parallel (FP64 compares
         // run on the FP64 pipe: a serial scan by one thread cost ~15% here)
         if (warp == 0) {
-            int best = n;
+            // a lane without candidates keeps (-1, k): never chosen over a
+            // real norm (>= 0), and a valid column if every norm is NaN
+            int best = k;
             double bn = -1.0;
             for (int j = k + lane; j < n; j += 32)
                 if (cn[j] > bn) {

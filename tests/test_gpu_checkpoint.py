@@ -62,6 +62,12 @@ def test_resumed_context_continues_the_chain(qmc):
     bad[-1] = -1
     with pytest.raises(qmc.QMCError):
         b.set_state(bad)
+    # a non-finite field or step is refused before it reaches the device
+    for k in (7, 3 * L * nf):
+        bad = st.copy()
+        bad[k] = np.nan
+        with pytest.raises(qmc.QMCError):
+            b.set_state(bad)
 
 
 def test_checkpoint_file_round_trip(qmc, tmp_path):
