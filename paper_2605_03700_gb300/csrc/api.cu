@@ -17,6 +17,7 @@
 // MALA to stay exact.
 #include <math.h>
 #include <cmath>
+#include <cstdlib>
 #include <stdio.h>
 #include <string.h>
 
@@ -98,8 +99,18 @@ struct qmc_ctx {
     Op Gx(const void *p, long long s) const { return Op{p, s, gp}; }
 };
 
+// Scratch buffers are written before every read.  With QMC_POISON_SCRATCH
+// set in the environment they start as all-ones bytes (NaN as doubles, -1 as
+// ints) instead of zeros, so a read before a write shows up as NaN in the
+// parity checks: the stand-in for a race/initialisation checker.
+static bool poison_scratch()
+{
+    const char *v = getenv("QMC_POISON_SCRATCH");
+    return v && *v && *v != '0';
+}
+
 template <class T>
-static int dalloc(qmc_ctx *ctx, T **p, size_t count, size_t elem = sizeof(T))
+static int dalloc(qmc_ctx *ctx, T **p, size_t count, size_t elem = sizeof(T), bool scratch = false)
 {
     void *q = nullptr;
     size_t bytes = (count ? count : 1) * elem;
@@ -108,7 +119,7 @@ static int dalloc(qmc_ctx *ctx, T **p, size_t count, size_t elem = sizeof(T))
         ctx->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
         return QMC_ERR_OOM;
     }
-    cudaMemset(q, 0, bytes);
+    cudaMemset(q, scratch && poison_scratch() ? 0xFF : 0, bytes);
     ctx->allocs.push_back(q);
     *p = (T *)q;
     return 0;
@@ -124,6 +135,17 @@ static int dalloc(qmc_ctx *ctx, T **p, size_t count, size_t elem = sizeof(T))
     do {                                                          \
         int r_ = dalloc(ctx, &(ptr), (size_t)(count), ctx->gsz);  \
         if (r_) return r_;                                        \
+    } while (0)
+// scratch (written before read; poisoned under QMC_POISON_SCRATCH)
+#define DAS(ptr, count)                                                             \
+    do {                                                                            \
+        int r_ = dalloc(ctx, &(ptr), (size_t)(count), sizeof(*(ptr)), true);        \
+        if (r_) return r_;                                                          \
+    } while (0)
+#define DAGS(ptr, count)                                                            \
+    do {                                                                            \
+        int r_ = dalloc(ctx, &(ptr), (size_t)(count), ctx->gsz, true);              \
+        if (r_) return r_;                                                          \
     } while (0)
 
 static const cd ONE = {1, 0}, ZERO = {0, 0}, MONE = {-1, 0};
@@ -783,33 +805,33 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
     DA(ctx->B, (size_t)nb * L * NN);
     DA(ctx->Binv, (size_t)nb * L * NN);
     DA(ctx->G, (size_t)nb * NN);
-    DA(ctx->LQ, (size_t)nb * (nsp + 1) * NN);
-    DA(ctx->LW, (size_t)nb * (nsp + 1) * NN);
-    DA(ctx->LD, (size_t)nb * (nsp + 1) * N);
-    DA(ctx->RQ, (size_t)nb * NN);
-    DA(ctx->RW, (size_t)nb * NN);
-    DA(ctx->RD, (size_t)nb * N);
+    DAS(ctx->LQ, (size_t)nb * (nsp + 1) * NN);
+    DAS(ctx->LW, (size_t)nb * (nsp + 1) * NN);
+    DAS(ctx->LD, (size_t)nb * (nsp + 1) * N);
+    DAS(ctx->RQ, (size_t)nb * NN);
+    DAS(ctx->RW, (size_t)nb * NN);
+    DAS(ctx->RD, (size_t)nb * N);
     DA(ctx->V, (size_t)nb * 4 * NN);
-    DA(ctx->Vp, (size_t)nb * 4 * NN);
+    DAS(ctx->Vp, (size_t)nb * 4 * NN);
     DA(ctx->T, (size_t)nb * 3 * NN);
-    DA(ctx->Tp, (size_t)nb * 3 * NN);
+    DAS(ctx->Tp, (size_t)nb * 3 * NN);
     DA(ctx->lam, (size_t)nb * 7 * N);
     DA(ctx->Dg, (size_t)nb * 7 * N);
     DA(ctx->Dgi, (size_t)nb * 7 * N);
-    DA(ctx->lamp, (size_t)nb * 7 * N);
-    DA(ctx->Dgp, (size_t)nb * 7 * N);
-    DA(ctx->Dgip, (size_t)nb * 7 * N);
-    DA(ctx->Up, (size_t)nb * 4 * n2);
-    DA(ctx->Wp, (size_t)nb * 4 * n);
-    DA(ctx->Bp, (size_t)nb * NN);
-    DA(ctx->Bpi, (size_t)nb * NN);
-    DAG(ctx->Ah, (size_t)nb * NN);
-    DAG(ctx->Y1, (size_t)nb * NN);
-    DAG(ctx->Cacc, (size_t)nb * 4 * NN);
-    DAG(ctx->At, (size_t)nb * 4 * NN);
-    DAG(ctx->F1, (size_t)nb * NN);
-    DAG(ctx->F2, (size_t)nb * NN);
-    DA(ctx->Fm, (size_t)nb * 4 * n2);
+    DAS(ctx->lamp, (size_t)nb * 7 * N);
+    DAS(ctx->Dgp, (size_t)nb * 7 * N);
+    DAS(ctx->Dgip, (size_t)nb * 7 * N);
+    DAS(ctx->Up, (size_t)nb * 4 * n2);
+    DAS(ctx->Wp, (size_t)nb * 4 * n);
+    DAS(ctx->Bp, (size_t)nb * NN);
+    DAS(ctx->Bpi, (size_t)nb * NN);
+    DAGS(ctx->Ah, (size_t)nb * NN);
+    DAGS(ctx->Y1, (size_t)nb * NN);
+    DAGS(ctx->Cacc, (size_t)nb * 4 * NN);
+    DAGS(ctx->At, (size_t)nb * 4 * NN);
+    DAGS(ctx->F1, (size_t)nb * NN);
+    DAGS(ctx->F2, (size_t)nb * NN);
+    DAS(ctx->Fm, (size_t)nb * 4 * n2);
     if (ctx->gp == TY_C64) {
         ctx->lamG = ctx->lam;
         ctx->DgG = ctx->Dg;
@@ -831,30 +853,30 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
         DA(ctx->W32, (size_t)nb * 4 * n);
         DAG(ctx->Fm32, (size_t)nb * 4 * n2);
     }
-    DA(ctx->NSx, (size_t)nb * 4 * n2);
-    DA(ctx->NSy, (size_t)nb * 4 * n2);
-    DA(ctx->NSz, (size_t)nb * 4 * n2);
-    DA(ctx->NSs, (size_t)nb * 4 * n2);
-    DA(ctx->NSr, (size_t)nb * 4 * n2);
-    DA(ctx->NSe, (size_t)nb * 4 * n2);
+    DAS(ctx->NSx, (size_t)nb * 4 * n2);
+    DAS(ctx->NSy, (size_t)nb * 4 * n2);
+    DAS(ctx->NSz, (size_t)nb * 4 * n2);
+    DAS(ctx->NSs, (size_t)nb * 4 * n2);
+    DAS(ctx->NSr, (size_t)nb * 4 * n2);
+    DAS(ctx->NSe, (size_t)nb * 4 * n2);
     DA(ctx->always, nb);
-    DA(ctx->tq, (size_t)nb * 4 * nq);
-    DA(ctx->X1, (size_t)nb * NN);
-    DA(ctx->X2, (size_t)nb * NN);
-    DA(ctx->M, (size_t)nb * NN);
-    DA(ctx->Gp, (size_t)nb * NN);
-    DA(ctx->Gs, (size_t)nb * NN);
-    DA(ctx->Qt, (size_t)nb * NN);
-    DA(ctx->Vt, (size_t)nb * NN);
+    DAS(ctx->tq, (size_t)nb * 4 * nq);
+    DAS(ctx->X1, (size_t)nb * NN);
+    DAS(ctx->X2, (size_t)nb * NN);
+    DAS(ctx->M, (size_t)nb * NN);
+    DAS(ctx->Gp, (size_t)nb * NN);
+    DAS(ctx->Gs, (size_t)nb * NN);
+    DAS(ctx->Qt, (size_t)nb * NN);
+    DAS(ctx->Vt, (size_t)nb * NN);
     DA(ctx->Eye, (size_t)nb * NN);
-    DA(ctx->dinvR, (size_t)nb * N);
-    DA(ctx->dinvL, (size_t)nb * N);
+    DAS(ctx->dinvR, (size_t)nb * N);
+    DAS(ctx->dinvL, (size_t)nb * N);
     DA(ctx->logdet, nb);
-    DA(ctx->ax, (size_t)nb * 4 * nq * 2);
-    DA(ctx->phip, (size_t)nb * nf);
-    DA(ctx->grad, (size_t)nb * nf);
-    DA(ctx->gradp, (size_t)nb * nf);
-    DA(ctx->Dt, (size_t)nb * N);
+    DAS(ctx->ax, (size_t)nb * 4 * nq * 2);
+    DAS(ctx->phip, (size_t)nb * nf);
+    DAS(ctx->grad, (size_t)nb * nf);
+    DAS(ctx->gradp, (size_t)nb * nf);
+    DAS(ctx->Dt, (size_t)nb * N);
     DA(ctx->ones, (size_t)nb * N);
     DA(ctx->stats, (size_t)nb * 4);
     DA(ctx->eps, nb);
@@ -862,7 +884,7 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
     DA(ctx->series, (size_t)nb * ctx->o.series_capacity * QMC_NOBS);
     DA(ctx->trace, (size_t)nb * (ctx->o.trace_capacity > 0 ? ctx->o.trace_capacity : 1) * QMC_NTRACE);
     DA(ctx->trace_n, nb);
-    DA(ctx->piv, (size_t)nb * N);
+    DAS(ctx->piv, (size_t)nb * N);
     DA(ctx->flag, nb);
     DA(ctx->errf, nb);
     cudaStream_t s = ctx->st;

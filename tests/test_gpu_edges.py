@@ -61,3 +61,32 @@ def test_zero_sweeps_change_nothing(qmc):
     g.sweep(0)
     g.sync()
     assert np.array_equal(g.fields(0), f0) and np.array_equal(g.green(0), G0)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_poisoned_scratch_changes_nothing(qmc, monkeypatch, precision):
+    """QMC_POISON_SCRATCH fills every scratch buffer with NaN bytes at
+    creation: a buffer read before it is written would turn the chain into
+    NaNs.  The Langevin and learned sweeps must still make the oracle's
+    decisions (FP64) or track it (mixed)."""
+    from oracle import learned as LN
+    from tests.test_gpu_parity import _compare_mixed
+    monkeypatch.setenv("QMC_POISON_SCRATCH", "1")
+    nsw, L = 6, 10
+    g = qmc.Chain(qmc.QMC_TORUS, 4, 1.0, 0.1, 1.5, 0.1, 3, n_stab=5, precision=precision,
+                  trace_capacity=2 * nsw * L)
+    o = O.Chain(M.TORUS, 4, 1.0, 0.1, 1.5, 0.1, 3, n_stab=5)
+    o.enable_trace(2 * nsw * L)
+    nf = 4 * o.nq
+    net = qmc.Net(nf, 16, 16, 5)
+    th = np.zeros(LN.n_params(nf, 16))
+    g.sweep(nsw)
+    g.sweep_learned(net, nsw, 0.0)
+    g.sync()
+    o.sweep(nsw)
+    o.sweep_learned(nsw, th, 16, 0.0)
+    if precision == 0:
+        _compare_chain(g, 0, o, 2 * nsw, g.trace(0), o.trace())
+    else:
+        assert _compare_mixed(g, 0, o, 2 * nsw, 2 * nsw * L // 2) > 0
+    assert np.all(np.isfinite(g.series()[0][:, :13]))
