@@ -81,7 +81,7 @@ struct qmc_ctx {
     double *Wp;
     // gradient / wrap scratch in the compute type gp (aliases of the FP64
     // diagonals when gp is FP64)
-    void *Ah, *Y1, *Cacc, *At, *lamG, *DgG, *DgiG, *lampG, *DgpG, *DgipG, *F1, *F2;
+    void *Ah, *Y1, *Cacc, *At, *lamG, *DgG, *DgiG, *lampG, *DgpG, *DgipG;
     // eigensolver scratch: channel matrices (FP64, FP32 copy) and the FP32
     // eigenpairs and FP64 polish buffers of the mixed mode
     cd *Fm;
@@ -829,8 +829,6 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
     DAGS(ctx->Y1, (size_t)nb * NN);
     DAGS(ctx->Cacc, (size_t)nb * 4 * NN);
     DAGS(ctx->At, (size_t)nb * 4 * NN);
-    DAGS(ctx->F1, (size_t)nb * NN);
-    DAGS(ctx->F2, (size_t)nb * NN);
     DAS(ctx->Fm, (size_t)nb * 4 * n2);
     if (ctx->gp == TY_C64) {
         ctx->lamG = ctx->lam;
