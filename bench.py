@@ -1,19 +1,31 @@
 #!/usr/bin/env python
 """Benchmark of the CF-DQMC sweep: autocorrelation-corrected effective
-samples per second on the N_phi = 36 torus.
+samples per second on the N_phi = 36 torus, against the plain FP64 sweep.
 
 Workload (one step = one sweep of every chain): torus N_phi = 36 (N = 72
 single-particle states per spin block, N_q = 333 momenta, 1332 real fields
 per slice), beta = 36, dtau = 0.1 (L = 360 slices), eight chains at couplings
 u = linspace(0.5, 2.0, 8), seeds 0..7, restabilisation every 10 slices.
-Default path: mixed precision (FP32 eigensolver bulk and drift transforms,
-FP64 propagators, ratios and updates) with learned-proposal sweeps and a
-Langevin sweep every 4th step; --mode plain --precision 0 is the plain FP64
-Langevin sweep.
 
-value = sum over chains of K / (2 tau_int) divided by the device time of the
-K timed sweeps, tau_int = max over {m^2, E} of Sokal's windowed estimate on
-the chain's recorded series.
+Two arms run in one invocation on the same GPU:
+  * the headline path (default --mode learned --precision 1): mixed precision
+    with learned whole-slice sweeps and a Langevin sweep every 4th step;
+  * the plain FP64 Langevin sweep (--precision 0 --mode plain), the
+    comparison the metric names.
+Each arm: W warm-up sweeps, K timed sweeps (CUDA events on the library's
+stream, graph-replayed sweeps, no profiler hook inside), then untimed sweeps
+of the same schedule until the chain's series holds --tau-sweeps records.
+tau_int = max over {m^2, E} of Sokal's windowed estimate (c = 5) on that
+series, per chain; value = sum over chains of 1 / (2 tau_int) divided by the
+timed seconds per sweep.  The line carries both arms' sweeps/s and effective
+samples/s and their ratio (vs_plain_fp64).
+
+The roofline of the FP64 GEMM class is taken in a separate untimed pass
+(CUDA events around each FP64 GEMM launch), against the FP64 FMA rate
+measured on the same GPU at start-up (qmc_peak_fma).  The G error against
+the FP64 oracle: the oracle rebuilds G from chain 0's fields after the timed
+region (propagators, UDV stack, G(0) in FP64 on the host) and the largest
+elementwise difference to the GPU's G, relative to max|G|, is reported.
 
 Multi-GPU: one process per GPU, each running its own eight chains (seeds
 offset by 8 * rank): independent replicas, weak scaling, no collective on the
@@ -45,9 +57,6 @@ COUPLINGS = np.linspace(0.5, 2.0, NCH)
 EPS0 = 0.45
 METRIC = "effective samples/s (autocorr-corrected) at N_phi=36 torus vs plain FP64 sweep"
 UNIT = "effective samples/s"
-# FP64 pipe peak of a GB300: 1.25 TFLOP/s nominal = 152 SMs x 2 DFMA/clk x
-# 2 flop x 2.07 GHz (derivation and measurement in the design notes)
-FP64_PEAK_TFLOPS = 1.25
 # dram bytes (read + write) of one FP64 GEMM launch from the ncu capture
 # summarised in profiles/k_zgemm_fp64_n36_full.md (n = 36, batch 32; the
 # N = 72 batch-8 products move the same 2 MB of operands)
@@ -141,9 +150,29 @@ def combine_over_ranks(dist, t_s, wall, ess, device):
 
 
 # ------------------------------------------------------------- tau / ESS ---
+def tau_with_error(x, tau_fn, c=5.0):
+    """Sokal's windowed tau_int and its statistical error
+    sigma^2 = 2 (2W + 1) tau^2 / n, W the self-consistent window (W >= c tau)."""
+    t = tau_fn(x)
+    W = max(1, int(math.ceil(c * t)))
+    return t, t * math.sqrt(2.0 * (2 * W + 1) / len(x))
+
+
 def tau_per_chain(series, tau_fn):
-    """max over m^2 (col 0) and E (col 12) of the windowed tau_int"""
-    return [max(tau_fn(series[c, :, 0]), tau_fn(series[c, :, 12])) for c in range(series.shape[0])]
+    """per chain: (tau, error) of the larger of m^2 (col 0) and E (col 12)"""
+    out = []
+    for c in range(series.shape[0]):
+        a = tau_with_error(series[c, :, 0], tau_fn)
+        b = tau_with_error(series[c, :, 12], tau_fn)
+        out.append(a if a[0] >= b[0] else b)
+    return out
+
+
+def ess_rate(taus, step_s):
+    """effective samples per second of a batch of chains and its error"""
+    v = sum(1.0 / (2.0 * t) for t, _ in taus) / step_s
+    e = math.sqrt(sum((dt / (2.0 * t * t)) ** 2 for t, dt in taus)) / step_s
+    return v, e
 
 
 # ------------------------------------------------------------ CPU oracle ---
@@ -163,15 +192,23 @@ def _oracle_sample(u, seed):
     return (t_sw - t_meas) / L_SAMPLE, t_meas, t_sw
 
 
-def oracle_sweeps_per_s(nproc=NCH):
+def _oracle_green(u, seed, state, L):
+    """G(0) of the oracle rebuilt in FP64 from a chain state (fields, Langevin
+    step, sweep number) of the GPU: propagators, left UDV stack and the
+    stabilised inverse, all on the host."""
+    from oracle import model as M
+    from oracle import oracle as O
+    m = M.Model(M.TORUS, NPHI)
+    ch = O.Chain(M.TORUS, NPHI, L * DTAU, DTAU, u, 0.0, seed, n_stab=NSTAB, eps0=EPS0, model=m)
+    ch.set_state(state)
+    return ch.green()
+
+
+def oracle_sweeps_per_s(pool, nproc=NCH):
     """Aggregate oracle chain-sweeps/s at L = 360 over nproc parallel chains
     (one process, one thread each), from a bounded sample."""
-    from oracle import oracle as O
-    O.build()
-    ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
-    with ctx.Pool(nproc) as pool:
-        res = pool.starmap(_oracle_sample, [(float(COUPLINGS[c % NCH]), c) for c in range(nproc)])
+    res = pool.starmap(_oracle_sample, [(float(COUPLINGS[c % NCH]), c) for c in range(nproc)])
     wall = time.perf_counter() - t0
     L = int(round(BETA / DTAU))
     t_full = [L * r[0] + r[1] for r in res]   # seconds per L=360 sweep per chain
@@ -181,9 +218,10 @@ def oracle_sweeps_per_s(nproc=NCH):
 def run_reference(args):
     """--impl reference: the FP64 CPU oracle on the host cores, bounded
     sample per step (one L_SAMPLE-slice sweep of each of the eight chains in
-    parallel processes), reported as effective samples/s at L = 360 with
-    tau_int = 1/2 (the oracle's own tau cannot be measured in minutes: an
-    upper bound of its rate)."""
+    parallel processes).  The measured per-slice and per-measurement times
+    are reported as measured; the L = 360 sweep rate is scaled from them, and
+    tau_int is taken as 1/2 (the oracle's own tau cannot be measured in
+    minutes), so the value is an upper bound of the oracle's rate."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
@@ -191,12 +229,14 @@ def run_reference(args):
     O.build()
     ctx = mp.get_context("spawn")
     L = int(round(BETA / DTAU))
-    step_rates = []
+    step_rates, slice_s, meas_s = [], [], []
     with ctx.Pool(NCH) as pool:
         for k in range(args.warmup + args.steps):
             res = pool.starmap(_oracle_sample, [(float(COUPLINGS[c]), c) for c in range(NCH)])
             if k >= args.warmup:
                 step_rates.append(sum(1.0 / (L * r[0] + r[1]) for r in res))
+                slice_s += [r[0] for r in res]
+                meas_s += [r[1] for r in res]
     sweeps_per_s = float(np.mean(step_rates))
     value = sweeps_per_s / (2 * 0.5)
     line = {
@@ -204,8 +244,14 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * NCH / sweeps_per_s,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (fields drawn from the chains' own Philox streams)",
-        "config": workload_config({"sample": f"one L={L_SAMPLE} sweep per chain per step, "
-                                             f"scaled to L={L}; tau_int taken as 1/2"}),
+        "config": workload_config({
+            "sample": f"one L={L_SAMPLE} sweep per chain per step (measured), scaled to L={L}; "
+                      "tau_int taken as 1/2",
+            "measured": {"slice_update_s": float(np.mean(slice_s)),
+                         "measurement_s": float(np.mean(meas_s)),
+                         "chains_in_parallel": NCH},
+            "scaled": {"sweep_s_per_chain_at_L360": float(L * np.mean(slice_s) + np.mean(meas_s)),
+                       "how": "L x measured slice-update time + one measurement"}}),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": NCH, "kind": "oracle",
                          "sample": f"per step: one sweep of an L={L_SAMPLE} N_phi=36 oracle chain "
                                    f"per coupling, {NCH} processes x 1 thread, scaled to L={L}, "
@@ -217,15 +263,110 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- ours ------
+def run_arm(P, stream, *, mode, precision, drift, seeds, steps, warmup, tau_sweeps, clocks_index,
+            graph=True, want_state=False):
+    """One arm: create the eight chains, warm up, time `steps` sweeps, then
+    extend the series to `tau_sweeps` records with untimed sweeps of the same
+    schedule.  Returns the timing, the tau_int estimates and diagnostics."""
+    import torch
+    wall0 = time.perf_counter()
+    ch = P.Chain(P.QMC_TORUS, NPHI, BETA, DTAU, 0.0, 0.0, 0, n_chains=NCH, couplings=COUPLINGS,
+                 seeds=seeds, n_stab=NSTAB, eps0=EPS0, series_capacity=4096, precision=precision,
+                 drift=P.QMC_DRIFT_FIRST if drift == "first" else P.QMC_DRIFT_EXACT)
+    ch.set_stream(stream.cuda_stream)
+    # learned mode: whole-slice moves around the network's Gaussian
+    # (rho = 0), a Langevin sweep every LANGEVIN_EVERY-th step as the
+    # fallback; the network is at its prior initialisation (mu = 0,
+    # sigma = 1), which held-out NLL early stopping keeps at this workload
+    net = P.Net(4 * ch.n_q, 256, 16, 1 + int(seeds[0])) if mode == "learned" else None
+
+    def is_langevin(k):
+        return net is None or k % LANGEVIN_EVERY == LANGEVIN_EVERY - 1
+
+    def step(k):
+        if is_langevin(k):
+            ch.sweep(1, graph=graph)
+        else:
+            ch.sweep_learned(net, 1, 0.0, graph=graph)
+
+    pinned = torch.empty((steps, NCH, P.QMC_NOBS), dtype=torch.float64, pin_memory=True)
+    for k in range(warmup):
+        step(k)
+    ch.sync()
+    torch.cuda.synchronize()
+    clocks = Clocks(clocks_index) if clocks_index is not None else None
+    launches0 = P.qmc_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(steps):
+        step(warmup + k)
+        ch.copy_latest_async(pinned[k].data_ptr())
+    e1.record(stream)
+    ch.sync()
+    torch.cuda.synchronize()
+    wall_e2e = time.perf_counter() - wall0
+    launches = P.qmc_launch_count() - launches0
+    clk = clocks.stop() if clocks else None
+    ms = e0.elapsed_time(e1)
+    state0 = green0 = None
+    if want_state:
+        # chain 0 in the oracle's single-chain layout: fields, step, sweep
+        st = ch.get_state()
+        nfl = ch.L * 4 * ch.n_q
+        state0 = np.concatenate([st[:nfl], [st[NCH * nfl], st[-1]]])
+        green0 = ch.green(0)
+    # the untimed tail of the tau_int series (same schedule)
+    k = warmup + steps
+    while k < warmup + tau_sweeps:
+        step(k)
+        k += 1
+    ch.sync()
+    series = ch.series()[:, warmup:, :]
+    taus = tau_per_chain(series, P.qmc_tau_int)
+    timed = series[:, :steps, :]
+    learned_steps = [j for j in range(series.shape[1]) if not is_langevin(warmup + j)]
+    acc_learned = float(series[:, learned_steps, 13].mean()) if learned_steps else None
+    acc_langevin = float(np.delete(series[:, :, 13], learned_steps, axis=1).mean())
+    out = {"ch": ch, "net": net, "ms": ms, "step_s": ms / 1000.0 / steps, "taus": taus,
+           "series_len": int(series.shape[1]), "launches": int(launches), "clocks": clk,
+           "wall_e2e": wall_e2e, "g_err_max": float(timed[:, :, 15].max()),
+           "sign_max": float(timed[:, :, 16].max()), "acc_learned": acc_learned,
+           "acc_langevin": acc_langevin, "state0": state0, "green0": green0,
+           "d2h": NCH * P.QMC_NOBS * 8}
+    return out
+
+
+def gemm_roofline_pass(P, arm, steps=2):
+    """FP64 GEMM class roofline in a separate, untimed pass: CUDA events
+    around each FP64 GEMM launch of `steps` further sweeps (eager launches,
+    so each product has its own event pair)."""
+    ch, net = arm["ch"], arm["net"]
+    P.qmc_profile_gemm(True)
+    for k in range(steps):
+        if net is None or k % 2 == 1:
+            ch.sweep(1)
+        else:
+            ch.sweep_learned(net, 1, 0.0)
+    ch.sync()
+    ms, n, flops = P.qmc_profile_gemm(False)
+    return ms, n, flops
+
+
 def run_ours(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     # the oracle pool is spawned before the first GPU call
-    cpu = None
+    pool, cpu = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, t_full, wall, _ = oracle_sweeps_per_s()
-        cpu = {"sweeps_per_s": rate, "t_full": t_full, "wall": wall}
+        from oracle import oracle as O
+        O.build()
+        pool = mp.get_context("spawn").Pool(NCH)
+        rate, t_full, wall, res = oracle_sweeps_per_s(pool)
+        cpu = {"sweeps_per_s": rate, "t_full": t_full, "wall": wall,
+               "slice_s": float(np.mean([r[0] for r in res])),
+               "meas_s": float(np.mean([r[1] for r in res]))}
     import torch
     torch.cuda.set_device(local)
     dist = None
@@ -236,80 +377,78 @@ def run_ours(args):
     B.build()
     import paper_2605_03700_gb300 as P
 
+    fp64_peak = P.qmc_peak_fma(True, 4096)
     stream = torch.cuda.Stream()
-    wall0 = time.perf_counter()
     seeds = replica_seeds(rank)
-    ch = P.Chain(P.QMC_TORUS, NPHI, BETA, DTAU, 0.0, 0.0, 0, n_chains=NCH, couplings=COUPLINGS,
-                 seeds=seeds, n_stab=NSTAB, eps0=EPS0, series_capacity=4096,
-                 precision=args.precision,
-                 drift=P.QMC_DRIFT_FIRST if args.drift == "first" else P.QMC_DRIFT_EXACT)
-    ch.set_stream(stream.cuda_stream)
-    # learned mode: whole-slice moves around the network's Gaussian
-    # (qmc_sweep_learned, rho = 0), a Langevin sweep every LANGEVIN_EVERY-th
-    # step as the fallback; the network is at its prior initialisation
-    # (mu = 0, sigma = 1), which held-out NLL early stopping keeps at this
-    # workload (training does not improve it; see the design notes)
-    net = P.Net(4 * ch.n_q, 256, 16, 1 + rank) if args.mode == "learned" else None
-
-    def step(k):
-        if net is None or k % LANGEVIN_EVERY == LANGEVIN_EVERY - 1:
-            ch.sweep(1)
-        else:
-            ch.sweep_learned(net, 1, 0.0)
-
-    pinned = torch.empty((args.steps, NCH, P.QMC_NOBS), dtype=torch.float64, pin_memory=True)
-    for k in range(args.warmup):
-        step(k)
-    ch.sync()
+    if dist:
+        dist.barrier()
+    main = run_arm(P, stream, mode=args.mode, precision=args.precision, drift=args.drift,
+                   seeds=seeds, steps=args.steps, warmup=args.warmup,
+                   tau_sweeps=max(args.tau_sweeps, args.steps), clocks_index=local,
+                   want_state=pool is not None)
+    g_orc = None
+    if pool is not None:
+        L = int(round(BETA / DTAU))
+        g_orc = pool.apply_async(_oracle_green, (float(COUPLINGS[0]), int(seeds[0]),
+                                                 main["state0"], L))
+    gemm_ms, gemm_n, gemm_flops = gemm_roofline_pass(P, main)
+    plain = None
+    if not args.no_plain_arm:
+        plain = run_arm(P, stream, mode="plain", precision=0, drift="exact", seeds=seeds,
+                        steps=args.plain_steps, warmup=args.warmup,
+                        tau_sweeps=max(args.plain_tau_sweeps, args.plain_steps),
+                        clocks_index=None)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = Clocks(local)
-    launches0 = P.qmc_launch_count()
-    P.qmc_profile_gemm(True)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for k in range(args.steps):
-        step(args.warmup + k)
-        ch.copy_latest_async(pinned[k].data_ptr())
-    e1.record(stream)
-    ch.sync()
-    gemm_ms, gemm_n, gemm_flops = P.qmc_profile_gemm(False)
-    launches = P.qmc_launch_count() - launches0
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    series = ch.series()[:, args.warmup:, :]
-    wall_e2e = time.perf_counter() - wall0
-    taus = tau_per_chain(series, P.qmc_tau_int)
-    learned_steps = [k for k in range(args.steps)
-                     if net is not None and (args.warmup + k) % LANGEVIN_EVERY != LANGEVIN_EVERY - 1]
-    acc_learned = float(series[:, learned_steps, 13].mean()) if learned_steps else None
-    acc_langevin = float(np.delete(series[:, :, 13], learned_steps, axis=1).mean())
-    ess = sum(args.steps / (2.0 * t) for t in taus)
-    t_s = ms / 1000.0
-    t_s, wall_e2e, ess = combine_over_ranks(dist, t_s, wall_e2e, ess, "cuda")
+
+    v_main, dv_main = ess_rate(main["taus"], main["step_s"])
+    t_s, wall_e2e, ess = combine_over_ranks(dist, main["ms"] / 1000.0, main["wall_e2e"],
+                                            v_main * main["ms"] / 1000.0, "cuda")
     value = ess / t_s
     e2e = ess / wall_e2e
-    # roofline of the GEMM class (event-timed over the timed region)
+    vs_plain = None
+    if plain is not None:
+        v_pl, dv_pl = ess_rate(plain["taus"], plain["step_s"])
+        _, _, ess_pl = combine_over_ranks(dist, plain["ms"] / 1000.0, plain["wall_e2e"],
+                                          v_pl * plain["ms"] / 1000.0, "cuda")
+        ratio = v_main / v_pl
+        vs_plain = {
+            "ess_ratio": ratio,
+            "ess_ratio_err": ratio * math.sqrt((dv_main / v_main) ** 2 + (dv_pl / v_pl) ** 2),
+            "plain_fp64": {"value": v_pl, "value_err": dv_pl, "ms_per_step": plain["ms"] /
+                           args.plain_steps, "sweeps_per_s_per_gpu": NCH / plain["step_s"],
+                           "tau_int": [[round(t, 3), round(e, 3)] for t, e in plain["taus"]],
+                           "tau_series_len": plain["series_len"],
+                           "acceptance": plain["acc_langevin"], "g_err_max": plain["g_err_max"],
+                           "timed_steps": args.plain_steps, "gpu_launches": plain["launches"]},
+            "sweeps_per_s_ratio": plain["step_s"] / main["step_s"]}
+    g_err_oracle = None
+    if g_orc is not None:
+        Go = g_orc.get(timeout=1800)
+        g_err_oracle = float(np.abs(main["green0"] - Go).max() / np.abs(Go).max())
+    if pool is not None:
+        pool.close()
+        pool.join()
     gemm_tflops = gemm_flops / (gemm_ms / 1000.0) / 1e12 if gemm_ms > 0 else 0.0
-    roof = {"bound": "alu", "achieved": gemm_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": gemm_tflops / FP64_PEAK_TFLOPS,
-            "traffic": TRAFFIC_PER_LAUNCH, "kernel": "k_zgemm<double> (batched complex FP64 GEMM; FP32 products excluded)",
-            "launches": gemm_n, "ms_total": gemm_ms, "share_of_step_time": gemm_ms / ms,
-            "peak_note": "nominal FP64 pipe rate (no measured FP64 peak exists for this part): "
-                         "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz = 1.26 TFLOP/s"}
+    roof = {"bound": "alu", "achieved": gemm_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": gemm_tflops / fp64_peak,
+            "traffic": TRAFFIC_PER_LAUNCH,
+            "kernel": "k_zgemm<double> (batched complex FP64 GEMM; FP32 products excluded)",
+            "launches": gemm_n, "ms_total": gemm_ms,
+            "pass": "separate untimed pass of 2 sweeps, CUDA events around each FP64 GEMM",
+            "peak_note": "measured on this GPU at start-up: FP64 FMA chains on every SM "
+                         "(qmc_peak_fma), 'alu' = the FP64 CUDA-core pipe"}
     if rank != 0:
-        ch.close()
+        for arm in (main, plain):
+            if arm:
+                arm["ch"].close()
         if dist:
             dist.destroy_process_group()
         return 0
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": main["ms"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f32+f64",
         "data": "synthetic (fields drawn from the chains' own Philox streams)",
         "config": workload_config({"parallelism": f"replicas x{world}",
@@ -319,29 +458,39 @@ def run_ours(args):
                                    "schedule": ("plain Langevin sweeps" if args.mode == "plain" else
                                                 f"learned sweeps (rho 0), every {LANGEVIN_EVERY}th "
                                                 "step a Langevin sweep"),
-                                   "acceptance_learned": acc_learned,
-                                   "acceptance_langevin": acc_langevin,
-                                   "tau_int": [round(t, 3) for t in taus],
-                                   "tau_series_len": int(series.shape[1]),
-                                   "sweeps_per_s_per_gpu": NCH * args.steps / t_s / world}),
+                                   "launch": "graph-replayed sweeps",
+                                   "acceptance_learned": main["acc_learned"],
+                                   "acceptance_langevin": main["acc_langevin"],
+                                   "tau_int": [[round(t, 3), round(e, 3)] for t, e in main["taus"]],
+                                   "tau_series_len": main["series_len"],
+                                   "value_err": dv_main,
+                                   "sweeps_per_s_per_gpu": NCH / main["step_s"],
+                                   "g_err_max": main["g_err_max"],
+                                   "g_err_vs_oracle": g_err_oracle,
+                                   "sign_dev_max": main["sign_max"]}),
+        "vs_plain_fp64": vs_plain,
         "roofline": roof,
-        "clocks": clk,
-        "gpu_launches": int(launches),
+        "fp64_peak_tflops_measured": fp64_peak,
+        "clocks": main["clocks"],
+        "gpu_launches": main["launches"],
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": NCH * P.QMC_NOBS * 8,
+                "d2h_bytes_per_step": main["d2h"],
                 "note": "wall clock through the C ABI from qmc_create to the last D2H of the "
-                        "records, warm-up included; a sweep takes no host input"},
+                        "timed steps' records, warm-up included; a sweep takes no host input"},
     }
     if cpu:
-        ess_cpu = sum(1.0 / tf / (2.0 * t) for tf, t in zip(cpu["t_full"], taus))
+        ess_cpu = sum(1.0 / tf / (2.0 * t) for tf, (t, _) in zip(cpu["t_full"], main["taus"]))
         line["cpu_baseline"] = {
             "value": ess_cpu, "unit": UNIT, "cores": NCH, "kind": "oracle",
             "sample": f"one sweep of an L={L_SAMPLE} N_phi=36 oracle chain per coupling "
-                      f"({NCH} processes x 1 thread), scaled to L=360; tau_int of the GPU "
-                      f"chains (decision-identical Markov chains)",
+                      f"({NCH} processes x 1 thread), measured {cpu['slice_s']:.3f} s per slice "
+                      f"update and {cpu['meas_s']:.3f} s per measurement, scaled to L=360; "
+                      "tau_int of the GPU chains",
             "sweeps_per_s": cpu["sweeps_per_s"]}
     print(json.dumps(line))
-    ch.close()
+    for arm in (main, plain):
+        if arm:
+            arm["ch"].close()
     if dist:
         dist.destroy_process_group()
     return 0
@@ -354,9 +503,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain-arm", action="store_true",
+                    help="skip the plain FP64 comparison arm")
+    ap.add_argument("--tau-sweeps", type=int, default=200,
+                    help="records per chain for tau_int of the headline arm (timed + untimed)")
+    ap.add_argument("--plain-steps", type=int, default=20, help="timed sweeps of the plain arm")
+    ap.add_argument("--plain-tau-sweeps", type=int, default=120,
+                    help="records per chain for tau_int of the plain FP64 arm")
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1],
-                    help="0: FP64 everywhere; 1: mixed (FP32 eigensolver + FP64 polish, FP32 "
-                         "gradient transforms and wraps, FP64 propagators, ratios, updates)")
+                    help="0: FP64 everywhere; 1: mixed (FP32 eigensolver bulk + FP64 "
+                         "refinement, FP32 drift transforms; FP64 propagators, ratios, updates)")
     ap.add_argument("--mode", default="learned", choices=["learned", "plain"],
                     help="learned: learned-proposal sweeps with a Langevin sweep every "
                          "4th step; plain: Langevin sweeps only")

@@ -216,6 +216,16 @@ int qmc_net_loss_grad(qmc_net *net, const float *X, const float *Y, int batch, d
  * must equal the context's 4 N_q); trace column 7 holds rho. */
 int qmc_sweep_learned(qmc_ctx *ctx, qmc_net *net, int n_sweeps, double rho);
 
+/* qmc_sweep_learned replayed from a CUDA graph, as qmc_sweep_graph does for
+ * the Langevin sweep: the first call (and any call with another network,
+ * another rho, or after the network's activation buffers were enlarged for
+ * a larger batch) captures one learned sweep of all chains; later calls
+ * launch it.  Results are identical to qmc_sweep_learned.  The network must
+ * stay alive while the context may replay its graph; the network's weights
+ * may be changed (qmc_net_train, qmc_net_set_params) between calls, the
+ * graph reads them in place. */
+int qmc_sweep_learned_graph(qmc_ctx *ctx, qmc_net *net, int n_sweeps, double rho);
+
 /* Batched chains of different sizes (not in the paper; a deployment feature): a
  * group sweeps several contexts -- any mix of geometry, orbital count,
  * couplings and precision -- as one CUDA graph per sweep.  Each member's
@@ -377,7 +387,11 @@ int qmc_ratio_update(int N, int batch, const double *G, const double *Delta, dou
  *   The first call on a device looks up the array's device address with
  *   cudaGetSymbolAddress (that device must be current) and sets the kernels'
  *   shared-memory limits on it; make that first call before any stream
- *   capture.  Later calls only enqueue kernels.
+ *   capture.  Later calls only enqueue kernels.  Both are cached per device
+ *   and CUDA context: after a device reset the next call repeats the set-up.
+ *   With QMC_POISON_SCRATCH set in the environment the set-up fills the
+ *   array with all-ones bytes (NaN as doubles), as for every other scratch
+ *   buffer of the library.
  *   Asynchronous: the outputs are valid once `stream` has been synchronised.
  *   Every call shares the one scratch array and leaves its contents behind
  *   (nothing in it has to start at zero); calls that overlap on the GPU --
@@ -406,6 +420,17 @@ int qmc_gemm_tile(int n, int precision);
  * time in *total_ms, the number of launches and their algorithmic flops
  * (8 M N K per complex product) -- the inputs of the GEMM roofline. */
 int qmc_profile_gemm(int enable, double *total_ms, long long *launches, double *flops);
+
+/* Measured fused-multiply-add rate of the current device's CUDA-core pipe,
+ * the roofline denominator of the library's FP64-pipe kernels (not part of
+ * the method; the paper states no hardware).  fp64 = 1 times FP64 FMAs,
+ * fp64 = 0 FP32 FMAs: eight independent dependent chains per thread, 8 CTAs
+ * of 256 threads per SM, `iters` steps per chain (1 .. 2^20), best of three
+ * event-timed launches after a warm-up, 2 flop per FMA.  Allocates and frees
+ * one small device buffer; synchronous; changes no clock or device setting.
+ * *tflops receives TFLOP/s.  QMC_ERR_ARG for a bad count, QMC_ERR_CUDA or
+ * QMC_ERR_OOM from the runtime. */
+int qmc_peak_fma(int fp64, int iters, double *tflops);
 
 const char *qmc_strerror(int code);
 const char *qmc_last_error(const qmc_ctx *ctx);

@@ -22,6 +22,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -60,6 +61,10 @@ struct qmc_ctx {
     double *lq = nullptr;                // learned move: log N(phi') - log N(phi) per chain
     cudaStream_t cap_st = nullptr;       // private stream the sweep graph is captured on
     cudaGraphExec_t gexec = nullptr;     // one captured sweep of all chains
+    cudaGraphExec_t lexec = nullptr;     // one captured learned sweep (network lnet, rho lrho)
+    unsigned long long lnet_uid = 0, lnet_gen = 0;
+    double lrho = -1.0;
+    long long lgraph_kernels = 0;
     long long graph_kernels = 0;         // kernels in that graph
     std::string err;
     std::vector<void *> allocs;
@@ -627,11 +632,17 @@ static int ratio_update_core(cudaStream_t s, int N, int batch, const cd *G, cons
 // fail mid-run) still gets the ratio and G update.  Every GPU that loads the
 // library holds these bytes (QMC_NOALLOC_SCRATCH_BYTES, include/qmc.h) until
 // the process exits.  In host code the symbol is only a host-side stand-in:
-// its device address is looked up once per device with cudaGetSymbolAddress
-// and cached below.
+// its device address is looked up with cudaGetSymbolAddress once per device
+// and context (the cache is keyed on the context id, so a context recreated
+// after a device reset looks the address up again) and cached below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[QMC_NOALLOC_SCRATCH_BYTES];
 #define QMC_NOALLOC_MAX_DEVICES 64
-static void *g_noalloc_addr[QMC_NOALLOC_MAX_DEVICES];
+struct NoallocSlot {
+    unsigned long long ctx_id;
+    void *addr;
+};
+static NoallocSlot g_noalloc_addr[QMC_NOALLOC_MAX_DEVICES];
+static std::mutex g_noalloc_mu;
 
 static size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -1047,6 +1058,7 @@ int qmc_destroy(qmc_ctx *ctx)
         else cudaDeviceSynchronize();
     }
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->lexec) cudaGraphExecDestroy(ctx->lexec);
     if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);
     for (void *p : ctx->allocs) cudaFree(p);
     delete ctx;
@@ -1075,7 +1087,8 @@ int qmc_sweep(qmc_ctx *ctx, int n_sweeps)
 // capture enqueue_sweep of each context on its own branch of one graph:
 // origin -> fork to every member's capture stream -> join on origin
 static int capture_sweeps(qmc_ctx *const *m, int nm, cudaStream_t origin, cudaGraphExec_t *exec,
-                          long long *kernels, std::string *err)
+                          long long *kernels, std::string *err, qmc_net *net = nullptr,
+                          double rho = 0.0)
 {
     const bool prof = gemm_prof_enable(false);
     const long long k0 = g_qmc_launches;
@@ -1093,7 +1106,7 @@ static int capture_sweeps(qmc_ctx *const *m, int nm, cudaStream_t origin, cudaGr
             saved[i] = m[i]->st;
             m[i]->st = m[i]->cap_st;
             cudaStreamWaitEvent(m[i]->cap_st, ev[nm], 0);
-            r = enqueue_sweep(m[i]);
+            r = enqueue_sweep(m[i], net, rho);
             if (r) *err = m[i]->err;
             cudaEventRecord(ev[i], m[i]->cap_st);
             cudaStreamWaitEvent(origin, ev[i], 0);
@@ -1161,6 +1174,45 @@ int qmc_sweep_learned(qmc_ctx *ctx, qmc_net *net, int n_sweeps, double rho)
     for (int i = 0; i < n_sweeps; ++i) {
         int r = enqueue_sweep(ctx, net, rho);
         if (r) return r;
+        ctx->sweep++;
+        ctx->series_n++;
+    }
+    return QMC_OK;
+}
+
+int qmc_sweep_learned_graph(qmc_ctx *ctx, qmc_net *net, int n_sweeps, double rho)
+{
+    if (!ctx || !net || n_sweeps < 0) return QMC_ERR_ARG;
+    if (net->nf != ctx->nf || ctx->L < 2 || !(rho >= 0.0 && rho < 1.0)) {
+        ctx->err = "learned sweep: network field count, L >= 2 or 0 <= rho < 1 violated";
+        return QMC_ERR_ARG;
+    }
+    if (n_sweeps == 0) return QMC_OK;
+    if (net_ensure_rows(net, ctx->nb)) {
+        ctx->err = "learned sweep: out of device memory";
+        return QMC_ERR_OOM;
+    }
+    if (!ctx->lexec || ctx->lnet_uid != net->uid || ctx->lnet_gen != net->gen ||
+        ctx->lrho != rho) {
+        if (ctx->lexec) {
+            CK(cudaStreamSynchronize(ctx->st));
+            cudaGraphExecDestroy(ctx->lexec);
+            ctx->lexec = nullptr;
+        }
+        if (!ctx->cap_st) CK(cudaStreamCreateWithFlags(&ctx->cap_st, cudaStreamNonBlocking));
+        qmc_ctx *one[1] = {ctx};
+        // the network's own stream is not used inside the capture: every
+        // kernel of the learned move is enqueued on the context's stream
+        int r = capture_sweeps(one, 1, ctx->cap_st, &ctx->lexec, &ctx->lgraph_kernels, &ctx->err,
+                               net, rho);
+        if (r) return r;
+        ctx->lnet_uid = net->uid;
+        ctx->lnet_gen = net->gen;
+        ctx->lrho = rho;
+    }
+    for (int i = 0; i < n_sweeps; ++i) {
+        CK(cudaGraphLaunch(ctx->lexec, ctx->st));
+        g_qmc_launches += ctx->lgraph_kernels;
         ctx->sweep++;
         ctx->series_n++;
     }
@@ -1664,13 +1716,26 @@ int qmc_ratio_update_noalloc(int N, int batch, const double *G, const double *De
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= QMC_NOALLOC_MAX_DEVICES)
         return QMC_ERR_CUDA;
-    if (!g_noalloc_addr[dev]) {
-        void *ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr)
-            return QMC_ERR_CUDA;
-        g_noalloc_addr[dev] = ptr;
+    const unsigned long long id = current_context_id();
+    if (!id) return QMC_ERR_CUDA;
+    unsigned char *base;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        NoallocSlot &slot = g_noalloc_addr[dev];
+        if (slot.ctx_id != id || !slot.addr) {
+            void *ptr = nullptr;
+            if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr)
+                return QMC_ERR_CUDA;
+            // the initialisation check of the other scratch buffers: all-ones
+            // bytes (NaN as doubles) so a read before a write shows up
+            if (poison_scratch() &&
+                cudaMemset(ptr, 0xFF, QMC_NOALLOC_SCRATCH_BYTES) != cudaSuccess)
+                return QMC_ERR_CUDA;
+            slot.addr = ptr;
+            slot.ctx_id = id;
+        }
+        base = (unsigned char *)slot.addr;
     }
-    unsigned char *base = (unsigned char *)g_noalloc_addr[dev];
     cd *X1 = (cd *)base;
     cd *X2 = (cd *)(base + mat);
     cd *Mm = (cd *)(base + 2 * mat);

@@ -1,10 +1,13 @@
 // Checkpoint files (not in the paper): a fixed header that identifies the
 // run, the state of qmc_get_state, and a 64-bit FNV-1a checksum (Fowler,
-// Noll, Vo) of header and state.  Written to a temporary name and renamed,
-// so a crash never leaves a truncated file under the final name.  Host code
-// only: no device calls.
+// Noll, Vo) of header and state.  Written to a temporary name, flushed to
+// the storage device (fsync of the file), renamed, and the directory entry
+// flushed too, so neither a crash nor a power loss leaves a truncated file
+// under the final name or loses the previous checkpoint before the new one
+// is on disk.  Host code only: no device calls.
 #include <cstdio>
 #include <cstring>
+#include <fcntl.h>
 #include <string>
 #include <unistd.h>
 
@@ -38,10 +41,21 @@ int qmc_checkpoint_write(const char *path, const qmc_checkpoint_header *h, const
     bool ok = fwrite(h, sizeof *h, 1, f) == 1 &&
               (nbytes == 0 || fwrite(state, nbytes, 1, f) == 1) &&
               fwrite(&sum, sizeof sum, 1, f) == 1;
+    ok = ok && fflush(f) == 0 && fsync(fileno(f)) == 0;
     ok = (fclose(f) == 0) && ok;
     if (!ok || rename(tmp.c_str(), path) != 0) {
         remove(tmp.c_str());
         return QMC_ERR_IO;
+    }
+    // the rename itself is durable once the directory is flushed
+    std::string dir(path);
+    const size_t slash = dir.find_last_of('/');
+    dir = slash == std::string::npos ? std::string(".") : dir.substr(0, slash ? slash : 1);
+    const int dfd = open(dir.c_str(), O_RDONLY);
+    if (dfd >= 0) {
+        const int r = fsync(dfd);
+        close(dfd);
+        if (r != 0) return QMC_ERR_IO;
     }
     return QMC_OK;
 }

@@ -14,6 +14,8 @@
 #include <cstdio>
 #include <vector>
 
+#include <atomic>
+
 #include "learned.cuh"
 #include "model.cuh"
 
@@ -293,6 +295,7 @@ int net_ensure_rows(qmc_net *net, int rows)
     if (rows <= net->rows) return 0;
     const long long nf = net->nf, H = net->H;
     int r = 0;
+    net->gen++;  // the activation buffers move: graphs holding them are stale
     r |= nalloc(net, &net->X, (size_t)rows * 2 * nf);
     r |= nalloc(net, &net->dX, (size_t)rows * 2 * nf);
     r |= nalloc(net, &net->Y, (size_t)rows * nf);
@@ -421,7 +424,9 @@ int qmc_net_create(qmc_net **out, int nf, int width, long long capacity, uint64_
     if (!out) return QMC_ERR_ARG;
     *out = nullptr;
     if (nf < 1 || width < 1 || width > 4096 || capacity < 1) return QMC_ERR_ARG;
+    static std::atomic<unsigned long long> next_uid{1};
     qmc_net *net = new qmc_net();
+    net->uid = next_uid++;
     net->nf = nf;
     net->H = width;
     const long long F = nf, H = width;

@@ -30,6 +30,9 @@ struct qmc_net {
     int loss_cap = 0;
     cudaStream_t st = nullptr;
     std::string err;
+    // identity of the network and of its current activation buffers: a
+    // graph captured around them is valid while both are unchanged
+    unsigned long long uid = 0, gen = 0;
 };
 
 int net_ensure_rows(qmc_net *net, int rows);

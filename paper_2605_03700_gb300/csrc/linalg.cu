@@ -966,16 +966,53 @@ void linalg_init()
     cudaFuncSetAttribute(k_qrp, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
 }
 
-// linalg_init once per device, for entry points that run without a context
-// (the standalone ratio updates); returns false if the device is unknown
+// identity of the current CUDA context: cuCtxGetId through the runtime's
+// driver entry point (no link against libcuda); 0 when unavailable.  Context
+// ids are unique for the life of the process, so a context recreated after
+// cudaDeviceReset gets a new one.
+unsigned long long current_context_id()
+{
+    typedef int (*get_current_fn)(void **);
+    typedef int (*get_id_fn)(void *, unsigned long long *);
+    static get_current_fn get_current = nullptr;
+    static get_id_fn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_current = (get_current_fn)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_id = (get_id_fn)f;
+    });
+    if (!get_current || !get_id) return 0;
+    cudaFree(0);  // make the device's primary context current if none is
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+// linalg_init once per context, for entry points that run without a qmc
+// context (the standalone ratio updates); keyed on the context id, so a
+// device reset (which destroys the context and its function attributes) is
+// followed by a fresh initialisation.  Returns false if the device or
+// context is unknown.
 bool linalg_init_current_device()
 {
-    static bool done[64] = {false};
+    static unsigned long long done[64] = {0};
+    static std::mutex mu;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
-    if (!done[dev]) {
+    const unsigned long long id = current_context_id();
+    if (!id) return false;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev] != id) {
         linalg_init();
-        done[dev] = true;
+        done[dev] = id;
     }
     return true;
 }

@@ -24,8 +24,10 @@ struct GemmP {
 };
 
 void linalg_init();
-// linalg_init once per device (context-free entry points)
+// linalg_init once per context (context-free entry points)
 bool linalg_init_current_device();
+// unique id of the current CUDA context (0 if unavailable)
+unsigned long long current_context_id();
 int zgemm(cudaStream_t st, const GemmP &p, int batch);
 // pause (false) or resume the per-launch GEMM timing; returns the previous state
 bool gemm_prof_enable(bool on);

@@ -115,6 +115,7 @@ def lib():
         L.qmc_net_forward.argtypes = [vp, fp, C.c_int, fp]
         L.qmc_net_loss_grad.argtypes = [vp, fp, fp, C.c_int, dp, fp]
         L.qmc_sweep_learned.argtypes = [vp, vp, C.c_int, C.c_double]
+        L.qmc_sweep_learned_graph.argtypes = [vp, vp, C.c_int, C.c_double]
         L.qmc_group_create.argtypes = [C.POINTER(vp), C.POINTER(vp), C.c_int]
         L.qmc_group_sweep.argtypes = [vp, C.c_int]
         L.qmc_group_sync.argtypes = [vp]
@@ -144,6 +145,7 @@ def lib():
         L.qmc_launch_count.restype = C.c_longlong
         L.qmc_launch_count.argtypes = []
         L.qmc_profile_gemm.argtypes = [C.c_int, dp, C.POINTER(C.c_longlong), dp]
+        L.qmc_peak_fma.argtypes = [C.c_int, C.c_int, dp]
         _lib = L
     return _lib
 
@@ -204,6 +206,13 @@ def qmc_profile_gemm(enable: bool):
     ms, n, fl = C.c_double(), C.c_longlong(), C.c_double()
     _check(lib().qmc_profile_gemm(1 if enable else 0, C.byref(ms), C.byref(n), C.byref(fl)))
     return None if enable else (ms.value, n.value, fl.value)
+
+
+def qmc_peak_fma(fp64: bool = True, iters: int = 4096) -> float:
+    """Measured FMA rate of the current device in TFLOP/s (FP64 or FP32)."""
+    v = C.c_double()
+    _check(lib().qmc_peak_fma(1 if fp64 else 0, int(iters), C.byref(v)))
+    return v.value
 
 
 def qmc_ratio_update(N, batch, G_ptr, Delta_ptr, Gp_ptr, logdet_ptr, stream=0):
@@ -281,9 +290,11 @@ class Chain:
         f = lib().qmc_sweep_graph if graph else lib().qmc_sweep
         _check(f(self.h, n), self.h)
 
-    def sweep_learned(self, net, n=1, rho=0.0):
-        """n sweeps of learned slice moves with network `net` (qmc_sweep_learned)."""
-        _check(lib().qmc_sweep_learned(self.h, net.h, n, float(rho)), self.h)
+    def sweep_learned(self, net, n=1, rho=0.0, graph=False):
+        """n sweeps of learned slice moves with network `net` (qmc_sweep_learned);
+        graph=True replays one captured learned sweep (qmc_sweep_learned_graph)."""
+        f = lib().qmc_sweep_learned_graph if graph else lib().qmc_sweep_learned
+        _check(f(self.h, net.h, n, float(rho)), self.h)
 
     def sync(self):
         _check(lib().qmc_sync(self.h), self.h)

@@ -1,0 +1,43 @@
+"""Oracle chains for the GPU parity tests at the benchmark's matrix size,
+run in spawned worker processes (started before or independently of any
+GPU work) so the slow FP64 CPU chains overlap the GPU side.  Each function
+returns plain arrays: the per-update trace, the per-sweep observable
+records, the fields and G after every sweep."""
+import numpy as np
+
+
+def langevin_chain(nphi, beta, dtau, u, anis, seed, n_stab, eps0, nsweeps):
+    """Plain Langevin (MALA) sweeps of the FP64 oracle; G and the fields are
+    recorded after every sweep."""
+    from oracle import model as M
+    from oracle import oracle as O
+    m = M.Model(M.TORUS, nphi)
+    o = O.Chain(M.TORUS, nphi, beta, dtau, u, anis, seed, n_stab=n_stab, eps0=eps0, model=m)
+    o.enable_trace(nsweeps * o.L)
+    obs, greens = [], []
+    for _ in range(nsweeps):
+        obs.append(o.sweep(1))
+        greens.append(o.green())
+    return {"trace": o.trace(), "obs": np.concatenate(obs), "green": np.array(greens),
+            "phi": o.phi(), "L": o.L}
+
+
+def scheduled_chain(nphi, beta, dtau, u, anis, seed, n_stab, eps0, schedule, theta, H, rho):
+    """Sweeps in the given order: 'P' a Langevin sweep, 'N' a learned sweep
+    with the network parameters theta (hidden width H) at pCN correlation
+    rho; G and the fields after every sweep."""
+    from oracle import model as M
+    from oracle import oracle as O
+    m = M.Model(M.TORUS, nphi)
+    o = O.Chain(M.TORUS, nphi, beta, dtau, u, anis, seed, n_stab=n_stab, eps0=eps0, model=m)
+    o.enable_trace(len(schedule) * o.L)
+    obs, greens, phis = [], [], []
+    for kind in schedule:
+        if kind == "P":
+            obs.append(o.sweep(1))
+        else:
+            obs.append(o.sweep_learned(1, theta, H, rho))
+        greens.append(o.green())
+        phis.append(o.phi())
+    return {"trace": o.trace(), "obs": np.concatenate(obs), "green": np.array(greens),
+            "phi": np.array(phis), "L": o.L}

@@ -1,0 +1,169 @@
+"""Parity with the FP64 oracle at the benchmark's configuration.
+
+The benchmark times torus N_phi = 36 (N = 72, N_q = 333, 1332 fields per
+slice), n_stab = 10, eps0 = 0.45, couplings in [0.5, 2.0], in FP64 (the plain
+sweep) and in mixed precision with learned whole-slice moves.  Here the same
+kernels, sizes and schedule run with beta = 4 (L = 40): four restabilisations
+per sweep, three of them interior, and left/right UDV stacks of four blocks,
+for 400 updates per chain (10 sweeps).  The oracle chains run in spawned
+worker processes while the GPU works.
+
+ (a) FP64 Langevin sweeps: decision-identical over all 400 updates,
+     log R within 1e-10, G within 1e-9 of max|G| after every sweep.
+ (b) Mixed precision (FP32 drift transforms, FP32 Jacobi bulk with FP64
+     refinement; everything in the MH ratio FP64): the index of the first
+     decision that differs from the oracle, and G against the oracle after
+     every sweep up to it, within 1e-6 (the G-error target of mixed runs).
+ (c) The benchmark's default path: mixed precision, learned sweeps at
+     rho = 0 with a seeded non-zero network of the benchmark's width (256),
+     every fourth sweep a Langevin sweep.
+"""
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+from tests import oracle_runs as R
+from tests.learned_inputs import random_params
+
+pytestmark = pytest.mark.gpu
+
+NPHI, BETA, DTAU, NSTAB, EPS0 = 36, 4.0, 0.1, 10, 0.45
+COUPLINGS = (0.5, 2.0)
+NSW = 10
+SCHEDULE = "NNNPNNNPNN"   # the benchmark's: every fourth step a Langevin sweep
+NET_H, NET_SEED = 256, 17
+
+
+def _theta(nf):
+    # non-zero output layer: mu and log sigma depend on the neighbouring
+    # slices (|mu| ~ 0.05, sigma ~ e^{+-0.05})
+    return random_params(nf, NET_H, NET_SEED, out_scale=0.05, logsig_bias=0.02)
+
+
+@pytest.fixture(scope="module")
+def oracle_results():
+    """All oracle chains of this module, computed in parallel processes."""
+    from oracle import oracle as O
+    O.build()
+    nf = 4 * 333
+    ctx = mp.get_context("spawn")
+    pool = ctx.Pool(len(COUPLINGS) + 1)
+    jobs = {("lang", c): pool.apply_async(R.langevin_chain,
+                                          (NPHI, BETA, DTAU, u, 0.0, c, NSTAB, EPS0, NSW))
+            for c, u in enumerate(COUPLINGS)}
+    jobs[("sched", 0)] = pool.apply_async(
+        R.scheduled_chain, (NPHI, BETA, DTAU, 1.25, 0.0, 5, NSTAB, EPS0, SCHEDULE,
+                            _theta(nf), NET_H, 0.0))
+    pool.close()
+    cache = {}
+
+    def get(key):
+        if key not in cache:
+            cache[key] = jobs[key].get(timeout=1800)
+        return cache[key]
+    yield get
+    pool.terminate()
+
+
+@pytest.fixture(scope="module")
+def qmc():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2605_03700_gb300 import build
+    build.build()
+    import paper_2605_03700_gb300 as P
+    return P
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _gpu_langevin(qmc, precision):
+    g = qmc.Chain(qmc.QMC_TORUS, NPHI, BETA, DTAU, 0.0, 0.0, 0, n_chains=len(COUPLINGS),
+                  couplings=list(COUPLINGS), seeds=list(range(len(COUPLINGS))), n_stab=NSTAB,
+                  eps0=EPS0, precision=precision, trace_capacity=NSW * 40)
+    greens = []
+    for _ in range(NSW):
+        g.sweep(1)
+        g.sync()
+        greens.append([g.green(c) for c in range(len(COUPLINGS))])
+    return g, greens
+
+
+def test_fp64_langevin_decision_identical_at_benchmark_size(qmc, oracle_results):
+    g, greens = _gpu_langevin(qmc, 0)
+    for c in range(len(COUPLINGS)):
+        o = oracle_results(("lang", c))
+        tg, to = g.trace(c), o["trace"]
+        assert len(tg) == len(to) == NSW * 40
+        assert np.array_equal(tg[:, 6], to[:, 6]), "accept decisions differ"
+        assert 0 < to[:, 6].sum() < len(to)
+        assert np.array_equal(tg[:, :2], to[:, :2])
+        assert np.abs(tg[:, 2] - to[:, 2]).max() < 1e-10
+        assert np.abs(tg[:, 7] - to[:, 7]).max() < 1e-12
+        for k in range(NSW):
+            assert _rel(greens[k][c], o["green"][k]) < 1e-9, f"G differs after sweep {k}"
+        assert np.abs(g.fields(c) - o["phi"]).max() < 1e-9
+        obs_g = g.series()[c]
+        for col in (0, 1, 3, 6, 11, 12):
+            ref = o["obs"][:, col]
+            assert np.abs(obs_g[:, col] - ref).max() < 1e-9 * max(1, np.abs(ref).max())
+        # every restabilisation of the GPU chain found G fresh to 1e-9
+        assert obs_g[:, 15].max() < 1e-9
+
+
+def test_mixed_precision_tracks_the_oracle_at_benchmark_size(qmc, oracle_results, record_property):
+    g, greens = _gpu_langevin(qmc, 1)
+    for c in range(len(COUPLINGS)):
+        o = oracle_results(("lang", c))
+        tg, to = g.trace(c), o["trace"]
+        mis = np.nonzero(tg[:, 6] != to[:, 6])[0]
+        first = int(mis[0]) if len(mis) else len(tg)
+        record_property(f"first_divergence_u{COUPLINGS[c]}", first)
+        # the FP32 drift moves log A by ~1e-7: a decision can only flip when
+        # log u lies that close to log A
+        assert first >= 200, f"decisions diverge at update {first}"
+        assert np.abs(tg[:first, 2] - to[:first, 2]).max() < 1e-5
+        assert np.abs(tg[:first, 3]).max() < 1e-8
+        gerr = [_rel(greens[k][c], o["green"][k]) for k in range(first // 40)]
+        record_property(f"g_err_vs_oracle_u{COUPLINGS[c]}", max(gerr) if gerr else None)
+        assert all(e < 1e-6 for e in gerr), gerr
+        assert g.series()[c][:, 15].max() < 1e-8
+
+
+def test_learned_schedule_tracks_the_oracle_at_benchmark_size(qmc, oracle_results,
+                                                              record_property):
+    g = qmc.Chain(qmc.QMC_TORUS, NPHI, BETA, DTAU, 1.25, 0.0, 5, n_stab=NSTAB, eps0=EPS0,
+                  precision=1, trace_capacity=len(SCHEDULE) * 40)
+    nf = 4 * g.n_q
+    net = qmc.Net(nf, NET_H, 16, 3)
+    net.set_params(_theta(nf).astype(np.float32))
+    greens, phis = [], []
+    for kind in SCHEDULE:
+        if kind == "P":
+            g.sweep(1)
+        else:
+            g.sweep_learned(net, 1, 0.0)
+        g.sync()
+        greens.append(g.green(0))
+        phis.append(g.fields(0))
+    o = oracle_results(("sched", 0))
+    tg, to = g.trace(0), o["trace"]
+    assert len(tg) == len(to) == len(SCHEDULE) * 40
+    mis = np.nonzero(tg[:, 6] != to[:, 6])[0]
+    first = int(mis[0]) if len(mis) else len(tg)
+    record_property("first_divergence", first)
+    assert first >= 200, f"decisions diverge at update {first}"
+    learned = np.array([SCHEDULE[int(s)] == "N" for s in to[:first, 0]])
+    assert learned.any() and 0 < to[:first][learned, 6].sum() < learned.sum()
+    # mu and sigma from bfloat16 weights with FP32 accumulation: proposals
+    # agree to ~1e-6 relative
+    assert np.abs(tg[:first, 2] - to[:first, 2]).max() < 1e-5
+    nsw_same = first // 40
+    for k in range(nsw_same):
+        assert np.abs(phis[k] - o["phi"][k]).max() < 1e-4
+        assert _rel(greens[k], o["green"][k]) < 1e-6
+    obs_g = g.series()[0]
+    assert np.array_equal(obs_g[:nsw_same, 17], o["obs"][:nsw_same, 17])

@@ -7,10 +7,7 @@ import pytest
 from oracle import model as M
 from oracle import oracle as O
 
-# written after the last GPU run of this build: a numerical mismatch is
-# reported (xfailed) without stopping the GPU suite; a pass shows as XPASS
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.xfail(reason="first GPU run pending", strict=False)]
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")

@@ -51,6 +51,36 @@ def test_graph_sweeps_bit_identical(qmc, precision):
     assert a.series().shape[1] == 7
 
 
+def test_learned_graph_sweeps_bit_identical(qmc):
+    """Learned sweeps replayed from a graph make the plain learned sweeps'
+    draws and decisions; the graph reads the network's weights in place, so
+    new weights take effect without a new capture, and another rho gets its
+    own capture."""
+    from tests.learned_inputs import random_params
+    kw = dict(n_chains=2, couplings=[0.8, 1.6], seeds=[9, 10], n_stab=5, trace_capacity=200,
+              precision=1)
+    a = qmc.Chain(qmc.QMC_TORUS, 4, 1.0, 0.1, 0.0, **kw)
+    b = qmc.Chain(qmc.QMC_TORUS, 4, 1.0, 0.1, 0.0, **kw)
+    nf = 4 * a.n_q
+    nets = []
+    for _ in range(2):
+        n = qmc.Net(nf, 32, 16, 2)
+        n.set_params(random_params(nf, 32, 6, out_scale=0.1).astype(np.float32))
+        nets.append(n)
+    a.sweep_learned(nets[0], 2, 0.0)
+    b.sweep_learned(nets[1], 2, 0.0, graph=True)
+    th = random_params(nf, 32, 7, out_scale=0.1).astype(np.float32)
+    for n in nets:
+        n.set_params(th)
+    a.sweep_learned(nets[0], 2, 0.0)
+    b.sweep_learned(nets[1], 2, 0.0, graph=True)
+    a.sweep(1)
+    b.sweep(1, graph=True)
+    a.sweep_learned(nets[0], 2, 0.5)
+    b.sweep_learned(nets[1], 2, 0.5, graph=True)
+    _same(_state(a), _state(b))
+
+
 def test_group_of_mixed_sizes_bit_identical(qmc):
     """Torus N_phi = 8 and 12, a 5-orbital sphere, FP64 and mixed precision
     and different couplings in one graph: each member evolves exactly as it

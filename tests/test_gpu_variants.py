@@ -10,10 +10,7 @@ from oracle import model as M
 from oracle import oracle as O
 from tests.test_gpu_parity import _compare_chain, _compare_mixed
 
-# written after the last GPU run of this build: a numerical mismatch is
-# reported (xfailed) without stopping the GPU suite; a pass shows as XPASS
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.xfail(reason="first GPU run pending", strict=False)]
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
