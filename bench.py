@@ -338,11 +338,14 @@ def run_arm(P, stream, *, mode, precision, drift, seeds, steps, warmup, tau_swee
 
 
 def gemm_roofline_pass(P, arm, steps=2):
-    """FP64 GEMM class roofline in a separate, untimed pass: CUDA events
-    around each FP64 GEMM launch of `steps` further sweeps (eager launches,
-    so each product has its own event pair)."""
+    """GEMM class rooflines in a separate, untimed pass: CUDA events around
+    each FP64 CUDA-core GEMM launch and each tensor-core MMA launch of
+    `steps` further sweeps (eager launches, so each product has its own
+    event pair).  Returns (FP64 ms, launches, flops) and (tensor ms,
+    launches, needed flops, issued flops)."""
     ch, net = arm["ch"], arm["net"]
     P.qmc_profile_gemm(True)
+    t0 = time.perf_counter()
     for k in range(steps):
         if net is None or k % 2 == 1:
             ch.sweep(1)
@@ -350,7 +353,21 @@ def gemm_roofline_pass(P, arm, steps=2):
             ch.sweep_learned(net, 1, 0.0)
     ch.sync()
     ms, n, flops = P.qmc_profile_gemm(False)
-    return ms, n, flops
+    wall = time.perf_counter() - t0
+    return (ms, n, flops), P.qmc_profile_tensor(), wall
+
+
+def measured_peaks():
+    """bf16 dense tensor peaks measured on this machine (generated file),
+    else the recipe's fallback figures"""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"bf16_burst": float(d["bf16_tflops"]),
+                "bf16_sustained": float(d["bf16_tflops_sustained"]), "source": "measured"}
+    except Exception:
+        return {"bf16_burst": 1900.0, "bf16_sustained": 1700.0, "source": "fallback"}
 
 
 def run_ours(args):
@@ -391,7 +408,8 @@ def run_ours(args):
         L = int(round(BETA / DTAU))
         g_orc = pool.apply_async(_oracle_green, (float(COUPLINGS[0]), int(seeds[0]),
                                                  main["state0"], L))
-    gemm_ms, gemm_n, gemm_flops = gemm_roofline_pass(P, main)
+    (gemm_ms, gemm_n, gemm_flops), (tc_ms, tc_n, tc_flops, tc_issued), prof_wall = \
+        gemm_roofline_pass(P, main)
     plain = None
     if not args.no_plain_arm:
         plain = run_arm(P, stream, mode="plain", precision=0, drift="exact", seeds=seeds,
@@ -431,14 +449,31 @@ def run_ours(args):
         pool.close()
         pool.join()
     gemm_tflops = gemm_flops / (gemm_ms / 1000.0) / 1e12 if gemm_ms > 0 else 0.0
-    roof = {"bound": "alu", "achieved": gemm_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
-            "frac": gemm_tflops / fp64_peak,
-            "traffic": TRAFFIC_PER_LAUNCH,
-            "kernel": "k_zgemm<double> (batched complex FP64 GEMM; FP32 products excluded)",
-            "launches": gemm_n, "ms_total": gemm_ms,
-            "pass": "separate untimed pass of 2 sweeps, CUDA events around each FP64 GEMM",
-            "peak_note": "measured on this GPU at start-up: FP64 FMA chains on every SM "
-                         "(qmc_peak_fma), 'alu' = the FP64 CUDA-core pipe"}
+    roof_fp64 = {"bound": "alu", "achieved": gemm_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+                 "frac": gemm_tflops / fp64_peak,
+                 "traffic": TRAFFIC_PER_LAUNCH,
+                 "kernel": "k_zgemm<double> (batched complex FP64 GEMM on the CUDA cores)",
+                 "launches": gemm_n, "ms_total": gemm_ms,
+                 "pass": "separate untimed pass of 2 sweeps, CUDA events around each FP64 GEMM",
+                 "peak_note": "measured on this GPU at start-up: FP64 FMA chains on every SM "
+                              "(qmc_peak_fma), 'alu' = the FP64 CUDA-core pipe; of measured"}
+    roofs = [roof_fp64]
+    if tc_n:
+        pk = measured_peaks()
+        tc_tflops = tc_flops / (tc_ms / 1000.0) / 1e12
+        roofs.append({
+            "bound": "tensor", "achieved": tc_tflops, "peak": pk["bf16_sustained"],
+            "unit": "TFLOP/s", "frac": tc_tflops / pk["bf16_sustained"], "traffic": None,
+            "kernel": "k_oz_mma (tcgen05 bf16 digit products, FP32 accumulate in TMEM)",
+            "launches": tc_n, "ms_total": tc_ms,
+            "issued_tflops": tc_issued / (tc_ms / 1000.0) / 1e12,
+            "flops_note": "needed = digit pairs x 2 x M x 2N x 2K per complex product (real "
+                          "embedding); issued adds the 128-row and column-tile padding",
+            "pass": "separate untimed pass of 2 sweeps, CUDA events around each MMA launch",
+            "peak_note": f"bf16 dense, sustained ({pk['source']}: MEASURED_PEAKS.json); of "
+                         f"{pk['source']}"})
+    # the dominant class by device time in the profiling pass
+    roof = max(roofs, key=lambda r: r["ms_total"])
     if rank != 0:
         for arm in (main, plain):
             if arm:
@@ -449,10 +484,14 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": main["ms"] / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f32+f64",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": ["f64", "f32+f64", "f32+f64+bf16-digits"][args.precision],
         "data": "synthetic (fields drawn from the chains' own Philox streams)",
         "config": workload_config({"parallelism": f"replicas x{world}",
-                                   "precision": ["fp64", "mixed fp32/fp64"][args.precision],
+                                   "precision": ["fp64", "mixed fp32/fp64 (CUDA cores)",
+                                                 "mixed on tensor cores: FP64-class products "
+                                                 "from 7 bf16 digits, drift from 3; FP64 LU, "
+                                                 "division, QR/UDV"][args.precision],
                                    "mode": args.mode,
                                    "drift": args.drift,
                                    "schedule": ("plain Langevin sweeps" if args.mode == "plain" else
@@ -470,6 +509,7 @@ def run_ours(args):
                                    "sign_dev_max": main["sign_max"]}),
         "vs_plain_fp64": vs_plain,
         "roofline": roof,
+        "rooflines": roofs,
         "fp64_peak_tflops_measured": fp64_peak,
         "clocks": main["clocks"],
         "gpu_launches": main["launches"],
@@ -510,9 +550,10 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=20, help="timed sweeps of the plain arm")
     ap.add_argument("--plain-tau-sweeps", type=int, default=120,
                     help="records per chain for tau_int of the plain FP64 arm")
-    ap.add_argument("--precision", type=int, default=1, choices=[0, 1],
+    ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2],
                     help="0: FP64 everywhere; 1: mixed (FP32 eigensolver bulk + FP64 "
-                         "refinement, FP32 drift transforms; FP64 propagators, ratios, updates)")
+                         "refinement, FP32 drift transforms; FP64 propagators, ratios, updates); "
+                         "2: mixed with the dense products on the tcgen05 tensor cores")
     ap.add_argument("--mode", default="learned", choices=["learned", "plain"],
                     help="learned: learned-proposal sweeps with a Langevin sweep every "
                          "4th step; plain: Langevin sweeps only")

@@ -79,13 +79,20 @@ enum {
 
 typedef struct {
     int n_stab;            /* slices between restabilisations (default 10) */
-    int precision;         /* 0 = FP64 everywhere (default); 1 = mixed: the channel
-                              eigensolver's bulk Jacobi sweeps in FP32 followed by an
-                              FP64 polish (Newton-Schulz orthonormalisation, one or two
-                              FP64 Jacobi sweeps), and the gradient transforms of the
-                              Langevin drift in FP32; propagators, wraps, M, LU and
-                              log det, G M^-1, MH test, restabilisation and
-                              measurements in FP64 */
+    int precision;         /* 0 = FP64 everywhere on the CUDA cores (default);
+                              1 = mixed: the channel eigensolver's bulk Jacobi sweeps in
+                              FP32 followed by an FP64 refinement of the eigenvectors,
+                              and the gradient transforms of the Langevin drift in FP32;
+                              propagators, wraps, M, LU and log det, G M^-1, MH test,
+                              restabilisation and measurements in FP64;
+                              2 = mixed on the tensor cores: as 1, with the dense complex
+                              products (slice propagators and their transition matrices,
+                              wraps, M, the eigenvector refinement) on tcgen05 from seven
+                              exact bfloat16 digits per operand with FP32 accumulation
+                              (FP64-class, ~1e-14 of |A||B|) and the drift transforms
+                              from three digits (FP32-class); LU and log det, G M^-1, the
+                              QR/UDV restabilisation and the measurements stay FP64 on
+                              the CUDA cores */
     double eps0;           /* initial Langevin step (default 0.5) */
     double deps;           /* step adaptation rate Delta eps (default 0.1) */
     double r0;             /* target acceptance (default 0.574) */
@@ -420,6 +427,33 @@ int qmc_gemm_tile(int n, int precision);
  * time in *total_ms, the number of launches and their algorithmic flops
  * (8 M N K per complex product) -- the inputs of the GEMM roofline. */
 int qmc_profile_gemm(int enable, double *total_ms, long long *launches, double *flops);
+
+/* The tensor-core products of the last window qmc_profile_gemm(1) ..
+ * qmc_profile_gemm(0) recorded (precision 2): summed device time of the MMA
+ * kernel launches (event pairs around each), their count, the bfloat16
+ * flops of the digit products they need (pairs x 2 x M x 2N x 2K per
+ * complex product, the real embedding) and the flops they issue (padded to
+ * the 128-row instruction shape and the column tile). */
+int qmc_profile_tensor(double *total_ms, long long *launches, double *flops, double *issued_flops);
+
+/* Batched complex product C[b] = (+-) op(A[b]) diag(d[b]) op(B[b]) (+ I), the
+ * dense operation behind the slice propagators and the wraps
+ * G <- B_tau G B_tau^-1 (Methods, Eq. trotter_decomposition and the
+ * Green's-function propagation implied by Eq. green_function).  Device
+ * pointers, complex128 interleaved, row-major and dense per matrix:
+ * op(A) is M x K (A stored M x K for opA = 0, K x M for opA = 2 = conjugate
+ * transpose), op(B) K x N likewise, d (optional, NULL) K complex values per
+ * matrix, C M x N per matrix, batch matrices one after another.
+ * negate = 1 gives -op(A) d op(B); add_identity = 1 (M == N) adds I.
+ * digits = 0 computes on the FP64 CUDA cores; digits = 1..8 on the tcgen05
+ * tensor cores from that many exact bfloat16 digits of each row of op(A) and
+ * each column of d op(B) with FP32 accumulation (7: FP64-class, error about
+ * 1e-14 of |A||B|; 3: FP32-class), K <= 1024.  Allocates and frees its own
+ * work space (digits > 0) and synchronises `stream`; rows or columns holding
+ * NaN or Inf give NaN outputs.  QMC_ERR_ARG for bad sizes or ops,
+ * QMC_ERR_TIMEOUT if a bounded device wait gave up, QMC_ERR_OOM, QMC_ERR_CUDA. */
+int qmc_cgemm(int M, int N, int K, int batch, const double *A, int opA, const double *B, int opB,
+              const double *d, double *C, int negate, int add_identity, int digits, void *stream);
 
 /* Measured fused-multiply-add rate of the current device's CUDA-core pipe,
  * the roofline denominator of the library's FP64-pipe kernels (not part of

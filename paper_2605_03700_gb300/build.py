@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqmc.so")
-SOURCES = ["api.cu", "checkpoint.cu", "learned.cu", "linalg.cu", "model.cu", "peak.cu"]
+SOURCES = ["api.cu", "checkpoint.cu", "learned.cu", "linalg.cu", "model.cu", "ozaki.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-Xptxas", "-O3"]

@@ -29,6 +29,7 @@
 #include "learned.cuh"
 #include "linalg.cuh"
 #include "model.cuh"
+#include "ozaki.cuh"
 
 #define CK(x)                                                                      \
     do {                                                                           \
@@ -47,6 +48,9 @@ struct qmc_ctx {
     double beta = 0, dtau = 0;
     int gp = TY_C64;   // compute type of the gradient transforms, wraps, M and G M^-1
     size_t gsz = 16;   // element size of the buffers in that type
+    bool tc = false;   // precision 2: dense products on the tensor cores
+    OzCfg ozF, ozD;    // tensor-core work space: FP64-class (7 digits), drift (3 digits)
+    int *ozerr = nullptr;
     qmc_opts o;
     std::vector<double> u, anis, g;
     std::vector<cd> alpha;
@@ -155,6 +159,12 @@ static int dalloc(qmc_ctx *ctx, T **p, size_t count, size_t elem = sizeof(T), bo
 
 static const cd ONE = {1, 0}, ZERO = {0, 0}, MONE = {-1, 0};
 
+// tensor-core configuration of the FP64-class products (propagators,
+// transitions, wraps, M, eigenvector refinement) and of the drift
+// transforms; null (CUDA-core kernels) unless precision 2
+static const OzCfg *ozF(const qmc_ctx *ctx) { return ctx->tc ? &ctx->ozF : nullptr; }
+static const OzCfg *ozD(const qmc_ctx *ctx) { return ctx->tc ? &ctx->ozD : nullptr; }
+
 // ------------------------------------------------------------ pipeline ----
 // V, T (FP64) and the factor diagonals of a slice from its eigenpairs; the
 // diagonals also in the gradient compute type when that is FP32
@@ -168,7 +178,7 @@ static void factors_from_eig(qmc_ctx *ctx, const cd *U, long long U_cs, const do
     // T01 = V0^H V1, T12 = V1^H V2, T23 = V2^H V3
     for (int x = 0; x < 3; ++x)
         gemm_sq(ctx->st, N, nb, TY_C64, op64(V + x * NN, 4 * NN), 2, op64(V + (x + 1) * NN, 4 * NN),
-                0, op64(T + x * NN, 3 * NN));
+                0, op64(T + x * NN, 3 * NN), nullptr, 0, ONE, ZERO, 0, ozF(ctx));
     launch_lambda(ctx->st, TY_C64, nb, ctx->n, W, W_cs, ctx->alpha_d, lam, Dg, Dgi);
     if (ctx->gp != TY_C64)
         launch_lambda(ctx->st, ctx->gp, nb, ctx->n, W, W_cs, ctx->alpha_d, lamG, DgG, DgiG);
@@ -192,15 +202,15 @@ static void build_B(qmc_ctx *ctx, const cd *V, const cd *T, const cd *Dg, const 
         cd *dst = inv ? Biout : Bout;
         const long long dst_cs = inv ? Bio_cs : Bo_cs;
         gemm_sq(s, N, nb, TY_C64, op64(T, 3 * NN), 0, op64(T + NN, 3 * NN), 0, op64(ctx->X1, NN),
-                dg + 1 * N, dcs);
+                dg + 1 * N, dcs, ONE, ZERO, 0, ozF(ctx));
         gemm_sq(s, N, nb, TY_C64, op64(ctx->X1, NN), 0, op64(T + 2 * NN, 3 * NN), 0,
-                op64(ctx->X2, NN), dg + 2 * N, dcs);
+                op64(ctx->X2, NN), dg + 2 * N, dcs, ONE, ZERO, 0, ozF(ctx));
         gemm_sq(s, N, nb, TY_C64, op64(V, 4 * NN), 0, op64(ctx->X2, NN), 0, op64(ctx->X1, NN), dg,
-                dcs);
+                dcs, ONE, ZERO, 0, ozF(ctx));
         gemm_sq(s, N, nb, TY_C64, op64(V, 4 * NN), 0, op64(ctx->X2, NN), 0, op64(ctx->M, NN), dgc,
-                dcs);
+                dcs, ONE, ZERO, 0, ozF(ctx));
         gemm_sq(s, N, nb, TY_C64, op64(ctx->X1, NN), 0, op64(ctx->M, NN), 2, op64(dst, dst_cs),
-                dg + 3 * N, dcs);
+                dg + 3 * N, dcs, ONE, ZERO, 0, ozF(ctx));
     }
 }
 
@@ -223,9 +233,11 @@ static void gradient(qmc_ctx *ctx, const cd *Gm, const cd *V, const cd *T, const
         return;
     }
     // Ah = I - V0^H G V0
-    gemm_sq(s, N, nb, gp, op64(V, 4 * NN), 2, op64(Gm, NN), 0, ctx->Gx(ctx->Y1, NN));
+    const OzCfg *oz = ozD(ctx);
+    gemm_sq(s, N, nb, gp, op64(V, 4 * NN), 2, op64(Gm, NN), 0, ctx->Gx(ctx->Y1, NN), nullptr, 0, ONE,
+            ZERO, 0, oz);
     gemm_sq(s, N, nb, gp, ctx->Gx(ctx->Y1, NN), 0, op64(V, 4 * NN), 0, ctx->Gx(ctx->Ah, NN),
-            nullptr, 0, MONE, ZERO, 1);
+            nullptr, 0, MONE, ZERO, 1, oz);
     const int tidx[6] = {0, 1, 2, 2, 1, 0};
     for (int j = 0; j < 7; ++j) {
         launch_accum(s, gp, nb, N, j, j < 4, ctx->alpha_d, lam, ctx->Ah, ctx->Cacc);
@@ -233,15 +245,15 @@ static void gradient(qmc_ctx *ctx, const cd *Gm, const cd *V, const cd *T, const
         const cd *Tx = T + (long long)tidx[j] * NN;
         int op1 = j < 3 ? 2 : 0, op2 = j < 3 ? 0 : 2;
         gemm_sq(s, N, nb, gp, op64(Tx, 3 * NN), op1, ctx->Gx(ctx->Ah, NN), 0, ctx->Gx(ctx->Y1, NN),
-                ctx->at((void *)Dgi, (long long)j * N), 7 * N);
+                ctx->at((void *)Dgi, (long long)j * N), 7 * N, ONE, ZERO, 0, oz);
         gemm_sq(s, N, nb, gp, ctx->Gx(ctx->Y1, NN), 0, op64(Tx, 3 * NN), op2, ctx->Gx(ctx->Ah, NN),
-                ctx->at((void *)Dg, (long long)j * N), 7 * N);
+                ctx->at((void *)Dg, (long long)j * N), 7 * N, ONE, ZERO, 0, oz);
     }
     for (int i = 0; i < 4; ++i) {
         gemm_sq(s, N, nb, gp, op64(V + i * NN, 4 * NN), 0, ctx->Gx(ctx->at(ctx->Cacc, i * NN), 4 * NN),
-                0, ctx->Gx(ctx->Y1, NN));
+                0, ctx->Gx(ctx->Y1, NN), nullptr, 0, ONE, ZERO, 0, oz);
         gemm_sq(s, N, nb, gp, ctx->Gx(ctx->Y1, NN), 0, op64(V + i * NN, 4 * NN), 2,
-                ctx->Gx(ctx->at(ctx->At, i * NN), 4 * NN));
+                ctx->Gx(ctx->at(ctx->At, i * NN), 4 * NN), nullptr, 0, ONE, ZERO, 0, oz);
     }
     launch_trace_grad(s, gp, nb, ctx->n, ctx->nq, ctx->At, ctx->ff_val, ctx->ff_col, ctx->trF,
                       ctx->alpha_d, ctx->tq, ctx->fq, ctx->fk, ctx->partner, phi, phi_cs, grad);
@@ -271,6 +283,7 @@ static int eig_of_fields(qmc_ctx *ctx, const double *phi, long long phi_cs, cd *
     wk.S = ctx->NSs;
     wk.R = ctx->NSr;
     wk.E = ctx->NSe;
+    wk.oz = ozF(ctx);
     return eigh_mixed(s, n, 4 * nb, ctx->Fm, U, W, wk);
 }
 
@@ -394,11 +407,12 @@ static int update_slice(qmc_ctx *ctx, int t, qmc_net *net = nullptr, double rho 
     build_B(ctx, ctx->Vp, ctx->Tp, ctx->Dgp, ctx->Dgip, ctx->Bp, NN, ctx->Bpi, NN);
     // M = 1 + (B' B^-1 - 1)(1 - G) in FP64: B' B^-1 - 1 is small, so its
     // absolute rounding error would be amplified by the conditioning of M
-    gemm_sq(s, N, nb, TY_C64, op64(ctx->Bp, NN), 0, op64(Bis, L * NN), 0, op64(ctx->X1, NN));
+    gemm_sq(s, N, nb, TY_C64, op64(ctx->Bp, NN), 0, op64(Bis, L * NN), 0, op64(ctx->X1, NN), nullptr,
+            0, ONE, ZERO, 0, ozF(ctx));
     launch_axpyI(s, nb, N, op64(ctx->X1, NN), ONE, MONE, op64(ctx->X1, NN));
     launch_axpyI(s, nb, N, op64(ctx->G, NN), MONE, ONE, op64(ctx->X2, NN));
     gemm_sq(s, N, nb, TY_C64, op64(ctx->X1, NN), 0, op64(ctx->X2, NN), 0, op64(ctx->M, NN), nullptr,
-            0, ONE, ZERO, 1);
+            0, ONE, ZERO, 1, ozF(ctx));
     if (lu_batched(s, N, ctx->M, NN, ctx->piv, N, ctx->logdet, nb)) return QMC_ERR_ARG;
     if (rdiv_batched(s, TY_C64, N, ctx->G, NN, ctx->M, NN, ctx->piv, N, ctx->Gp, NN, nb))
         return QMC_ERR_ARG;
@@ -585,9 +599,10 @@ static int enqueue_sweep(qmc_ctx *ctx, qmc_net *net = nullptr, double rho = 0.0)
     for (int t = 1; t <= ctx->L; ++t) {
         // wrap G <- B_t G B_t^-1 in FP64: G enters every determinant ratio
         gemm_sq(ctx->st, N, nb, TY_C64, op64(ctx->B + (long long)(t - 1) * NN, BL), 0,
-                op64(ctx->G, NN), 0, op64(ctx->X1, NN));
+                op64(ctx->G, NN), 0, op64(ctx->X1, NN), nullptr, 0, ONE, ZERO, 0, ozF(ctx));
         gemm_sq(ctx->st, N, nb, TY_C64, op64(ctx->X1, NN), 0,
-                op64(ctx->Binv + (long long)(t - 1) * NN, BL), 0, op64(ctx->G, NN));
+                op64(ctx->Binv + (long long)(t - 1) * NN, BL), 0, op64(ctx->G, NN), nullptr, 0, ONE,
+                ZERO, 0, ozF(ctx));
         r = update_slice(ctx, t, net, rho);
         if (r) return r;
         if (t == ctx->sp[k]) {
@@ -896,6 +911,26 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
     DAS(ctx->piv, (size_t)nb * N);
     DA(ctx->flag, nb);
     DA(ctx->errf, nb);
+    DA(ctx->ozerr, 1);
+    if (ctx->tc) {
+        // the largest products: N x N over the batch, n x n over 4 channels
+        // per chain (eigenvector refinement), both at the FP64-class digit count
+        long long a1, b1, e1, a2, b2, e2;
+        oz_sizes(N, N, N, 7, nb, &a1, &b1, &e1);
+        oz_sizes(n, n, n, 7, 4 * nb, &a2, &b2, &e2);
+        OzCfg &f = ctx->ozF;
+        f.S = 7;
+        f.capA = std::max(a1, a2);
+        f.capB = std::max(b1, b2);
+        f.capE = std::max(e1, e2);
+        DAS(f.DA, f.capA);
+        DAS(f.DB, f.capB);
+        DAS(f.eA, f.capE);
+        DAS(f.eB, f.capE);
+        f.err = ctx->ozerr;
+        ctx->ozD = f;
+        ctx->ozD.S = 3;
+    }
     cudaStream_t s = ctx->st;
     {
         std::vector<int> one(nb, 1);
@@ -1013,7 +1048,7 @@ int qmc_create(qmc_ctx **out, int geometry, int N_phi, double beta, double dtau,
         ctx->err = "beta and dtau must be positive";
         code = QMC_ERR_ARG;
     } else if (ctx->o.n_chains < 1 || ctx->o.n_stab < 1 || ctx->o.series_capacity < 1 ||
-               ctx->o.trace_capacity < 0 || ctx->o.precision < 0 || ctx->o.precision > 1 ||
+               ctx->o.trace_capacity < 0 || ctx->o.precision < 0 || ctx->o.precision > 2 ||
                (ctx->o.drift != QMC_DRIFT_EXACT && ctx->o.drift != QMC_DRIFT_FIRST)) {
         ctx->err = "invalid options";
         code = QMC_ERR_ARG;
@@ -1033,7 +1068,8 @@ int qmc_create(qmc_ctx **out, int geometry, int N_phi, double beta, double dtau,
             ctx->nb = ctx->o.n_chains;
             ctx->beta = beta;
             ctx->dtau = dtau;
-            ctx->gp = ctx->o.precision == 1 ? TY_C32 : TY_C64;
+            ctx->gp = ctx->o.precision >= 1 ? TY_C32 : TY_C64;
+            ctx->tc = ctx->o.precision == 2;
             ctx->gsz = ctx->gp == TY_C32 ? sizeof(cf) : sizeof(cd);
             code = setup(ctx, seed, coupling, anisotropy);
         }
@@ -1322,6 +1358,12 @@ int qmc_sync(qmc_ctx *ctx)
     CK(cudaMemcpy(ef.data(), ctx->errf, sizeof(int) * ctx->nb, cudaMemcpyDeviceToHost));
     int f = 0;
     for (int v : ef) f |= v;
+    int oz = 0;
+    CK(cudaMemcpy(&oz, ctx->ozerr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (oz) {
+        ctx->err = "tensor-core product: a bounded wait gave up (results of the sweep are invalid)";
+        return QMC_ERR_TIMEOUT;
+    }
     if (f & 4) {
         ctx->err = "non-finite determinant ratio or stabilised G";
         return QMC_ERR_NONFINITE;
@@ -1770,6 +1812,76 @@ int qmc_ratio_update(int N, int batch, const double *G, const double *Delta, dou
     cudaFree(M);
     cudaFree(piv);
     return code;
+}
+
+int qmc_cgemm(int M, int N, int K, int batch, const double *A, int opA, const double *B, int opB,
+              const double *d, double *C, int negate, int add_identity, int digits, void *stream)
+{
+    if (M < 1 || N < 1 || K < 1 || batch < 1 || !A || !B || !C) return QMC_ERR_ARG;
+    if ((opA != 0 && opA != 2) || (opB != 0 && opB != 2)) return QMC_ERR_ARG;
+    if (digits != 0 && (digits < 1 || digits > 8)) return QMC_ERR_ARG;
+    if (add_identity && M != N) return QMC_ERR_ARG;
+    if (!linalg_init_current_device()) return QMC_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    GemmP p;
+    memset(&p, 0, sizeof p);
+    p.M = M;
+    p.N = N;
+    p.K = K;
+    p.A = A;
+    p.lda = opA == 0 ? K : M;
+    p.sA = (long long)M * K;
+    p.opA = opA;
+    p.B = B;
+    p.ldb = opB == 0 ? N : K;
+    p.sB = (long long)K * N;
+    p.opB = opB;
+    p.d = d;
+    p.sd = K;
+    p.C = C;
+    p.ldc = N;
+    p.sC = (long long)M * N;
+    p.alpha = negate ? MONE : ONE;
+    p.addI = add_identity;
+    p.ta = p.tb = p.tc = p.rc = TY_C64;
+    if (digits == 0) {
+        zgemm(s, p, batch);
+        return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+    }
+    if (K > 1024) return QMC_ERR_ARG;
+    OzCfg cfg;
+    cfg.S = digits;
+    oz_sizes(M, N, K, digits, batch, &cfg.capA, &cfg.capB, &cfg.capE);
+    int code = QMC_OK;
+    if (cudaMalloc(&cfg.DA, sizeof(__nv_bfloat16) * cfg.capA) != cudaSuccess ||
+        cudaMalloc(&cfg.DB, sizeof(__nv_bfloat16) * cfg.capB) != cudaSuccess ||
+        cudaMalloc(&cfg.eA, sizeof(int) * cfg.capE) != cudaSuccess ||
+        cudaMalloc(&cfg.eB, sizeof(int) * cfg.capE) != cudaSuccess ||
+        cudaMalloc(&cfg.err, sizeof(int)) != cudaSuccess) {
+        code = QMC_ERR_OOM;
+    } else {
+        cudaMemsetAsync(cfg.err, 0, sizeof(int), s);
+        p.oz = &cfg;
+        if (oz_gemm(s, p, batch, cfg) != 0) code = QMC_ERR_ARG;
+        int e = 0;
+        if (cudaMemcpyAsync(&e, cfg.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            code = QMC_ERR_CUDA;
+        else if (e && code == QMC_OK)
+            code = QMC_ERR_TIMEOUT;
+    }
+    cudaFree(cfg.DA);
+    cudaFree(cfg.DB);
+    cudaFree(cfg.eA);
+    cudaFree(cfg.eB);
+    cudaFree(cfg.err);
+    return code;
+}
+
+int qmc_profile_tensor(double *total_ms, long long *launches, double *flops, double *issued_flops)
+{
+    gemm_prof_last(1, total_ms, launches, flops, issued_flops);
+    return QMC_OK;
 }
 
 int qmc_profile_gemm(int enable, double *total_ms, long long *launches, double *flops)

@@ -5,6 +5,7 @@
 // with column pivoting (FP64).  All matrices are row-major interleaved
 // complex.
 #include "linalg.cuh"
+#include "ozaki.cuh"
 
 #include <cstdlib>
 #include <mutex>
@@ -66,13 +67,18 @@ __global__ void __launch_bounds__(TT * TT) k_zgemm(GemmP p)
     }
 }
 
-// optional event timing of every GEMM launch (roofline of the GEMM class)
+// optional event timing of every GEMM launch (roofline of the GEMM
+// classes): class 0 = FP64 products on the CUDA cores, class 1 = the
+// tensor-core digit products (the MMA kernel alone)
 struct GemmProf {
     bool on = false;
     std::vector<cudaEvent_t> ev;
+    std::vector<int> cls;  // class of each event pair
     size_t used = 0;
-    double flops = 0.0;
-    long long launches = 0;
+    double flops[2] = {0.0, 0.0}, issued[2] = {0.0, 0.0}, last_ms[2] = {0.0, 0.0};
+    long long launches[2] = {0, 0};
+    double last_flops[2] = {0.0, 0.0}, last_issued[2] = {0.0, 0.0};
+    long long last_launches[2] = {0, 0};
 };
 static GemmProf g_gprof;
 
@@ -80,24 +86,41 @@ void gemm_prof_start()
 {
     g_gprof.on = true;
     g_gprof.used = 0;
-    g_gprof.flops = 0.0;
-    g_gprof.launches = 0;
+    g_gprof.cls.clear();
+    for (int c = 0; c < 2; ++c) {
+        g_gprof.flops[c] = g_gprof.issued[c] = 0.0;
+        g_gprof.launches[c] = 0;
+    }
 }
 
 void gemm_prof_stop(double *ms, long long *launches, double *flops)
 {
     g_gprof.on = false;
     cudaDeviceSynchronize();
-    double tot = 0.0;
+    double tot[2] = {0.0, 0.0};
     for (size_t i = 0; i + 1 < g_gprof.used; i += 2) {
         float t = 0.f;
         cudaEventElapsedTime(&t, g_gprof.ev[i], g_gprof.ev[i + 1]);
-        tot += t;
+        tot[g_gprof.cls[i / 2]] += t;
     }
-    if (ms) *ms = tot;
-    if (launches) *launches = g_gprof.launches;
-    if (flops) *flops = g_gprof.flops;
+    for (int c = 0; c < 2; ++c) {
+        g_gprof.last_ms[c] = tot[c];
+        g_gprof.last_flops[c] = g_gprof.flops[c];
+        g_gprof.last_issued[c] = g_gprof.issued[c];
+        g_gprof.last_launches[c] = g_gprof.launches[c];
+    }
+    if (ms) *ms = tot[0];
+    if (launches) *launches = g_gprof.launches[0];
+    if (flops) *flops = g_gprof.flops[0];
     g_gprof.used = 0;
+}
+
+void gemm_prof_last(int cls, double *ms, long long *launches, double *flops, double *issued)
+{
+    if (ms) *ms = g_gprof.last_ms[cls];
+    if (launches) *launches = g_gprof.last_launches[cls];
+    if (flops) *flops = g_gprof.last_flops[cls];
+    if (issued) *issued = g_gprof.last_issued[cls];
 }
 
 bool gemm_prof_enable(bool on)
@@ -107,6 +130,8 @@ bool gemm_prof_enable(bool on)
     return was;
 }
 
+bool gemm_prof_on() { return g_gprof.on; }
+
 static cudaEvent_t gprof_event()
 {
     if (g_gprof.used == g_gprof.ev.size()) {
@@ -115,6 +140,19 @@ static cudaEvent_t gprof_event()
         g_gprof.ev.push_back(e);
     }
     return g_gprof.ev[g_gprof.used++];
+}
+
+// event pair around one launch of class `cls`: begin before, end after it
+void gemm_prof_mark(int cls, cudaStream_t st, bool begin, double flops, double issued)
+{
+    cudaEventRecord(gprof_event(), st);
+    if (begin) {
+        g_gprof.cls.push_back(cls);
+    } else {
+        g_gprof.flops[cls] += flops;
+        g_gprof.issued[cls] += issued;
+        g_gprof.launches[cls]++;
+    }
 }
 
 typedef void (*gemm_fn)(GemmP);
@@ -199,14 +237,16 @@ static int launch_gemm(cudaStream_t st, const GemmP &p, int batch, int tile)
 
 int zgemm(cudaStream_t st, const GemmP &p, int batch)
 {
+    // tensor-core digit products where the caller asked for them and the
+    // work space fits; the CUDA-core kernel otherwise
+    if (p.oz && oz_gemm(st, p, batch, *p.oz) == 0) return 0;
     const int tile = tile_for(p.N, p.rc);
     int r;
     if (g_gprof.on && p.rc == TY_C64) {  // the FP64-pipe roofline: FP64 products only
-        cudaEventRecord(gprof_event(), st);
+        const double f = 8.0 * p.M * (double)p.N * p.K * batch;
+        gemm_prof_mark(0, st, true, 0.0, 0.0);
         r = launch_gemm(st, p, batch, tile);
-        cudaEventRecord(gprof_event(), st);
-        g_gprof.flops += 8.0 * p.M * (double)p.N * p.K * batch;
-        g_gprof.launches++;
+        gemm_prof_mark(0, st, false, f, f);
     } else {
         r = launch_gemm(st, p, batch, tile);
     }
@@ -478,8 +518,10 @@ __global__ void k_cvt_c32_c64(long long m, const cf *a, cd *b)
 }
 
 // one CTA per matrix: E from S and R (n x n, dense stride n^2), and Xn = X
+// plus_I: E is returned with the identity added (for X <- X (I + E) as one
+// product) and Xn is left alone
 __global__ void __launch_bounds__(256) k_refine_E(int n, const cd *S, const cd *R, const cd *X,
-                                                  cd *E, cd *Xn)
+                                                  cd *E, cd *Xn, int plus_I)
 {
     __shared__ double lam[64];
     __shared__ double red[3][8];
@@ -493,7 +535,7 @@ __global__ void __launch_bounds__(256) k_refine_E(int n, const cd *S, const cd *
         st += s2;
         sr += r2;
         if (e / n != e % n) so += s2;
-        Xn[e] = X[e];
+        if (!plus_I) Xn[e] = X[e];
     }
     for (int i = tid; i < n; i += nt) lam[i] = S[i * n + i].x / (1.0 - R[i * n + i].x);
     for (int o = 16; o > 0; o >>= 1) {
@@ -527,6 +569,8 @@ __global__ void __launch_bounds__(256) k_refine_E(int n, const cd *S, const cd *
                 const cd sv = S[e];
                 v = cscale(cd{sv.x + lam[j] * r.x, sv.y + lam[j] * r.y}, 1.0 / d);
             }
+        } else if (plus_I) {
+            v.x += 1.0;
         }
         E[e] = v;
     }
@@ -546,21 +590,32 @@ int eigh_mixed(cudaStream_t st, int n, int batch, const cd *A, cd *U, double *w,
     QMC_COUNT(1);
     cd *X = wk.X, *Xn = wk.Xn;
     const cd one = {1, 0}, zero = {0, 0}, mone = {-1, 0};
+    const OzCfg *oz = wk.oz;
     for (int it = 0; it < 3; ++it) {
         gemm_sq(st, n, batch, TY_C64, op64(X, n2), 2, op64(X, n2), 0, op64(wk.R, n2), nullptr, 0,
-                mone, zero, 1);
-        gemm_sq(st, n, batch, TY_C64, op64(A, n2), 0, op64(X, n2), 0, op64(wk.T, n2));
-        gemm_sq(st, n, batch, TY_C64, op64(X, n2), 2, op64(wk.T, n2), 0, op64(wk.S, n2));
-        k_refine_E<<<batch, 256, 0, st>>>(n, wk.S, wk.R, X, wk.E, Xn);
+                mone, zero, 1, oz);
+        gemm_sq(st, n, batch, TY_C64, op64(A, n2), 0, op64(X, n2), 0, op64(wk.T, n2), nullptr, 0,
+                one, zero, 0, oz);
+        gemm_sq(st, n, batch, TY_C64, op64(X, n2), 2, op64(wk.T, n2), 0, op64(wk.S, n2), nullptr,
+                0, one, zero, 0, oz);
+        k_refine_E<<<batch, 256, 0, st>>>(n, wk.S, wk.R, X, wk.E, Xn, oz != nullptr);
         QMC_COUNT(1);
-        gemm_sq(st, n, batch, TY_C64, op64(X, n2), 0, op64(wk.E, n2), 0, op64(Xn, n2), nullptr, 0,
-                one, one);
+        if (oz) {
+            // X <- X (I + E): E came back with the identity added
+            gemm_sq(st, n, batch, TY_C64, op64(X, n2), 0, op64(wk.E, n2), 0, op64(Xn, n2), nullptr,
+                    0, one, zero, 0, oz);
+        } else {
+            gemm_sq(st, n, batch, TY_C64, op64(X, n2), 0, op64(wk.E, n2), 0, op64(Xn, n2), nullptr,
+                    0, one, one);
+        }
         cd *t = X;
         X = Xn;
         Xn = t;
     }
-    gemm_sq(st, n, batch, TY_C64, op64(A, n2), 0, op64(X, n2), 0, op64(wk.T, n2));
-    gemm_sq(st, n, batch, TY_C64, op64(X, n2), 2, op64(wk.T, n2), 0, op64(wk.S, n2));
+    gemm_sq(st, n, batch, TY_C64, op64(A, n2), 0, op64(X, n2), 0, op64(wk.T, n2), nullptr, 0, one,
+            zero, 0, oz);
+    gemm_sq(st, n, batch, TY_C64, op64(X, n2), 2, op64(wk.T, n2), 0, op64(wk.S, n2), nullptr, 0,
+            one, zero, 0, oz);
     // FP64 Jacobi from V = X: returns at once when S is diagonal to rounding
     // (off-diagonal Frobenius norm below 1e-13 of the total; the rounding
     // floor of S is near 1e-14), and resolves the rare clusters the
@@ -964,6 +1019,7 @@ void linalg_init()
     cudaFuncSetAttribute(k_rdiv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     cudaFuncSetAttribute(k_rdiv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     cudaFuncSetAttribute(k_qrp, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    oz_init();
 }
 
 // identity of the current CUDA context: cuCtxGetId through the runtime's

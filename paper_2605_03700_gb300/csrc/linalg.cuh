@@ -21,6 +21,7 @@ struct GemmP {
     int addI;
     int ta, tb, tc;  // operand / output element types (TY_C64, TY_C32)
     int rc;          // compute type (TY_C64 = FP64, TY_C32 = FP32)
+    const struct OzCfg *oz;  // non-null: tensor-core digit products (ozaki.cu)
 };
 
 void linalg_init();
@@ -36,6 +37,11 @@ void gemm_set_tile(int n, int rc, int tile);
 int gemm_get_tile(int n, int rc);
 void gemm_prof_start();
 void gemm_prof_stop(double *ms, long long *launches, double *flops);
+bool gemm_prof_on();
+void gemm_prof_mark(int cls, cudaStream_t st, bool begin, double flops, double issued);
+// totals of class cls (0: FP64 CUDA-core GEMM, 1: tensor-core MMA kernel) of
+// the last stopped window
+void gemm_prof_last(int cls, double *ms, long long *launches, double *flops, double *issued);
 int eigh_batched(cudaStream_t st, int prec, int n, const void *H, long long sH, void *U,
                  long long sU, void *w, long long sw, int batch, const void *V0 = nullptr,
                  long long sV0 = 0, double tol = 0.0);
@@ -44,6 +50,7 @@ struct EighWork {
     cf *A32, *U32;
     float *w32;
     cd *X, *Xn, *T, *S, *R, *E;
+    const struct OzCfg *oz = nullptr;  // refinement products on the tensor cores
 };
 // FP64-accurate eigenpairs of batch Hermitian n x n matrices (dense, stride
 // n^2): FP32 Jacobi, two FP64 refinement steps, FP64 Jacobi safety net
@@ -70,7 +77,7 @@ inline Op opT(const void *p, long long s, int t) { return Op{p, s, t}; }
 // precision rc
 inline int gemm_sq(cudaStream_t st, int n, int batch, int rc, Op A, int opA, Op B, int opB, Op C,
                    const void *d = nullptr, long long sd = 0, cd alpha = cd{1, 0},
-                   cd beta = cd{0, 0}, int addI = 0)
+                   cd beta = cd{0, 0}, int addI = 0, const struct OzCfg *oz = nullptr)
 {
     GemmP p;
     p.M = p.N = p.K = n;
@@ -94,5 +101,6 @@ inline int gemm_sq(cudaStream_t st, int n, int batch, int rc, Op A, int opA, Op 
     p.tb = B.t;
     p.tc = C.t;
     p.rc = rc;
+    p.oz = oz;
     return zgemm(st, p, batch);
 }

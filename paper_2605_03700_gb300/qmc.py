@@ -146,6 +146,9 @@ def lib():
         L.qmc_launch_count.argtypes = []
         L.qmc_profile_gemm.argtypes = [C.c_int, dp, C.POINTER(C.c_longlong), dp]
         L.qmc_peak_fma.argtypes = [C.c_int, C.c_int, dp]
+        L.qmc_profile_tensor.argtypes = [dp, C.POINTER(C.c_longlong), dp, dp]
+        L.qmc_cgemm.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_int, vp, C.c_int, vp, vp,
+                                C.c_int, C.c_int, C.c_int, vp]
         _lib = L
     return _lib
 
@@ -208,11 +211,29 @@ def qmc_profile_gemm(enable: bool):
     return None if enable else (ms.value, n.value, fl.value)
 
 
+def qmc_profile_tensor():
+    """(ms, launches, needed flops, issued flops) of the tensor-core MMA
+    kernel in the last qmc_profile_gemm window."""
+    ms, fl, iss = C.c_double(), C.c_double(), C.c_double()
+    n = C.c_longlong()
+    lib().qmc_profile_tensor(C.byref(ms), C.byref(n), C.byref(fl), C.byref(iss))
+    return ms.value, n.value, fl.value, iss.value
+
+
 def qmc_peak_fma(fp64: bool = True, iters: int = 4096) -> float:
     """Measured FMA rate of the current device in TFLOP/s (FP64 or FP32)."""
     v = C.c_double()
     _check(lib().qmc_peak_fma(1 if fp64 else 0, int(iters), C.byref(v)))
     return v.value
+
+
+def qmc_cgemm(M, N, K, batch, A_ptr, opA, B_ptr, opB, d_ptr, C_ptr, negate=0, add_identity=0,
+              digits=7, stream=0):
+    """Batched complex product on device pointers (qmc_cgemm); digits 0 = FP64
+    CUDA cores, 1..8 = tensor cores from that many bfloat16 digits."""
+    _check(lib().qmc_cgemm(M, N, K, batch, C.c_void_p(A_ptr), opA, C.c_void_p(B_ptr), opB,
+                           C.c_void_p(d_ptr) if d_ptr else None, C.c_void_p(C_ptr), negate,
+                           add_identity, digits, C.c_void_p(stream) if stream else None))
 
 
 def qmc_ratio_update(N, batch, G_ptr, Delta_ptr, Gp_ptr, logdet_ptr, stream=0):

@@ -11,12 +11,14 @@ worker processes while the GPU works.
  (a) FP64 Langevin sweeps: decision-identical over all 400 updates,
      log R within 1e-10, G within 1e-9 of max|G| after every sweep.
  (b) Mixed precision (FP32 drift transforms, FP32 Jacobi bulk with FP64
-     refinement; everything in the MH ratio FP64): the index of the first
-     decision that differs from the oracle, and G against the oracle after
-     every sweep up to it, within 1e-6 (the G-error target of mixed runs).
+     refinement; everything in the MH ratio FP64-accurate), on the CUDA
+     cores (precision 1) and with the dense products on the tensor cores
+     (precision 2): the index of the first decision that differs from the
+     oracle, and G against the oracle after every sweep up to it, within
+     1e-6 (the G-error target of mixed runs).
  (c) The benchmark's default path: mixed precision, learned sweeps at
      rho = 0 with a seeded non-zero network of the benchmark's width (256),
-     every fourth sweep a Langevin sweep.
+     every fourth sweep a Langevin sweep, in both mixed modes.
 """
 import multiprocessing as mp
 
@@ -114,8 +116,10 @@ def test_fp64_langevin_decision_identical_at_benchmark_size(qmc, oracle_results)
         assert obs_g[:, 15].max() < 1e-9
 
 
-def test_mixed_precision_tracks_the_oracle_at_benchmark_size(qmc, oracle_results, record_property):
-    g, greens = _gpu_langevin(qmc, 1)
+@pytest.mark.parametrize("precision", [1, 2])
+def test_mixed_precision_tracks_the_oracle_at_benchmark_size(qmc, oracle_results, record_property,
+                                                             precision):
+    g, greens = _gpu_langevin(qmc, precision)
     for c in range(len(COUPLINGS)):
         o = oracle_results(("lang", c))
         tg, to = g.trace(c), o["trace"]
@@ -133,10 +137,11 @@ def test_mixed_precision_tracks_the_oracle_at_benchmark_size(qmc, oracle_results
         assert g.series()[c][:, 15].max() < 1e-8
 
 
+@pytest.mark.parametrize("precision", [1, 2])
 def test_learned_schedule_tracks_the_oracle_at_benchmark_size(qmc, oracle_results,
-                                                              record_property):
+                                                              record_property, precision):
     g = qmc.Chain(qmc.QMC_TORUS, NPHI, BETA, DTAU, 1.25, 0.0, 5, n_stab=NSTAB, eps0=EPS0,
-                  precision=1, trace_capacity=len(SCHEDULE) * 40)
+                  precision=precision, trace_capacity=len(SCHEDULE) * 40)
     nf = 4 * g.n_q
     net = qmc.Net(nf, NET_H, 16, 3)
     net.set_params(_theta(nf).astype(np.float32))

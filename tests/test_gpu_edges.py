@@ -60,7 +60,7 @@ def test_zero_sweeps_change_nothing(qmc):
     assert np.array_equal(g.fields(0), f0) and np.array_equal(g.green(0), G0)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_poisoned_scratch_changes_nothing(qmc, monkeypatch, precision):
     """QMC_POISON_SCRATCH fills every scratch buffer with NaN bytes at
     creation: a buffer read before it is written would turn the chain into

@@ -37,7 +37,7 @@ def _same(a, b):
         assert x.shape == y.shape and np.array_equal(x, y)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_graph_sweeps_bit_identical(qmc, precision):
     kw = dict(n_chains=3, couplings=[0.5, 1.0, 1.5], seeds=[4, 5, 6], n_stab=4,
               trace_capacity=200, precision=precision)

@@ -204,9 +204,10 @@ def _compare_mixed(gpu, c, orc, nsw, min_identical):
     return first
 
 
-def test_mixed_precision_config1_tracks_the_oracle(qmc):
+@pytest.mark.parametrize("precision", [1, 2])
+def test_mixed_precision_config1_tracks_the_oracle(qmc, precision):
     nsw = 200
-    g = qmc.Chain(qmc.QMC_TORUS, 4, 2.0, 0.1, 1.0, 0.0, 0, n_stab=5, precision=1,
+    g = qmc.Chain(qmc.QMC_TORUS, 4, 2.0, 0.1, 1.0, 0.0, 0, n_stab=5, precision=precision,
                   trace_capacity=nsw * 20)
     g.sweep(nsw)
     g.sync()
@@ -218,12 +219,14 @@ def test_mixed_precision_config1_tracks_the_oracle(qmc):
     assert s[:, 15].max() < 1e-9 and s[:, 16].max() < 1e-9
 
 
-def test_mixed_precision_nphi36_propagators_and_ratios(qmc):
+@pytest.mark.parametrize("precision", [1, 2])
+def test_mixed_precision_nphi36_propagators_and_ratios(qmc, precision):
     """The benchmark's matrix size: propagators built through the FP32+polish
-    eigensolver equal the oracle's (FP64 Jacobi) to 1e-10, the first updates
-    make the oracle's decisions and G stays within 1e-6."""
-    g = qmc.Chain(qmc.QMC_TORUS, 36, 0.4, 0.1, 2.0, 0.0, 0, n_stab=10, eps0=0.2, precision=1,
-                  trace_capacity=8)
+    eigensolver (and, in precision 2, tensor-core products) equal the
+    oracle's (FP64 Jacobi) to 1e-10, the first updates make the oracle's
+    decisions and G stays within 1e-6."""
+    g = qmc.Chain(qmc.QMC_TORUS, 36, 0.4, 0.1, 2.0, 0.0, 0, n_stab=10, eps0=0.2,
+                  precision=precision, trace_capacity=8)
     m = M.Model(M.TORUS, 36)
     o = O.Chain(M.TORUS, 36, 0.4, 0.1, 2.0, 0.0, 0, n_stab=10, eps0=0.2, model=m)
     for t in (1, 3):
@@ -238,10 +241,11 @@ def test_mixed_precision_nphi36_propagators_and_ratios(qmc):
     _compare_mixed(g, 0, o, 2, 8)
 
 
-def test_mixed_precision_full_workload_properties(qmc):
+@pytest.mark.parametrize("precision", [1, 2])
+def test_mixed_precision_full_workload_properties(qmc, precision):
     us = np.linspace(0.5, 2.0, 8)
     g = qmc.Chain(qmc.QMC_TORUS, 36, 36.0, 0.1, 0.0, 0.0, 0, n_chains=8, couplings=us,
-                  seeds=np.arange(8), n_stab=10, eps0=0.45, precision=1)
+                  seeds=np.arange(8), n_stab=10, eps0=0.45, precision=precision)
     g.sweep(2)
     g.sync()
     s = g.series()
