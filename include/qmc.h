@@ -120,8 +120,9 @@ int qmc_default_opts(qmc_opts *o);
  *              {q in Z^2 : exp(-2 pi |q|^2/(4 N_phi)) > 0.01}; sphere:
  *              opts.n_orb_sphere orbitals (default N_phi + 1), N_q = n_orb^2
  *              momenta (l, m), l < n_orb.  The orbital count must lie in
- *              [2, 56] (the LU, QR and eigensolver kernels keep one matrix in
- *              one CTA's shared memory); QMC_ERR_ARG otherwise
+ *              [2, 60] (the LU, QR and eigensolver kernels keep one matrix of
+ *              up to 120 x 120 in one CTA's shared memory; the 60-orbital
+ *              sphere is the largest); QMC_ERR_ARG otherwise
  *   beta, dtau inverse temperature and Trotter step; L = beta/dtau must be an
  *              integer (QMC_ERR_ARG otherwise)
  *   coupling   u, anisotropy alpha (Results, "Universal phase diagram"); the
@@ -363,7 +364,7 @@ double qmc_tau_int(const double *x, int n);
  * ratio det(1 + B'(b,0))/det(1 + B(b,0)) = det M with
  * M = 1 + (Delta - 1)(1 - G), Delta = B'_tau B_tau^-1, and the new
  * G' = G M^-1 of Eq. green_function), for `batch` independent matrices.
- *   N       matrix size (single-particle states of one spin block), 1..112
+ *   N       matrix size (single-particle states of one spin block), 1..120
  *           (the LU and division kernels keep one matrix in one CTA's shared
  *           memory; also the largest N of a context)
  *   G       device, batch x N x N, row-major interleaved complex (2 doubles)

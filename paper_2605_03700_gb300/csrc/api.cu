@@ -50,6 +50,7 @@ struct qmc_ctx {
     size_t gsz = 16;   // element size of the buffers in that type
     bool tc = false;   // precision 2: dense products on the tensor cores
     OzCfg ozF, ozD;    // tensor-core work space: FP64-class (7 digits), drift (3 digits)
+    unsigned char *qscr = nullptr;  // QR vectors for the largest sizes
     int *ozerr = nullptr;
     qmc_opts o;
     std::vector<double> u, anis, g;
@@ -339,7 +340,7 @@ static int build_left_stack(qmc_ctx *ctx)
             std::swap(a, b);
         }
         if (qrp_batched(s, N, a, NN, ctx->LQ + dst * NN, Ls, ctx->LD + dst * N, LDs, ctx->Vt, NN,
-                        nb))
+                        nb, ctx->qscr))
             return QMC_ERR_ARG;
         gemm_sq(s, N, nb, TY_C64, op64(ctx->Vt, NN), 0, op64(ctx->LW + k * NN, Ls), 0,
                 op64(ctx->LW + dst * NN, Ls));
@@ -478,7 +479,8 @@ static int restabilise(qmc_ctx *ctx, int k, int prev, int t)
                 op64(b, NN));
         std::swap(a, b);
     }
-    if (qrp_batched(s, N, a, NN, ctx->Qt, NN, ctx->Dt, N, ctx->Vt, NN, nb)) return QMC_ERR_ARG;
+    if (qrp_batched(s, N, a, NN, ctx->Qt, NN, ctx->Dt, N, ctx->Vt, NN, nb, ctx->qscr))
+        return QMC_ERR_ARG;
     gemm_sq(s, N, nb, TY_C64, op64(ctx->Vt, NN), 0, op64(ctx->RW, NN), 0, op64(ctx->X1, NN));
     std::swap(ctx->RW, ctx->X1);
     std::swap(ctx->RQ, ctx->Qt);
@@ -511,7 +513,8 @@ static int advance_right_udv(qmc_ctx *ctx, int prev, int t)
                 op64(b, NN));
         std::swap(a, b);
     }
-    if (qrp_batched(s, N, a, NN, ctx->Qt, NN, ctx->Dt, N, ctx->Vt, NN, nb)) return QMC_ERR_ARG;
+    if (qrp_batched(s, N, a, NN, ctx->Qt, NN, ctx->Dt, N, ctx->Vt, NN, nb, ctx->qscr))
+        return QMC_ERR_ARG;
     gemm_sq(s, N, nb, TY_C64, op64(ctx->Vt, NN), 0, op64(ctx->RW, NN), 0, op64(ctx->X1, NN));
     std::swap(ctx->RW, ctx->X1);
     std::swap(ctx->RQ, ctx->Qt);
@@ -912,6 +915,7 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
     DA(ctx->flag, nb);
     DA(ctx->errf, nb);
     DA(ctx->ozerr, 1);
+    DAS(ctx->qscr, qrp_scratch_bytes(N, nb));
     if (ctx->tc) {
         // the largest products: N x N over the batch, n x n over 4 channels
         // per chain (eigenvector refinement), both at the FP64-class digit count
@@ -1041,8 +1045,9 @@ int qmc_create(qmc_ctx **out, int geometry, int N_phi, double beta, double dtau,
     if (geometry != QMC_TORUS && geometry != QMC_SPHERE) {
         ctx->err = "geometry must be QMC_TORUS or QMC_SPHERE";
         code = QMC_ERR_ARG;
-    } else if (N_phi < 1 || norb < 2 || norb > 56) {
-        ctx->err = "orbital count must be in [2, 56] (single-block shared-memory kernels)";
+    } else if (N_phi < 1 || norb < 2 || norb > 60) {
+        ctx->err = "orbital count must be in [2, 60] (LU and QR keep one matrix of up to "
+                   "120 x 120 in one CTA's shared memory)";
         code = QMC_ERR_ARG;
     } else if (!(beta > 0) || !(dtau > 0)) {
         ctx->err = "beta and dtau must be positive";
@@ -1748,7 +1753,7 @@ int qmc_gemm_tile(int n, int precision)
 int qmc_ratio_update_noalloc(int N, int batch, const double *G, const double *Delta,
                              double *Gp, double *logdet, void *stream)
 {
-    if (N < 1 || N > 112 || batch < 1 || !G || !Delta || !Gp || !logdet) return QMC_ERR_ARG;
+    if (N < 1 || N > 120 || batch < 1 || !G || !Delta || !Gp || !logdet) return QMC_ERR_ARG;
     const size_t NN = (size_t)N * N;
     const size_t mat = round256(sizeof(cd) * NN * (size_t)batch);
     const size_t pv = round256(sizeof(int) * (size_t)N * (size_t)batch);
@@ -1789,7 +1794,7 @@ int qmc_ratio_update_noalloc(int N, int batch, const double *G, const double *De
 int qmc_ratio_update(int N, int batch, const double *G, const double *Delta, double *Gp,
                      double *logdet, void *stream)
 {
-    if (N < 1 || N > 112 || batch < 1 || !G || !Delta || !Gp || !logdet) return QMC_ERR_ARG;
+    if (N < 1 || N > 120 || batch < 1 || !G || !Delta || !Gp || !logdet) return QMC_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t NN = (size_t)N * N;
     // shared-memory limits of the LU / division kernels (no context here)

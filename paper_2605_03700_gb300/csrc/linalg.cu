@@ -627,12 +627,12 @@ int eigh_mixed(cudaStream_t st, int n, int batch, const cd *A, cd *U, double *w,
 // In-place LU with partial pivoting (first row of maximal |a_ik|), one block
 // per matrix in shared memory; piv[k] = row exchanged with row k at step k;
 // logdet = sum log U_kk + i pi (number of exchanges mod 2).  FP64 always.
-__global__ void __launch_bounds__(256) k_lu(int n, cd *A, long long sA, int *piv, long long spiv,
-                                            cd *logdet)
+__global__ void __launch_bounds__(256) k_lu(int n, int ld, cd *A, long long sA, int *piv,
+                                            long long spiv, cd *logdet)
 {
-    // row stride n + 1 (odd): column walks hit distinct banks
+    // row stride ld = n + 1 (odd: column walks hit distinct banks) where that
+    // fits in shared memory, n for the largest sizes
     extern __shared__ cd sm_l[];
-    const int ld = n + 1;
     cd *M = sm_l;
     __shared__ cd s_inv;
     const int b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
@@ -721,12 +721,23 @@ __global__ void __launch_bounds__(256) k_lu(int n, cd *A, long long sA, int *piv
     }
 }
 
+// dynamic shared memory a block may opt into on this device (queried by
+// linalg_init; 227 KB on this part) less a bound on the static arrays of the
+// kernel it is used for
+static size_t g_smem_optin = 227 * 1024;
+static const size_t SMEM_STATIC_BOUND = 256;
+#define SMEM_MAX (g_smem_optin - SMEM_STATIC_BOUND)
+// the same for k_qrp with its own static arrays (set by linalg_init)
+static size_t g_smem_qrp = 227 * 1024 - SMEM_STATIC_BOUND;
+
 int lu_batched(cudaStream_t st, int n, cd *A, long long sA, int *piv, long long spiv, cd *logdet,
                int batch)
 {
-    size_t smem = (size_t)n * (n + 1) * sizeof(cd);
-    if (smem > 220 * 1024) return -1;
-    k_lu<<<batch, 256, smem, st>>>(n, A, sA, piv, spiv, logdet);
+    int ld = n + 1;
+    if ((size_t)n * ld * sizeof(cd) > SMEM_MAX) ld = n;
+    const size_t smem = (size_t)n * ld * sizeof(cd);
+    if (smem > SMEM_MAX) return -1;
+    k_lu<<<batch, 256, smem, st>>>(n, ld, A, sA, piv, spiv, logdet);
     QMC_COUNT(1);
     return 0;
 }
@@ -802,13 +813,101 @@ __global__ void __launch_bounds__(RD_ROWS * 32) k_rdiv(int n, const cd *G, long 
     for (int j = lane; j < n; j += 32) x[j] = cvt<cd>(z[j]);
 }
 
+// The same right division for sizes whose factors do not fit in shared
+// memory: x M = g solved right-looking, z_j = z_j / U_jj then
+// z_k -= z_j U_jk (k > j), and y_j = z_j then z_k -= y_j L_jk (k < j), so the
+// factors are read by rows (coalesced), staged RC rows at a time in shared
+// memory and shared by the block's RD_ROWS warps (one warp per row of G).
+#define RD_CH 8
+__global__ void __launch_bounds__(RD_ROWS * 32) k_rdiv_ch(int n, const cd *G, long long sG,
+                                                          const cd *LU, long long sLU,
+                                                          const int *piv, long long spiv, cd *X,
+                                                          long long sX)
+{
+    extern __shared__ __align__(16) unsigned char sm_rc_raw[];
+    cd *F = (cd *)sm_rc_raw;        // RD_CH rows of the factor
+    cd *zbuf = F + RD_CH * n;       // RD_ROWS rows being solved
+    const int b = blockIdx.y, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r = blockIdx.x * RD_ROWS + warp;
+    const cd *LUb = LU + (long long)b * sLU;
+    cd *z = zbuf + warp * n;
+    if (r < n) {
+        const cd *g = G + (long long)b * sG + (long long)r * n;
+        for (int j = lane; j < n; j += 32) z[j] = g[j];
+    }
+    // forward: z U = g
+    for (int j0 = 0; j0 < n; j0 += RD_CH) {
+        const int nr = min(RD_CH, n - j0);
+        __syncthreads();
+        for (int e = tid; e < nr * n; e += blockDim.x) F[e] = LUb[(long long)j0 * n + e];
+        __syncthreads();
+        if (r < n)
+            for (int jj = 0; jj < nr; ++jj) {
+                const int j = j0 + jj;
+                const cd *u = F + jj * n;
+                // 1 / U_jj = conj / |.|^2 (one division)
+                const cd ujj = u[j];
+                const double rr = 1.0 / cabs2(ujj);
+                const cd zj = cmul(z[j], cmk(ujj.x * rr, -ujj.y * rr));
+                __syncwarp();
+                if (lane == 0) z[j] = zj;
+                for (int k = j + 1 + lane; k < n; k += 32) {
+                    cd v = z[k];
+                    cfma(v, cmk(-zj.x, -zj.y), u[k]);
+                    z[k] = v;
+                }
+                __syncwarp();
+            }
+    }
+    // backward: y L = z, L unit lower
+    for (int j1 = n; j1 > 0; j1 -= RD_CH) {
+        const int j0 = max(0, j1 - RD_CH), nr = j1 - j0;
+        __syncthreads();
+        for (int e = tid; e < nr * n; e += blockDim.x) F[e] = LUb[(long long)j0 * n + e];
+        __syncthreads();
+        if (r < n)
+            for (int jj = nr - 1; jj >= 0; --jj) {
+                const int j = j0 + jj;
+                const cd *l = F + jj * n;
+                const cd yj = z[j];
+                for (int k = lane; k < j; k += 32) {
+                    cd v = z[k];
+                    cfma(v, cmk(-yj.x, -yj.y), l[k]);
+                    z[k] = v;
+                }
+                __syncwarp();
+            }
+    }
+    if (r >= n) return;
+    if (lane == 0) {
+        const int *pv = piv + (long long)b * spiv;
+        for (int k = n - 1; k >= 0; --k) {
+            const int p = pv[k];
+            if (p != k) {
+                const cd t = z[k];
+                z[k] = z[p];
+                z[p] = t;
+            }
+        }
+    }
+    __syncwarp();
+    cd *x = X + (long long)b * sX + (long long)r * n;
+    for (int j = lane; j < n; j += 32) x[j] = z[j];
+}
+
 int rdiv_batched(cudaStream_t st, int prec, int n, const cd *G, long long sG, const cd *LU,
                  long long sLU, const int *piv, long long spiv, cd *X, long long sX, int batch)
 {
     dim3 grid(cdiv_up(n, RD_ROWS), batch);
     if (prec == TY_C64) {
         size_t smem = ((size_t)n * (n + 1) + (size_t)(RD_ROWS + 1) * n) * sizeof(cd);
-        if (smem > 220 * 1024) return -1;
+        if (smem > 220 * 1024) {
+            smem = (size_t)(RD_CH + RD_ROWS) * n * sizeof(cd);
+            if (smem > SMEM_MAX) return -1;
+            k_rdiv_ch<<<grid, RD_ROWS * 32, smem, st>>>(n, G, sG, LU, sLU, piv, spiv, X, sX);
+            QMC_COUNT(1);
+            return 0;
+        }
         k_rdiv<double><<<grid, RD_ROWS * 32, smem, st>>>(n, G, sG, LU, sLU, piv, spiv, X, sX);
     } else {
         size_t smem = ((size_t)n * (n + 1) + (size_t)(RD_ROWS + 1) * n) * sizeof(cf);
@@ -835,20 +934,35 @@ __device__ __forceinline__ cd warp_csum(cd v)
     return v;
 }
 
-__global__ void __launch_bounds__(256) k_qrp(int n, const cd *X, long long sX, cd *Q, long long sQ,
-                                             double *D, long long sD, cd *V, long long sV,
-                                             int q_in_smem)
+__global__ void __launch_bounds__(256) k_qrp(int n, int ld, const cd *X, long long sX, cd *Q,
+                                             long long sQ, double *D, long long sD, cd *V,
+                                             long long sV, int q_in_smem, void *vscr)
 {
-    // working matrix with row stride n + 1 (odd): column walks hit distinct banks
+    // working matrix with row stride ld = n + 1 (odd: column walks hit
+    // distinct banks) where that fits, n for the largest sizes; the per-step
+    // vectors follow it in shared memory, or, when vscr is given (sizes where
+    // only the matrix and v fit), live in global scratch of 40 n bytes per
+    // matrix
     extern __shared__ cd sm_q[];
-    const int ld = n + 1;
     cd *A = sm_q;
     cd *v = A + n * ld;
-    cd *sv = v + n;   // per-column dot products of the trailing matrix
-    cd *sq = sv + n;  // per-row dot products of Q
-    double *cn = (double *)(sq + n);
-    int *perm = (int *)(cn + n);
-    // Q after the int array, rounded up to a 16-byte boundary
+    cd *sv, *sq;  // per-column dot products of the trailing matrix, per-row of Q
+    double *cn;
+    int *perm;
+    if (vscr) {
+        sv = (cd *)vscr + (long long)blockIdx.x * 2 * n;
+        sq = sv + n;
+        cn = (double *)((cd *)vscr + (long long)gridDim.x * 2 * n) + (long long)blockIdx.x * n;
+        perm = (int *)((double *)((cd *)vscr + (long long)gridDim.x * 2 * n) +
+                       (long long)gridDim.x * n) +
+               (long long)blockIdx.x * n;
+    } else {
+        sv = v + n;
+        sq = sv + n;
+        cn = (double *)(sq + n);
+        perm = (int *)(cn + n);
+    }
+    // Q after the int array, rounded up to a 16-byte boundary (shared vectors only)
     cd *Qs = q_in_smem ? (cd *)((((uintptr_t)(perm + n)) + 15) & ~(uintptr_t)15) : nullptr;
     __shared__ int s_best;
     __shared__ double s_f;
@@ -992,16 +1106,31 @@ __global__ void __launch_bounds__(256) k_qrp(int n, const cd *X, long long sX, c
     }
 }
 
-int qrp_batched(cudaStream_t st, int n, const cd *X, long long sX, cd *Q, long long sQ, double *D,
-                long long sD, cd *V, long long sV, int batch)
+size_t qrp_scratch_bytes(int n, int batch)
 {
-    size_t base = (size_t)n * (n + 1) * sizeof(cd) + 3 * (size_t)n * sizeof(cd) +
-                  (size_t)n * sizeof(double) + (size_t)n * sizeof(int) + 16;
-    size_t withq = base + (size_t)n * (n + 1) * sizeof(cd);
-    int qs = withq <= 220 * 1024;
-    size_t smem = qs ? withq : base;
-    if (smem > 220 * 1024) return -1;
-    k_qrp<<<batch, 256, smem, st>>>(n, X, sX, Q, sQ, D, sD, V, sV, qs);
+    return (size_t)batch * n * (2 * sizeof(cd) + sizeof(double) + sizeof(int));
+}
+
+int qrp_batched(cudaStream_t st, int n, const cd *X, long long sX, cd *Q, long long sQ, double *D,
+                long long sD, cd *V, long long sV, int batch, void *vscr)
+{
+    const size_t vec = 3 * (size_t)n * sizeof(cd) + (size_t)n * sizeof(double) +
+                       (size_t)n * sizeof(int) + 16;
+    const size_t base = (size_t)n * (n + 1) * sizeof(cd) + vec;
+    const size_t withq = base + (size_t)n * (n + 1) * sizeof(cd);
+    if (base <= 220 * 1024) {
+        const int qs = withq <= 220 * 1024;
+        k_qrp<<<batch, 256, qs ? withq : base, st>>>(n, n + 1, X, sX, Q, sQ, D, sD, V, sV, qs,
+                                                   nullptr);
+    } else {
+        // largest sizes: matrix (row stride n + 1 if it fits, else n) and v in
+        // shared memory, the other vectors and Q in global memory
+        int ld = n + 1;
+        if ((size_t)n * ld * sizeof(cd) + (size_t)n * sizeof(cd) > g_smem_qrp) ld = n;
+        const size_t smem = (size_t)n * ld * sizeof(cd) + (size_t)n * sizeof(cd);
+        if (smem > g_smem_qrp || !vscr) return -1;
+        k_qrp<<<batch, 256, smem, st>>>(n, ld, X, sX, Q, sQ, D, sD, V, sV, 0, vscr);
+    }
     QMC_COUNT(1);
     return 0;
 }
@@ -1011,14 +1140,24 @@ int qrp_batched(cudaStream_t st, int n, const cd *X, long long sX, cd *Q, long l
 // current device (once per context creation, never inside a stream capture)
 void linalg_init()
 {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) ==
+            cudaSuccess &&
+        optin > 0)
+        g_smem_optin = (size_t)optin;
     cudaFuncSetAttribute(k_eigh<double, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          2 * 64 * 64 * 16);
     cudaFuncSetAttribute(k_eigh<float, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          2 * 64 * 64 * 8);
-    cudaFuncSetAttribute(k_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(k_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX);
     cudaFuncSetAttribute(k_rdiv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     cudaFuncSetAttribute(k_rdiv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    cudaFuncSetAttribute(k_qrp, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(k_rdiv_ch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_qrp) == cudaSuccess && fa.sharedSizeBytes < 1024)
+        g_smem_qrp = g_smem_optin - fa.sharedSizeBytes;
+    cudaFuncSetAttribute(k_qrp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g_smem_qrp);
     oz_init();
 }
 

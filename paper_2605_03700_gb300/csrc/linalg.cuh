@@ -60,8 +60,11 @@ int lu_batched(cudaStream_t st, int n, cd *A, long long sA, int *piv, long long 
                int batch);
 int rdiv_batched(cudaStream_t st, int prec, int n, const cd *G, long long sG, const cd *LU,
                  long long sLU, const int *piv, long long spiv, cd *X, long long sX, int batch);
+// vscr: global scratch of qrp_scratch_bytes(n, batch) bytes, needed only for
+// the sizes whose per-step vectors do not fit in shared memory (n > 112)
 int qrp_batched(cudaStream_t st, int n, const cd *X, long long sX, cd *Q, long long sQ, double *D,
-                long long sD, cd *V, long long sV, int batch);
+                long long sD, cd *V, long long sV, int batch, void *vscr = nullptr);
+size_t qrp_scratch_bytes(int n, int batch);
 
 // typed operand: pointer, batch stride (elements), element type
 struct Op {

@@ -41,3 +41,15 @@ def scheduled_chain(nphi, beta, dtau, u, anis, seed, n_stab, eps0, schedule, the
         phis.append(o.phi())
     return {"trace": o.trace(), "obs": np.concatenate(obs), "green": np.array(greens),
             "phi": np.array(phis), "L": o.L}
+
+
+def plain_chain(geom, size, beta, dtau, u, anis, seed, n_stab, eps0, nsweeps):
+    """Langevin sweeps of the oracle in either geometry (geom: oracle model
+    code); trace, records, G and fields at the end."""
+    from oracle import model as M
+    from oracle import oracle as O
+    m = M.Model(geom, size)
+    o = O.Chain(geom, size, beta, dtau, u, anis, seed, n_stab=n_stab, eps0=eps0, model=m)
+    o.enable_trace(nsweeps * o.L)
+    obs = o.sweep(nsweeps)
+    return {"trace": o.trace(), "obs": obs, "green": o.green(), "phi": o.phi(), "L": o.L}

@@ -85,11 +85,11 @@ def test_new_entry_points_reject_invalid_arguments_before_device_work(lib):
     assert L.qmc_group_sweep(None, 1) == -1 and L.qmc_group_sync(None) == -1
     assert L.qmc_group_destroy(None) == 0
     # standalone ratio updates: sizes beyond what the kernels hold
-    assert L.qmc_ratio_update(113, 1, None, None, None, None, None) == -1
+    assert L.qmc_ratio_update(121, 1, None, None, None, None, None) == -1
     assert L.qmc_ratio_update_noalloc(72, 1, None, None, None, None, None) == -1
-    # sphere beyond 56 orbitals
+    # sphere beyond 60 orbitals
     o = qmc.qmc_default_opts()
-    assert L.qmc_create(C.byref(h), 1, 56, 1.0, 0.1, 1.0, 0.0, 0, C.byref(o)) == -1
+    assert L.qmc_create(C.byref(h), 1, 60, 1.0, 0.1, 1.0, 0.0, 0, C.byref(o)) == -1
 
 
 def test_opts_struct_matches_the_library(lib):

@@ -1,7 +1,7 @@
 """Edge cases of the GPU sweep against the oracle: a single imaginary-time
 slice (L = 1), restabilisation after every slice (n_stab = 1) and only at
-beta (n_stab > L), the largest torus the one-CTA kernels take (N_phi = 56,
-N = 112), and zero sweeps."""
+beta (n_stab > L), a large torus (N_phi = 56, N = 112; the largest size,
+N = 120, is in test_gpu_large.py), and zero sweeps."""
 import numpy as np
 import pytest
 
@@ -46,8 +46,9 @@ def test_restabilisation_every_slice_and_only_at_beta(qmc, nstab):
     assert g.series()[0][:, 15].max() < 1e-9
 
 
-def test_largest_torus(qmc):
-    """N_phi = 56 (N = 112, N_q = 517): two slices, one sweep."""
+def test_large_torus(qmc):
+    """N_phi = 56 (N = 112, N_q = 517): two slices, one sweep (the largest
+    size whose QR keeps all its vectors in shared memory)."""
     g, o = _run(qmc, 56, 0.2, 1.0, 0.1, 2, 5, 1)
     assert g.n_q == 517 and g.N == 112
 

@@ -1,0 +1,102 @@
+"""Parity with the FP64 oracle at the largest matrix size the kernels take,
+N = 120 (one spin block of 60 orbitals): the torus at N_phi = 60 (N_q = 553)
+and the 60-orbital sphere of the benchmark's learned-proposal workload
+(N_q = 3600, Methods Eq. sphere_density_operator).  At this size the LU keeps
+its matrix at row stride n, QR with pivoting keeps only the matrix and the
+Householder vector in shared memory, and the right division stages its
+factors in row chunks.  The oracle chains run in spawned workers while the
+GPU works: identical decisions, log R within 1e-10 (relative to
+max(1, |log R|)), G within 1e-9 of max|G|; in precision 2 (dense products on
+the tensor cores) the chain tracks the oracle."""
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+from oracle import model as M
+from tests import oracle_runs as R
+
+pytestmark = pytest.mark.gpu
+
+TORUS = dict(size=60, beta=1.0, u=1.0, anis=0.1, seed=2, n_stab=5, eps0=0.3, nsw=2)
+# the paper's sphere couplings (u <= 0.3): at u = 1.2 the sphere's larger
+# form factors make B ill-conditioned and two FP64 evaluation orders of the
+# same ratio already differ by ~1e-8 (see test_gpu_sphere.py)
+SPHERE = dict(size=60, beta=1.0, u=0.3, anis=0.0, seed=3, n_stab=5, eps0=0.3, nsw=1)
+
+
+@pytest.fixture(scope="module")
+def oracle_results():
+    from oracle import oracle as O
+    O.build()
+    pool = mp.get_context("spawn").Pool(2)
+    jobs = {}
+    for key, geom, c in (("torus", M.TORUS, TORUS), ("sphere", M.SPHERE, SPHERE)):
+        jobs[key] = pool.apply_async(R.plain_chain, (geom, c["size"], c["beta"], 0.1, c["u"],
+                                                     c["anis"], c["seed"], c["n_stab"],
+                                                     c["eps0"], c["nsw"]))
+    pool.close()
+    cache = {}
+
+    def get(key):
+        if key not in cache:
+            cache[key] = jobs[key].get(timeout=1800)
+        return cache[key]
+    yield get
+    pool.terminate()
+
+
+@pytest.fixture(scope="module")
+def qmc():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2605_03700_gb300 import build
+    build.build()
+    import paper_2605_03700_gb300 as P
+    return P
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _gpu(qmc, geom, c, precision):
+    nphi = c["size"] if geom == qmc.QMC_TORUS else c["size"] - 1
+    L = int(round(c["beta"] / 0.1))
+    g = qmc.Chain(geom, nphi, c["beta"], 0.1, c["u"], c["anis"], c["seed"], n_stab=c["n_stab"],
+                  eps0=c["eps0"], precision=precision, trace_capacity=c["nsw"] * L)
+    assert g.N == 120
+    g.sweep(c["nsw"])
+    g.sync()
+    return g
+
+
+@pytest.mark.parametrize("geom_name", ["torus", "sphere"])
+def test_fp64_decision_identical_at_n120(qmc, oracle_results, geom_name):
+    geom, c = ((qmc.QMC_TORUS, TORUS) if geom_name == "torus" else (qmc.QMC_SPHERE, SPHERE))
+    g = _gpu(qmc, geom, c, 0)
+    o = oracle_results(geom_name)
+    tg, to = g.trace(0), o["trace"]
+    assert len(tg) == len(to) == c["nsw"] * o["L"]
+    assert np.array_equal(tg[:, 6], to[:, 6]), "accept decisions differ"
+    assert (np.abs(tg[:, 2] - to[:, 2]) / np.maximum(1, np.abs(to[:, 2]))).max() < 1e-10
+    assert _rel(g.green(0), o["green"]) < 1e-9
+    assert np.abs(g.fields(0) - o["phi"]).max() < 1e-9
+    obs = g.series()[0]
+    for col in (0, 1, 11, 12):
+        ref = o["obs"][:, col]
+        assert np.abs(obs[:, col] - ref).max() < 1e-9 * max(1, np.abs(ref).max())
+    assert obs[:, 15].max() < 1e-9
+
+
+def test_tensor_core_precision_tracks_the_oracle_at_n120(qmc, oracle_results):
+    g = _gpu(qmc, qmc.QMC_TORUS, TORUS, 2)
+    o = oracle_results("torus")
+    tg, to = g.trace(0), o["trace"]
+    mis = np.nonzero(tg[:, 6] != to[:, 6])[0]
+    first = int(mis[0]) if len(mis) else len(tg)
+    assert first >= 10, f"decisions diverge at update {first}"
+    assert np.abs(tg[:first, 2] - to[:first, 2]).max() < 1e-5
+    if first == len(tg):
+        assert _rel(g.green(0), o["green"]) < 1e-6
+    assert g.series()[0][:, 15].max() < 1e-8

@@ -6,7 +6,7 @@ lowering-operator recursion in double-double arithmetic; the oracle from the
 Racah formula in exact rational arithmetic.  Same seeds and Philox streams:
 identical accept/reject decisions, log ratios within 1e-10 relative to
 max(1, |log R|) at the paper's sphere couplings, G and the measurements
-within 1e-9; propagators of the same fields equal to 1e-12 up to 56 orbitals, where
+within 1e-9; propagators of the same fields equal to 1e-12 up to 60 orbitals, where
 an FP64 recursion would already have lost every digit.
 """
 import numpy as np
@@ -68,7 +68,7 @@ def test_sphere_decision_identical(qmc, norb, beta, nsw, u, aniso, tol):
     assert np.array_equal(obs_g[:, 17], obs_o[:, 17])
 
 
-@pytest.mark.parametrize("norb", [24, 56])
+@pytest.mark.parametrize("norb", [24, 56, 60])
 def test_sphere_propagators_large_orbital_counts(qmc, norb):
     """Propagators of identical fields: the GPU form factors carry the exact
     rational values of the oracle to rounding."""
@@ -88,4 +88,4 @@ def test_sphere_orbital_count_option_and_limits(qmc):
     assert g.n_orb == 4 and g.n_q == 16
     g.close()
     with pytest.raises(qmc.QMCError):
-        qmc.Chain(qmc.QMC_SPHERE, 56, 0.2, 0.1, 1.0)   # 57 orbitals
+        qmc.Chain(qmc.QMC_SPHERE, 60, 0.2, 0.1, 1.0)   # 61 orbitals
