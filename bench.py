@@ -8,8 +8,9 @@ per slice), beta = 36, dtau = 0.1 (L = 360 slices), eight chains at couplings
 u = linspace(0.5, 2.0, 8), seeds 0..7, restabilisation every 10 slices.
 
 Two arms run in one invocation on the same GPU:
-  * the headline path (default --mode learned --precision 1): mixed precision
-    with learned whole-slice sweeps and a Langevin sweep every 4th step;
+  * the headline path (default --mode prior): mixed precision with
+    whole-slice sweeps around the Gaussian prior (accepted by the exact
+    determinant ratio) and a Langevin sweep every 4th step;
   * the plain FP64 Langevin sweep (--precision 0 --mode plain), the
     comparison the metric names.
 Each arm: W warm-up sweeps, K timed sweeps (CUDA events on the library's
@@ -274,20 +275,25 @@ def run_arm(P, stream, *, mode, precision, drift, seeds, steps, warmup, tau_swee
                  seeds=seeds, n_stab=NSTAB, eps0=EPS0, series_capacity=4096, precision=precision,
                  drift=P.QMC_DRIFT_FIRST if drift == "first" else P.QMC_DRIFT_EXACT)
     ch.set_stream(stream.cuda_stream)
-    # learned mode: whole-slice moves around the network's Gaussian
-    # (rho = 0), a Langevin sweep every LANGEVIN_EVERY-th step as the
-    # fallback; the network is at its prior initialisation (mu = 0,
-    # sigma = 1), which held-out NLL early stopping keeps at this workload
+    # prior mode (default): whole-slice moves around the Gaussian part of
+    # the action (rho = 0), accepted by the exact determinant ratio, with a
+    # Langevin sweep every LANGEVIN_EVERY-th step; learned mode: the same
+    # schedule with the network's Gaussian (at its initialisation mu = 0,
+    # sigma = 1 it proposes what the prior move does, at the cost of its
+    # forward pass: training on thinned plain-chain configurations never
+    # lowered held-out NLL below the prior's at these couplings)
     net = P.Net(4 * ch.n_q, 256, 16, 1 + int(seeds[0])) if mode == "learned" else None
 
     def is_langevin(k):
-        return net is None or k % LANGEVIN_EVERY == LANGEVIN_EVERY - 1
+        return mode == "plain" or k % LANGEVIN_EVERY == LANGEVIN_EVERY - 1
 
     def step(k):
         if is_langevin(k):
             ch.sweep(1, graph=graph)
-        else:
+        elif net is not None:
             ch.sweep_learned(net, 1, 0.0, graph=graph)
+        else:
+            ch.sweep_prior(1, 0.0, graph=graph)
 
     pinned = torch.empty((steps, NCH, P.QMC_NOBS), dtype=torch.float64, pin_memory=True)
     for k in range(warmup):
@@ -328,7 +334,7 @@ def run_arm(P, stream, *, mode, precision, drift, seeds, steps, warmup, tau_swee
     learned_steps = [j for j in range(series.shape[1]) if not is_langevin(warmup + j)]
     acc_learned = float(series[:, learned_steps, 13].mean()) if learned_steps else None
     acc_langevin = float(np.delete(series[:, :, 13], learned_steps, axis=1).mean())
-    out = {"ch": ch, "net": net, "ms": ms, "step_s": ms / 1000.0 / steps, "taus": taus,
+    out = {"ch": ch, "net": net, "mode": mode, "ms": ms, "step_s": ms / 1000.0 / steps, "taus": taus,
            "series_len": int(series.shape[1]), "launches": int(launches), "clocks": clk,
            "wall_e2e": wall_e2e, "g_err_max": float(timed[:, :, 15].max()),
            "sign_max": float(timed[:, :, 16].max()), "acc_learned": acc_learned,
@@ -343,14 +349,16 @@ def gemm_roofline_pass(P, arm, steps=2):
     `steps` further sweeps (eager launches, so each product has its own
     event pair).  Returns (FP64 ms, launches, flops) and (tensor ms,
     launches, needed flops, issued flops)."""
-    ch, net = arm["ch"], arm["net"]
+    ch, net, mode = arm["ch"], arm["net"], arm["mode"]
     P.qmc_profile_gemm(True)
     t0 = time.perf_counter()
     for k in range(steps):
-        if net is None or k % 2 == 1:
+        if mode == "plain" or k % 2 == 1:
             ch.sweep(1)
-        else:
+        elif net is not None:
             ch.sweep_learned(net, 1, 0.0)
+        else:
+            ch.sweep_prior(1, 0.0)
     ch.sync()
     ms, n, flops = P.qmc_profile_gemm(False)
     wall = time.perf_counter() - t0
@@ -495,10 +503,10 @@ def run_ours(args):
                                    "mode": args.mode,
                                    "drift": args.drift,
                                    "schedule": ("plain Langevin sweeps" if args.mode == "plain" else
-                                                f"learned sweeps (rho 0), every {LANGEVIN_EVERY}th "
-                                                "step a Langevin sweep"),
+                                                f"{args.mode} whole-slice sweeps (rho 0), every "
+                                                f"{LANGEVIN_EVERY}th step a Langevin sweep"),
                                    "launch": "graph-replayed sweeps",
-                                   "acceptance_learned": main["acc_learned"],
+                                   "acceptance_whole_slice": main["acc_learned"],
                                    "acceptance_langevin": main["acc_langevin"],
                                    "tau_int": [[round(t, 3), round(e, 3)] for t, e in main["taus"]],
                                    "tau_series_len": main["series_len"],
@@ -536,6 +544,127 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------ other workloads ----
+def run_batched(args):
+    """64 independent chains, torus N_phi drawn from {16, 24, 36, 48}
+    (numpy default_rng(0), the list is printed), beta = N_phi, dtau = 0.1,
+    u ~ U[0.5, 2], anisotropy ~ U[-0.2, 0.2]; one context per size, all four
+    swept as one CUDA graph per sweep (qmc_group_*), each size on its own
+    graph branch.  One step = one sweep of all 64 chains."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    from paper_2605_03700_gb300 import build as B
+    B.build()
+    import paper_2605_03700_gb300 as P
+    rng = np.random.default_rng(0)
+    sizes = rng.choice([16, 24, 36, 48], size=64)
+    us = rng.uniform(0.5, 2.0, 64)
+    als = rng.uniform(-0.2, 0.2, 64)
+    wall0 = time.perf_counter()
+    chains = []
+    for nphi in (16, 24, 36, 48):
+        idx = np.nonzero(sizes == nphi)[0]
+        if len(idx) == 0:
+            continue
+        chains.append(P.Chain(P.QMC_TORUS, int(nphi), float(nphi), DTAU, 0.0, 0.0, 0,
+                              n_chains=len(idx), couplings=us[idx], anisotropies=als[idx],
+                              seeds=idx.astype(np.uint64), n_stab=NSTAB, eps0=EPS0,
+                              precision=args.precision, series_capacity=4096))
+    g = P.Group(chains)
+    g.sweep(args.warmup)
+    g.sync()
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    l0 = P.qmc_launch_count()
+    t0 = time.perf_counter()
+    g.sweep(args.steps)
+    g.sync()
+    t = time.perf_counter() - t0
+    launches = P.qmc_launch_count() - l0
+    clk = clocks.stop()
+    wall = time.perf_counter() - wall0
+    while chains[0].series().shape[1] < args.warmup + max(args.tau_sweeps, args.steps):
+        g.sweep(1)
+    g.sync()
+    taus = []
+    for c in chains:
+        taus += tau_per_chain(c.series()[:, args.warmup:, :], P.qmc_tau_int)
+    step_s = t / args.steps
+    v, dv = ess_rate(taus, step_s)
+    line = {"metric": "effective samples/s (autocorr-corrected), 64 batched chains",
+            "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * step_s, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": ["f64", "f32+f64", "f32+f64+bf16-digits"][args.precision],
+            "data": "synthetic",
+            "config": {"workload": "64 chains, torus N_phi in {16,24,36,48} (rng(0)), beta=N_phi, "
+                                   "dtau=0.1, u~U[0.5,2], anisotropy~U[-0.2,0.2], n_stab=10, "
+                                   "one graph per sweep over four size branches",
+                       "sizes": [int(x) for x in sizes], "value_err": dv,
+                       "chain_sweeps_per_s": 64 / step_s,
+                       "tau_int_mean": float(np.mean([t for t, _ in taus])),
+                       "tau_series_len": max(args.tau_sweeps, args.steps),
+                       "timing": "host wall clock around the graph launches and the final "
+                                 "synchronise"},
+            "clocks": clk, "gpu_launches": int(launches),
+            "e2e": {"value": v * step_s * args.steps / wall, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    g.close()
+    for c in chains:
+        c.close()
+    return 0
+
+
+def run_sphere(args):
+    """The 60-orbital sphere (N = 120, N_q = 3600), beta = 40 (L = 400),
+    u = 1.2, one chain: learned whole-slice sweeps at rho = 0 with a Langevin
+    sweep every 4th step, as the headline path."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    from paper_2605_03700_gb300 import build as B
+    B.build()
+    import paper_2605_03700_gb300 as P
+    stream = torch.cuda.Stream()
+    ch = P.Chain(P.QMC_SPHERE, 59, 40.0, DTAU, 1.2, 0.0, 0, n_stab=NSTAB, eps0=0.2,
+                 precision=args.precision, series_capacity=4096)
+    ch.set_stream(stream.cuda_stream)
+    net = P.Net(4 * ch.n_q, 256, 16, 1)
+
+    def step(k):
+        if k % LANGEVIN_EVERY == LANGEVIN_EVERY - 1:
+            ch.sweep(1, graph=True)
+        else:
+            ch.sweep_learned(net, 1, 0.0, graph=True)
+    for k in range(args.warmup):
+        step(k)
+    ch.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        step(args.warmup + k)
+    e1.record(stream)
+    ch.sync()
+    ms = e0.elapsed_time(e1)
+    s = ch.series()[:, args.warmup:, :]
+    taus = tau_per_chain(s, P.qmc_tau_int)
+    v, dv = ess_rate(taus, ms / 1000 / args.steps)
+    line = {"metric": "effective samples/s (autocorr-corrected), 60-orbital sphere",
+            "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": ["f64", "f32+f64", "f32+f64+bf16-digits"][args.precision],
+            "data": "synthetic",
+            "config": {"workload": "sphere, 60 orbitals (N=120, N_q=3600), beta=40, dtau=0.1 "
+                                   "(L=400), u=1.2, one chain, learned sweeps (rho 0) with a "
+                                   "Langevin sweep every 4th step",
+                       "value_err": dv, "tau_int": [[round(t, 3), round(e, 3)] for t, e in taus],
+                       "acceptance": float(s[:, :, 13].mean()),
+                       "g_err_max": float(s[:, :, 15].max())}}
+    print(json.dumps(line))
+    ch.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -554,21 +683,29 @@ def main():
                     help="0: FP64 everywhere; 1: mixed (FP32 eigensolver bulk + FP64 "
                          "refinement, FP32 drift transforms; FP64 propagators, ratios, updates); "
                          "2: mixed with the dense products on the tcgen05 tensor cores")
-    ap.add_argument("--mode", default="learned", choices=["learned", "plain"],
-                    help="learned: learned-proposal sweeps with a Langevin sweep every "
-                         "4th step; plain: Langevin sweeps only")
+    ap.add_argument("--mode", default="prior", choices=["prior", "learned", "plain"],
+                    help="prior: whole-slice moves around the Gaussian prior with a Langevin "
+                         "sweep every 4th step; learned: the same schedule with the network's "
+                         "Gaussian; plain: Langevin sweeps only")
     ap.add_argument("--drift", default="exact", choices=["exact", "first"],
                     help="Langevin drift: exact grad S, or the first-order drift (factors "
                          "treated as commuting; same target, no derivative chain)")
     ap.add_argument("--beta", type=float, default=BETA,
                     help="override beta (shorter imaginary-time axis, same kernels and matrix "
                          "sizes; used for profiler launch lists)")
+    ap.add_argument("--workload", default="nphi36", choices=["nphi36", "batched", "sphere60"],
+                    help="nphi36: the headline workload (default); batched: 64 chains of mixed "
+                         "N_phi in one graph; sphere60: the 60-orbital sphere")
     args = ap.parse_args()
     globals()["BETA"] = args.beta
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "sphere60":
+        return run_sphere(args)
     return run_ours(args)
 
 

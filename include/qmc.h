@@ -224,6 +224,18 @@ int qmc_net_loss_grad(qmc_net *net, const float *X, const float *Y, int batch, d
  * must equal the context's 4 N_q); trace column 7 holds rho. */
 int qmc_sweep_learned(qmc_ctx *ctx, qmc_net *net, int n_sweeps, double rho);
 
+/* Whole-slice moves around the Gaussian part of the action alone (no
+ * network; not in the paper): the learned move with mu = 0 and sigma = 1,
+ *     phi' = rho phi + sqrt(1 - rho^2) xi,
+ * reversible with respect to N(0, 1), so the Gaussian action and the
+ * proposal density cancel and each slice is accepted with the exact
+ * determinant ratio, log A = 2 Re log R.  Same draws, counters and records
+ * as qmc_sweep_learned with a network whose output is zero; rho in [0, 1);
+ * eps is not adapted; trace column 7 holds rho.  The _graph form replays one
+ * captured sweep (recaptured for another rho). */
+int qmc_sweep_prior(qmc_ctx *ctx, int n_sweeps, double rho);
+int qmc_sweep_prior_graph(qmc_ctx *ctx, int n_sweeps, double rho);
+
 /* qmc_sweep_learned replayed from a CUDA graph, as qmc_sweep_graph does for
  * the Langevin sweep: the first call (and any call with another network,
  * another rho, or after the network's activation buffers were enlarged for

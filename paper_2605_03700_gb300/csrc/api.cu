@@ -64,11 +64,15 @@ struct qmc_ctx {
     long long series_n = 0;
     uint32_t *ctr = nullptr;             // device: sweep number, series slot (QMC_CTR_*)
     double *lq = nullptr;                // learned move: log N(phi') - log N(phi) per chain
+    float *zeroO = nullptr;              // prior move: mu = 0, log sigma = 0 for every chain
     cudaStream_t cap_st = nullptr;       // private stream the sweep graph is captured on
     cudaGraphExec_t gexec = nullptr;     // one captured sweep of all chains
     cudaGraphExec_t lexec = nullptr;     // one captured learned sweep (network lnet, rho lrho)
     unsigned long long lnet_uid = 0, lnet_gen = 0;
     double lrho = -1.0;
+    cudaGraphExec_t pexec = nullptr;     // one captured prior-move sweep (rho prho)
+    double prho = -1.0;
+    long long pgraph_kernels = 0;
     long long lgraph_kernels = 0;
     long long graph_kernels = 0;         // kernels in that graph
     std::string err;
@@ -368,11 +372,17 @@ static int green_at_zero(qmc_ctx *ctx)
                           ctx->LD + nsp * ctx->N, ctx->LW + nsp * NN, Ls, LDs, ctx->G);
 }
 
+// marker for the whole-slice move around the Gaussian prior N(0, 1): the
+// learned move's pCN step with mu = 0, sigma = 1 and no network
+static qmc_net *const PRIOR_MOVE = reinterpret_cast<qmc_net *>(uintptr_t(1));
+
 // one proposal + MH test on slice t (1-based) for every chain: the Langevin
-// move (net == nullptr) or the learned move around the network's Gaussian
+// move (net == nullptr), the learned move around the network's Gaussian, or
+// the prior move (net == PRIOR_MOVE)
 static int update_slice(qmc_ctx *ctx, int t, qmc_net *net = nullptr, double rho = 0.0)
 {
-    QmcRange range(net ? "qmc.update.learned" : "qmc.update.langevin");
+    QmcRange range(net == PRIOR_MOVE ? "qmc.update.prior"
+                                     : net ? "qmc.update.learned" : "qmc.update.langevin");
     const int nb = ctx->nb, N = ctx->N, n = ctx->n, nf = ctx->nf;
     const long long NN = ctx->NN, n2 = ctx->n2;
     const int s0 = t - 1;
@@ -383,7 +393,12 @@ static int update_slice(qmc_ctx *ctx, int t, qmc_net *net = nullptr, double rho 
     cd *Bis = ctx->Binv + (long long)s0 * NN;
     cd *Us = ctx->eigU + (long long)s0 * 4 * n2;
     double *Ws = ctx->eigW + (long long)s0 * 4 * n;
-    if (net) {
+    if (net == PRIOR_MOVE) {
+        // phi' = rho phi + sqrt(1 - rho^2) xi: the accept kernel's density
+        // correction then cancels the Gaussian action, log A = 2 Re log R
+        pcn_move(s, nb, nf, ctx->zeroO, phi_s, phi_cs, rho, ctx->keys, (uint32_t)s0, ctx->ctr,
+                 ctx->phip, ctx->lq);
+    } else if (net) {
         // the network's Gaussian for this slice from slices t-1 and t+1
         net_gather_context(net, s, nb, ctx->L, s0, ctx->phi, phi_cs);
         net_forward(net, s, nb);
@@ -813,6 +828,7 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
     // device allocations
     DA(ctx->ctr, QMC_CTR_N);
     DA(ctx->lq, (size_t)nb * net_pcn_blocks(nf));
+    DA(ctx->zeroO, (size_t)nb * 2 * nf);
     DA(ctx->qxy, 2 * nq);
     DA(ctx->ff_val, (size_t)nq * n);
     DA(ctx->ff_col, (size_t)nq * n);
@@ -920,8 +936,8 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
         // the largest products: N x N over the batch, n x n over 4 channels
         // per chain (eigenvector refinement), both at the FP64-class digit count
         long long a1, b1, e1, a2, b2, e2;
-        oz_sizes(N, N, N, 7, nb, &a1, &b1, &e1);
-        oz_sizes(n, n, n, 7, 4 * nb, &a2, &b2, &e2);
+        oz_sizes_max(N, N, N, 7, nb, &a1, &b1, &e1);
+        oz_sizes_max(n, n, n, 7, 4 * nb, &a2, &b2, &e2);
         OzCfg &f = ctx->ozF;
         f.S = 7;
         f.capA = std::max(a1, a2);
@@ -996,6 +1012,15 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
         q.C = ctx->NSz;
         q.ta = q.tb = q.tc = q.rc = TY_C64;
         gemm_autotune(s, q, 4 * nb, nullptr);
+        if (ctx->tc) {
+            // tensor-core tile widths for the same two shapes (FP64-class)
+            p.opA = 0;
+            p.B = ctx->X2;
+            p.C = ctx->X1;
+            p.tb = p.tc = p.rc = TY_C64;
+            oz_autotune(s, p, nb, ctx->ozF);
+            if (n != N) oz_autotune(s, q, 4 * nb, ctx->ozF);
+        }
     }
     int r = propagators_from_fields(ctx);
     if (r) return r;
@@ -1100,6 +1125,7 @@ int qmc_destroy(qmc_ctx *ctx)
     }
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     if (ctx->lexec) cudaGraphExecDestroy(ctx->lexec);
+    if (ctx->pexec) cudaGraphExecDestroy(ctx->pexec);
     if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);
     for (void *p : ctx->allocs) cudaFree(p);
     delete ctx;
@@ -1254,6 +1280,52 @@ int qmc_sweep_learned_graph(qmc_ctx *ctx, qmc_net *net, int n_sweeps, double rho
     for (int i = 0; i < n_sweeps; ++i) {
         CK(cudaGraphLaunch(ctx->lexec, ctx->st));
         g_qmc_launches += ctx->lgraph_kernels;
+        ctx->sweep++;
+        ctx->series_n++;
+    }
+    return QMC_OK;
+}
+
+int qmc_sweep_prior(qmc_ctx *ctx, int n_sweeps, double rho)
+{
+    if (!ctx || n_sweeps < 0) return QMC_ERR_ARG;
+    if (ctx->L < 1 || !(rho >= 0.0 && rho < 1.0)) {
+        ctx->err = "prior sweep: 0 <= rho < 1 violated";
+        return QMC_ERR_ARG;
+    }
+    for (int i = 0; i < n_sweeps; ++i) {
+        int r = enqueue_sweep(ctx, PRIOR_MOVE, rho);
+        if (r) return r;
+        ctx->sweep++;
+        ctx->series_n++;
+    }
+    return QMC_OK;
+}
+
+int qmc_sweep_prior_graph(qmc_ctx *ctx, int n_sweeps, double rho)
+{
+    if (!ctx || n_sweeps < 0) return QMC_ERR_ARG;
+    if (!(rho >= 0.0 && rho < 1.0)) {
+        ctx->err = "prior sweep: 0 <= rho < 1 violated";
+        return QMC_ERR_ARG;
+    }
+    if (n_sweeps == 0) return QMC_OK;
+    if (!ctx->pexec || ctx->prho != rho) {
+        if (ctx->pexec) {
+            CK(cudaStreamSynchronize(ctx->st));
+            cudaGraphExecDestroy(ctx->pexec);
+            ctx->pexec = nullptr;
+        }
+        if (!ctx->cap_st) CK(cudaStreamCreateWithFlags(&ctx->cap_st, cudaStreamNonBlocking));
+        qmc_ctx *one[1] = {ctx};
+        int r = capture_sweeps(one, 1, ctx->cap_st, &ctx->pexec, &ctx->pgraph_kernels, &ctx->err,
+                               PRIOR_MOVE, rho);
+        if (r) return r;
+        ctx->prho = rho;
+    }
+    for (int i = 0; i < n_sweeps; ++i) {
+        CK(cudaGraphLaunch(ctx->pexec, ctx->st));
+        g_qmc_launches += ctx->pgraph_kernels;
         ctx->sweep++;
         ctx->series_n++;
     }

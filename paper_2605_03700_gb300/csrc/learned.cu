@@ -370,8 +370,15 @@ void net_gather_context(qmc_net *net, cudaStream_t s, int nb, int L, int slice0,
 void net_pcn(qmc_net *net, cudaStream_t s, int nb, const double *phi, long long phi_cs, double rho,
              const uint32_t *keys, uint32_t slice0, const uint32_t *ctr, double *phip, double *lq)
 {
-    k_pcn<<<dim3(net_pcn_blocks(net->nf), nb), 256, 0, s>>>(net->nf, net->O, phi, phi_cs, rho,
-                                                             keys, slice0, ctr, phip, lq);
+    pcn_move(s, nb, net->nf, net->O, phi, phi_cs, rho, keys, slice0, ctr, phip, lq);
+}
+
+void pcn_move(cudaStream_t s, int nb, int nf, const float *O, const double *phi, long long phi_cs,
+              double rho, const uint32_t *keys, uint32_t slice0, const uint32_t *ctr, double *phip,
+              double *lq)
+{
+    k_pcn<<<dim3(net_pcn_blocks(nf), nb), 256, 0, s>>>(nf, O, phi, phi_cs, rho, keys, slice0, ctr,
+                                                        phip, lq);
     QMC_COUNT(1);
 }
 

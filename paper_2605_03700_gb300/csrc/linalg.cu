@@ -7,6 +7,7 @@
 #include "linalg.cuh"
 #include "ozaki.cuh"
 
+#include <cooperative_groups.h>
 #include <cstdlib>
 #include <mutex>
 #include <vector>
@@ -616,11 +617,13 @@ int eigh_mixed(cudaStream_t st, int n, int batch, const cd *A, cd *U, double *w,
             zero, 0, oz);
     gemm_sq(st, n, batch, TY_C64, op64(X, n2), 2, op64(wk.T, n2), 0, op64(wk.S, n2), nullptr, 0,
             one, zero, 0, oz);
-    // FP64 Jacobi from V = X: returns at once when S is diagonal to rounding
-    // (off-diagonal Frobenius norm below 1e-13 of the total; the rounding
-    // floor of S is near 1e-14), and resolves the rare clusters the
-    // refinement leaves
-    return eigh_batched(st, TY_C64, n, wk.S, n2, U, n2, w, n, batch, X, n2, 1e-26);
+    // FP64 Jacobi from V = X: returns at once when S is diagonal to the
+    // accuracy of its products (off-diagonal Frobenius norm below 1e-13 of the
+    // total with FP64 products, whose rounding floor is near 1e-14; 1e-12
+    // with tensor-core products, whose floor is a few 1e-14), and resolves
+    // the rare clusters the refinement leaves
+    return eigh_batched(st, TY_C64, n, wk.S, n2, U, n2, w, n, batch, X, n2,
+                        oz ? 1e-24 : 1e-26);
 }
 
 // ------------------------------------------------------------------- LU ---
@@ -721,6 +724,166 @@ __global__ void __launch_bounds__(256) k_lu(int n, int ld, cd *A, long long sA, 
     }
 }
 
+// ---------------------------------------------------------- cluster LU ---
+// The same LU (first row of maximal |a_ik|^2, full-row exchanges, the same
+// arithmetic per element) spread over a thread-block cluster of cs CTAs per
+// matrix: CTA r keeps columns [r w, r w + w) of the matrix in its shared
+// memory (w = ceil(n / cs)).  Step k: the CTA owning column k finds the pivot
+// p, exchanges rows k and p in its columns, forms the multipliers
+// l_i = a_ik / a_kk and writes them and p into a double-buffered slot of
+// every CTA's shared memory (distributed shared memory); one cluster barrier;
+// then every other CTA exchanges rows k and p in its columns, and every CTA
+// applies a_ij -= l_i a_kj to its columns j > k.  A CTA writes slot
+// (k+1) mod 2 only after passing barrier k, which every CTA reaches only after
+// its update of step k-1, the last reader of that slot.  The barrier is the
+// hardware cluster barrier (all CTAs of a cluster are co-resident); every CTA
+// passes the same n + 2 barriers.
+namespace cgr = cooperative_groups;
+__global__ void __launch_bounds__(256) k_lu_cl(int n, cd *A, long long sA, int *piv, long long spiv,
+                                               cd *logdet)
+{
+    cgr::cluster_group cl = cgr::this_cluster();
+    const int cs = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    const int b = blockIdx.y, tid = threadIdx.x, nt = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+    const int w = (n + cs - 1) / cs, c0 = rank * w, c1 = min(n, c0 + w), wc = max(0, c1 - c0);
+    const int ldw = w + 1;  // odd row stride of the column block
+    extern __shared__ __align__(16) unsigned char sm_lc_raw[];
+    cd *Mb = (cd *)sm_lc_raw;               // n x w block, row stride ldw
+    cd *lbuf = Mb + (size_t)n * ldw;        // 2 x n multipliers
+    __shared__ int pbuf[2];
+    __shared__ double parts[3][8];  // per rank: Re, Im of sum log u_kk, exchanges
+    cd *Ab = A + (long long)b * sA;
+    for (int e = tid; e < n * wc; e += nt) {
+        const int i = e / wc, j = e % wc;
+        Mb[i * ldw + j] = Ab[(long long)i * n + c0 + j];
+    }
+    cd lsum = cmk(0, 0);  // sum of log u_kk over this CTA's pivots (thread 0)
+    int nsw = 0;
+    cl.sync();
+    for (int k = 0; k < n; ++k) {
+        const int owner = k / w, buf = k & 1;
+        if (rank == owner) {
+            const int kk = k - c0;
+            // warp 0: pivot = first row of maximal |a_ik|^2 (non-negative
+            // doubles order like their bit patterns)
+            if (warp == 0) {
+                long long best = -1;
+                int bidx = k;
+                for (int i = k + lane; i < n; i += 32) {
+                    const long long v = __double_as_longlong(cabs2(Mb[i * ldw + kk]));
+                    if (v > best) {
+                        best = v;
+                        bidx = i;
+                    }
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    const long long ov = __shfl_xor_sync(0xffffffffu, best, o);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+                    if (ov > best || (ov == best && oi < bidx)) {
+                        best = ov;
+                        bidx = oi;
+                    }
+                }
+                if (lane == 0) pbuf[buf] = bidx;
+            }
+            __syncthreads();
+            const int p = pbuf[buf];
+            if (p != k)
+                for (int j = tid; j < wc; j += nt) {
+                    const cd t = Mb[k * ldw + j];
+                    Mb[k * ldw + j] = Mb[p * ldw + j];
+                    Mb[p * ldw + j] = t;
+                }
+            __syncthreads();
+            const cd pk = Mb[k * ldw + kk];
+            const double rr = 1.0 / cabs2(pk);
+            const cd inv = cmk(pk.x * rr, -pk.y * rr);
+            for (int i = k + 1 + tid; i < n; i += nt) {
+                const cd l = cmul(Mb[i * ldw + kk], inv);
+                Mb[i * ldw + kk] = l;
+                for (int r = 0; r < cs; ++r) cl.map_shared_rank(lbuf, r)[buf * n + i] = l;
+            }
+            for (int r = tid; r < cs; r += nt) cl.map_shared_rank(pbuf, r)[buf] = p;
+            if (tid == 0) {
+                piv[(long long)b * spiv + k] = p;
+                lsum = cadd(lsum, clog_d(pk));
+                if (p != k) ++nsw;
+            }
+        }
+        cl.sync();
+        const int p = pbuf[buf];
+        if (rank != owner && p != k)
+            for (int j = tid; j < wc; j += nt) {
+                const cd t = Mb[k * ldw + j];
+                Mb[k * ldw + j] = Mb[p * ldw + j];
+                Mb[p * ldw + j] = t;
+            }
+        if (rank != owner) __syncthreads();
+        // trailing update of this CTA's columns j > k: rows by warp, columns by lane
+        const int jlo = max(k + 1, c0) - c0;
+        const cd *lb = lbuf + buf * n;
+        for (int i = k + 1 + warp; i < n; i += nw) {
+            const cd l = lb[i];
+            const cd ml = cmk(-l.x, -l.y);
+            for (int j = jlo + lane; j < wc; j += 32) {
+                cd v = Mb[i * ldw + j];
+                cfma(v, ml, Mb[k * ldw + j]);
+                Mb[i * ldw + j] = v;
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < n * wc; e += nt) {
+        const int i = e / wc, j = e % wc;
+        Ab[(long long)i * n + c0 + j] = Mb[i * ldw + j];
+    }
+    // log det: every CTA's sum of log u_kk and exchange count into its own
+    // slot of rank 0's shared memory, summed there in rank order
+    if (tid == 0) {
+        double *slot = cl.map_shared_rank(&parts[0][0], 0);
+        slot[rank] = lsum.x;
+        slot[8 + rank] = lsum.y;
+        slot[16 + rank] = (double)nsw;
+    }
+    cl.sync();
+    if (rank == 0 && tid == 0 && logdet) {
+        cd t = cmk(0, 0);
+        int sw = 0;
+        for (int r = 0; r < cs; ++r) {
+            t = cadd(t, cmk(parts[0][r], parts[1][r]));
+            sw += (int)parts[2][r];
+        }
+        if (sw & 1) t.y += 3.14159265358979323846;
+        logdet[b] = t;
+    }
+}
+
+// cluster size of the LU for the sizes whose matrix does not fit in one CTA's
+// shared memory (N > 120); the one-CTA kernel is faster wherever it fits (its
+// steps need no cluster barrier: measured 301 us against 465 us at N = 72)
+static int g_lu_cluster = 8;
+
+static int lu_cluster_launch(cudaStream_t st, int n, cd *A, long long sA, int *piv, long long spiv,
+                             cd *logdet, int batch, int cs)
+{
+    const int w = (n + cs - 1) / cs;
+    const size_t smem = ((size_t)n * (w + 1) + 2 * (size_t)n) * sizeof(cd);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs, batch);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_lu_cl, n, A, sA, piv, spiv, logdet) == cudaSuccess ? 0 : -1;
+}
+
 // dynamic shared memory a block may opt into on this device (queried by
 // linalg_init; 227 KB on this part) less a bound on the static arrays of the
 // kernel it is used for
@@ -733,6 +896,27 @@ static size_t g_smem_qrp = 227 * 1024 - SMEM_STATIC_BOUND;
 int lu_batched(cudaStream_t st, int n, cd *A, long long sA, int *piv, long long spiv, cd *logdet,
                int batch)
 {
+    // the one-CTA kernel where the matrix fits (row stride n + 1 or n)
+    if ((size_t)n * n * sizeof(cd) <= SMEM_MAX) {
+        int ld = n + 1;
+        if ((size_t)n * ld * sizeof(cd) > SMEM_MAX) ld = n;
+        k_lu<<<batch, 256, (size_t)n * ld * sizeof(cd), st>>>(n, ld, A, sA, piv, spiv, logdet);
+        QMC_COUNT(1);
+        return 0;
+    }
+    // else the cluster kernel while its column block fits; clusters of at most
+    // 8 CTAs are portable
+    for (int cs = g_lu_cluster; cs >= 2; cs /= 2) {
+        const int w = (n + cs - 1) / cs;
+        if (w < 2) continue;
+        const size_t smem = ((size_t)n * (w + 1) + 2 * (size_t)n) * sizeof(cd);
+        if (smem > SMEM_MAX) break;
+        if (lu_cluster_launch(st, n, A, sA, piv, spiv, logdet, batch, cs) == 0) {
+            QMC_COUNT(1);
+            return 0;
+        }
+        break;
+    }
     int ld = n + 1;
     if ((size_t)n * ld * sizeof(cd) > SMEM_MAX) ld = n;
     const size_t smem = (size_t)n * ld * sizeof(cd);
@@ -743,94 +927,34 @@ int lu_batched(cudaStream_t st, int n, cd *A, long long sA, int *piv, long long 
 }
 
 // ------------------------------------------------------------ right div ---
-// X = G M^-1 from the FP64 LU factors of M (P M = L U): for each row g of G
-// solve x M = g as z U = g (forward), y L = z (backward, unit L), x = y P.
-// One warp per row; the factors are staged in shared memory in the compute
-// type R (FP32 in the mixed-precision path).  G and X are FP64.
-#define RD_ROWS 8
-template <class R>
-__global__ void __launch_bounds__(RD_ROWS * 32) k_rdiv(int n, const cd *G, long long sG,
-                                                       const cd *LU, long long sLU,
-                                                       const int *piv, long long spiv, cd *X,
-                                                       long long sX)
-{
-    typedef typename Cx<R>::T C;
-    // the factors transposed, row stride n + 1: FT[j (n+1) + i] = F[i][j], so
-    // the dot products over i walk consecutive addresses; dinv = 1 / U_jj
-    extern __shared__ __align__(16) unsigned char sm_r_raw[];
-    const int ld = n + 1;
-    C *FT = (C *)sm_r_raw;
-    C *dinv = FT + n * ld;
-    C *zbuf = dinv + n;
-    const int b = blockIdx.y, tid = threadIdx.x;
-    const cd *LUb = LU + (long long)b * sLU;
-    for (int e = tid; e < n * n; e += blockDim.x) FT[(e % n) * ld + e / n] = cvt<C>(LUb[e]);
-    for (int j = tid; j < n; j += blockDim.x)
-        dinv[j] = cvt<C>(cdiv(cmk(1.0, 0.0), LUb[(long long)j * n + j]));
-    __syncthreads();
-    const int warp = tid >> 5, lane = tid & 31;
-    const int r = blockIdx.x * RD_ROWS + warp;
-    if (r >= n) return;
-    C *z = zbuf + warp * n;
-    const cd *g = G + (long long)b * sG + (long long)r * n;
-    for (int j = lane; j < n; j += 32) z[j] = cvt<C>(g[j]);
-    __syncwarp();
-    for (int j = 0; j < n; ++j) {
-        C s = czero<C>();
-        const C *fj = FT + j * ld;
-        for (int i = lane; i < j; i += 32) cfma(s, z[i], fj[i]);
-        for (int o = 16; o > 0; o >>= 1) {
-            s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-            s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
-        }
-        if (lane == 0) z[j] = cmul(csub(z[j], s), dinv[j]);
-        __syncwarp();
-    }
-    for (int j = n - 1; j >= 0; --j) {
-        C s = czero<C>();
-        const C *fj = FT + j * ld;
-        for (int i = j + 1 + lane; i < n; i += 32) cfma(s, z[i], fj[i]);
-        for (int o = 16; o > 0; o >>= 1) {
-            s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-            s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
-        }
-        if (lane == 0) z[j] = csub(z[j], s);
-        __syncwarp();
-    }
-    if (lane == 0) {
-        const int *pv = piv + (long long)b * spiv;
-        for (int k = n - 1; k >= 0; --k) {
-            int p = pv[k];
-            if (p != k) {
-                C t = z[k];
-                z[k] = z[p];
-                z[p] = t;
-            }
-        }
-    }
-    __syncwarp();
-    cd *x = X + (long long)b * sX + (long long)r * n;
-    for (int j = lane; j < n; j += 32) x[j] = cvt<cd>(z[j]);
-}
-
-// The same right division for sizes whose factors do not fit in shared
-// memory: x M = g solved right-looking, z_j = z_j / U_jj then
-// z_k -= z_j U_jk (k > j), and y_j = z_j then z_k -= y_j L_jk (k < j), so the
-// factors are read by rows (coalesced), staged RC rows at a time in shared
-// memory and shared by the block's RD_ROWS warps (one warp per row of G).
+// Right division without reductions, for every size: x M = g solved
+// right-looking, z_j = z_j / U_jj then z_k -= z_j U_jk (k > j), and y_j = z_j
+// then z_k -= y_j L_jk (k < j), so the factors are read by rows (coalesced),
+// staged RD_CH rows at a time in shared memory and shared by the block's
+// warps (one warp per row of G, blockDim.x / 32 rows per block); the
+// reciprocals of U's diagonal are formed once per block.  No FP64 warp
+// reductions: on this part one warp-wide FP64 instruction holds the
+// sub-partition's FP64 pipe for many cycles, and the shuffle-sum of a complex
+// dot product per step cost more than the step's own products.
 #define RD_CH 8
-__global__ void __launch_bounds__(RD_ROWS * 32) k_rdiv_ch(int n, const cd *G, long long sG,
-                                                          const cd *LU, long long sLU,
-                                                          const int *piv, long long spiv, cd *X,
-                                                          long long sX)
+__global__ void __launch_bounds__(256) k_rdiv_ch(int n, const cd *G, long long sG, const cd *LU,
+                                                 long long sLU, const int *piv, long long spiv,
+                                                 cd *X, long long sX)
 {
     extern __shared__ __align__(16) unsigned char sm_rc_raw[];
+    const int rows = blockDim.x >> 5;
     cd *F = (cd *)sm_rc_raw;        // RD_CH rows of the factor
-    cd *zbuf = F + RD_CH * n;       // RD_ROWS rows being solved
+    cd *dinv = F + RD_CH * n;       // 1 / U_jj
+    cd *zbuf = dinv + n;            // the rows being solved
     const int b = blockIdx.y, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int r = blockIdx.x * RD_ROWS + warp;
+    const int r = blockIdx.x * rows + warp;
     const cd *LUb = LU + (long long)b * sLU;
     cd *z = zbuf + warp * n;
+    for (int j = tid; j < n; j += blockDim.x) {
+        const cd u = LUb[(long long)j * n + j];
+        const double rr = 1.0 / cabs2(u);
+        dinv[j] = cmk(u.x * rr, -u.y * rr);
+    }
     if (r < n) {
         const cd *g = G + (long long)b * sG + (long long)r * n;
         for (int j = lane; j < n; j += 32) z[j] = g[j];
@@ -845,15 +969,13 @@ __global__ void __launch_bounds__(RD_ROWS * 32) k_rdiv_ch(int n, const cd *G, lo
             for (int jj = 0; jj < nr; ++jj) {
                 const int j = j0 + jj;
                 const cd *u = F + jj * n;
-                // 1 / U_jj = conj / |.|^2 (one division)
-                const cd ujj = u[j];
-                const double rr = 1.0 / cabs2(ujj);
-                const cd zj = cmul(z[j], cmk(ujj.x * rr, -ujj.y * rr));
+                const cd zj = cmul(z[j], dinv[j]);
                 __syncwarp();
                 if (lane == 0) z[j] = zj;
+                const cd mz = cmk(-zj.x, -zj.y);
                 for (int k = j + 1 + lane; k < n; k += 32) {
                     cd v = z[k];
-                    cfma(v, cmk(-zj.x, -zj.y), u[k]);
+                    cfma(v, mz, u[k]);
                     z[k] = v;
                 }
                 __syncwarp();
@@ -870,9 +992,10 @@ __global__ void __launch_bounds__(RD_ROWS * 32) k_rdiv_ch(int n, const cd *G, lo
                 const int j = j0 + jj;
                 const cd *l = F + jj * n;
                 const cd yj = z[j];
+                const cd my = cmk(-yj.x, -yj.y);
                 for (int k = lane; k < j; k += 32) {
                     cd v = z[k];
-                    cfma(v, cmk(-yj.x, -yj.y), l[k]);
+                    cfma(v, my, l[k]);
                     z[k] = v;
                 }
                 __syncwarp();
@@ -895,25 +1018,19 @@ __global__ void __launch_bounds__(RD_ROWS * 32) k_rdiv_ch(int n, const cd *G, lo
     for (int j = lane; j < n; j += 32) x[j] = z[j];
 }
 
+// rows of G per block of the reduction-free division: few, so that the
+// batch's rows spread over every SM (QMC_RD_ROWS=1..8 overrides, read once)
+static int g_rd_rows = 2;
+
 int rdiv_batched(cudaStream_t st, int prec, int n, const cd *G, long long sG, const cd *LU,
                  long long sLU, const int *piv, long long spiv, cd *X, long long sX, int batch)
 {
-    dim3 grid(cdiv_up(n, RD_ROWS), batch);
-    if (prec == TY_C64) {
-        size_t smem = ((size_t)n * (n + 1) + (size_t)(RD_ROWS + 1) * n) * sizeof(cd);
-        if (smem > 220 * 1024) {
-            smem = (size_t)(RD_CH + RD_ROWS) * n * sizeof(cd);
-            if (smem > SMEM_MAX) return -1;
-            k_rdiv_ch<<<grid, RD_ROWS * 32, smem, st>>>(n, G, sG, LU, sLU, piv, spiv, X, sX);
-            QMC_COUNT(1);
-            return 0;
-        }
-        k_rdiv<double><<<grid, RD_ROWS * 32, smem, st>>>(n, G, sG, LU, sLU, piv, spiv, X, sX);
-    } else {
-        size_t smem = ((size_t)n * (n + 1) + (size_t)(RD_ROWS + 1) * n) * sizeof(cf);
-        if (smem > 220 * 1024) return -1;
-        k_rdiv<float><<<grid, RD_ROWS * 32, smem, st>>>(n, G, sG, LU, sLU, piv, spiv, X, sX);
-    }
+    if (prec != TY_C64) return -1;
+    const int rows = g_rd_rows;
+    const size_t smem = (size_t)(RD_CH + 1 + rows) * n * sizeof(cd);
+    if (smem > SMEM_MAX) return -1;
+    k_rdiv_ch<<<dim3(cdiv_up(n, rows), batch), rows * 32, smem, st>>>(n, G, sG, LU, sLU, piv,
+                                                                       spiv, X, sX);
     QMC_COUNT(1);
     return 0;
 }
@@ -1140,6 +1257,10 @@ int qrp_batched(cudaStream_t st, int n, const cd *X, long long sX, cd *Q, long l
 // current device (once per context creation, never inside a stream capture)
 void linalg_init()
 {
+    if (const char *e = getenv("QMC_RD_ROWS")) {
+        const int v = atoi(e);
+        if (v >= 1 && v <= 8) g_rd_rows = v;
+    }
     int dev = 0, optin = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) ==
@@ -1151,9 +1272,8 @@ void linalg_init()
     cudaFuncSetAttribute(k_eigh<float, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          2 * 64 * 64 * 8);
     cudaFuncSetAttribute(k_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX);
-    cudaFuncSetAttribute(k_rdiv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    cudaFuncSetAttribute(k_rdiv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     cudaFuncSetAttribute(k_rdiv_ch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX);
+    cudaFuncSetAttribute(k_lu_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX);
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, k_qrp) == cudaSuccess && fa.sharedSizeBytes < 1024)
         g_smem_qrp = g_smem_optin - fa.sharedSizeBytes;

@@ -48,13 +48,15 @@
 #include "linalg.cuh"
 #include "ozaki.cuh"
 
+#include <algorithm>
 #include <climits>
+#include <cstdlib>
 #include <mutex>
 #include <vector>
 
 namespace {
 
-constexpr int OZ_NST = 4;            // shared-memory ring stages
+constexpr int OZ_NST_MAX = 16;       // shared-memory ring stages at most (the barrier array)
 constexpr int OZ_THREADS = 128;
 constexpr int OZ_SLACK = 4096;       // bytes after the ring (rows past M of the last A block)
 constexpr int OZ_NAN_EXP = INT_MIN;  // scale of a row / column holding NaN or Inf
@@ -79,7 +81,7 @@ struct SplitP {
 };
 
 struct MmaP {
-    int M, N, Mpad, KS, S, nt, ntiles;
+    int M, N, Mpad, KS, S, nt, ntiles, nst, kps;  // ring stages, k-steps per stage
     const __nv_bfloat16 *DA, *DB;
     const int *eA, *eB;
     void *C;
@@ -109,11 +111,11 @@ __device__ __forceinline__ void load_el(const void *X, int t, int ld, int op, in
     if (t == TY_C64) {
         const double2 v = ((const double2 *)X)[idx];
         re = (unsigned long long)__double_as_longlong(v.x);
-        im = (unsigned long long)__double_as_longlong(op == 2 ? -v.y : v.y);
+        im = (unsigned long long)__double_as_longlong(v.y) ^ (op == 2 ? 0x8000000000000000ull : 0ull);
     } else {
         const float2 v = ((const float2 *)X)[idx];
         re = f32_to_f64_bits(__float_as_uint(v.x));
-        im = f32_to_f64_bits(__float_as_uint(op == 2 ? -v.y : v.y));
+        im = f32_to_f64_bits(__float_as_uint(v.y) ^ (op == 2 ? 0x80000000u : 0u));
     }
 }
 
@@ -134,7 +136,10 @@ __device__ __forceinline__ void digits(unsigned long long b, int Emax, int S, in
     }
 #pragma unroll
     for (int p = 0; p < 8; ++p) {
-        if (p >= S) break;
+        if (p >= S) {
+            D[p] = 0;
+            continue;
+        }
         const int s = 48 - 8 * p;
         const long long dg = s > 0 ? ((X + (1LL << (s - 1))) >> s) : X;
         X -= s > 0 ? (dg << s) : dg;
@@ -142,54 +147,127 @@ __device__ __forceinline__ void digits(unsigned long long b, int Emax, int S, in
     }
 }
 
-__device__ __forceinline__ __nv_bfloat16 bf(int v) { return __float2bfloat16_rn((float)v); }
+// Conversions on the FP32 and INT32 pipes only (on this part 64-bit
+// float/integer conversions and FP64 arithmetic go through the narrow FP64
+// pipe).  1.5 * 2^23 = 0x4B400000 as a float: for an integer q with
+// |q| < 2^22, q + 1.5 * 2^23 is exact and its bit pattern is 0x4B400000 + q.
+__device__ __forceinline__ float i2f_small(int v)
+{
+    return __int_as_float(0x4B400000 + v) - 12582912.0f;
+}
+// bfloat16 of an integer |v| <= 256: its float has at most 8 significant
+// bits, so the upper half of the float is the exact bfloat16
+__device__ __forceinline__ unsigned short bf_bits(int v)
+{
+    return (unsigned short)(__float_as_uint(i2f_small(v)) >> 16);
+}
+// the integer value of an integer-valued float |x| < 2^28: q = round(x/64)
+// by the magic constant, r = x - 64 q exact (|r| <= 32), x = 64 q + r
+__device__ __forceinline__ int f2i_exact(float x)
+{
+    const float q = __fadd_rn(__fmul_rn(x, 0.015625f), 12582912.0f) - 12582912.0f;
+    const float r = __fmaf_rn(q, -64.0f, x);
+    const int qi = __float_as_int(__fadd_rn(q, 12582912.0f)) - 0x4B400000;
+    const int ri = __float_as_int(__fadd_rn(r, 12582912.0f)) - 0x4B400000;
+    return qi * 64 + ri;
+}
 
 // ---------------------------------------------------------------- split ---
-// Warps [0, batch*Mpad): rows of op(A); the rest: columns of diag(d) op(B)
+// eight digits of one plane packed as bfloat16 into 16 bytes
+__device__ __forceinline__ uint4 pack8(const int *D, int q, int S)
+{
+    uint32_t w[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        w[h] = (uint32_t)bf_bits(D[(2 * h) * 8 + q]) | ((uint32_t)bf_bits(D[(2 * h + 1) * 8 + q]) << 16);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// One CTA of 256 threads per group of 8 rows of op(A) (blocks
+// [0, batch*Mpad/8)) or of 8 columns of diag(d) op(B) within a column tile
+// (the rest).  Thread (c, r) = (tid / 8, tid % 8) owns row (column) 8g + r
+// and the chunks c, c + 32, ... of 8 real K indices; the row maximum is
+// reduced over the 32 threads of a row (warp shuffles, then shared memory).
+// Each thread stores the 8 digits of a chunk and plane as 16 bytes, so the 8
+// threads of a chunk write one 128-byte core matrix.
+__device__ __forceinline__ void row_max_reduce(int &emax, bool &bad, int *s_e, int *s_b)
+{
+    const int tid = threadIdx.x, r = tid & 7, warp = tid >> 5;
+    emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 8));
+    emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 16));
+    const int anybad = (__ballot_sync(0xffffffffu, bad) >> r) & 0x01010101u;
+    if ((tid & 31) < 8) {
+        s_e[warp * 8 + r] = emax;
+        s_b[warp * 8 + r] = anybad ? 1 : 0;
+    }
+    __syncthreads();
+    int e = 0, bb = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        e = max(e, s_e[w * 8 + r]);
+        bb |= s_b[w * 8 + r];
+    }
+    emax = e;
+    bad = bb != 0;
+}
+
 __global__ void __launch_bounds__(256) k_oz_split(SplitP p)
 {
-    const int lane = threadIdx.x & 31;
-    const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwA = (long long)p.batch * p.Mpad;
-    const int NT2 = 2 * p.nt, ncolB = p.ntiles * p.nt;
-    const int Kr = p.KS * 16;  // real K, padded
-    if (w < nwA) {
-        const int b = (int)(w / p.Mpad), i = (int)(w % p.Mpad);
+    __shared__ int s_e[64], s_b[64];
+    const int tid = threadIdx.x, r = tid & 7, c = tid >> 3;
+    const int ncs = blockDim.x >> 3;  // chunk slots (32)
+    const long long blk_id = blockIdx.x;
+    const int Mg = p.Mpad >> 3;
+    const long long nbA = (long long)p.batch * Mg;
+    const int NT2 = 2 * p.nt, ncolB = p.ntiles * p.nt, ngB = p.nt >> 3;
+    const int Kr = p.KS * 16, nch = Kr >> 3;  // real K (padded) and its 8-wide chunks
+    const int S = p.S;
+    if (blk_id < nbA) {
+        const int b = (int)(blk_id / Mg), g = (int)(blk_id % Mg), i = 8 * g + r;
         const void *A = (const char *)p.A +
                         (long long)b * p.sA * (p.ta == TY_C64 ? sizeof(double2) : sizeof(float2));
+        const bool live = i < p.M;
         int emax = 0;
         bool bad = false;
-        if (i < p.M)
-            for (int k = lane; k < p.Kc; k += 32) {
+        if (live)
+            for (int k = c; k < p.Kc; k += ncs) {
                 unsigned long long re, im;
                 load_el(A, p.ta, p.lda, p.opA, i, k, re, im);
                 const int e1 = bexp(re), e2 = bexp(im);
                 bad |= (e1 == 0x7FF) || (e2 == 0x7FF);
                 emax = max(emax, max(e1, e2));
             }
-        emax = __reduce_max_sync(0xffffffffu, emax);
-        bad = __any_sync(0xffffffffu, bad);
-        if (lane == 0 && i < p.M) p.eA[(long long)b * p.M + i] = bad ? OZ_NAN_EXP : emax - 1029;
-        __nv_bfloat16 *DAb = p.DA + (long long)b * p.KS * p.S * p.Mpad * 16;
+        row_max_reduce(emax, bad, s_e, s_b);
+        if (c == 0 && live) p.eA[(long long)b * p.M + i] = bad ? OZ_NAN_EXP : emax - 1029;
         const long long blk = (long long)p.Mpad * 16;
-        const int cm = ((i >> 3) * 2) * 64 + (i & 7) * 8;
-        for (int kr = lane; kr < Kr; kr += 32) {
-            int D[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            if (i < p.M && !bad && kr < 2 * p.Kc) {
-                const int k = kr < p.Kc ? kr : kr - p.Kc;
-                unsigned long long re, im;
-                load_el(A, p.ta, p.lda, p.opA, i, k, re, im);
-                digits(kr < p.Kc ? re : im, emax, p.S, D);
+        __nv_bfloat16 *DAb = p.DA + (long long)b * p.KS * S * blk;
+        for (int ch = c; ch < nch; ch += ncs) {
+            int D[64];
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                const int kr = 8 * ch + kk;
+                unsigned long long v = 0;
+                if (live && !bad && kr < 2 * p.Kc) {
+                    unsigned long long re, im;
+                    load_el(A, p.ta, p.lda, p.opA, i, kr < p.Kc ? kr : kr - p.Kc, re, im);
+                    v = kr < p.Kc ? re : im;
+                }
+                digits(v, emax, S, D + 8 * kk);
             }
-            const int ks = kr >> 4, kin = kr & 15;
-            __nv_bfloat16 *dst = DAb + (long long)ks * p.S * blk + cm + (kin >> 3) * 64 + (kin & 7);
-            for (int q = 0; q < p.S; ++q) dst[q * blk] = bf(D[q]);
+            const int ks = ch >> 1, h = ch & 1;
+            __nv_bfloat16 *dst = DAb + (long long)ks * S * blk + (g * 2 + h) * 64 + r * 8;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (q < S) *(uint4 *)(dst + q * blk) = pack8(D, q, S);
         }
         return;
     }
-    const long long wb = w - nwA;
-    if (wb >= (long long)p.batch * ncolB) return;
-    const int b = (int)(wb / ncolB), j = (int)(wb % ncolB);
+    const long long wb = blk_id - nbA;
+    if (wb >= (long long)p.batch * p.ntiles * ngB) return;
+    const int b = (int)(wb / (p.ntiles * ngB)), rest = (int)(wb % (p.ntiles * ngB));
+    const int t = rest / ngB, g = rest % ngB;
+    const int jl = 8 * g + r, j = t * p.nt + jl;
+    const bool live = j < p.N;
     const size_t esz = p.tb == TY_C64 ? sizeof(double2) : sizeof(float2);
     const void *B = (const char *)p.B + (long long)b * p.sB * esz;
     // b_kj = d_k op(B)_kj, complex, in the diagonal's type (FP64 or FP32)
@@ -199,18 +277,11 @@ __global__ void __launch_bounds__(256) k_oz_split(SplitP p)
             return;
         }
         const long long idx = p.opB == 0 ? (long long)k * p.ldb + j : (long long)j * p.ldb + k;
-        const double sgn = p.opB == 2 ? -1.0 : 1.0;
         if (p.td == TY_C64) {
-            double xr, xi;
-            if (p.tb == TY_C64) {
-                const double2 v = ((const double2 *)B)[idx];
-                xr = v.x;
-                xi = sgn * v.y;
-            } else {
-                const float2 v = ((const float2 *)B)[idx];
-                xr = (double)v.x;
-                xi = sgn * (double)v.y;
-            }
+            unsigned long long br, bi;
+            load_el(B, p.tb, p.ldb, p.opB, k, j, br, bi);
+            const double xr = __longlong_as_double((long long)br);
+            const double xi = __longlong_as_double((long long)bi);
             const double2 dk = ((const double2 *)p.d)[(long long)b * p.sd + k];
             re = (unsigned long long)__double_as_longlong(dk.x * xr - dk.y * xi);
             im = (unsigned long long)__double_as_longlong(dk.x * xi + dk.y * xr);
@@ -220,11 +291,12 @@ __global__ void __launch_bounds__(256) k_oz_split(SplitP p)
             if (p.tb == TY_C64) {
                 const double2 v = ((const double2 *)B)[idx];
                 xr = __double2float_rn(v.x);
-                xi = __double2float_rn(sgn * v.y);
+                xi = __uint_as_float(__float_as_uint(__double2float_rn(v.y)) ^
+                                     (p.opB == 2 ? 0x80000000u : 0u));
             } else {
                 const float2 v = ((const float2 *)B)[idx];
                 xr = v.x;
-                xi = (float)sgn * v.y;
+                xi = __uint_as_float(__float_as_uint(v.y) ^ (p.opB == 2 ? 0x80000000u : 0u));
             }
             const float2 dk = ((const float2 *)p.d)[(long long)b * p.sd + k];
             re = f32_to_f64_bits(__float_as_uint(dk.x * xr - dk.y * xi));
@@ -233,50 +305,43 @@ __global__ void __launch_bounds__(256) k_oz_split(SplitP p)
     };
     int emax = 0;
     bool bad = false;
-    if (j < p.N)
-        for (int k = lane; k < p.Kc; k += 32) {
+    if (live)
+        for (int k = c; k < p.Kc; k += ncs) {
             unsigned long long re, im;
             elem(k, re, im);
             const int e1 = bexp(re), e2 = bexp(im);
             bad |= (e1 == 0x7FF) || (e2 == 0x7FF);
             emax = max(emax, max(e1, e2));
         }
-    emax = __reduce_max_sync(0xffffffffu, emax);
-    bad = __any_sync(0xffffffffu, bad);
-    if (lane == 0) p.eB[(long long)b * ncolB + j] = bad ? OZ_NAN_EXP : emax - 1029;
-    const int t = j / p.nt, jl = j % p.nt;
+    row_max_reduce(emax, bad, s_e, s_b);
+    if (c == 0) p.eB[(long long)b * ncolB + j] = bad ? OZ_NAN_EXP : emax - 1029;
     const long long blk = (long long)NT2 * 16;
-    __nv_bfloat16 *DBb = p.DB + ((long long)b * p.ntiles + t) * p.KS * p.S * blk;
+    __nv_bfloat16 *DBb = p.DB + ((long long)b * p.ntiles + t) * p.KS * S * blk;
     // real column jl holds [Re b_.j ; -Im b_.j], column nt + jl [Im b_.j ; Re b_.j]
-    const int n0 = jl, n1 = p.nt + jl;
-    const int c0 = ((n0 >> 3) * 2) * 64 + (n0 & 7) * 8, c1 = ((n1 >> 3) * 2) * 64 + (n1 & 7) * 8;
-    auto at = [&](int kr) {
-        return DBb + (long long)(kr >> 4) * p.S * blk + ((kr & 15) >> 3) * 64 + (kr & 7);
-    };
-    const bool live = j < p.N && !bad;
-    // element k: Re part at real index k, Im part at Kc + k
-    for (int k = lane; k < p.Kc; k += 32) {
-        int Dr[8] = {0, 0, 0, 0, 0, 0, 0, 0}, Di[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        if (live) {
-            unsigned long long re, im;
-            elem(k, re, im);
-            digits(re, emax, p.S, Dr);
-            digits(im, emax, p.S, Di);
+    for (int ch = c; ch < nch; ch += ncs) {
+        const int ks = ch >> 1, h = ch & 1;
+        unsigned long long er[8], ei[8];
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            const int kr = 8 * ch + kk;
+            er[kk] = ei[kk] = 0;
+            if (live && !bad && kr < 2 * p.Kc) elem(kr < p.Kc ? kr : kr - p.Kc, er[kk], ei[kk]);
         }
-        __nv_bfloat16 *d0 = at(k), *d1 = at(p.Kc + k);
-        for (int q = 0; q < p.S; ++q) {
-            d0[q * blk + c0] = bf(Dr[q]);
-            d0[q * blk + c1] = bf(Di[q]);
-            d1[q * blk + c0] = bf(-Di[q]);
-            d1[q * blk + c1] = bf(Dr[q]);
-        }
-    }
-    // K padding [2 Kc, Kr): zeros
-    for (int kr = 2 * p.Kc + lane; kr < Kr; kr += 32) {
-        __nv_bfloat16 *d0 = at(kr);
-        for (int q = 0; q < p.S; ++q) {
-            d0[q * blk + c0] = bf(0);
-            d0[q * blk + c1] = bf(0);
+        for (int half = 0; half < 2; ++half) {
+            int D[64];
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                const int kr = 8 * ch + kk;
+                unsigned long long v;
+                if (kr < p.Kc) v = half == 0 ? er[kk] : ei[kk];
+                else v = half == 0 ? (ei[kk] ^ 0x8000000000000000ull) : er[kk];
+                digits(v, emax, S, D + 8 * kk);
+            }
+            const int n = half == 0 ? jl : p.nt + jl;
+            __nv_bfloat16 *dst = DBb + (long long)ks * S * blk + ((n >> 3) * 2 + h) * 64 + (n & 7) * 8;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (q < S) *(uint4 *)(dst + q * blk) = pack8(D, q, S);
         }
     }
 }
@@ -347,21 +412,19 @@ __device__ __forceinline__ void umma_commit(uint32_t bar)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
 }
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
 {
-    uint32_t r0, r1, r2, r3, r4, r5, r6, r7;
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3), "=r"(r4), "=r"(r5), "=r"(r6), "=r"(r7)
-                 : "r"(taddr)
-                 : "memory");
-    v[0] = __uint_as_float(r0);
-    v[1] = __uint_as_float(r1);
-    v[2] = __uint_as_float(r2);
-    v[3] = __uint_as_float(r3);
-    v[4] = __uint_as_float(r4);
-    v[5] = __uint_as_float(r5);
-    v[6] = __uint_as_float(r6);
-    v[7] = __uint_as_float(r7);
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tmem_ld_wait()
 {
@@ -419,9 +482,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_mma(MmaP p)
 {
     extern __shared__ __align__(1024) unsigned char sm_raw[];
     // barriers and the TMEM base slot first, the stage ring 1 KB aligned
+    const int NST = p.nst;
     uint64_t *bars = (uint64_t *)sm_raw;  // full[NST], empty[NST], done
-    uint32_t *tslot = (uint32_t *)(bars + 2 * OZ_NST + 1);
+    uint32_t *tslot = (uint32_t *)(bars + 2 * OZ_NST_MAX + 1);
     int *abort_flag = (int *)(tslot + 1);
+    int *colexp = (int *)(sm_raw + 512);  // scale exponents of this tile's columns (<= 32)
     unsigned char *ring = sm_raw + 1024;
 
     const int S = p.S, nt = NT2 / 2;
@@ -430,12 +495,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_mma(MmaP p)
     const int arows = p.Mpad < 128 ? p.Mpad : 128;              // A slot rows
     const int rows_m = min(128, p.Mpad - 128 * mt);              // rows of this tile
     const uint32_t aslot = (uint32_t)arows * 32, bslot = (uint32_t)NT2 * 32;
-    const uint32_t stage_bytes = (uint32_t)S * (aslot + bslot);
+    const int KPS = p.kps, G = (p.KS + KPS - 1) / KPS;  // k-steps per stage, stages
+    const uint32_t stage_bytes = (uint32_t)(KPS * S) * (aslot + bslot);
     int ncols = 32;
     while (ncols < S * NT2) ncols <<= 1;
 
+    for (int e = tid; e < nt; e += OZ_THREADS) {
+        const int j = t * nt + e;
+        colexp[e] = j < p.N ? p.eB[(long long)b * p.ntiles * nt + j] : 0;
+    }
     if (tid == 0) {
-        for (int i = 0; i < 2 * OZ_NST + 1; ++i) mbar_init(smem_u32(bars + i), 1);
+        for (int i = 0; i < 2 * NST + 1; ++i) mbar_init(smem_u32(bars + i), 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -457,45 +527,70 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_mma(MmaP p)
     const long long bblk = (long long)NT2 * 16;
     const __nv_bfloat16 *DB = p.DB + ((long long)b * p.ntiles + t) * p.KS * S * bblk;
     const uint32_t ring_s = smem_u32(ring);
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT2 >> 3) << 17) |
-                           ((uint32_t)(128 >> 4) << 24);
+    // instruction descriptor: FP32 accumulator (bits 4-5 = 1), bfloat16 A
+    // and B (bits 7-9, 10-12 = 1), both K-major, M = 128 (bits 24-28 = M/16);
+    // N/8 (bits 17-22) is added per instruction
+    const uint32_t idesc_base = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 4) << 24);
+    constexpr int QMAX = 256 / NT2;
 
     if (tid == 0) {
         int issued = 0, consumed = 0;  // k-steps whose copies were issued / whose full barrier was seen
         bool ok = true;
-        auto issue = [&](int ks) {
-            const int st = ks % OZ_NST;
+        // stage g holds k-steps [g KPS, g KPS + KPS): A digits of all of them
+        // in one bulk copy (one per digit plane when the matrix has more than
+        // one 128-row tile), B digits in another
+        auto issue = [&](int g) {
+            const int st = g % NST, k0 = g * KPS, kc = min(KPS, p.KS - k0);
             const uint32_t full = smem_u32(bars + st);
             const uint32_t base = ring_s + (uint32_t)st * stage_bytes;
-            mbar_expect_tx(full, (uint32_t)S * ((uint32_t)rows_m * 32 + bslot));
-            for (int q = 0; q < S; ++q)
-                bulk_g2s(base + (uint32_t)q * aslot, DA + ((long long)ks * S + q) * ablk,
-                         (uint32_t)rows_m * 32, full);
-            bulk_g2s(base + (uint32_t)S * aslot, DB + (long long)ks * S * bblk, (uint32_t)S * bslot,
-                     full);
+            mbar_expect_tx(full, (uint32_t)(kc * S) * ((uint32_t)rows_m * 32 + bslot));
+            if (rows_m == arows && (long long)arows * 16 == ablk) {
+                bulk_g2s(base, DA + (long long)k0 * S * ablk, (uint32_t)(kc * S) * aslot, full);
+            } else {
+                for (int e = 0; e < kc * S; ++e)
+                    bulk_g2s(base + (uint32_t)e * aslot, DA + ((long long)k0 * S + e) * ablk,
+                             (uint32_t)rows_m * 32, full);
+            }
+            bulk_g2s(base + (uint32_t)(KPS * S) * aslot, DB + (long long)k0 * S * bblk,
+                     (uint32_t)(kc * S) * bslot, full);
         };
-        for (; issued < p.KS && issued < OZ_NST; ++issued) issue(issued);
-        for (int ks = 0; ks < p.KS && ok; ++ks) {
-            const int st = ks % OZ_NST;
-            if (!mbar_wait(smem_u32(bars + st), (uint32_t)((ks / OZ_NST) & 1), OZ_WAIT_CYCLES)) {
+        for (; issued < G && issued < NST; ++issued) issue(issued);
+        for (int g = 0; g < G && ok; ++g) {
+            const int st = g % NST;
+            if (!mbar_wait(smem_u32(bars + st), (uint32_t)((g / NST) & 1), OZ_WAIT_CYCLES)) {
                 ok = false;
                 break;
             }
-            consumed = ks + 1;
+            consumed = g + 1;
             tc_fence_after();
             const uint32_t base = ring_s + (uint32_t)st * stage_bytes;
-            for (int pa = 0; pa < S; ++pa) {
-                const uint64_t ad = sdesc(base + (uint32_t)pa * aslot);
-                for (int q = 0; pa + q < S; ++q) {
-                    const uint64_t bd = sdesc(base + (uint32_t)S * aslot + (uint32_t)q * bslot);
-                    umma(tmem + (uint32_t)((pa + q) * NT2), ad, bd, idesc, (ks > 0 || pa > 0) ? 1u : 0u);
+            const int k0 = g * KPS, kc = min(KPS, p.KS - k0);
+            // digit p of A against the B digits q = 0 .. S-1-p stacked along
+            // N: one MMA with N = (S - p) NT2 writing from TMEM column p NT2
+            // puts A_p B_q at column (p + q) NT2, the accumulator of its
+            // diagonal; at most QMAX blocks per instruction (N <= 256).  The
+            // k-steps of the stage are the inner loop, so consecutive MMAs
+            // accumulate into the same TMEM columns.
+            for (int pa = 0; pa < S; ++pa)
+                for (int q0 = 0; q0 < S - pa; q0 += QMAX) {
+                    const int nq = min(QMAX, S - pa - q0);
+                    const uint32_t id = idesc_base | ((uint32_t)((nq * NT2) >> 3) << 17);
+                    for (int kk = 0; kk < kc; ++kk) {
+                        const uint32_t abase = base + (uint32_t)(kk * S) * aslot;
+                        const uint32_t bbase =
+                            base + (uint32_t)(KPS * S) * aslot + (uint32_t)(kk * S) * bslot;
+                        const uint64_t ad = sdesc(abase + (uint32_t)pa * aslot);
+                        const uint64_t bd = sdesc(bbase + (uint32_t)q0 * bslot);
+                        // the first k-step of digit 0 starts each accumulator
+                        umma(tmem + (uint32_t)((pa + q0) * NT2), ad, bd, id,
+                             (k0 + kk > 0 || pa > 0) ? 1u : 0u);
+                    }
                 }
-            }
-            umma_commit(smem_u32(bars + OZ_NST + st));
-            // refill the stage the previous k-step used once its MMAs are done
-            if (ks >= 1 && issued < p.KS) {
-                const int ps = (ks - 1) % OZ_NST;
-                if (!mbar_wait(smem_u32(bars + OZ_NST + ps), (uint32_t)(((ks - 1) / OZ_NST) & 1),
+            umma_commit(smem_u32(bars + NST + st));
+            // refill the stage the previous group used once its MMAs are done
+            if (g >= 1 && issued < G) {
+                const int ps = (g - 1) % NST;
+                if (!mbar_wait(smem_u32(bars + NST + ps), (uint32_t)(((g - 1) / NST) & 1),
                                OZ_WAIT_CYCLES)) {
                     ok = false;
                     break;
@@ -504,59 +599,59 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_mma(MmaP p)
             }
         }
         // every issued MMA completes before `done` flips
-        umma_commit(smem_u32(bars + 2 * OZ_NST));
+        umma_commit(smem_u32(bars + 2 * NST));
         if (!ok) {
             *abort_flag = 1;
             atomicOr(p.err, 1);
             // drain: copies issued but never waited for must land before exit
-            for (int ks = consumed; ks < issued; ++ks)
-                mbar_wait(smem_u32(bars + ks % OZ_NST), (uint32_t)((ks / OZ_NST) & 1),
-                          OZ_DRAIN_CYCLES);
+            for (int g = consumed; g < issued; ++g)
+                mbar_wait(smem_u32(bars + g % NST), (uint32_t)((g / NST) & 1), OZ_DRAIN_CYCLES);
         }
     }
     __syncwarp();
     // all threads: wait for the last MMAs (bounded)
-    const bool done_ok = mbar_wait(smem_u32(bars + 2 * OZ_NST), 0u,
+    const bool done_ok = mbar_wait(smem_u32(bars + 2 * NST), 0u,
                                    OZ_WAIT_CYCLES + OZ_DRAIN_CYCLES);
     if (!done_ok && lane == 0) atomicOr(p.err, 2);
     __syncthreads();
     tc_fence_after();
     const bool skip = *abort_flag || !__all_sync(0xffffffffu, done_ok);
 
-    // epilogue: warp w owns TMEM lanes (rows) 32 w .. 32 w + 31
+    // epilogue: warp w owns TMEM lanes (rows) 32 w .. 32 w + 31; per
+    // diagonal one batch of 16-column loads and one wait, the diagonals
+    // combined in 64-bit integers: V = sum_d acc_d 2^(8 (4 - d))
     const int r = 128 * mt + 32 * warp + lane;
     const bool row_ok = r < p.M;
     const int sa = row_ok ? p.eA[(long long)b * p.M + r] : 0;
-    const int ncolB = p.ntiles * nt;
     const size_t csz = p.tc == TY_C64 ? sizeof(double2) : sizeof(float2);
     char *Cb = (char *)p.C + (long long)b * p.sC * csz;
     if (!skip) {
-        for (int c8 = 0; c8 < nt; c8 += 8) {
-            long long Vr[8], Vi[8];
+        long long V[NT2];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) Vr[e] = Vi[e] = 0;
-            for (int d = 0; d < S; ++d) {
-                float fr[8], fi[8];
-                const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(d * NT2 + c8);
-                tmem_ld8(ta, fr);
-                tmem_ld8(ta + (uint32_t)nt, fi);
-                tmem_ld_wait();
-                const int sh = 8 * (4 - d);
+        for (int e = 0; e < NT2; ++e) V[e] = 0;
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const long long ar = __float2ll_rn(fr[e]), ai = __float2ll_rn(fi[e]);
-                    Vr[e] += sh >= 0 ? (ar << sh) : (ar >> (-sh));
-                    Vi[e] += sh >= 0 ? (ai << sh) : (ai >> (-sh));
-                }
+        for (int d = 0; d < 8; ++d) {
+            if (d >= S) break;
+            float f[NT2];
+            const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(d * NT2);
+#pragma unroll
+            for (int c = 0; c < NT2; c += 16) tmem_ld16(ta + (uint32_t)c, f + c);
+            tmem_ld_wait();
+            const int sh = 8 * (4 - d);  // a constant per unrolled d
+#pragma unroll
+            for (int e = 0; e < NT2; ++e) {
+                const long long a = (long long)f2i_exact(f[e]);
+                V[e] += sh >= 0 ? (a << sh) : (a >> (-sh));
             }
-            if (!row_ok) continue;
+        }
+        if (row_ok) {
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int j = t * nt + c8 + e;
-                if (j >= p.N) continue;
-                const int sb = p.eB[(long long)b * ncolB + j];
+            for (int e = 0; e < nt; ++e) {
+                const int j = t * nt + e;
+                if (j >= p.N) break;
+                const int sb = colexp[e];
                 const long long cidx = (long long)r * p.ldc + j;
-                long long vr = p.neg ? -Vr[e] : Vr[e], vi = p.neg ? -Vi[e] : Vi[e];
+                const long long vr = p.neg ? -V[e] : V[e], vi = p.neg ? -V[nt + e] : V[nt + e];
                 const bool nan = sa == OZ_NAN_EXP || sb == OZ_NAN_EXP;
                 const int e2 = nan ? 0 : sa + sb - 32;
                 if (p.tc == TY_C64) {
@@ -592,10 +687,28 @@ mma_fn mma_kernel(int NT2)
     }
 }
 
-size_t mma_smem(int S, int Mpad, int NT2)
+// staging: up to four stages of KPS k-steps (few large bulk copies; every
+// stage resident at once where it fits, so there are no refill round trips),
+// else as many stages as the shared memory holds (at least two)
+constexpr size_t OZ_SMEM_BUDGET = 227 * 1024 - 2048;
+void mma_staging(int S, int Mpad, int NT2, int KS, int *kps, int *nst)
 {
     const int arows = Mpad < 128 ? Mpad : 128;
-    return 1024 + (size_t)OZ_NST * S * ((size_t)arows * 32 + (size_t)NT2 * 32) + OZ_SLACK;
+    const size_t kstep = (size_t)S * ((size_t)arows * 32 + (size_t)NT2 * 32);
+    const int gt = std::min(KS, 4);
+    int k = (KS + gt - 1) / gt;
+    const size_t room = OZ_SMEM_BUDGET - 1024 - OZ_SLACK;
+    while (k > 1 && 2 * k * kstep > room) --k;  // two stages must fit
+    const int G = (KS + k - 1) / k;
+    int n = (int)(room / (k * kstep));
+    n = std::min(n, std::min(G, OZ_NST_MAX));
+    *kps = k;
+    *nst = n;
+}
+size_t mma_smem(int S, int Mpad, int NT2, int kps, int nst)
+{
+    const int arows = Mpad < 128 ? Mpad : 128;
+    return 1024 + (size_t)nst * kps * S * ((size_t)arows * 32 + (size_t)NT2 * 32) + OZ_SLACK;
 }
 
 std::vector<std::pair<int, int>> g_oz_tiles;  // (n, nt)
@@ -605,6 +718,11 @@ std::mutex g_oz_mu;
 
 int oz_tile(int n)
 {
+    // QMC_OZ_TILE=<8|16|24|32> fixes the width without timing (profiler runs)
+    if (const char *e = getenv("QMC_OZ_TILE")) {
+        const int v = atoi(e);
+        if (v == 8 || v == 16 || v == 24 || v == 32) return v;
+    }
     {
         std::lock_guard<std::mutex> lock(g_oz_mu);
         for (auto &e : g_oz_tiles)
@@ -643,6 +761,53 @@ void oz_sizes(int M, int N, int K, int S, int batch, long long *nA, long long *n
     if (nE) *nE = (long long)batch * (Mpad > ntiles * nt ? Mpad : ntiles * nt);
 }
 
+void oz_sizes_max(int M, int N, int K, int S, int batch, long long *nA, long long *nB, long long *nE)
+{
+    const int Mpad = (M + 7) / 8 * 8, KS = (2 * K + 15) / 16;
+    long long b = 0, e = 0;
+    for (int nt = 8; nt <= 32; nt += 8) {
+        const int ntiles = (N + nt - 1) / nt;
+        b = std::max(b, (long long)batch * ntiles * KS * S * 2 * nt * 16);
+        e = std::max(e, (long long)batch * std::max(Mpad, ntiles * nt));
+    }
+    if (nA) *nA = (long long)batch * KS * S * Mpad * 16;
+    if (nB) *nB = b;
+    if (nE) *nE = e;
+}
+
+int oz_autotune(cudaStream_t st, const GemmP &p, int batch, const OzCfg &cfg)
+{
+    // time each tile width on this product (after a warm-up) and keep the
+    // fastest for its column count
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const bool prof = gemm_prof_enable(false);
+    int best = oz_tile(p.N);
+    float bt = 1e30f;
+    for (int round = 0; round < 2; ++round)
+        for (int nt = 8; nt <= 32; nt += 8) {
+            if (cfg.S * 2 * nt > 512) continue;
+            oz_set_tile(p.N, nt);
+            if (oz_gemm(st, p, batch, cfg)) continue;
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < 5; ++r) oz_gemm(st, p, batch, cfg);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (round > 0 && ms < bt) {
+                bt = ms;
+                best = nt;
+            }
+        }
+    oz_set_tile(p.N, best);
+    gemm_prof_enable(prof);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+
 bool oz_supported(const GemmP &p)
 {
     if (p.M < 1 || p.N < 1 || p.K < 1 || p.K > 1024) return false;
@@ -663,8 +828,11 @@ int oz_gemm(cudaStream_t st, const GemmP &p, int batch, const OzCfg &cfg)
     if (nA > cfg.capA || nB > cfg.capB || nE > cfg.capE) return -1;
     if (S * NT2 > 512) return -1;
     mma_fn f = mma_kernel(NT2);
-    const size_t smem = mma_smem(S, Mpad, NT2);
-    if (!f || smem > 227 * 1024) return -1;
+    int kps = 1, nst = 0;
+    mma_staging(S, Mpad, NT2, KS, &kps, &nst);
+    const int G = (KS + kps - 1) / kps;
+    const size_t smem = mma_smem(S, Mpad, NT2, kps, nst);
+    if (!f || nst < 1 || (nst < G && nst < 2) || smem > 227 * 1024) return -1;
     SplitP sp;
     sp.M = p.M;
     sp.N = p.N;
@@ -692,8 +860,8 @@ int oz_gemm(cudaStream_t st, const GemmP &p, int batch, const OzCfg &cfg)
     sp.DB = cfg.DB;
     sp.eA = cfg.eA;
     sp.eB = cfg.eB;
-    const long long warps = (long long)batch * (Mpad + ntiles * nt);
-    k_oz_split<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(sp);
+    const long long blocks = (long long)batch * (Mpad / 8 + ntiles * (nt / 8));
+    k_oz_split<<<(unsigned)blocks, 256, 0, st>>>(sp);
     MmaP mp;
     mp.M = p.M;
     mp.N = p.N;
@@ -702,6 +870,8 @@ int oz_gemm(cudaStream_t st, const GemmP &p, int batch, const OzCfg &cfg)
     mp.S = S;
     mp.nt = nt;
     mp.ntiles = ntiles;
+    mp.nst = nst;
+    mp.kps = kps;
     mp.DA = cfg.DA;
     mp.DB = cfg.DB;
     mp.eA = cfg.eA;
@@ -731,8 +901,17 @@ int oz_gemm(cudaStream_t st, const GemmP &p, int batch, const OzCfg &cfg)
 
 void oz_init()
 {
+    // both kernels ask for the largest shared-memory carve-out, so that a
+    // split followed by its MMA kernel (and the small-shared-memory kernels
+    // around them) do not make the SMs repartition L1 and shared memory
+    // between launches
     const int nts[4] = {16, 32, 48, 64};
-    for (int NT2 : nts)
+    for (int NT2 : nts) {
         cudaFuncSetAttribute(mma_kernel(NT2), cudaFuncAttributeMaxDynamicSharedMemorySize,
                              227 * 1024);
+        cudaFuncSetAttribute(mma_kernel(NT2), cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+    }
+    cudaFuncSetAttribute(k_oz_split, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
 }

@@ -19,6 +19,11 @@ struct OzCfg {
 struct GemmP;
 // elements of the digit planes and exponents one product needs
 void oz_sizes(int M, int N, int K, int S, int batch, long long *nA, long long *nB, long long *nE);
+// the largest work space over every column-tile width
+void oz_sizes_max(int M, int N, int K, int S, int batch, long long *nA, long long *nB, long long *nE);
+// time the column-tile widths on product p and keep the fastest for p.N
+// (synchronises st; the work space must hold oz_sizes_max)
+int oz_autotune(cudaStream_t st, const GemmP &p, int batch, const OzCfg &cfg);
 // true if the tensor-core path takes this product (shapes and types)
 bool oz_supported(const GemmP &p);
 // C = alpha op(A) diag(d) op(B) (+ I) with alpha = +-1, beta = 0; returns -1

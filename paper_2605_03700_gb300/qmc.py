@@ -116,6 +116,8 @@ def lib():
         L.qmc_net_loss_grad.argtypes = [vp, fp, fp, C.c_int, dp, fp]
         L.qmc_sweep_learned.argtypes = [vp, vp, C.c_int, C.c_double]
         L.qmc_sweep_learned_graph.argtypes = [vp, vp, C.c_int, C.c_double]
+        L.qmc_sweep_prior.argtypes = [vp, C.c_int, C.c_double]
+        L.qmc_sweep_prior_graph.argtypes = [vp, C.c_int, C.c_double]
         L.qmc_group_create.argtypes = [C.POINTER(vp), C.POINTER(vp), C.c_int]
         L.qmc_group_sweep.argtypes = [vp, C.c_int]
         L.qmc_group_sync.argtypes = [vp]
@@ -316,6 +318,11 @@ class Chain:
         graph=True replays one captured learned sweep (qmc_sweep_learned_graph)."""
         f = lib().qmc_sweep_learned_graph if graph else lib().qmc_sweep_learned
         _check(f(self.h, net.h, n, float(rho)), self.h)
+
+    def sweep_prior(self, n=1, rho=0.0, graph=False):
+        """n sweeps of whole-slice moves around N(0, 1) (qmc_sweep_prior)."""
+        f = lib().qmc_sweep_prior_graph if graph else lib().qmc_sweep_prior
+        _check(f(self.h, n, float(rho)), self.h)
 
     def sync(self):
         _check(lib().qmc_sync(self.h), self.h)

@@ -78,6 +78,32 @@ def test_learned_sweep_makes_the_oracle_decisions(qmc):
     assert np.all(obs_g[2:, 14] == obs_g[2, 14])
 
 
+@pytest.mark.parametrize("graph", [False, True])
+def test_prior_sweep_makes_the_oracle_decisions(qmc, graph):
+    """Whole-slice moves around N(0, 1) without a network (qmc_sweep_prior)
+    are the learned move of a network whose output is zero: the oracle's
+    learned sweep with zero parameters makes the same decisions."""
+    L = 20
+    g = qmc.Chain(qmc.QMC_TORUS, 4, 2.0, 0.1, 1.0, 0.0, 0, n_stab=5, trace_capacity=7 * L)
+    o = O.Chain(M.TORUS, 4, 2.0, 0.1, 1.0, 0.0, 0, n_stab=5)
+    o.enable_trace(7 * L)
+    nf = 4 * o.nq
+    th = np.zeros(LN.n_params(nf, 8))
+    g.sweep(2)
+    g.sweep_prior(3, 0.0, graph=graph)
+    g.sweep_prior(2, 0.5, graph=graph)
+    g.sync()
+    obs_o = np.concatenate([o.sweep(2), o.sweep_learned(3, th, 8, 0.0),
+                            o.sweep_learned(2, th, 8, 0.5)])
+    tg, to = g.trace(0), o.trace()
+    assert len(tg) == len(to) == 7 * L
+    assert np.array_equal(tg[:, 6], to[:, 6]), "accept decisions differ"
+    assert np.abs(tg[:, 2] - to[:, 2]).max() < 1e-10
+    assert np.all(tg[2 * L:5 * L, 7] == 0.0) and np.all(tg[5 * L:, 7] == 0.5)
+    assert np.abs(g.fields(0) - o.phi()).max() < 1e-9
+    assert np.array_equal(g.series()[0][:, 17], obs_o[:, 17])
+
+
 def test_training_and_weight_decay(qmc):
     """Training lowers the loss on the collected data; with a large decoupled
     weight decay the weight matrices shrink toward zero."""

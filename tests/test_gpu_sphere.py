@@ -68,8 +68,11 @@ def test_sphere_decision_identical(qmc, norb, beta, nsw, u, aniso, tol):
     assert np.array_equal(obs_g[:, 17], obs_o[:, 17])
 
 
-@pytest.mark.parametrize("norb", [24, 56, 60])
-def test_sphere_propagators_large_orbital_counts(qmc, norb):
+# G(0) bound per orbital count: at 60 orbitals G is conditioned ~1e11 (two
+# FP64 evaluation orders of the same ratio differ by ~5e-7 there, see
+# test_gpu_large.py), so G from identical propagators agrees to ~1e-10 only
+@pytest.mark.parametrize("norb,tol_g", [(24, 1e-10), (56, 1e-10), (60, 1e-8)])
+def test_sphere_propagators_large_orbital_counts(qmc, norb, tol_g):
     """Propagators of identical fields: the GPU form factors carry the exact
     rational values of the oracle to rounding."""
     g = qmc.Chain(qmc.QMC_SPHERE, norb - 1, 0.2, 0.1, 1.0, 0.0, 5, n_stab=2)
@@ -80,7 +83,7 @@ def test_sphere_propagators_large_orbital_counts(qmc, norb):
         B, Bi = g.propagator(t)
         Bo, Boi = o.B(t)
         assert _rel(B, Bo) < 1e-12 and _rel(Bi, Boi) < 1e-12
-    assert _rel(g.green(0), o.green()) < 1e-10
+    assert _rel(g.green(0), o.green()) < tol_g
 
 
 def test_sphere_orbital_count_option_and_limits(qmc):
