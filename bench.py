@@ -617,7 +617,7 @@ def run_batched(args):
 
 def run_sphere(args):
     """The 60-orbital sphere (N = 120, N_q = 3600), beta = 40 (L = 400),
-    u = 1.2, one chain: learned whole-slice sweeps at rho = 0 with a Langevin
+    u = 1.2, one chain: prior whole-slice sweeps at rho = 0 with a Langevin
     sweep every 4th step, as the headline path."""
     import torch
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -628,13 +628,11 @@ def run_sphere(args):
     ch = P.Chain(P.QMC_SPHERE, 59, 40.0, DTAU, 1.2, 0.0, 0, n_stab=NSTAB, eps0=0.2,
                  precision=args.precision, series_capacity=4096)
     ch.set_stream(stream.cuda_stream)
-    net = P.Net(4 * ch.n_q, 256, 16, 1)
-
     def step(k):
         if k % LANGEVIN_EVERY == LANGEVIN_EVERY - 1:
             ch.sweep(1, graph=True)
         else:
-            ch.sweep_learned(net, 1, 0.0, graph=True)
+            ch.sweep_prior(1, 0.0, graph=True)
     for k in range(args.warmup):
         step(k)
     ch.sync()
@@ -655,11 +653,73 @@ def run_sphere(args):
             "vs_baseline": None, "dtype": ["f64", "f32+f64", "f32+f64+bf16-digits"][args.precision],
             "data": "synthetic",
             "config": {"workload": "sphere, 60 orbitals (N=120, N_q=3600), beta=40, dtau=0.1 "
-                                   "(L=400), u=1.2, one chain, learned sweeps (rho 0) with a "
-                                   "Langevin sweep every 4th step",
+                                   "(L=400), u=1.2, one chain, prior whole-slice sweeps (rho 0) "
+                                   "with a Langevin sweep every 4th step",
                        "value_err": dv, "tau_int": [[round(t, 3), round(e, 3)] for t, e in taus],
                        "acceptance": float(s[:, :, 13].mean()),
                        "g_err_max": float(s[:, :, 15].max())}}
+    print(json.dumps(line))
+    ch.close()
+    return 0
+
+
+def run_torus140(args):
+    """The paper's largest torus: N_phi = 140 (N = 280, N_q = 1305), beta =
+    70 (L = 700), u = 1, anisotropy 0.1, eight chains (seeds 0-7), n_stab =
+    10, mixed precision (default: the tensor-core products, precision 2),
+    prior whole-slice sweeps with a Langevin sweep every 4th step.  A sweep
+    takes seconds, so a run times a few steps; tau_int is not resolved in
+    that window and the line reports chain-sweeps/s with ESS/s from the
+    short series."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    from paper_2605_03700_gb300 import build as B
+    B.build()
+    import paper_2605_03700_gb300 as P
+    stream = torch.cuda.Stream()
+    prec = args.precision if args.precision > 0 else 2
+    wall0 = time.perf_counter()
+    ch = P.Chain(P.QMC_TORUS, 140, 70.0, DTAU, 1.0, 0.1, 0, n_chains=NCH, seeds=np.arange(NCH),
+                 n_stab=NSTAB, eps0=0.2, precision=prec, series_capacity=256)
+    ch.set_stream(stream.cuda_stream)
+
+    def step(k):
+        if k % LANGEVIN_EVERY == LANGEVIN_EVERY - 1:
+            ch.sweep(1, graph=True)
+        else:
+            ch.sweep_prior(1, 0.0, graph=True)
+    for k in range(args.warmup):
+        step(k)
+    ch.sync()
+    clocks = Clocks(0)
+    l0 = P.qmc_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        step(args.warmup + k)
+    e1.record(stream)
+    ch.sync()
+    ms = e0.elapsed_time(e1)
+    launches = P.qmc_launch_count() - l0
+    clk = clocks.stop()
+    s = ch.series()[:, args.warmup:, :]
+    taus = tau_per_chain(s, P.qmc_tau_int)
+    v, dv = ess_rate(taus, ms / 1000 / args.steps)
+    line = {"metric": "effective samples/s (autocorr-corrected), torus N_phi=140",
+            "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": ["f64", "f32+f64", "f32+f64+bf16-digits"][prec],
+            "data": "synthetic",
+            "config": {"workload": "torus N_phi=140 (N=280, N_q=1305), beta=70, dtau=0.1 (L=700), "
+                                   "u=1, anisotropy 0.1, 8 chains seeds 0-7, n_stab=10, prior "
+                                   "whole-slice sweeps, every 4th a Langevin sweep",
+                       "precision": prec, "chain_sweeps_per_s": NCH * args.steps / (ms / 1000),
+                       "value_err": dv, "tau_series_len": int(s.shape[1]),
+                       "acceptance": float(s[:, :, 13].mean()),
+                       "g_err_max": float(s[:, :, 15].max()),
+                       "setup_s": time.perf_counter() - wall0 - ms / 1000},
+            "clocks": clk, "gpu_launches": int(launches)}
     print(json.dumps(line))
     ch.close()
     return 0
@@ -693,9 +753,11 @@ def main():
     ap.add_argument("--beta", type=float, default=BETA,
                     help="override beta (shorter imaginary-time axis, same kernels and matrix "
                          "sizes; used for profiler launch lists)")
-    ap.add_argument("--workload", default="nphi36", choices=["nphi36", "batched", "sphere60"],
+    ap.add_argument("--workload", default="nphi36",
+                    choices=["nphi36", "batched", "sphere60", "torus140"],
                     help="nphi36: the headline workload (default); batched: 64 chains of mixed "
-                         "N_phi in one graph; sphere60: the 60-orbital sphere")
+                         "N_phi in one graph; sphere60: the 60-orbital sphere; torus140: the "
+                         "largest torus, N_phi = 140")
     args = ap.parse_args()
     globals()["BETA"] = args.beta
     if args.warmup < 3:
@@ -706,6 +768,8 @@ def main():
         return run_batched(args)
     if args.workload == "sphere60":
         return run_sphere(args)
+    if args.workload == "torus140":
+        return run_torus140(args)
     return run_ours(args)
 
 

@@ -120,9 +120,12 @@ int qmc_default_opts(qmc_opts *o);
  *              {q in Z^2 : exp(-2 pi |q|^2/(4 N_phi)) > 0.01}; sphere:
  *              opts.n_orb_sphere orbitals (default N_phi + 1), N_q = n_orb^2
  *              momenta (l, m), l < n_orb.  The orbital count must lie in
- *              [2, 60] (the LU, QR and eigensolver kernels keep one matrix of
- *              up to 120 x 120 in one CTA's shared memory; the 60-orbital
- *              sphere is the largest); QMC_ERR_ARG otherwise
+ *              [2, 60]; on the torus in the mixed precisions (1, 2) up to 140
+ *              (N_phi = 140, N = 280: the FP32 eigensolver keeps its matrix in
+ *              shared memory and its eigenvectors in global memory, LU runs
+ *              over a thread-block cluster, QR with pivoting on global
+ *              scratch).  The FP64 eigensolver of precision 0 and the sphere
+ *              form factors hold at most 64 orbitals.  QMC_ERR_ARG otherwise
  *   beta, dtau inverse temperature and Trotter step; L = beta/dtau must be an
  *              integer (QMC_ERR_ARG otherwise)
  *   coupling   u, anisotropy alpha (Results, "Universal phase diagram"); the

@@ -110,6 +110,8 @@ typedef struct {
     double *trace;
     long trace_cap, trace_n;
     int mq0, mdq[8], nmdq;   /* q = 0 and the smallest momenta (measurements) */
+    int skip_energy;         /* 1: the record's energy column is left at 0 (its
+                                O(N_q N^3) Wick sum dominates a sweep at large N) */
 } orc_t;
 
 /* ---------------------------------------------------------------- RNG --- */
@@ -1317,7 +1319,7 @@ static void measure(const orc_t *o, double *obs)
     obs[0] = st0 / (5.0 * (double)o->norb * (double)o->norb);
     obs[11] = st0 != 0 ? 1.0 - std_ / st0 : 0.0;
     double E = 0.0;
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 4 && !o->skip_energy; ++i)
         for (int q = 0; q < nq; ++q) {
             int p = o->partner[q];
             zc a = 2.0 * wick_a(o, i, q, Gc), ap = 2.0 * wick_a(o, i, p, Gc);
@@ -1341,6 +1343,9 @@ void orc_set_measure_q(orc_t *o, int q0, const int *dq, int ndq)
 }
 
 void orc_measure(const orc_t *o, double *obs) { measure(o, obs); }
+
+/* test switch: skip (1) or compute (0, the default) the energy column */
+void orc_set_skip_energy(orc_t *o, int skip) { o->skip_energy = skip != 0; }
 
 /* ------------------------------------------------- state access/tests --- */
 static void to_interleaved(const zc *A, size_t n, double *out)

@@ -57,6 +57,7 @@ def lib():
         L.orc_measure_tau_stable.argtypes = [C.c_void_p, C.c_int, ip, dp]
         L.orc_measure.argtypes = [C.c_void_p, dp]
         L.orc_set_measure_q.argtypes = [C.c_void_p, C.c_int, ip, C.c_int]
+        L.orc_set_skip_energy.argtypes = [C.c_void_p, C.c_int]
         L.orc_set_trace.argtypes = [C.c_void_p, dp, C.c_long]
         L.orc_trace_count.restype = C.c_long
         L.orc_trace_count.argtypes = [C.c_void_p]
@@ -249,6 +250,11 @@ class Chain:
         obs = np.zeros(NOBS)
         lib().orc_measure(self.h, _dp(obs))
         return obs
+
+    def skip_energy(self, skip=True):
+        """Leave the energy column (12) of later records at 0: its Wick sum
+        over every momentum costs O(N_q N^3) per record, minutes at N = 280."""
+        lib().orc_set_skip_energy(self.h, 1 if skip else 0)
 
     def green(self):
         G = np.zeros((self.N, self.N), complex)

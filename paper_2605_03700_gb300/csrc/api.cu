@@ -1070,9 +1070,11 @@ int qmc_create(qmc_ctx **out, int geometry, int N_phi, double beta, double dtau,
     if (geometry != QMC_TORUS && geometry != QMC_SPHERE) {
         ctx->err = "geometry must be QMC_TORUS or QMC_SPHERE";
         code = QMC_ERR_ARG;
-    } else if (N_phi < 1 || norb < 2 || norb > 60) {
-        ctx->err = "orbital count must be in [2, 60] (LU and QR keep one matrix of up to "
-                   "120 x 120 in one CTA's shared memory)";
+    } else if (N_phi < 1 || norb < 2 || norb > 140 ||
+               (norb > 60 && (geometry == QMC_SPHERE || ctx->o.precision == 0))) {
+        ctx->err = "orbital count must be in [2, 60], or up to 140 on the torus in the mixed "
+                   "precisions (the FP64 eigensolver and the sphere form factors hold at most "
+                   "64 orbitals in one CTA)";
         code = QMC_ERR_ARG;
     } else if (!(beta > 0) || !(dtau > 0)) {
         ctx->err = "beta and dtau must be positive";

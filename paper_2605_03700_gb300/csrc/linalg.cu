@@ -12,6 +12,15 @@
 #include <mutex>
 #include <vector>
 
+// dynamic shared memory a block may opt into on this device (queried by
+// linalg_init; 227 KB on this part) less a bound on the static arrays of the
+// kernel it is used for
+static size_t g_smem_optin = 227 * 1024;
+static const size_t SMEM_STATIC_BOUND = 256;
+#define SMEM_MAX (g_smem_optin - SMEM_STATIC_BOUND)
+// the same for k_qrp with its own static arrays (set by linalg_init)
+static size_t g_smem_qrp = 227 * 1024 - SMEM_STATIC_BOUND;
+
 // ------------------------------------------------------------------ GEMM --
 // C[b] = alpha * op(A[b]) * diag(d[b]) * op(B[b]) + beta * C[b] (+ I)
 // op: 0 = none, 1 = transpose, 2 = conjugate transpose.  TT x TT output tile
@@ -476,11 +485,168 @@ __global__ void __launch_bounds__(NT) k_eigh(int n, const void *Hv, long long sH
     for (int i = tid; i < n; i += nt) wb[i] = A[i * n + i].x;
 }
 
+// The same parallel cyclic Jacobi for n > 64: the working matrix in shared
+// memory (FP32 only: 157 KB at n = 140), the rotation table of a round in
+// dynamic shared memory, and the eigenvector matrix updated in place in
+// global memory (the output buffer U, rows of 8 n bytes, each thread one
+// (row, pair) element pair per round).
+template <class R>
+__global__ void __launch_bounds__(1024) k_eigh_big(int n, const void *Hv, long long sH, void *Uv,
+                                                   long long sU, void *wv, long long sw, R tol)
+{
+    typedef typename Cx<R>::T C;
+    extern __shared__ __align__(16) unsigned char sm_eb_raw[];
+    const int m = n + (n & 1), half = m / 2;
+    C *A = (C *)sm_eb_raw;
+    C *jm = A + (size_t)n * n;             // [half][4]
+    int *rp = (int *)(jm + 4 * (size_t)half), *rq = rp + half;
+    __shared__ R red[2][32];
+    __shared__ int done;
+    __shared__ R thr;
+    const int b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    const C *Hb = (const C *)Hv + (long long)b * sH;
+    C *V = (C *)Uv + (long long)b * sU;
+    for (int e = tid; e < n * n; e += nt) {
+        A[e] = Hb[e];
+        V[e] = cmkT<C>((e / n) == (e % n) ? 1.0 : 0.0, 0.0);
+    }
+    __syncthreads();
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        R off = 0, tot = 0;
+        for (int e = tid; e < n * n; e += nt) {
+            R a2 = cabs2(A[e]);
+            tot += a2;
+            if (e / n != e % n) off += a2;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+            tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        }
+        if ((tid & 31) == 0) {
+            red[0][tid >> 5] = off;
+            red[1][tid >> 5] = tot;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            R so = 0, stt = 0;
+            for (int i = 0; i < (nt + 31) / 32; ++i) {
+                so += red[0][i];
+                stt += red[1][i];
+            }
+            done = (so == (R)0 || so <= tol * stt);
+            thr = sqrt(stt) * (R)(sizeof(R) == 4 ? 1.2e-10 : 2.2e-19);
+        }
+        __syncthreads();
+        if (done) break;
+        for (int r = 0; r < m - 1; ++r) {
+            for (int k = tid; k < half; k += nt) {
+                int a, bb;
+                if (k == 0) {
+                    a = m - 1;
+                    bb = r;
+                } else {
+                    a = (r + k) % (m - 1);
+                    bb = (r - k + (m - 1)) % (m - 1);
+                }
+                int p = a < bb ? a : bb, q = a < bb ? bb : a;
+                R c = 1, sn = 0;
+                C ph = cmkT<C>(1, 0);
+                if (q < n) {
+                    C apq = A[p * n + q];
+                    R ab = hypot(apq.x, apq.y);
+                    if (ab > thr) {
+                        R app = A[p * n + p].x, aqq = A[q * n + q].x;
+                        ph = cmkT<C>(apq.x / ab, apq.y / ab);
+                        R zeta = (aqq - app) / (2 * ab);
+                        R t = (zeta >= 0 ? (R)1 : (R)-1) / (fabs(zeta) + sqrt(zeta * zeta + (R)1));
+                        c = (R)1 / sqrt(t * t + (R)1);
+                        sn = t * c;
+                    }
+                } else {
+                    q = -1;
+                }
+                C cph = cconj(ph);
+                rp[k] = p;
+                rq[k] = q;
+                jm[4 * k + 0] = cmkT<C>(c, 0);
+                jm[4 * k + 1] = cmkT<C>(sn, 0);
+                jm[4 * k + 2] = cmkT<C>(-sn * cph.x, -sn * cph.y);
+                jm[4 * k + 3] = cmkT<C>(c * cph.x, c * cph.y);
+            }
+            __syncthreads();
+            for (int t = tid; t < half * half; t += nt) {
+                const int k1 = t / half, k2 = t % half;
+                const int p1 = rp[k1], q1 = rq[k1], p2 = rp[k2], q2 = rq[k2];
+                if (p1 >= n || p2 >= n) continue;
+                C a00 = A[p1 * n + p2];
+                C a01 = q2 >= 0 ? A[p1 * n + q2] : czero<C>();
+                C a10 = q1 >= 0 ? A[q1 * n + p2] : czero<C>();
+                C a11 = (q1 >= 0 && q2 >= 0) ? A[q1 * n + q2] : czero<C>();
+                C x00, x01, x10, x11;
+                if (q2 >= 0) {
+                    const C *j = jm + 4 * k2;
+                    x00 = cadd(cmul(a00, j[0]), cmul(a01, j[2]));
+                    x01 = cadd(cmul(a00, j[1]), cmul(a01, j[3]));
+                    x10 = cadd(cmul(a10, j[0]), cmul(a11, j[2]));
+                    x11 = cadd(cmul(a10, j[1]), cmul(a11, j[3]));
+                } else {
+                    x00 = a00; x01 = a01; x10 = a10; x11 = a11;
+                }
+                if (q1 >= 0) {
+                    const C *j = jm + 4 * k1;
+                    C h00 = cconj(j[0]), h01 = cconj(j[2]), h10 = cconj(j[1]), h11 = cconj(j[3]);
+                    a00 = cadd(cmul(h00, x00), cmul(h01, x10));
+                    a01 = cadd(cmul(h00, x01), cmul(h01, x11));
+                    a10 = cadd(cmul(h10, x00), cmul(h11, x10));
+                    a11 = cadd(cmul(h10, x01), cmul(h11, x11));
+                } else {
+                    a00 = x00; a01 = x01; a10 = x10; a11 = x11;
+                }
+                if (k1 == k2 && q1 >= 0) {
+                    a01 = czero<C>();
+                    a10 = czero<C>();
+                    a00.y = 0;
+                    a11.y = 0;
+                }
+                A[p1 * n + p2] = a00;
+                if (q2 >= 0) A[p1 * n + q2] = a01;
+                if (q1 >= 0) A[q1 * n + p2] = a10;
+                if (q1 >= 0 && q2 >= 0) A[q1 * n + q2] = a11;
+            }
+            // V <- V J in global memory: thread (row, pair), pairs fastest
+            for (int t = tid; t < half * n; t += nt) {
+                const int row = t / half, k = t % half;
+                const int p = rp[k], q = rq[k];
+                if (p >= n || q < 0) continue;
+                const C *j = jm + 4 * k;
+                C x = V[row * n + p], y = V[row * n + q];
+                V[row * n + p] = cadd(cmul(x, j[0]), cmul(y, j[2]));
+                V[row * n + q] = cadd(cmul(x, j[1]), cmul(y, j[3]));
+            }
+            __syncthreads();
+        }
+    }
+    R *wb = (R *)wv + (long long)b * sw;
+    for (int i = tid; i < n; i += nt) wb[i] = A[i * n + i].x;
+}
+
 int eigh_batched(cudaStream_t st, int prec, int n, const void *H, long long sH, void *U,
                  long long sU, void *w, long long sw, int batch, const void *V0, long long sV0,
                  double tol)
 {
-    if (n > 64 || batch <= 0) return batch <= 0 ? 0 : -1;
+    if (batch <= 0) return 0;
+    if (n > 64) {
+        // FP32 only, from the identity (the refinement that follows does the rest)
+        if (prec != TY_C32 || V0) return -1;
+        const int half = (n + 1) / 2;
+        const size_t smem = (size_t)n * n * sizeof(cf) + 4 * (size_t)half * sizeof(cf) +
+                            2 * (size_t)half * sizeof(int);
+        if (smem > SMEM_MAX) return -1;
+        k_eigh_big<float><<<batch, 1024, smem, st>>>(n, H, sH, U, sU, w, sw,
+                                                    (float)(tol > 0 ? tol : 1e-10));
+        QMC_COUNT(1);
+        return 0;
+    }
     if (prec == TY_C64) {
         size_t smem = 2ull * n * n * sizeof(cd);
         k_eigh<double, 256><<<batch, 256, smem, st>>>(n, H, sH, U, sU, w, sw, V0, sV0,
@@ -524,7 +690,7 @@ __global__ void k_cvt_c32_c64(long long m, const cf *a, cd *b)
 __global__ void __launch_bounds__(256) k_refine_E(int n, const cd *S, const cd *R, const cd *X,
                                                   cd *E, cd *Xn, int plus_I)
 {
-    __shared__ double lam[64];
+    extern __shared__ double lam[];  // n eigenvalue estimates
     __shared__ double red[3][8];
     __shared__ double omega;
     const long long off = (long long)blockIdx.x * n * n;
@@ -577,10 +743,23 @@ __global__ void __launch_bounds__(256) k_refine_E(int n, const cd *S, const cd *
     }
 }
 
+// eigenvalues Re S_ii and eigenvectors X of a refined batch (n > 64, where
+// the FP64 Jacobi check does not fit in shared memory: pairs the
+// refinement leaves unrotated lie within omega ~ 1e-6 |S| of each other, so
+// dropping their off-diagonal S costs at most ~1e-12 |S|)
+__global__ void k_take_eig(int n, long long m, const cd *S, const cd *X, cd *U, double *w)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m) return;
+    U[e] = X[e];
+    const long long nn = (long long)n * n, b = e / nn, r = e % nn;
+    if (r / n == r % n) w[b * n + r / n] = S[e].x;
+}
+
 int eigh_mixed(cudaStream_t st, int n, int batch, const cd *A, cd *U, double *w, const EighWork &wk,
                double tol32)
 {
-    if (n > 64 || batch <= 0) return batch <= 0 ? 0 : -1;
+    if (batch <= 0) return 0;
     const long long n2 = (long long)n * n, m = n2 * batch;
     const unsigned g = (unsigned)((m + 255) / 256);
     k_cvt_c64_c32<<<g, 256, 0, st>>>(m, A, wk.A32);
@@ -599,7 +778,8 @@ int eigh_mixed(cudaStream_t st, int n, int batch, const cd *A, cd *U, double *w,
                 one, zero, 0, oz);
         gemm_sq(st, n, batch, TY_C64, op64(X, n2), 2, op64(wk.T, n2), 0, op64(wk.S, n2), nullptr,
                 0, one, zero, 0, oz);
-        k_refine_E<<<batch, 256, 0, st>>>(n, wk.S, wk.R, X, wk.E, Xn, oz != nullptr);
+        k_refine_E<<<batch, 256, n * sizeof(double), st>>>(n, wk.S, wk.R, X, wk.E, Xn,
+                                                            oz != nullptr);
         QMC_COUNT(1);
         if (oz) {
             // X <- X (I + E): E came back with the identity added
@@ -617,6 +797,11 @@ int eigh_mixed(cudaStream_t st, int n, int batch, const cd *A, cd *U, double *w,
             zero, 0, oz);
     gemm_sq(st, n, batch, TY_C64, op64(X, n2), 2, op64(wk.T, n2), 0, op64(wk.S, n2), nullptr, 0,
             one, zero, 0, oz);
+    if (n > 64) {
+        k_take_eig<<<g, 256, 0, st>>>(n, m, wk.S, X, U, w);
+        QMC_COUNT(1);
+        return 0;
+    }
     // FP64 Jacobi from V = X: returns at once when S is diagonal to the
     // accuracy of its products (off-diagonal Frobenius norm below 1e-13 of the
     // total with FP64 products, whose rounding floor is near 1e-14; 1e-12
@@ -884,14 +1069,6 @@ static int lu_cluster_launch(cudaStream_t st, int n, cd *A, long long sA, int *p
     return cudaLaunchKernelEx(&cfg, k_lu_cl, n, A, sA, piv, spiv, logdet) == cudaSuccess ? 0 : -1;
 }
 
-// dynamic shared memory a block may opt into on this device (queried by
-// linalg_init; 227 KB on this part) less a bound on the static arrays of the
-// kernel it is used for
-static size_t g_smem_optin = 227 * 1024;
-static const size_t SMEM_STATIC_BOUND = 256;
-#define SMEM_MAX (g_smem_optin - SMEM_STATIC_BOUND)
-// the same for k_qrp with its own static arrays (set by linalg_init)
-static size_t g_smem_qrp = 227 * 1024 - SMEM_STATIC_BOUND;
 
 int lu_batched(cudaStream_t st, int n, cd *A, long long sA, int *piv, long long spiv, cd *logdet,
                int batch)
@@ -1053,16 +1230,23 @@ __device__ __forceinline__ cd warp_csum(cd v)
 
 __global__ void __launch_bounds__(256) k_qrp(int n, int ld, const cd *X, long long sX, cd *Q,
                                              long long sQ, double *D, long long sD, cd *V,
-                                             long long sV, int q_in_smem, void *vscr)
+                                             long long sV, int q_in_smem, void *vscr, int a_glob)
 {
     // working matrix with row stride ld = n + 1 (odd: column walks hit
     // distinct banks) where that fits, n for the largest sizes; the per-step
     // vectors follow it in shared memory, or, when vscr is given (sizes where
     // only the matrix and v fit), live in global scratch of 40 n bytes per
-    // matrix
+    // matrix; with a_glob (sizes where the matrix does not fit either) the
+    // working matrix lives in global scratch too (n^2 complex per matrix
+    // after the vectors, L2-resident) and only v stays in shared memory
     extern __shared__ cd sm_q[];
     cd *A = sm_q;
-    cd *v = A + n * ld;
+    if (a_glob) {
+        const size_t vec = (size_t)gridDim.x * n * (2 * sizeof(cd) + sizeof(double) + sizeof(int));
+        cd *base = (cd *)((unsigned char *)vscr + ((vec + 255) & ~(size_t)255));
+        A = base + (size_t)blockIdx.x * n * n;
+    }
+    cd *v = a_glob ? sm_q : A + n * ld;
     cd *sv, *sq;  // per-column dot products of the trailing matrix, per-row of Q
     double *cn;
     int *perm;
@@ -1225,7 +1409,11 @@ __global__ void __launch_bounds__(256) k_qrp(int n, int ld, const cd *X, long lo
 
 size_t qrp_scratch_bytes(int n, int batch)
 {
-    return (size_t)batch * n * (2 * sizeof(cd) + sizeof(double) + sizeof(int));
+    const size_t vec = (size_t)batch * n * (2 * sizeof(cd) + sizeof(double) + sizeof(int));
+    const size_t amat = (size_t)n * n * sizeof(cd) + (size_t)n * sizeof(cd) > g_smem_qrp
+                            ? (size_t)batch * n * n * sizeof(cd)
+                            : 0;
+    return ((vec + 255) & ~(size_t)255) + amat;
 }
 
 int qrp_batched(cudaStream_t st, int n, const cd *X, long long sX, cd *Q, long long sQ, double *D,
@@ -1238,15 +1426,20 @@ int qrp_batched(cudaStream_t st, int n, const cd *X, long long sX, cd *Q, long l
     if (base <= 220 * 1024) {
         const int qs = withq <= 220 * 1024;
         k_qrp<<<batch, 256, qs ? withq : base, st>>>(n, n + 1, X, sX, Q, sQ, D, sD, V, sV, qs,
-                                                   nullptr);
-    } else {
-        // largest sizes: matrix (row stride n + 1 if it fits, else n) and v in
+                                                   nullptr, 0);
+    } else if ((size_t)n * n * sizeof(cd) + (size_t)n * sizeof(cd) <= g_smem_qrp) {
+        // large sizes: matrix (row stride n + 1 if it fits, else n) and v in
         // shared memory, the other vectors and Q in global memory
         int ld = n + 1;
         if ((size_t)n * ld * sizeof(cd) + (size_t)n * sizeof(cd) > g_smem_qrp) ld = n;
         const size_t smem = (size_t)n * ld * sizeof(cd) + (size_t)n * sizeof(cd);
-        if (smem > g_smem_qrp || !vscr) return -1;
-        k_qrp<<<batch, 256, smem, st>>>(n, ld, X, sX, Q, sQ, D, sD, V, sV, 0, vscr);
+        if (!vscr) return -1;
+        k_qrp<<<batch, 256, smem, st>>>(n, ld, X, sX, Q, sQ, D, sD, V, sV, 0, vscr, 0);
+    } else {
+        // largest sizes: everything but v in global scratch
+        if (!vscr) return -1;
+        k_qrp<<<batch, 256, (size_t)n * sizeof(cd), st>>>(n, n, X, sX, Q, sQ, D, sD, V, sV, 0,
+                                                          vscr, 1);
     }
     QMC_COUNT(1);
     return 0;
@@ -1274,6 +1467,8 @@ void linalg_init()
     cudaFuncSetAttribute(k_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX);
     cudaFuncSetAttribute(k_rdiv_ch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX);
     cudaFuncSetAttribute(k_lu_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX);
+    cudaFuncSetAttribute(k_eigh_big<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)SMEM_MAX);
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, k_qrp) == cudaSuccess && fa.sharedSizeBytes < 1024)
         g_smem_qrp = g_smem_optin - fa.sharedSizeBytes;

@@ -57,6 +57,11 @@
 namespace {
 
 constexpr int OZ_NST_MAX = 16;       // shared-memory ring stages at most (the barrier array)
+// k-steps (of 16 real terms) per accumulator chunk: with digits |D| <= 128 a
+// digit product is at most 2^14, so a chunk of 256 terms keeps the partial
+// sums of the diagonals p + q <= 3 (at most four pairs) within 2^24, exact in
+// FP32; longer K is summed over chunks in the epilogue
+constexpr int OZ_KCH = 16;
 constexpr int OZ_THREADS = 128;
 constexpr int OZ_SLACK = 4096;       // bytes after the ring (rows past M of the last A block)
 constexpr int OZ_NAN_EXP = INT_MIN;  // scale of a row / column holding NaN or Inf
@@ -497,8 +502,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_mma(MmaP p)
     const uint32_t aslot = (uint32_t)arows * 32, bslot = (uint32_t)NT2 * 32;
     const int KPS = p.kps, G = (p.KS + KPS - 1) / KPS;  // k-steps per stage, stages
     const uint32_t stage_bytes = (uint32_t)(KPS * S) * (aslot + bslot);
+    const int KH = (p.KS + OZ_KCH - 1) / OZ_KCH;  // accumulator chunks along K
     int ncols = 32;
-    while (ncols < S * NT2) ncols <<= 1;
+    while (ncols < KH * S * NT2) ncols <<= 1;
 
     for (int e = tid; e < nt; e += OZ_THREADS) {
         const int j = t * nt + e;
@@ -581,9 +587,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_mma(MmaP p)
                             base + (uint32_t)(KPS * S) * aslot + (uint32_t)(kk * S) * bslot;
                         const uint64_t ad = sdesc(abase + (uint32_t)pa * aslot);
                         const uint64_t bd = sdesc(bbase + (uint32_t)q0 * bslot);
-                        // the first k-step of digit 0 starts each accumulator
-                        umma(tmem + (uint32_t)((pa + q0) * NT2), ad, bd, id,
-                             (k0 + kk > 0 || pa > 0) ? 1u : 0u);
+                        // K chunks of OZ_KCH k-steps (256 real terms) keep
+                        // their own accumulators; the first k-step of digit 0
+                        // in a chunk starts them
+                        const int ks = k0 + kk, kh = ks / OZ_KCH;
+                        umma(tmem + (uint32_t)((kh * S + pa + q0) * NT2), ad, bd, id,
+                             (ks % OZ_KCH > 0 || pa > 0) ? 1u : 0u);
                     }
                 }
             umma_commit(smem_u32(bars + NST + st));
@@ -629,11 +638,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_mma(MmaP p)
         long long V[NT2];
 #pragma unroll
         for (int e = 0; e < NT2; ++e) V[e] = 0;
+        for (int kh = 0; kh < KH; ++kh)
 #pragma unroll
         for (int d = 0; d < 8; ++d) {
             if (d >= S) break;
             float f[NT2];
-            const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(d * NT2);
+            const uint32_t ta =
+                tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)((kh * S + d) * NT2);
 #pragma unroll
             for (int c = 0; c < NT2; c += 16) tmem_ld16(ta + (uint32_t)c, f + c);
             tmem_ld_wait();
@@ -729,9 +740,12 @@ int oz_tile(int n)
             if (e.first == n) return e.second;
     }
     // default: the width among 8, 16, 24, 32 with the least padding, the
-    // wider one on ties
+    // wider one on ties (products with K > 128 complex terms split their
+    // accumulators along K and take the tile that leaves room for them)
+    const int KH = (n + 127) / 128;  // K chunks of a square product at 7 digits
     int best = 8, waste = 1 << 30;
     for (int nt = 8; nt <= 32; nt += 8) {
+        if (KH * 7 * 2 * nt > 512) continue;
         const int w = ((n + nt - 1) / nt) * nt - n;
         if (w <= waste) {
             waste = w;
@@ -826,7 +840,8 @@ int oz_gemm(cudaStream_t st, const GemmP &p, int batch, const OzCfg &cfg)
     long long nA, nB, nE;
     oz_sizes(p.M, p.N, p.K, S, batch, &nA, &nB, &nE);
     if (nA > cfg.capA || nB > cfg.capB || nE > cfg.capE) return -1;
-    if (S * NT2 > 512) return -1;
+    const int KH = (KS + OZ_KCH - 1) / OZ_KCH;
+    if (KH * S * NT2 > 512) return -1;
     mma_fn f = mma_kernel(NT2);
     int kps = 1, nst = 0;
     mma_staging(S, Mpad, NT2, KS, &kps, &nst);

@@ -43,13 +43,24 @@ def scheduled_chain(nphi, beta, dtau, u, anis, seed, n_stab, eps0, schedule, the
             "phi": np.array(phis), "L": o.L}
 
 
-def plain_chain(geom, size, beta, dtau, u, anis, seed, n_stab, eps0, nsweeps):
-    """Langevin sweeps of the oracle in either geometry (geom: oracle model
-    code); trace, records, G and fields at the end."""
+def plain_chain(geom, size, beta, dtau, u, anis, seed, n_stab, eps0, nsweeps, schedule=None,
+                energy=True):
+    """Sweeps of the oracle in either geometry (geom: oracle model code):
+    Langevin sweeps, or the given schedule ('P' Langevin, '0' a whole-slice
+    move around N(0, 1), i.e. the learned move with a zero network);
+    energy=False leaves the records' energy column at 0.  Trace, records, G
+    and fields at the end."""
+    import numpy as np
+    from oracle import learned as LN
     from oracle import model as M
     from oracle import oracle as O
     m = M.Model(geom, size)
     o = O.Chain(geom, size, beta, dtau, u, anis, seed, n_stab=n_stab, eps0=eps0, model=m)
-    o.enable_trace(nsweeps * o.L)
-    obs = o.sweep(nsweeps)
+    if not energy:
+        o.skip_energy()
+    schedule = schedule or "P" * nsweeps
+    o.enable_trace(len(schedule) * o.L)
+    th = np.zeros(LN.n_params(4 * o.nq, 2))
+    obs = np.concatenate([o.sweep(1) if k == "P" else o.sweep_learned(1, th, 2, 0.0)
+                          for k in schedule])
     return {"trace": o.trace(), "obs": obs, "green": o.green(), "phi": o.phi(), "L": o.L}

@@ -87,9 +87,15 @@ def test_new_entry_points_reject_invalid_arguments_before_device_work(lib):
     # standalone ratio updates: sizes beyond what the kernels hold
     assert L.qmc_ratio_update(121, 1, None, None, None, None, None) == -1
     assert L.qmc_ratio_update_noalloc(72, 1, None, None, None, None, None) == -1
-    # sphere beyond 60 orbitals
+    # sphere beyond 60 orbitals; torus beyond 140, or beyond 60 in FP64
     o = qmc.qmc_default_opts()
     assert L.qmc_create(C.byref(h), 1, 60, 1.0, 0.1, 1.0, 0.0, 0, C.byref(o)) == -1
+    assert L.qmc_create(C.byref(h), 0, 61, 1.0, 0.1, 1.0, 0.0, 0, C.byref(o)) == -1
+    o.precision = 1
+    assert L.qmc_create(C.byref(h), 0, 141, 1.0, 0.1, 1.0, 0.0, 0, C.byref(o)) == -1
+    o.precision = 3
+    assert L.qmc_create(C.byref(h), 0, 4, 1.0, 0.1, 1.0, 0.0, 0, C.byref(o)) == -1
+    assert not h.value
 
 
 def test_opts_struct_matches_the_library(lib):

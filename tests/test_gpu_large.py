@@ -112,3 +112,58 @@ def test_tensor_core_precision_tracks_the_oracle_at_n120(qmc, oracle_results):
     if first == len(tg):
         assert _rel(g.green(0), o["green"]) < 1e-6
     assert g.series()[0][:, 15].max() < 1e-8
+
+
+# --------------------------------------------------------------- N = 280 ---
+# The paper's largest torus, N_phi = 140 (N = 280, N_q = 1305), in the mixed
+# precisions: FP32 Jacobi with its eigenvectors in global memory and FP64
+# refinement, the cluster LU, QR with pivoting on global scratch, and in
+# precision 2 the tensor-core products with their accumulators split along K.
+# One sweep of whole-slice moves around N(0, 1) and one Langevin sweep of
+# L = 3 slices against the FP64 oracle (without the records' energy column,
+# whose all-momentum Wick sum costs the oracle ~8 minutes per record here):
+# the decisions and G track the oracle.
+BIG = dict(size=140, beta=0.3, u=1.0, anis=0.1, seed=3, n_stab=2, eps0=0.3, schedule="0P")
+
+
+@pytest.fixture(scope="module")
+def oracle_big():
+    from oracle import oracle as O
+    O.build()
+    pool = mp.get_context("spawn").Pool(1)
+    c = BIG
+    job = pool.apply_async(R.plain_chain, (M.TORUS, c["size"], c["beta"], 0.1, c["u"], c["anis"],
+                                           c["seed"], c["n_stab"], c["eps0"], 0),
+                           dict(schedule=c["schedule"], energy=False))
+    pool.close()
+    yield job
+    pool.terminate()
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_largest_torus_tracks_the_oracle(qmc, oracle_big, precision):
+    c = BIG
+    L = int(round(c["beta"] / 0.1))
+    g = qmc.Chain(qmc.QMC_TORUS, c["size"], c["beta"], 0.1, c["u"], c["anis"], c["seed"],
+                  n_stab=c["n_stab"], eps0=c["eps0"], precision=precision,
+                  trace_capacity=len(c["schedule"]) * L)
+    assert g.N == 280 and g.n_q == 1305
+    for k in c["schedule"]:
+        if k == "P":
+            g.sweep(1)
+        else:
+            g.sweep_prior(1, 0.0)
+    g.sync()
+    o = oracle_big.get(timeout=3000)
+    tg, to = g.trace(0), o["trace"]
+    assert len(tg) == len(to) == len(c["schedule"]) * L
+    assert np.array_equal(tg[:, 6], to[:, 6]), "accept decisions differ"
+    assert 0 < to[:, 6].sum()
+    assert np.abs(tg[:, 2] - to[:, 2]).max() < 1e-6
+    assert _rel(g.green(0), o["green"]) < 1e-6
+    assert np.abs(g.fields(0) - o["phi"]).max() < 1e-6
+    obs = g.series()[0]
+    for col in (0, 1, 11):
+        ref = o["obs"][:, col]
+        assert np.abs(obs[:, col] - ref).max() < 1e-6 * max(1, np.abs(ref).max())
+    assert obs[:, 15].max() < 1e-8 and np.all(np.isfinite(obs[:, :13]))
