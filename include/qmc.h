@@ -235,7 +235,14 @@ int qmc_sweep_learned(qmc_ctx *ctx, qmc_net *net, int n_sweeps, double rho);
  * determinant ratio, log A = 2 Re log R.  Same draws, counters and records
  * as qmc_sweep_learned with a network whose output is zero; rho in [0, 1);
  * eps is not adapted; trace column 7 holds rho.  The _graph form replays one
- * captured sweep (recaptured for another rho). */
+ * captured sweep (recaptured for another rho).
+ * A slice's proposal depends only on its own fields, which no earlier update
+ * of the sweep changes, so the proposals' eigenpairs and propagators are
+ * computed ahead in chunks of about L/4 slices, each chunk one batch over
+ * (chain, slice) on a second stream of the library, overlapping the
+ * sequential updates of the previous chunk.  The first call allocates that
+ * stage (at most ~2 GB of device memory; QMC_ERR_OOM if it fails); results
+ * are bit-identical to computing each proposal at its own update. */
 int qmc_sweep_prior(qmc_ctx *ctx, int n_sweeps, double rho);
 int qmc_sweep_prior_graph(qmc_ctx *ctx, int n_sweeps, double rho);
 

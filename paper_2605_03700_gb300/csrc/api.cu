@@ -42,6 +42,43 @@
 
 std::atomic<long long> g_qmc_launches{0};  // host-side count, any thread
 
+// One batch of (chain, slice) matrices for the propagator pipeline
+// (channel eigenpairs -> factors -> B, B^-1): its stream, size, couplings
+// per batch entry and scratch.  The sweep's own lane has one entry per chain;
+// the prior-move stage has one per (chain, slice) of a chunk of slices.
+struct Lane {
+    cudaStream_t st = nullptr;
+    int nb = 0;                 // batch entries
+    const cd *alpha = nullptr;  // [nb][4] alpha_i of each entry
+    cd *Fm = nullptr;           // channel matrices [nb][4][n^2]
+    void *Fm32 = nullptr, *U32 = nullptr;
+    float *W32 = nullptr;
+    cd *NSx = nullptr, *NSy = nullptr, *NSz = nullptr, *NSs = nullptr, *NSr = nullptr,
+       *NSe = nullptr;          // eigensolver work, [nb][4][n^2]
+    cd *X1 = nullptr, *X2 = nullptr, *M = nullptr;  // [nb][N^2]
+    const OzCfg *oz = nullptr;  // tensor-core work space of this lane (precision 2)
+};
+
+// Prior whole-slice moves precomputed in chunks of C slices.  The proposal
+// of slice t, phi'_t = rho phi_t + sqrt(1 - rho^2) xi_t, depends only on the
+// slice's own fields, which no earlier update of the sweep touches, so the
+// proposals' eigenpairs and propagators of a whole chunk are one batch of
+// nb * C entries on a second stream while the sequential updates of the
+// previous chunk run: the batch fills the GPU where one slice's eight
+// chains occupy a few SMs.  Outputs are double-buffered, [chain][z][...].
+struct PriorStage {
+    int C = 0, nchunk = 0;
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, ready[2] = {nullptr, nullptr}, used[2] = {nullptr, nullptr};
+    double *phip[2] = {nullptr, nullptr}, *lq[2] = {nullptr, nullptr}, *Wp[2] = {nullptr, nullptr};
+    cd *Up[2] = {nullptr, nullptr}, *Bp[2] = {nullptr, nullptr}, *Bpi[2] = {nullptr, nullptr};
+    cd *V = nullptr, *T = nullptr, *lam = nullptr, *Dg = nullptr, *Dgi = nullptr;
+    cd *alpha = nullptr;       // alpha of chain c repeated C times, [c][z][4]
+    cd *alpha_last = nullptr;  // the same for the last chunk's length
+    OzCfg oz;
+    Lane ln;
+};
+
 struct qmc_ctx {
     int geom = 0, nphi = 0, n = 0, N = 0, nq = 0, nf = 0, L = 0, nb = 0;
     long long NN = 0, n2 = 0;
@@ -70,6 +107,7 @@ struct qmc_ctx {
     cudaGraphExec_t lexec = nullptr;     // one captured learned sweep (network lnet, rho lrho)
     unsigned long long lnet_uid = 0, lnet_gen = 0;
     double lrho = -1.0;
+    PriorStage ps;                       // batched prior-move proposals (allocated on first use)
     cudaGraphExec_t pexec = nullptr;     // one captured prior-move sweep (rho prho)
     double prho = -1.0;
     long long pgraph_kernels = 0;
@@ -170,23 +208,48 @@ static const cd ONE = {1, 0}, ZERO = {0, 0}, MONE = {-1, 0};
 static const OzCfg *ozF(const qmc_ctx *ctx) { return ctx->tc ? &ctx->ozF : nullptr; }
 static const OzCfg *ozD(const qmc_ctx *ctx) { return ctx->tc ? &ctx->ozD : nullptr; }
 
+// the sweep's own lane: one entry per chain on the context's stream
+static Lane main_lane(const qmc_ctx *ctx)
+{
+    Lane l;
+    l.st = ctx->st;
+    l.nb = ctx->nb;
+    l.alpha = ctx->alpha_d;
+    l.Fm = ctx->Fm;
+    l.Fm32 = ctx->Fm32;
+    l.U32 = ctx->U32;
+    l.W32 = ctx->W32;
+    l.NSx = ctx->NSx;
+    l.NSy = ctx->NSy;
+    l.NSz = ctx->NSz;
+    l.NSs = ctx->NSs;
+    l.NSr = ctx->NSr;
+    l.NSe = ctx->NSe;
+    l.X1 = ctx->X1;
+    l.X2 = ctx->X2;
+    l.M = ctx->M;
+    l.oz = ozF(ctx);
+    return l;
+}
+
 // ------------------------------------------------------------ pipeline ----
 // V, T (FP64) and the factor diagonals of a slice from its eigenpairs; the
-// diagonals also in the gradient compute type when that is FP32
-static void factors_from_eig(qmc_ctx *ctx, const cd *U, long long U_cs, const double *W,
-                             long long W_cs, cd *V, cd *T, cd *lam, cd *Dg, cd *Dgi, void *lamG,
-                             void *DgG, void *DgiG)
+// diagonals also in the gradient compute type when that is FP32 (lamG
+// non-null)
+static void factors_from_eig(const qmc_ctx *ctx, const Lane &ln, const cd *U, long long U_cs,
+                             const double *W, long long W_cs, cd *V, cd *T, cd *lam, cd *Dg,
+                             cd *Dgi, void *lamG, void *DgG, void *DgiG)
 {
-    const int nb = ctx->nb, N = ctx->N;
+    const int nb = ln.nb, N = ctx->N;
     const long long NN = ctx->NN;
-    launch_build_V(ctx->st, TY_C64, nb, ctx->n, U, U_cs, V);
+    launch_build_V(ln.st, TY_C64, nb, ctx->n, U, U_cs, V);
     // T01 = V0^H V1, T12 = V1^H V2, T23 = V2^H V3
     for (int x = 0; x < 3; ++x)
-        gemm_sq(ctx->st, N, nb, TY_C64, op64(V + x * NN, 4 * NN), 2, op64(V + (x + 1) * NN, 4 * NN),
-                0, op64(T + x * NN, 3 * NN), nullptr, 0, ONE, ZERO, 0, ozF(ctx));
-    launch_lambda(ctx->st, TY_C64, nb, ctx->n, W, W_cs, ctx->alpha_d, lam, Dg, Dgi);
-    if (ctx->gp != TY_C64)
-        launch_lambda(ctx->st, ctx->gp, nb, ctx->n, W, W_cs, ctx->alpha_d, lamG, DgG, DgiG);
+        gemm_sq(ln.st, N, nb, TY_C64, op64(V + x * NN, 4 * NN), 2, op64(V + (x + 1) * NN, 4 * NN),
+                0, op64(T + x * NN, 3 * NN), nullptr, 0, ONE, ZERO, 0, ln.oz);
+    launch_lambda(ln.st, TY_C64, nb, ctx->n, W, W_cs, ln.alpha, lam, Dg, Dgi);
+    if (ctx->gp != TY_C64 && lamG)
+        launch_lambda(ln.st, ctx->gp, nb, ctx->n, W, W_cs, ln.alpha, lamG, DgG, DgiG);
 }
 
 // B = V0 D0 T01 D1 T12 D2 T23 D3 T23^H D2 T12^H D1 T01^H D0 V0^H and the
@@ -195,27 +258,29 @@ static void factors_from_eig(qmc_ctx *ctx, const cd *U, long long U_cs, const do
 // sign-free region D1, D2 are real (alpha_1,2 real: g_1,2 = -2u <= 0) and D0
 // is a phase (alpha_0 imaginary: g_0 > 0), so D0^* = D0^-1.  Five products
 // per matrix instead of seven.
-static void build_B(qmc_ctx *ctx, const cd *V, const cd *T, const cd *Dg, const cd *Dgi, cd *Bout,
-                    long long Bo_cs, cd *Biout, long long Bio_cs)
+static void build_B(const qmc_ctx *ctx, const Lane &ln, const cd *V, const cd *T, const cd *Dg,
+                    const cd *Dgi, cd *Bout, long long Bo_cs, cd *Biout, long long Bio_cs)
 {
-    const int nb = ctx->nb, N = ctx->N;
+    const int nb = ln.nb, N = ctx->N;
     const long long NN = ctx->NN, dcs = 7LL * N;
-    cudaStream_t s = ctx->st;
+    cudaStream_t s = ln.st;
+    const OzCfg *oz = ln.oz;
+    cd *X1 = ln.X1, *X2 = ln.X2, *Mx = ln.M;
     for (int inv = 0; inv < 2; ++inv) {
         const cd *dg = inv ? Dgi : Dg;   // D_j (or D_j^-1) at Trotter position j
         const cd *dgc = inv ? Dg : Dgi;  // conj of position 0: D0^* = D0^-1
         cd *dst = inv ? Biout : Bout;
         const long long dst_cs = inv ? Bio_cs : Bo_cs;
-        gemm_sq(s, N, nb, TY_C64, op64(T, 3 * NN), 0, op64(T + NN, 3 * NN), 0, op64(ctx->X1, NN),
-                dg + 1 * N, dcs, ONE, ZERO, 0, ozF(ctx));
-        gemm_sq(s, N, nb, TY_C64, op64(ctx->X1, NN), 0, op64(T + 2 * NN, 3 * NN), 0,
-                op64(ctx->X2, NN), dg + 2 * N, dcs, ONE, ZERO, 0, ozF(ctx));
-        gemm_sq(s, N, nb, TY_C64, op64(V, 4 * NN), 0, op64(ctx->X2, NN), 0, op64(ctx->X1, NN), dg,
-                dcs, ONE, ZERO, 0, ozF(ctx));
-        gemm_sq(s, N, nb, TY_C64, op64(V, 4 * NN), 0, op64(ctx->X2, NN), 0, op64(ctx->M, NN), dgc,
-                dcs, ONE, ZERO, 0, ozF(ctx));
-        gemm_sq(s, N, nb, TY_C64, op64(ctx->X1, NN), 0, op64(ctx->M, NN), 2, op64(dst, dst_cs),
-                dg + 3 * N, dcs, ONE, ZERO, 0, ozF(ctx));
+        gemm_sq(s, N, nb, TY_C64, op64(T, 3 * NN), 0, op64(T + NN, 3 * NN), 0, op64(X1, NN),
+                dg + 1 * N, dcs, ONE, ZERO, 0, oz);
+        gemm_sq(s, N, nb, TY_C64, op64(X1, NN), 0, op64(T + 2 * NN, 3 * NN), 0, op64(X2, NN),
+                dg + 2 * N, dcs, ONE, ZERO, 0, oz);
+        gemm_sq(s, N, nb, TY_C64, op64(V, 4 * NN), 0, op64(X2, NN), 0, op64(X1, NN), dg, dcs, ONE,
+                ZERO, 0, oz);
+        gemm_sq(s, N, nb, TY_C64, op64(V, 4 * NN), 0, op64(X2, NN), 0, op64(Mx, NN), dgc, dcs, ONE,
+                ZERO, 0, oz);
+        gemm_sq(s, N, nb, TY_C64, op64(X1, NN), 0, op64(Mx, NN), 2, op64(dst, dst_cs), dg + 3 * N,
+                dcs, ONE, ZERO, 0, oz);
     }
 }
 
@@ -270,26 +335,27 @@ static void gradient(qmc_ctx *ctx, const cd *Gm, const cd *V, const cd *T, const
 // (GEMMs over all chains and channels), and the FP64 Jacobi only as a check
 // that returns at once unless a near-degenerate cluster is left: the same
 // eigenpairs as the FP64 solver, at a fraction of its FP64 work.
-static int eig_of_fields(qmc_ctx *ctx, const double *phi, long long phi_cs, cd *U, double *W)
+static int eig_of_fields(const qmc_ctx *ctx, const Lane &ln, const double *phi, long long phi_cs,
+                         cd *U, double *W)
 {
-    const int nb = ctx->nb, n = ctx->n;
+    const int nb = ln.nb, n = ctx->n;
     const long long n2 = ctx->n2;
-    cudaStream_t s = ctx->st;
+    cudaStream_t s = ln.st;
     launch_assemble(s, TY_C64, nb, n, ctx->nq, phi, phi_cs, ctx->fkind, ctx->frA, ctx->frB,
-                    ctx->aptr, ctx->aq, ctx->ff_val, ctx->Fm);
-    if (ctx->gp == TY_C64) return eigh_batched(s, TY_C64, n, ctx->Fm, n2, U, n2, W, n, 4 * nb);
+                    ctx->aptr, ctx->aq, ctx->ff_val, ln.Fm);
+    if (ctx->gp == TY_C64) return eigh_batched(s, TY_C64, n, ln.Fm, n2, U, n2, W, n, 4 * nb);
     EighWork wk;
-    wk.A32 = (cf *)ctx->Fm32;
-    wk.U32 = (cf *)ctx->U32;
-    wk.w32 = ctx->W32;
-    wk.X = ctx->NSx;
-    wk.Xn = ctx->NSy;
-    wk.T = ctx->NSz;
-    wk.S = ctx->NSs;
-    wk.R = ctx->NSr;
-    wk.E = ctx->NSe;
-    wk.oz = ozF(ctx);
-    return eigh_mixed(s, n, 4 * nb, ctx->Fm, U, W, wk);
+    wk.A32 = (cf *)ln.Fm32;
+    wk.U32 = (cf *)ln.U32;
+    wk.w32 = ln.W32;
+    wk.X = ln.NSx;
+    wk.Xn = ln.NSy;
+    wk.T = ln.NSz;
+    wk.S = ln.NSs;
+    wk.R = ln.NSr;
+    wk.E = ln.NSe;
+    wk.oz = ln.oz;
+    return eigh_mixed(s, n, 4 * nb, ln.Fm, U, W, wk);
 }
 
 // G = QL DbL^-1 [DbR^-1 QR^H QL DbL^-1 + DsR WR WL^H DsL]^-1 DbR^-1 QR^H (FP64)
@@ -376,10 +442,20 @@ static int green_at_zero(qmc_ctx *ctx)
 // learned move's pCN step with mu = 0, sigma = 1 and no network
 static qmc_net *const PRIOR_MOVE = reinterpret_cast<qmc_net *>(uintptr_t(1));
 
+// A proposal computed ahead of its update: fields, density correction,
+// eigenpairs and propagators of each chain at the given chain strides.
+struct Proposal {
+    const double *phip = nullptr, *lq = nullptr, *Wp = nullptr;
+    const cd *Up = nullptr, *Bp = nullptr, *Bpi = nullptr;
+    long long phip_cs = 0, lq_cs = 0, Wp_cs = 0, Up_cs = 0, B_cs = 0;
+};
+
 // one proposal + MH test on slice t (1-based) for every chain: the Langevin
 // move (net == nullptr), the learned move around the network's Gaussian, or
-// the prior move (net == PRIOR_MOVE)
-static int update_slice(qmc_ctx *ctx, int t, qmc_net *net = nullptr, double rho = 0.0)
+// the prior move (net == PRIOR_MOVE; pre != nullptr: computed ahead by the
+// prior stage)
+static int update_slice(qmc_ctx *ctx, int t, qmc_net *net = nullptr, double rho = 0.0,
+                        const Proposal *pre = nullptr)
 {
     QmcRange range(net == PRIOR_MOVE ? "qmc.update.prior"
                                      : net ? "qmc.update.learned" : "qmc.update.langevin");
@@ -393,7 +469,23 @@ static int update_slice(qmc_ctx *ctx, int t, qmc_net *net = nullptr, double rho 
     cd *Bis = ctx->Binv + (long long)s0 * NN;
     cd *Us = ctx->eigU + (long long)s0 * 4 * n2;
     double *Ws = ctx->eigW + (long long)s0 * 4 * n;
-    if (net == PRIOR_MOVE) {
+    // the proposal's fields, eigenpairs and propagators (this slice's own
+    // buffers unless computed ahead)
+    Proposal pr;
+    pr.phip = ctx->phip;
+    pr.phip_cs = nf;
+    pr.lq = ctx->lq;
+    pr.lq_cs = net_pcn_blocks(nf);
+    pr.Up = ctx->Up;
+    pr.Up_cs = 4 * n2;
+    pr.Wp = ctx->Wp;
+    pr.Wp_cs = 4 * n;
+    pr.Bp = ctx->Bp;
+    pr.Bpi = ctx->Bpi;
+    pr.B_cs = NN;
+    if (pre) {
+        pr = *pre;
+    } else if (net == PRIOR_MOVE) {
         // phi' = rho phi + sqrt(1 - rho^2) xi: the accept kernel's density
         // correction then cancels the Gaussian action, log A = 2 Re log R
         pcn_move(s, nb, nf, ctx->zeroO, phi_s, phi_cs, rho, ctx->keys, (uint32_t)s0, ctx->ctr,
@@ -406,25 +498,28 @@ static int update_slice(qmc_ctx *ctx, int t, qmc_net *net = nullptr, double rho 
                 ctx->lq);
     } else {
         // forward gradient at the current fields
-        factors_from_eig(ctx, Us, L * 4 * n2, Ws, L * 4 * n, ctx->V, ctx->T, ctx->lam, ctx->Dg,
-                         ctx->Dgi, ctx->lamG, ctx->DgG, ctx->DgiG);
+        factors_from_eig(ctx, main_lane(ctx), Us, L * 4 * n2, Ws, L * 4 * n, ctx->V, ctx->T,
+                         ctx->lam, ctx->Dg, ctx->Dgi, ctx->lamG, ctx->DgG, ctx->DgiG);
         gradient(ctx, ctx->G, ctx->V, ctx->T, ctx->lamG, ctx->DgG, ctx->DgiG, phi_s, phi_cs,
                  ctx->grad);
         launch_propose(s, nb, nf, phi_s, phi_cs, ctx->grad, ctx->eps, ctx->keys, (uint32_t)s0,
                        ctx->ctr, ctx->phip);
     }
     // proposal factors and propagators
-    if (eig_of_fields(ctx, ctx->phip, nf, ctx->Up, ctx->Wp)) {
-        ctx->err = "eigensolver: unsupported size";
-        return QMC_ERR_ARG;
+    if (!pre) {
+        const Lane ln = main_lane(ctx);
+        if (eig_of_fields(ctx, ln, ctx->phip, nf, ctx->Up, ctx->Wp)) {
+            ctx->err = "eigensolver: unsupported size";
+            return QMC_ERR_ARG;
+        }
+        factors_from_eig(ctx, ln, ctx->Up, 4 * n2, ctx->Wp, 4 * n, ctx->Vp, ctx->Tp, ctx->lamp,
+                         ctx->Dgp, ctx->Dgip, ctx->lampG, ctx->DgpG, ctx->DgipG);
+        build_B(ctx, ln, ctx->Vp, ctx->Tp, ctx->Dgp, ctx->Dgip, ctx->Bp, NN, ctx->Bpi, NN);
     }
-    factors_from_eig(ctx, ctx->Up, 4 * n2, ctx->Wp, 4 * n, ctx->Vp, ctx->Tp, ctx->lamp, ctx->Dgp,
-                     ctx->Dgip, ctx->lampG, ctx->DgpG, ctx->DgipG);
-    build_B(ctx, ctx->Vp, ctx->Tp, ctx->Dgp, ctx->Dgip, ctx->Bp, NN, ctx->Bpi, NN);
     // M = 1 + (B' B^-1 - 1)(1 - G) in FP64: B' B^-1 - 1 is small, so its
     // absolute rounding error would be amplified by the conditioning of M
-    gemm_sq(s, N, nb, TY_C64, op64(ctx->Bp, NN), 0, op64(Bis, L * NN), 0, op64(ctx->X1, NN), nullptr,
-            0, ONE, ZERO, 0, ozF(ctx));
+    gemm_sq(s, N, nb, TY_C64, op64(pr.Bp, pr.B_cs), 0, op64(Bis, L * NN), 0, op64(ctx->X1, NN),
+            nullptr, 0, ONE, ZERO, 0, ozF(ctx));
     launch_axpyI(s, nb, N, op64(ctx->X1, NN), ONE, MONE, op64(ctx->X1, NN));
     launch_axpyI(s, nb, N, op64(ctx->G, NN), MONE, ONE, op64(ctx->X2, NN));
     gemm_sq(s, N, nb, TY_C64, op64(ctx->X1, NN), 0, op64(ctx->X2, NN), 0, op64(ctx->M, NN), nullptr,
@@ -440,12 +535,14 @@ static int update_slice(qmc_ctx *ctx, int t, qmc_net *net = nullptr, double rho 
     ap.nq = ctx->nq;
     ap.phi = phi_s;
     ap.phi_cs = phi_cs;
-    ap.phip = ctx->phip;
+    ap.phip = pr.phip;
+    ap.phip_cs = pr.phip_cs;
     ap.grad = ctx->grad;
     ap.gradp = ctx->gradp;
     ap.eps = ctx->eps;
-    ap.lq = net ? ctx->lq : nullptr;
+    ap.lq = net ? pr.lq : nullptr;
     ap.lq_n = net_pcn_blocks(nf);
+    ap.lq_cs = pr.lq_cs;
     ap.rho = rho;
     ap.alpha = ctx->alpha_d;
     ap.logdet = ctx->logdet;
@@ -468,15 +565,177 @@ static int update_slice(qmc_ctx *ctx, int t, qmc_net *net = nullptr, double rho 
     CommitP cp;
     cp.flag = ctx->flag;
     cp.nseg = 6;
-    cp.seg[0] = CommitSeg{ctx->B + (long long)s0 * NN, ctx->Bp, NN * 4, L * NN * 4, NN * 4};
-    cp.seg[1] = CommitSeg{Bis, ctx->Bpi, NN * 4, L * NN * 4, NN * 4};
-    cp.seg[2] = CommitSeg{Us, ctx->Up, 4 * n2 * 4, L * 4 * n2 * 4, 4 * n2 * 4};
-    cp.seg[3] = CommitSeg{Ws, ctx->Wp, 4 * n * 2, L * 4 * n * 2, 4 * n * 2};
+    cp.seg[0] = CommitSeg{ctx->B + (long long)s0 * NN, pr.Bp, NN * 4, L * NN * 4, pr.B_cs * 4};
+    cp.seg[1] = CommitSeg{Bis, pr.Bpi, NN * 4, L * NN * 4, pr.B_cs * 4};
+    cp.seg[2] = CommitSeg{Us, pr.Up, 4 * n2 * 4, L * 4 * n2 * 4, pr.Up_cs * 4};
+    cp.seg[3] = CommitSeg{Ws, pr.Wp, 4 * n * 2, L * 4 * n * 2, pr.Wp_cs * 2};
     cp.seg[4] = CommitSeg{ctx->G, ctx->Gp, NN * 4, NN * 4, NN * 4};
-    cp.seg[5] = CommitSeg{(void *)phi_s, ctx->phip, (long long)nf * 2, phi_cs * 2,
-                          (long long)nf * 2};
+    cp.seg[5] = CommitSeg{(void *)phi_s, pr.phip, (long long)nf * 2, phi_cs * 2, pr.phip_cs * 2};
     launch_commit(s, nb, cp);
     return 0;
+}
+
+// ------------------------------------------------- prior-move stage ----
+// device bytes the prior stage holds per (chain, slice) entry of a chunk
+static size_t prior_entry_bytes(const qmc_ctx *ctx)
+{
+    const size_t n = ctx->n, N = ctx->N, n2 = n * n, NN = N * N, nf = ctx->nf;
+    const size_t out = nf * 8 + net_pcn_blocks((int)nf) * 8 + 4 * n2 * 16 + 4 * n * 8 + 2 * NN * 16;
+    size_t scr = 4 * n2 * 16 + 6 * 4 * n2 * 16 + 4 * NN * 16 + 3 * NN * 16 + 3 * 7 * N * 16 +
+                 3 * NN * 16 + 2 * 4 * 16;
+    if (ctx->gp != TY_C64) scr += 2 * 4 * n2 * 8 + 4 * n * 4;
+    return 2 * out + scr;
+}
+
+// alpha of every chain repeated over cz slices: [c][z][4]
+static int prior_alpha(qmc_ctx *ctx, cd **dst, int cz)
+{
+    const int nb = ctx->nb;
+    std::vector<cd> rep((size_t)nb * cz * 4);
+    for (int c = 0; c < nb; ++c)
+        for (int z = 0; z < cz; ++z)
+            for (int i = 0; i < 4; ++i) rep[((size_t)c * cz + z) * 4 + i] = ctx->alpha[4 * c + i];
+    DA(*dst, rep.size());
+    CK(cudaMemcpy(*dst, rep.data(), sizeof(cd) * rep.size(), cudaMemcpyHostToDevice));
+    return 0;
+}
+
+// Allocate the prior stage once per context: chunks of C slices, C about a
+// quarter of the sweep (so the first chunk, which overlaps only the left
+// stack, stays short) and within a 2 GB budget.  Never called inside a
+// stream capture.
+static int prior_stage_ensure(qmc_ctx *ctx)
+{
+    PriorStage &ps = ctx->ps;
+    if (ps.C > 0) return 0;
+    const int nb = ctx->nb, L = ctx->L, n = ctx->n, N = ctx->N, nf = ctx->nf;
+    const long long NN = ctx->NN, n2 = ctx->n2;
+    const size_t budget = 2ull << 30;
+    const long long fit = (long long)(budget / ((size_t)nb * prior_entry_bytes(ctx)));
+    int C = (L + 3) / 4;
+    if (C > fit) C = (int)std::max(1LL, fit);
+    // batched products index the 4 channel matrices of an entry in grid z
+    if (4LL * nb * C > 65535) C = std::max(1, 65535 / (4 * nb));
+    const long long E = (long long)nb * C;  // entries of a full chunk
+    const int lqn = net_pcn_blocks(nf);
+    for (int b = 0; b < 2; ++b) {
+        DAS(ps.phip[b], E * nf);
+        DAS(ps.lq[b], E * lqn);
+        DAS(ps.Up[b], E * 4 * n2);
+        DAS(ps.Wp[b], E * 4 * n);
+        DAS(ps.Bp[b], E * NN);
+        DAS(ps.Bpi[b], E * NN);
+    }
+    Lane &l = ps.ln;
+    DAS(l.Fm, E * 4 * n2);
+    if (ctx->gp != TY_C64) {
+        DAGS(l.Fm32, E * 4 * n2);
+        DAGS(l.U32, E * 4 * n2);
+        DAS(l.W32, E * 4 * n);
+    }
+    DAS(l.NSx, E * 4 * n2);
+    DAS(l.NSy, E * 4 * n2);
+    DAS(l.NSz, E * 4 * n2);
+    DAS(l.NSs, E * 4 * n2);
+    DAS(l.NSr, E * 4 * n2);
+    DAS(l.NSe, E * 4 * n2);
+    DAS(l.X1, E * NN);
+    DAS(l.X2, E * NN);
+    DAS(l.M, E * NN);
+    DAS(ps.V, E * 4 * NN);
+    DAS(ps.T, E * 3 * NN);
+    DAS(ps.lam, E * 7 * N);
+    DAS(ps.Dg, E * 7 * N);
+    DAS(ps.Dgi, E * 7 * N);
+    int r = prior_alpha(ctx, &ps.alpha, C);
+    if (r) return r;
+    const int last = L - (L + C - 1) / C * C + C;  // slices of the last chunk
+    if (last != C) {
+        r = prior_alpha(ctx, &ps.alpha_last, last);
+        if (r) return r;
+    } else {
+        ps.alpha_last = ps.alpha;
+    }
+    if (ctx->tc) {
+        long long a1, b1, e1, a2, b2, e2;
+        oz_sizes_max(N, N, N, 7, (int)E, &a1, &b1, &e1);
+        oz_sizes_max(n, n, n, 7, (int)(4 * E), &a2, &b2, &e2);
+        OzCfg &f = ps.oz;
+        f.S = 7;
+        f.capA = std::max(a1, a2);
+        f.capB = std::max(b1, b2);
+        f.capE = std::max(e1, e2);
+        DAS(f.DA, f.capA);
+        DAS(f.DB, f.capB);
+        DAS(f.eA, f.capE);
+        DAS(f.eB, f.capE);
+        f.err = ctx->ozerr;
+        l.oz = &ps.oz;
+    }
+    CK(cudaStreamCreateWithFlags(&ps.side, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&ps.fork, cudaEventDisableTiming));
+    for (int b = 0; b < 2; ++b) {
+        CK(cudaEventCreateWithFlags(&ps.ready[b], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ps.used[b], cudaEventDisableTiming));
+    }
+    ps.nchunk = (L + C - 1) / C;
+    ps.C = C;
+    return 0;
+}
+
+// slices in chunk j
+static int prior_chunk_len(const qmc_ctx *ctx, int j)
+{
+    return std::min(ctx->ps.C, ctx->L - j * ctx->ps.C);
+}
+
+// Proposals of chunk j into buffer j % 2 on the side stream: the fields of
+// every (chain, slice) entry, then their eigenpairs, factors and propagators
+// as one batch.  Entries are [c][z] at the chunk's own length.
+static int enqueue_prior_chunk(qmc_ctx *ctx, int j, double rho)
+{
+    PriorStage &ps = ctx->ps;
+    const int b = j & 1, t0 = j * ps.C, cz = prior_chunk_len(ctx, j);
+    const int nf = ctx->nf, n = ctx->n;
+    const long long NN = ctx->NN, n2 = ctx->n2;
+    Lane ln = ps.ln;
+    ln.st = ps.side;
+    ln.nb = ctx->nb * cz;
+    ln.alpha = cz == ps.C ? ps.alpha : ps.alpha_last;
+    pcn_move(ps.side, ctx->nb, nf, ctx->zeroO, ctx->phi + (long long)t0 * nf,
+             (long long)ctx->L * nf, rho, ctx->keys, (uint32_t)t0, ctx->ctr, ps.phip[b], ps.lq[b],
+             cz);
+    if (eig_of_fields(ctx, ln, ps.phip[b], nf, ps.Up[b], ps.Wp[b])) {
+        ctx->err = "eigensolver: unsupported size";
+        return QMC_ERR_ARG;
+    }
+    factors_from_eig(ctx, ln, ps.Up[b], 4 * n2, ps.Wp[b], 4 * n, ps.V, ps.T, ps.lam, ps.Dg, ps.Dgi,
+                     nullptr, nullptr, nullptr);
+    build_B(ctx, ln, ps.V, ps.T, ps.Dg, ps.Dgi, ps.Bp[b], NN, ps.Bpi[b], NN);
+    CK(cudaEventRecord(ps.ready[b], ps.side));
+    return 0;
+}
+
+// the precomputed proposal of 0-based slice s0 (in chunk s0 / C)
+static Proposal prior_proposal(const qmc_ctx *ctx, int s0)
+{
+    const PriorStage &ps = ctx->ps;
+    const int j = s0 / ps.C, z = s0 - j * ps.C, b = j & 1, cz = prior_chunk_len(ctx, j);
+    const int nf = ctx->nf, n = ctx->n, lqn = net_pcn_blocks(nf);
+    const long long NN = ctx->NN, n2 = ctx->n2;
+    Proposal p;
+    p.phip = ps.phip[b] + (long long)z * nf;
+    p.phip_cs = (long long)cz * nf;
+    p.lq = ps.lq[b] + (long long)z * lqn;
+    p.lq_cs = (long long)cz * lqn;
+    p.Up = ps.Up[b] + (long long)z * 4 * n2;
+    p.Up_cs = (long long)cz * 4 * n2;
+    p.Wp = ps.Wp[b] + (long long)z * 4 * n;
+    p.Wp_cs = (long long)cz * 4 * n;
+    p.Bp = ps.Bp[b] + (long long)z * NN;
+    p.Bpi = ps.Bpi[b] + (long long)z * NN;
+    p.B_cs = (long long)cz * NN;
+    return p;
 }
 
 // right stack advanced over slices (prev, t], fresh G(t) and its error
@@ -607,7 +866,18 @@ static void measure_into(qmc_ctx *ctx, double *out, long long out_cs,
 static int enqueue_sweep(qmc_ctx *ctx, qmc_net *net = nullptr, double rho = 0.0)
 {
     QmcRange range("qmc.sweep");
-    int r = build_left_stack(ctx);
+    PriorStage &ps = ctx->ps;
+    // prior moves: the first two chunks of proposals start on the side
+    // stream while the left stack is built
+    const bool staged = net == PRIOR_MOVE && ps.C > 0;
+    int r = 0;
+    if (staged) {
+        CK(cudaEventRecord(ps.fork, ctx->st));
+        CK(cudaStreamWaitEvent(ps.side, ps.fork, 0));
+        for (int j = 0; j < std::min(2, ps.nchunk); ++j)
+            if ((r = enqueue_prior_chunk(ctx, j, rho))) return r;
+    }
+    r = build_left_stack(ctx);
     if (r) return r;
     r = green_at_zero(ctx);
     if (r) return r;
@@ -615,14 +885,27 @@ static int enqueue_sweep(qmc_ctx *ctx, qmc_net *net = nullptr, double rho = 0.0)
     const long long NN = ctx->NN, BL = (long long)ctx->L * NN;
     int k = 0, prev = 0;
     for (int t = 1; t <= ctx->L; ++t) {
+        Proposal pre;
+        int j = 0;
+        if (staged) {
+            j = (t - 1) / ps.C;
+            if ((t - 1) % ps.C == 0) CK(cudaStreamWaitEvent(ctx->st, ps.ready[j & 1], 0));
+            pre = prior_proposal(ctx, t - 1);
+        }
         // wrap G <- B_t G B_t^-1 in FP64: G enters every determinant ratio
         gemm_sq(ctx->st, N, nb, TY_C64, op64(ctx->B + (long long)(t - 1) * NN, BL), 0,
                 op64(ctx->G, NN), 0, op64(ctx->X1, NN), nullptr, 0, ONE, ZERO, 0, ozF(ctx));
         gemm_sq(ctx->st, N, nb, TY_C64, op64(ctx->X1, NN), 0,
                 op64(ctx->Binv + (long long)(t - 1) * NN, BL), 0, op64(ctx->G, NN), nullptr, 0, ONE,
                 ZERO, 0, ozF(ctx));
-        r = update_slice(ctx, t, net, rho);
+        r = update_slice(ctx, t, net, rho, staged ? &pre : nullptr);
         if (r) return r;
+        if (staged && t == j * ps.C + prior_chunk_len(ctx, j) && j + 2 < ps.nchunk) {
+            // chunk j's buffers are consumed: chunk j + 2 may overwrite them
+            CK(cudaEventRecord(ps.used[j & 1], ctx->st));
+            CK(cudaStreamWaitEvent(ps.side, ps.used[j & 1], 0));
+            if ((r = enqueue_prior_chunk(ctx, j + 2, rho))) return r;
+        }
         if (t == ctx->sp[k]) {
             r = restabilise(ctx, k, prev, t);
             if (r) return r;
@@ -687,7 +970,8 @@ static int propagators_from_fields(qmc_ctx *ctx)
     const long long NN = ctx->NN, n2 = ctx->n2, L = ctx->L;
     cudaStream_t s = ctx->st;
     for (int t = 0; t < ctx->L; ++t) {
-        if (eig_of_fields(ctx, ctx->phi + (long long)t * nf, L * nf, ctx->Up, ctx->Wp)) {
+        if (eig_of_fields(ctx, main_lane(ctx), ctx->phi + (long long)t * nf, L * nf, ctx->Up,
+                          ctx->Wp)) {
             ctx->err = "eigensolver: unsupported size";
             return QMC_ERR_ARG;
         }
@@ -699,10 +983,10 @@ static int propagators_from_fields(qmc_ctx *ctx)
         cp.seg[1] = CommitSeg{ctx->eigW + (long long)t * 4 * n, ctx->Wp, 4LL * n * 2,
                               L * 4 * n * 2, 4LL * n * 2};
         launch_commit(s, nb, cp);
-        factors_from_eig(ctx, ctx->Up, 4 * n2, ctx->Wp, 4 * n, ctx->V, ctx->T, ctx->lam, ctx->Dg,
-                         ctx->Dgi, ctx->lamG, ctx->DgG, ctx->DgiG);
-        build_B(ctx, ctx->V, ctx->T, ctx->Dg, ctx->Dgi, ctx->B + (long long)t * NN, L * NN,
-                ctx->Binv + (long long)t * NN, L * NN);
+        factors_from_eig(ctx, main_lane(ctx), ctx->Up, 4 * n2, ctx->Wp, 4 * n, ctx->V, ctx->T,
+                         ctx->lam, ctx->Dg, ctx->Dgi, ctx->lamG, ctx->DgG, ctx->DgiG);
+        build_B(ctx, main_lane(ctx), ctx->V, ctx->T, ctx->Dg, ctx->Dgi, ctx->B + (long long)t * NN,
+                L * NN, ctx->Binv + (long long)t * NN, L * NN);
     }
     return 0;
 }
@@ -788,7 +1072,10 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
         if (x == 0 && y == 0) ctx->q0 = q;
         if (sph ? x == 1 : abs(x) + abs(y) == 1) ctx->dq.push_back(q);
     }
-    linalg_init();
+    if (!linalg_init()) {
+        ctx->err = "kernel shared-memory limits refused on this device";
+        return QMC_ERR_CUDA;
+    }
     // couplings per chain
     ctx->u.resize(nb);
     ctx->anis.resize(nb);
@@ -1129,6 +1416,13 @@ int qmc_destroy(qmc_ctx *ctx)
     if (ctx->lexec) cudaGraphExecDestroy(ctx->lexec);
     if (ctx->pexec) cudaGraphExecDestroy(ctx->pexec);
     if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);
+    PriorStage &ps = ctx->ps;
+    if (ps.side) {
+        cudaStreamSynchronize(ps.side);
+        cudaStreamDestroy(ps.side);
+    }
+    for (cudaEvent_t e : {ps.fork, ps.ready[0], ps.ready[1], ps.used[0], ps.used[1]})
+        if (e) cudaEventDestroy(e);
     for (void *p : ctx->allocs) cudaFree(p);
     delete ctx;
     return QMC_OK;
@@ -1295,6 +1589,9 @@ int qmc_sweep_prior(qmc_ctx *ctx, int n_sweeps, double rho)
         ctx->err = "prior sweep: 0 <= rho < 1 violated";
         return QMC_ERR_ARG;
     }
+    if (n_sweeps == 0) return QMC_OK;
+    int r0 = prior_stage_ensure(ctx);
+    if (r0) return r0;
     for (int i = 0; i < n_sweeps; ++i) {
         int r = enqueue_sweep(ctx, PRIOR_MOVE, rho);
         if (r) return r;
@@ -1312,6 +1609,8 @@ int qmc_sweep_prior_graph(qmc_ctx *ctx, int n_sweeps, double rho)
         return QMC_ERR_ARG;
     }
     if (n_sweeps == 0) return QMC_OK;
+    int r0 = prior_stage_ensure(ctx);
+    if (r0) return r0;
     if (!ctx->pexec || ctx->prho != rho) {
         if (ctx->pexec) {
             CK(cudaStreamSynchronize(ctx->st));

@@ -238,27 +238,30 @@ __global__ void k_gather_ctx(int nf, int L, int s0, const double *phi, long long
 }
 
 // phi' = mu + rho (phi - mu) + sqrt(1 - rho^2) sigma xi, xi the Langevin noise
-// stream of this slice and sweep; lq = log N(phi') - log N(phi) (FP64)
+// stream of this slice and sweep; lq = log N(phi') - log N(phi) (FP64).
+// blockIdx.z runs over consecutive slices slice0 + z (fields at stride nf);
+// outputs are [chain][z] with gridDim.z slices per chain
 __global__ void __launch_bounds__(256) k_pcn(int nf, const float *O, const double *phi,
                                              long long phi_cs, double rho, const uint32_t *keys,
                                              uint32_t slice0, const uint32_t *ctr, double *phip,
                                              double *lq)
 {
     __shared__ double red[8];
-    const int c = blockIdx.y;
+    const int c = blockIdx.y, z = blockIdx.z;
+    const long long row = (long long)c * gridDim.z + z;  // output row of (chain, slice)
     const uint32_t sweep = ctr[QMC_CTR_SWEEP];
     const double cr = sqrt(1.0 - rho * rho);
-    const double *ph = phi + (long long)c * phi_cs;
+    const double *ph = phi + (long long)c * phi_cs + (long long)z * nf;
     const float *o = O + (long long)c * 2 * nf;
     double part = 0.0;
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f < nf) {
         const double mu = (double)o[f], sig = exp((double)o[nf + f]);
-        const double xi = rng_normal((uint32_t)f, slice0, sweep, RNG_NOISE, keys[2 * c],
-                                     keys[2 * c + 1]);
+        const double xi = rng_normal((uint32_t)f, slice0 + (uint32_t)z, sweep, RNG_NOISE,
+                                     keys[2 * c], keys[2 * c + 1]);
         const double x = ph[f];
         const double xp = mu + rho * (x - mu) + cr * sig * xi;
-        phip[(long long)c * nf + f] = xp;
+        phip[row * nf + f] = xp;
         const double is = 1.0 / sig;
         const double a = (xp - mu) * is, b = (x - mu) * is;
         part += -0.5 * a * a + 0.5 * b * b;
@@ -269,7 +272,7 @@ __global__ void __launch_bounds__(256) k_pcn(int nf, const float *O, const doubl
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        lq[(long long)c * gridDim.x + blockIdx.x] = t;  // partial of this block
+        lq[row * gridDim.x + blockIdx.x] = t;  // partial of this block
     }
 }
 
@@ -375,10 +378,10 @@ void net_pcn(qmc_net *net, cudaStream_t s, int nb, const double *phi, long long 
 
 void pcn_move(cudaStream_t s, int nb, int nf, const float *O, const double *phi, long long phi_cs,
               double rho, const uint32_t *keys, uint32_t slice0, const uint32_t *ctr, double *phip,
-              double *lq)
+              double *lq, int nslices)
 {
-    k_pcn<<<dim3(net_pcn_blocks(nf), nb), 256, 0, s>>>(nf, O, phi, phi_cs, rho, keys, slice0, ctr,
-                                                        phip, lq);
+    k_pcn<<<dim3(net_pcn_blocks(nf), nb, nslices), 256, 0, s>>>(nf, O, phi, phi_cs, rho, keys,
+                                                                 slice0, ctr, phip, lq);
     QMC_COUNT(1);
 }
 

@@ -49,10 +49,12 @@ inline int net_pcn_blocks(int nf) { return (nf + 255) / 256; }
 void net_pcn(qmc_net *net, cudaStream_t s, int nb, const double *phi, long long phi_cs, double rho,
              const uint32_t *keys, uint32_t slice0, const uint32_t *ctr, double *phip, double *lq);
 // the same move around given Gaussians O[c][2 nf] = [mu, log sigma] per chain
-// (all zero: the Gaussian part of the action, N(0, 1))
+// (all zero: the Gaussian part of the action, N(0, 1)), for nslices
+// consecutive slices slice0.. (fields phi + z nf): phip[c][z][nf] and
+// lq[c][z][net_pcn_blocks(nf)]
 void pcn_move(cudaStream_t s, int nb, int nf, const float *O, const double *phi, long long phi_cs,
               double rho, const uint32_t *keys, uint32_t slice0, const uint32_t *ctr, double *phip,
-              double *lq);
+              double *lq, int nslices = 1);
 // append the configuration [L][nf] of each of nb chains (chain stride phi_cs)
 // to the training ring; the first call fixes L
 int net_collect_fields(qmc_net *net, cudaStream_t s, int nb, int L, int nf, const double *phi,

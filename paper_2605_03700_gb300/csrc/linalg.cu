@@ -16,7 +16,7 @@
 // linalg_init; 227 KB on this part) less a bound on the static arrays of the
 // kernel it is used for
 static size_t g_smem_optin = 227 * 1024;
-static const size_t SMEM_STATIC_BOUND = 256;
+static const size_t SMEM_STATIC_BOUND = 1024;
 #define SMEM_MAX (g_smem_optin - SMEM_STATIC_BOUND)
 // the same for k_qrp with its own static arrays (set by linalg_init)
 static size_t g_smem_qrp = 227 * 1024 - SMEM_STATIC_BOUND;
@@ -1448,7 +1448,19 @@ int qrp_batched(cudaStream_t st, int n, const cd *X, long long sX, cd *Q, long l
 // ------------------------------------------------------------------ init --
 // dynamic shared-memory limits of the one-CTA-per-matrix kernels, set on the
 // current device (once per context creation, never inside a stream capture)
-void linalg_init()
+// the dynamic shared-memory limit `want` for kernel f, which must leave room
+// for the kernel's static arrays within the opt-in maximum; false if they do
+// not fit the bound the dispatch checks assume or the driver refuses it
+static bool set_dyn_smem(const void *f, size_t want)
+{
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, f) != cudaSuccess) return false;
+    if (fa.sharedSizeBytes + want > g_smem_optin) return false;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want) ==
+           cudaSuccess;
+}
+
+bool linalg_init()
 {
     if (const char *e = getenv("QMC_RD_ROWS")) {
         const int v = atoi(e);
@@ -1460,20 +1472,19 @@ void linalg_init()
             cudaSuccess &&
         optin > 0)
         g_smem_optin = (size_t)optin;
-    cudaFuncSetAttribute(k_eigh<double, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         2 * 64 * 64 * 16);
-    cudaFuncSetAttribute(k_eigh<float, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         2 * 64 * 64 * 8);
-    cudaFuncSetAttribute(k_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX);
-    cudaFuncSetAttribute(k_rdiv_ch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX);
-    cudaFuncSetAttribute(k_lu_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX);
-    cudaFuncSetAttribute(k_eigh_big<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)SMEM_MAX);
+    bool ok = set_dyn_smem((const void *)k_eigh<double, 256>, 2 * 64 * 64 * 16);
+    ok &= set_dyn_smem((const void *)k_eigh<float, 1024>, 2 * 64 * 64 * 8);
+    ok &= set_dyn_smem((const void *)k_lu, SMEM_MAX);
+    ok &= set_dyn_smem((const void *)k_rdiv_ch, SMEM_MAX);
+    ok &= set_dyn_smem((const void *)k_lu_cl, SMEM_MAX);
+    ok &= set_dyn_smem((const void *)k_eigh_big<float>, SMEM_MAX);
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, k_qrp) == cudaSuccess && fa.sharedSizeBytes < 1024)
         g_smem_qrp = g_smem_optin - fa.sharedSizeBytes;
-    cudaFuncSetAttribute(k_qrp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g_smem_qrp);
-    oz_init();
+    ok &= set_dyn_smem((const void *)k_qrp, g_smem_qrp);
+    ok &= oz_init();
+    cudaGetLastError();  // a refused attribute is reported through the return value
+    return ok;
 }
 
 // identity of the current CUDA context: cuCtxGetId through the runtime's
@@ -1521,7 +1532,7 @@ bool linalg_init_current_device()
     if (!id) return false;
     std::lock_guard<std::mutex> lock(mu);
     if (done[dev] != id) {
-        linalg_init();
+        if (!linalg_init()) return false;
         done[dev] = id;
     }
     return true;

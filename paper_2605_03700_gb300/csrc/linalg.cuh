@@ -24,7 +24,8 @@ struct GemmP {
     const struct OzCfg *oz;  // non-null: tensor-core digit products (ozaki.cu)
 };
 
-void linalg_init();
+// kernel shared-memory limits on the current device; false if one is refused
+bool linalg_init();
 // linalg_init once per context (context-free entry points)
 bool linalg_init_current_device();
 // unique id of the current CUDA context (0 if unavailable)

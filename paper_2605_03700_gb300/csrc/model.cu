@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(256) k_accept(AcceptP p)
     const int c = blockIdx.x, tid = threadIdx.x;
     const int nq = p.nq, nf = 4 * nq;
     const double *ph = p.phi + (long long)c * p.phi_cs;
-    const double *pp = p.phip + (long long)c * nf;
+    const double *pp = p.phip + (long long)c * p.phip_cs;
     const bool learned = p.lq != nullptr;
     const double *g = learned ? nullptr : p.grad + (long long)c * nf;
     const double *gp = learned ? nullptr : p.gradp + (long long)c * nf;
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(256) k_accept(AcceptP p)
         // reference-density correction (both exact MH for the same target)
         double lqc = 0.0;
         if (learned)
-            for (int j = 0; j < p.lq_n; ++j) lqc += p.lq[(long long)c * p.lq_n + j];
+            for (int j = 0; j < p.lq_n; ++j) lqc += p.lq[(long long)c * p.lq_cs + j];
         double logA = learned ? 2.0 * lr.x - (s0p - s0) - lqc
                               : 2.0 * lr.x - (s0p - s0) - bw / (2 * e * e) + fw / (2 * e * e);
         u32x4 wv = philox10(u32x4{0u, (uint32_t)(p.slice - 1), sweep, (uint32_t)RNG_ACCEPT},

@@ -11,8 +11,10 @@ struct AcceptP {
     const double *phi;
     long long phi_cs;
     const double *phip, *grad, *gradp, *eps;
+    long long phip_cs;  // chain stride of phip (the proposal fields)
     const double *lq;  // non-null: learned move, lq = log N(phi') - log N(phi) per chain
-    int lq_n;          // as lq_n partial sums per chain, lq[c * lq_n + j]
+    int lq_n;          // as lq_n partial sums per chain, lq[c * lq_cs + j]
+    long long lq_cs;
     double rho;        // its pCN parameter (recorded in the trace)
     const cd *alpha, *logdet, *trF;
     const int *fkind, *frA, *frB;

@@ -914,19 +914,21 @@ int oz_gemm(cudaStream_t st, const GemmP &p, int batch, const OzCfg &cfg)
     return 0;
 }
 
-void oz_init()
+bool oz_init()
 {
     // both kernels ask for the largest shared-memory carve-out, so that a
     // split followed by its MMA kernel (and the small-shared-memory kernels
     // around them) do not make the SMs repartition L1 and shared memory
     // between launches
     const int nts[4] = {16, 32, 48, 64};
+    bool ok = true;
     for (int NT2 : nts) {
-        cudaFuncSetAttribute(mma_kernel(NT2), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             227 * 1024);
-        cudaFuncSetAttribute(mma_kernel(NT2), cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
+        ok &= cudaFuncSetAttribute(mma_kernel(NT2), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   227 * 1024) == cudaSuccess;
+        ok &= cudaFuncSetAttribute(mma_kernel(NT2), cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   cudaSharedmemCarveoutMaxShared) == cudaSuccess;
     }
-    cudaFuncSetAttribute(k_oz_split, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         cudaSharedmemCarveoutMaxShared);
+    ok &= cudaFuncSetAttribute(k_oz_split, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               cudaSharedmemCarveoutMaxShared) == cudaSuccess;
+    return ok;
 }

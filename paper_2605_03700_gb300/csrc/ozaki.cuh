@@ -32,4 +32,5 @@ int oz_gemm(cudaStream_t st, const GemmP &p, int batch, const OzCfg &cfg);
 // column-tile width (complex columns) the tensor-core GEMM uses for n
 int oz_tile(int n);
 void oz_set_tile(int n, int nt);
-void oz_init();
+// kernel attributes (shared memory) on the current device; false if refused
+bool oz_init();

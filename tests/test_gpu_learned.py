@@ -104,6 +104,37 @@ def test_prior_sweep_makes_the_oracle_decisions(qmc, graph):
     assert np.array_equal(g.series()[0][:, 17], obs_o[:, 17])
 
 
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_prior_stage_equals_per_slice_proposals(qmc, precision):
+    """Prior sweeps compute every slice's proposal ahead, in chunks of slices
+    batched over (chain, slice) on a second stream; the learned sweep of a
+    network whose output is zero makes the same move one slice at a time.
+    Both run the same kernels on each matrix, so two copies of one batch
+    (three chains with different couplings, L = 22: chunks 6, 6, 6, 4) stay
+    bit-identical through eager and graph-replayed sweeps."""
+    kw = dict(n_chains=3, couplings=[0.5, 1.0, 1.6], anisotropies=[0.0, 0.1, -0.1],
+              seeds=[4, 5, 6], n_stab=5, precision=precision, trace_capacity=6 * 22)
+    a = qmc.Chain(qmc.QMC_TORUS, 5, 2.2, 0.1, 1.0, 0.0, 0, **kw)
+    b = qmc.Chain(qmc.QMC_TORUS, 5, 2.2, 0.1, 1.0, 0.0, 0, **kw)
+    net = qmc.Net(4 * a.n_q, 16, 16, 2)
+    for ch in (a, b):
+        ch.sweep(1)
+    a.sweep_prior(2, 0.3)
+    a.sweep_prior(3, 0.0, graph=True)
+    b.sweep_learned(net, 2, 0.3)
+    b.sweep_learned(net, 3, 0.0, graph=True)
+    for ch in (a, b):
+        ch.sync()
+    for c in range(3):
+        ta, tb = a.trace(c), b.trace(c)
+        assert len(ta) == 6 * 22
+        assert np.array_equal(ta, tb)
+        assert np.array_equal(a.fields(c), b.fields(c))
+        assert np.array_equal(a.green(c), b.green(c))
+        assert 0 < ta[22:, 6].sum() < 5 * 22
+    assert np.array_equal(a.series(), b.series())
+
+
 def test_training_and_weight_decay(qmc):
     """Training lowers the loss on the collected data; with a large decoupled
     weight decay the weight matrices shrink toward zero."""
