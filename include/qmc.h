@@ -49,7 +49,8 @@ enum {
     QMC_ERR_ARG = -1,       /* invalid argument or unsupported size */
     QMC_ERR_CUDA = -2,      /* a CUDA call failed */
     QMC_ERR_OOM = -3,       /* device allocation failed */
-    QMC_ERR_UNSTABLE = -4,  /* G error at a restabilisation above opts.stab_tol */
+    QMC_ERR_UNSTABLE = -4,  /* G error at a restabilisation above opts.stab_tol, or the
+                               eigensolver left nearly degenerate pairs coupled */
     QMC_ERR_SIGN = -5,      /* an accepted update had |sin Im log R| above opts.sign_tol */
     QMC_ERR_NONFINITE = -6, /* a determinant ratio or field became NaN/Inf */
     QMC_ERR_TIMEOUT = -7,   /* a device-side bounded wait gave up */
@@ -477,6 +478,23 @@ int qmc_profile_tensor(double *total_ms, long long *launches, double *flops, dou
  * QMC_ERR_TIMEOUT if a bounded device wait gave up, QMC_ERR_OOM, QMC_ERR_CUDA. */
 int qmc_cgemm(int M, int N, int K, int batch, const double *A, int opA, const double *B, int opB,
               const double *d, double *C, int negate, int add_identity, int digits, void *stream);
+
+/* Eigenpairs A = U diag(w) U^H of `batch` Hermitian n x n matrices, the
+ * solver behind every slice propagator (Methods, Eq.
+ * trotter_decomposition_methods: the exponentials of the channel matrices
+ * through their eigenpairs).  A, U: device, batch x n x n complex128
+ * row-major (interleaved re, im), U's columns the eigenvectors; w: device,
+ * batch x n doubles, ascending within the FP64 Jacobi (precision 0), in the
+ * order of the FP32 solution otherwise.  precision 0: FP64 Jacobi (n <= 64);
+ * 1: FP32 Jacobi, three FP64 refinement steps (Ogita-Aishima, with pairs
+ * whose correction is not small only re-orthogonalised), then the remaining
+ * coupled pairs rotated out in FP64 (the full FP64 Jacobi from the refined
+ * vectors for n <= 64; 2 x 2 rotations of the coupled pairs for n > 64);
+ * 2: as 1 with the refinement products on the tensor cores.  n <= 140.
+ * Allocates and frees its own work space and synchronises `stream`.
+ * QMC_ERR_ARG for bad sizes, QMC_ERR_UNSTABLE if coupled pairs were left,
+ * QMC_ERR_TIMEOUT, QMC_ERR_OOM, QMC_ERR_CUDA. */
+int qmc_eigh(int n, int batch, const double *A, double *U, double *w, int precision, void *stream);
 
 /* Measured fused-multiply-add rate of the current device's CUDA-core pipe,
  * the roofline denominator of the library's FP64-pipe kernels (not part of

@@ -89,6 +89,7 @@ struct qmc_ctx {
     OzCfg ozF, ozD;    // tensor-core work space: FP64-class (7 digits), drift (3 digits)
     unsigned char *qscr = nullptr;  // QR vectors for the largest sizes
     int *ozerr = nullptr;
+    int *eigerr = nullptr;  // device flag: eigensolver left coupled pairs (n > 64)
     qmc_opts o;
     std::vector<double> u, anis, g;
     std::vector<cd> alpha;
@@ -355,6 +356,7 @@ static int eig_of_fields(const qmc_ctx *ctx, const Lane &ln, const double *phi, 
     wk.R = ln.NSr;
     wk.E = ln.NSe;
     wk.oz = ln.oz;
+    wk.err = ctx->eigerr;
     return eigh_mixed(s, n, 4 * nb, ln.Fm, U, W, wk);
 }
 
@@ -1218,6 +1220,7 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
     DA(ctx->flag, nb);
     DA(ctx->errf, nb);
     DA(ctx->ozerr, 1);
+    DA(ctx->eigerr, 1);
     DAS(ctx->qscr, qrp_scratch_bytes(N, nb));
     if (ctx->tc) {
         // the largest products: N x N over the batch, n x n over 4 channels
@@ -1742,6 +1745,12 @@ int qmc_sync(qmc_ctx *ctx)
         ctx->err = "tensor-core product: a bounded wait gave up (results of the sweep are invalid)";
         return QMC_ERR_TIMEOUT;
     }
+    int eg = 0;
+    CK(cudaMemcpy(&eg, ctx->eigerr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (eg) {
+        ctx->err = "eigensolver: nearly degenerate eigenvalue pairs left coupled";
+        return QMC_ERR_UNSTABLE;
+    }
     if (f & 4) {
         ctx->err = "non-finite determinant ratio or stabilised G";
         return QMC_ERR_NONFINITE;
@@ -2189,6 +2198,67 @@ int qmc_ratio_update(int N, int batch, const double *G, const double *Delta, dou
     cudaFree(X2);
     cudaFree(M);
     cudaFree(piv);
+    return code;
+}
+
+int qmc_eigh(int n, int batch, const double *A, double *U, double *w, int precision, void *stream)
+{
+    if (n < 1 || batch < 1 || !A || !U || !w || precision < 0 || precision > 2) return QMC_ERR_ARG;
+    if (n > 140 || (n > 64 && precision == 0)) return QMC_ERR_ARG;
+    if ((long long)batch * n > (1LL << 31)) return QMC_ERR_ARG;
+    if (!linalg_init_current_device()) return QMC_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    const cd *Ad = (const cd *)A;
+    cd *Ud = (cd *)U;
+    if (precision == 0) {
+        if (eigh_batched(s, TY_C64, n, Ad, (long long)n * n, Ud, (long long)n * n, w, n, batch))
+            return QMC_ERR_ARG;
+        return cudaStreamSynchronize(s) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+    }
+    const size_t m = (size_t)n * n * batch;
+    std::vector<void *> mem;
+    auto grab = [&](size_t bytes) -> void * {
+        void *q = nullptr;
+        if (cudaMalloc(&q, bytes ? bytes : 1) != cudaSuccess) return nullptr;
+        mem.push_back(q);
+        return q;
+    };
+    EighWork wk;
+    wk.A32 = (cf *)grab(m * sizeof(cf));
+    wk.U32 = (cf *)grab(m * sizeof(cf));
+    wk.w32 = (float *)grab((size_t)n * batch * sizeof(float));
+    wk.X = (cd *)grab(m * sizeof(cd));
+    wk.Xn = (cd *)grab(m * sizeof(cd));
+    wk.T = (cd *)grab(m * sizeof(cd));
+    wk.S = (cd *)grab(m * sizeof(cd));
+    wk.R = (cd *)grab(m * sizeof(cd));
+    wk.E = (cd *)grab(m * sizeof(cd));
+    wk.err = (int *)grab(sizeof(int));
+    OzCfg cfg;
+    int code = QMC_OK;
+    if (mem.size() != 10) code = QMC_ERR_OOM;
+    if (code == QMC_OK && precision == 2) {
+        cfg.S = 7;
+        oz_sizes_max(n, n, n, 7, batch, &cfg.capA, &cfg.capB, &cfg.capE);
+        cfg.DA = (__nv_bfloat16 *)grab(sizeof(__nv_bfloat16) * cfg.capA);
+        cfg.DB = (__nv_bfloat16 *)grab(sizeof(__nv_bfloat16) * cfg.capB);
+        cfg.eA = (int *)grab(sizeof(int) * cfg.capE);
+        cfg.eB = (int *)grab(sizeof(int) * cfg.capE);
+        cfg.err = wk.err;
+        if (mem.size() != 14) code = QMC_ERR_OOM;
+        wk.oz = &cfg;
+    }
+    if (code == QMC_OK) {
+        cudaMemsetAsync(wk.err, 0, sizeof(int), s);
+        if (eigh_mixed(s, n, batch, Ad, Ud, w, wk)) code = QMC_ERR_ARG;
+        int e = 0;
+        if (cudaMemcpyAsync(&e, wk.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            code = QMC_ERR_CUDA;
+        else if (e && code == QMC_OK)
+            code = QMC_ERR_UNSTABLE;
+    }
+    for (void *q : mem) cudaFree(q);
     return code;
 }
 

@@ -733,8 +733,18 @@ __global__ void __launch_bounds__(256) k_refine_E(int n, const cd *S, const cd *
         if (i != j) {
             const double d = lam[j] - lam[i];
             if (fabs(d) > omega) {
-                const cd sv = S[e];
-                v = cscale(cd{sv.x + lam[j] * r.x, sv.y + lam[j] * r.y}, 1.0 / d);
+                // the first-order correction of the pair, and of its mirror
+                // (j, i): a pair whose correction is not small (eigenvalues
+                // nearly degenerate against the remaining coupling) gets the
+                // orthogonalisation alone, on both sides so that E + E^H
+                // stays R; the coupling is rotated out afterwards.  Without
+                // this, such a pair drifted into the separated branch as
+                // omega shrank and lost X its unitarity.
+                const cd sv = S[e], sm = S[j * n + i], rm = R[j * n + i];
+                const double id = 1.0 / d;
+                const cd q = cscale(cd{sv.x + lam[j] * r.x, sv.y + lam[j] * r.y}, id);
+                const cd qm = cscale(cd{sm.x + lam[i] * rm.x, sm.y + lam[i] * rm.y}, -id);
+                if (fmax(cabs2(q), cabs2(qm)) <= 1e-8) v = q;
             }
         } else if (plus_I) {
             v.x += 1.0;
@@ -743,17 +753,108 @@ __global__ void __launch_bounds__(256) k_refine_E(int n, const cd *S, const cd *
     }
 }
 
-// eigenvalues Re S_ii and eigenvectors X of a refined batch (n > 64, where
-// the FP64 Jacobi check does not fit in shared memory: pairs the
-// refinement leaves unrotated lie within omega ~ 1e-6 |S| of each other, so
-// dropping their off-diagonal S costs at most ~1e-12 |S|)
-__global__ void k_take_eig(int n, long long m, const cd *S, const cd *X, cd *U, double *w)
+// Eigenpairs of a refined batch for sizes whose FP64 Jacobi check does not
+// fit in shared memory (n > 64): U = X, w = Re S_ii, after the pairs the
+// refinement left coupled (|s_pq| above 1e-12 of the largest |s_ii|: nearly
+// degenerate eigenvalues) are rotated out by 2 x 2 Jacobi rotations in FP64,
+// S <- J^H S J and U <- U J, cyclically over the listed pairs (the rotation
+// of the Jacobi kernel above).  One CTA per matrix, S rotated in place in
+// global memory; a few pairs at most, usually none.  *err is set if more
+// than RP_MAX pairs are coupled or 16 passes leave one above the threshold.
+#define RP_MAX 64
+__global__ void __launch_bounds__(256) k_resolve_pairs(int n, cd *S, const cd *X, cd *U, double *w,
+                                                       int *err)
 {
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= m) return;
-    U[e] = X[e];
-    const long long nn = (long long)n * n, b = e / nn, r = e % nn;
-    if (r / n == r % n) w[b * n + r / n] = S[e].x;
+    __shared__ int npair, pp[RP_MAX], pq[RP_MAX], again;
+    __shared__ double red[8], thr;
+    __shared__ cd jm[4];
+    const int b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    const long long nn = (long long)n * n;
+    S += b * nn;
+    X += b * nn;
+    U += b * nn;
+    w += (long long)b * n;
+    for (long long e = tid; e < nn; e += nt) U[e] = X[e];
+    double mx = 0.0;
+    for (int i = tid; i < n; i += nt) mx = fmax(mx, fabs(S[(long long)i * n + i].x));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((tid & 31) == 0) red[tid >> 5] = mx;
+    if (tid == 0) npair = 0;
+    __syncthreads();
+    if (tid == 0) {
+        double m = 0.0;
+        for (int k = 0; k < nt / 32; ++k) m = fmax(m, red[k]);
+        thr = 1e-12 * m + 1e-300;
+    }
+    __syncthreads();
+    for (long long e = tid; e < nn; e += nt) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        if (i < j && cabs2(S[e]) > thr * thr) {
+            const int k = atomicAdd(&npair, 1);
+            if (k < RP_MAX) {
+                pp[k] = i;
+                pq[k] = j;
+            }
+        }
+    }
+    __syncthreads();
+    const int np = min(npair, RP_MAX);
+    if (tid == 0 && npair > RP_MAX) atomicOr(err, 1);
+    for (int pass = 0; pass < 16 && np > 0; ++pass) {
+        if (tid == 0) again = 0;
+        __syncthreads();
+        for (int k = 0; k < np; ++k) {
+            const int p = pp[k], q = pq[k];
+            if (tid == 0) {
+                const cd apq = S[(long long)p * n + q];
+                const double ab = hypot(apq.x, apq.y);
+                double c = 1.0, sn = 0.0;
+                cd ph = cmk(1, 0);
+                if (ab > thr) {
+                    again = 1;
+                    const double app = S[(long long)p * n + p].x, aqq = S[(long long)q * n + q].x;
+                    ph = cmk(apq.x / ab, apq.y / ab);
+                    const double zeta = (aqq - app) / (2 * ab);
+                    const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(zeta * zeta + 1.0));
+                    c = 1.0 / sqrt(t * t + 1.0);
+                    sn = t * c;
+                }
+                const cd cph = cconj(ph);
+                jm[0] = cmk(c, 0);
+                jm[1] = cmk(sn, 0);
+                jm[2] = cmk(-sn * cph.x, -sn * cph.y);
+                jm[3] = cmk(c * cph.x, c * cph.y);
+            }
+            __syncthreads();
+            const cd j0 = jm[0], j1 = jm[1], j2 = jm[2], j3 = jm[3];
+            // columns p, q of S and U: (x_p, x_q) <- (x_p, x_q) J
+            for (int r = tid; r < 2 * n; r += nt) {
+                cd *M = r < n ? S : U;
+                const long long row = (long long)(r % n) * n;
+                const cd a = M[row + p], bq = M[row + q];
+                M[row + p] = cadd(cmul(a, j0), cmul(bq, j2));
+                M[row + q] = cadd(cmul(a, j1), cmul(bq, j3));
+            }
+            __syncthreads();
+            // rows p, q of S: J^H (row_p; row_q)
+            for (int col = tid; col < n; col += nt) {
+                const cd a = S[(long long)p * n + col], bq = S[(long long)q * n + col];
+                S[(long long)p * n + col] = cadd(cmul(cconj(j0), a), cmul(cconj(j2), bq));
+                S[(long long)q * n + col] = cadd(cmul(cconj(j1), a), cmul(cconj(j3), bq));
+            }
+            __syncthreads();
+            if (tid == 0) {  // the rotated pivot block is diagonal
+                S[(long long)p * n + q] = cmk(0, 0);
+                S[(long long)q * n + p] = cmk(0, 0);
+                S[(long long)p * n + p].y = 0;
+                S[(long long)q * n + q].y = 0;
+            }
+            __syncthreads();
+        }
+        if (!again) break;
+        if (pass == 15 && tid == 0) atomicOr(err, 1);
+    }
+    for (int i = tid; i < n; i += nt) w[i] = S[(long long)i * n + i].x;
 }
 
 int eigh_mixed(cudaStream_t st, int n, int batch, const cd *A, cd *U, double *w, const EighWork &wk,
@@ -798,7 +899,8 @@ int eigh_mixed(cudaStream_t st, int n, int batch, const cd *A, cd *U, double *w,
     gemm_sq(st, n, batch, TY_C64, op64(X, n2), 2, op64(wk.T, n2), 0, op64(wk.S, n2), nullptr, 0,
             one, zero, 0, oz);
     if (n > 64) {
-        k_take_eig<<<g, 256, 0, st>>>(n, m, wk.S, X, U, w);
+        if (!wk.err) return -1;
+        k_resolve_pairs<<<batch, 256, 0, st>>>(n, wk.S, X, U, w, wk.err);
         QMC_COUNT(1);
         return 0;
     }
@@ -909,122 +1011,156 @@ __global__ void __launch_bounds__(256) k_lu(int n, int ld, cd *A, long long sA, 
     }
 }
 
-// ---------------------------------------------------------- cluster LU ---
-// The same LU (first row of maximal |a_ik|^2, full-row exchanges, the same
-// arithmetic per element) spread over a thread-block cluster of cs CTAs per
-// matrix: CTA r keeps columns [r w, r w + w) of the matrix in its shared
-// memory (w = ceil(n / cs)).  Step k: the CTA owning column k finds the pivot
-// p, exchanges rows k and p in its columns, forms the multipliers
-// l_i = a_ik / a_kk and writes them and p into a double-buffered slot of
-// every CTA's shared memory (distributed shared memory); one cluster barrier;
-// then every other CTA exchanges rows k and p in its columns, and every CTA
-// applies a_ij -= l_i a_kj to its columns j > k.  A CTA writes slot
-// (k+1) mod 2 only after passing barrier k, which every CTA reaches only after
-// its update of step k-1, the last reader of that slot.  The barrier is the
-// hardware cluster barrier (all CTAs of a cluster are co-resident); every CTA
-// passes the same n + 2 barriers.
+// ------------------------------------------------- blocked cluster LU ---
+// The same LU (first row of maximal |a_ik|^2, full-row exchanges) blocked in
+// panels of LB columns and spread over a cluster of cs CTAs per matrix.
+// Panel q (columns [q LB, q LB + LB)) lives in CTA q mod cs, at local columns
+// (q / cs) LB ..; so the shrinking trailing matrix stays spread over every
+// CTA.  Step q: (1) warp 0 of the owner factors the panel alone (pivot
+// search by shuffles, exchanges inside the panel, multipliers, rank-1
+// updates of the panel's later columns: no CTA barrier inside the panel);
+// (2) one cluster barrier; (3) every CTA reads the panel's pivots and its
+// multiplier block (rows below the panel's top, distributed shared memory)
+// and applies the exchanges to its other columns; (4) every CTA forms the
+// panel's rows of U in its columns right of the panel (forward substitution
+// with the unit lower block) and updates its trailing rows,
+// a_ij -= sum_k l_ik u_kj with k in panel order.  Per element that is the
+// unblocked algorithm's sequence of operations, deferred.  The owner changes
+// a factored panel again only by later exchanges, after the next barrier,
+// which every reader passes only after step (3).
+#define LU_LB 8
 namespace cgr = cooperative_groups;
-__global__ void __launch_bounds__(256) k_lu_cl(int n, cd *A, long long sA, int *piv, long long spiv,
-                                               cd *logdet)
+__global__ void __launch_bounds__(256) k_lu_bc(int n, cd *A, long long sA, int *piv,
+                                               long long spiv, cd *logdet)
 {
     cgr::cluster_group cl = cgr::this_cluster();
     const int cs = (int)cl.num_blocks(), rank = (int)cl.block_rank();
     const int b = blockIdx.y, tid = threadIdx.x, nt = blockDim.x;
-    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-    const int w = (n + cs - 1) / cs, c0 = rank * w, c1 = min(n, c0 + w), wc = max(0, c1 - c0);
-    const int ldw = w + 1;  // odd row stride of the column block
-    extern __shared__ __align__(16) unsigned char sm_lc_raw[];
-    cd *Mb = (cd *)sm_lc_raw;               // n x w block, row stride ldw
-    cd *lbuf = Mb + (size_t)n * ldw;        // 2 x n multipliers
-    __shared__ int pbuf[2];
-    __shared__ double parts[3][8];  // per rank: Re, Im of sum log u_kk, exchanges
+    const int warp = tid >> 5, lane = tid & 31;
+    const int np = (n + LU_LB - 1) / LU_LB;        // panels
+    const int mine = (np - rank + cs - 1) / cs;    // panels of this CTA
+    const int W = ((np + cs - 1) / cs) * LU_LB;    // local column capacity
+    const int ldw = W + 1;
+    extern __shared__ __align__(16) unsigned char sm_lb_raw[];
+    cd *Mb = (cd *)sm_lb_raw;                      // n x W, row stride ldw
+    cd *Lp = Mb + (size_t)n * ldw;                 // n x LU_LB multipliers of the current panel
+    int *pv = (int *)(Lp + (size_t)n * LU_LB);     // pivots of this CTA's panels, by global row
+    __shared__ double parts[3][8];
     cd *Ab = A + (long long)b * sA;
-    for (int e = tid; e < n * wc; e += nt) {
-        const int i = e / wc, j = e % wc;
-        Mb[i * ldw + j] = Ab[(long long)i * n + c0 + j];
+    // local column lc <-> global column: panel q = (lc / LB) cs + rank
+    auto gcol = [&](int lc) { return ((lc / LU_LB) * cs + rank) * LU_LB + lc % LU_LB; };
+    const int wl = mine * LU_LB;  // local columns in use (the last panel may be ragged)
+    for (int e = tid; e < n * wl; e += nt) {
+        const int i = e / wl, lc = e % wl, j = gcol(lc);
+        Mb[i * ldw + lc] = j < n ? Ab[(long long)i * n + j] : cmk(0, 0);
     }
-    cd lsum = cmk(0, 0);  // sum of log u_kk over this CTA's pivots (thread 0)
+    cd lsum = cmk(0, 0);  // sum of log u_kk over this CTA's pivots (warp 0, lane 0)
     int nsw = 0;
     cl.sync();
-    for (int k = 0; k < n; ++k) {
-        const int owner = k / w, buf = k & 1;
-        if (rank == owner) {
-            const int kk = k - c0;
-            // warp 0: pivot = first row of maximal |a_ik|^2 (non-negative
-            // doubles order like their bit patterns)
-            if (warp == 0) {
-                long long best = -1;
+    for (int q = 0; q < np; ++q) {
+        const int owner = q % cs, k0 = q * LU_LB, kb = min(LU_LB, n - k0);
+        const int lq = (q / cs) * LU_LB;  // the panel's first local column in its owner
+        if (rank == owner && warp == 0) {
+            for (int kk = 0; kk < kb; ++kk) {
+                const int k = k0 + kk, lc = lq + kk;
+                double best = -1.0;
                 int bidx = k;
                 for (int i = k + lane; i < n; i += 32) {
-                    const long long v = __double_as_longlong(cabs2(Mb[i * ldw + kk]));
+                    const double v = cabs2(Mb[i * ldw + lc]);
                     if (v > best) {
                         best = v;
                         bidx = i;
                     }
                 }
                 for (int o = 16; o > 0; o >>= 1) {
-                    const long long ov = __shfl_xor_sync(0xffffffffu, best, o);
+                    const double ov = __shfl_xor_sync(0xffffffffu, best, o);
                     const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
                     if (ov > best || (ov == best && oi < bidx)) {
                         best = ov;
                         bidx = oi;
                     }
                 }
-                if (lane == 0) pbuf[buf] = bidx;
-            }
-            __syncthreads();
-            const int p = pbuf[buf];
-            if (p != k)
-                for (int j = tid; j < wc; j += nt) {
-                    const cd t = Mb[k * ldw + j];
-                    Mb[k * ldw + j] = Mb[p * ldw + j];
-                    Mb[p * ldw + j] = t;
+                const int p = bidx;
+                if (p != k && lane < kb) {
+                    const cd t = Mb[k * ldw + lq + lane];
+                    Mb[k * ldw + lq + lane] = Mb[p * ldw + lq + lane];
+                    Mb[p * ldw + lq + lane] = t;
                 }
-            __syncthreads();
-            const cd pk = Mb[k * ldw + kk];
-            const double rr = 1.0 / cabs2(pk);
-            const cd inv = cmk(pk.x * rr, -pk.y * rr);
-            for (int i = k + 1 + tid; i < n; i += nt) {
-                const cd l = cmul(Mb[i * ldw + kk], inv);
-                Mb[i * ldw + kk] = l;
-                for (int r = 0; r < cs; ++r) cl.map_shared_rank(lbuf, r)[buf * n + i] = l;
-            }
-            for (int r = tid; r < cs; r += nt) cl.map_shared_rank(pbuf, r)[buf] = p;
-            if (tid == 0) {
-                piv[(long long)b * spiv + k] = p;
-                lsum = cadd(lsum, clog_d(pk));
-                if (p != k) ++nsw;
+                __syncwarp();
+                const cd pk = Mb[k * ldw + lc];
+                const double r = 1.0 / cabs2(pk);
+                const cd inv = cmk(pk.x * r, -pk.y * r);
+                for (int i = k + 1 + lane; i < n; i += 32) {
+                    const cd l = cmul(Mb[i * ldw + lc], inv);
+                    Mb[i * ldw + lc] = l;
+                    const cd ml = cmk(-l.x, -l.y);
+                    for (int j = kk + 1; j < kb; ++j) {
+                        cd v = Mb[i * ldw + lq + j];
+                        cfma(v, ml, Mb[k * ldw + lq + j]);
+                        Mb[i * ldw + lq + j] = v;
+                    }
+                }
+                if (lane == 0) {
+                    pv[k] = p;
+                    piv[(long long)b * spiv + k] = p;
+                    lsum = cadd(lsum, clog_d(pk));
+                    if (p != k) ++nsw;
+                }
+                __syncwarp();
             }
         }
         cl.sync();
-        const int p = pbuf[buf];
-        if (rank != owner && p != k)
-            for (int j = tid; j < wc; j += nt) {
-                const cd t = Mb[k * ldw + j];
-                Mb[k * ldw + j] = Mb[p * ldw + j];
-                Mb[p * ldw + j] = t;
-            }
-        if (rank != owner) __syncthreads();
-        // trailing update of this CTA's columns j > k: rows by warp, columns by lane
-        const int jlo = max(k + 1, c0) - c0;
-        const cd *lb = lbuf + buf * n;
-        for (int i = k + 1 + warp; i < n; i += nw) {
-            const cd l = lb[i];
-            const cd ml = cmk(-l.x, -l.y);
-            for (int j = jlo + lane; j < wc; j += 32) {
-                cd v = Mb[i * ldw + j];
-                cfma(v, ml, Mb[k * ldw + j]);
-                Mb[i * ldw + j] = v;
+        // (3) pivots and multipliers of panel q from its owner
+        const int *opv = cl.map_shared_rank(pv, owner);
+        const cd *oM = cl.map_shared_rank(Mb, owner);
+        for (int e = tid; e < (n - k0) * kb; e += nt) {
+            const int i = k0 + e / kb, kk = e % kb;
+            Lp[i * LU_LB + kk] = oM[i * ldw + lq + kk];
+        }
+        // exchanges in every local column outside panel q, in step order:
+        // thread per column
+        for (int lc = tid; lc < wl; lc += nt) {
+            if (rank == owner && lc >= lq && lc < lq + LU_LB) continue;
+            for (int kk = 0; kk < kb; ++kk) {
+                const int k = k0 + kk, p = opv[k];
+                if (p != k) {
+                    const cd t = Mb[k * ldw + lc];
+                    Mb[k * ldw + lc] = Mb[p * ldw + lc];
+                    Mb[p * ldw + lc] = t;
+                }
             }
         }
         __syncthreads();
+        // (4) rows k0.. of U in local columns right of the panel: thread per column
+        const int lfirst = (q / cs + (rank <= owner)) * LU_LB;
+        for (int lc = lfirst + tid; lc < wl; lc += nt) {
+            for (int kk = 1; kk < kb; ++kk) {
+                cd v = Mb[(k0 + kk) * ldw + lc];
+                for (int m = 0; m < kk; ++m) {
+                    const cd l = Lp[(k0 + kk) * LU_LB + m];
+                    cfma(v, cmk(-l.x, -l.y), Mb[(k0 + m) * ldw + lc]);
+                }
+                Mb[(k0 + kk) * ldw + lc] = v;
+            }
+        }
+        __syncthreads();
+        // trailing rows below the panel: element per thread, k in panel order
+        const int rows = n - k0 - kb, cols = wl - lfirst;
+        for (int e = tid; e < rows * cols; e += nt) {
+            const int i = k0 + kb + e / cols, lc = lfirst + e % cols;
+            cd v = Mb[i * ldw + lc];
+            for (int kk = 0; kk < kb; ++kk) {
+                const cd l = Lp[i * LU_LB + kk];
+                cfma(v, cmk(-l.x, -l.y), Mb[(k0 + kk) * ldw + lc]);
+            }
+            Mb[i * ldw + lc] = v;
+        }
+        __syncthreads();
     }
-    for (int e = tid; e < n * wc; e += nt) {
-        const int i = e / wc, j = e % wc;
-        Ab[(long long)i * n + c0 + j] = Mb[i * ldw + j];
+    for (int e = tid; e < n * wl; e += nt) {
+        const int i = e / wl, lc = e % wl, j = gcol(lc);
+        if (j < n) Ab[(long long)i * n + j] = Mb[i * ldw + lc];
     }
-    // log det: every CTA's sum of log u_kk and exchange count into its own
-    // slot of rank 0's shared memory, summed there in rank order
     if (tid == 0) {
         double *slot = cl.map_shared_rank(&parts[0][0], 0);
         slot[rank] = lsum.x;
@@ -1044,20 +1180,19 @@ __global__ void __launch_bounds__(256) k_lu_cl(int n, cd *A, long long sA, int *
     }
 }
 
-// cluster size of the LU for the sizes whose matrix does not fit in one CTA's
-// shared memory (N > 120); the one-CTA kernel is faster wherever it fits (its
-// steps need no cluster barrier: measured 301 us against 465 us at N = 72)
-static int g_lu_cluster = 8;
-
-static int lu_cluster_launch(cudaStream_t st, int n, cd *A, long long sA, int *piv, long long spiv,
-                             cd *logdet, int batch, int cs)
+static size_t lu_bc_smem(int n, int cs)
 {
-    const int w = (n + cs - 1) / cs;
-    const size_t smem = ((size_t)n * (w + 1) + 2 * (size_t)n) * sizeof(cd);
+    const int np = (n + LU_LB - 1) / LU_LB, W = ((np + cs - 1) / cs) * LU_LB;
+    return (size_t)n * (W + 1) * sizeof(cd) + (size_t)n * LU_LB * sizeof(cd) + (size_t)n * 4;
+}
+
+static int lu_bc_launch(cudaStream_t st, int n, cd *A, long long sA, int *piv, long long spiv,
+                        cd *logdet, int batch, int cs)
+{
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs, batch);
     cfg.blockDim = dim3(256);
-    cfg.dynamicSmemBytes = smem;
+    cfg.dynamicSmemBytes = lu_bc_smem(n, cs);
     cfg.stream = st;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1066,33 +1201,26 @@ static int lu_cluster_launch(cudaStream_t st, int n, cd *A, long long sA, int *p
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_lu_cl, n, A, sA, piv, spiv, logdet) == cudaSuccess ? 0 : -1;
+    return cudaLaunchKernelEx(&cfg, k_lu_bc, n, A, sA, piv, spiv, logdet) == cudaSuccess ? 0 : -1;
 }
 
+// CTAs per matrix of the blocked cluster LU (QMC_LU_CS=1..8 overrides, read
+// once; 1 = the one-CTA kernel)
+static int g_lu_cs = 4;
 
 int lu_batched(cudaStream_t st, int n, cd *A, long long sA, int *piv, long long spiv, cd *logdet,
                int batch)
 {
-    // the one-CTA kernel where the matrix fits (row stride n + 1 or n)
-    if ((size_t)n * n * sizeof(cd) <= SMEM_MAX) {
-        int ld = n + 1;
-        if ((size_t)n * ld * sizeof(cd) > SMEM_MAX) ld = n;
-        k_lu<<<batch, 256, (size_t)n * ld * sizeof(cd), st>>>(n, ld, A, sA, piv, spiv, logdet);
-        QMC_COUNT(1);
-        return 0;
-    }
-    // else the cluster kernel while its column block fits; clusters of at most
-    // 8 CTAs are portable
-    for (int cs = g_lu_cluster; cs >= 2; cs /= 2) {
-        const int w = (n + cs - 1) / cs;
-        if (w < 2) continue;
-        const size_t smem = ((size_t)n * (w + 1) + 2 * (size_t)n) * sizeof(cd);
-        if (smem > SMEM_MAX) break;
-        if (lu_cluster_launch(st, n, A, sA, piv, spiv, logdet, batch, cs) == 0) {
+    // the blocked cluster kernel: the configured cluster size, grown until
+    // the column blocks fit (8 CTAs at most: portable clusters)
+    int cs = g_lu_cs;
+    while (cs > 1 && cs < 8 && lu_bc_smem(n, cs) > SMEM_MAX) cs *= 2;
+    if (cs > 1 && lu_bc_smem(n, cs) <= SMEM_MAX) {
+        if (lu_bc_launch(st, n, A, sA, piv, spiv, logdet, batch, cs) == 0) {
             QMC_COUNT(1);
             return 0;
         }
-        break;
+        cudaGetLastError();  // not launched: the one-CTA kernel below, if it fits
     }
     int ld = n + 1;
     if ((size_t)n * ld * sizeof(cd) > SMEM_MAX) ld = n;
@@ -1466,6 +1594,10 @@ bool linalg_init()
         const int v = atoi(e);
         if (v >= 1 && v <= 8) g_rd_rows = v;
     }
+    if (const char *e = getenv("QMC_LU_CS")) {
+        const int v = atoi(e);
+        if (v == 1 || v == 2 || v == 4 || v == 8) g_lu_cs = v;
+    }
     int dev = 0, optin = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) ==
@@ -1476,7 +1608,7 @@ bool linalg_init()
     ok &= set_dyn_smem((const void *)k_eigh<float, 1024>, 2 * 64 * 64 * 8);
     ok &= set_dyn_smem((const void *)k_lu, SMEM_MAX);
     ok &= set_dyn_smem((const void *)k_rdiv_ch, SMEM_MAX);
-    ok &= set_dyn_smem((const void *)k_lu_cl, SMEM_MAX);
+    ok &= set_dyn_smem((const void *)k_lu_bc, SMEM_MAX);
     ok &= set_dyn_smem((const void *)k_eigh_big<float>, SMEM_MAX);
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, k_qrp) == cudaSuccess && fa.sharedSizeBytes < 1024)

@@ -52,9 +52,11 @@ struct EighWork {
     float *w32;
     cd *X, *Xn, *T, *S, *R, *E;
     const struct OzCfg *oz = nullptr;  // refinement products on the tensor cores
+    int *err = nullptr;  // device flag: coupled pairs left unresolved (n > 64)
 };
 // FP64-accurate eigenpairs of batch Hermitian n x n matrices (dense, stride
-// n^2): FP32 Jacobi, two FP64 refinement steps, FP64 Jacobi safety net
+// n^2): FP32 Jacobi, three FP64 refinement steps, then the pairs the
+// refinement leaves coupled resolved by FP64 Jacobi rotations
 int eigh_mixed(cudaStream_t st, int n, int batch, const cd *A, cd *U, double *w,
                const EighWork &wk, double tol32 = 1e-10);
 int lu_batched(cudaStream_t st, int n, cd *A, long long sA, int *piv, long long spiv, cd *logdet,

@@ -151,6 +151,7 @@ def lib():
         L.qmc_profile_tensor.argtypes = [dp, C.POINTER(C.c_longlong), dp, dp]
         L.qmc_cgemm.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_int, vp, C.c_int, vp, vp,
                                 C.c_int, C.c_int, C.c_int, vp]
+        L.qmc_eigh.argtypes = [C.c_int, C.c_int, vp, vp, vp, C.c_int, vp]
         _lib = L
     return _lib
 
@@ -236,6 +237,14 @@ def qmc_cgemm(M, N, K, batch, A_ptr, opA, B_ptr, opB, d_ptr, C_ptr, negate=0, ad
     _check(lib().qmc_cgemm(M, N, K, batch, C.c_void_p(A_ptr), opA, C.c_void_p(B_ptr), opB,
                            C.c_void_p(d_ptr) if d_ptr else None, C.c_void_p(C_ptr), negate,
                            add_identity, digits, C.c_void_p(stream) if stream else None))
+
+
+def qmc_eigh(n, batch, A_ptr, U_ptr, w_ptr, precision=1, stream=0):
+    """Eigenpairs of a batch of Hermitian matrices on device pointers
+    (qmc_eigh); precision 0 = FP64 Jacobi, 1 = FP32 + FP64 refinement,
+    2 = refinement products on the tensor cores."""
+    _check(lib().qmc_eigh(n, batch, C.c_void_p(A_ptr), C.c_void_p(U_ptr), C.c_void_p(w_ptr),
+                          precision, C.c_void_p(stream) if stream else None))
 
 
 def qmc_ratio_update(N, batch, G_ptr, Delta_ptr, Gp_ptr, logdet_ptr, stream=0):

@@ -87,6 +87,12 @@ def test_new_entry_points_reject_invalid_arguments_before_device_work(lib):
     # standalone ratio updates: sizes beyond what the kernels hold
     assert L.qmc_ratio_update(121, 1, None, None, None, None, None) == -1
     assert L.qmc_ratio_update_noalloc(72, 1, None, None, None, None, None) == -1
+    # eigensolver: null buffers, n beyond 140, FP64 beyond 64, unknown precision
+    assert L.qmc_eigh(36, 1, None, None, None, 1, None) == -1
+    one = C.c_void_p(1)
+    assert L.qmc_eigh(141, 1, one, one, one, 1, None) == -1
+    assert L.qmc_eigh(65, 1, one, one, one, 0, None) == -1
+    assert L.qmc_eigh(36, 1, one, one, one, 3, None) == -1
     # sphere beyond 60 orbitals; torus beyond 140, or beyond 60 in FP64
     o = qmc.qmc_default_opts()
     assert L.qmc_create(C.byref(h), 1, 60, 1.0, 0.1, 1.0, 0.0, 0, C.byref(o)) == -1
