@@ -44,6 +44,17 @@ enum { QMC_TORUS = 0, QMC_SPHERE = 1 };
  * exact because the MH test evaluates both proposal densities with it. */
 enum { QMC_DRIFT_EXACT = 0, QMC_DRIFT_FIRST = 1 };
 
+/* Field sets of a slice (qmc_opts.slice_kind).  SHARED: the paper's reading
+ * of Methods, Eq. trotter_decomposition_methods: one field set per channel,
+ * N_q real fields each, shared by the channel's two half-factors
+ * (4 N_q fields per slice).  INDEP: every one of the seven factors
+ * e^{-c_j dtau g_i H_i^2} decoupled with its own set, exponent coefficient
+ * sqrt(-c_j dtau g_i) (c_j = 1/2 for the half-factors, 1 for the middle
+ * one): 7 N_q fields per slice, seven eigendecompositions and no palindrome
+ * in B; the same O(dtau^2) order with a smaller error (no coupling of the
+ * half-factors through a shared field).  Fields are stored [slice][set][N_q]. */
+enum { QMC_SLICE_SHARED = 0, QMC_SLICE_INDEP = 2 };
+
 enum {
     QMC_OK = 0,
     QMC_ERR_ARG = -1,       /* invalid argument or unsupported size */
@@ -109,6 +120,7 @@ typedef struct {
     double sign_tol;       /* QMC_ERR_SIGN threshold on accepted updates (default 1e-6);
                               record column 16 is the maximum over all updates */
     int drift;             /* QMC_DRIFT_EXACT (default) or QMC_DRIFT_FIRST */
+    int slice_kind;        /* QMC_SLICE_SHARED (default) or QMC_SLICE_INDEP */
 } qmc_opts;
 
 /* Fill *o with the defaults listed above. */

@@ -50,6 +50,7 @@ struct Lane {
     cudaStream_t st = nullptr;
     int nb = 0;                 // batch entries
     const cd *alpha = nullptr;  // [nb][4] alpha_i of each entry
+    const cd *coef = nullptr;   // [nb][7] factor coefficients (a field set per factor), or null
     cd *Fm = nullptr;           // channel matrices [nb][4][n^2]
     void *Fm32 = nullptr, *U32 = nullptr;
     float *W32 = nullptr;
@@ -75,12 +76,14 @@ struct PriorStage {
     cd *V = nullptr, *T = nullptr, *lam = nullptr, *Dg = nullptr, *Dgi = nullptr;
     cd *alpha = nullptr;       // alpha of chain c repeated C times, [c][z][4]
     cd *alpha_last = nullptr;  // the same for the last chunk's length
+    cd *coef = nullptr, *coef_last = nullptr;  // the factor coefficients likewise, [c][z][7]
     OzCfg oz;
     Lane ln;
 };
 
 struct qmc_ctx {
     int geom = 0, nphi = 0, n = 0, N = 0, nq = 0, nf = 0, L = 0, nb = 0;
+    int ns = 4;  // field sets per slice: 4 (one per channel), 7 (one per Trotter factor)
     long long NN = 0, n2 = 0;
     double beta = 0, dtau = 0;
     int gp = TY_C64;   // compute type of the gradient transforms, wraps, M and G M^-1
@@ -93,6 +96,7 @@ struct qmc_ctx {
     qmc_opts o;
     std::vector<double> u, anis, g;
     std::vector<cd> alpha;
+    std::vector<cd> coef;  // [nb][7] sqrt(-c_j dtau g_i), a field set per factor only
     std::vector<uint64_t> seeds;
     std::vector<int> sp;  // stabilisation slices, ascending, last == L
     int q0 = 0;
@@ -122,6 +126,7 @@ struct qmc_ctx {
     int *ff_col = nullptr, *qxy = nullptr, *partner = nullptr, *fkind = nullptr, *frA = nullptr,
         *frB = nullptr, *fq = nullptr, *fk = nullptr, *aptr = nullptr, *aq = nullptr;
     cd *alpha_d = nullptr;
+    cd *coef_d = nullptr;  // device copy of coef (null with shared field sets)
     double *g_d = nullptr;
     uint32_t *keys = nullptr;
     // chain state (FP64)
@@ -216,6 +221,7 @@ static Lane main_lane(const qmc_ctx *ctx)
     l.st = ctx->st;
     l.nb = ctx->nb;
     l.alpha = ctx->alpha_d;
+    l.coef = ctx->coef_d;
     l.Fm = ctx->Fm;
     l.Fm32 = ctx->Fm32;
     l.U32 = ctx->U32;
@@ -241,16 +247,18 @@ static void factors_from_eig(const qmc_ctx *ctx, const Lane &ln, const cd *U, lo
                              const double *W, long long W_cs, cd *V, cd *T, cd *lam, cd *Dg,
                              cd *Dgi, void *lamG, void *DgG, void *DgiG)
 {
-    const int nb = ln.nb, N = ctx->N;
+    const int nb = ln.nb, N = ctx->N, ns = ctx->ns;
     const long long NN = ctx->NN;
-    launch_build_V(ln.st, TY_C64, nb, ctx->n, U, U_cs, V);
-    // T01 = V0^H V1, T12 = V1^H V2, T23 = V2^H V3
-    for (int x = 0; x < 3; ++x)
-        gemm_sq(ln.st, N, nb, TY_C64, op64(V + x * NN, 4 * NN), 2, op64(V + (x + 1) * NN, 4 * NN),
-                0, op64(T + x * NN, 3 * NN), nullptr, 0, ONE, ZERO, 0, ln.oz);
-    launch_lambda(ln.st, TY_C64, nb, ctx->n, W, W_cs, ln.alpha, lam, Dg, Dgi);
+    launch_build_V(ln.st, TY_C64, nb, ns, ctx->n, U, U_cs, V);
+    // transitions T_x = V_x^H V_{x+1} between consecutive field sets (shared
+    // sets: T01, T12, T23; a set per factor: T01 .. T56)
+    for (int x = 0; x < ns - 1; ++x)
+        gemm_sq(ln.st, N, nb, TY_C64, op64(V + x * NN, ns * NN), 2,
+                op64(V + (x + 1) * NN, ns * NN), 0, op64(T + x * NN, (ns - 1) * NN), nullptr, 0,
+                ONE, ZERO, 0, ln.oz);
+    launch_lambda(ln.st, TY_C64, nb, ns, ctx->n, W, W_cs, ln.alpha, ln.coef, lam, Dg, Dgi);
     if (ctx->gp != TY_C64 && lamG)
-        launch_lambda(ln.st, ctx->gp, nb, ctx->n, W, W_cs, ln.alpha, lamG, DgG, DgiG);
+        launch_lambda(ln.st, ctx->gp, nb, ns, ctx->n, W, W_cs, ln.alpha, ln.coef, lamG, DgG, DgiG);
 }
 
 // B = V0 D0 T01 D1 T12 D2 T23 D3 T23^H D2 T12^H D1 T01^H D0 V0^H and the
@@ -267,6 +275,34 @@ static void build_B(const qmc_ctx *ctx, const Lane &ln, const cd *V, const cd *T
     cudaStream_t s = ln.st;
     const OzCfg *oz = ln.oz;
     cd *X1 = ln.X1, *X2 = ln.X2, *Mx = ln.M;
+    if (ctx->ns == 7) {
+        // a field set per factor: no palindrome.  B = V0 D0 T01 D1 ... T56 D6
+        // V6^H and B^-1 = V6 D6^-1 T56^H D5^-1 ... T01^H D0^-1 V0^H, seven
+        // products each (T_x = V_x^H V_{x+1} at T + x N^2)
+        const long long Vs = 7 * NN, Ts = 6 * NN;
+        for (int inv = 0; inv < 2; ++inv) {
+            const cd *dg = inv ? Dgi : Dg;
+            cd *dst = inv ? Biout : Bout;
+            const long long dst_cs = inv ? Bio_cs : Bo_cs;
+            cd *a = X1, *b = X2;
+            if (!inv)
+                gemm_sq(s, N, nb, TY_C64, op64(V, Vs), 0, op64(T, Ts), 0, op64(a, NN), dg, dcs, ONE,
+                        ZERO, 0, oz);
+            else
+                gemm_sq(s, N, nb, TY_C64, op64(V + 6 * NN, Vs), 0, op64(T + 5 * NN, Ts), 2,
+                        op64(a, NN), dg + 6 * N, dcs, ONE, ZERO, 0, oz);
+            for (int x = 1; x <= 5; ++x) {
+                const int j = inv ? 6 - x : x;  // factor whose diagonal comes next
+                const cd *Tx = inv ? T + (long long)(j - 1) * NN : T + (long long)j * NN;
+                gemm_sq(s, N, nb, TY_C64, op64(a, NN), 0, op64(Tx, Ts), inv ? 2 : 0, op64(b, NN),
+                        dg + (long long)j * N, dcs, ONE, ZERO, 0, oz);
+                std::swap(a, b);
+            }
+            gemm_sq(s, N, nb, TY_C64, op64(a, NN), 0, op64(inv ? V : V + 6 * NN, Vs), 2,
+                    op64(dst, dst_cs), dg + (inv ? 0 : 6) * N, dcs, ONE, ZERO, 0, oz);
+        }
+        return;
+    }
     for (int inv = 0; inv < 2; ++inv) {
         const cd *dg = inv ? Dgi : Dg;   // D_j (or D_j^-1) at Trotter position j
         const cd *dgc = inv ? Dg : Dgi;  // conj of position 0: D0^* = D0^-1
@@ -294,40 +330,45 @@ static void gradient(qmc_ctx *ctx, const cd *Gm, const cd *V, const cd *T, const
                      const void *Dg, const void *Dgi, const double *phi, long long phi_cs,
                      double *grad)
 {
-    const int nb = ctx->nb, N = ctx->N, gp = ctx->gp;
-    const long long NN = ctx->NN;
+    const int nb = ctx->nb, N = ctx->N, gp = ctx->gp, ns = ctx->ns;
+    const long long NN = ctx->NN, Vs = ns * NN, Ts = (ns - 1) * NN;
     cudaStream_t s = ctx->st;
     if (ctx->o.drift == QMC_DRIFT_FIRST) {
-        launch_first_drift(s, gp, nb, N, Gm, ctx->alpha_d, ctx->At);
-        launch_trace_grad(s, gp, nb, ctx->n, ctx->nq, ctx->At, ctx->ff_val, ctx->ff_col, ctx->trF,
-                          ctx->alpha_d, ctx->tq, ctx->fq, ctx->fk, ctx->partner, phi, phi_cs, grad);
+        launch_first_drift(s, gp, nb, ns, N, Gm, ctx->alpha_d, ctx->coef_d, ctx->At);
+        launch_trace_grad(s, gp, nb, ns, ctx->n, ctx->nq, ctx->At, ctx->ff_val, ctx->ff_col,
+                          ctx->trF, ctx->alpha_d, ctx->coef_d, ctx->tq, ctx->fq, ctx->fk,
+                          ctx->partner, phi, phi_cs, grad);
         return;
     }
     // Ah = I - V0^H G V0
     const OzCfg *oz = ozD(ctx);
-    gemm_sq(s, N, nb, gp, op64(V, 4 * NN), 2, op64(Gm, NN), 0, ctx->Gx(ctx->Y1, NN), nullptr, 0, ONE,
+    gemm_sq(s, N, nb, gp, op64(V, Vs), 2, op64(Gm, NN), 0, ctx->Gx(ctx->Y1, NN), nullptr, 0, ONE,
             ZERO, 0, oz);
-    gemm_sq(s, N, nb, gp, ctx->Gx(ctx->Y1, NN), 0, op64(V, 4 * NN), 0, ctx->Gx(ctx->Ah, NN),
-            nullptr, 0, MONE, ZERO, 1, oz);
+    gemm_sq(s, N, nb, gp, ctx->Gx(ctx->Y1, NN), 0, op64(V, Vs), 0, ctx->Gx(ctx->Ah, NN), nullptr, 0,
+            MONE, ZERO, 1, oz);
+    // from factor j's eigenbasis to factor j + 1's: shared sets walk T01, T12,
+    // T23 and back (the palindrome), a set per factor T01 .. T56
     const int tidx[6] = {0, 1, 2, 2, 1, 0};
     for (int j = 0; j < 7; ++j) {
-        launch_accum(s, gp, nb, N, j, j < 4, ctx->alpha_d, lam, ctx->Ah, ctx->Cacc);
+        launch_accum(s, gp, nb, N, j, ns == 7 || j < 4, ns, ctx->alpha_d, ctx->coef_d, lam, ctx->Ah,
+                     ctx->Cacc);
         if (j == 6) break;
-        const cd *Tx = T + (long long)tidx[j] * NN;
-        int op1 = j < 3 ? 2 : 0, op2 = j < 3 ? 0 : 2;
-        gemm_sq(s, N, nb, gp, op64(Tx, 3 * NN), op1, ctx->Gx(ctx->Ah, NN), 0, ctx->Gx(ctx->Y1, NN),
+        const cd *Tx = T + (long long)(ns == 7 ? j : tidx[j]) * NN;
+        int op1 = (ns == 7 || j < 3) ? 2 : 0, op2 = (ns == 7 || j < 3) ? 0 : 2;
+        gemm_sq(s, N, nb, gp, op64(Tx, Ts), op1, ctx->Gx(ctx->Ah, NN), 0, ctx->Gx(ctx->Y1, NN),
                 ctx->at((void *)Dgi, (long long)j * N), 7 * N, ONE, ZERO, 0, oz);
-        gemm_sq(s, N, nb, gp, ctx->Gx(ctx->Y1, NN), 0, op64(Tx, 3 * NN), op2, ctx->Gx(ctx->Ah, NN),
+        gemm_sq(s, N, nb, gp, ctx->Gx(ctx->Y1, NN), 0, op64(Tx, Ts), op2, ctx->Gx(ctx->Ah, NN),
                 ctx->at((void *)Dg, (long long)j * N), 7 * N, ONE, ZERO, 0, oz);
     }
-    for (int i = 0; i < 4; ++i) {
-        gemm_sq(s, N, nb, gp, op64(V + i * NN, 4 * NN), 0, ctx->Gx(ctx->at(ctx->Cacc, i * NN), 4 * NN),
-                0, ctx->Gx(ctx->Y1, NN), nullptr, 0, ONE, ZERO, 0, oz);
-        gemm_sq(s, N, nb, gp, ctx->Gx(ctx->Y1, NN), 0, op64(V + i * NN, 4 * NN), 2,
-                ctx->Gx(ctx->at(ctx->At, i * NN), 4 * NN), nullptr, 0, ONE, ZERO, 0, oz);
+    for (int i = 0; i < ns; ++i) {
+        gemm_sq(s, N, nb, gp, op64(V + i * NN, Vs), 0, ctx->Gx(ctx->at(ctx->Cacc, i * NN), Vs), 0,
+                ctx->Gx(ctx->Y1, NN), nullptr, 0, ONE, ZERO, 0, oz);
+        gemm_sq(s, N, nb, gp, ctx->Gx(ctx->Y1, NN), 0, op64(V + i * NN, Vs), 2,
+                ctx->Gx(ctx->at(ctx->At, i * NN), Vs), nullptr, 0, ONE, ZERO, 0, oz);
     }
-    launch_trace_grad(s, gp, nb, ctx->n, ctx->nq, ctx->At, ctx->ff_val, ctx->ff_col, ctx->trF,
-                      ctx->alpha_d, ctx->tq, ctx->fq, ctx->fk, ctx->partner, phi, phi_cs, grad);
+    launch_trace_grad(s, gp, nb, ns, ctx->n, ctx->nq, ctx->At, ctx->ff_val, ctx->ff_col, ctx->trF,
+                      ctx->alpha_d, ctx->coef_d, ctx->tq, ctx->fq, ctx->fk, ctx->partner, phi,
+                      phi_cs, grad);
 }
 
 // FP64 eigenpairs (U [nb][4][n^2], W [nb][4][n]) of the four channel matrices
@@ -342,9 +383,10 @@ static int eig_of_fields(const qmc_ctx *ctx, const Lane &ln, const double *phi, 
     const int nb = ln.nb, n = ctx->n;
     const long long n2 = ctx->n2;
     cudaStream_t s = ln.st;
-    launch_assemble(s, TY_C64, nb, n, ctx->nq, phi, phi_cs, ctx->fkind, ctx->frA, ctx->frB,
+    const int ns = ctx->ns;
+    launch_assemble(s, TY_C64, nb, ns, n, ctx->nq, phi, phi_cs, ctx->fkind, ctx->frA, ctx->frB,
                     ctx->aptr, ctx->aq, ctx->ff_val, ln.Fm);
-    if (ctx->gp == TY_C64) return eigh_batched(s, TY_C64, n, ln.Fm, n2, U, n2, W, n, 4 * nb);
+    if (ctx->gp == TY_C64) return eigh_batched(s, TY_C64, n, ln.Fm, n2, U, n2, W, n, ns * nb);
     EighWork wk;
     wk.A32 = (cf *)ln.Fm32;
     wk.U32 = (cf *)ln.U32;
@@ -357,7 +399,7 @@ static int eig_of_fields(const qmc_ctx *ctx, const Lane &ln, const double *phi, 
     wk.E = ln.NSe;
     wk.oz = ln.oz;
     wk.err = ctx->eigerr;
-    return eigh_mixed(s, n, 4 * nb, ln.Fm, U, W, wk);
+    return eigh_mixed(s, n, ns * nb, ln.Fm, U, W, wk);
 }
 
 // G = QL DbL^-1 [DbR^-1 QR^H QL DbL^-1 + DsR WR WL^H DsL]^-1 DbR^-1 QR^H (FP64)
@@ -469,8 +511,9 @@ static int update_slice(qmc_ctx *ctx, int t, qmc_net *net = nullptr, double rho 
     const double *phi_s = ctx->phi + (long long)s0 * nf;
     const long long phi_cs = L * nf;
     cd *Bis = ctx->Binv + (long long)s0 * NN;
-    cd *Us = ctx->eigU + (long long)s0 * 4 * n2;
-    double *Ws = ctx->eigW + (long long)s0 * 4 * n;
+    const int ns = ctx->ns;
+    cd *Us = ctx->eigU + (long long)s0 * ns * n2;
+    double *Ws = ctx->eigW + (long long)s0 * ns * n;
     // the proposal's fields, eigenpairs and propagators (this slice's own
     // buffers unless computed ahead)
     Proposal pr;
@@ -479,9 +522,9 @@ static int update_slice(qmc_ctx *ctx, int t, qmc_net *net = nullptr, double rho 
     pr.lq = ctx->lq;
     pr.lq_cs = net_pcn_blocks(nf);
     pr.Up = ctx->Up;
-    pr.Up_cs = 4 * n2;
+    pr.Up_cs = ns * n2;
     pr.Wp = ctx->Wp;
-    pr.Wp_cs = 4 * n;
+    pr.Wp_cs = ns * n;
     pr.Bp = ctx->Bp;
     pr.Bpi = ctx->Bpi;
     pr.B_cs = NN;
@@ -500,7 +543,7 @@ static int update_slice(qmc_ctx *ctx, int t, qmc_net *net = nullptr, double rho 
                 ctx->lq);
     } else {
         // forward gradient at the current fields
-        factors_from_eig(ctx, main_lane(ctx), Us, L * 4 * n2, Ws, L * 4 * n, ctx->V, ctx->T,
+        factors_from_eig(ctx, main_lane(ctx), Us, L * ns * n2, Ws, L * ns * n, ctx->V, ctx->T,
                          ctx->lam, ctx->Dg, ctx->Dgi, ctx->lamG, ctx->DgG, ctx->DgiG);
         gradient(ctx, ctx->G, ctx->V, ctx->T, ctx->lamG, ctx->DgG, ctx->DgiG, phi_s, phi_cs,
                  ctx->grad);
@@ -514,7 +557,7 @@ static int update_slice(qmc_ctx *ctx, int t, qmc_net *net = nullptr, double rho 
             ctx->err = "eigensolver: unsupported size";
             return QMC_ERR_ARG;
         }
-        factors_from_eig(ctx, ln, ctx->Up, 4 * n2, ctx->Wp, 4 * n, ctx->Vp, ctx->Tp, ctx->lamp,
+        factors_from_eig(ctx, ln, ctx->Up, ns * n2, ctx->Wp, ns * n, ctx->Vp, ctx->Tp, ctx->lamp,
                          ctx->Dgp, ctx->Dgip, ctx->lampG, ctx->DgpG, ctx->DgipG);
         build_B(ctx, ln, ctx->Vp, ctx->Tp, ctx->Dgp, ctx->Dgip, ctx->Bp, NN, ctx->Bpi, NN);
     }
@@ -535,6 +578,8 @@ static int update_slice(qmc_ctx *ctx, int t, qmc_net *net = nullptr, double rho 
                  ctx->gradp);
     AcceptP ap;
     ap.nq = ctx->nq;
+    ap.ns = ns;
+    ap.coef = ctx->coef_d;
     ap.phi = phi_s;
     ap.phi_cs = phi_cs;
     ap.phip = pr.phip;
@@ -569,34 +614,47 @@ static int update_slice(qmc_ctx *ctx, int t, qmc_net *net = nullptr, double rho 
     cp.nseg = 6;
     cp.seg[0] = CommitSeg{ctx->B + (long long)s0 * NN, pr.Bp, NN * 4, L * NN * 4, pr.B_cs * 4};
     cp.seg[1] = CommitSeg{Bis, pr.Bpi, NN * 4, L * NN * 4, pr.B_cs * 4};
-    cp.seg[2] = CommitSeg{Us, pr.Up, 4 * n2 * 4, L * 4 * n2 * 4, pr.Up_cs * 4};
-    cp.seg[3] = CommitSeg{Ws, pr.Wp, 4 * n * 2, L * 4 * n * 2, pr.Wp_cs * 2};
+    cp.seg[2] = CommitSeg{Us, pr.Up, ns * n2 * 4, L * ns * n2 * 4, pr.Up_cs * 4};
+    cp.seg[3] = CommitSeg{Ws, pr.Wp, ns * n * 2, L * ns * n * 2, pr.Wp_cs * 2};
     cp.seg[4] = CommitSeg{ctx->G, ctx->Gp, NN * 4, NN * 4, NN * 4};
     cp.seg[5] = CommitSeg{(void *)phi_s, pr.phip, (long long)nf * 2, phi_cs * 2, pr.phip_cs * 2};
     launch_commit(s, nb, cp);
     return 0;
 }
 
+// A non-blocking stream at the device's highest (or lowest) priority.  The
+// sweep is captured on a high-priority stream and the prior stage runs on a
+// low-priority one, and graphs are instantiated with node priorities, so the
+// sequential chain of updates gets SMs first while the batched proposals of
+// later slices fill the rest.
+static cudaError_t make_stream(cudaStream_t *s, bool high)
+{
+    int least = 0, greatest = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e != cudaSuccess) return e;
+    return cudaStreamCreateWithPriority(s, cudaStreamNonBlocking, high ? greatest : least);
+}
+
 // ------------------------------------------------- prior-move stage ----
 // device bytes the prior stage holds per (chain, slice) entry of a chunk
 static size_t prior_entry_bytes(const qmc_ctx *ctx)
 {
-    const size_t n = ctx->n, N = ctx->N, n2 = n * n, NN = N * N, nf = ctx->nf;
-    const size_t out = nf * 8 + net_pcn_blocks((int)nf) * 8 + 4 * n2 * 16 + 4 * n * 8 + 2 * NN * 16;
-    size_t scr = 4 * n2 * 16 + 6 * 4 * n2 * 16 + 4 * NN * 16 + 3 * NN * 16 + 3 * 7 * N * 16 +
-                 3 * NN * 16 + 2 * 4 * 16;
-    if (ctx->gp != TY_C64) scr += 2 * 4 * n2 * 8 + 4 * n * 4;
+    const size_t n = ctx->n, N = ctx->N, n2 = n * n, NN = N * N, nf = ctx->nf, ns = ctx->ns;
+    const size_t out = nf * 8 + net_pcn_blocks((int)nf) * 8 + ns * n2 * 16 + ns * n * 8 + 2 * NN * 16;
+    size_t scr = ns * n2 * 16 + 6 * ns * n2 * 16 + ns * NN * 16 + (ns - 1) * NN * 16 +
+                 3 * 7 * N * 16 + 3 * NN * 16 + 2 * 4 * 16 + 2 * 7 * 16;
+    if (ctx->gp != TY_C64) scr += 2 * ns * n2 * 8 + ns * n * 4;
     return 2 * out + scr;
 }
 
-// alpha of every chain repeated over cz slices: [c][z][4]
-static int prior_alpha(qmc_ctx *ctx, cd **dst, int cz)
+// per-chain values (w per chain) repeated over cz slices: [c][z][w]
+static int prior_repeat(qmc_ctx *ctx, cd **dst, const std::vector<cd> &src, int w, int cz)
 {
     const int nb = ctx->nb;
-    std::vector<cd> rep((size_t)nb * cz * 4);
+    std::vector<cd> rep((size_t)nb * cz * w);
     for (int c = 0; c < nb; ++c)
         for (int z = 0; z < cz; ++z)
-            for (int i = 0; i < 4; ++i) rep[((size_t)c * cz + z) * 4 + i] = ctx->alpha[4 * c + i];
+            for (int i = 0; i < w; ++i) rep[((size_t)c * cz + z) * w + i] = src[(size_t)w * c + i];
     DA(*dst, rep.size());
     CK(cudaMemcpy(*dst, rep.data(), sizeof(cd) * rep.size(), cudaMemcpyHostToDevice));
     return 0;
@@ -617,46 +675,50 @@ static int prior_stage_ensure(qmc_ctx *ctx)
     int C = (L + 3) / 4;
     if (C > fit) C = (int)std::max(1LL, fit);
     // batched products index the 4 channel matrices of an entry in grid z
-    if (4LL * nb * C > 65535) C = std::max(1, 65535 / (4 * nb));
+    const int ns = ctx->ns;
+    if ((long long)ns * nb * C > 65535) C = std::max(1, 65535 / (ns * nb));
     const long long E = (long long)nb * C;  // entries of a full chunk
     const int lqn = net_pcn_blocks(nf);
     for (int b = 0; b < 2; ++b) {
         DAS(ps.phip[b], E * nf);
         DAS(ps.lq[b], E * lqn);
-        DAS(ps.Up[b], E * 4 * n2);
-        DAS(ps.Wp[b], E * 4 * n);
+        DAS(ps.Up[b], E * ns * n2);
+        DAS(ps.Wp[b], E * ns * n);
         DAS(ps.Bp[b], E * NN);
         DAS(ps.Bpi[b], E * NN);
     }
     Lane &l = ps.ln;
-    DAS(l.Fm, E * 4 * n2);
+    DAS(l.Fm, E * ns * n2);
     if (ctx->gp != TY_C64) {
-        DAGS(l.Fm32, E * 4 * n2);
-        DAGS(l.U32, E * 4 * n2);
-        DAS(l.W32, E * 4 * n);
+        DAGS(l.Fm32, E * ns * n2);
+        DAGS(l.U32, E * ns * n2);
+        DAS(l.W32, E * ns * n);
     }
-    DAS(l.NSx, E * 4 * n2);
-    DAS(l.NSy, E * 4 * n2);
-    DAS(l.NSz, E * 4 * n2);
-    DAS(l.NSs, E * 4 * n2);
-    DAS(l.NSr, E * 4 * n2);
-    DAS(l.NSe, E * 4 * n2);
+    DAS(l.NSx, E * ns * n2);
+    DAS(l.NSy, E * ns * n2);
+    DAS(l.NSz, E * ns * n2);
+    DAS(l.NSs, E * ns * n2);
+    DAS(l.NSr, E * ns * n2);
+    DAS(l.NSe, E * ns * n2);
     DAS(l.X1, E * NN);
     DAS(l.X2, E * NN);
     DAS(l.M, E * NN);
-    DAS(ps.V, E * 4 * NN);
-    DAS(ps.T, E * 3 * NN);
+    DAS(ps.V, E * ns * NN);
+    DAS(ps.T, E * (ns - 1) * NN);
     DAS(ps.lam, E * 7 * N);
     DAS(ps.Dg, E * 7 * N);
     DAS(ps.Dgi, E * 7 * N);
-    int r = prior_alpha(ctx, &ps.alpha, C);
+    int r = prior_repeat(ctx, &ps.alpha, ctx->alpha, 4, C);
     if (r) return r;
+    if (ns == 7 && (r = prior_repeat(ctx, &ps.coef, ctx->coef, 7, C))) return r;
     const int last = L - (L + C - 1) / C * C + C;  // slices of the last chunk
     if (last != C) {
-        r = prior_alpha(ctx, &ps.alpha_last, last);
+        r = prior_repeat(ctx, &ps.alpha_last, ctx->alpha, 4, last);
         if (r) return r;
+        if (ns == 7 && (r = prior_repeat(ctx, &ps.coef_last, ctx->coef, 7, last))) return r;
     } else {
         ps.alpha_last = ps.alpha;
+        ps.coef_last = ps.coef;
     }
     if (ctx->tc) {
         long long a1, b1, e1, a2, b2, e2;
@@ -674,7 +736,7 @@ static int prior_stage_ensure(qmc_ctx *ctx)
         f.err = ctx->ozerr;
         l.oz = &ps.oz;
     }
-    CK(cudaStreamCreateWithFlags(&ps.side, cudaStreamNonBlocking));
+    CK(make_stream(&ps.side, false));
     CK(cudaEventCreateWithFlags(&ps.fork, cudaEventDisableTiming));
     for (int b = 0; b < 2; ++b) {
         CK(cudaEventCreateWithFlags(&ps.ready[b], cudaEventDisableTiming));
@@ -704,6 +766,7 @@ static int enqueue_prior_chunk(qmc_ctx *ctx, int j, double rho)
     ln.st = ps.side;
     ln.nb = ctx->nb * cz;
     ln.alpha = cz == ps.C ? ps.alpha : ps.alpha_last;
+    ln.coef = cz == ps.C ? ps.coef : ps.coef_last;
     pcn_move(ps.side, ctx->nb, nf, ctx->zeroO, ctx->phi + (long long)t0 * nf,
              (long long)ctx->L * nf, rho, ctx->keys, (uint32_t)t0, ctx->ctr, ps.phip[b], ps.lq[b],
              cz);
@@ -711,7 +774,8 @@ static int enqueue_prior_chunk(qmc_ctx *ctx, int j, double rho)
         ctx->err = "eigensolver: unsupported size";
         return QMC_ERR_ARG;
     }
-    factors_from_eig(ctx, ln, ps.Up[b], 4 * n2, ps.Wp[b], 4 * n, ps.V, ps.T, ps.lam, ps.Dg, ps.Dgi,
+    factors_from_eig(ctx, ln, ps.Up[b], ctx->ns * n2, ps.Wp[b], ctx->ns * n, ps.V, ps.T, ps.lam,
+                     ps.Dg, ps.Dgi,
                      nullptr, nullptr, nullptr);
     build_B(ctx, ln, ps.V, ps.T, ps.Dg, ps.Dgi, ps.Bp[b], NN, ps.Bpi[b], NN);
     CK(cudaEventRecord(ps.ready[b], ps.side));
@@ -730,10 +794,11 @@ static Proposal prior_proposal(const qmc_ctx *ctx, int s0)
     p.phip_cs = (long long)cz * nf;
     p.lq = ps.lq[b] + (long long)z * lqn;
     p.lq_cs = (long long)cz * lqn;
-    p.Up = ps.Up[b] + (long long)z * 4 * n2;
-    p.Up_cs = (long long)cz * 4 * n2;
-    p.Wp = ps.Wp[b] + (long long)z * 4 * n;
-    p.Wp_cs = (long long)cz * 4 * n;
+    const int ns = ctx->ns;
+    p.Up = ps.Up[b] + (long long)z * ns * n2;
+    p.Up_cs = (long long)cz * ns * n2;
+    p.Wp = ps.Wp[b] + (long long)z * ns * n;
+    p.Wp_cs = (long long)cz * ns * n;
     p.Bp = ps.Bp[b] + (long long)z * NN;
     p.Bpi = ps.Bpi[b] + (long long)z * NN;
     p.B_cs = (long long)cz * NN;
@@ -980,12 +1045,13 @@ static int propagators_from_fields(qmc_ctx *ctx)
         CommitP cp;
         cp.flag = ctx->always;
         cp.nseg = 2;
-        cp.seg[0] = CommitSeg{ctx->eigU + (long long)t * 4 * n2, ctx->Up, 4 * n2 * 4,
-                              L * 4 * n2 * 4, 4 * n2 * 4};
-        cp.seg[1] = CommitSeg{ctx->eigW + (long long)t * 4 * n, ctx->Wp, 4LL * n * 2,
-                              L * 4 * n * 2, 4LL * n * 2};
+        const long long ns = ctx->ns;
+        cp.seg[0] = CommitSeg{ctx->eigU + (long long)t * ns * n2, ctx->Up, ns * n2 * 4,
+                              L * ns * n2 * 4, ns * n2 * 4};
+        cp.seg[1] = CommitSeg{ctx->eigW + (long long)t * ns * n, ctx->Wp, ns * n * 2,
+                              L * ns * n * 2, ns * n * 2};
         launch_commit(s, nb, cp);
-        factors_from_eig(ctx, main_lane(ctx), ctx->Up, 4 * n2, ctx->Wp, 4 * n, ctx->V, ctx->T,
+        factors_from_eig(ctx, main_lane(ctx), ctx->Up, ns * n2, ctx->Wp, ns * n, ctx->V, ctx->T,
                          ctx->lam, ctx->Dg, ctx->Dgi, ctx->lamG, ctx->DgG, ctx->DgiG);
         build_B(ctx, main_lane(ctx), ctx->V, ctx->T, ctx->Dg, ctx->Dgi, ctx->B + (long long)t * NN,
                 L * NN, ctx->Binv + (long long)t * NN, L * NN);
@@ -1018,7 +1084,8 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
     }
     const int nq = (int)qxy.size() / 2;
     ctx->nq = nq;
-    ctx->nf = 4 * nq;
+    ctx->ns = ctx->o.slice_kind == QMC_SLICE_INDEP ? 7 : 4;
+    ctx->nf = ctx->ns * nq;
     std::vector<int> partner(nq), fkind(nq), frA(nq), frB(nq), fq(nq), fk(nq);
     // partner: -q on the torus, (l, -m) on the sphere (n_q^dagger = n_qbar)
     for (int q = 0; q < nq; ++q) {
@@ -1084,6 +1151,7 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
     ctx->seeds.resize(nb);
     ctx->g.resize(4 * nb);
     ctx->alpha.resize(4 * nb);
+    if (ctx->ns == 7) ctx->coef.resize(7 * nb);
     std::vector<uint32_t> keys(2 * nb);
     for (int c = 0; c < nb; ++c) {
         double u = ctx->o.couplings ? ctx->o.couplings[c] : coupling;
@@ -1103,6 +1171,12 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
             double v = -ctx->dtau * gg[i];
             ctx->alpha[4 * c + i] = v >= 0 ? cmk(sqrt(v), 0.0) : cmk(0.0, sqrt(-v));
         }
+        // a field set per factor: each half-factor decoupled on its own,
+        // exponent coefficient sqrt(-c_j dtau g_i)
+        for (int j = 0; j < 7 && ctx->ns == 7; ++j) {
+            double v = -trotter_coef(j) * ctx->dtau * gg[trotter_channel(j)];
+            ctx->coef[7 * c + j] = v >= 0 ? cmk(sqrt(v), 0.0) : cmk(0.0, sqrt(-v));
+        }
         keys[2 * c] = (uint32_t)(sd & 0xffffffffu);
         keys[2 * c + 1] = (uint32_t)(sd >> 32);
     }
@@ -1113,7 +1187,7 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
     const int nsp = (int)ctx->sp.size();
     const int N = ctx->N;
     const long long NN = ctx->NN, n2 = ctx->n2, L = ctx->L;
-    const int nf = ctx->nf;
+    const int nf = ctx->nf, ns = ctx->ns;
     // device allocations
     DA(ctx->ctr, QMC_CTR_N);
     DA(ctx->lq, (size_t)nb * net_pcn_blocks(nf));
@@ -1131,11 +1205,12 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
     DA(ctx->aptr, aptr.size());
     DA(ctx->aq, aq.size());
     DA(ctx->alpha_d, 4 * nb);
+    if (ctx->ns == 7) DA(ctx->coef_d, 7 * nb);
     DA(ctx->g_d, 4 * nb);
     DA(ctx->keys, 2 * nb);
     DA(ctx->phi, (size_t)nb * L * nf);
-    DA(ctx->eigU, (size_t)nb * L * 4 * n2);
-    DA(ctx->eigW, (size_t)nb * L * 4 * n);
+    DA(ctx->eigU, (size_t)nb * L * ns * n2);
+    DA(ctx->eigW, (size_t)nb * L * ns * n);
     DA(ctx->B, (size_t)nb * L * NN);
     DA(ctx->Binv, (size_t)nb * L * NN);
     DA(ctx->G, (size_t)nb * NN);
@@ -1145,25 +1220,25 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
     DAS(ctx->RQ, (size_t)nb * NN);
     DAS(ctx->RW, (size_t)nb * NN);
     DAS(ctx->RD, (size_t)nb * N);
-    DA(ctx->V, (size_t)nb * 4 * NN);
-    DAS(ctx->Vp, (size_t)nb * 4 * NN);
-    DA(ctx->T, (size_t)nb * 3 * NN);
-    DAS(ctx->Tp, (size_t)nb * 3 * NN);
+    DA(ctx->V, (size_t)nb * ns * NN);
+    DAS(ctx->Vp, (size_t)nb * ns * NN);
+    DA(ctx->T, (size_t)nb * (ns - 1) * NN);
+    DAS(ctx->Tp, (size_t)nb * (ns - 1) * NN);
     DA(ctx->lam, (size_t)nb * 7 * N);
     DA(ctx->Dg, (size_t)nb * 7 * N);
     DA(ctx->Dgi, (size_t)nb * 7 * N);
     DAS(ctx->lamp, (size_t)nb * 7 * N);
     DAS(ctx->Dgp, (size_t)nb * 7 * N);
     DAS(ctx->Dgip, (size_t)nb * 7 * N);
-    DAS(ctx->Up, (size_t)nb * 4 * n2);
-    DAS(ctx->Wp, (size_t)nb * 4 * n);
+    DAS(ctx->Up, (size_t)nb * ns * n2);
+    DAS(ctx->Wp, (size_t)nb * ns * n);
     DAS(ctx->Bp, (size_t)nb * NN);
     DAS(ctx->Bpi, (size_t)nb * NN);
     DAGS(ctx->Ah, (size_t)nb * NN);
     DAGS(ctx->Y1, (size_t)nb * NN);
-    DAGS(ctx->Cacc, (size_t)nb * 4 * NN);
-    DAGS(ctx->At, (size_t)nb * 4 * NN);
-    DAS(ctx->Fm, (size_t)nb * 4 * n2);
+    DAGS(ctx->Cacc, (size_t)nb * ns * NN);
+    DAGS(ctx->At, (size_t)nb * ns * NN);
+    DAS(ctx->Fm, (size_t)nb * ns * n2);
     if (ctx->gp == TY_C64) {
         ctx->lamG = ctx->lam;
         ctx->DgG = ctx->Dg;
@@ -1181,18 +1256,18 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
         DAG(ctx->lampG, (size_t)nb * 7 * N);
         DAG(ctx->DgpG, (size_t)nb * 7 * N);
         DAG(ctx->DgipG, (size_t)nb * 7 * N);
-        DAG(ctx->U32, (size_t)nb * 4 * n2);
-        DA(ctx->W32, (size_t)nb * 4 * n);
-        DAG(ctx->Fm32, (size_t)nb * 4 * n2);
+        DAG(ctx->U32, (size_t)nb * ns * n2);
+        DA(ctx->W32, (size_t)nb * ns * n);
+        DAG(ctx->Fm32, (size_t)nb * ns * n2);
     }
-    DAS(ctx->NSx, (size_t)nb * 4 * n2);
-    DAS(ctx->NSy, (size_t)nb * 4 * n2);
-    DAS(ctx->NSz, (size_t)nb * 4 * n2);
-    DAS(ctx->NSs, (size_t)nb * 4 * n2);
-    DAS(ctx->NSr, (size_t)nb * 4 * n2);
-    DAS(ctx->NSe, (size_t)nb * 4 * n2);
+    DAS(ctx->NSx, (size_t)nb * ns * n2);
+    DAS(ctx->NSy, (size_t)nb * ns * n2);
+    DAS(ctx->NSz, (size_t)nb * ns * n2);
+    DAS(ctx->NSs, (size_t)nb * ns * n2);
+    DAS(ctx->NSr, (size_t)nb * ns * n2);
+    DAS(ctx->NSe, (size_t)nb * ns * n2);
     DA(ctx->always, nb);
-    DAS(ctx->tq, (size_t)nb * 4 * nq);
+    DAS(ctx->tq, (size_t)nb * ns * nq);
     DAS(ctx->X1, (size_t)nb * NN);
     DAS(ctx->X2, (size_t)nb * NN);
     DAS(ctx->M, (size_t)nb * NN);
@@ -1227,7 +1302,7 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
         // per chain (eigenvector refinement), both at the FP64-class digit count
         long long a1, b1, e1, a2, b2, e2;
         oz_sizes_max(N, N, N, 7, nb, &a1, &b1, &e1);
-        oz_sizes_max(n, n, n, 7, 4 * nb, &a2, &b2, &e2);
+        oz_sizes_max(n, n, n, 7, ns * nb, &a2, &b2, &e2);
         OzCfg &f = ctx->ozF;
         f.S = 7;
         f.capA = std::max(a1, a2);
@@ -1256,6 +1331,9 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
     CK(cudaMemcpyAsync(ctx->aptr, aptr.data(), sizeof(int) * aptr.size(), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->aq, aq.data(), sizeof(int) * aq.size(), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->alpha_d, ctx->alpha.data(), sizeof(cd) * 4 * nb, cudaMemcpyHostToDevice, s));
+    if (ns == 7)
+        CK(cudaMemcpyAsync(ctx->coef_d, ctx->coef.data(), sizeof(cd) * 7 * nb,
+                           cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->g_d, ctx->g.data(), sizeof(double) * 4 * nb, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->keys, keys.data(), sizeof(uint32_t) * 2 * nb, cudaMemcpyHostToDevice, s));
     {
@@ -1301,7 +1379,7 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
         q.B = ctx->NSy;
         q.C = ctx->NSz;
         q.ta = q.tb = q.tc = q.rc = TY_C64;
-        gemm_autotune(s, q, 4 * nb, nullptr);
+        gemm_autotune(s, q, ns * nb, nullptr);
         if (ctx->tc) {
             // tensor-core tile widths for the same two shapes (FP64-class)
             p.opA = 0;
@@ -1309,7 +1387,7 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
             p.C = ctx->X1;
             p.tb = p.tc = p.rc = TY_C64;
             oz_autotune(s, p, nb, ctx->ozF);
-            if (n != N) oz_autotune(s, q, 4 * nb, ctx->ozF);
+            if (n != N) oz_autotune(s, q, ns * nb, ctx->ozF);
         }
     }
     int r = propagators_from_fields(ctx);
@@ -1371,7 +1449,8 @@ int qmc_create(qmc_ctx **out, int geometry, int N_phi, double beta, double dtau,
         code = QMC_ERR_ARG;
     } else if (ctx->o.n_chains < 1 || ctx->o.n_stab < 1 || ctx->o.series_capacity < 1 ||
                ctx->o.trace_capacity < 0 || ctx->o.precision < 0 || ctx->o.precision > 2 ||
-               (ctx->o.drift != QMC_DRIFT_EXACT && ctx->o.drift != QMC_DRIFT_FIRST)) {
+               (ctx->o.drift != QMC_DRIFT_EXACT && ctx->o.drift != QMC_DRIFT_FIRST) ||
+               (ctx->o.slice_kind != QMC_SLICE_SHARED && ctx->o.slice_kind != QMC_SLICE_INDEP)) {
         ctx->err = "invalid options";
         code = QMC_ERR_ARG;
     } else {
@@ -1484,7 +1563,8 @@ static int capture_sweeps(qmc_ctx *const *m, int nm, cudaStream_t origin, cudaGr
             r = QMC_ERR_CUDA;
         }
     }
-    if (r == QMC_OK && cudaGraphInstantiate(exec, graph, 0) != cudaSuccess) {
+    if (r == QMC_OK &&
+        cudaGraphInstantiate(exec, graph, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess) {
         *err = "cudaGraphInstantiate failed";
         r = QMC_ERR_CUDA;
     }
@@ -1504,7 +1584,7 @@ int qmc_sweep_graph(qmc_ctx *ctx, int n_sweeps)
     if (n_sweeps == 0) return QMC_OK;
     if (!ctx->gexec) {
         qmc_ctx *one[1] = {ctx};
-        if (!ctx->cap_st) CK(cudaStreamCreateWithFlags(&ctx->cap_st, cudaStreamNonBlocking));
+        if (!ctx->cap_st) CK(make_stream(&ctx->cap_st, true));
         int r = capture_sweeps(one, 1, ctx->cap_st, &ctx->gexec, &ctx->graph_kernels, &ctx->err);
         if (r) return r;
     }
@@ -1565,7 +1645,7 @@ int qmc_sweep_learned_graph(qmc_ctx *ctx, qmc_net *net, int n_sweeps, double rho
             cudaGraphExecDestroy(ctx->lexec);
             ctx->lexec = nullptr;
         }
-        if (!ctx->cap_st) CK(cudaStreamCreateWithFlags(&ctx->cap_st, cudaStreamNonBlocking));
+        if (!ctx->cap_st) CK(make_stream(&ctx->cap_st, true));
         qmc_ctx *one[1] = {ctx};
         // the network's own stream is not used inside the capture: every
         // kernel of the learned move is enqueued on the context's stream
@@ -1620,7 +1700,7 @@ int qmc_sweep_prior_graph(qmc_ctx *ctx, int n_sweeps, double rho)
             cudaGraphExecDestroy(ctx->pexec);
             ctx->pexec = nullptr;
         }
-        if (!ctx->cap_st) CK(cudaStreamCreateWithFlags(&ctx->cap_st, cudaStreamNonBlocking));
+        if (!ctx->cap_st) CK(make_stream(&ctx->cap_st, true));
         qmc_ctx *one[1] = {ctx};
         int r = capture_sweeps(one, 1, ctx->cap_st, &ctx->pexec, &ctx->pgraph_kernels, &ctx->err,
                                PRIOR_MOVE, rho);
@@ -1659,7 +1739,7 @@ int qmc_group_create(qmc_group **out, qmc_ctx *const *members, int n_members)
     g->m.assign(members, members + n_members);
     cudaError_t e = cudaStreamCreateWithFlags(&g->origin, cudaStreamNonBlocking);
     for (qmc_ctx *c : g->m)
-        if (e == cudaSuccess && !c->cap_st) e = cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking);
+        if (e == cudaSuccess && !c->cap_st) e = make_stream(&c->cap_st, true);
     g->ev.resize(n_members + 1, nullptr);
     for (auto &v : g->ev)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v, cudaEventDisableTiming);
@@ -2035,6 +2115,8 @@ int qmc_checkpoint_header_of(const qmc_ctx *ctx, qmc_checkpoint_header *h)
     ph = qmc_fnv1a(ctx->u.data(), sizeof(double) * ctx->u.size(), ph);
     ph = qmc_fnv1a(ctx->anis.data(), sizeof(double) * ctx->anis.size(), ph);
     ph = qmc_fnv1a(ctx->seeds.data(), sizeof(uint64_t) * ctx->seeds.size(), ph);
+    if (ctx->o.slice_kind != QMC_SLICE_SHARED)
+        ph = qmc_fnv1a(&ctx->o.slice_kind, sizeof(int), ph);
     h->params_hash = ph;
     h->n_doubles = state_doubles(ctx);
     return QMC_OK;

@@ -734,12 +734,13 @@ __global__ void __launch_bounds__(256) k_refine_E(int n, const cd *S, const cd *
             const double d = lam[j] - lam[i];
             if (fabs(d) > omega) {
                 // the first-order correction of the pair, and of its mirror
-                // (j, i): a pair whose correction is not small (eigenvalues
+                // (j, i): a pair whose correction exceeds 1e-4 (eigenvalues
                 // nearly degenerate against the remaining coupling) gets the
                 // orthogonalisation alone, on both sides so that E + E^H
                 // stays R; the coupling is rotated out afterwards.  Without
                 // this, such a pair drifted into the separated branch as
-                // omega shrank and lost X its unitarity.
+                // omega shrank and lost X its unitarity (measured: a bound
+                // of 1e-2 still let pairs lose it within the three steps).
                 const cd sv = S[e], sm = S[j * n + i], rm = R[j * n + i];
                 const double id = 1.0 / d;
                 const cd q = cscale(cd{sv.x + lam[j] * r.x, sv.y + lam[j] * r.y}, id);
@@ -759,13 +760,14 @@ __global__ void __launch_bounds__(256) k_refine_E(int n, const cd *S, const cd *
 // degenerate eigenvalues) are rotated out by 2 x 2 Jacobi rotations in FP64,
 // S <- J^H S J and U <- U J, cyclically over the listed pairs (the rotation
 // of the Jacobi kernel above).  One CTA per matrix, S rotated in place in
-// global memory; a few pairs at most, usually none.  *err is set if more
-// than RP_MAX pairs are coupled or 16 passes leave one above the threshold.
+// global memory; a few pairs at most, usually none.  *err is set if 16
+// passes (each rotating up to RP_MAX listed pairs) leave one above the
+// threshold.
 #define RP_MAX 64
 __global__ void __launch_bounds__(256) k_resolve_pairs(int n, cd *S, const cd *X, cd *U, double *w,
                                                        int *err)
 {
-    __shared__ int npair, pp[RP_MAX], pq[RP_MAX], again;
+    __shared__ int npair, pp[RP_MAX], pq[RP_MAX];
     __shared__ double red[8], thr;
     __shared__ cd jm[4];
     const int b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
@@ -779,30 +781,34 @@ __global__ void __launch_bounds__(256) k_resolve_pairs(int n, cd *S, const cd *X
     for (int i = tid; i < n; i += nt) mx = fmax(mx, fabs(S[(long long)i * n + i].x));
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((tid & 31) == 0) red[tid >> 5] = mx;
-    if (tid == 0) npair = 0;
     __syncthreads();
     if (tid == 0) {
         double m = 0.0;
         for (int k = 0; k < nt / 32; ++k) m = fmax(m, red[k]);
         thr = 1e-12 * m + 1e-300;
     }
-    __syncthreads();
-    for (long long e = tid; e < nn; e += nt) {
-        const int i = (int)(e / n), j = (int)(e % n);
-        if (i < j && cabs2(S[e]) > thr * thr) {
-            const int k = atomicAdd(&npair, 1);
-            if (k < RP_MAX) {
-                pp[k] = i;
-                pq[k] = j;
+    // passes: list the pairs above the threshold (a rotation can couple a
+    // pair that was below it), rotate each once; stop when none is listed
+    for (int pass = 0;; ++pass) {
+        if (tid == 0) npair = 0;
+        __syncthreads();
+        for (long long e = tid; e < nn; e += nt) {
+            const int i = (int)(e / n), j = (int)(e % n);
+            if (i < j && cabs2(S[e]) > thr * thr) {
+                const int k = atomicAdd(&npair, 1);
+                if (k < RP_MAX) {
+                    pp[k] = i;
+                    pq[k] = j;
+                }
             }
         }
-    }
-    __syncthreads();
-    const int np = min(npair, RP_MAX);
-    if (tid == 0 && npair > RP_MAX) atomicOr(err, 1);
-    for (int pass = 0; pass < 16 && np > 0; ++pass) {
-        if (tid == 0) again = 0;
         __syncthreads();
+        const int np = min(npair, RP_MAX);
+        if (np == 0) break;
+        if (pass == 16) {
+            if (tid == 0) atomicOr(err, 1);
+            break;
+        }
         for (int k = 0; k < np; ++k) {
             const int p = pp[k], q = pq[k];
             if (tid == 0) {
@@ -811,7 +817,6 @@ __global__ void __launch_bounds__(256) k_resolve_pairs(int n, cd *S, const cd *X
                 double c = 1.0, sn = 0.0;
                 cd ph = cmk(1, 0);
                 if (ab > thr) {
-                    again = 1;
                     const double app = S[(long long)p * n + p].x, aqq = S[(long long)q * n + q].x;
                     ph = cmk(apq.x / ab, apq.y / ab);
                     const double zeta = (aqq - app) / (2 * ab);
@@ -851,8 +856,6 @@ __global__ void __launch_bounds__(256) k_resolve_pairs(int n, cd *S, const cd *X
             }
             __syncthreads();
         }
-        if (!again) break;
-        if (pass == 15 && tid == 0) atomicOr(err, 1);
     }
     for (int i = tid; i < n; i += nt) w[i] = S[(long long)i * n + i].x;
 }
@@ -1044,8 +1047,10 @@ __global__ void __launch_bounds__(256) k_lu_bc(int n, cd *A, long long sA, int *
     extern __shared__ __align__(16) unsigned char sm_lb_raw[];
     cd *Mb = (cd *)sm_lb_raw;                      // n x W, row stride ldw
     cd *Lp = Mb + (size_t)n * ldw;                 // n x LU_LB multipliers of the current panel
-    int *pv = (int *)(Lp + (size_t)n * LU_LB);     // pivots of this CTA's panels, by global row
-    __shared__ double parts[3][8];
+    cd *ud = Lp + (size_t)n * LU_LB;               // u_kk gathered in rank 0 (log det)
+    int *pv = (int *)(ud + n);                     // pivots of this CTA's panels, by global row
+    __shared__ double red[2][8];
+    __shared__ int nswr[8];
     cd *Ab = A + (long long)b * sA;
     // local column lc <-> global column: panel q = (lc / LB) cs + rank
     auto gcol = [&](int lc) { return ((lc / LU_LB) * cs + rank) * LU_LB + lc % LU_LB; };
@@ -1054,8 +1059,7 @@ __global__ void __launch_bounds__(256) k_lu_bc(int n, cd *A, long long sA, int *
         const int i = e / wl, lc = e % wl, j = gcol(lc);
         Mb[i * ldw + lc] = j < n ? Ab[(long long)i * n + j] : cmk(0, 0);
     }
-    cd lsum = cmk(0, 0);  // sum of log u_kk over this CTA's pivots (warp 0, lane 0)
-    int nsw = 0;
+    int nsw = 0;  // row exchanges of this CTA's panels (warp 0, lane 0)
     cl.sync();
     for (int q = 0; q < np; ++q) {
         const int owner = q % cs, k0 = q * LU_LB, kb = min(LU_LB, n - k0);
@@ -1103,7 +1107,7 @@ __global__ void __launch_bounds__(256) k_lu_bc(int n, cd *A, long long sA, int *
                 if (lane == 0) {
                     pv[k] = p;
                     piv[(long long)b * spiv + k] = p;
-                    lsum = cadd(lsum, clog_d(pk));
+                    cl.map_shared_rank(ud, 0)[k] = pk;
                     if (p != k) ++nsw;
                 }
                 __syncwarp();
@@ -1161,29 +1165,38 @@ __global__ void __launch_bounds__(256) k_lu_bc(int n, cd *A, long long sA, int *
         const int i = e / wl, lc = e % wl, j = gcol(lc);
         if (j < n) Ab[(long long)i * n + j] = Mb[i * ldw + lc];
     }
-    if (tid == 0) {
-        double *slot = cl.map_shared_rank(&parts[0][0], 0);
-        slot[rank] = lsum.x;
-        slot[8 + rank] = lsum.y;
-        slot[16 + rank] = (double)nsw;
-    }
+    if (tid == 0) cl.map_shared_rank(nswr, 0)[rank] = nsw;
     cl.sync();
-    if (rank == 0 && tid == 0 && logdet) {
+    // log det = sum_k log u_kk (+ i pi per row exchange) in rank 0, in the
+    // one-CTA kernel's order: a term per thread, warp trees, warps in order
+    if (rank == 0 && logdet) {
         cd t = cmk(0, 0);
-        int sw = 0;
-        for (int r = 0; r < cs; ++r) {
-            t = cadd(t, cmk(parts[0][r], parts[1][r]));
-            sw += (int)parts[2][r];
+        for (int k = tid; k < n; k += nt) t = cadd(t, clog_d(ud[k]));
+        for (int o = 16; o > 0; o >>= 1) {
+            t.x += __shfl_xor_sync(0xffffffffu, t.x, o);
+            t.y += __shfl_xor_sync(0xffffffffu, t.y, o);
         }
-        if (sw & 1) t.y += 3.14159265358979323846;
-        logdet[b] = t;
+        if (lane == 0) {
+            red[0][warp] = t.x;
+            red[1][warp] = t.y;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            cd u = cmk(0, 0);
+            int sw = 0;
+            for (int w = 0; w < nt / 32; ++w) u = cadd(u, cmk(red[0][w], red[1][w]));
+            for (int r = 0; r < cs; ++r) sw += nswr[r];
+            if (sw & 1) u.y += 3.14159265358979323846;
+            logdet[b] = u;
+        }
     }
 }
 
 static size_t lu_bc_smem(int n, int cs)
 {
     const int np = (n + LU_LB - 1) / LU_LB, W = ((np + cs - 1) / cs) * LU_LB;
-    return (size_t)n * (W + 1) * sizeof(cd) + (size_t)n * LU_LB * sizeof(cd) + (size_t)n * 4;
+    return (size_t)n * (W + 1) * sizeof(cd) + (size_t)n * (LU_LB + 1) * sizeof(cd) +
+           (size_t)n * 4;
 }
 
 static int lu_bc_launch(cudaStream_t st, int n, cd *A, long long sA, int *piv, long long spiv,

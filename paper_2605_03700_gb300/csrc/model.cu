@@ -224,10 +224,10 @@ __global__ void k_assemble(int n, int nq, const double *phi, long long phi_cs, c
         int q = aq[t];
         cfma(s, zfield(ph, fkind[q], frA[q], frB[q]), val[q * n + k]);
     }
-    ((C *)Fv)[((long long)c * 4 + i) * n * n + e] = cvt<C>(s);
+    ((C *)Fv)[((long long)c * gridDim.y + i) * n * n + e] = cvt<C>(s);
 }
 
-// V_i = R_i (x) U_i, the eigenvectors of O^i (x) F^(i)
+// V_s = R_i (x) U_s, the eigenvectors of O^i (x) F^(i) of set s (channel i)
 template <class R>
 __global__ void k_build_V(int n, const void *Uv, long long U_cs, void *Vv)
 {
@@ -239,15 +239,17 @@ __global__ void k_build_V(int n, const void *Uv, long long U_cs, void *Vv)
     int r = e / N, cc = e % N;
     int v = r / n, k = r % n, w = cc / n, kp = cc % n;
     C u = ((const C *)Uv)[(long long)c * U_cs + (long long)i * n * n + k * n + kp];
-    ((C *)Vv)[((long long)c * 4 + i) * N * N + e] = cmul(cvt<C>(valley_R(i, v, w)), u);
+    const int ch = set_channel(gridDim.y, i);
+    ((C *)Vv)[((long long)c * gridDim.y + i) * N * N + e] = cmul(cvt<C>(valley_R(ch, v, w)), u);
 }
 
-// lambda_j(x) = c_j alpha_i o_i(v) w_i(k) for the seven factors, and
+// lambda_j(x) = a_j o_i(v) w_s(k) for the seven factors (a_j = c_j alpha_i
+// with shared field sets, sqrt(-c_j dtau g_i) with a set per factor), and
 // D_j = e^{lambda_j}, Dinv_j = e^{-lambda_j} (eigenvalues w in FP64, outputs
 // in the compute type)
 template <class R>
-__global__ void k_lambda(int n, const void *wv, long long w_cs, const cd *alpha, void *lamv,
-                         void *Dgv, void *Dgiv)
+__global__ void k_lambda(int n, int ns, const void *wv, long long w_cs, const cd *alpha,
+                         const cd *coef, void *lamv, void *Dgv, void *Dgiv)
 {
     typedef typename Cx<R>::T C;
     int N = 2 * n;
@@ -256,8 +258,10 @@ __global__ void k_lambda(int n, const void *wv, long long w_cs, const cd *alpha,
     if (x >= N) return;
     int i = trotter_channel(j);
     int v = x / n, k = x % n;
-    double mu = valley_o(i, v) * ((const double *)wv)[(long long)c * w_cs + i * n + k];
-    cd a = cscale(alpha[c * 4 + i], trotter_coef(j) * mu);
+    double mu = valley_o(i, v) *
+                ((const double *)wv)[(long long)c * w_cs + factor_set(ns, j) * n + k];
+    // shared sets: c_j alpha_i; a set per factor: its own coefficient
+    cd a = coef ? cscale(coef[c * 7 + j], mu) : cscale(alpha[c * 4 + i], trotter_coef(j) * mu);
     long long o = ((long long)c * 7 + j) * N + x;
     ((C *)lamv)[o] = cvt<C>(a);
     ((C *)Dgv)[o] = cvt<C>(cexp_d(a));
@@ -283,11 +287,12 @@ template <class C> QMC_DEVFN C phi1(C x)
     return cdiv(e, x);
 }
 
-// C_i (+)= a_j * (Ah o Phi_j), Phi_j[m][k] = phi1(lambda_j[k] - lambda_j[m]):
+// C_s (+)= a_j * (Ah o Phi_j) into the set s of factor j,
+// Phi_j[m][k] = phi1(lambda_j[k] - lambda_j[m]):
 // the Daleckii-Krein form of int_0^1 e^{-sX} A e^{sX} ds in the eigenbasis
 template <class R>
-__global__ void k_accum(int N, int j, int first, const cd *alpha, const void *lamv,
-                        const void *Ahv, void *Caccv)
+__global__ void k_accum(int N, int j, int first, int ns, const cd *alpha, const cd *coef,
+                        const void *lamv, const void *Ahv, void *Caccv)
 {
     typedef typename Cx<R>::T C;
     int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -296,17 +301,18 @@ __global__ void k_accum(int N, int j, int first, const cd *alpha, const void *la
     int i = trotter_channel(j);
     int m = e / N, k = e % N;
     const C *lj = (const C *)lamv + ((long long)c * 7 + j) * N;
-    C a = cvt<C>(cscale(alpha[c * 4 + i], trotter_coef(j)));
+    C a = cvt<C>(coef ? coef[c * 7 + j] : cscale(alpha[c * 4 + i], trotter_coef(j)));
     C v = cmul(a, cmul(((const C *)Ahv)[(long long)c * N * N + e], phi1(csub(lj[k], lj[m]))));
-    C *dst = (C *)Caccv + ((long long)c * 4 + i) * N * N + e;
+    C *dst = (C *)Caccv + ((long long)c * ns + factor_set(ns, j)) * N * N + e;
     *dst = first ? v : cadd(*dst, v);
 }
 
 // First-order drift: Atilde^(i) = alpha_i (1 - G) for every channel (each
 // factor's derivative Tr[(1 - G) dX_j]; the coefficients c_j of a channel's
-// factors sum to one); grid (N^2 / 256, 4 channels, chains)
+// factors sum to one); with a set per factor a_j (1 - G) per factor; grid
+// (N^2 / 256, field sets, chains)
 template <class R>
-__global__ void k_first_drift(int N, const cd *G, const cd *alpha, void *Atv)
+__global__ void k_first_drift(int N, const cd *G, const cd *alpha, const cd *coef, void *Atv)
 {
     typedef typename Cx<R>::T C;
     int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -315,21 +321,24 @@ __global__ void k_first_drift(int N, const cd *G, const cd *alpha, void *Atv)
     cd g = G[(long long)c * N * N + e];
     cd v = cmk(-g.x, -g.y);
     if (e / N == e % N) v.x += 1.0;
-    ((C *)Atv)[((long long)c * 4 + i) * N * N + e] = cvt<C>(cmul(alpha[c * 4 + i], v));
+    const cd a = coef ? coef[c * 7 + i] : alpha[c * 4 + i];
+    ((C *)Atv)[((long long)c * gridDim.y + i) * N * N + e] = cvt<C>(cmul(a, v));
 }
 
-// t^(i)_q = Tr[(O^i (x) F_q) Atilde^(i)] - delta_{i0} alpha_0 Tr F_q
-// (accumulated in FP64)
+// t^(s)_q = Tr[(O^i (x) F_q) Atilde^(s)] - delta_{i0} a Tr F_q for field set s
+// of channel i (a = alpha_0 for shared sets, the factor's coefficient for a
+// set per factor; accumulated in FP64)
 template <class R>
 __global__ void k_trace_t(int n, int nq, const void *Atv, const cd *val, const int *col,
-                          const cd *trF, const cd *alpha, cd *t)
+                          const cd *trF, const cd *alpha, const cd *coef, cd *t)
 {
     typedef typename Cx<R>::T C;
     int q = blockIdx.x * blockDim.x + threadIdx.x;
-    int i = blockIdx.y, c = blockIdx.z;
+    int set = blockIdx.y, c = blockIdx.z, ns = gridDim.y;
     if (q >= nq) return;
     int N = 2 * n;
-    const C *A = (const C *)Atv + ((long long)c * 4 + i) * N * N;
+    const int i = set_channel(ns, set);
+    const C *A = (const C *)Atv + ((long long)c * ns + set) * N * N;
     cd s = cmk(0, 0);
     for (int v = 0; v < 2; ++v) {
         int w = (i == 1 || i == 2) ? 1 - v : v;
@@ -340,25 +349,25 @@ __global__ void k_trace_t(int n, int nq, const void *Atv, const cd *val, const i
             cfma(s, cmul(o, val[q * n + k]), cvt<cd>(A[(w * n + cc) * N + (v * n + k)]));
         }
     }
-    if (i == 0) s = csub(s, cmul(alpha[c * 4], trF[q]));
-    t[((long long)c * 4 + i) * nq + q] = s;
+    if (i == 0) s = csub(s, cmul(coef ? coef[c * 7 + set] : alpha[c * 4], trF[q]));
+    t[((long long)c * ns + set) * nq + q] = s;
 }
 
 // grad_phi S = phi - 2 Re d ln(bracket)/d phi for every real field
-__global__ void k_grad(int nq, const int *fq, const int *fk, const int *partner,
+__global__ void k_grad(int nq, int ns, const int *fq, const int *fk, const int *partner,
                        const double *phi, long long phi_cs, const cd *t, double *grad)
 {
     int f = blockIdx.x * blockDim.x + threadIdx.x;
     int c = blockIdx.y;
-    if (f >= 4 * nq) return;
+    if (f >= ns * nq) return;
     int i = f / nq, r = f % nq;
     int q = fq[r], kind = fk[r];
-    const cd *ti = t + ((long long)c * 4 + i) * nq;
+    const cd *ti = t + ((long long)c * ns + i) * nq;
     double d;
     if (kind == 0) d = 1.4142135623730951 * ti[q].x;
     else if (kind == 1) d = ti[q].x + ti[partner[q]].x;
     else d = -(ti[q].y - ti[partner[q]].y);
-    grad[(long long)c * 4 * nq + f] = phi[(long long)c * phi_cs + f] - 2.0 * d;
+    grad[(long long)c * ns * nq + f] = phi[(long long)c * phi_cs + f] - 2.0 * d;
 }
 
 // phi' = phi - (eps^2/2) grad + eps xi (Methods, Eq. langevin_proposal with
@@ -418,7 +427,7 @@ __global__ void __launch_bounds__(256) k_accept(AcceptP p)
     const uint32_t sweep = p.ctr[QMC_CTR_SWEEP];
     __shared__ double sh[32];
     const int c = blockIdx.x, tid = threadIdx.x;
-    const int nq = p.nq, nf = 4 * nq;
+    const int nq = p.nq, nf = p.ns * nq;
     const double *ph = p.phi + (long long)c * p.phi_cs;
     const double *pp = p.phip + (long long)c * p.phip_cs;
     const bool learned = p.lq != nullptr;
@@ -438,6 +447,9 @@ __global__ void __launch_bounds__(256) k_accept(AcceptP p)
             bw += y * y;
         }
     }
+    // channel-0 background sums: set 0, and with a set per factor also set 6
+    // (the second channel-0 half-factor), each weighted by its coefficient
+    double tr6 = 0, ti6 = 0, trp6 = 0, tip6 = 0;
     for (int q = tid; q < nq; q += blockDim.x) {
         cd z = zfield(ph, p.fkind[q], p.frA[q], p.frB[q]);
         cd zp = zfield(pp, p.fkind[q], p.frA[q], p.frB[q]);
@@ -446,6 +458,15 @@ __global__ void __launch_bounds__(256) k_accept(AcceptP p)
         ti += a.y;
         trp += b.x;
         tip += b.y;
+        if (p.coef) {
+            cd z6 = zfield(ph + 6 * nq, p.fkind[q], p.frA[q], p.frB[q]);
+            cd zp6 = zfield(pp + 6 * nq, p.fkind[q], p.frA[q], p.frB[q]);
+            cd a6 = cmul(z6, p.trF[q]), b6 = cmul(zp6, p.trF[q]);
+            tr6 += a6.x;
+            ti6 += a6.y;
+            trp6 += b6.x;
+            tip6 += b6.y;
+        }
     }
     s0 = block_sum(s0, sh);
     s0p = block_sum(s0p, sh);
@@ -455,10 +476,23 @@ __global__ void __launch_bounds__(256) k_accept(AcceptP p)
     ti = block_sum(ti, sh);
     trp = block_sum(trp, sh);
     tip = block_sum(tip, sh);
+    if (p.coef) {
+        tr6 = block_sum(tr6, sh);
+        ti6 = block_sum(ti6, sh);
+        trp6 = block_sum(trp6, sh);
+        tip6 = block_sum(tip6, sh);
+    }
     if (tid == 0) {
-        cd a0 = p.alpha[c * 4];
-        cd w0 = cscale(cmul(a0, cmk(tr, ti)), 2.0);
-        cd w0p = cscale(cmul(a0, cmk(trp, tip)), 2.0);
+        cd w0, w0p;
+        if (p.coef) {
+            const cd a0 = p.coef[c * 7], a6 = p.coef[c * 7 + 6];
+            w0 = cscale(cadd(cmul(a0, cmk(tr, ti)), cmul(a6, cmk(tr6, ti6))), 2.0);
+            w0p = cscale(cadd(cmul(a0, cmk(trp, tip)), cmul(a6, cmk(trp6, tip6))), 2.0);
+        } else {
+            const cd a0 = p.alpha[c * 4];
+            w0 = cscale(cmul(a0, cmk(tr, ti)), 2.0);
+            w0p = cscale(cmul(a0, cmk(trp, tip)), 2.0);
+        }
         cd lr = csub(p.logdet[c], cscale(csub(w0p, w0), 0.5));
         // Langevin move: the proposal densities; learned move: the pCN
         // reference-density correction (both exact MH for the same target)
@@ -852,58 +886,63 @@ void launch_init_phi(cudaStream_t s, int nb, int L, int nf, const uint32_t *keys
     k_init_phi<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(nb, L, nf, keys, phi);
     QMC_COUNT(1);
 }
-void launch_assemble(cudaStream_t s, int prec, int nb, int n, int nq, const double *phi,
+void launch_assemble(cudaStream_t s, int prec, int nb, int ns, int n, int nq, const double *phi,
                      long long phi_cs, const int *fkind, const int *frA, const int *frB,
                      const int *aptr, const int *aq, const cd *val, void *F)
 {
-    dim3 g(cdiv_up(n * n, 128), 4, nb);
+    dim3 g(cdiv_up(n * n, 128), ns, nb);
     if (prec == TY_C64)
         k_assemble<double><<<g, 128, 0, s>>>(n, nq, phi, phi_cs, fkind, frA, frB, aptr, aq, val, F);
     else
         k_assemble<float><<<g, 128, 0, s>>>(n, nq, phi, phi_cs, fkind, frA, frB, aptr, aq, val, F);
     QMC_COUNT(1);
 }
-void launch_build_V(cudaStream_t s, int prec, int nb, int n, const void *U, long long U_cs, void *V)
+void launch_build_V(cudaStream_t s, int prec, int nb, int ns, int n, const void *U, long long U_cs,
+                    void *V)
 {
     int N = 2 * n;
-    dim3 g(cdiv_up(N * N, 256), 4, nb);
+    dim3 g(cdiv_up(N * N, 256), ns, nb);
     if (prec == TY_C64) k_build_V<double><<<g, 256, 0, s>>>(n, U, U_cs, V);
     else k_build_V<float><<<g, 256, 0, s>>>(n, U, U_cs, V);
     QMC_COUNT(1);
 }
-void launch_lambda(cudaStream_t s, int prec, int nb, int n, const void *w, long long w_cs,
-                   const cd *alpha, void *lam, void *Dg, void *Dgi)
+void launch_lambda(cudaStream_t s, int prec, int nb, int ns, int n, const void *w, long long w_cs,
+                   const cd *alpha, const cd *coef, void *lam, void *Dg, void *Dgi)
 {
     dim3 g(cdiv_up(2 * n, 128), 7, nb);
-    if (prec == TY_C64) k_lambda<double><<<g, 128, 0, s>>>(n, w, w_cs, alpha, lam, Dg, Dgi);
-    else k_lambda<float><<<g, 128, 0, s>>>(n, w, w_cs, alpha, lam, Dg, Dgi);
+    if (prec == TY_C64)
+        k_lambda<double><<<g, 128, 0, s>>>(n, ns, w, w_cs, alpha, coef, lam, Dg, Dgi);
+    else k_lambda<float><<<g, 128, 0, s>>>(n, ns, w, w_cs, alpha, coef, lam, Dg, Dgi);
     QMC_COUNT(1);
 }
-void launch_accum(cudaStream_t s, int prec, int nb, int N, int j, int first, const cd *alpha,
-                  const void *lam, const void *Ah, void *Cacc)
+void launch_accum(cudaStream_t s, int prec, int nb, int N, int j, int first, int ns,
+                  const cd *alpha, const cd *coef, const void *lam, const void *Ah, void *Cacc)
 {
     dim3 g(cdiv_up(N * N, 256), nb);
-    if (prec == TY_C64) k_accum<double><<<g, 256, 0, s>>>(N, j, first, alpha, lam, Ah, Cacc);
-    else k_accum<float><<<g, 256, 0, s>>>(N, j, first, alpha, lam, Ah, Cacc);
+    if (prec == TY_C64)
+        k_accum<double><<<g, 256, 0, s>>>(N, j, first, ns, alpha, coef, lam, Ah, Cacc);
+    else k_accum<float><<<g, 256, 0, s>>>(N, j, first, ns, alpha, coef, lam, Ah, Cacc);
     QMC_COUNT(1);
 }
-void launch_first_drift(cudaStream_t s, int prec, int nb, int N, const cd *G, const cd *alpha,
-                        void *At)
+void launch_first_drift(cudaStream_t s, int prec, int nb, int ns, int N, const cd *G,
+                        const cd *alpha, const cd *coef, void *At)
 {
-    dim3 g(cdiv_up(N * N, 256), 4, nb);
-    if (prec == TY_C64) k_first_drift<double><<<g, 256, 0, s>>>(N, G, alpha, At);
-    else k_first_drift<float><<<g, 256, 0, s>>>(N, G, alpha, At);
+    dim3 g(cdiv_up(N * N, 256), ns, nb);
+    if (prec == TY_C64) k_first_drift<double><<<g, 256, 0, s>>>(N, G, alpha, coef, At);
+    else k_first_drift<float><<<g, 256, 0, s>>>(N, G, alpha, coef, At);
     QMC_COUNT(1);
 }
-void launch_trace_grad(cudaStream_t s, int prec, int nb, int n, int nq, const void *At,
-                       const cd *val, const int *col, const cd *trF, const cd *alpha, cd *t,
-                       const int *fq, const int *fk, const int *partner, const double *phi,
-                       long long phi_cs, double *grad)
+void launch_trace_grad(cudaStream_t s, int prec, int nb, int ns, int n, int nq, const void *At,
+                       const cd *val, const int *col, const cd *trF, const cd *alpha,
+                       const cd *coef, cd *t, const int *fq, const int *fk, const int *partner,
+                       const double *phi, long long phi_cs, double *grad)
 {
-    dim3 g(cdiv_up(nq, 64), 4, nb);
-    if (prec == TY_C64) k_trace_t<double><<<g, 64, 0, s>>>(n, nq, At, val, col, trF, alpha, t);
-    else k_trace_t<float><<<g, 64, 0, s>>>(n, nq, At, val, col, trF, alpha, t);
-    k_grad<<<dim3(cdiv_up(4 * nq, 128), nb), 128, 0, s>>>(nq, fq, fk, partner, phi, phi_cs, t, grad);
+    dim3 g(cdiv_up(nq, 64), ns, nb);
+    if (prec == TY_C64)
+        k_trace_t<double><<<g, 64, 0, s>>>(n, nq, At, val, col, trF, alpha, coef, t);
+    else k_trace_t<float><<<g, 64, 0, s>>>(n, nq, At, val, col, trF, alpha, coef, t);
+    k_grad<<<dim3(cdiv_up(ns * nq, 128), nb), 128, 0, s>>>(nq, ns, fq, fk, partner, phi, phi_cs, t,
+                                                           grad);
     QMC_COUNT(2);
 }
 void launch_propose(cudaStream_t s, int nb, int nf, const double *phi, long long phi_cs,

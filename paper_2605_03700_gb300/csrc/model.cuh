@@ -8,6 +8,8 @@ enum { QMC_CTR_SWEEP = 0, QMC_CTR_SERIES = 1, QMC_CTR_N = 2 };
 
 struct AcceptP {
     int nq;
+    int ns;            // field sets per slice (4 shared, 7 a set per factor)
+    const cd *coef;    // a set per factor: the factors' coefficients [chain][7]; else null
     const double *phi;
     long long phi_cs;
     const double *phip, *grad, *gradp, *eps;
@@ -61,20 +63,24 @@ struct MeasP {
 void launch_ff_torus(cudaStream_t s, int n, int nq, const int *qxy, cd *val, int *col, cd *trF);
 void launch_ff_sphere(cudaStream_t s, int n, cd *val, int *col, cd *trF);
 void launch_init_phi(cudaStream_t s, int nb, int L, int nf, const uint32_t *keys, double *phi);
-void launch_assemble(cudaStream_t s, int prec, int nb, int n, int nq, const double *phi,
+// ns: field sets per slice (4: one per channel, shared by both half-factors;
+// 7: one per factor); coef: with 7 sets, the factors' exponent coefficients
+// [chain][7], else null (the channel alphas with c_j are used)
+void launch_assemble(cudaStream_t s, int prec, int nb, int ns, int n, int nq, const double *phi,
                      long long phi_cs, const int *fkind, const int *frA, const int *frB,
                      const int *aptr, const int *aq, const cd *val, void *F);
-void launch_build_V(cudaStream_t s, int prec, int nb, int n, const void *U, long long U_cs, void *V);
-void launch_lambda(cudaStream_t s, int prec, int nb, int n, const void *w, long long w_cs,
-                   const cd *alpha, void *lam, void *Dg, void *Dgi);
-void launch_accum(cudaStream_t s, int prec, int nb, int N, int j, int first, const cd *alpha,
-                  const void *lam, const void *Ah, void *Cacc);
-void launch_first_drift(cudaStream_t s, int prec, int nb, int N, const cd *G, const cd *alpha,
-                        void *At);
-void launch_trace_grad(cudaStream_t s, int prec, int nb, int n, int nq, const void *At,
-                       const cd *val, const int *col, const cd *trF, const cd *alpha, cd *t,
-                       const int *fq, const int *fk, const int *partner, const double *phi,
-                       long long phi_cs, double *grad);
+void launch_build_V(cudaStream_t s, int prec, int nb, int ns, int n, const void *U, long long U_cs,
+                    void *V);
+void launch_lambda(cudaStream_t s, int prec, int nb, int ns, int n, const void *w, long long w_cs,
+                   const cd *alpha, const cd *coef, void *lam, void *Dg, void *Dgi);
+void launch_accum(cudaStream_t s, int prec, int nb, int N, int j, int first, int ns,
+                  const cd *alpha, const cd *coef, const void *lam, const void *Ah, void *Cacc);
+void launch_first_drift(cudaStream_t s, int prec, int nb, int ns, int N, const cd *G,
+                        const cd *alpha, const cd *coef, void *At);
+void launch_trace_grad(cudaStream_t s, int prec, int nb, int ns, int n, int nq, const void *At,
+                       const cd *val, const int *col, const cd *trF, const cd *alpha,
+                       const cd *coef, cd *t, const int *fq, const int *fk, const int *partner,
+                       const double *phi, long long phi_cs, double *grad);
 void launch_propose(cudaStream_t s, int nb, int nf, const double *phi, long long phi_cs,
                     const double *grad, const double *eps, const uint32_t *keys, uint32_t slice,
                     const uint32_t *ctr, double *phip);

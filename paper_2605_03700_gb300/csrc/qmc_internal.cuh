@@ -186,6 +186,18 @@ __host__ __device__ __forceinline__ int trotter_channel(int j)
 }
 __host__ __device__ __forceinline__ double trotter_coef(int j) { return j == 3 ? 1.0 : 0.5; }
 
+// Field sets per slice: ns = 4 (the paper's reading, one set per channel
+// shared by both half-factors) or 7 (one set per factor).  The channel of
+// set s, and the set of factor j.
+__host__ __device__ __forceinline__ int set_channel(int ns, int s)
+{
+    return ns == 7 ? trotter_channel(s) : s;
+}
+__host__ __device__ __forceinline__ int factor_set(int ns, int j)
+{
+    return ns == 7 ? j : trotter_channel(j);
+}
+
 // valley rotations R_i with O^i = R_i diag(o_i) R_i^H (O = I, tau_x, tau_y,
 // tau_z); entry (v, w) and the eigenvalue sign o_i[w]
 __host__ __device__ __forceinline__ cd valley_R(int i, int v, int w)

@@ -20,6 +20,7 @@ QMC_SPHERE = 1
 QMC_NOBS = 20
 QMC_NTRACE = 8
 QMC_DRIFT_EXACT, QMC_DRIFT_FIRST = 0, 1
+QMC_SLICE_SHARED, QMC_SLICE_INDEP = 0, 2
 OBS_NAMES = ["m2", "S1_0", "S2_0", "S3_0", "S4_0", "S5_0", "S1_dq", "S2_dq",
              "S3_dq", "S4_dq", "S5_dq", "R", "E", "acc", "eps", "stab_err",
              "sign_dev", "n_acc", "_", "_"]
@@ -43,6 +44,7 @@ class qmc_opts(C.Structure):
         ("stab_tol", C.c_double),
         ("sign_tol", C.c_double),
         ("drift", C.c_int),
+        ("slice_kind", C.c_int),
     ]
 
 
@@ -265,10 +267,11 @@ class Chain:
                  n_chains=1, couplings=None, anisotropies=None, seeds=None, n_stab=10,
                  eps0=0.5, deps=0.1, r0=0.574, n_adapt=-1, series_capacity=4096,
                  trace_capacity=0, stab_tol=1e-6, sign_tol=1e-6, precision=0, n_orb_sphere=0,
-                 drift=0, stream=None):
+                 drift=0, slice_kind=0, stream=None):
         o = qmc_default_opts()
         o.n_stab = n_stab
         o.drift = drift
+        o.slice_kind = slice_kind
         o.n_orb_sphere = n_orb_sphere
         o.precision = precision
         o.eps0, o.deps, o.r0, o.n_adapt = eps0, deps, r0, n_adapt
@@ -300,6 +303,8 @@ class Chain:
         self.n_orb, self.n_q, self.L, self.n_chains = n_orb.value, n_q.value, L.value, nb.value
         self.N = 2 * self.n_orb
         self.trace_capacity = trace_capacity
+        # field sets per slice: 4 (one per channel) or 7 (one per factor)
+        self.n_sets = 7 if slice_kind == QMC_SLICE_INDEP else 4
 
     def close(self):
         if getattr(self, "h", None):
@@ -412,7 +417,7 @@ class Chain:
         return B, Bi
 
     def fields(self, chain=0):
-        p = np.zeros((self.L, 4, self.n_q))
+        p = np.zeros((self.L, self.n_sets, self.n_q))
         _check(lib().qmc_get_fields(self.h, chain, _dp(p), p.size), self.h)
         return p
 

@@ -28,8 +28,10 @@ def qmc():
 def _eigh(qmc, A, precision):
     import torch
     b, n, _ = A.shape
-    At = torch.tensor(A, dtype=torch.complex128, device="cuda")
-    Ut = torch.full_like(At, complex(np.nan, np.nan))
+    # row-major device buffers (a numpy sum with a transposed operand may be
+    # laid out column-major, and full_like would keep that layout)
+    At = torch.tensor(np.ascontiguousarray(A), dtype=torch.complex128, device="cuda").contiguous()
+    Ut = torch.full((b, n, n), complex(np.nan, np.nan), dtype=torch.complex128, device="cuda")
     wt = torch.full((b, n), np.nan, dtype=torch.float64, device="cuda")
     qmc.qmc_eigh(n, b, At.data_ptr(), Ut.data_ptr(), wt.data_ptr(), precision)
     return Ut.cpu().numpy(), wt.cpu().numpy()
@@ -50,17 +52,18 @@ def _planted(rng, b, n, deltas):
     return np.array(out)
 
 
-def _check(A, U, w, tol):
+def _check(A, U, w, tol, what):
     n = A.shape[1]
     I = np.eye(n)
     un = np.abs(np.conj(np.swapaxes(U, 1, 2)) @ U - I).max((1, 2))
     rec = np.abs(U @ (w[:, :, None] * np.conj(np.swapaxes(U, 1, 2))) - A).max((1, 2))
     scale = np.abs(A).max((1, 2))
-    assert np.all(np.isfinite(U)) and np.all(np.isfinite(w))
-    assert un.max() < tol, un.max()
-    assert (rec / scale).max() < tol, (rec / scale).max()
+    assert np.all(np.isfinite(U)) and np.all(np.isfinite(w)), what
+    assert un.max() < tol, (what, "unitarity", un.max(), int(un.argmax()))
+    assert (rec / scale).max() < tol, (what, "reconstruction", (rec / scale).max(),
+                                       int((rec / scale).argmax()))
     ref = np.linalg.eigvalsh(A)
-    assert np.abs(np.sort(w, axis=1) - ref).max() < tol * scale.max()
+    assert np.abs(np.sort(w, axis=1) - ref).max() < tol * scale.max(), what
 
 
 DELTAS = [0.0, 1e-9, 1e-8, 1e-7, 3e-7, 1e-6, 3e-6, 1e-5, 1e-4]
@@ -72,7 +75,7 @@ def test_nearly_degenerate_pairs(qmc, n, precision):
     rng = np.random.default_rng(n * 10 + precision)
     A = _planted(rng, 2 * len(DELTAS), n, DELTAS)
     U, w = _eigh(qmc, A, precision)
-    _check(A, U, w, 5e-13 if n <= 64 else 2e-12)
+    _check(A, U, w, 5e-13 if n <= 64 else 2e-12, f"precision {precision}")
 
 
 @pytest.mark.parametrize("n", [36, 140])
@@ -84,4 +87,4 @@ def test_channel_like_random_matrices(qmc, n):
     A = (X + np.conj(np.swapaxes(X, 1, 2))) / 2
     for precision in ([0, 1, 2] if n <= 64 else [1, 2]):
         U, w = _eigh(qmc, A, precision)
-        _check(A, U, w, 5e-13 if n <= 64 else 2e-12)
+        _check(A, U, w, 5e-13 if n <= 64 else 2e-12, f"precision {precision}")
