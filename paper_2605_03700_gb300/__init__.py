@@ -7,10 +7,10 @@ from .qmc import (QMC_DRIFT_EXACT, QMC_DRIFT_FIRST, QMC_SLICE_SHARED, QMC_SLICE_
                   OBS_NAMES, Chain, Group, Net, QMCError,
                   lib, qmc_default_opts, qmc_launch_count, qmc_profile_gemm,
                   qmc_ratio_update, qmc_tau_int, qmc_gemm_tile, qmc_peak_fma, qmc_cgemm, qmc_profile_tensor,
-                  qmc_eigh)
+                  qmc_eigh, qmc_udv)
 
 __all__ = ["Chain", "Group", "Net", "QMCError", "QMC_TORUS", "QMC_SPHERE", "QMC_NOBS", "QMC_NTRACE",
            "QMC_DRIFT_EXACT", "QMC_DRIFT_FIRST", "QMC_SLICE_SHARED", "QMC_SLICE_INDEP",
            "OBS_NAMES", "lib", "qmc_default_opts", "qmc_tau_int", "qmc_launch_count",
            "qmc_profile_gemm", "qmc_ratio_update", "qmc_gemm_tile", "qmc_peak_fma", "qmc_cgemm", "qmc_profile_tensor",
-           "qmc_eigh"]
+           "qmc_eigh", "qmc_udv"]

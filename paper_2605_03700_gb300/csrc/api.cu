@@ -2283,6 +2283,24 @@ int qmc_ratio_update(int N, int batch, const double *G, const double *Delta, dou
     return code;
 }
 
+int qmc_udv(int n, int batch, const double *X, double *Q, double *D, double *V, void *stream)
+{
+    if (n < 1 || n > 280 || batch < 1 || !X || !Q || !D || !V) return QMC_ERR_ARG;
+    if (!linalg_init_current_device()) return QMC_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    void *scr = nullptr;
+    const size_t sb = qrp_scratch_bytes(n, batch);
+    if (cudaMalloc(&scr, sb ? sb : 1) != cudaSuccess) return QMC_ERR_OOM;
+    const long long nn = (long long)n * n;
+    int code = qrp_batched(s, n, (const cd *)X, nn, (cd *)Q, nn, D, n, (cd *)V, nn, batch, scr)
+                   ? QMC_ERR_ARG
+                   : QMC_OK;
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+        code = QMC_ERR_CUDA;
+    cudaFree(scr);
+    return code;
+}
+
 int qmc_eigh(int n, int batch, const double *A, double *U, double *w, int precision, void *stream)
 {
     if (n < 1 || batch < 1 || !A || !U || !w || precision < 0 || precision > 2) return QMC_ERR_ARG;

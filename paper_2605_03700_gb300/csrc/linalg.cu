@@ -1051,6 +1051,8 @@ __global__ void __launch_bounds__(256) k_lu_bc(int n, cd *A, long long sA, int *
     int *pv = (int *)(ud + n);                     // pivots of this CTA's panels, by global row
     __shared__ double red[2][8];
     __shared__ int nswr[8];
+    __shared__ cd s_pk, s_inv;
+    __shared__ int s_p, s_nsw;
     cd *Ab = A + (long long)b * sA;
     // local column lc <-> global column: panel q = (lc / LB) cs + rank
     auto gcol = [&](int lc) { return ((lc / LU_LB) * cs + rank) * LU_LB + lc % LU_LB; };
@@ -1059,58 +1061,76 @@ __global__ void __launch_bounds__(256) k_lu_bc(int n, cd *A, long long sA, int *
         const int i = e / wl, lc = e % wl, j = gcol(lc);
         Mb[i * ldw + lc] = j < n ? Ab[(long long)i * n + j] : cmk(0, 0);
     }
-    int nsw = 0;  // row exchanges of this CTA's panels (warp 0, lane 0)
+    if (tid == 0) s_nsw = 0;  // row exchanges of this CTA's panels
     cl.sync();
     for (int q = 0; q < np; ++q) {
         const int owner = q % cs, k0 = q * LU_LB, kb = min(LU_LB, n - k0);
         const int lq = (q / cs) * LU_LB;  // the panel's first local column in its owner
-        if (rank == owner && warp == 0) {
+        if (rank == owner) {
+            // warps over the panel's columns (warp w owns column lq + w),
+            // lanes over rows: on this part an FP64 warp instruction holds a
+            // sub-partition's FP64 pipe for tens of cycles, so the panel's
+            // rank-1 updates run on all four sub-partitions
             for (int kk = 0; kk < kb; ++kk) {
                 const int k = k0 + kk, lc = lq + kk;
-                double best = -1.0;
-                int bidx = k;
-                for (int i = k + lane; i < n; i += 32) {
-                    const double v = cabs2(Mb[i * ldw + lc]);
-                    if (v > best) {
-                        best = v;
-                        bidx = i;
+                if (warp == kk) {
+                    double best = -1.0;
+                    int bidx = k;
+                    for (int i = k + lane; i < n; i += 32) {
+                        const double v = cabs2(Mb[i * ldw + lc]);
+                        if (v > best) {
+                            best = v;
+                            bidx = i;
+                        }
+                    }
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+                        const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+                        if (ov > best || (ov == best && oi < bidx)) {
+                            best = ov;
+                            bidx = oi;
+                        }
+                    }
+                    if (lane == 0) {
+                        const int p = bidx;
+                        const cd pk = Mb[p * ldw + lc];  // u_kk: the pivot row's entry
+                        const double r = 1.0 / cabs2(pk);
+                        s_pk = pk;
+                        s_inv = cmk(pk.x * r, -pk.y * r);
+                        s_p = p;
+                        pv[k] = p;
+                        piv[(long long)b * spiv + k] = p;
+                        cl.map_shared_rank(ud, 0)[k] = pk;
+                        if (p != k) ++s_nsw;
                     }
                 }
-                for (int o = 16; o > 0; o >>= 1) {
-                    const double ov = __shfl_xor_sync(0xffffffffu, best, o);
-                    const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
-                    if (ov > best || (ov == best && oi < bidx)) {
-                        best = ov;
-                        bidx = oi;
-                    }
-                }
-                const int p = bidx;
-                if (p != k && lane < kb) {
-                    const cd t = Mb[k * ldw + lq + lane];
-                    Mb[k * ldw + lq + lane] = Mb[p * ldw + lq + lane];
-                    Mb[p * ldw + lq + lane] = t;
+                __syncthreads();
+                const int p = s_p;
+                // the row exchange in every panel column, by its warp
+                if (warp < kb && lane == 0 && p != k) {
+                    const cd t = Mb[k * ldw + lq + warp];
+                    Mb[k * ldw + lq + warp] = Mb[p * ldw + lq + warp];
+                    Mb[p * ldw + lq + warp] = t;
                 }
                 __syncwarp();
-                const cd pk = Mb[k * ldw + lc];
-                const double r = 1.0 / cabs2(pk);
-                const cd inv = cmk(pk.x * r, -pk.y * r);
-                for (int i = k + 1 + lane; i < n; i += 32) {
-                    const cd l = cmul(Mb[i * ldw + lc], inv);
-                    Mb[i * ldw + lc] = l;
-                    const cd ml = cmk(-l.x, -l.y);
-                    for (int j = kk + 1; j < kb; ++j) {
-                        cd v = Mb[i * ldw + lq + j];
-                        cfma(v, ml, Mb[k * ldw + lq + j]);
-                        Mb[i * ldw + lq + j] = v;
+                if (warp == kk) {
+                    const cd inv = s_inv;
+                    for (int i = k + 1 + lane; i < n; i += 32)
+                        Mb[i * ldw + lc] = cmul(Mb[i * ldw + lc], inv);
+                }
+                __syncthreads();
+                // later panel columns: a_ij -= l_ik a_kj (each warp its column;
+                // the next step's pivot warp reads only its own column)
+                if (warp > kk && warp < kb) {
+                    const int c = lq + warp;
+                    const cd ukj = Mb[k * ldw + c];
+                    for (int i = k + 1 + lane; i < n; i += 32) {
+                        const cd l = Mb[i * ldw + lc];
+                        cd v = Mb[i * ldw + c];
+                        cfma(v, cmk(-l.x, -l.y), ukj);
+                        Mb[i * ldw + c] = v;
                     }
                 }
-                if (lane == 0) {
-                    pv[k] = p;
-                    piv[(long long)b * spiv + k] = p;
-                    cl.map_shared_rank(ud, 0)[k] = pk;
-                    if (p != k) ++nsw;
-                }
-                __syncwarp();
             }
         }
         cl.sync();
@@ -1165,7 +1185,7 @@ __global__ void __launch_bounds__(256) k_lu_bc(int n, cd *A, long long sA, int *
         const int i = e / wl, lc = e % wl, j = gcol(lc);
         if (j < n) Ab[(long long)i * n + j] = Mb[i * ldw + lc];
     }
-    if (tid == 0) cl.map_shared_rank(nswr, 0)[rank] = nsw;
+    if (tid == 0) cl.map_shared_rank(nswr, 0)[rank] = s_nsw;
     cl.sync();
     // log det = sum_k log u_kk (+ i pi per row exchange) in rank 0, in the
     // one-CTA kernel's order: a term per thread, warp trees, warps in order
@@ -1548,6 +1568,305 @@ __global__ void __launch_bounds__(256) k_qrp(int n, int ld, const cd *X, long lo
     }
 }
 
+// --------------------------------------------- blocked cluster UDV (QR) ---
+// X = Q D V for the stabilisation stacks with the column order fixed before
+// the factorisation ("pre-pivoting": columns by descending 2-norm, ties by
+// index), then Householder QR without further pivoting, X P = Q R,
+// D = |diag R|, V = D^-1 R P^T (Bai, Lee, Li and Xu, Linear Algebra Appl.
+// 435 (2011): for the graded products of the stabilisation this ordering is
+// as accurate as column pivoting, and the factorisation blocks).  Panels of
+// QR_B columns of the permuted matrix, cyclic over a cluster of cs CTAs
+// (panel q in CTA q mod cs), each CTA keeping its columns of A and of Q in
+// shared memory.  Panel q: the owner's warps over the panel's columns run
+// the Householder steps (warp kk forms v_k and alpha, the later columns'
+// warps apply H_k), then the compact-WY factor T (H_k0 .. H_k0+kb-1 =
+// I - V T V^H) from the inner products of the panel's vectors; one cluster
+// barrier; every CTA copies V and T (distributed shared memory) and updates
+// its columns right of the panel, A <- A - V (T^H (V^H A)).  Q is formed
+// afterwards by backward accumulation, Q <- (I - V_q T_q V_q^H) Q from the
+// last panel to the first, on each CTA's columns of Q (read-only use of the
+// owners' vectors, which no later step changes).
+#define QR_B 8
+__global__ void __launch_bounds__(256) k_qr_bc(int n, const cd *X, long long sX, cd *Q,
+                                               long long sQ, double *D, long long sD, cd *V,
+                                               long long sV)
+{
+    cgr::cluster_group cl = cgr::this_cluster();
+    const int cs = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    const int b = blockIdx.y, tid = threadIdx.x, nt = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int np = (n + QR_B - 1) / QR_B;
+    const int mine = (np - rank + cs - 1) / cs;
+    const int W = ((np + cs - 1) / cs) * QR_B, ldw = W + 1, wl = mine * QR_B;
+    const int mmax = (np + cs - 1) / cs;  // panels per CTA at most
+    extern __shared__ __align__(16) unsigned char sm_qb_raw[];
+    cd *A = (cd *)sm_qb_raw;                    // n x W (row stride ldw): R and the vectors
+    cd *Qm = A + (size_t)n * ldw;               // n x W: this CTA's columns of Q
+    cd *Vp = Qm + (size_t)n * ldw;              // n x QR_B: the current panel's V
+    cd *Wt = Vp + (size_t)n * QR_B;             // QR_B x W: V^H A (or V^H Q)
+    cd *Wt2 = Wt + (size_t)QR_B * W;            // QR_B x W: T^H W (or T W)
+    cd *Tp = Wt2 + (size_t)QR_B * W;            // QR_B x QR_B: the current panel's T
+    cd *Tall = Tp + QR_B * QR_B;                // mmax x QR_B x QR_B: T of own panels
+    cd *v0a = Tall + (size_t)mmax * QR_B * QR_B;  // v_k[k] per column k (owner's)
+    cd *Yp = v0a + n;                           // QR_B x QR_B inner products v_l^H v_j
+    double *fa = (double *)(Yp + QR_B * QR_B);  // 2 / |v_k|^2 per column k (owner's)
+    double *nrm = fa + n;                       // column norms of X, then |R_kk| (all rows)
+    int *perm = (int *)(nrm + n);               // permuted column -> column of X
+    const cd *Xb = X + (long long)b * sX;
+    auto gcol = [&](int lc) { return ((lc / QR_B) * cs + rank) * QR_B + lc % QR_B; };
+
+    // pre-pivoting: 2-norms of X's columns (one thread per column, rows in
+    // order) and their descending order; every CTA computes the same
+    for (int j = tid; j < n; j += nt) {
+        double s2 = 0.0;
+        for (int i = 0; i < n; ++i) s2 += cabs2(Xb[(long long)i * n + j]);
+        nrm[j] = s2;
+    }
+    __syncthreads();
+    for (int j = tid; j < n; j += nt) {
+        // non-negative doubles order like their bit patterns; NaN goes last
+        const long long kj = isnan(nrm[j]) ? -1LL : __double_as_longlong(nrm[j]);
+        int r = 0;
+        for (int i = 0; i < n; ++i) {
+            const long long ki = isnan(nrm[i]) ? -1LL : __double_as_longlong(nrm[i]);
+            r += (ki > kj || (ki == kj && i < j));
+        }
+        perm[r] = j;
+    }
+    __syncthreads();
+    for (int e = tid; e < n * wl; e += nt) {
+        const int i = e / wl, lc = e % wl, pc = gcol(lc);
+        A[i * ldw + lc] = pc < n ? Xb[(long long)i * n + perm[pc]] : cmk(0, 0);
+        Qm[i * ldw + lc] = cmk(pc < n && i == pc ? 1.0 : 0.0, 0.0);
+    }
+    cl.sync();
+    for (int q = 0; q < np; ++q) {
+        const int owner = q % cs, k0 = q * QR_B, kb = min(QR_B, n - k0);
+        const int lq = (q / cs) * QR_B;
+        if (rank == owner) {
+            for (int kk = 0; kk < kb; ++kk) {
+                const int k = k0 + kk, lc = lq + kk;
+                if (warp == kk) {
+                    // v = x - alpha e_k, alpha = -e^{i arg x_k} |x|; the tail
+                    // norm summed directly
+                    double tail = 0.0;
+                    for (int i = k + 1 + lane; i < n; i += 32) tail += cabs2(A[i * ldw + lc]);
+                    for (int o = 16; o > 0; o >>= 1) tail += __shfl_xor_sync(0xffffffffu, tail, o);
+                    if (lane == 0) {
+                        const cd x0 = A[k * ldw + lc];
+                        const double ax0 = sqrt(cabs2(x0));
+                        const double xn = sqrt(tail + ax0 * ax0);
+                        const double rax = ax0 > 0 ? 1.0 / ax0 : 0.0;
+                        const cd ph = ax0 > 0 ? cmk(x0.x * rax, x0.y * rax) : cmk(1, 0);
+                        const cd alpha = cmk(-ph.x * xn, -ph.y * xn);
+                        const cd v0 = csub(x0, alpha);
+                        const double vn = tail + cabs2(v0);
+                        v0a[k] = v0;
+                        fa[k] = (xn == 0.0 || vn == 0.0) ? 0.0 : 2.0 / vn;
+                        A[k * ldw + lc] = alpha;
+                    }
+                }
+                __syncthreads();
+                // H_k on the panel's later columns, each by its warp
+                if (warp > kk && warp < kb && fa[k] != 0.0) {
+                    const int c = lq + warp;
+                    const cd v0 = v0a[k];
+                    cd sacc = lane == 0 ? cmul(cconj(v0), A[k * ldw + c]) : cmk(0, 0);
+                    for (int i = k + 1 + lane; i < n; i += 32)
+                        cfma(sacc, cconj(A[i * ldw + lc]), A[i * ldw + c]);
+                    for (int o = 16; o > 0; o >>= 1) {
+                        sacc.x += __shfl_xor_sync(0xffffffffu, sacc.x, o);
+                        sacc.y += __shfl_xor_sync(0xffffffffu, sacc.y, o);
+                    }
+                    const cd sm = cscale(sacc, -fa[k]);
+                    if (lane == 0) {
+                        cd a = A[k * ldw + c];
+                        cfma(a, sm, v0);
+                        A[k * ldw + c] = a;
+                    }
+                    for (int i = k + 1 + lane; i < n; i += 32) {
+                        cd a = A[i * ldw + c];
+                        cfma(a, sm, A[i * ldw + lc]);
+                        A[i * ldw + c] = a;
+                    }
+                }
+            }
+            __syncthreads();
+            // T: T_jj = f_j, T[0:j, j] = -f_j T[0:j, 0:j] y[0:j, j] with
+            // y_lj = v_l^H v_j (rows >= k0 + j, where v_j starts)
+            for (int pr = warp; pr < kb * kb; pr += nt / 32) {
+                const int l = pr / kb, j = pr % kb;
+                if (l >= j) continue;
+                const int kj = k0 + j;
+                cd y = lane == 0 ? cmul(cconj(A[kj * ldw + lq + l]), v0a[kj]) : cmk(0, 0);
+                for (int i = kj + 1 + lane; i < n; i += 32)
+                    cfma(y, cconj(A[i * ldw + lq + l]), A[i * ldw + lq + j]);
+                for (int o = 16; o > 0; o >>= 1) {
+                    y.x += __shfl_xor_sync(0xffffffffu, y.x, o);
+                    y.y += __shfl_xor_sync(0xffffffffu, y.y, o);
+                }
+                if (lane == 0) Yp[l * QR_B + j] = y;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                cd *T = Tall + (size_t)(q / cs) * QR_B * QR_B;
+                for (int e = 0; e < QR_B * QR_B; ++e) T[e] = cmk(0, 0);
+                for (int j = 0; j < kb; ++j) {
+                    const double fj = fa[k0 + j];
+                    T[j * QR_B + j] = cmk(fj, 0);
+                    for (int m = 0; m < j; ++m) {
+                        cd acc = cmk(0, 0);
+                        for (int l = m; l < j; ++l) cfma(acc, T[m * QR_B + l], Yp[l * QR_B + j]);
+                        T[m * QR_B + j] = cscale(acc, -fj);
+                    }
+                }
+            }
+        }
+        cl.sync();
+        // V and T of panel q from its owner (V_ij = 0 above the vector's start)
+        {
+            const cd *oA = cl.map_shared_rank(A, owner);
+            const cd *ov0 = cl.map_shared_rank(v0a, owner);
+            const cd *oT = cl.map_shared_rank(Tall, owner) + (size_t)(q / cs) * QR_B * QR_B;
+            for (int e = tid; e < (n - k0) * QR_B; e += nt) {
+                const int i = k0 + e / QR_B, m = e % QR_B;
+                cd v = cmk(0, 0);
+                if (m < kb && i >= k0 + m) v = i == k0 + m ? ov0[i] : oA[i * ldw + lq + m];
+                Vp[i * QR_B + m] = v;
+            }
+            for (int e = tid; e < QR_B * QR_B; e += nt) Tp[e] = oT[e];
+        }
+        __syncthreads();
+        // this CTA's columns right of the panel: A <- A - V (T^H (V^H A))
+        const int lfirst = (q / cs + (rank <= owner)) * QR_B, ncol = wl - lfirst;
+        if (ncol > 0) {
+            for (int e = tid; e < kb * ncol; e += nt) {
+                const int m = e / ncol, c = lfirst + e % ncol;
+                cd acc = cmk(0, 0);
+                for (int i = k0 + m; i < n; ++i) cfma(acc, cconj(Vp[i * QR_B + m]), A[i * ldw + c]);
+                Wt[m * W + c - lfirst] = acc;
+            }
+            __syncthreads();
+            for (int e = tid; e < kb * ncol; e += nt) {
+                const int m = e / ncol, c = e % ncol;
+                cd acc = cmk(0, 0);
+                for (int l = 0; l <= m; ++l) cfma(acc, cconj(Tp[l * QR_B + m]), Wt[l * W + c]);
+                Wt2[m * W + c] = acc;
+            }
+            __syncthreads();
+            for (int e = tid; e < (n - k0) * ncol; e += nt) {
+                const int i = k0 + e / ncol, c = e % ncol;
+                cd a = A[i * ldw + lfirst + c];
+                for (int m = 0; m < kb; ++m) {
+                    const cd v = Vp[i * QR_B + m];
+                    cfma(a, cmk(-v.x, -v.y), Wt2[m * W + c]);
+                }
+                A[i * ldw + lfirst + c] = a;
+            }
+        }
+        __syncthreads();
+    }
+    // Q = (I - V_0 T_0 V_0^H) ... (I - V_last T_last V_last^H), applied to
+    // this CTA's identity columns from the last panel to the first; columns
+    // j < k0 are still e_j there and need no update
+    for (int q = np - 1; q >= 0; --q) {
+        const int owner = q % cs, k0 = q * QR_B, kb = min(QR_B, n - k0);
+        const int lq = (q / cs) * QR_B;
+        {
+            const cd *oA = cl.map_shared_rank(A, owner);
+            const cd *ov0 = cl.map_shared_rank(v0a, owner);
+            const cd *oT = cl.map_shared_rank(Tall, owner) + (size_t)(q / cs) * QR_B * QR_B;
+            for (int e = tid; e < (n - k0) * QR_B; e += nt) {
+                const int i = k0 + e / QR_B, m = e % QR_B;
+                cd v = cmk(0, 0);
+                if (m < kb && i >= k0 + m) v = i == k0 + m ? ov0[i] : oA[i * ldw + lq + m];
+                Vp[i * QR_B + m] = v;
+            }
+            for (int e = tid; e < QR_B * QR_B; e += nt) Tp[e] = oT[e];
+        }
+        __syncthreads();
+        for (int e = tid; e < kb * wl; e += nt) {
+            const int m = e / wl, c = e % wl;
+            cd acc = cmk(0, 0);
+            if (gcol(c) >= k0)
+                for (int i = k0 + m; i < n; ++i)
+                    cfma(acc, cconj(Vp[i * QR_B + m]), Qm[i * ldw + c]);
+            Wt[m * W + c] = acc;
+        }
+        __syncthreads();
+        for (int e = tid; e < kb * wl; e += nt) {
+            const int m = e / wl, c = e % wl;
+            cd acc = cmk(0, 0);
+            for (int l = m; l < kb; ++l) cfma(acc, Tp[m * QR_B + l], Wt[l * W + c]);
+            Wt2[m * W + c] = acc;
+        }
+        __syncthreads();
+        for (int e = tid; e < (n - k0) * wl; e += nt) {
+            const int i = k0 + e / wl, c = e % wl;
+            if (gcol(c) < k0) continue;
+            cd a = Qm[i * ldw + c];
+            for (int m = 0; m < kb; ++m) {
+                const cd v = Vp[i * QR_B + m];
+                cfma(a, cmk(-v.x, -v.y), Wt2[m * W + c]);
+            }
+            Qm[i * ldw + c] = a;
+        }
+        __syncthreads();
+    }
+    // D_k = |R_kk| from the owners of the diagonal into every CTA, then
+    // V = D^-1 R P^T and Q from each CTA's columns
+    for (int lc = tid; lc < wl; lc += nt) {
+        const int pc = gcol(lc);
+        if (pc >= n) continue;
+        const double dk = sqrt(cabs2(A[pc * ldw + lc]));
+        for (int r = 0; r < cs; ++r) cl.map_shared_rank(nrm, r)[pc] = dk;
+    }
+    cl.sync();
+    double *Db = D + (long long)b * sD;
+    cd *Vb = V + (long long)b * sV;
+    cd *Qg = Q + (long long)b * sQ;
+    if (rank == 0)
+        for (int i = tid; i < n; i += nt) Db[i] = nrm[i];
+    for (int e = tid; e < n * wl; e += nt) {
+        const int i = e / wl, lc = e % wl, pc = gcol(lc);
+        if (pc >= n) continue;
+        const cd r = i <= pc ? A[i * ldw + lc] : cmk(0, 0);
+        Vb[(long long)i * n + perm[pc]] = cscale(r, 1.0 / nrm[i]);
+        Qg[(long long)i * n + pc] = Qm[i * ldw + lc];
+    }
+    cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+static size_t qr_bc_smem(int n, int cs)
+{
+    const int np = (n + QR_B - 1) / QR_B, mmax = (np + cs - 1) / cs, W = mmax * QR_B;
+    const size_t cdn = 2 * (size_t)n * (W + 1) + (size_t)n * QR_B + 2 * (size_t)QR_B * W +
+                       QR_B * QR_B + (size_t)mmax * QR_B * QR_B + n + QR_B * QR_B;
+    return cdn * sizeof(cd) + 2 * (size_t)n * sizeof(double) + (size_t)n * sizeof(int);
+}
+
+static int qr_bc_launch(cudaStream_t st, int n, const cd *X, long long sX, cd *Q, long long sQ,
+                        double *D, long long sD, cd *V, long long sV, int batch, int cs)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs, batch);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = qr_bc_smem(n, cs);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_qr_bc, n, X, sX, Q, sQ, D, sD, V, sV) == cudaSuccess ? 0 : -1;
+}
+
+// CTAs per matrix of the blocked UDV (QMC_QR_CS=1 keeps the column-pivoted
+// one-CTA kernel; 2, 4, 8), read once
+static int g_qr_cs = 4;
+
 size_t qrp_scratch_bytes(int n, int batch)
 {
     const size_t vec = (size_t)batch * n * (2 * sizeof(cd) + sizeof(double) + sizeof(int));
@@ -1560,6 +1879,16 @@ size_t qrp_scratch_bytes(int n, int batch)
 int qrp_batched(cudaStream_t st, int n, const cd *X, long long sX, cd *Q, long long sQ, double *D,
                 long long sD, cd *V, long long sV, int batch, void *vscr)
 {
+    // the blocked pre-pivoted kernel over a cluster where its columns fit
+    int cs = g_qr_cs;
+    while (cs > 1 && cs < 8 && qr_bc_smem(n, cs) > SMEM_MAX) cs *= 2;
+    if (cs > 1 && qr_bc_smem(n, cs) <= SMEM_MAX) {
+        if (qr_bc_launch(st, n, X, sX, Q, sQ, D, sD, V, sV, batch, cs) == 0) {
+            QMC_COUNT(1);
+            return 0;
+        }
+        cudaGetLastError();  // not launched: the column-pivoted kernel below
+    }
     const size_t vec = 3 * (size_t)n * sizeof(cd) + (size_t)n * sizeof(double) +
                        (size_t)n * sizeof(int) + 16;
     const size_t base = (size_t)n * (n + 1) * sizeof(cd) + vec;
@@ -1611,6 +1940,10 @@ bool linalg_init()
         const int v = atoi(e);
         if (v == 1 || v == 2 || v == 4 || v == 8) g_lu_cs = v;
     }
+    if (const char *e = getenv("QMC_QR_CS")) {
+        const int v = atoi(e);
+        if (v == 1 || v == 2 || v == 4 || v == 8) g_qr_cs = v;
+    }
     int dev = 0, optin = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) ==
@@ -1622,6 +1955,7 @@ bool linalg_init()
     ok &= set_dyn_smem((const void *)k_lu, SMEM_MAX);
     ok &= set_dyn_smem((const void *)k_rdiv_ch, SMEM_MAX);
     ok &= set_dyn_smem((const void *)k_lu_bc, SMEM_MAX);
+    ok &= set_dyn_smem((const void *)k_qr_bc, SMEM_MAX);
     ok &= set_dyn_smem((const void *)k_eigh_big<float>, SMEM_MAX);
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, k_qrp) == cudaSuccess && fa.sharedSizeBytes < 1024)

@@ -154,6 +154,7 @@ def lib():
         L.qmc_cgemm.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_int, vp, C.c_int, vp, vp,
                                 C.c_int, C.c_int, C.c_int, vp]
         L.qmc_eigh.argtypes = [C.c_int, C.c_int, vp, vp, vp, C.c_int, vp]
+        L.qmc_udv.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -247,6 +248,12 @@ def qmc_eigh(n, batch, A_ptr, U_ptr, w_ptr, precision=1, stream=0):
     2 = refinement products on the tensor cores."""
     _check(lib().qmc_eigh(n, batch, C.c_void_p(A_ptr), C.c_void_p(U_ptr), C.c_void_p(w_ptr),
                           precision, C.c_void_p(stream) if stream else None))
+
+
+def qmc_udv(n, batch, X_ptr, Q_ptr, D_ptr, V_ptr, stream=0):
+    """X = Q diag(D) V on device pointers (qmc_udv)."""
+    _check(lib().qmc_udv(n, batch, C.c_void_p(X_ptr), C.c_void_p(Q_ptr), C.c_void_p(D_ptr),
+                         C.c_void_p(V_ptr), C.c_void_p(stream) if stream else None))
 
 
 def qmc_ratio_update(N, batch, G_ptr, Delta_ptr, Gp_ptr, logdet_ptr, stream=0):

@@ -93,6 +93,9 @@ def test_new_entry_points_reject_invalid_arguments_before_device_work(lib):
     assert L.qmc_eigh(141, 1, one, one, one, 1, None) == -1
     assert L.qmc_eigh(65, 1, one, one, one, 0, None) == -1
     assert L.qmc_eigh(36, 1, one, one, one, 3, None) == -1
+    # UDV: null buffers, n beyond 280
+    assert L.qmc_udv(72, 1, None, None, None, None, None) == -1
+    assert L.qmc_udv(281, 1, one, one, one, one, None) == -1
     # sphere beyond 60 orbitals; torus beyond 140, or beyond 60 in FP64
     o = qmc.qmc_default_opts()
     assert L.qmc_create(C.byref(h), 1, 60, 1.0, 0.1, 1.0, 0.0, 0, C.byref(o)) == -1
