@@ -907,11 +907,19 @@ int eigh_mixed(cudaStream_t st, int n, int batch, const cd *A, cd *U, double *w,
         QMC_COUNT(1);
         return 0;
     }
-    // FP64 Jacobi from V = X: returns at once when S is diagonal to the
-    // accuracy of its products (off-diagonal Frobenius norm below 1e-13 of the
-    // total with FP64 products, whose rounding floor is near 1e-14; 1e-12
-    // with tensor-core products, whose floor is a few 1e-14), and resolves
-    // the rare clusters the refinement leaves
+    // the pairs the refinement left coupled first, by 2 x 2 rotations of
+    // only those pairs (a full FP64 Jacobi sweep over all pairs took ~0.5 ms
+    // per batch whenever one matrix of the batch had one), then the FP64
+    // Jacobi from V = U: it returns at once when S is diagonal to the
+    // accuracy of its products (off-diagonal Frobenius norm below 1e-13 of
+    // the total with FP64 products, whose rounding floor is near 1e-14;
+    // 1e-12 with tensor-core products, whose floor is a few 1e-14)
+    if (wk.err) {
+        k_resolve_pairs<<<batch, 256, 0, st>>>(n, wk.S, X, U, w, wk.err);
+        QMC_COUNT(1);
+        return eigh_batched(st, TY_C64, n, wk.S, n2, U, n2, w, n, batch, U, n2,
+                            oz ? 1e-24 : 1e-26);
+    }
     return eigh_batched(st, TY_C64, n, wk.S, n2, U, n2, w, n, batch, X, n2,
                         oz ? 1e-24 : 1e-26);
 }
