@@ -102,7 +102,12 @@ typedef struct {
                               wraps, M, the eigenvector refinement) on tcgen05 from seven
                               exact bfloat16 digits per operand with FP32 accumulation
                               (FP64-class, ~1e-14 of |A||B|) and the drift transforms
-                              from three digits (FP32-class); LU and log det, G M^-1, the
+                              from three digits (FP32-class), for every product of at
+                              least 4e7 complex multiply-adds (M N K x batch: the
+                              batched prior-move proposals, N >= 280, the large
+                              refinement batches; smaller ones run on the CUDA cores as
+                              in 1, where the tensor path's split and latency cost more);
+                              LU and log det, G M^-1, the
                               QR/UDV restabilisation and the measurements stay FP64 on
                               the CUDA cores */
     double eps0;           /* initial Langevin step (default 0.5) */

@@ -245,11 +245,29 @@ static int launch_gemm(cudaStream_t st, const GemmP &p, int batch, int tile)
     return 0;
 }
 
+// Smallest product (M N K batch complex multiply-adds) sent to the tensor
+// cores when the caller allows them: below it the digit split, the 128-row
+// instruction shape and the launch latency cost more than the CUDA-core
+// kernel (measured at N = 72: 8 products take ~35 us as digit products and
+// ~27 us in FP64; 720 of them ~10x less on the tensor cores).
+// QMC_OZ_MIN_WORK overrides (read once).
+static double oz_min_work()
+{
+    static double v = [] {
+        const char *e = getenv("QMC_OZ_MIN_WORK");
+        return e ? atof(e) : 4e7;
+    }();
+    return v;
+}
+
 int zgemm(cudaStream_t st, const GemmP &p, int batch)
 {
-    // tensor-core digit products where the caller asked for them and the
-    // work space fits; the CUDA-core kernel otherwise
-    if (p.oz && oz_gemm(st, p, batch, *p.oz) == 0) return 0;
+    // tensor-core digit products where the caller asked for them, the
+    // product is large enough and the work space fits; the CUDA-core kernel
+    // otherwise
+    if (p.oz && (double)p.M * p.N * p.K * batch >= oz_min_work() &&
+        oz_gemm(st, p, batch, *p.oz) == 0)
+        return 0;
     const int tile = tile_for(p.N, p.rc);
     int r;
     if (g_gprof.on && p.rc == TY_C64) {  // the FP64-pipe roofline: FP64 products only
@@ -771,6 +789,7 @@ __global__ void __launch_bounds__(256) k_resolve_pairs(int n, cd *S, const cd *X
     __shared__ double red[8], thr;
     __shared__ cd jm[4];
     const int b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31;
     const long long nn = (long long)n * n;
     S += b * nn;
     X += b * nn;
@@ -787,22 +806,40 @@ __global__ void __launch_bounds__(256) k_resolve_pairs(int n, cd *S, const cd *X
         for (int k = 0; k < nt / 32; ++k) m = fmax(m, red[k]);
         thr = 1e-12 * m + 1e-300;
     }
-    // passes: list the pairs above the threshold (a rotation can couple a
-    // pair that was below it), rotate each once; stop when none is listed
+    // passes: list the pairs above the threshold in row-major order (a
+    // rotation can couple a pair that was below it), rotate each once; stop
+    // when none is listed.  The list is compacted in order (ballots and a
+    // running base), so the rotations and their rounding are deterministic.
+    __shared__ int wcnt[8];
     for (int pass = 0;; ++pass) {
         if (tid == 0) npair = 0;
         __syncthreads();
-        for (long long e = tid; e < nn; e += nt) {
-            const int i = (int)(e / n), j = (int)(e % n);
-            if (i < j && cabs2(S[e]) > thr * thr) {
-                const int k = atomicAdd(&npair, 1);
+        for (long long e0 = 0; e0 < nn; e0 += nt) {
+            const long long e = e0 + tid;
+            bool hit = false;
+            int i = 0, j = 0;
+            if (e < nn) {
+                i = (int)(e / n);
+                j = (int)(e % n);
+                hit = i < j && cabs2(S[e]) > thr * thr;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, hit);
+            if (lane == 0) wcnt[warp] = __popc(bal);
+            __syncthreads();
+            int base = npair;
+            for (int w = 0; w < warp; ++w) base += wcnt[w];
+            if (hit) {
+                const int k = base + __popc(bal & ((1u << lane) - 1u));
                 if (k < RP_MAX) {
                     pp[k] = i;
                     pq[k] = j;
                 }
             }
+            __syncthreads();
+            if (tid == 0)
+                for (int w = 0; w < nt / 32; ++w) npair += wcnt[w];
+            __syncthreads();
         }
-        __syncthreads();
         const int np = min(npair, RP_MAX);
         if (np == 0) break;
         if (pass == 16) {
