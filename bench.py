@@ -8,9 +8,11 @@ per slice), beta = 36, dtau = 0.1 (L = 360 slices), eight chains at couplings
 u = linspace(0.5, 2.0, 8), seeds 0..7, restabilisation every 10 slices.
 
 Two arms run in one invocation on the same GPU:
-  * the headline path (default --mode prior): mixed precision with
-    whole-slice sweeps around the Gaussian prior (accepted by the exact
-    determinant ratio) and a Langevin sweep every 4th step;
+  * the headline path (default --mode prior --precision 2): mixed precision
+    with whole-slice sweeps around the Gaussian prior (accepted by the exact
+    determinant ratio; their proposals' propagators computed ahead in
+    batches, with the batched products on the tensor cores) and a Langevin
+    sweep every 4th step;
   * the plain FP64 Langevin sweep (--precision 0 --mode plain), the
     comparison the metric names.
 Each arm: W warm-up sweeps, K timed sweeps (CUDA events on the library's
@@ -739,10 +741,12 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=20, help="timed sweeps of the plain arm")
     ap.add_argument("--plain-tau-sweeps", type=int, default=120,
                     help="records per chain for tau_int of the plain FP64 arm")
-    ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2],
+    ap.add_argument("--precision", type=int, default=2, choices=[0, 1, 2],
                     help="0: FP64 everywhere; 1: mixed (FP32 eigensolver bulk + FP64 "
                          "refinement, FP32 drift transforms; FP64 propagators, ratios, updates); "
-                         "2: mixed with the dense products on the tcgen05 tensor cores")
+                         "2 (default): as 1, with the large dense products (the batched "
+                         "prior-move proposals) on the tcgen05 tensor cores from FP64-exact "
+                         "bfloat16 digits")
     ap.add_argument("--mode", default="prior", choices=["prior", "learned", "plain"],
                     help="prior: whole-slice moves around the Gaussian prior with a Langevin "
                          "sweep every 4th step; learned: the same schedule with the network's "

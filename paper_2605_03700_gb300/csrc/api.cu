@@ -673,6 +673,11 @@ static int prior_stage_ensure(qmc_ctx *ctx)
     const size_t budget = 2ull << 30;
     const long long fit = (long long)(budget / ((size_t)nb * prior_entry_bytes(ctx)));
     int C = (L + 3) / 4;
+    // QMC_PRIOR_CHUNK=<slices> sets the chunk length (still within the budget)
+    if (const char *e = getenv("QMC_PRIOR_CHUNK")) {
+        const int v = atoi(e);
+        if (v >= 1) C = std::min(v, L);
+    }
     if (C > fit) C = (int)std::max(1LL, fit);
     // batched products index the 4 channel matrices of an entry in grid z
     const int ns = ctx->ns;

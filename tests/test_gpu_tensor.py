@@ -58,7 +58,8 @@ def _rand(rng, *shape):
 
 
 @pytest.mark.parametrize("M,N,K,batch", [(72, 72, 72, 3), (36, 36, 36, 5), (5, 7, 9, 2),
-                                         (120, 120, 120, 2), (130, 40, 72, 2), (280, 56, 16, 1)])
+                                         (120, 120, 120, 2), (130, 40, 72, 2), (280, 56, 16, 1),
+                                         (72, 72, 72, 720)])
 @pytest.mark.parametrize("opA,opB", [(0, 0), (2, 0), (0, 2)])
 def test_products_match_fp64(qmc, M, N, K, batch, opA, opB):
     rng = np.random.default_rng(M * 1000 + N * 10 + K + 7 * opA + 3 * opB)
