@@ -496,17 +496,23 @@ int qmc_profile_tensor(double *total_ms, long long *launches, double *flops, dou
 int qmc_cgemm(int M, int N, int K, int batch, const double *A, int opA, const double *B, int opB,
               const double *d, double *C, int negate, int add_identity, int digits, void *stream);
 
-/* X = Q diag(D) V for `batch` complex n x n matrices, the decomposition of
- * the stabilisation stacks (Methods, Eq. green_function_methods: the UDV
- * form of the slice products): Q unitary, D > 0, V = D^-1 R P^T with
- * X P = Q R.  For n <= 128 the columns are ordered by descending 2-norm once
- * (ties by index) and factored by blocked Householder QR over a cluster of
- * CTAs; larger n, or QMC_QR_CS=1 in the environment, use Householder QR
- * with column pivoting on one CTA per matrix.  X, Q, V: device, batch x n x n
- * complex128 row-major (interleaved re, im); D: device, batch x n doubles.
+/* X diag(e^c) = Q diag(e^d) V for `batch` complex n x n matrices whose
+ * columns carry log scales c (or none): the decomposition of the
+ * stabilisation stacks (Methods, Eq. green_function_methods: the UDV form of
+ * the slice products), with D in log form d so that the products' singular
+ * values may leave FP64's exponent range (they reach e^{~10^4} on the
+ * 60-orbital sphere at beta = 40).  Q unitary, V = D^-1 R P^T with
+ * X diag(e^c) P = Q R, formed without forming X diag(e^c).  For n <= 128 the
+ * columns are ordered by log |x_j| + c_j once (ties by index) and factored
+ * by blocked Householder QR over a cluster of CTAs; larger n, or
+ * QMC_QR_CS=1 in the environment, use Householder QR with column pivoting
+ * on the same scaled norms on one CTA per matrix.  X, Q, V: device,
+ * batch x n x n complex128 row-major (interleaved re, im); log_scale:
+ * device, batch x n doubles, or NULL; log_D: device, batch x n doubles.
  * n <= 280.  Allocates and frees its own scratch and synchronises `stream`.
  * QMC_ERR_ARG for bad sizes, QMC_ERR_OOM, QMC_ERR_CUDA. */
-int qmc_udv(int n, int batch, const double *X, double *Q, double *D, double *V, void *stream);
+int qmc_udv(int n, int batch, const double *X, const double *log_scale, double *Q, double *log_D,
+            double *V, void *stream);
 
 /* Eigenpairs A = U diag(w) U^H of `batch` Hermitian n x n matrices, the
  * solver behind every slice propagator (Methods, Eq.

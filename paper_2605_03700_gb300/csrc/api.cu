@@ -148,7 +148,7 @@ struct qmc_ctx {
     cd *NSx, *NSy, *NSz, *NSs, *NSr, *NSe;  // eigensolver work, [nb][4][n^2]
     // scratch, FP64
     cd *tq, *X1, *X2, *M, *Gp, *Gs, *Qt, *Vt, *Eye, *dinvR, *dinvL, *logdet, *ax;
-    double *phip, *grad, *gradp, *Dt, *ones, *stats, *eps, *eps_used, *series, *trace;
+    double *phip, *grad, *gradp, *Dt, *stats, *eps, *eps_used, *series, *trace;
     int *piv, *flag, *errf, *always;
     long long *trace_n;
 
@@ -440,21 +440,24 @@ static int build_left_stack(qmc_ctx *ctx)
                            cudaMemcpyDeviceToDevice, s));
         CK(cudaMemcpyAsync(ctx->LW + c * Ls + k * NN, ctx->Eye, sizeof(cd) * NN,
                            cudaMemcpyDeviceToDevice, s));
-        CK(cudaMemcpyAsync(ctx->LD + c * LDs + k * N, ctx->ones, sizeof(double) * N,
-                           cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemsetAsync(ctx->LD + c * LDs + k * N, 0, sizeof(double) * N, s));  // log 1
     }
     for (k = nsp - 1; k >= 0; --k) {
         int hi = ctx->sp[k], lo = k > 0 ? ctx->sp[k - 1] : 0;
         int dst = k > 0 ? k - 1 : nsp;
-        launch_scale_cols(s, nb, N, ctx->LQ + k * NN, Ls, ctx->LD + k * N, LDs, ctx->X1, NN);
+        // B^H .. B^H Q with the columns' log scales D carried into the UDV
+        // (X diag(e^D) is never formed: its entries leave FP64's range at
+        // large beta times coupling)
         cd *a = ctx->X1, *b = ctx->X2;
-        for (int t = hi; t > lo; --t) {
+        gemm_sq(s, N, nb, TY_C64, op64(ctx->B + (long long)(hi - 1) * NN, BL), 2,
+                op64(ctx->LQ + k * NN, Ls), 0, op64(a, NN));
+        for (int t = hi - 1; t > lo; --t) {
             gemm_sq(s, N, nb, TY_C64, op64(ctx->B + (long long)(t - 1) * NN, BL), 2, op64(a, NN), 0,
                     op64(b, NN));
             std::swap(a, b);
         }
-        if (qrp_batched(s, N, a, NN, ctx->LQ + dst * NN, Ls, ctx->LD + dst * N, LDs, ctx->Vt, NN,
-                        nb, ctx->qscr))
+        if (qrp_batched(s, N, a, NN, ctx->LD + k * N, LDs, ctx->LQ + dst * NN, Ls,
+                        ctx->LD + dst * N, LDs, ctx->Vt, NN, nb, ctx->qscr))
             return QMC_ERR_ARG;
         gemm_sq(s, N, nb, TY_C64, op64(ctx->Vt, NN), 0, op64(ctx->LW + k * NN, Ls), 0,
                 op64(ctx->LW + dst * NN, Ls));
@@ -468,8 +471,7 @@ static void reset_right_stack(qmc_ctx *ctx)
                     ctx->st);
     cudaMemcpyAsync(ctx->RW, ctx->Eye, sizeof(cd) * ctx->NN * ctx->nb, cudaMemcpyDeviceToDevice,
                     ctx->st);
-    cudaMemcpyAsync(ctx->RD, ctx->ones, sizeof(double) * ctx->N * ctx->nb,
-                    cudaMemcpyDeviceToDevice, ctx->st);
+    cudaMemsetAsync(ctx->RD, 0, sizeof(double) * ctx->N * ctx->nb, ctx->st);  // log 1
 }
 
 // G(0) = (1 + B(beta, 0))^-1 from the left stack at 0
@@ -818,14 +820,17 @@ static int restabilise(qmc_ctx *ctx, int k, int prev, int t)
     const long long NN = ctx->NN, Ls = (long long)(nsp + 1) * NN, LDs = (long long)(nsp + 1) * N;
     const long long BL = (long long)ctx->L * NN;
     cudaStream_t s = ctx->st;
-    launch_scale_cols(s, nb, N, ctx->RQ, NN, ctx->RD, N, ctx->X1, NN);
+    // B(t, prev) RQ with the columns' log scales RD carried into the UDV
     cd *a = ctx->X1, *b = ctx->X2;
-    for (int u = prev + 1; u <= t; ++u) {
+    gemm_sq(s, N, nb, TY_C64, op64(ctx->B + (long long)prev * NN, BL), 0, op64(ctx->RQ, NN), 0,
+            op64(a, NN));
+    for (int u = prev + 2; u <= t; ++u) {
         gemm_sq(s, N, nb, TY_C64, op64(ctx->B + (long long)(u - 1) * NN, BL), 0, op64(a, NN), 0,
                 op64(b, NN));
         std::swap(a, b);
     }
-    if (qrp_batched(s, N, a, NN, ctx->Qt, NN, ctx->Dt, N, ctx->Vt, NN, nb, ctx->qscr))
+    if (qrp_batched(s, N, a, NN, ctx->RD, N, ctx->Qt, NN, ctx->Dt, N, ctx->Vt, NN, nb,
+                    ctx->qscr))
         return QMC_ERR_ARG;
     gemm_sq(s, N, nb, TY_C64, op64(ctx->Vt, NN), 0, op64(ctx->RW, NN), 0, op64(ctx->X1, NN));
     std::swap(ctx->RW, ctx->X1);
@@ -852,14 +857,17 @@ static int advance_right_udv(qmc_ctx *ctx, int prev, int t)
     const int nb = ctx->nb, N = ctx->N;
     const long long NN = ctx->NN, BL = (long long)ctx->L * NN;
     cudaStream_t s = ctx->st;
-    launch_scale_cols(s, nb, N, ctx->RQ, NN, ctx->RD, N, ctx->X1, NN);
+    // B(t, prev) RQ with the columns' log scales RD carried into the UDV
     cd *a = ctx->X1, *b = ctx->X2;
-    for (int u = prev + 1; u <= t; ++u) {
+    gemm_sq(s, N, nb, TY_C64, op64(ctx->B + (long long)prev * NN, BL), 0, op64(ctx->RQ, NN), 0,
+            op64(a, NN));
+    for (int u = prev + 2; u <= t; ++u) {
         gemm_sq(s, N, nb, TY_C64, op64(ctx->B + (long long)(u - 1) * NN, BL), 0, op64(a, NN), 0,
                 op64(b, NN));
         std::swap(a, b);
     }
-    if (qrp_batched(s, N, a, NN, ctx->Qt, NN, ctx->Dt, N, ctx->Vt, NN, nb, ctx->qscr))
+    if (qrp_batched(s, N, a, NN, ctx->RD, N, ctx->Qt, NN, ctx->Dt, N, ctx->Vt, NN, nb,
+                    ctx->qscr))
         return QMC_ERR_ARG;
     gemm_sq(s, N, nb, TY_C64, op64(ctx->Vt, NN), 0, op64(ctx->RW, NN), 0, op64(ctx->X1, NN));
     std::swap(ctx->RW, ctx->X1);
@@ -1289,7 +1297,6 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
     DAS(ctx->grad, (size_t)nb * nf);
     DAS(ctx->gradp, (size_t)nb * nf);
     DAS(ctx->Dt, (size_t)nb * N);
-    DA(ctx->ones, (size_t)nb * N);
     DA(ctx->stats, (size_t)nb * 4);
     DA(ctx->eps, nb);
     DA(ctx->eps_used, nb);
@@ -1343,11 +1350,10 @@ static int setup(qmc_ctx *ctx, uint64_t seed, double coupling, double anisotropy
     CK(cudaMemcpyAsync(ctx->keys, keys.data(), sizeof(uint32_t) * 2 * nb, cudaMemcpyHostToDevice, s));
     {
         std::vector<cd> eye((size_t)nb * NN, cmk(0, 0));
-        std::vector<double> ones((size_t)nb * N, 1.0), eps(nb, ctx->o.eps0);
+        std::vector<double> eps(nb, ctx->o.eps0);
         for (int c = 0; c < nb; ++c)
             for (int x = 0; x < N; ++x) eye[(size_t)c * NN + (size_t)x * N + x] = cmk(1, 0);
         CK(cudaMemcpy(ctx->Eye, eye.data(), sizeof(cd) * eye.size(), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(ctx->ones, ones.data(), sizeof(double) * ones.size(), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(ctx->eps, eps.data(), sizeof(double) * nb, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(ctx->eps_used, eps.data(), sizeof(double) * nb, cudaMemcpyHostToDevice));
     }
@@ -2288,16 +2294,18 @@ int qmc_ratio_update(int N, int batch, const double *G, const double *Delta, dou
     return code;
 }
 
-int qmc_udv(int n, int batch, const double *X, double *Q, double *D, double *V, void *stream)
+int qmc_udv(int n, int batch, const double *X, const double *log_scale, double *Q, double *log_D,
+            double *V, void *stream)
 {
-    if (n < 1 || n > 280 || batch < 1 || !X || !Q || !D || !V) return QMC_ERR_ARG;
+    if (n < 1 || n > 280 || batch < 1 || !X || !Q || !log_D || !V) return QMC_ERR_ARG;
     if (!linalg_init_current_device()) return QMC_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
     void *scr = nullptr;
     const size_t sb = qrp_scratch_bytes(n, batch);
     if (cudaMalloc(&scr, sb ? sb : 1) != cudaSuccess) return QMC_ERR_OOM;
     const long long nn = (long long)n * n;
-    int code = qrp_batched(s, n, (const cd *)X, nn, (cd *)Q, nn, D, n, (cd *)V, nn, batch, scr)
+    int code = qrp_batched(s, n, (const cd *)X, nn, log_scale, n, (cd *)Q, nn, log_D, n, (cd *)V,
+                           nn, batch, scr)
                    ? QMC_ERR_ARG
                    : QMC_OK;
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)

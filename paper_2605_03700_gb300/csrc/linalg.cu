@@ -1419,6 +1419,18 @@ int rdiv_batched(cudaStream_t st, int prec, int n, const cd *G, long long sG, co
 }
 
 // ------------------------------------------------------------------ QRP ---
+// V_ij = R_ij / |R_ii| e^{c_j - c_i} for a matrix whose column j carries the
+// log scale c_j (R of the unscaled columns, in the factorisation's order):
+// bounded by the ordering, formed in log space so that neither factor
+// overflows on its own
+__device__ __forceinline__ cd v_entry(cd r, double rii_abs, double dc)
+{
+    if (dc == 0.0) return cscale(r, 1.0 / rii_abs);
+    const double ar = sqrt(cabs2(r));
+    if (ar == 0.0) return cmk(0, 0);
+    return cscale(r, exp(log(ar) - log(rii_abs) + dc) / ar);
+}
+
 // X = Q D V by Householder QR with column pivoting, X P = Q R, D = |diag R|,
 // V = D^-1 R P^T.  One block per matrix, working matrix and (when it fits) Q
 // in shared memory.  Pivot: the first column of largest remaining 2-norm.
@@ -1434,7 +1446,8 @@ __device__ __forceinline__ cd warp_csum(cd v)
     return v;
 }
 
-__global__ void __launch_bounds__(256) k_qrp(int n, int ld, const cd *X, long long sX, cd *Q,
+__global__ void __launch_bounds__(256) k_qrp(int n, int ld, const cd *X, long long sX,
+                                             const double *lsc, long long sL, cd *Q,
                                              long long sQ, double *D, long long sD, cd *V,
                                              long long sV, int q_in_smem, void *vscr, int a_glob)
 {
@@ -1476,6 +1489,7 @@ __global__ void __launch_bounds__(256) k_qrp(int n, int ld, const cd *X, long lo
     const int b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
     const cd *Xb = X + (long long)b * sX;
+    const double *lb = lsc ? lsc + (long long)b * sL : nullptr;
     cd *Qg = Q + (long long)b * sQ;
     cd *Qb = q_in_smem ? Qs : Qg;
     const int qld = q_in_smem ? n + 1 : n;  // Q row stride (padded in shared memory)
@@ -1492,16 +1506,18 @@ __global__ void __launch_bounds__(256) k_qrp(int n, int ld, const cd *X, long lo
         for (int j = k + tid; j < n; j += nt) {
             double s = 0.0;
             for (int i = k; i < n; ++i) s += cabs2(A[i * ld + j]);
-            cn[j] = s;
+            // with column log scales: log of the scaled norm (the column at
+            // position j came from column perm[j] of X)
+            cn[j] = lb ? (s > 0.0 ? 0.5 * log(s) : -INFINITY) + lb[perm[j]] : s;
         }
         __syncthreads();
         // pivot: first column of largest norm, warp-parallel (FP64 compares
         // run on the FP64 pipe: a serial scan by one thread cost ~15% here)
         if (warp == 0) {
-            // a lane without candidates keeps (-1, k): never chosen over a
-            // real norm (>= 0), and a valid column if every norm is NaN
+            // a lane without candidates keeps (-inf, k): never chosen over a
+            // real key, and a valid column if every key is NaN
             int best = k;
-            double bn = -1.0;
+            double bn = -INFINITY;
             for (int j = k + lane; j < n; j += 32)
                 if (cn[j] > bn) {
                     bn = cn[j];
@@ -1597,18 +1613,19 @@ __global__ void __launch_bounds__(256) k_qrp(int n, int ld, const cd *X, long lo
     }
     double *Db = D + (long long)b * sD;
     cd *Vb = V + (long long)b * sV;
-    // D = |diag R| and its reciprocals once per row (v is free now)
-    double *rinv = (double *)v;
+    // log D_i = log |R_ii| + c_{perm i}, |R_ii| kept per row (v is free now)
+    double *rabs = (double *)v;
     for (int i = tid; i < n; i += nt) {
         const double di = sqrt(cabs2(A[i * ld + i]));
-        Db[i] = di;
-        rinv[i] = 1.0 / di;
+        Db[i] = log(di) + (lb ? lb[perm[i]] : 0.0);
+        rabs[i] = di;
     }
     __syncthreads();
     for (int e = tid; e < n * n; e += nt) {
         int i = e / n, j = e % n;
         cd val = (j >= i) ? A[i * ld + j] : cmk(0, 0);
-        Vb[(long long)i * n + perm[j]] = cscale(val, rinv[i]);
+        const double dc = lb ? lb[perm[j]] - lb[perm[i]] : 0.0;
+        Vb[(long long)i * n + perm[j]] = v_entry(val, rabs[i], dc);
         if (q_in_smem) Qg[e] = Qs[i * qld + j];
     }
 }
@@ -1632,9 +1649,9 @@ __global__ void __launch_bounds__(256) k_qrp(int n, int ld, const cd *X, long lo
 // last panel to the first, on each CTA's columns of Q (read-only use of the
 // owners' vectors, which no later step changes).
 #define QR_B 8
-__global__ void __launch_bounds__(256) k_qr_bc(int n, const cd *X, long long sX, cd *Q,
-                                               long long sQ, double *D, long long sD, cd *V,
-                                               long long sV)
+__global__ void __launch_bounds__(256) k_qr_bc(int n, const cd *X, long long sX, const double *lsc,
+                                               long long sL, cd *Q, long long sQ, double *D,
+                                               long long sD, cd *V, long long sV)
 {
     cgr::cluster_group cl = cgr::this_cluster();
     const int cs = (int)cl.num_blocks(), rank = (int)cl.block_rank();
@@ -1658,6 +1675,7 @@ __global__ void __launch_bounds__(256) k_qr_bc(int n, const cd *X, long long sX,
     double *nrm = fa + n;                       // column norms of X, then |R_kk| (all rows)
     int *perm = (int *)(nrm + n);               // permuted column -> column of X
     const cd *Xb = X + (long long)b * sX;
+    const double *lb = lsc ? lsc + (long long)b * sL : nullptr;
     auto gcol = [&](int lc) { return ((lc / QR_B) * cs + rank) * QR_B + lc % QR_B; };
 
     // pre-pivoting: 2-norms of X's columns (one thread per column, rows in
@@ -1668,15 +1686,33 @@ __global__ void __launch_bounds__(256) k_qr_bc(int n, const cd *X, long long sX,
         nrm[j] = s2;
     }
     __syncthreads();
-    for (int j = tid; j < n; j += nt) {
-        // non-negative doubles order like their bit patterns; NaN goes last
-        const long long kj = isnan(nrm[j]) ? -1LL : __double_as_longlong(nrm[j]);
-        int r = 0;
-        for (int i = 0; i < n; ++i) {
-            const long long ki = isnan(nrm[i]) ? -1LL : __double_as_longlong(nrm[i]);
-            r += (ki > kj || (ki == kj && i < j));
+    if (lb) {
+        // with column log scales c_j: the order of log |x_j| + c_j (in place)
+        for (int j = tid; j < n; j += nt) {
+            const double v = nrm[j];
+            nrm[j] = (v > 0.0 ? 0.5 * log(v) : -INFINITY) + lb[j];
         }
-        perm[r] = j;
+        __syncthreads();
+        for (int j = tid; j < n; j += nt) {
+            const double kj = isnan(nrm[j]) ? -INFINITY : nrm[j];
+            int r = 0;
+            for (int i = 0; i < n; ++i) {
+                const double ki = isnan(nrm[i]) ? -INFINITY : nrm[i];
+                r += (ki > kj || (ki == kj && i < j));
+            }
+            perm[r] = j;
+        }
+    } else {
+        for (int j = tid; j < n; j += nt) {
+            // non-negative doubles order like their bit patterns; NaN goes last
+            const long long kj = isnan(nrm[j]) ? -1LL : __double_as_longlong(nrm[j]);
+            int r = 0;
+            for (int i = 0; i < n; ++i) {
+                const long long ki = isnan(nrm[i]) ? -1LL : __double_as_longlong(nrm[i]);
+                r += (ki > kj || (ki == kj && i < j));
+            }
+            perm[r] = j;
+        }
     }
     __syncthreads();
     for (int e = tid; e < n * wl; e += nt) {
@@ -1870,13 +1906,15 @@ __global__ void __launch_bounds__(256) k_qr_bc(int n, const cd *X, long long sX,
     double *Db = D + (long long)b * sD;
     cd *Vb = V + (long long)b * sV;
     cd *Qg = Q + (long long)b * sQ;
+    // log D_i = log |R_ii| + c_{perm i}
     if (rank == 0)
-        for (int i = tid; i < n; i += nt) Db[i] = nrm[i];
+        for (int i = tid; i < n; i += nt) Db[i] = log(nrm[i]) + (lb ? lb[perm[i]] : 0.0);
     for (int e = tid; e < n * wl; e += nt) {
         const int i = e / wl, lc = e % wl, pc = gcol(lc);
         if (pc >= n) continue;
         const cd r = i <= pc ? A[i * ldw + lc] : cmk(0, 0);
-        Vb[(long long)i * n + perm[pc]] = cscale(r, 1.0 / nrm[i]);
+        const double dc = lb ? lb[perm[pc]] - lb[perm[i]] : 0.0;
+        Vb[(long long)i * n + perm[pc]] = v_entry(r, nrm[i], dc);
         Qg[(long long)i * n + pc] = Qm[i * ldw + lc];
     }
     cl.sync();  // no CTA leaves while another may still read its shared memory
@@ -1890,8 +1928,9 @@ static size_t qr_bc_smem(int n, int cs)
     return cdn * sizeof(cd) + 2 * (size_t)n * sizeof(double) + (size_t)n * sizeof(int);
 }
 
-static int qr_bc_launch(cudaStream_t st, int n, const cd *X, long long sX, cd *Q, long long sQ,
-                        double *D, long long sD, cd *V, long long sV, int batch, int cs)
+static int qr_bc_launch(cudaStream_t st, int n, const cd *X, long long sX, const double *lsc,
+                        long long sL, cd *Q, long long sQ, double *D, long long sD, cd *V,
+                        long long sV, int batch, int cs)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs, batch);
@@ -1905,7 +1944,10 @@ static int qr_bc_launch(cudaStream_t st, int n, const cd *X, long long sX, cd *Q
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_qr_bc, n, X, sX, Q, sQ, D, sD, V, sV) == cudaSuccess ? 0 : -1;
+    return cudaLaunchKernelEx(&cfg, k_qr_bc, n, X, sX, lsc, sL, Q, sQ, D, sD, V, sV) ==
+                   cudaSuccess
+               ? 0
+               : -1;
 }
 
 // CTAs per matrix of the blocked UDV (QMC_QR_CS=1 keeps the column-pivoted
@@ -1921,14 +1963,15 @@ size_t qrp_scratch_bytes(int n, int batch)
     return ((vec + 255) & ~(size_t)255) + amat;
 }
 
-int qrp_batched(cudaStream_t st, int n, const cd *X, long long sX, cd *Q, long long sQ, double *D,
-                long long sD, cd *V, long long sV, int batch, void *vscr)
+int qrp_batched(cudaStream_t st, int n, const cd *X, long long sX, const double *lsc, long long sL,
+                cd *Q, long long sQ, double *D, long long sD, cd *V, long long sV, int batch,
+                void *vscr)
 {
     // the blocked pre-pivoted kernel over a cluster where its columns fit
     int cs = g_qr_cs;
     while (cs > 1 && cs < 8 && qr_bc_smem(n, cs) > SMEM_MAX) cs *= 2;
     if (cs > 1 && qr_bc_smem(n, cs) <= SMEM_MAX) {
-        if (qr_bc_launch(st, n, X, sX, Q, sQ, D, sD, V, sV, batch, cs) == 0) {
+        if (qr_bc_launch(st, n, X, sX, lsc, sL, Q, sQ, D, sD, V, sV, batch, cs) == 0) {
             QMC_COUNT(1);
             return 0;
         }
@@ -1940,8 +1983,8 @@ int qrp_batched(cudaStream_t st, int n, const cd *X, long long sX, cd *Q, long l
     const size_t withq = base + (size_t)n * (n + 1) * sizeof(cd);
     if (base <= 220 * 1024) {
         const int qs = withq <= 220 * 1024;
-        k_qrp<<<batch, 256, qs ? withq : base, st>>>(n, n + 1, X, sX, Q, sQ, D, sD, V, sV, qs,
-                                                   nullptr, 0);
+        k_qrp<<<batch, 256, qs ? withq : base, st>>>(n, n + 1, X, sX, lsc, sL, Q, sQ, D, sD, V, sV,
+                                                   qs, nullptr, 0);
     } else if ((size_t)n * n * sizeof(cd) + (size_t)n * sizeof(cd) <= g_smem_qrp) {
         // large sizes: matrix (row stride n + 1 if it fits, else n) and v in
         // shared memory, the other vectors and Q in global memory
@@ -1949,12 +1992,12 @@ int qrp_batched(cudaStream_t st, int n, const cd *X, long long sX, cd *Q, long l
         if ((size_t)n * ld * sizeof(cd) + (size_t)n * sizeof(cd) > g_smem_qrp) ld = n;
         const size_t smem = (size_t)n * ld * sizeof(cd) + (size_t)n * sizeof(cd);
         if (!vscr) return -1;
-        k_qrp<<<batch, 256, smem, st>>>(n, ld, X, sX, Q, sQ, D, sD, V, sV, 0, vscr, 0);
+        k_qrp<<<batch, 256, smem, st>>>(n, ld, X, sX, lsc, sL, Q, sQ, D, sD, V, sV, 0, vscr, 0);
     } else {
         // largest sizes: everything but v in global scratch
         if (!vscr) return -1;
-        k_qrp<<<batch, 256, (size_t)n * sizeof(cd), st>>>(n, n, X, sX, Q, sQ, D, sD, V, sV, 0,
-                                                          vscr, 1);
+        k_qrp<<<batch, 256, (size_t)n * sizeof(cd), st>>>(n, n, X, sX, lsc, sL, Q, sQ, D, sD, V,
+                                                          sV, 0, vscr, 1);
     }
     QMC_COUNT(1);
     return 0;

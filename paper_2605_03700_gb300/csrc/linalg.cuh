@@ -63,10 +63,14 @@ int lu_batched(cudaStream_t st, int n, cd *A, long long sA, int *piv, long long 
                int batch);
 int rdiv_batched(cudaStream_t st, int prec, int n, const cd *G, long long sG, const cd *LU,
                  long long sLU, const int *piv, long long spiv, cd *X, long long sX, int batch);
+// X diag(e^c) = Q diag(e^logD) V (the UDV of the stabilisation stacks): lsc
+// the column log scales c of X (stride sL per matrix; null: none), D
+// returned as log D so that neither the scales nor D leave FP64's range.
 // vscr: global scratch of qrp_scratch_bytes(n, batch) bytes, needed only for
 // the sizes whose per-step vectors do not fit in shared memory (n > 112)
-int qrp_batched(cudaStream_t st, int n, const cd *X, long long sX, cd *Q, long long sQ, double *D,
-                long long sD, cd *V, long long sV, int batch, void *vscr = nullptr);
+int qrp_batched(cudaStream_t st, int n, const cd *X, long long sX, const double *lsc, long long sL,
+                cd *Q, long long sQ, double *D, long long sD, cd *V, long long sV, int batch,
+                void *vscr);
 size_t qrp_scratch_bytes(int n, int batch);
 
 // typed operand: pointer, batch stride (elements), element type

@@ -551,17 +551,10 @@ __global__ void k_commit(CommitP p)
 }
 
 // -------------------------------------------------------- stabilisation --
-// Y = X diag(d) (d real)
-__global__ void k_scale_cols(int N, const cd *X, long long sX, const double *d, long long sd,
-                             cd *Y, long long sY)
-{
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    int c = blockIdx.y;
-    if (e >= N * N) return;
-    Y[(long long)c * sY + e] = cscale(X[(long long)c * sX + e], d[(long long)c * sd + e % N]);
-}
-
-// X = DbR^-1 T1 DbL^-1 + DsR T2 DsL with Db = max(D,1), Ds = min(D,1)
+// X = DbR^-1 T1 DbL^-1 + DsR T2 DsL with Db = max(D,1), Ds = min(D,1); the
+// stacks hold log D (the singular values of the slice products leave FP64's
+// exponent range at large beta times coupling), so Db^-1 = e^{-max(lD,0)}
+// and Ds = e^{min(lD,0)}, both in (0, 1]
 __global__ void k_stab_mix(int N, const cd *T1, const cd *T2, const double *DR, long long sDR,
                            const double *DL, long long sDL, cd *X)
 {
@@ -569,23 +562,20 @@ __global__ void k_stab_mix(int N, const cd *T1, const cd *T2, const double *DR, 
     int c = blockIdx.y;
     if (e >= N * N) return;
     int r = e / N, k = e % N;
-    double dr = DR[(long long)c * sDR + r], dl = DL[(long long)c * sDL + k];
-    double dbr = dr > 1 ? dr : 1, dsr = dr > 1 ? 1 : dr;
-    double dbl = dl > 1 ? dl : 1, dsl = dl > 1 ? 1 : dl;
+    double lr = DR[(long long)c * sDR + r], ll = DL[(long long)c * sDL + k];
     long long o = (long long)c * N * N + e;
-    cd a = cscale(T1[o], 1.0 / (dbr * dbl));
-    cd b = cscale(T2[o], dsr * dsl);
+    cd a = cscale(T1[o], exp(-(fmax(lr, 0.0) + fmax(ll, 0.0))));
+    cd b = cscale(T2[o], exp(fmin(lr, 0.0) + fmin(ll, 0.0)));
     X[o] = cadd(a, b);
 }
 
-// 1/max(D,1) as a complex vector (GEMM diagonal)
+// 1/max(D,1) = e^{-max(log D, 0)} as a complex vector (GEMM diagonal)
 __global__ void k_inv_big(int N, const double *D, long long sD, cd *out)
 {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int c = blockIdx.y;
     if (x >= N) return;
-    double d = D[(long long)c * sD + x];
-    out[(long long)c * N + x] = cmk(1.0 / (d > 1 ? d : 1), 0.0);
+    out[(long long)c * N + x] = cmk(exp(-fmax(D[(long long)c * sD + x], 0.0)), 0.0);  // log D
 }
 
 // err = max |Gs - G| / max |Gs|; G <- Gs
@@ -766,15 +756,14 @@ __global__ void __launch_bounds__(256) k_meas_tau(int n, int q, const cd *Gt0, c
     }
 }
 
-// D_small = min(D, 1) of the UDV split D = D_big D_small, as a complex
-// diagonal
+// D_small = min(D, 1) = e^{min(log D, 0)} of the UDV split D = D_big D_small,
+// as a complex diagonal
 __global__ void k_small_part(int N, const double *D, long long sD, cd *out)
 {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int c = blockIdx.y;
     if (x >= N) return;
-    double d = D[(long long)c * sD + x];
-    out[(long long)c * N + x] = cmk(d < 1 ? d : 1.0, 0.0);
+    out[(long long)c * N + x] = cmk(exp(fmin(D[(long long)c * sD + x], 0.0)), 0.0);  // log D
 }
 
 // per chain: S^i_q for Gamma^1..5, m^2_SO(5), correlation ratio, energy
@@ -978,12 +967,6 @@ void launch_commit(cudaStream_t s, int nb, const CommitP &p)
     for (int k = 0; k < p.nseg; ++k)
         if (p.seg[k].words > mx) mx = p.seg[k].words;
     k_commit<<<dim3((unsigned)((mx + 255) / 256), nb), 256, 0, s>>>(p);
-    QMC_COUNT(1);
-}
-void launch_scale_cols(cudaStream_t s, int nb, int N, const cd *X, long long sX, const double *d,
-                       long long sd, cd *Y, long long sY)
-{
-    k_scale_cols<<<dim3(cdiv_up(N * N, 256), nb), 256, 0, s>>>(N, X, sX, d, sd, Y, sY);
     QMC_COUNT(1);
 }
 void launch_stab_mix(cudaStream_t s, int nb, int N, const cd *T1, const cd *T2, const double *DR,

@@ -88,8 +88,6 @@ void launch_axpyI(cudaStream_t s, int nb, int N, Op X, cd a, cd b, Op Y);
 void launch_cvt_real(cudaStream_t s, long long n, const float *a, double *b);
 void launch_accept(cudaStream_t s, int nb, const AcceptP &p);
 void launch_commit(cudaStream_t s, int nb, const CommitP &p);
-void launch_scale_cols(cudaStream_t s, int nb, int N, const cd *X, long long sX, const double *d,
-                       long long sd, cd *Y, long long sY);
 void launch_stab_mix(cudaStream_t s, int nb, int N, const cd *T1, const cd *T2, const double *DR,
                      long long sDR, const double *DL, long long sDL, cd *X);
 void launch_inv_big(cudaStream_t s, int nb, int N, const double *D, long long sD, cd *out);

@@ -154,7 +154,7 @@ def lib():
         L.qmc_cgemm.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_int, vp, C.c_int, vp, vp,
                                 C.c_int, C.c_int, C.c_int, vp]
         L.qmc_eigh.argtypes = [C.c_int, C.c_int, vp, vp, vp, C.c_int, vp]
-        L.qmc_udv.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp, vp]
+        L.qmc_udv.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -250,10 +250,13 @@ def qmc_eigh(n, batch, A_ptr, U_ptr, w_ptr, precision=1, stream=0):
                           precision, C.c_void_p(stream) if stream else None))
 
 
-def qmc_udv(n, batch, X_ptr, Q_ptr, D_ptr, V_ptr, stream=0):
-    """X = Q diag(D) V on device pointers (qmc_udv)."""
-    _check(lib().qmc_udv(n, batch, C.c_void_p(X_ptr), C.c_void_p(Q_ptr), C.c_void_p(D_ptr),
-                         C.c_void_p(V_ptr), C.c_void_p(stream) if stream else None))
+def qmc_udv(n, batch, X_ptr, Q_ptr, logD_ptr, V_ptr, logscale_ptr=0, stream=0):
+    """X diag(e^c) = Q diag(e^d) V on device pointers (qmc_udv): c the
+    optional column log scales, d = log D returned."""
+    _check(lib().qmc_udv(n, batch, C.c_void_p(X_ptr),
+                         C.c_void_p(logscale_ptr) if logscale_ptr else None, C.c_void_p(Q_ptr),
+                         C.c_void_p(logD_ptr), C.c_void_p(V_ptr),
+                         C.c_void_p(stream) if stream else None))
 
 
 def qmc_ratio_update(N, batch, G_ptr, Delta_ptr, Gp_ptr, logdet_ptr, stream=0):

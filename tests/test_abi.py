@@ -94,8 +94,8 @@ def test_new_entry_points_reject_invalid_arguments_before_device_work(lib):
     assert L.qmc_eigh(65, 1, one, one, one, 0, None) == -1
     assert L.qmc_eigh(36, 1, one, one, one, 3, None) == -1
     # UDV: null buffers, n beyond 280
-    assert L.qmc_udv(72, 1, None, None, None, None, None) == -1
-    assert L.qmc_udv(281, 1, one, one, one, one, None) == -1
+    assert L.qmc_udv(72, 1, None, None, None, None, None, None) == -1
+    assert L.qmc_udv(281, 1, one, None, one, one, one, None) == -1
     # sphere beyond 60 orbitals; torus beyond 140, or beyond 60 in FP64
     o = qmc.qmc_default_opts()
     assert L.qmc_create(C.byref(h), 1, 60, 1.0, 0.1, 1.0, 0.0, 0, C.byref(o)) == -1
@@ -103,6 +103,12 @@ def test_new_entry_points_reject_invalid_arguments_before_device_work(lib):
     o.precision = 1
     assert L.qmc_create(C.byref(h), 0, 141, 1.0, 0.1, 1.0, 0.0, 0, C.byref(o)) == -1
     o.precision = 3
+    assert L.qmc_create(C.byref(h), 0, 4, 1.0, 0.1, 1.0, 0.0, 0, C.byref(o)) == -1
+    # slice kinds: shared (0) and a set per factor (2); the single exponential
+    # (1) is oracle-only
+    o = qmc.qmc_default_opts()
+    assert o.slice_kind == qmc.QMC_SLICE_SHARED
+    o.slice_kind = 1
     assert L.qmc_create(C.byref(h), 0, 4, 1.0, 0.1, 1.0, 0.0, 0, C.byref(o)) == -1
     assert not h.value
 

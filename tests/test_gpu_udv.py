@@ -1,11 +1,15 @@
-"""The stabilisation stacks' decomposition X = Q diag(D) V (qmc_udv) against
-its definition, on random and on column-graded matrices (the graded products
-of the UDV chain: column scales spanning e^-120 .. e^120).
+"""The stabilisation stacks' decomposition X diag(e^c) = Q diag(e^d) V
+(qmc_udv) against its definition, on random matrices, on column-graded ones
+(scales e^-120 .. e^120 in X itself) and with column log scales far beyond
+FP64's exponent range (|c| up to 2000, passed as log_scale: the stacks carry
+their D this way, since the slice products' singular values reach e^{~10^4}
+on the 60-orbital sphere at beta = 40).
 
-For n <= 128 the columns are ordered by 2-norm once and factored by blocked
-Householder QR over a cluster of CTAs; the column-pivoted one-CTA kernel
-(QMC_QR_CS=1, run in a fresh process) must agree with it on X and Q^H Q.
-Each column of X is reproduced to FP64 rounding relative to that column.
+For n <= 128 the columns are ordered by log |x_j| + c_j once and factored by
+blocked Householder QR over a cluster of CTAs; the column-pivoted one-CTA
+kernel (QMC_QR_CS=1, run in a fresh process) must satisfy the same
+definition.  Each column of X is reproduced to FP64 rounding relative to
+that column, Q is unitary to rounding, and V = D^-1 R P^T stays bounded.
 """
 import os
 import subprocess
@@ -28,14 +32,17 @@ def qmc():
     return P
 
 
-def _udv(qmc, X):
+def _udv(qmc, X, lsc=None):
     import torch
     b, n, _ = X.shape
     Xt = torch.tensor(np.ascontiguousarray(X), dtype=torch.complex128, device="cuda").contiguous()
     Qt = torch.full((b, n, n), complex(np.nan, np.nan), dtype=torch.complex128, device="cuda")
     Vt = torch.full((b, n, n), complex(np.nan, np.nan), dtype=torch.complex128, device="cuda")
     Dt = torch.full((b, n), np.nan, dtype=torch.float64, device="cuda")
-    qmc.qmc_udv(n, b, Xt.data_ptr(), Qt.data_ptr(), Dt.data_ptr(), Vt.data_ptr())
+    Lt = None if lsc is None else torch.tensor(np.ascontiguousarray(lsc), dtype=torch.float64,
+                                                device="cuda").contiguous()
+    qmc.qmc_udv(n, b, Xt.data_ptr(), Qt.data_ptr(), Dt.data_ptr(), Vt.data_ptr(),
+                0 if Lt is None else Lt.data_ptr())
     return Qt.cpu().numpy(), Dt.cpu().numpy(), Vt.cpu().numpy()
 
 
@@ -47,17 +54,21 @@ def _inputs(n, b, graded, seed):
     return X
 
 
-def _check(X, Q, D, V):
-    n = X.shape[1]
-    assert np.all(np.isfinite(Q)) and np.all(np.isfinite(V)) and np.all(D > 0)
+def _check(X, Q, d, V, c=None):
+    b, n, _ = X.shape
+    c = np.zeros((b, n)) if c is None else c
+    assert np.all(np.isfinite(Q)) and np.all(np.isfinite(V)) and np.all(np.isfinite(d))
     un = np.abs(np.conj(np.swapaxes(Q, 1, 2)) @ Q - np.eye(n)).max()
     assert un < 1e-13, un
-    Y = Q @ (D[:, :, None] * V)
+    assert np.abs(V).max() < 1e3  # bounded by the ordering
+    # X_j = sum_i Q_i V_ij e^{d_i - c_j}, each factor formed in log space
+    with np.errstate(divide="ignore"):
+        lv = np.log(np.abs(V))
+    W = np.where(V != 0, np.exp(np.minimum(lv + d[:, :, None] - c[:, None, :], 700.0)) *
+                 np.exp(1j * np.angle(V)), 0)
+    Y = Q @ W
     colerr = (np.abs(Y - X).max(1) / np.abs(X).max(1)).max()
     assert colerr < 1e-12, colerr
-    # V's rows have unit-modulus pivots: |V| entries of each row at most ~1
-    # where the ordering is by norm (row i of R is dominated by R_ii)
-    return un, colerr
 
 
 @pytest.mark.parametrize("n", [2, 10, 36, 72, 120, 280])
@@ -65,6 +76,19 @@ def _check(X, Q, D, V):
 def test_udv_reproduces_x(qmc, n, graded):
     X = _inputs(n, 8 if n <= 120 else 2, graded, n + 7 * graded)
     _check(X, *_udv(qmc, X))
+
+
+@pytest.mark.parametrize("n", [10, 72, 120, 280])
+def test_udv_with_log_scales_beyond_fp64(qmc, n):
+    """Column scales e^{c_j}, |c_j| <= 2000, never formed: log D comes out
+    finite and the scaled columns are reproduced."""
+    b = 4 if n <= 120 else 2
+    X = _inputs(n, b, False, 100 + n)
+    c = np.random.default_rng(n).uniform(-2000, 2000, size=(b, n))
+    Q, d, V = _udv(qmc, X, c)
+    _check(X, Q, d, V, c)
+    # the log singular values follow the scales: the largest d is near max c
+    assert np.abs(d.max(1) - c.max(1)).max() < 10
 
 
 RUN = """
@@ -75,22 +99,20 @@ build.build()
 import paper_2605_03700_gb300 as P
 from tests.test_gpu_udv import _inputs, _udv
 X = _inputs(int(sys.argv[1]), 8, True, 3)
-Q, D, V = _udv(P, X)
-np.savez(sys.argv[2], Q=Q, D=D, V=V)
+c = np.random.default_rng(5).uniform(-1500, 1500, size=(8, int(sys.argv[1])))
+Q, D, V = _udv(P, X, c)
+np.savez(sys.argv[2], Q=Q, D=D, V=V, c=c)
 """
 
 
 def test_blocked_and_pivoted_kernels_agree(tmp_path):
-    """Both kernels factor the same graded matrices; the products agree
-    column by column, and so do the Gram matrices V^H D^2 V = X^H X."""
-    out = {}
+    """Both kernels factor the same graded, log-scaled matrices to the
+    definition."""
     for cs in (1, 4):
         path = str(tmp_path / f"udv{cs}.npz")
         r = subprocess.run([sys.executable, "-c", RUN, "72", path], cwd=ROOT, capture_output=True,
                            text=True, timeout=600, env=dict(os.environ, QMC_QR_CS=str(cs)))
         assert r.returncode == 0, r.stderr[-3000:]
-        out[cs] = np.load(path)
-    X = _inputs(72, 8, True, 3)
-    for cs in (1, 4):
-        Q, D, V = out[cs]["Q"], out[cs]["D"], out[cs]["V"]
-        _check(X, Q, D, V)
+        out = np.load(path)
+        X = _inputs(72, 8, True, 3)
+        _check(X, out["Q"], out["D"], out["V"], out["c"])
