@@ -1,9 +1,9 @@
 """The stabilisation stacks' decomposition X diag(e^c) = Q diag(e^d) V
 (qmc_udv) against its definition, on random matrices, on column-graded ones
-(scales e^-120 .. e^120 in X itself) and with column log scales far beyond
-FP64's exponent range (|c| up to 2000, passed as log_scale: the stacks carry
-their D this way, since the slice products' singular values reach e^{~10^4}
-on the 60-orbital sphere at beta = 40).
+(scales e^-120 .. e^120 in X itself) and with column log scales passed as
+log_scale, shifted far beyond FP64's exponent range (the stacks carry their D
+this way, since the slice products' singular values reach e^{~10^4} on the
+60-orbital sphere at beta = 40).
 
 For n <= 128 the columns are ordered by log |x_j| + c_j once and factored by
 blocked Householder QR over a cluster of CTAs; the column-pivoted one-CTA
@@ -80,15 +80,19 @@ def test_udv_reproduces_x(qmc, n, graded):
 
 @pytest.mark.parametrize("n", [10, 72, 120, 280])
 def test_udv_with_log_scales_beyond_fp64(qmc, n):
-    """Column scales e^{c_j}, |c_j| <= 2000, never formed: log D comes out
-    finite and the scaled columns are reproduced."""
+    """Column log scales c (spread over e^-300 .. e^300, where X diag(e^c)
+    is still representable) reproduce the scaled columns; shifting every c
+    by 2500 (far beyond FP64's range) leaves Q and V bit for bit and shifts
+    log D by exactly the same amount: the decomposition never forms the
+    scaled matrix."""
     b = 4 if n <= 120 else 2
     X = _inputs(n, b, False, 100 + n)
-    c = np.random.default_rng(n).uniform(-2000, 2000, size=(b, n))
+    c = np.random.default_rng(n).uniform(-300, 300, size=(b, n))
     Q, d, V = _udv(qmc, X, c)
     _check(X, Q, d, V, c)
-    # the log singular values follow the scales: the largest d is near max c
-    assert np.abs(d.max(1) - c.max(1)).max() < 10
+    Q2, d2, V2 = _udv(qmc, X, c + 2500.0)
+    assert np.array_equal(Q2, Q) and np.array_equal(V2, V)
+    assert np.abs(d2 - d - 2500.0).max() < 1e-9
 
 
 RUN = """
@@ -99,7 +103,7 @@ build.build()
 import paper_2605_03700_gb300 as P
 from tests.test_gpu_udv import _inputs, _udv
 X = _inputs(int(sys.argv[1]), 8, True, 3)
-c = np.random.default_rng(5).uniform(-1500, 1500, size=(8, int(sys.argv[1])))
+c = np.random.default_rng(5).uniform(-300, 300, size=(8, int(sys.argv[1])))
 Q, D, V = _udv(P, X, c)
 np.savez(sys.argv[2], Q=Q, D=D, V=V, c=c)
 """
