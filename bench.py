@@ -630,10 +630,6 @@ def run_sphere(args):
     u = args.sphere_u
     workload = (f"sphere, 60 orbitals (N=120, N_q=3600), beta=40, dtau=0.1 (L=400), u={u}, one "
                 "chain, prior whole-slice sweeps (rho 0) with a Langevin sweep every 4th step")
-    # the weight of this model is real and positive; the computed Im log R of
-    # an update carries rounding that grows with the conditioning of M (G at
-    # 60 orbitals is conditioned ~1e11 already at u = 0.3), so the check that
-    # flags a complex ratio takes a bound above that noise (--sphere-sign-tol)
     ch = P.Chain(P.QMC_SPHERE, 59, 40.0, DTAU, u, 0.0, 0, n_stab=NSTAB, eps0=0.2,
                  precision=args.precision, series_capacity=4096,
                  sign_tol=args.sphere_sign_tol)
@@ -788,12 +784,11 @@ def main():
                          "sizes; used for profiler launch lists)")
     ap.add_argument("--sphere-u", type=float, default=1.2,
                     help="coupling of --workload sphere60 (the workload's 1.2; the paper's sphere "
-                         "runs use u <= 0.3)")
-    ap.add_argument("--sphere-sign-tol", type=float, default=1e-3,
+                         "scans use 0.075 .. 0.3)")
+    ap.add_argument("--sphere-sign-tol", type=float, default=1e-6,
                     help="bound on |sin Im log R| of accepted updates for --workload sphere60 "
-                         "(the ratio is real in exact arithmetic; its computed phase is rounding "
-                         "scaled by the conditioning of M, ~1e11 at 60 orbitals; a complex "
-                         "weight would give O(1))")
+                         "(the library's default; the ratio is real in exact arithmetic and its "
+                         "computed phase is rounding scaled by the conditioning of M)")
     ap.add_argument("--workload", default="nphi36",
                     choices=["nphi36", "batched", "sphere60", "torus140"],
                     help="nphi36: the headline workload (default); batched: 64 chains of mixed "

@@ -21,8 +21,9 @@ What is built here, and the passage each piece follows:
   (4 pi sqrt(N_phi)).
 * sphere monopole-harmonic form factors (Methods,
   Eq. sphere_density_operator), with orbital label m_k = k - 1 - s
-  substituted for the literal "k" inside the 3j symbol and the phase, and
-  with n_{l,-m} taken as n_{l,m}^dagger (see ``sphere_form_factors``).
+  substituted for the literal "k" inside the 3j symbol and the phase, with
+  n_{l,-m} taken as n_{l,m}^dagger, and scaled by 1/(2 pi sqrt(n_orb)) so that
+  the sphere carries the torus's normalisation (see ``sphere_form_factors``).
 * the real-field parametrisation of the sum of squares (Methods,
   Eq. interaction_squares): for a self-conjugate q, Q = sqrt(2) n_q; for a
   pair (q, qbar) with F_qbar = F_q^dagger, Q_A = n_q + n_qbar and
@@ -173,12 +174,24 @@ def sphere_form_factors(norb: int, qs):
     m_k = r - s and the phase (-1)^{s + m_k + m} = (-1)^{r + m}.  The paper's
     formula obeys F_{l,-m} = (-1)^m F_{l,m}^dagger; the rotation-invariant
     interaction sum_m n_{l,m} n_{l,m}^dagger is used, i.e. for m < 0 the table
-    holds F_{l,|m|}^dagger."""
+    holds F_{l,|m|}^dagger.
+
+    Normalisation.  As printed, F_{0,0} = (-1)^{2s}/2 I and (3j orthogonality)
+    sum_q ||F_q||_F^2 = n_orb^2 / 4: the weight per orbital grows with the
+    system, so the effective coupling would grow with n_orb.  The
+    torus of Eq. torus_density_operator has F_0 = I / (4 pi sqrt(N_phi)) and
+    a size-independent weight 1/(16 pi^2) per orbital, and the paper finds
+    one critical coupling for all sphere sizes N_phi = 15..59 (u_c ~ 0.17,
+    finite-size scaling in Results), close to the torus's 0.20 (Supp.
+    Fig. S4): both need a size-independent scale, matching the torus's.  Reading: the printed expression times 1/(2 pi sqrt(n_orb)),
+    which makes F_{0,0} = (-1)^{2s} I / (4 pi sqrt(n_orb)) and the weight
+    exactly 1/(16 pi^2) per orbital, the torus's values."""
     s2 = norb - 1                      # 2s
     s = Fraction(s2, 2)
     nq = len(qs)
     val = np.zeros((nq, norb), dtype=complex)
     col = np.full((nq, norb), -1, dtype=np.int32)
+    kappa = 1.0 / (2.0 * math.pi * math.sqrt(norb))
     red = {}
     for l in range(norb):
         red[l] = wigner3j(s, l, s, -s, 0, s)
@@ -192,7 +205,7 @@ def sphere_form_factors(norb: int, qs):
                 mk = Fraction(r) - s
                 w = wigner3j(s, l, s, -mk, -m, mk + m)
                 sign = -1.0 if (r + m) % 2 else 1.0
-                v = sign * (s2 + 1) * math.sqrt(2 * l + 1) / 2.0 * w * red[l]
+                v = sign * (s2 + 1) * math.sqrt(2 * l + 1) / 2.0 * w * red[l] * kappa
                 val[iq, r] = v
                 col[iq, r] = c
             cache[(l, m)] = iq

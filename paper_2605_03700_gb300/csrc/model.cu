@@ -84,12 +84,18 @@ __device__ __forceinline__ dd dd_sqrt_int(long long d)
 // Sphere form factors (Methods, Eq. sphere_density_operator): for q = (l, m),
 // index q = l^2 + l + m, the n_orb = 2s + 1 LLL orbitals m_k = r - s (row r)
 // and m >= 0, F_q[r, r + m] = (-1)^{2s} sqrt(2l + 1) / 2
-//   x <s m_k; l m | s m_k + m> <s s; l 0 | s s>,
+//   x <s m_k; l m | s m_k + m> <s s; l 0 | s s> (before the scale below),
 // which is the paper's (2s + 1) sqrt(2l + 1) / 2 (-1)^{s + m_k + m} times its
 // two 3j symbols, rewritten with (j1 j2 j3; m1 m2 m3) = (-1)^{j1 - j2 - m3}
 // <j1 m1; j2 m2 | j3 -m3> / sqrt(2 j3 + 1) and the reflection symmetry of the
 // Clebsch-Gordan coefficients.  F_{l,-m} = F_{l,m}^dagger (the rotation-
-// invariant pairing of n_{l,m} with its adjoint).
+// invariant pairing of n_{l,m} with its adjoint).  Every entry is further
+// scaled by 1/(2 pi sqrt(n_orb)): F_{0,0} becomes (-1)^{2s} I / (4 pi
+// sqrt(n_orb)) and sum_q ||F_q||_F^2 = n_orb / (16 pi^2), the torus's q = 0
+// table and its size-independent weight per orbital, without which the
+// effective coupling would grow with n_orb (the printed expression gives
+// n_orb / 4 per orbital) and no single critical coupling could hold across
+// sphere sizes, as the paper's finite-size scaling finds.
 // The coefficients <s m1; l m2 | s M> come from the highest-weight state
 // (J+ |s s> = 0 fixes the ratios along m1 + m2 = s; Condon-Shortley sign:
 // positive at m1 = s) and the lowering operator J- = j1- + j2-, one M at a
@@ -134,7 +140,8 @@ __global__ void __launch_bounds__(64) k_ff_sphere(int n, cd *val, int *col)
     }
     __syncthreads();
     const double sgn = (S2 & 1) ? -1.0 : 1.0;
-    const dd pref = dd_mul(dd{sgn * 0.5, 0.0}, dd_mul(dd_sqrt_int(2 * l + 1), c0));
+    const double kappa = 1.0 / (2.0 * 3.141592653589793 * sqrt((double)n));
+    const dd pref = dd_mul(dd{sgn * 0.5 * kappa, 0.0}, dd_mul(dd_sqrt_int(2 * l + 1), c0));
     int cur = 0;
     for (int iM = S2; iM >= 0; --iM) {  // M = iM - s
         // emit <s m1; l m | s M> for this thread's m1 with 0 <= m <= l

@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 from paper_2605_03700_gb300 import fss
+from tests.sphere_units import sphere_u
 
 UC, DS, DV = 0.163, 2.46, 0.53
 SIZES = [15, 20, 27, 36, 45, 59]
@@ -195,9 +196,10 @@ def test_channels_against_the_oracle_chain_and_exact_diagonalisation():
     """Torus N_phi = 2, u = 4, alpha = 0.3, beta = 2: the SO(5) channel
     reproduces the sweep's own m^2 and R columns, and the VBS and AFM m^2 and
     R (ratio of means) agree with exact diagonalisation within 4 sigma.
-    Sphere N_phi = 2, u = 1, alpha = -0.8 (U_K > U_N): VBS order exceeds AFM
-    order in both m^2 and R, as exact diagonalisation says (S^1_0 = 2.58 vs
-    S^3_0 = 2.25); a swapped channel assignment fails here.  (At N_phi = 2 the
+    Sphere N_phi = 2, u = 79, alpha = -63 (strong coupling,
+    tests/sphere_units.py; U_K > U_N): VBS order exceeds AFM order in both m^2
+    and R, as exact diagonalisation says (S^1_0 = 0.0327 vs S^3_0 = 0.0285);
+    a swapped channel assignment fails here.  (At N_phi = 2 the
     torus channels differ by < 1%, too little to tell them apart.)"""
     from oracle import ed as E
     from oracle import model as M
@@ -218,10 +220,11 @@ def test_channels_against_the_oracle_chain_and_exact_diagonalisation():
             assert abs(mu - exact) < 4 * err, (chn, k, mu, exact, err)
 
     m = M.Model(M.SPHERE, 2)
-    ref = E.ED(m, M.couplings(1.0, -0.8), 2.0).observables()
+    us, als = sphere_u(1.0, 2), sphere_u(-0.8, 2)
+    ref = E.ED(m, M.couplings(us, als), 2.0).observables()
     assert ref["S0"][0] > 1.1 * ref["S0"][2]
     assert ref["Sdq"][0] / ref["S0"][0] < ref["Sdq"][2] / ref["S0"][2]
-    ch = O.Chain(M.SPHERE, 2, 2.0, 0.1, 1.0, -0.8, seed=2, n_stab=5, n_adapt=150, model=m)
+    ch = O.Chain(M.SPHERE, 2, 2.0, 0.1, us, als, seed=2, n_stab=5, n_adapt=150, model=m)
     ch.sweep(150)
     b = ch.sweep(2000).reshape(20, -1, 20).mean(1)
     mv, Rv = fss.order_parameters(b, 2, "VBS")

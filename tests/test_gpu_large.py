@@ -1,7 +1,8 @@
 """Parity with the FP64 oracle at the largest matrix size the kernels take,
 N = 120 (one spin block of 60 orbitals): the torus at N_phi = 60 (N_q = 553)
 and the 60-orbital sphere of the benchmark's learned-proposal workload
-(N_q = 3600, Methods Eq. sphere_density_operator).  At this size the LU keeps
+(N_q = 3600, Methods Eq. sphere_density_operator) at its coupling u = 1.2
+and at a strong coupling.  At this size the LU keeps
 its matrix at row stride n, QR with pivoting keeps only the matrix and the
 Householder vector in shared memory, and the right division stages its
 factors in row chunks.  The oracle chains run in spawned workers while the
@@ -15,23 +16,27 @@ import pytest
 
 from oracle import model as M
 from tests import oracle_runs as R
+from tests.sphere_units import sphere_u
 
 pytestmark = pytest.mark.gpu
 
 TORUS = dict(size=60, beta=1.0, u=1.0, anis=0.1, seed=2, n_stab=5, eps0=0.3, nsw=2)
-# the paper's sphere couplings (u <= 0.3): at u = 1.2 the sphere's larger
-# form factors make B ill-conditioned and two FP64 evaluation orders of the
-# same ratio already differ by ~1e-8 (see test_gpu_sphere.py)
-SPHERE = dict(size=60, beta=1.0, u=0.3, anis=0.0, seed=3, n_stab=5, eps0=0.3, nsw=1)
+# the sphere at the workload's coupling u = 1.2 (torus-matched form factors),
+# and at a strong coupling, 4 pi^2 n_orb * 0.3 (tests/sphere_units.py), where
+# B is ill-conditioned
+SPHERE_W = dict(size=60, beta=1.0, u=1.2, anis=0.0, seed=3, n_stab=5, eps0=0.3, nsw=1)
+SPHERE = dict(size=60, beta=1.0, u=sphere_u(0.3, 60), anis=0.0, seed=3, n_stab=5, eps0=0.3,
+              nsw=1)
+CASES = {"torus": (M.TORUS, TORUS), "sphere": (M.SPHERE, SPHERE), "sphere_w": (M.SPHERE, SPHERE_W)}
 
 
 @pytest.fixture(scope="module")
 def oracle_results():
     from oracle import oracle as O
     O.build()
-    pool = mp.get_context("spawn").Pool(2)
+    pool = mp.get_context("spawn").Pool(3)
     jobs = {}
-    for key, geom, c in (("torus", M.TORUS, TORUS), ("sphere", M.SPHERE, SPHERE)):
+    for key, (geom, c) in CASES.items():
         jobs[key] = pool.apply_async(R.plain_chain, (geom, c["size"], c["beta"], 0.1, c["u"],
                                                      c["anis"], c["seed"], c["n_stab"],
                                                      c["eps0"], c["nsw"]))
@@ -75,17 +80,19 @@ def _gpu(qmc, geom, c, precision):
     return g
 
 
-# (geometry, log R tolerance relative to max(1, |log R|), G tolerance,
-# restabilisation drift bound).  On the 60-orbital sphere G(tau) has
-# condition number ~2e11 even at u = 0.3: the oracle's stable ratio and its
-# brute-force determinant ratio of the same proposal differ by 3e-7 .. 5e-7
-# there, so two FP64 evaluation orders cannot agree better; the torus at the
-# same N is well conditioned.
+# (case, log R tolerance relative to max(1, |log R|), G tolerance,
+# restabilisation drift bound).  On the 60-orbital sphere at the strong
+# coupling G(tau) has condition number ~2e11: the oracle's stable ratio and
+# its brute-force determinant ratio of the same proposal differ by
+# 3e-7 .. 5e-7 there, so two FP64 evaluation orders cannot agree better; the
+# torus and the sphere at the workload's coupling are well conditioned.
 @pytest.mark.parametrize("geom_name,tol_logr,tol_g,tol_stab", [("torus", 1e-10, 1e-9, 1e-9),
+                                                               ("sphere_w", 1e-10, 1e-9, 1e-9),
                                                                ("sphere", 1e-6, 1e-5, 1e-4)])
 def test_fp64_decision_identical_at_n120(qmc, oracle_results, geom_name, tol_logr, tol_g,
                                          tol_stab):
-    geom, c = ((qmc.QMC_TORUS, TORUS) if geom_name == "torus" else (qmc.QMC_SPHERE, SPHERE))
+    geom = qmc.QMC_TORUS if geom_name == "torus" else qmc.QMC_SPHERE
+    c = CASES[geom_name][1]
     g = _gpu(qmc, geom, c, 0)
     o = oracle_results(geom_name)
     tg, to = g.trace(0), o["trace"]
@@ -101,9 +108,11 @@ def test_fp64_decision_identical_at_n120(qmc, oracle_results, geom_name, tol_log
     assert obs[:, 15].max() < tol_stab
 
 
-def test_tensor_core_precision_tracks_the_oracle_at_n120(qmc, oracle_results):
-    g = _gpu(qmc, qmc.QMC_TORUS, TORUS, 2)
-    o = oracle_results("torus")
+@pytest.mark.parametrize("geom_name", ["torus", "sphere_w"])
+def test_tensor_core_precision_tracks_the_oracle_at_n120(qmc, oracle_results, geom_name):
+    geom = qmc.QMC_TORUS if geom_name == "torus" else qmc.QMC_SPHERE
+    g = _gpu(qmc, geom, CASES[geom_name][1], 2)
+    o = oracle_results(geom_name)
     tg, to = g.trace(0), o["trace"]
     mis = np.nonzero(tg[:, 6] != to[:, 6])[0]
     first = int(mis[0]) if len(mis) else len(tg)

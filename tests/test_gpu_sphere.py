@@ -5,15 +5,19 @@ The GPU builds the form factors from Clebsch-Gordan coefficients by the
 lowering-operator recursion in double-double arithmetic; the oracle from the
 Racah formula in exact rational arithmetic.  Same seeds and Philox streams:
 identical accept/reject decisions, log ratios within 1e-10 relative to
-max(1, |log R|) at the paper's sphere couplings, G and the measurements
+max(1, |log R|) (1e-7 at the strongest coupling), G and the measurements
 within 1e-9; propagators of the same fields equal to 1e-12 up to 60 orbitals, where
-an FP64 recursion would already have lost every digit.
+an FP64 recursion would already have lost every digit.  The form factors
+carry the torus's normalisation (1/(2 pi sqrt(n_orb)) times the printed
+expression), so the paper's couplings behave as on the torus; strong-coupling
+cases take u scaled by 4 pi^2 n_orb.
 """
 import numpy as np
 import pytest
 
 from oracle import model as M
 from oracle import oracle as O
+from tests.sphere_units import sphere_u
 
 pytestmark = pytest.mark.gpu
 
@@ -33,14 +37,17 @@ def _rel(a, b):
 
 
 # (orbitals, beta, sweeps, coupling u, anisotropy, bound on the relative log-ratio
-# difference).  The sphere form factors are ~15x the torus ones, so u = 1.2
-# makes B far worse conditioned: G(0) of identical propagators (1e-14) already
-# differs by ~1e-12 between two FP64 evaluation orders, and the ratios by
-# ~1e-8.  The paper's sphere runs use u <= 0.3, where the bound is 1e-10.
-@pytest.mark.parametrize("norb,beta,nsw,u,aniso,tol", [(3, 2.0, 100, 0.3, 0.0, 1e-10),
-                                                       (4, 1.0, 60, 0.3, 0.15, 1e-10),
-                                                       (7, 0.6, 12, 0.3, -0.1, 1e-10),
-                                                       (7, 0.6, 12, 1.2, -0.1, 1e-7)])
+# difference).  The paper's couplings (u = 0.3, the workload's 1.2) at the
+# torus-matched normalisation, and strong couplings (tests/sphere_units.py):
+# at 4 pi^2 n_orb * 1.2 B is far worse conditioned, G(0) of identical
+# propagators (1e-14) already differs by ~1e-12 between two FP64 evaluation
+# orders, and the ratios by ~1e-8.
+@pytest.mark.parametrize("norb,beta,nsw,u,aniso,tol", [
+    (3, 2.0, 100, 0.3, 0.0, 1e-10),
+    (7, 2.0, 20, 1.2, 0.1, 1e-10),
+    (4, 1.0, 60, sphere_u(0.3, 4), sphere_u(0.15, 4), 1e-10),
+    (7, 0.6, 12, sphere_u(0.3, 7), sphere_u(-0.1, 7), 1e-10),
+    (7, 0.6, 12, sphere_u(1.2, 7), sphere_u(-0.1, 7), 1e-7)])
 def test_sphere_decision_identical(qmc, norb, beta, nsw, u, aniso, tol):
     L = int(round(beta / 0.1))
     g = qmc.Chain(qmc.QMC_SPHERE, norb - 1, beta, 0.1, u, aniso, 3, n_stab=5,
@@ -68,16 +75,20 @@ def test_sphere_decision_identical(qmc, norb, beta, nsw, u, aniso, tol):
     assert np.array_equal(obs_g[:, 17], obs_o[:, 17])
 
 
-# G(0) bound per orbital count: at 60 orbitals G is conditioned ~1e11 (two
-# FP64 evaluation orders of the same ratio differ by ~5e-7 there, see
-# test_gpu_large.py), so G from identical propagators agrees to ~1e-10 only
-@pytest.mark.parametrize("norb,tol_g", [(24, 1e-10), (56, 1e-10), (60, 1e-8)])
+# G(0) bound per orbital count at that coupling: G's conditioning grows with
+# the orbital count (~1e11 at 60, where two FP64 evaluation orders of the same
+# ratio differ by ~5e-7, see test_gpu_large.py), so G from identical
+# propagators agrees to 1e-10 at 24 orbitals, ~2e-10 at 56, ~1e-9 at 60
+@pytest.mark.parametrize("norb,tol_g", [(24, 1e-10), (56, 1e-9), (60, 1e-8)])
 def test_sphere_propagators_large_orbital_counts(qmc, norb, tol_g):
     """Propagators of identical fields: the GPU form factors carry the exact
-    rational values of the oracle to rounding."""
-    g = qmc.Chain(qmc.QMC_SPHERE, norb - 1, 0.2, 0.1, 1.0, 0.0, 5, n_stab=2)
+    rational values of the oracle to rounding.  Strong coupling
+    (4 pi^2 n_orb), so that the form factors' part of B is O(1) and their
+    rounding shows in B."""
+    u = sphere_u(1.0, norb)
+    g = qmc.Chain(qmc.QMC_SPHERE, norb - 1, 0.2, 0.1, u, 0.0, 5, n_stab=2)
     m = M.Model(M.SPHERE, norb)
-    o = O.Chain(M.SPHERE, norb, 0.2, 0.1, 1.0, 0.0, 5, n_stab=2, model=m)
+    o = O.Chain(M.SPHERE, norb, 0.2, 0.1, u, 0.0, 5, n_stab=2, model=m)
     assert np.abs(g.fields(0) - o.phi()).max() < 1e-13
     for t in (1, 2):
         B, Bi = g.propagator(t)

@@ -16,6 +16,7 @@ import scipy.stats as st
 
 from oracle import model as M
 from oracle import oracle as O
+from tests.sphere_units import sphere_u
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -113,17 +114,36 @@ def test_wigner3j_matches_sympy():
 
 @pytest.mark.parametrize("norb", [3, 4, 7])
 def test_sphere_F00_closed_form_and_rotation_invariance(norb):
-    """F_{0,0} = (-1)^{2s}/2 * identity; sum_m F_{l,m} F_{l,m}^dagger is
-    proportional to the identity for every l (rotation invariance, the
-    addition theorem for the monopole-harmonic matrix elements)."""
+    """F_{0,0} = (-1)^{2s} I / (4 pi sqrt(n_orb)), the torus's q = 0 table
+    (the printed (-1)^{2s} I / 2 times the normalisation 1/(2 pi sqrt(n_orb)));
+    sum_m F_{l,m} F_{l,m}^dagger is proportional to the identity for every l
+    (rotation invariance, the addition theorem for the monopole-harmonic
+    matrix elements)."""
     m = M.Model(M.SPHERE, norb)
     s2 = norb - 1
     F00 = m.dense_F(m.qs.index((0, 0)))
-    assert np.abs(F00 - ((-1) ** s2) * 0.5 * np.eye(norb)).max() < 1e-14
+    assert np.abs(F00 - ((-1) ** s2) / (4 * math.pi * math.sqrt(norb)) * np.eye(norb)).max() < 1e-15
     for l in range(norb):
         S = sum(m.dense_F(m.qs.index((l, mm))) @ m.dense_F(m.qs.index((l, mm))).conj().T
                 for mm in range(-l, l + 1))
         assert np.abs(S - S[0, 0] * np.eye(norb)).max() < 1e-12 * max(1, abs(S[0, 0]))
+
+
+@pytest.mark.parametrize("norb", [2, 5, 8])
+def test_sphere_weight_per_orbital_matches_the_torus(norb):
+    """sum_q ||F_q||_F^2 / n_orb = 1/(16 pi^2) exactly on the sphere: for each
+    l, sum_m of the squared 3j symbols (s l s; -m_k -m m_k+m) over the pairs
+    is 1/(2s+1) per row (3j orthogonality), and sum_l (2l+1)
+    (s l s; -s 0 s)^2 = 1.  On the torus the same sum is
+    sum_q pref(q)^2 = 1/(16 pi^2) up to the cut of the Gaussian (~1e-4 at
+    N_phi >= 8), so both geometries carry the same weight per orbital at
+    every size."""
+    m = M.Model(M.SPHERE, norb)
+    w = sum(np.linalg.norm(m.dense_F(q)) ** 2 for q in range(m.nq)) / norb
+    assert abs(w * 16 * math.pi ** 2 - 1) < 1e-13
+    t = M.Model(M.TORUS, 4 * norb)
+    wt = sum(np.linalg.norm(t.dense_F(q)) ** 2 for q in range(t.nq)) / t.norb
+    assert abs(wt * 16 * math.pi ** 2 - 1) < 1e-3
 
 
 def test_background_is_half_the_four_flavour_trace():
@@ -255,7 +275,7 @@ def test_determinant_equals_fock_trace_and_is_real(u, al):
     assert abs(math.sin(ref.imag)) < 1e-10
 
 
-@pytest.mark.parametrize("geom,size,u,al", [(M.TORUS, 4, 5.0, 0.3), (M.TORUS, 3, 0.5, -0.2), (M.SPHERE, 3, 1.0, 0.1)])
+@pytest.mark.parametrize("geom,size,u,al", [(M.TORUS, 4, 5.0, 0.3), (M.TORUS, 3, 0.5, -0.2), (M.SPHERE, 3, sphere_u(1.0, 3), sphere_u(0.1, 3))])
 def test_weight_is_sign_free_on_random_fields(geom, size, u, al):
     for seed in range(3):
         ch = O.Chain(geom, size, 1.0, 0.1, u, al, seed=seed)
@@ -264,7 +284,7 @@ def test_weight_is_sign_free_on_random_fields(geom, size, u, al):
 
 
 # ---------------------------------------------------------- derivatives ---
-@pytest.mark.parametrize("geom,size,u,al,t", [(M.TORUS, 2, 2.0, 0.3, 2), (M.TORUS, 4, 1.0, 0.0, 3), (M.SPHERE, 2, 1.0, 0.2, 1)])
+@pytest.mark.parametrize("geom,size,u,al,t", [(M.TORUS, 2, 2.0, 0.3, 2), (M.TORUS, 4, 1.0, 0.0, 3), (M.SPHERE, 2, sphere_u(1.0, 2), sphere_u(0.2, 2), 1)])
 def test_gradient_matches_finite_differences(geom, size, u, al, t):
     ch = O.Chain(geom, size, 0.5, 0.1, u, al, seed=11)
     g = ch.gradient(t)
@@ -308,7 +328,7 @@ def test_stabilised_green_matches_brute_force_and_stays_fresh():
     assert np.abs(ch.green() - ch.green_bruteforce(ch.L)).max() < 1e-11
     assert obs[:, 15].max() < 1e-9          # |G_wrap - G_stable| / max|G|
     # long beta: stabilisation keeps the wrapped G within 1e-9 of a fresh one
-    ch2 = O.Chain(M.SPHERE, 3, 20.0, 0.1, 1.0, 0.0, seed=1, n_stab=10)
+    ch2 = O.Chain(M.SPHERE, 3, 20.0, 0.1, sphere_u(1.0, 3), 0.0, seed=1, n_stab=10)
     obs2 = ch2.sweep(1)
     assert obs2[:, 15].max() < 1e-8
     assert obs2[:, 16].max() < 1e-8

@@ -14,6 +14,7 @@ from oracle import analysis as A
 from oracle import ed as E
 from oracle import model as M
 from oracle import oracle as O
+from tests.sphere_units import sphere_u
 
 
 def _mean_err(x, nb=25):
@@ -35,7 +36,7 @@ def _compare(geom, size, u, al, beta, dtau, nsw, seed, g=None):
     return out, obs
 
 
-@pytest.mark.parametrize("geom,size,u,al", [(M.TORUS, 2, 4.0, 0.3), (M.SPHERE, 2, 1.0, 0.2)])
+@pytest.mark.parametrize("geom,size,u,al", [(M.TORUS, 2, 4.0, 0.3), (M.SPHERE, 2, sphere_u(1.0, 2), sphere_u(0.2, 2))])
 def test_monte_carlo_matches_exact_diagonalisation(geom, size, u, al):
     dev, obs = _compare(geom, size, u, al, beta=2.0, dtau=0.05, nsw=2500, seed=1)
     for k, z in dev.items():

@@ -16,6 +16,7 @@ import pytest
 from oracle import ed as E
 from oracle import model as M
 from oracle import oracle as O
+from tests.sphere_units import sphere_u
 
 
 def _chain(beta=1.0, dtau=0.1, u=2.0, al=0.2, seed=3, g=None):
@@ -196,14 +197,16 @@ def test_stabilisation_point_scheme(nphi, beta, nstab):
 
 
 def test_sphere_time_displaced_structure_factor_matches_ed():
-    """Sphere n_orb = 2, u = 1, alpha = 0.2, beta = 2, dtau = 0.05: Monte
+    """Sphere n_orb = 2, u = 79, alpha = 15.8 (strong coupling, tests/sphere_units.py),
+    beta = 2, dtau = 0.05: Monte
     Carlo S^1_0(tau) and S^3_0(tau) (l = 0) at tau = 0.1 and 0.25 within 4
     sigma of ED (the sphere's form factors in the time-displaced Wick
     contractions)."""
     m = M.Model(M.SPHERE, 2)
     beta, dtau = 2.0, 0.05
-    ed = E.ED(m, M.couplings(1.0, 0.2), beta)
-    ch = O.Chain(M.SPHERE, 2, beta, dtau, 1.0, 0.2, seed=7, n_stab=5, n_adapt=150, model=m)
+    us, als = sphere_u(1.0, 2), sphere_u(0.2, 2)
+    ed = E.ED(m, M.couplings(us, als), beta)
+    ch = O.Chain(M.SPHERE, 2, beta, dtau, us, als, seed=7, n_stab=5, n_adapt=150, model=m)
     ch.sweep(150)
     taus = [2, 5]
     rec = []

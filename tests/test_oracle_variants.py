@@ -16,6 +16,7 @@ from oracle import ed as E
 from oracle import model as M
 from oracle import oracle as O
 from tests.test_oracle_pins import _bilinear, _jw
+from tests.sphere_units import sphere_u
 
 OV = [np.eye(2), np.array([[0, 1], [1, 0]]), np.array([[0, -1j], [1j, 0]]), np.diag([1, -1])]
 ORDER = [(0, .5), (1, .5), (2, .5), (3, 1.0), (2, .5), (1, .5), (0, .5)]
@@ -69,7 +70,7 @@ def test_determinant_equals_fock_trace_and_is_real(kind, u, al):
 
 
 @pytest.mark.parametrize("kind", [O.SLICE_SINGLE, O.SLICE_INDEP])
-@pytest.mark.parametrize("geom,size,u,al", [(M.TORUS, 4, 5.0, 0.3), (M.SPHERE, 3, 1.0, 0.1)])
+@pytest.mark.parametrize("geom,size,u,al", [(M.TORUS, 4, 5.0, 0.3), (M.SPHERE, 3, sphere_u(1.0, 3), sphere_u(0.1, 3))])
 def test_variants_are_sign_free_on_random_fields(kind, geom, size, u, al):
     for seed in range(3):
         ch = O.Chain(geom, size, 1.0, 0.1, u, al, seed=seed, slice_kind=kind)
@@ -81,7 +82,7 @@ def _action(ch):
 
 
 @pytest.mark.parametrize("kind", [O.SLICE_SINGLE, O.SLICE_INDEP])
-@pytest.mark.parametrize("geom,size,u,al,t", [(M.TORUS, 2, 2.0, 0.3, 2), (M.SPHERE, 2, 1.0, 0.2, 1)])
+@pytest.mark.parametrize("geom,size,u,al,t", [(M.TORUS, 2, 2.0, 0.3, 2), (M.SPHERE, 2, sphere_u(1.0, 2), sphere_u(0.2, 2), 1)])
 def test_exact_drift_matches_finite_differences(kind, geom, size, u, al, t):
     ch = O.Chain(geom, size, 0.5, 0.1, u, al, seed=11, slice_kind=kind)
     g = ch.gradient(t)
