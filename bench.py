@@ -11,8 +11,11 @@ Two arms run in one invocation on the same GPU:
   * the headline path (default --mode prior --precision 2): mixed precision
     with whole-slice sweeps around the Gaussian prior (accepted by the exact
     determinant ratio; their proposals' propagators computed ahead in
-    batches, with the batched products on the tensor cores) and a Langevin
-    sweep every 4th step;
+    batches, with the batched products on the tensor cores); a Langevin
+    sweep every n-th step is the fallback (--langevin-every n, fixed: a
+    choice of move that depends on the chain's own acceptances would not
+    leave the target invariant), off by default since the whole-slice
+    acceptance is 0.63 here;
   * the plain FP64 Langevin sweep (--precision 0 --mode plain), the
     comparison the metric names.
 Each arm: W warm-up sweeps, K timed sweeps (CUDA events on the library's
@@ -67,8 +70,22 @@ TRAFFIC_PER_LAUNCH = 1338624
 # oracle sample: one sweep of an L_SAMPLE-slice chain at the same N_phi, one
 # process per chain, scaled to L = 360
 L_SAMPLE = 10
-# learned mode: one Langevin sweep per LANGEVIN_EVERY steps
-LANGEVIN_EVERY = 4
+# whole-slice modes: one Langevin sweep per LANGEVIN_EVERY steps (0: none;
+# --langevin-every)
+LANGEVIN_EVERY = 0
+
+
+def langevin_step(k):
+    """True if step k of a whole-slice schedule is a Langevin sweep."""
+    return LANGEVIN_EVERY > 0 and k % LANGEVIN_EVERY == LANGEVIN_EVERY - 1
+
+
+def schedule_text(kind):
+    if LANGEVIN_EVERY == 0:
+        return f"{kind} whole-slice sweeps (rho 0) only"
+    if LANGEVIN_EVERY == 1:
+        return "Langevin sweeps only"
+    return f"{kind} whole-slice sweeps (rho 0), every {LANGEVIN_EVERY}th step a Langevin sweep"
 
 
 def workload_config(extra=None):
@@ -279,7 +296,7 @@ def run_arm(P, stream, *, mode, precision, drift, seeds, steps, warmup, tau_swee
     ch.set_stream(stream.cuda_stream)
     # prior mode (default): whole-slice moves around the Gaussian part of
     # the action (rho = 0), accepted by the exact determinant ratio, with a
-    # Langevin sweep every LANGEVIN_EVERY-th step; learned mode: the same
+    # Langevin sweep every LANGEVIN_EVERY-th step if set; learned mode: the same
     # schedule with the network's Gaussian (at its initialisation mu = 0,
     # sigma = 1 it proposes what the prior move does, at the cost of its
     # forward pass: training on thinned plain-chain configurations never
@@ -287,7 +304,7 @@ def run_arm(P, stream, *, mode, precision, drift, seeds, steps, warmup, tau_swee
     net = P.Net(4 * ch.n_q, 256, 16, 1 + int(seeds[0])) if mode == "learned" else None
 
     def is_langevin(k):
-        return mode == "plain" or k % LANGEVIN_EVERY == LANGEVIN_EVERY - 1
+        return mode == "plain" or langevin_step(k)
 
     def step(k):
         if is_langevin(k):
@@ -335,7 +352,8 @@ def run_arm(P, stream, *, mode, precision, drift, seeds, steps, warmup, tau_swee
     timed = series[:, :steps, :]
     learned_steps = [j for j in range(series.shape[1]) if not is_langevin(warmup + j)]
     acc_learned = float(series[:, learned_steps, 13].mean()) if learned_steps else None
-    acc_langevin = float(np.delete(series[:, :, 13], learned_steps, axis=1).mean())
+    lang = np.delete(series[:, :, 13], learned_steps, axis=1)
+    acc_langevin = float(lang.mean()) if lang.size else None
     out = {"ch": ch, "net": net, "mode": mode, "ms": ms, "step_s": ms / 1000.0 / steps, "taus": taus,
            "series_len": int(series.shape[1]), "launches": int(launches), "clocks": clk,
            "wall_e2e": wall_e2e, "g_err_max": float(timed[:, :, 15].max()),
@@ -505,8 +523,7 @@ def run_ours(args):
                                    "mode": args.mode,
                                    "drift": args.drift,
                                    "schedule": ("plain Langevin sweeps" if args.mode == "plain" else
-                                                f"{args.mode} whole-slice sweeps (rho 0), every "
-                                                f"{LANGEVIN_EVERY}th step a Langevin sweep"),
+                                                schedule_text(args.mode)),
                                    "launch": "graph-replayed sweeps",
                                    "acceptance_whole_slice": main["acc_learned"],
                                    "acceptance_langevin": main["acc_langevin"],
@@ -619,8 +636,8 @@ def run_batched(args):
 
 def run_sphere(args):
     """The 60-orbital sphere (N = 120, N_q = 3600), beta = 40 (L = 400),
-    u = 1.2, one chain: prior whole-slice sweeps at rho = 0 with a Langevin
-    sweep every 4th step, as the headline path."""
+    u = 1.2, one chain: prior whole-slice sweeps at rho = 0 in the headline
+    path's schedule."""
     import torch
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     from paper_2605_03700_gb300 import build as B
@@ -629,13 +646,13 @@ def run_sphere(args):
     stream = torch.cuda.Stream()
     u = args.sphere_u
     workload = (f"sphere, 60 orbitals (N=120, N_q=3600), beta=40, dtau=0.1 (L=400), u={u}, one "
-                "chain, prior whole-slice sweeps (rho 0) with a Langevin sweep every 4th step")
+                f"chain, {schedule_text('prior')}")
     ch = P.Chain(P.QMC_SPHERE, 59, 40.0, DTAU, u, 0.0, 0, n_stab=NSTAB, eps0=0.2,
                  precision=args.precision, series_capacity=4096,
                  sign_tol=args.sphere_sign_tol)
     ch.set_stream(stream.cuda_stream)
     def step(k):
-        if k % LANGEVIN_EVERY == LANGEVIN_EVERY - 1:
+        if langevin_step(k):
             ch.sweep(1, graph=True)
         else:
             ch.sweep_prior(1, 0.0, graph=True)
@@ -694,7 +711,7 @@ def run_torus140(args):
     """The paper's largest torus: N_phi = 140 (N = 280, N_q = 1305), beta =
     70 (L = 700), u = 1, anisotropy 0.1, eight chains (seeds 0-7), n_stab =
     10, mixed precision (default: the tensor-core products, precision 2),
-    prior whole-slice sweeps with a Langevin sweep every 4th step.  A sweep
+    prior whole-slice sweeps in the headline path's schedule.  A sweep
     takes seconds, so a run times a few steps; tau_int is not resolved in
     that window and the line reports chain-sweeps/s with ESS/s from the
     short series."""
@@ -711,7 +728,7 @@ def run_torus140(args):
     ch.set_stream(stream.cuda_stream)
 
     def step(k):
-        if k % LANGEVIN_EVERY == LANGEVIN_EVERY - 1:
+        if langevin_step(k):
             ch.sweep(1, graph=True)
         else:
             ch.sweep_prior(1, 0.0, graph=True)
@@ -739,8 +756,8 @@ def run_torus140(args):
             "vs_baseline": None, "dtype": ["f64", "f32+f64", "f32+f64+bf16-digits"][prec],
             "data": "synthetic",
             "config": {"workload": "torus N_phi=140 (N=280, N_q=1305), beta=70, dtau=0.1 (L=700), "
-                                   "u=1, anisotropy 0.1, 8 chains seeds 0-7, n_stab=10, prior "
-                                   "whole-slice sweeps, every 4th a Langevin sweep",
+                                   "u=1, anisotropy 0.1, 8 chains seeds 0-7, n_stab=10, "
+                                   + schedule_text("prior"),
                        "precision": prec, "chain_sweeps_per_s": NCH * args.steps / (ms / 1000),
                        "value_err": dv, "tau_series_len": int(s.shape[1]),
                        "acceptance": float(s[:, :, 13].mean()),
@@ -773,15 +790,19 @@ def main():
                          "prior-move proposals) on the tcgen05 tensor cores from FP64-exact "
                          "bfloat16 digits")
     ap.add_argument("--mode", default="prior", choices=["prior", "learned", "plain"],
-                    help="prior: whole-slice moves around the Gaussian prior with a Langevin "
-                         "sweep every 4th step; learned: the same schedule with the network's "
-                         "Gaussian; plain: Langevin sweeps only")
+                    help="prior: whole-slice moves around the Gaussian prior (with a Langevin "
+                         "sweep every --langevin-every steps); learned: the same schedule with "
+                         "the network's Gaussian; plain: Langevin sweeps only")
     ap.add_argument("--drift", default="exact", choices=["exact", "first"],
                     help="Langevin drift: exact grad S, or the first-order drift (factors "
                          "treated as commuting; same target, no derivative chain)")
     ap.add_argument("--beta", type=float, default=BETA,
                     help="override beta (shorter imaginary-time axis, same kernels and matrix "
                          "sizes; used for profiler launch lists)")
+    ap.add_argument("--langevin-every", type=int, default=LANGEVIN_EVERY,
+                    help="whole-slice schedules: a Langevin sweep every n-th step, the fallback "
+                         "where whole-slice acceptance is low (0, default: whole-slice sweeps "
+                         "only; 1: Langevin only)")
     ap.add_argument("--sphere-u", type=float, default=1.2,
                     help="coupling of --workload sphere60 (the workload's 1.2; the paper's sphere "
                          "scans use 0.075 .. 0.3)")
@@ -796,6 +817,9 @@ def main():
                          "largest torus, N_phi = 140")
     args = ap.parse_args()
     globals()["BETA"] = args.beta
+    if args.langevin_every < 0:
+        ap.error("--langevin-every must be >= 0")
+    globals()["LANGEVIN_EVERY"] = args.langevin_every
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

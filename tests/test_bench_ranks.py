@@ -54,3 +54,14 @@ def test_single_process_needs_no_collective():
     import bench
     assert bench.combine_over_ranks(None, 1.5, 2.0, 3.0, "cpu") == (1.5, 2.0, 3.0)
     assert np.array_equal(bench.replica_seeds(0), np.arange(8))
+
+
+def test_whole_slice_schedule(monkeypatch):
+    """--langevin-every n: a Langevin sweep at steps n-1, 2n-1, ...; 0 never
+    (the default), 1 always."""
+    import bench
+    for n, want in ((0, []), (1, list(range(8))), (4, [3, 7]), (3, [2, 5])):
+        monkeypatch.setattr(bench, "LANGEVIN_EVERY", n)
+        assert [k for k in range(8) if bench.langevin_step(k)] == want
+    monkeypatch.setattr(bench, "LANGEVIN_EVERY", 0)
+    assert "only" in bench.schedule_text("prior")
