@@ -12,14 +12,25 @@ worker processes while the GPU works.
      log R within 1e-10, G within 1e-9 of max|G| after every sweep.
  (b) Mixed precision (FP32 drift transforms, FP32 Jacobi bulk with FP64
      refinement; everything in the MH ratio FP64-accurate), on the CUDA
-     cores (precision 1) and with the dense products on the tensor cores
-     (precision 2): the index of the first decision that differs from the
+     cores (precision 1) and in precision 2 (whose products at these batch
+     sizes stay below the tensor-core threshold; (d) moves them all onto
+     the tensor cores): the index of the first decision that differs from the
      oracle, and G against the oracle after every sweep up to it, within
      1e-6 (the G-error target of mixed runs).
- (c) The benchmark's default path: mixed precision, learned sweeps at
-     rho = 0 with a seeded non-zero network of the benchmark's width (256),
-     every fourth sweep a Langevin sweep, in both mixed modes.
+ (c) Learned sweeps at rho = 0 with a seeded non-zero network of the
+     benchmark's width (256), every fourth sweep a Langevin sweep, in both
+     mixed modes.
+ (d) The benchmark's default schedule: whole-slice moves around N(0, 1)
+     only, their proposals computed ahead in batches (qmc_sweep_prior,
+     graph-replayed), in FP64 (decision-identical, log R 1e-10, G 1e-9) and
+     in precision 2, once with the default tensor-core threshold (at L = 40
+     the stage's batches are small and stay on the CUDA cores) and once with
+     every product on the tensor cores (QMC_OZ_MIN_WORK=1, in a fresh
+     process): decisions tracking the oracle, G within 1e-6.
 """
+import os
+import subprocess
+import sys
 import multiprocessing as mp
 
 import numpy as np
@@ -50,10 +61,14 @@ def oracle_results():
     O.build()
     nf = 4 * 333
     ctx = mp.get_context("spawn")
-    pool = ctx.Pool(len(COUPLINGS) + 1)
+    pool = ctx.Pool(len(COUPLINGS) + 2)
     jobs = {("lang", c): pool.apply_async(R.langevin_chain,
                                           (NPHI, BETA, DTAU, u, 0.0, c, NSTAB, EPS0, NSW))
             for c, u in enumerate(COUPLINGS)}
+    from oracle import model as M
+    jobs[("prior", 0)] = pool.apply_async(
+        R.plain_chain, (M.TORUS, NPHI, BETA, DTAU, 1.25, 0.0, 5, NSTAB, EPS0, NSW),
+        dict(schedule="0" * NSW))
     jobs[("sched", 0)] = pool.apply_async(
         R.scheduled_chain, (NPHI, BETA, DTAU, 1.25, 0.0, 5, NSTAB, EPS0, SCHEDULE,
                             _theta(nf), NET_H, 0.0))
@@ -172,3 +187,52 @@ def test_learned_schedule_tracks_the_oracle_at_benchmark_size(qmc, oracle_result
         assert _rel(greens[k], o["green"][k]) < 1e-6
     obs_g = g.series()[0]
     assert np.array_equal(obs_g[:nsw_same, 17], o["obs"][:nsw_same, 17])
+
+
+PRIOR_RUN = """
+import sys
+import numpy as np
+sys.path.insert(0, ".")
+from paper_2605_03700_gb300 import build
+build.build()
+import paper_2605_03700_gb300 as P
+prec, nsw, path = int(sys.argv[1]), int(sys.argv[2]), sys.argv[3]
+g = P.Chain(P.QMC_TORUS, 36, 4.0, 0.1, 1.25, 0.0, 5, n_stab=10, eps0=0.45, precision=prec,
+            trace_capacity=nsw * 40)
+g.sweep_prior(nsw, 0.0, graph=True)
+g.sync()
+np.savez(path, trace=g.trace(0), green=g.green(0), phi=g.fields(0), obs=g.series()[0])
+"""
+
+
+@pytest.mark.parametrize("precision,min_work", [(0, None), (2, None), (2, "1")])
+def test_default_schedule_tracks_the_oracle_at_benchmark_size(oracle_results, tmp_path,
+                                                             precision, min_work):
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ)
+    env.pop("QMC_OZ_MIN_WORK", None)
+    if min_work is not None:
+        env["QMC_OZ_MIN_WORK"] = min_work
+    path = str(tmp_path / "prior.npz")
+    r = subprocess.run([sys.executable, "-c", PRIOR_RUN, str(precision), str(NSW), path], cwd=root,
+                       env=env, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stderr[-3000:]
+    g = np.load(path)
+    o = oracle_results(("prior", 0))
+    tg, to = g["trace"], o["trace"]
+    assert len(tg) == len(to) == NSW * 40
+    assert 0 < to[:, 6].sum() < len(to)
+    if precision == 0:
+        assert np.array_equal(tg[:, 6], to[:, 6]), "accept decisions differ"
+        assert (np.abs(tg[:, 2] - to[:, 2]) / np.maximum(1, np.abs(to[:, 2]))).max() < 1e-10
+        assert _rel(g["green"], o["green"]) < 1e-9
+        assert np.abs(g["phi"] - o["phi"]).max() < 1e-9
+        assert np.array_equal(g["obs"][:, 17], o["obs"][:, 17])
+        return
+    mis = np.nonzero(tg[:, 6] != to[:, 6])[0]
+    first = int(mis[0]) if len(mis) else len(tg)
+    assert first >= 200, f"decisions diverge at update {first}"
+    assert (np.abs(tg[:first, 2] - to[:first, 2]) / np.maximum(1, np.abs(to[:first, 2]))).max() < 1e-6
+    if first == len(tg):
+        assert _rel(g["green"], o["green"]) < 1e-6
+        assert np.abs(g["phi"] - o["phi"]).max() < 1e-9
