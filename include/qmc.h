@@ -133,7 +133,10 @@ int qmc_default_opts(qmc_opts *o);
 
 /* Create a batch of chains on the current CUDA device.
  *   geometry   QMC_TORUS (magnetic torus, Methods Eq. torus_density_operator)
- *              or QMC_SPHERE (monopole sphere, Eq. sphere_density_operator)
+ *              or QMC_SPHERE (monopole sphere, Eq. sphere_density_operator,
+ *              scaled by 1/(2 pi sqrt(n_orb)) to the torus's normalisation:
+ *              F_{0,0} = (-1)^{2s} I / (4 pi sqrt(n_orb)) and
+ *              sum_q ||F_q||^2 = n_orb / (16 pi^2), as on the torus)
  *   N_phi      flux quanta; torus: N_phi orbitals and momenta
  *              {q in Z^2 : exp(-2 pi |q|^2/(4 N_phi)) > 0.01}; sphere:
  *              opts.n_orb_sphere orbitals (default N_phi + 1), N_q = n_orb^2
@@ -500,8 +503,8 @@ int qmc_cgemm(int M, int N, int K, int batch, const double *A, int opA, const do
  * columns carry log scales c (or none): the decomposition of the
  * stabilisation stacks (Methods, Eq. green_function_methods: the UDV form of
  * the slice products), with D in log form d so that the products' singular
- * values may leave FP64's exponent range (they reach e^{~10^4} on the
- * 60-orbital sphere at beta = 40).  Q unitary, V = D^-1 R P^T with
+ * values may leave FP64's exponent range (they grow like e^{c beta u}
+ * with the slice count and the coupling).  Q unitary, V = D^-1 R P^T with
  * X diag(e^c) P = Q R, formed without forming X diag(e^c).  For n <= 128 the
  * columns are ordered by log |x_j| + c_j once (ties by index) and factored
  * by blocked Householder QR over a cluster of CTAs; larger n, or

@@ -2,8 +2,8 @@
 (qmc_udv) against its definition, on random matrices, on column-graded ones
 (scales e^-120 .. e^120 in X itself) and with column log scales passed as
 log_scale, shifted far beyond FP64's exponent range (the stacks carry their D
-this way, since the slice products' singular values reach e^{~10^4} on the
-60-orbital sphere at beta = 40).
+this way, since the slice products' singular values grow like
+e^{c beta u} and leave FP64's range at large beta times coupling).
 
 For n <= 128 the columns are ordered by log |x_j| + c_j once and factored by
 blocked Householder QR over a cluster of CTAs; the column-pivoted one-CTA
