@@ -44,7 +44,7 @@ pytestmark = pytest.mark.gpu
 NPHI, BETA, DTAU, NSTAB, EPS0 = 36, 4.0, 0.1, 10, 0.45
 COUPLINGS = (0.5, 2.0)
 NSW = 10
-SCHEDULE = "NNNPNNNPNN"   # the benchmark's: every fourth step a Langevin sweep
+SCHEDULE = "NNNPNNNPNN"   # the benchmark's --langevin-every 4: every fourth step Langevin
 NET_H, NET_SEED = 256, 17
 
 
