@@ -1096,7 +1096,7 @@ __global__ void __launch_bounds__(256) k_lu_bc(int n, cd *A, long long sA, int *
     int *pv = (int *)(ud + n);                     // pivots of this CTA's panels, by global row
     __shared__ double red[2][8];
     __shared__ int nswr[8];
-    __shared__ cd s_pk, s_inv;
+    __shared__ cd s_inv;
     __shared__ int s_p, s_nsw;
     cd *Ab = A + (long long)b * sA;
     // local column lc <-> global column: panel q = (lc / LB) cs + rank
@@ -1140,7 +1140,6 @@ __global__ void __launch_bounds__(256) k_lu_bc(int n, cd *A, long long sA, int *
                         const int p = bidx;
                         const cd pk = Mb[p * ldw + lc];  // u_kk: the pivot row's entry
                         const double r = 1.0 / cabs2(pk);
-                        s_pk = pk;
                         s_inv = cmk(pk.x * r, -pk.y * r);
                         s_p = p;
                         pv[k] = p;
