@@ -2007,7 +2007,7 @@ int qrp_batched(cudaStream_t st, int n, const cd *X, long long sX, const double 
 // current device (once per context creation, never inside a stream capture)
 // the dynamic shared-memory limit `want` for kernel f, which must leave room
 // for the kernel's static arrays within the opt-in maximum; false if they do
-// not fit the bound the dispatch checks assume or the driver refuses it
+// not fit the bound the dispatch checks assume or the CUDA runtime refuses the attribute
 static bool set_dyn_smem(const void *f, size_t want)
 {
     cudaFuncAttributes fa;
