@@ -71,8 +71,9 @@ TRAFFIC_PER_LAUNCH = 1338624
 # process per chain, scaled to L = 360
 L_SAMPLE = 10
 # whole-slice modes: one Langevin sweep per LANGEVIN_EVERY steps (0: none;
-# --langevin-every)
+# --langevin-every); pCN correlation of the whole-slice moves (--rho)
 LANGEVIN_EVERY = 0
+RHO = 0.0
 
 
 def langevin_step(k):
@@ -82,10 +83,11 @@ def langevin_step(k):
 
 def schedule_text(kind):
     if LANGEVIN_EVERY == 0:
-        return f"{kind} whole-slice sweeps (rho 0) only"
+        return f"{kind} whole-slice sweeps (rho {RHO:g}) only"
     if LANGEVIN_EVERY == 1:
         return "Langevin sweeps only"
-    return f"{kind} whole-slice sweeps (rho 0), every {LANGEVIN_EVERY}th step a Langevin sweep"
+    return (f"{kind} whole-slice sweeps (rho {RHO:g}), every {LANGEVIN_EVERY}th step a Langevin "
+            "sweep")
 
 
 def workload_config(extra=None):
@@ -316,9 +318,9 @@ def run_arm(P, stream, *, mode, precision, drift, seeds, steps, warmup, tau_swee
         if is_langevin(k):
             ch.sweep(1, graph=graph)
         elif net is not None:
-            ch.sweep_learned(net, 1, 0.0, graph=graph)
+            ch.sweep_learned(net, 1, RHO, graph=graph)
         else:
-            ch.sweep_prior(1, 0.0, graph=graph)
+            ch.sweep_prior(1, RHO, graph=graph)
 
     pinned = torch.empty((steps, NCH, P.QMC_NOBS), dtype=torch.float64, pin_memory=True)
     for k in range(warmup):
@@ -372,19 +374,19 @@ def run_arm(P, stream, *, mode, precision, drift, seeds, steps, warmup, tau_swee
 def gemm_roofline_pass(P, arm, steps=2):
     """GEMM class rooflines in a separate, untimed pass: CUDA events around
     each FP64 CUDA-core GEMM launch and each tensor-core MMA launch of
-    `steps` further sweeps (eager launches, so each product has its own
-    event pair).  Returns (FP64 ms, launches, flops) and (tensor ms,
-    launches, needed flops, issued flops)."""
+    `steps` further sweeps of the arm's own schedule (eager launches, so
+    each product has its own event pair).  Returns (FP64 ms, launches,
+    flops) and (tensor ms, launches, needed flops, issued flops)."""
     ch, net, mode = arm["ch"], arm["net"], arm["mode"]
     P.qmc_profile_gemm(True)
     t0 = time.perf_counter()
     for k in range(steps):
-        if mode == "plain" or k % 2 == 1:
+        if mode == "plain" or langevin_step(k):
             ch.sweep(1)
         elif net is not None:
-            ch.sweep_learned(net, 1, 0.0)
+            ch.sweep_learned(net, 1, RHO)
         else:
-            ch.sweep_prior(1, 0.0)
+            ch.sweep_prior(1, RHO)
     ch.sync()
     ms, n, flops = P.qmc_profile_gemm(False)
     wall = time.perf_counter() - t0
@@ -661,7 +663,7 @@ def run_sphere(args):
         if langevin_step(k):
             ch.sweep(1, graph=True)
         else:
-            ch.sweep_prior(1, 0.0, graph=True)
+            ch.sweep_prior(1, RHO, graph=True)
     try:
         for k in range(args.warmup):
             step(k)
@@ -737,7 +739,7 @@ def run_torus140(args):
         if langevin_step(k):
             ch.sweep(1, graph=True)
         else:
-            ch.sweep_prior(1, 0.0, graph=True)
+            ch.sweep_prior(1, RHO, graph=True)
     for k in range(args.warmup):
         step(k)
     ch.sync()
@@ -809,6 +811,10 @@ def main():
                     help="whole-slice schedules: a Langevin sweep every n-th step, the fallback "
                          "where whole-slice acceptance is low (0, default: whole-slice sweeps "
                          "only; 1: Langevin only)")
+    ap.add_argument("--rho", type=float, default=RHO,
+                    help="pCN correlation of the whole-slice moves, 0 <= rho < 1 (0: independent "
+                         "proposals from the prior; rho > 0 keeps the move exact and raises its "
+                         "acceptance where it would collapse)")
     ap.add_argument("--sphere-u", type=float, default=1.2,
                     help="coupling of --workload sphere60 (the workload's 1.2; the paper's sphere "
                          "scans use 0.075 .. 0.3)")
@@ -826,6 +832,9 @@ def main():
     if args.langevin_every < 0:
         ap.error("--langevin-every must be >= 0")
     globals()["LANGEVIN_EVERY"] = args.langevin_every
+    if not 0.0 <= args.rho < 1.0:
+        ap.error("--rho must lie in [0, 1)")
+    globals()["RHO"] = args.rho
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
