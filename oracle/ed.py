@@ -17,7 +17,6 @@ This construction works directly with fermion operators on bit strings
 from __future__ import annotations
 
 import itertools
-import math
 
 import numpy as np
 

@@ -9,7 +9,6 @@ n_stab), batches of chains with different couplings, the full matrix size of
 the N_phi = 36 workload, and its full imaginary-time length on
 size-independent properties.
 """
-import math
 
 import numpy as np
 import pytest

@@ -4,12 +4,11 @@ closed forms, the optimiser's first step, the exactly solvable
 non-interacting limit, stationarity of N(0,1) there for any network, and
 agreement of the learned chain's observables with the Langevin chain."""
 import numpy as np
-import pytest
 
 from oracle import learned as LN
 from oracle import model as M
 from oracle import oracle as O
-from tests.learned_inputs import bf16_exact, random_batch, random_params
+from tests.learned_inputs import random_batch, random_params
 
 
 def test_gradient_matches_central_differences():
